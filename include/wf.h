@@ -1,0 +1,169 @@
+/*
+ * wf.h - C ABI of the GB300 quasi-implicit ADS wildfire time step.
+ *
+ * The library advances the temperature T and fuel phi of the reduced
+ * energy-balance wildfire model (paper Sec. 2, Eq. energy) on a 2-D
+ * tensor-product B-spline space of degree p (Sec. 3.1, "Matrix
+ * formulation": open uniform knots, n elements per direction, N = n + p
+ * coefficients per direction).  One time step is either
+ *
+ *   Peaceman-Rachford (Sec. 3.1, Eq. matrixPR):
+ *     (X(tau/2,+) (x) M^y) T*      = (M^x (x) Y(tau/2,-)) T^n + tau/2 F
+ *     (M^x (x) Y(tau/2,+)) T^{n+1} = (X(tau/2,-) (x) M^y) T*  + tau/2 F
+ *   or Strang splitting with Crank-Nicolson (Sec. 3.2, Eq. matrixCN),
+ *
+ * with X(theta,+-) = M^x +- theta (C_d K^x + c_W b_x G^x + c_chi M^x),
+ * Y(theta,+-) = M^y +- theta (C_d K^y + c_W b_y G^y), F the Gauss-quadrature
+ * load vector of the explicit nonlinear terms (Sec. 3, normalised form;
+ * Sec. 7 listing "compute_rhs") and the fuel advanced by the explicit Euler
+ * L2 projection of the same listing.  Every 2-D solve is done as
+ * independent 1-D banded solves along x and then along y (Sec. 4).
+ *
+ * Conventions common to every call
+ *  - Return value: WF_OK (0) on success, a negative WF_E* code on failure,
+ *    WF_PENDING (> 0) from wf_poll while a request runs.  wf_strerror()
+ *    names every code.  No call aborts the process.
+ *  - Host arrays are row-major [Ny][Nx] float64 with Nx = nx + p, x fastest.
+ *    The caller owns them; the library copies what it needs before
+ *    returning (or, for wf_step, never touches host memory).
+ *  - The library owns all device memory it allocates and one CUDA stream
+ *    per handle (or the caller's stream, see wf_set_stream).
+ *  - A handle is not thread-safe: one thread at a time per handle.  The
+ *    server object (wf_server_*) is thread-safe.
+ */
+#ifndef WF_H
+#define WF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define WF_OK 0
+#define WF_PENDING 1         /* wf_poll: request admitted or queued, not finished */
+#define WF_EINVAL (-1)       /* invalid argument */
+#define WF_ENOMEM (-2)       /* device allocation failed or HBM budget exhausted */
+#define WF_ESINGULAR (-3)    /* a 1-D operator had a pivot below 1e-300 * ||A|| */
+#define WF_EUNSTABLE (-4)    /* a temperature became non-finite or exceeded 1e5 K */
+#define WF_ETIMEOUT (-5)     /* a bounded device wait gave up */
+#define WF_ECUDA (-6)        /* a CUDA runtime call failed (no device, launch error, ...) */
+#define WF_ETRUNC (-7)       /* the chunked line solve could not reach its truncation tolerance */
+#define WF_ENOTFOUND (-8)    /* unknown request ticket */
+
+/* ---- choices ----------------------------------------------------------- */
+#define WF_PR 0              /* Peaceman-Rachford, Sec. 3.1 */
+#define WF_STRANG_CN 1       /* Strang splitting + Crank-Nicolson, Sec. 3.2 */
+#define WF_FP32 0            /* FP32 quadrature and substitution, FP64 1-D factorisation */
+#define WF_FP64 1            /* everything in FP64 (verification mode) */
+#define WF_F_ONCE 0          /* PR: F(T^n, phi^n) used in both substeps (default) */
+#define WF_F_PER_SUBSTEP 1   /* PR: F(T*, phi^n) in the second substep */
+
+/*
+ * Model parameters.  Defaults (wf_params_default) are the paper's Table
+ * "Model parameters" (Sec. 2.2) plus these readings: A_r = 1e-4,
+ * M/M_1 = 1, T_a = 300 K (exponent of the normalised form), heat scale
+ * 1e4 and fuel rate 300 (listing of Sec. 7), fuel threshold 0.2 with a
+ * 1e-6 guard, heat release not scaled by fuel.  Lx, Ly are the physical
+ * extents in metres; the mean wind (wind_x, wind_y) is treated
+ * implicitly in the 1-D operators.
+ */
+typedef struct wf_params {
+    double Lx, Ly;
+    double rho, cp, kappa, sigma, eps, ch, hc, cW, chi, T_amb, T_ig, delta_x, delta_z;
+    double A_r, M_ratio, T_a, heat_scale, fuel_rate, fuel_thresh, thresh_guard;
+    double wind_x, wind_y;
+    int scheme;              /* WF_PR | WF_STRANG_CN */
+    int precision;           /* WF_FP32 | WF_FP64 */
+    int F_timing;            /* WF_F_ONCE | WF_F_PER_SUBSTEP (PR only) */
+    int scale_heat_by_fuel;  /* 0 (default) or 1 */
+} wf_params;
+
+typedef struct wf_handle wf_handle;
+
+/* Fill *p with the defaults above and Lx = Ly = 100 (m).  Never fails for p != NULL. */
+int wf_params_default(wf_params* p);
+
+/*
+ * Create a simulation on nx x ny elements of degree p (1..3) with time
+ * step dt > 0.  Builds, on the GPU and in FP64, the Gauss tables, the 1-D
+ * matrices M, K, G (Sec. 3.1) and the banded LU factors of every 1-D
+ * operator of the chosen scheme.  The state is zero until wf_set_state.
+ * Errors: WF_EINVAL (sizes, p, dt, params), WF_ENOMEM, WF_ESINGULAR,
+ * WF_ETRUNC, WF_ECUDA.  On error *out is NULL.
+ */
+int wf_create(int nx, int ny, int p, double dt, const wf_params* params, wf_handle** out);
+
+/*
+ * Copy the state from host arrays T and fuel, each n = Nx*Ny float64
+ * values ([Ny][Nx]).  Converts to the handle's precision on the device.
+ * Waits for earlier work on the handle's stream.  Errors: WF_EINVAL
+ * (NULL pointer or n != Nx*Ny), WF_ECUDA.
+ */
+int wf_set_state(wf_handle* h, const double* T, const double* fuel, size_t n);
+
+/*
+ * Set the explicit, spatially varying part b'(x, y) of the wind:
+ *   b'_x(x,y) = sum_r fx_r(x) gx_r(y),  b'_y(x,y) = sum_r fy_r(x) gy_r(y),
+ * r < rank (0..4), each factor a 1-D spline of the handle's degree and
+ * knots given by its coefficients.  `factors` holds, in this order,
+ * fx (rank*Nx), gx (rank*Ny), fy (rank*Nx), gy (rank*Ny) float64 values.
+ * rank 0 (factors may be NULL) removes the variation.
+ * Errors: WF_EINVAL, WF_ECUDA.
+ */
+int wf_set_wind(wf_handle* h, int rank, const double* factors);
+
+/*
+ * Enqueue nsteps >= 0 time steps on the handle's stream and return
+ * without waiting.  Steps are replayed from a CUDA graph captured on the
+ * first call.  Errors: WF_EINVAL, WF_ECUDA (launch failure).
+ */
+int wf_step(wf_handle* h, int nsteps);
+
+/*
+ * Wait for all enqueued work and report device status: WF_EUNSTABLE if a
+ * temperature became non-finite or exceeded 1e5 K since the last
+ * wf_sync, WF_OK otherwise.  The status flag is cleared by the call.
+ */
+int wf_sync(wf_handle* h);
+
+/*
+ * Wait for enqueued work and copy the state into host arrays T and fuel
+ * (n = Nx*Ny float64 each; either may be NULL to skip it).
+ * Errors: WF_EINVAL, WF_ECUDA.
+ */
+int wf_get_state(wf_handle* h, double* T, double* fuel, size_t n);
+
+/* Grid sizes of a handle (any pointer may be NULL).  Errors: WF_EINVAL. */
+int wf_get_dims(const wf_handle* h, int* Nx, int* Ny, int* p, int* precision);
+
+/*
+ * Use the caller's CUDA stream (a cudaStream_t passed as void*; NULL
+ * restores the handle's own stream).  The captured step graph is kept;
+ * it is launched on whichever stream is current.  Errors: WF_EINVAL.
+ */
+int wf_set_stream(wf_handle* h, void* stream);
+
+/*
+ * Per-kernel timing.  With on != 0, wf_step launches its kernels
+ * directly (no graph) with a CUDA event pair around each launch, on the
+ * launching stream; wf_kernel_times then returns, per kernel class k <
+ * max_k, the summed milliseconds ms[k], the launch count counts[k] and a
+ * NUL-terminated name (names[k], up to 47 characters, may be NULL), and
+ * resets the sums.  Returns the number of classes (>= 0) or an error.
+ */
+int wf_set_profiling(wf_handle* h, int on);
+int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], int max_k);
+
+/* Free every resource of the handle (NULL is accepted). */
+void wf_destroy(wf_handle* h);
+
+/* Static text for a status code. */
+const char* wf_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WF_H */

@@ -1,0 +1,798 @@
+// C ABI of libwf: handle life cycle, state transfer and the time-step driver.
+//
+// The step sequences follow the schemes of the paper:
+//   Peaceman-Rachford, Sec. 3.1 Eq. matrixPR (one explicit F per step, or per substep);
+//   Strang + Crank-Nicolson, Sec. 3.2 Eq. matrixCN;
+//   fuel: explicit Euler L2 projection of the Sec. 7 listing, (M^x (x) M^y) phi^{n+1} = Phi.
+// Each 2-D solve (A^x (x) B^y) X = R runs as an x pass (lines of A^x) and a y pass
+// (lines of B^y), Sec. 4.  The launches of one step are captured once into a CUDA
+// graph and replayed by wf_step.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "wf.h"
+#include "wf_internal.h"
+
+using namespace wf;
+
+namespace {
+
+constexpr double kTmax = 1e5;  // guard on |T| (K)
+
+struct Arena {
+    char* base = nullptr;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+struct Op {
+    double aM = 0, aK = 0, aG = 0;
+    bool factored = false;
+    Chunks ch{};
+    double *band64 = nullptr, *lu64 = nullptr, *spk64 = nullptr, *E64 = nullptr;
+    void *bandP = nullptr, *luP = nullptr, *spkP = nullptr, *EP = nullptr;
+};
+
+struct Dir {
+    int n = 0, N = 0;
+    double L = 0, h = 0;
+    double *B64 = nullptr, *D64 = nullptr;
+    void *BP = nullptr, *DP = nullptr, *wP = nullptr;
+    double *M64 = nullptr, *K64 = nullptr, *G64 = nullptr;
+    Op op[3];  // 0: M, 1: minus operator (explicit side), 2: plus operator (implicit side)
+};
+
+enum SiteId { S_RHS1, S_X1, S_Y1, S_Y2PRE, S_RHS2, S_MV2, S_X2, S_Y3, S_NSITES };
+const char* kSiteNames[S_NSITES] = {"rhs_quadrature_1", "xsolve_1", "ysolve_1", "ysolve_y_substep",
+                                    "rhs_quadrature_2", "matvec_2", "xsolve_2", "ysolve_2"};
+
+}  // namespace
+
+struct wf_handle {
+    int nx, ny, p, q, Nx, Ny, pitch, prec;
+    double dt;
+    wf_params prm;
+    Phys phys;
+    cudaStream_t own = nullptr, stream = nullptr;
+    void* mem = nullptr;
+    size_t mem_bytes = 0;
+    double *gxi = nullptr, *gw = nullptr;
+    Dir dx, dy;
+    void *T = nullptr, *phi = nullptr, *F = nullptr, *Phi = nullptr, *R = nullptr;
+    double* stage = nullptr;  // 2 * Nx * Ny doubles for host transfers
+    double* work64 = nullptr;
+    double* diag = nullptr;   // [2] factorisation diagnostics
+    int* status = nullptr;
+    int wind_rank = 0;
+    void *fxq = nullptr, *gxq = nullptr, *fyq = nullptr, *gyq = nullptr;
+    double* wind64 = nullptr;
+    cudaGraphExec_t g1 = nullptr, g8 = nullptr;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_free;
+    struct Pending {
+        int site;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    double site_ms[S_NSITES] = {0};
+    int site_cnt[S_NSITES] = {0};
+};
+
+namespace {
+
+#define WF_TRY(expr)                               \
+    do {                                           \
+        cudaError_t _e = (expr);                   \
+        if (_e != cudaSuccess) return WF_ECUDA;    \
+    } while (0)
+
+size_t esize(int prec) { return prec == WF_FP32 ? 4 : 8; }
+
+Chunks make_chunks(int N, int target) {
+    Chunks c;
+    c.N = N;
+    c.C = N / target;
+    if (c.C < 1) c.C = 1;
+    c.base = N / c.C;
+    c.rem = N % c.C;
+    return c;
+}
+
+void layout(wf_handle* h, Arena& A) {
+    const size_t es = esize(h->prec);
+    const size_t field = (size_t)h->Ny * h->pitch;
+    h->T = A.take<char>(field * es);
+    h->phi = A.take<char>(field * es);
+    h->F = A.take<char>(field * es);
+    h->Phi = A.take<char>(field * es);
+    h->R = A.take<char>(field * es);
+    h->stage = A.take<double>(2 * (size_t)h->Nx * h->Ny);
+    h->gxi = A.take<double>(16);
+    h->gw = A.take<double>(16);
+    h->diag = A.take<double>(2);
+    h->status = A.take<int>(4);
+    const int W = 2 * h->p + 1;
+    int maxN = h->Nx > h->Ny ? h->Nx : h->Ny;
+    h->work64 = A.take<double>((size_t)maxN * W);
+    Dir* ds[2] = {&h->dx, &h->dy};
+    for (Dir* d : ds) {
+        const size_t tab = (size_t)d->n * h->q * (h->p + 1);
+        d->B64 = A.take<double>(tab);
+        d->D64 = A.take<double>(tab);
+        if (h->prec == WF_FP32) {
+            d->BP = A.take<float>(tab);
+            d->DP = A.take<float>(tab);
+            d->wP = A.take<float>(16);
+        } else {
+            d->BP = d->B64;
+            d->DP = d->D64;
+            d->wP = A.take<double>(16);
+        }
+        d->M64 = A.take<double>((size_t)d->N * W);
+        d->K64 = A.take<double>((size_t)d->N * W);
+        d->G64 = A.take<double>((size_t)d->N * W);
+        for (Op& o : d->op) {
+            // every operator gets FP64 band and factor space (the explicit-side operator's
+            // factors are never used; they exist so one kernel builds every band)
+            const size_t nE = (size_t)(o.ch.C > 1 ? o.ch.C - 1 : 1) * h->p * h->p;
+            o.band64 = A.take<double>((size_t)d->N * W);
+            o.lu64 = A.take<double>((size_t)d->N * W);
+            o.spk64 = A.take<double>((size_t)d->N * 2 * h->p);
+            o.E64 = A.take<double>(nE);
+            if (h->prec == WF_FP32) {
+                o.bandP = A.take<float>((size_t)d->N * W);
+                o.luP = o.factored ? (void*)A.take<float>((size_t)d->N * W) : nullptr;
+                o.spkP = o.factored ? (void*)A.take<float>((size_t)d->N * 2 * h->p) : nullptr;
+                o.EP = o.factored ? (void*)A.take<float>(nE) : nullptr;
+            } else {
+                o.bandP = o.band64;
+                o.luP = o.lu64;
+                o.spkP = o.spk64;
+                o.EP = o.E64;
+            }
+        }
+    }
+    const size_t qx = (size_t)kMaxRank * h->nx * h->q, qy = (size_t)kMaxRank * h->ny * h->q;
+    h->fxq = A.take<char>(qx * es);
+    h->gxq = A.take<char>(qy * es);
+    h->fyq = A.take<char>(qx * es);
+    h->gyq = A.take<char>(qy * es);
+    h->wind64 = A.take<double>((size_t)2 * kMaxRank * (h->Nx + h->Ny));
+}
+
+void set_op_coeffs(wf_handle* h) {
+    const Phys& c = h->phys;
+    const double tau = h->dt;
+    double thx, thy;
+    if (h->prm.scheme == WF_PR) {
+        thx = thy = 0.5 * tau;
+    } else {
+        thx = 0.25 * tau;
+        thy = 0.5 * tau;
+    }
+    // x: A_x = C_d K + c_W b_x G + c_chi M;  op[1] = -theta A_x (band),  op[2] = X_+ = M + theta A_x
+    Op* ox = h->dx.op;
+    ox[0].aM = 1.0;
+    ox[1].aM = -thx * c.c_chi;
+    ox[1].aK = -thx * c.C_d;
+    ox[1].aG = -thx * c.c_W * h->prm.wind_x;
+    ox[2].aM = 1.0 + thx * c.c_chi;
+    ox[2].aK = thx * c.C_d;
+    ox[2].aG = thx * c.c_W * h->prm.wind_x;
+    // y: A_y = C_d K + c_W b_y G;  op[1] = -theta A_y (band),  op[2] = Y_+ = M + theta A_y
+    Op* oy = h->dy.op;
+    oy[0].aM = 1.0;
+    oy[1].aM = 0.0;
+    oy[1].aK = -thy * c.C_d;
+    oy[1].aG = -thy * c.c_W * h->prm.wind_y;
+    oy[2].aM = 1.0;
+    oy[2].aK = thy * c.C_d;
+    oy[2].aG = thy * c.c_W * h->prm.wind_y;
+    for (int k = 0; k < 3; ++k) {
+        ox[k].factored = (k != 1);
+        oy[k].factored = (k != 1);
+    }
+}
+
+Phys make_phys(const wf_params& p) {
+    Phys c;
+    const double inv = 1.0 / (p.rho * p.cp);
+    c.C_d = p.kappa * inv;
+    c.C_nld = 4.0 * p.sigma * p.eps * p.delta_x * inv;
+    c.c_rad = p.sigma * p.eps / p.delta_z * inv;
+    c.c_chi = p.chi * inv;
+    c.c_W = p.cW;
+    c.K_ign = -p.heat_scale * p.rho * p.ch * p.hc * p.M_ratio * p.A_r * inv;
+    c.k_f = p.fuel_rate * p.A_r;
+    c.T_a = p.T_a;
+    c.T_amb = p.T_amb;
+    c.T_ig = p.T_ig;
+    c.phi_min = p.fuel_thresh + p.thresh_guard;
+    c.heat_by_fuel = p.scale_heat_by_fuel ? 1 : 0;
+    return c;
+}
+
+bool params_ok(const wf_params& p) {
+    const double v[] = {p.Lx, p.Ly, p.rho, p.cp};
+    for (double x : v)
+        if (!(x > 0.0) || !isfinite(x)) return false;
+    const double w[] = {p.kappa, p.sigma, p.eps, p.ch, p.hc, p.cW, p.chi, p.T_amb, p.T_ig, p.delta_x, p.delta_z,
+                        p.A_r, p.M_ratio, p.T_a, p.heat_scale, p.fuel_rate, p.fuel_thresh, p.thresh_guard,
+                        p.wind_x, p.wind_y};
+    for (double x : w)
+        if (!isfinite(x) && !(x == INFINITY)) return false;
+    if (!(p.delta_z > 0.0)) return false;
+    if (p.scheme != WF_PR && p.scheme != WF_STRANG_CN) return false;
+    if (p.precision != WF_FP32 && p.precision != WF_FP64) return false;
+    if (p.F_timing != WF_F_ONCE && p.F_timing != WF_F_PER_SUBSTEP) return false;
+    return true;
+}
+
+int build_tables(wf_handle* h) {
+    cudaStream_t s = h->stream;
+    WF_TRY(launch_gauss(h->gxi, h->gw, h->q, s));
+    Dir* ds[2] = {&h->dx, &h->dy};
+    for (Dir* d : ds) {
+        WF_TRY(launch_basis(h->gxi, h->q, d->n, h->p, d->L, d->B64, d->D64, s));
+        WF_TRY(launch_assemble(d->B64, d->D64, h->gw, h->q, d->n, h->p, d->h, d->M64, d->K64, d->G64, s));
+        const size_t tab = (size_t)d->n * h->q * (h->p + 1);
+        if (h->prec == WF_FP32) {
+            WF_TRY(launch_to_f32(d->B64, (float*)d->BP, tab, s));
+            WF_TRY(launch_to_f32(d->D64, (float*)d->DP, tab, s));
+        }
+    }
+    // weights times element length, per direction, in P
+    double w[16];
+    WF_TRY(cudaMemcpyAsync(w, h->gw, sizeof(double) * h->q, cudaMemcpyDeviceToHost, s));
+    WF_TRY(cudaStreamSynchronize(s));
+    for (Dir* d : ds) {
+        if (h->prec == WF_FP32) {
+            float wf32[16];
+            for (int a = 0; a < h->q; ++a) wf32[a] = (float)(w[a] * d->h);
+            WF_TRY(cudaMemcpyAsync(d->wP, wf32, sizeof(float) * h->q, cudaMemcpyHostToDevice, s));
+        } else {
+            double w64[16];
+            for (int a = 0; a < h->q; ++a) w64[a] = w[a] * d->h;
+            WF_TRY(cudaMemcpyAsync(d->wP, w64, sizeof(double) * h->q, cudaMemcpyHostToDevice, s));
+        }
+    }
+    WF_TRY(cudaStreamSynchronize(s));  // the host weight arrays go out of scope
+    return WF_OK;
+}
+
+// returns WF_OK, WF_ESINGULAR or WF_ETRUNC (tolerance tol on the neglected spike entries)
+int build_factors(wf_handle* h, double tol, double* worst) {
+    cudaStream_t s = h->stream;
+    const int W = 2 * h->p + 1;
+    *worst = 0.0;
+    Dir* ds[2] = {&h->dx, &h->dy};
+    for (Dir* d : ds) {
+        for (Op& o : d->op) {
+            double zero[2] = {0.0, 0.0};
+            WF_TRY(cudaMemcpyAsync(h->diag, zero, sizeof(zero), cudaMemcpyHostToDevice, s));
+            WF_TRY(launch_factor(d->M64, d->K64, d->G64, o.aM, o.aK, o.aG, d->N, h->p, o.ch, o.band64, o.lu64,
+                                 o.spk64, o.E64, h->work64, h->diag, s));
+            double dg[2];
+            WF_TRY(cudaMemcpyAsync(dg, h->diag, sizeof(dg), cudaMemcpyDeviceToHost, s));
+            WF_TRY(cudaStreamSynchronize(s));
+            if (o.factored) {
+                if (dg[0] != 0.0) return WF_ESINGULAR;
+                if (dg[1] > *worst) *worst = dg[1];
+            }
+            if (h->prec != WF_FP32) continue;
+            WF_TRY(launch_to_f32(o.band64, (float*)o.bandP, (size_t)d->N * W, s));
+            if (o.factored) {
+                WF_TRY(launch_to_f32(o.lu64, (float*)o.luP, (size_t)d->N * W, s));
+                WF_TRY(launch_to_f32(o.spk64, (float*)o.spkP, (size_t)d->N * 2 * h->p, s));
+                WF_TRY(launch_to_f32(o.E64, (float*)o.EP, (size_t)(o.ch.C > 1 ? o.ch.C - 1 : 1) * h->p * h->p, s));
+            }
+        }
+    }
+    WF_TRY(cudaStreamSynchronize(s));
+    return *worst > tol ? WF_ETRUNC : WF_OK;
+}
+
+FactorV fv(const Op& o) {
+    FactorV f;
+    f.ch = o.ch;
+    f.lu = o.luP;
+    f.spk = o.spkP;
+    f.E = o.EP;
+    return f;
+}
+
+cudaEvent_t take_event(wf_handle* h) {
+    if (!h->ev_free.empty()) {
+        cudaEvent_t e = h->ev_free.back();
+        h->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+template <typename F>
+cudaError_t timed(wf_handle* h, int site, F&& launch) {
+    if (!h->profiling) return launch();
+    cudaEvent_t a = take_event(h), b = take_event(h);
+    cudaEventRecord(a, h->stream);
+    cudaError_t e = launch();
+    cudaEventRecord(b, h->stream);
+    h->pending.push_back({site, a, b});
+    return e;
+}
+
+// R = Rscale F + c1 (A1 (x) B1) T + c2 (A2 (x) B2) T  (A2 == nullptr drops the second term)
+RhsArgs rhs_args(wf_handle* h, const void* T, void* F, void* Phi, void* R, double Rscale, const Op& A1,
+                 const Op& B1, double c1, const Op* A2, const Op* B2, double c2) {
+    RhsArgs a;
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.Nx = h->Nx;
+    a.Ny = h->Ny;
+    a.pitch = h->pitch;
+    a.T = T;
+    a.phi = h->phi;
+    a.F = F;
+    a.Phi = Phi;
+    a.R = R;
+    a.Bx = h->dx.BP;
+    a.Dx = h->dx.DP;
+    a.By = h->dy.BP;
+    a.Dy = h->dy.DP;
+    a.wx = h->dx.wP;
+    a.wy = h->dy.wP;
+    a.wind_rank = h->wind_rank;
+    a.fxq = h->fxq;
+    a.gxq = h->gxq;
+    a.fyq = h->fyq;
+    a.gyq = h->gyq;
+    a.A1 = A1.bandP;
+    a.B1 = B1.bandP;
+    a.A2 = A2 ? A2->bandP : nullptr;
+    a.B2 = B2 ? B2->bandP : nullptr;
+    a.Rscale = Rscale;
+    a.c1 = c1;
+    a.c2 = c2;
+    a.tau = h->dt;
+    a.phys = h->phys;
+    return a;
+}
+
+LineArgs line_args(wf_handle* h, bool xdir) {
+    LineArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nlines = xdir ? h->Ny : h->Nx;
+    a.pitch = h->pitch;
+    a.tmax = kTmax;
+    return a;
+}
+
+void add_line(LineArgs& a, const void* in, void* out, const Op& o, const void* base = nullptr,
+              const void* premul = nullptr, double prescale = 1.0) {
+    a.in[a.narr] = in;
+    a.out[a.narr] = out;
+    a.f[a.narr] = fv(o);
+    a.base[a.narr] = base;
+    a.premul[a.narr] = premul;
+    a.prescale[a.narr] = prescale;
+    a.narr++;
+}
+
+// Enqueue one time step on h->stream.
+//
+// Every substep is solved for its increment: with X_+ = M + theta A_x and
+// Y_+ = M + theta A_y, the PR systems of Eq. matrixPR are identical to
+//   (X_+ (x) M^y) (T* - T^n)      = theta F - theta (A_x (x) M^y) T^n - theta (M^x (x) A_y) T^n
+//   (M^x (x) Y_+) (T^{n+1} - T*)  = theta F - theta (A_x (x) M^y) T*  - theta (M^x (x) A_y) T*
+// and the Strang/Crank-Nicolson systems of Eq. matrixCN to
+//   (X_+ (x) M^y) (T* - T^n)      = tau/2 F(T^n) - 2 theta_x (A_x (x) M^y) T^n        (theta_x = tau/4)
+//   (I (x) Y_+) (T** - T*)        = -2 theta_y (I (x) A_y) T*                         (theta_y = tau/2)
+//   (X_+ (x) M^y) (T^{n+1} - T**) = tau/2 F(T**) - 2 theta_x (A_x (x) M^y) T**
+// Rounding errors then scale with the increment instead of the temperature,
+// which keeps the FP32 path accurate through the inverse mass matrices.
+cudaError_t enqueue_step(wf_handle* h) {
+    cudaStream_t s = h->stream;
+    const int prec = h->prec, p = h->p;
+    Op* X = h->dx.op;
+    Op* Y = h->dy.op;
+    cudaError_t e;
+    if (h->prm.scheme == WF_PR) {
+        const double th = 0.5 * h->dt;
+        const bool once = h->prm.F_timing == WF_F_ONCE;
+        RhsArgs r1 = rhs_args(h, h->T, once ? h->F : nullptr, h->Phi, h->R, th, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
+        if ((e = timed(h, S_RHS1, [&] { return launch_rhs(prec, p, r1, s); })) != cudaSuccess) return e;
+        LineArgs x1 = line_args(h, true);
+        add_line(x1, h->R, h->R, X[2]);
+        add_line(x1, h->Phi, h->Phi, X[0]);
+        if ((e = timed(h, S_X1, [&] { return launch_xsolve(prec, p, x1, s); })) != cudaSuccess) return e;
+        LineArgs y1 = line_args(h, false);
+        add_line(y1, h->R, h->T, Y[0], h->T);
+        if (once) add_line(y1, h->Phi, h->phi, Y[0], h->phi);
+        if ((e = timed(h, S_Y1, [&] { return launch_ysolve(prec, p, y1, s); })) != cudaSuccess) return e;
+        if (once) {
+            MatvecArgs mv;
+            mv.Nx = h->Nx;
+            mv.Ny = h->Ny;
+            mv.pitch = h->pitch;
+            mv.T = h->T;
+            mv.F = h->F;
+            mv.R = h->R;
+            mv.A1 = X[1].bandP;
+            mv.B1 = Y[0].bandP;
+            mv.A2 = X[0].bandP;
+            mv.B2 = Y[1].bandP;
+            mv.Fscale = th;
+            mv.c1 = 1.0;
+            mv.c2 = 1.0;
+            if ((e = timed(h, S_MV2, [&] { return launch_matvec(prec, p, mv, s); })) != cudaSuccess) return e;
+        } else {
+            RhsArgs r2 = rhs_args(h, h->T, nullptr, nullptr, h->R, th, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
+            if ((e = timed(h, S_RHS2, [&] { return launch_rhs(prec, p, r2, s); })) != cudaSuccess) return e;
+        }
+        LineArgs x2 = line_args(h, true);
+        add_line(x2, h->R, h->R, X[0]);
+        if ((e = timed(h, S_X2, [&] { return launch_xsolve(prec, p, x2, s); })) != cudaSuccess) return e;
+        LineArgs y2 = line_args(h, false);
+        add_line(y2, h->R, h->T, Y[2], h->T);
+        if (!once) add_line(y2, h->Phi, h->phi, Y[0], h->phi);
+        y2.status = h->status;
+        if ((e = timed(h, S_Y3, [&] { return launch_ysolve(prec, p, y2, s); })) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
+    // Strang / Crank-Nicolson
+    const double half = 0.5 * h->dt;
+    RhsArgs r1 = rhs_args(h, h->T, nullptr, h->Phi, h->R, half, X[1], Y[0], 2.0, nullptr, nullptr, 0.0);
+    if ((e = timed(h, S_RHS1, [&] { return launch_rhs(prec, p, r1, s); })) != cudaSuccess) return e;
+    LineArgs x1 = line_args(h, true);
+    add_line(x1, h->R, h->R, X[2]);
+    add_line(x1, h->Phi, h->Phi, X[0]);
+    if ((e = timed(h, S_X1, [&] { return launch_xsolve(prec, p, x1, s); })) != cudaSuccess) return e;
+    LineArgs y1 = line_args(h, false);
+    add_line(y1, h->R, h->T, Y[0], h->T);
+    if ((e = timed(h, S_Y1, [&] { return launch_ysolve(prec, p, y1, s); })) != cudaSuccess) return e;
+    LineArgs yy = line_args(h, false);
+    add_line(yy, h->T, h->T, Y[2], h->T, Y[1].bandP, 2.0);
+    if ((e = timed(h, S_Y2PRE, [&] { return launch_ysolve(prec, p, yy, s); })) != cudaSuccess) return e;
+    RhsArgs r2 = rhs_args(h, h->T, nullptr, nullptr, h->R, half, X[1], Y[0], 2.0, nullptr, nullptr, 0.0);
+    if ((e = timed(h, S_RHS2, [&] { return launch_rhs(prec, p, r2, s); })) != cudaSuccess) return e;
+    LineArgs x2 = line_args(h, true);
+    add_line(x2, h->R, h->R, X[2]);
+    if ((e = timed(h, S_X2, [&] { return launch_xsolve(prec, p, x2, s); })) != cudaSuccess) return e;
+    LineArgs y2 = line_args(h, false);
+    add_line(y2, h->R, h->T, Y[0], h->T);
+    add_line(y2, h->Phi, h->phi, Y[0], h->phi);
+    y2.status = h->status;
+    if ((e = timed(h, S_Y3, [&] { return launch_ysolve(prec, p, y2, s); })) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+void drop_graphs(wf_handle* h) {
+    if (h->g1) cudaGraphExecDestroy(h->g1);
+    if (h->g8) cudaGraphExecDestroy(h->g8);
+    h->g1 = h->g8 = nullptr;
+}
+
+cudaError_t capture(wf_handle* h, int steps, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < steps && le == cudaSuccess; ++k) le = enqueue_step(h);
+    e = cudaStreamEndCapture(h->stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return le;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+void destroy(wf_handle* h) {
+    if (!h) return;
+    drop_graphs(h);
+    for (auto& pnd : h->pending) {
+        cudaEventDestroy(pnd.a);
+        cudaEventDestroy(pnd.b);
+    }
+    for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
+    if (h->mem) cudaFree(h->mem);
+    if (h->own) cudaStreamDestroy(h->own);
+    delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int wf_params_default(wf_params* p) {
+    if (!p) return WF_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->Lx = p->Ly = 100.0;
+    p->cp = 1.0;
+    p->rho = 1.293;
+    p->kappa = 0.3;
+    p->sigma = 5.67e-8;
+    p->eps = 0.05;
+    p->ch = 1.0;
+    p->hc = -70.0;
+    p->cW = 0.5;
+    p->chi = 2e-2;
+    p->T_amb = 300.0;
+    p->T_ig = 800.0;
+    p->delta_x = 3.5e-2 / 0.05;
+    p->delta_z = 1.5 * 0.05;
+    p->A_r = 1e-4;
+    p->M_ratio = 1.0;
+    p->T_a = 300.0;
+    p->heat_scale = 1e4;
+    p->fuel_rate = 300.0;
+    p->fuel_thresh = 0.2;
+    p->thresh_guard = 1e-6;
+    p->scheme = WF_PR;
+    p->precision = WF_FP32;
+    p->F_timing = WF_F_ONCE;
+    p->scale_heat_by_fuel = 0;
+    return WF_OK;
+}
+
+int wf_create(int nx, int ny, int p, double dt, const wf_params* params, wf_handle** out) {
+    if (!out) return WF_EINVAL;
+    *out = nullptr;
+    if (!params || nx < 1 || ny < 1 || p < 1 || p > kMaxP || !(dt > 0.0) || !isfinite(dt)) return WF_EINVAL;
+    if (nx > (1 << 15) || ny > (1 << 15)) return WF_EINVAL;
+    if (!params_ok(*params)) return WF_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaFree(0) != cudaSuccess) return WF_ECUDA;
+
+    wf_handle* h = new (std::nothrow) wf_handle();
+    if (!h) return WF_ENOMEM;
+    h->nx = nx;
+    h->ny = ny;
+    h->p = p;
+    h->q = p + 1;
+    h->Nx = nx + p;
+    h->Ny = ny + p;
+    h->pitch = (h->Nx + 31) / 32 * 32;
+    h->prec = params->precision;
+    h->dt = dt;
+    h->prm = *params;
+    h->phys = make_phys(*params);
+    h->dx.n = nx;
+    h->dx.N = h->Nx;
+    h->dx.L = params->Lx;
+    h->dx.h = params->Lx / nx;
+    h->dy.n = ny;
+    h->dy.N = h->Ny;
+    h->dy.L = params->Ly;
+    h->dy.h = params->Ly / ny;
+    if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
+        destroy(h);
+        return WF_ECUDA;
+    }
+    h->stream = h->own;
+    set_op_coeffs(h);
+
+    // chunk length: FP32 needs the neglected spike coupling below 1e-8, FP64 below 1e-15
+    const double tol = h->prec == WF_FP32 ? 1e-8 : 1e-15;
+    int target = h->prec == WF_FP32 ? 32 : 64;
+    const int G = line_rows_per_cta(h->prec);
+    int rc = WF_OK;
+    for (int attempt = 0; attempt < 12; ++attempt) {
+        Dir* ds[2] = {&h->dx, &h->dy};
+        for (Dir* d : ds) {
+            Chunks ch = make_chunks(d->N, target);
+            while (G * ch.C > 1024) ch = make_chunks(d->N, ch.base * 2);
+            for (Op& o : d->op) o.ch = ch;
+        }
+        if (h->mem) {
+            cudaFree(h->mem);
+            h->mem = nullptr;
+        }
+        Arena A;
+        layout(h, A);
+        h->mem_bytes = A.off + 256;
+        if (cudaMalloc(&h->mem, h->mem_bytes) != cudaSuccess) {
+            destroy(h);
+            return WF_ENOMEM;
+        }
+        Arena B;
+        B.base = reinterpret_cast<char*>(h->mem);
+        layout(h, B);
+        if ((rc = build_tables(h)) != WF_OK) break;
+        double worst = 0.0;
+        rc = build_factors(h, tol, &worst);
+        if (rc != WF_ETRUNC) break;
+        if (h->dx.op[0].ch.C == 1 && h->dy.op[0].ch.C == 1) break;
+        target *= 2;
+    }
+    if (rc != WF_OK) {
+        destroy(h);
+        return rc;
+    }
+    const size_t field = (size_t)h->Ny * h->pitch;
+    const int prec = h->prec;
+    if (launch_fill(prec, h->T, field, 0.0, h->stream) != cudaSuccess ||
+        launch_fill(prec, h->phi, field, 0.0, h->stream) != cudaSuccess ||
+        launch_fill(prec, h->F, field, 0.0, h->stream) != cudaSuccess ||
+        launch_fill(prec, h->Phi, field, 0.0, h->stream) != cudaSuccess ||
+        launch_fill(prec, h->R, field, 0.0, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        destroy(h);
+        return WF_ECUDA;
+    }
+    *out = h;
+    return WF_OK;
+}
+
+int wf_set_state(wf_handle* h, const double* T, const double* fuel, size_t n) {
+    if (!h || !T || !fuel || n != (size_t)h->Nx * h->Ny) return WF_EINVAL;
+    cudaStream_t s = h->stream;
+    double* st2 = h->stage + n;
+    WF_TRY(cudaMemcpyAsync(h->stage, T, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    WF_TRY(cudaMemcpyAsync(st2, fuel, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    WF_TRY(launch_convert_in(h->prec, h->stage, h->T, h->Nx, h->Ny, h->pitch, s));
+    WF_TRY(launch_convert_in(h->prec, st2, h->phi, h->Nx, h->Ny, h->pitch, s));
+    WF_TRY(cudaStreamSynchronize(s));
+    return WF_OK;
+}
+
+int wf_set_wind(wf_handle* h, int rank, const double* factors) {
+    if (!h || rank < 0 || rank > kMaxRank || (rank > 0 && !factors)) return WF_EINVAL;
+    cudaStream_t s = h->stream;
+    if (rank > 0) {
+        const size_t nx = (size_t)rank * h->Nx, ny = (size_t)rank * h->Ny;
+        const size_t total = 2 * (nx + ny);
+        for (size_t k = 0; k < total; ++k)
+            if (!isfinite(factors[k])) return WF_EINVAL;
+        WF_TRY(cudaMemcpyAsync(h->wind64, factors, total * sizeof(double), cudaMemcpyHostToDevice, s));
+        const double* fx = h->wind64;
+        const double* gx = fx + nx;
+        const double* fy = gx + ny;
+        const double* gy = fy + nx;
+        WF_TRY(launch_factor_points(h->prec, fx, rank, h->nx, h->p, h->dx.B64, h->fxq, s));
+        WF_TRY(launch_factor_points(h->prec, gx, rank, h->ny, h->p, h->dy.B64, h->gxq, s));
+        WF_TRY(launch_factor_points(h->prec, fy, rank, h->nx, h->p, h->dx.B64, h->fyq, s));
+        WF_TRY(launch_factor_points(h->prec, gy, rank, h->ny, h->p, h->dy.B64, h->gyq, s));
+        WF_TRY(cudaStreamSynchronize(s));
+    }
+    if (rank != h->wind_rank) drop_graphs(h);  // the rank is a kernel argument of the captured graph
+    h->wind_rank = rank;
+    return WF_OK;
+}
+
+int wf_step(wf_handle* h, int nsteps) {
+    if (!h || nsteps < 0) return WF_EINVAL;
+    if (nsteps == 0) return WF_OK;
+    if (h->profiling) {
+        for (int k = 0; k < nsteps; ++k)
+            if (enqueue_step(h) != cudaSuccess) return WF_ECUDA;
+        return WF_OK;
+    }
+    if (!h->g1) {
+        if (capture(h, 1, &h->g1) != cudaSuccess) {
+            drop_graphs(h);
+            return WF_ECUDA;
+        }
+        if (capture(h, 8, &h->g8) != cudaSuccess) {
+            drop_graphs(h);
+            return WF_ECUDA;
+        }
+    }
+    int k = 0;
+    for (; k + 8 <= nsteps; k += 8)
+        if (cudaGraphLaunch(h->g8, h->stream) != cudaSuccess) return WF_ECUDA;
+    for (; k < nsteps; ++k)
+        if (cudaGraphLaunch(h->g1, h->stream) != cudaSuccess) return WF_ECUDA;
+    return WF_OK;
+}
+
+int wf_sync(wf_handle* h) {
+    if (!h) return WF_EINVAL;
+    int st[4] = {0, 0, 0, 0};
+    WF_TRY(cudaMemcpyAsync(st, h->status, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    WF_TRY(cudaStreamSynchronize(h->stream));
+    if (st[0]) {
+        WF_TRY(cudaMemsetAsync(h->status, 0, sizeof(st), h->stream));
+        WF_TRY(cudaStreamSynchronize(h->stream));
+        return WF_EUNSTABLE;
+    }
+    return WF_OK;
+}
+
+int wf_get_state(wf_handle* h, double* T, double* fuel, size_t n) {
+    if (!h || n != (size_t)h->Nx * h->Ny) return WF_EINVAL;
+    cudaStream_t s = h->stream;
+    if (T) {
+        WF_TRY(launch_convert_out(h->prec, h->T, h->stage, h->Nx, h->Ny, h->pitch, s));
+        WF_TRY(cudaMemcpyAsync(T, h->stage, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    if (fuel) {
+        WF_TRY(launch_convert_out(h->prec, h->phi, h->stage + n, h->Nx, h->Ny, h->pitch, s));
+        WF_TRY(cudaMemcpyAsync(fuel, h->stage + n, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    WF_TRY(cudaStreamSynchronize(s));
+    return WF_OK;
+}
+
+int wf_get_dims(const wf_handle* h, int* Nx, int* Ny, int* p, int* precision) {
+    if (!h) return WF_EINVAL;
+    if (Nx) *Nx = h->Nx;
+    if (Ny) *Ny = h->Ny;
+    if (p) *p = h->p;
+    if (precision) *precision = h->prec;
+    return WF_OK;
+}
+
+int wf_set_stream(wf_handle* h, void* stream) {
+    if (!h) return WF_EINVAL;
+    h->stream = stream ? reinterpret_cast<cudaStream_t>(stream) : h->own;
+    return WF_OK;
+}
+
+int wf_set_profiling(wf_handle* h, int on) {
+    if (!h) return WF_EINVAL;
+    h->profiling = on != 0;
+    return WF_OK;
+}
+
+int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], int max_k) {
+    if (!h || max_k < 0) return WF_EINVAL;
+    for (auto& pnd : h->pending) {
+        if (cudaEventSynchronize(pnd.b) != cudaSuccess) return WF_ECUDA;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, pnd.a, pnd.b) != cudaSuccess) return WF_ECUDA;
+        h->site_ms[pnd.site] += t;
+        h->site_cnt[pnd.site] += 1;
+        h->ev_free.push_back(pnd.a);
+        h->ev_free.push_back(pnd.b);
+    }
+    h->pending.clear();
+    for (int k = 0; k < S_NSITES && k < max_k; ++k) {
+        if (ms) ms[k] = h->site_ms[k];
+        if (counts) counts[k] = h->site_cnt[k];
+        if (names) {
+            strncpy(names[k], kSiteNames[k], 47);
+            names[k][47] = 0;
+        }
+    }
+    for (int k = 0; k < S_NSITES; ++k) {
+        h->site_ms[k] = 0;
+        h->site_cnt[k] = 0;
+    }
+    return S_NSITES;
+}
+
+void wf_destroy(wf_handle* h) { destroy(h); }
+
+const char* wf_strerror(int code) {
+    switch (code) {
+        case WF_OK: return "ok";
+        case WF_PENDING: return "pending: request not finished";
+        case WF_EINVAL: return "invalid argument";
+        case WF_ENOMEM: return "out of device memory or HBM budget";
+        case WF_ESINGULAR: return "singular 1-D operator (pivot below 1e-300 ||A||)";
+        case WF_EUNSTABLE: return "unstable: temperature non-finite or above 1e5 K";
+        case WF_ETIMEOUT: return "bounded device wait timed out";
+        case WF_ECUDA: return "CUDA runtime error";
+        case WF_ETRUNC: return "chunked solve could not reach its truncation tolerance";
+        case WF_ENOTFOUND: return "unknown request ticket";
+    }
+    return "unknown status code";
+}
+
+}  // extern "C"

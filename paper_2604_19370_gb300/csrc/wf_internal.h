@@ -1,0 +1,119 @@
+// Internal declarations shared by the CUDA translation units of libwf.
+//
+// Data layout on the device (all fields of one handle):
+//   - coefficient fields T, phi, F, Phi, R: [Ny][pitch] in the handle's
+//     precision P (float or double), pitch = Nx rounded up to 32 elements
+//     so every row starts on a 128-byte boundary;
+//   - 1-D Gauss tables per direction: B[e][a][l] = B_{e+l}(x_{e,a}) and the
+//     derivative D[e][a][l], e < n, a < q = p+1, l <= p; weights w[a]*h;
+//   - 1-D banded matrices: band[r][d] = A[r][r+d-p], d in [0, 2p], zero
+//     outside the matrix;
+//   - chunked LU factors of a 1-D operator (see Factor below).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace wf {
+
+constexpr int kMaxP = 3;
+constexpr int kMaxRank = 4;
+
+// Normalised model coefficients (equation divided by rho*c_p).
+struct Phys {
+    double C_d, C_nld, c_rad, c_chi, c_W, K_ign, k_f, T_a, T_amb, T_ig, phi_min;
+    int heat_by_fuel;
+};
+
+// Partition of a line of N unknowns into C chunks of length base or base+1
+// (the first `rem` chunks are one longer).
+struct Chunks {
+    int N, C, base, rem;
+};
+__host__ __device__ inline int chunk_start(const Chunks& c, int k) { return k * c.base + (k < c.rem ? k : c.rem); }
+__host__ __device__ inline int chunk_len(const Chunks& c, int k) { return c.base + (k < c.rem ? 1 : 0); }
+
+// Chunked LU of a banded 1-D operator A (half-bandwidth p), truncated-SPIKE form.
+//   lu[r][0..p-1]  multipliers: forward row r subtracts lu[r][i-1] * y[r-i]
+//   lu[r][p]       1 / U[r][r]
+//   lu[r][p+j]     U[r][r+j], j = 1..p
+//   spk[r][0..p-1] V (right spike of the chunk holding r), spk[r][p..2p-1] W (left spike)
+//   E[k][p][p]     (I - W_{k+1}^top V_k^bottom)^{-1} for the interface between chunks k and k+1
+// Every product is chunk-local: entries coupling two chunks are carried by the spikes.
+struct FactorV {
+    Chunks ch;
+    const void* lu;
+    const void* spk;
+    const void* E;
+};
+
+// ---- tables and factorisation (FP64, wf_tables.cu) ---------------------------------
+cudaError_t launch_gauss(double* xi, double* w, int q, cudaStream_t s);
+cudaError_t launch_basis(const double* xi, int q, int n, int p, double L, double* B, double* D, cudaStream_t s);
+cudaError_t launch_assemble(const double* B, const double* D, const double* w, int q, int n, int p, double h,
+                            double* Mb, double* Kb, double* Gb, cudaStream_t s);
+// A = aM M + aK K + aG G: full band (band64) and chunked factors; diag[0] = 1.0 if a pivot was
+// below 1e-300 ||A||_inf, diag[1] = largest neglected spike entry (truncation measure).
+cudaError_t launch_factor(const double* Mb, const double* Kb, const double* Gb, double aM, double aK, double aG,
+                          int N, int p, Chunks ch, double* band64, double* lu64, double* spk64, double* E64,
+                          double* work64, double* diag, cudaStream_t s);
+cudaError_t launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s);
+// out[r][e*q+a] = sum_l B[e][a][l] coef[r][e+l]  (1-D spline factor at Gauss points)
+cudaError_t launch_factor_points(int prec, const double* coef, int rank, int n, int p, const double* B,
+                                 void* out, cudaStream_t s);
+cudaError_t launch_convert_in(int prec, const double* src, void* dst, int Nx, int Ny, int pitch, cudaStream_t s);
+cudaError_t launch_convert_out(int prec, const void* src, double* dst, int Nx, int Ny, int pitch, cudaStream_t s);
+cudaError_t launch_fill(int prec, void* dst, size_t n, double v, cudaStream_t s);
+
+// ---- quadrature right-hand side (wf_rhs.cu) ---------------------------------------
+struct RhsArgs {
+    int nx, ny, Nx, Ny, pitch;
+    const void* T;
+    const void* phi;
+    void* F;    // temperature load vector (optional)
+    void* Phi;  // fuel increment load vector -tau k_f int(E phi B_i B_j) (optional)
+    void* R;    // Rscale F + c1 (A1 (x) B1) T + c2 (A2 (x) B2) T (optional)
+    const void *Bx, *Dx, *By, *Dy, *wx, *wy;
+    int wind_rank;
+    const void *fxq, *gxq, *fyq, *gyq;  // [rank][n*q] factor values at Gauss points
+    const void *A1, *B1, *A2, *B2;      // bands along x (A) and y (B) for R; A2 may be NULL
+    double Rscale, c1, c2;
+    double tau;  // full time step (fuel update)
+    Phys phys;
+};
+cudaError_t launch_rhs(int prec, int p, const RhsArgs& a, cudaStream_t s);
+int rhs_items_per_dof(int p);  // informational
+
+// ---- line solves and matvec (wf_solve.cu) -------------------------------------------
+struct LineArgs {
+    int nlines;  // number of independent lines
+    int pitch;   // row pitch of the fields (elements)
+    int narr;    // 1 or 2 arrays (blockIdx.y)
+    const void* in[2];
+    void* out[2];
+    FactorV f[2];
+    const void* premul[2];  // y pass only: band applied along the line before the solve (or NULL)
+    double prescale[2];     // y pass only: factor of that band
+    const void* base[2];    // y pass only: out = base + solution (or NULL: out = solution)
+    int* status;            // y pass only: guard flag for out[0] (or NULL)
+    double tmax;
+};
+cudaError_t launch_xsolve(int prec, int p, const LineArgs& a, cudaStream_t s);
+cudaError_t launch_ysolve(int prec, int p, const LineArgs& a, cudaStream_t s);
+
+// R = Fscale F + c1 (A1 (x) B1) T + c2 (A2 (x) B2) T   (A2 may be NULL)
+struct MatvecArgs {
+    int Nx, Ny, pitch;
+    const void* T;
+    const void* F;
+    void* R;
+    const void *A1, *B1, *A2, *B2;
+    double Fscale, c1, c2;
+};
+cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s);
+
+// launch-shape helpers shared with the host driver
+int line_rows_per_cta(int prec);
+size_t line_smem_bytes(int prec, const Chunks& ch);
+
+}  // namespace wf

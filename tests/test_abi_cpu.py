@@ -1,0 +1,77 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+* libwf.so builds for sm_103a and exports every function include/wf.h declares;
+* the calls that need no device behave as documented: defaults, error strings,
+  argument validation before any CUDA call, and WF_ECUDA (not a crash) when no
+  device is present.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2604_19370_gb300.build import build_library
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return build_library()
+
+
+def _declared(root):
+    text = open(os.path.join(root, "include", "wf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(wf_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(libpath, repo_root):
+    L = ctypes.CDLL(libpath)
+    names = _declared(repo_root)
+    assert "wf_create" in names and "wf_step" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_defaults_and_strings(libpath):
+    from paper_2604_19370_gb300 import wf
+
+    p = wf.wf_params_default()
+    assert p.rho == 1.293 and p.kappa == 0.3 and p.T_ig == 800.0 and p.A_r == 1e-4
+    assert abs(p.delta_x - 0.7) < 1e-15 and abs(p.delta_z - 0.075) < 1e-15
+    assert p.scheme == wf.WF_PR and p.precision == wf.WF_FP32
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7, -8):
+        assert wf.wf_strerror(code) != "unknown status code"
+    assert wf.wf_strerror(-99) == "unknown status code"
+
+
+def test_argument_validation_without_device(libpath):
+    from paper_2604_19370_gb300 import wf
+
+    L = wf.lib()
+    p = wf.wf_params_default()
+    h = ctypes.c_void_p()
+    for nx, ny, deg, dt in [(0, 4, 2, 1e-3), (4, 4, 0, 1e-3), (4, 4, 4, 1e-3), (4, 4, 2, 0.0), (4, 4, 2, -1.0)]:
+        assert L.wf_create(nx, ny, deg, dt, ctypes.byref(p), ctypes.byref(h)) == wf.WF_EINVAL
+        assert not h.value
+    bad = wf.wf_params_default(scheme=7)
+    assert L.wf_create(4, 4, 2, 1e-3, ctypes.byref(bad), ctypes.byref(h)) == wf.WF_EINVAL
+    bad = wf.wf_params_default(rho=-1.0)
+    assert L.wf_create(4, 4, 2, 1e-3, ctypes.byref(bad), ctypes.byref(h)) == wf.WF_EINVAL
+    assert L.wf_step(None, 1) == wf.WF_EINVAL
+    assert L.wf_sync(None) == wf.WF_EINVAL
+    assert L.wf_get_dims(None, None, None, None, None) == wf.WF_EINVAL
+    L.wf_destroy(None)
+
+
+def test_no_device_reports_cuda_error(libpath):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    from paper_2604_19370_gb300 import wf
+
+    L = wf.lib()
+    p = wf.wf_params_default()
+    h = ctypes.c_void_p()
+    assert L.wf_create(8, 8, 2, 1e-3, ctypes.byref(p), ctypes.byref(h)) == wf.WF_ECUDA
+    assert not h.value
