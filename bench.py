@@ -1,0 +1,430 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 ADS wildfire time step.
+
+Workload (one time step = one "step"): 1024 x 1024 elements, quadratic
+B-splines (1026 x 1026 = 1,052,676 DOFs), Peaceman-Rachford, FP32 bulk with
+FP64 1-D factorisations, seeded synthetic terrain (fuel smoothed over 20
+elements, wind speed U[0,3] in a random direction plus a 10 % smooth
+variation).  The state is resident on the GPU; the L2 cache is flushed (a
+256 MiB write) before every timed step, so every step reads its inputs from
+HBM.  Each rank runs its own replica (the single domain does not shard; see
+the design doc).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ADS DOF-steps/s & HBM roofline frac, FP32 vs FP64 @ rel-L2; serving p50/p99"
+UNIT = "DOF-steps/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)), src="measured")
+    except Exception:
+        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, src="fallback")
+
+
+def fp32_alu_peak_tflops(sm_count: int, mhz: float) -> float:
+    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def algorithmic_costs(p: int) -> dict:
+    """Algorithmic bytes and flops per DOF of each kernel class (FP32, 4-byte values).
+
+    Flops count the sum-factorised quadrature once per element (no halo
+    recomputation), one FMA = 2 flops, 30 flops per Gauss point for the
+    pointwise terms (exp and reciprocal counted as one each).
+    """
+    q = nb = p + 1
+    W = 2 * p + 1
+    fma = 3 * q * nb + 4 * q * q * nb + 4 * q * q * nb + 3 * q * nb + 2 * (W * W + W)
+    rhs_flops = 2 * fma + 30 * q * q
+    return {
+        # read T, phi; write F, Phi, R
+        "rhs_quadrature_1": dict(bytes=20, flops=rhs_flops),
+        # two arrays (R with X_+, Phi with M^x): read + write each
+        "xsolve_1": dict(bytes=16, flops=2 * (4 * p + 1) * 2),
+        # two arrays: read solve input and base, write result
+        "ysolve_1": dict(bytes=24, flops=2 * (4 * p + 2) * 2),
+        # read T*, F; write R
+        "matvec_2": dict(bytes=12, flops=2 * 2 * (W * W + W) + 2),
+        "xsolve_2": dict(bytes=8, flops=(4 * p + 1) * 2),
+        "ysolve_2": dict(bytes=12, flops=(4 * p + 2) * 2),
+    }
+
+
+def _source_sha(name: str) -> str:
+    with open(os.path.join(ROOT, "paper_2604_19370_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _traffic_record(kernel_site: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        r = rec[kernel_site]
+        if r["source_sha"] != _source_sha(r["source"]):
+            return None
+        return float(r["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict:
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _oracle_sample(steps: int, which: str = "c2", scheme: str = "pr") -> dict:
+    """Run the FP64 oracle (ads mode) in a fresh single-threaded process; returns timing and state file."""
+    out = tempfile.mktemp(suffix=".npz")
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from scenarios import config_c2
+from oracle.step import Problem
+sc = config_c2()
+P = Problem.from_scenario(sc, scheme={scheme!r}, mode='ads')
+T, phi = sc.T0.copy(), sc.fuel0.copy()
+t0 = time.perf_counter()
+for _ in range({steps}):
+    T, phi = P.step(T, phi)
+dt = time.perf_counter() - t0
+np.savez({out!r}, T=T, phi=phi)
+print(json.dumps(dict(seconds=dt, dofs=sc.dofs)))
+"""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    res["state"] = out
+    res["steps"] = steps
+    return res
+
+
+def run_reference(args) -> None:
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    from scenarios import config_c2
+
+    sc = config_c2()
+    # each oracle step takes seconds: warm-up and timed steps are capped to a bounded sample
+    nsteps = min(args.warmup + args.steps, 24)
+    res = _oracle_sample(nsteps)
+    sec_per_step = res["seconds"] / nsteps
+    value = sc.dofs / sec_per_step
+    os.unlink(res["state"])
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": sec_per_step * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "c2_1024x1024_p2_pr", "nx": 1024, "ny": 1024, "p": 2, "dofs": sc.dofs,
+                   "scheme": "PR", "impl": "FP64 CPU oracle, ads mode (1-D banded solves)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{nsteps} PR steps of the 1026^2-DOF workload (FP64, ads mode)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args) -> None:
+    import numpy as np
+    import torch
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2604_19370_gb300.build import build_library
+
+    build_library()
+    from paper_2604_19370_gb300 import wf
+    from scenarios import config_c2
+
+    sc = config_c2(p=args.p) if args.nx == 1024 else None
+    if sc is None:
+        from scenarios import make_scenario
+
+        sc = make_scenario(f"n{args.nx}", args.nx, args.p, 1e-3, 1, 2001, fuel_sigma=20.0,
+                           wind_speed_range=(0.0, 3.0))
+    prec = wf.WF_FP64 if args.fp64 else wf.WF_FP32
+    scheme = wf.WF_STRANG_CN if args.strang else wf.WF_PR
+    sim = wf.simulation_from_scenario(sc, precision=prec, scheme=scheme)
+    stream = torch.cuda.Stream(device=dev)
+    wf.wf_set_stream(sim.h, stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    props = torch.cuda.get_device_properties(dev)
+
+    # warm-up: captures the graphs, settles clocks
+    with torch.cuda.stream(stream):
+        sim.step(args.warmup)
+    stream.synchronize()
+    if sim.sync() != wf.WF_OK:
+        raise RuntimeError("unstable during warm-up")
+
+    # timed region: K steps, L2 flushed before each, per-kernel CUDA events on the launching stream
+    wf.wf_set_profiling(sim.h, True)
+    wf.wf_kernel_times(sim.h)  # reset
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                wf.wf_step(sim.h, 1)
+                ev[k][1].record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize(dev)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kt = wf.wf_kernel_times(sim.h)
+    wf.wf_set_profiling(sim.h, False)
+    status = sim.sync()
+    ms_total = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_per_step = ms_total / args.steps
+    value = world * sc.dofs / (ms_per_step * 1e-3)
+
+    # same steps from CUDA graphs (the production launch path), for reference
+    gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            gev[k][0].record(stream)
+            wf.wf_step(sim.h, 1)
+            gev[k][1].record(stream)
+    stream.synchronize()
+    graph_ms = sum(a.elapsed_time(b) for a, b in gev) / args.steps
+
+    # end to end through the C ABI with pinned host buffers: set state, one step, read state
+    n = sc.dofs
+    hT = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hP = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hT.numpy()[:] = sc.T0.ravel()
+    hP.numpy()[:] = sc.fuel0.ravel()
+    e2e_steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        wf.wf_set_state_ptr(sim.h, hT.data_ptr(), hP.data_ptr(), n)
+        wf.wf_step(sim.h, 1)
+        wf.wf_get_state_ptr(sim.h, hT.data_ptr(), hP.data_ptr(), n)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # roofline of the dominant kernel class
+    peaks = _peaks()
+    costs = algorithmic_costs(sc.p if not args.fp64 else sc.p)
+    es = 8 if args.fp64 else 4
+    shares = {k: v[0] for k, v in kt.items() if v[1] > 0}
+    dom = max(shares, key=shares.get)
+    dom_ms = kt[dom][0] / kt[dom][1]
+    c = costs.get(dom, dict(bytes=0, flops=0))
+    bytes_per_launch = c["bytes"] * (es / 4) * sc.dofs
+    flops_per_launch = c["flops"] * sc.dofs
+    sm_count = props.multi_processor_count
+    alu_peak = fp32_alu_peak_tflops(sm_count, peaks["sm_max_mhz"])
+    balance = alu_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
+    ai = flops_per_launch / max(bytes_per_launch, 1)
+    if ai > balance and not args.fp64:
+        achieved = flops_per_launch / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak,
+                "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {peaks['sm_max_mhz']:.0f} MHz"}
+    else:
+        achieved = bytes_per_launch / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peaks['src']} copy bandwidth"}
+    tr = _traffic_record(dom)
+    roof.update({"kernel": dom, "ms_per_launch": dom_ms, "algorithmic_bytes_per_launch": bytes_per_launch,
+                 "algorithmic_flops_per_launch": flops_per_launch, "traffic": tr})
+    # whole-step HBM view: algorithmic bytes of all kernels of the step over the step time
+    step_bytes = sum(costs[k]["bytes"] for k in costs if k in shares) * (es / 4) * sc.dofs
+    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / sum(shares.values())}
+               for k, v in kt.items() if v[1] > 0}
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.fp64 else "f32",
+        "data": "synthetic",
+        "config": {"workload": f"c2_{sc.nx}x{sc.ny}_p{sc.p}_{'strang' if args.strang else 'pr'}",
+                   "nx": sc.nx, "ny": sc.ny, "p": sc.p, "dofs": sc.dofs,
+                   "scheme": "Strang-CN" if args.strang else "PR",
+                   "precision": "fp64" if args.fp64 else "fp32 bulk, fp64 1-D factorisation",
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "step_hbm_frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / peaks["hbm_gbs"],
+        "graph_ms_per_step": graph_ms,
+        "kernels": kernels,
+        "gpu_launches": int(sum(v[1] for v in kt.values())),
+        "e2e": {"value": world * sc.dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n,
+                "d2h_bytes_per_step": 2 * 8 * n, "ms_per_step": e2e_s * 1e3},
+        "clocks": clk.summary(),
+        "status": wf.wf_strerror(status),
+    }
+
+    # oracle baseline on a bounded sample (rank 0, N=1) and the rel-L2 of this path on the same steps
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ks = args.cpu_steps
+        res = _oracle_sample(ks, scheme="strang" if args.strang else "pr")
+        d = np.load(res["state"])
+        os.unlink(res["state"])
+        chk = wf.simulation_from_scenario(sc, precision=prec, scheme=scheme)
+        chk.step(ks)
+        Tg, pg = chk.state()
+        chk.close()
+        rl = float(np.linalg.norm(Tg - d["T"]) / np.linalg.norm(d["T"]))
+        rla = float(np.linalg.norm(Tg - d["T"]) / np.linalg.norm(d["T"] - 300.0))
+        rlp = float(np.linalg.norm(pg - d["phi"]) / np.linalg.norm(d["phi"]))
+        line["cpu_baseline"] = {"value": sc.dofs * ks / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{ks} PR steps of the same 1026^2-DOF workload, FP64, ads mode"}
+        line["rel_l2_vs_oracle"] = {"steps": ks, "T": rl, "T_minus_Tamb": rla, "phi": rlp}
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--p", type=int, default=2)
+    ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--strang", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()
