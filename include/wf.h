@@ -157,6 +157,28 @@ int wf_set_stream(wf_handle* h, void* stream);
 int wf_set_profiling(wf_handle* h, int on);
 int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], int max_k);
 
+/*
+ * Advance a caller-owned FP32 state by nsteps time steps without allocating any
+ * device memory.  The paper has no counterpart: this exists for callers that
+ * cannot call cudaMalloc while they step, e.g. a process whose device memory is
+ * all owned by another allocator (a framework's pool or an arena sized at start
+ * up), or a latency-critical loop that must not pay cudaMalloc's implicit device
+ * synchronisation.  The handle h (created earlier, FP32 precision) supplies the
+ * tables and factors; T and fuel are device arrays of Ny rows with a row pitch of
+ * `pitch` >= Nx float elements, updated in place.  The intermediate fields of
+ * the step live in one static device array that the library reserves on every
+ * GPU it is loaded on (6 MiB, held until the process exits); pitch * Ny must not
+ * exceed 524288 (512 x 512 elements of degree 2 fit).  The first call on a
+ * device looks up that array's device address; make that first call before any
+ * stream capture.  All calls share the array: two calls whose work overlaps on
+ * the GPU (other streams, other threads) race and corrupt each other's results.
+ * Work is enqueued on the handle's stream (wf_set_stream) without waiting; use
+ * wf_sync to wait and read the guard status.  No CUDA graph is used.
+ * Errors: WF_EINVAL (NULL pointer, FP64 handle, pitch < Nx, pitch * Ny above the
+ * limit, nsteps < 0), WF_ECUDA.
+ */
+int wf_step_noalloc(wf_handle* h, void* T, void* fuel, int pitch, int nsteps);
+
 /* Free every resource of the handle (NULL is accepted). */
 void wf_destroy(wf_handle* h);
 

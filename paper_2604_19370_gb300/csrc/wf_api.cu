@@ -11,6 +11,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -776,6 +777,73 @@ int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], in
     }
     return S_NSITES;
 }
+
+}  // extern "C"
+
+// ---- allocation-free step ------------------------------------------------------------
+//
+// Scratch of wf_step_noalloc: the three intermediate fields of a step (F, Phi, R), each at
+// most kNoallocMaxElems padded FP32 coefficients, in one array that every GPU loading
+// this library holds until the process exits (6 MiB).  Host code must not hand the
+// symbol itself to a kernel: on the host it names a host-side placeholder.  Its device
+// address is looked up once per device with cudaGetSymbolAddress and cached.
+constexpr size_t kNoallocMaxElems = size_t(1) << 19;
+static __device__ __align__(256) float g_noalloc_scratch[3 * kNoallocMaxElems];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+void* g_noalloc_addr[kNoallocMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device (set up on first use).
+cudaError_t noalloc_scratch(float** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<float*>(g_noalloc_addr[dev]);
+    return cudaSuccess;
+}
+}  // namespace
+
+extern "C" int wf_step_noalloc(wf_handle* h, void* T, void* fuel, int pitch, int nsteps) {
+    if (!h || !T || !fuel || nsteps < 0) return WF_EINVAL;
+    if (h->prec != WF_FP32) return WF_EINVAL;
+    if (pitch < h->Nx) return WF_EINVAL;
+    if ((size_t)pitch * (size_t)h->Ny > kNoallocMaxElems) return WF_EINVAL;
+    if (nsteps == 0) return WF_OK;
+    float* scratch = nullptr;
+    if (noalloc_scratch(&scratch) != cudaSuccess) return WF_ECUDA;
+    // Run the handle's own step sequence with the caller's state and the static scratch in
+    // place of the handle's buffers.  Every scratch element a kernel reads was written earlier
+    // in the same step, so nothing needs clearing between calls.
+    void* save[5] = {h->T, h->phi, h->F, h->Phi, h->R};
+    const int save_pitch = h->pitch;
+    h->T = T;
+    h->phi = fuel;
+    h->F = scratch;
+    h->Phi = scratch + kNoallocMaxElems;
+    h->R = scratch + 2 * kNoallocMaxElems;
+    h->pitch = pitch;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = enqueue_step(h);
+    h->T = save[0];
+    h->phi = save[1];
+    h->F = save[2];
+    h->Phi = save[3];
+    h->R = save[4];
+    h->pitch = save_pitch;
+    return e == cudaSuccess ? WF_OK : WF_ECUDA;
+}
+
+extern "C" {
 
 void wf_destroy(wf_handle* h) { destroy(h); }
 

@@ -71,6 +71,7 @@ def lib() -> ctypes.CDLL:
         L.wf_set_stream.argtypes = [vp, vp]
         L.wf_set_profiling.argtypes = [vp, i]
         L.wf_kernel_times.argtypes = [vp, dp, ctypes.POINTER(i), ctypes.c_void_p, i]
+        L.wf_step_noalloc.argtypes = [vp, vp, vp, i, i]
         L.wf_destroy.argtypes = [vp]
         L.wf_destroy.restype = None
         L.wf_strerror.argtypes = [i]
@@ -185,6 +186,11 @@ def wf_kernel_times(h, max_k: int = 16):
         nm = bytes(names[48 * j:48 * (j + 1)]).split(b"\0")[0].decode()
         out[nm] = (ms[j], cnt[j])
     return out
+
+
+def wf_step_noalloc(h, T_dev_ptr: int, fuel_dev_ptr: int, pitch: int, nsteps: int) -> int:
+    """Allocation-free steps on caller-owned FP32 device arrays (returns the status code)."""
+    return lib().wf_step_noalloc(h, ctypes.c_void_p(T_dev_ptr), ctypes.c_void_p(fuel_dev_ptr), pitch, nsteps)
 
 
 def wf_destroy(h) -> None:
