@@ -39,9 +39,13 @@ struct Arena {
 struct Op {
     double aM = 0, aK = 0, aG = 0;
     bool factored = false;
+    bool compact = false;
     Chunks ch{};
+    int mmax = 0;
     double *band64 = nullptr, *lu64 = nullptr, *spk64 = nullptr, *E64 = nullptr;
     void *bandP = nullptr, *luP = nullptr, *spkP = nullptr, *EP = nullptr;
+    double *luc64 = nullptr, *spkc64 = nullptr, *Ec64 = nullptr;
+    void *lucP = nullptr, *spkcP = nullptr, *EcP = nullptr;
 };
 
 struct Dir {
@@ -99,13 +103,20 @@ namespace {
 
 size_t esize(int prec) { return prec == WF_FP32 ? 4 : 8; }
 
-Chunks make_chunks(int N, int target) {
+// Chunks of length `base`; the last chunk takes the remainder and is merged into its
+// neighbour when it would be shorter than 2p, so every chunk holds at least 2p rows
+// and the interior chunks (1 .. C-2) lie entirely in the Toeplitz part of the operator.
+Chunks make_chunks(int N, int base, int p) {
     Chunks c;
     c.N = N;
-    c.C = N / target;
-    if (c.C < 1) c.C = 1;
-    c.base = N / c.C;
-    c.rem = N % c.C;
+    c.base = base;
+    c.C = (N + base - 1) / base;
+    c.last = N - (c.C - 1) * base;
+    if (c.C > 1 && c.last < 2 * p) {
+        c.C -= 1;
+        c.last += base;
+    }
+    if (c.C == 1) c.last = N;
     return c;
 }
 
@@ -120,7 +131,7 @@ void layout(wf_handle* h, Arena& A) {
     h->stage = A.take<double>(2 * (size_t)h->Nx * h->Ny);
     h->gxi = A.take<double>(16);
     h->gw = A.take<double>(16);
-    h->diag = A.take<double>(2);
+    h->diag = A.take<double>(4);
     h->status = A.take<int>(4);
     const int W = 2 * h->p + 1;
     int maxN = h->Nx > h->Ny ? h->Nx : h->Ny;
@@ -150,16 +161,26 @@ void layout(wf_handle* h, Arena& A) {
             o.lu64 = A.take<double>((size_t)d->N * W);
             o.spk64 = A.take<double>((size_t)d->N * 2 * h->p);
             o.E64 = A.take<double>(nE);
+            o.mmax = o.ch.base + 2 * h->p;
+            o.luc64 = A.take<double>((size_t)3 * o.mmax * W);
+            o.spkc64 = A.take<double>((size_t)3 * o.mmax * 2 * h->p);
+            o.Ec64 = A.take<double>((size_t)3 * h->p * h->p);
             if (h->prec == WF_FP32) {
                 o.bandP = A.take<float>((size_t)d->N * W);
                 o.luP = o.factored ? (void*)A.take<float>((size_t)d->N * W) : nullptr;
                 o.spkP = o.factored ? (void*)A.take<float>((size_t)d->N * 2 * h->p) : nullptr;
                 o.EP = o.factored ? (void*)A.take<float>(nE) : nullptr;
+                o.lucP = o.factored ? (void*)A.take<float>((size_t)3 * o.mmax * W) : nullptr;
+                o.spkcP = o.factored ? (void*)A.take<float>((size_t)3 * o.mmax * 2 * h->p) : nullptr;
+                o.EcP = o.factored ? (void*)A.take<float>((size_t)3 * h->p * h->p) : nullptr;
             } else {
                 o.bandP = o.band64;
                 o.luP = o.lu64;
                 o.spkP = o.spk64;
                 o.EP = o.E64;
+                o.lucP = o.luc64;
+                o.spkcP = o.spkc64;
+                o.EcP = o.Ec64;
             }
         }
     }
@@ -279,23 +300,28 @@ int build_factors(wf_handle* h, double tol, double* worst) {
     Dir* ds[2] = {&h->dx, &h->dy};
     for (Dir* d : ds) {
         for (Op& o : d->op) {
-            double zero[2] = {0.0, 0.0};
+            double zero[4] = {0.0, 0.0, 0.0, 0.0};
             WF_TRY(cudaMemcpyAsync(h->diag, zero, sizeof(zero), cudaMemcpyHostToDevice, s));
             WF_TRY(launch_factor(d->M64, d->K64, d->G64, o.aM, o.aK, o.aG, d->N, h->p, o.ch, o.band64, o.lu64,
                                  o.spk64, o.E64, h->work64, h->diag, s));
-            double dg[2];
+            WF_TRY(launch_compact(o.lu64, o.spk64, o.E64, h->p, o.ch, o.mmax, o.luc64, o.spkc64, o.Ec64, h->diag, s));
+            double dg[4];
             WF_TRY(cudaMemcpyAsync(dg, h->diag, sizeof(dg), cudaMemcpyDeviceToHost, s));
             WF_TRY(cudaStreamSynchronize(s));
             if (o.factored) {
                 if (dg[0] != 0.0) return WF_ESINGULAR;
                 if (dg[1] > *worst) *worst = dg[1];
             }
+            o.compact = o.factored && dg[2] == 0.0;
             if (h->prec != WF_FP32) continue;
             WF_TRY(launch_to_f32(o.band64, (float*)o.bandP, (size_t)d->N * W, s));
             if (o.factored) {
                 WF_TRY(launch_to_f32(o.lu64, (float*)o.luP, (size_t)d->N * W, s));
                 WF_TRY(launch_to_f32(o.spk64, (float*)o.spkP, (size_t)d->N * 2 * h->p, s));
                 WF_TRY(launch_to_f32(o.E64, (float*)o.EP, (size_t)(o.ch.C > 1 ? o.ch.C - 1 : 1) * h->p * h->p, s));
+                WF_TRY(launch_to_f32(o.luc64, (float*)o.lucP, (size_t)3 * o.mmax * W, s));
+                WF_TRY(launch_to_f32(o.spkc64, (float*)o.spkcP, (size_t)3 * o.mmax * 2 * h->p, s));
+                WF_TRY(launch_to_f32(o.Ec64, (float*)o.EcP, (size_t)3 * h->p * h->p, s));
             }
         }
     }
@@ -309,6 +335,11 @@ FactorV fv(const Op& o) {
     f.lu = o.luP;
     f.spk = o.spkP;
     f.E = o.EP;
+    f.compact = o.compact ? 1 : 0;
+    f.mmax = o.mmax;
+    f.luc = o.lucP;
+    f.spkc = o.spkcP;
+    f.Ec = o.EcP;
     return f;
 }
 
@@ -587,16 +618,23 @@ int wf_create(int nx, int ny, int p, double dt, const wf_params* params, wf_hand
     h->stream = h->own;
     set_op_coeffs(h);
 
-    // chunk length: FP32 needs the neglected spike coupling below 1e-8, FP64 below 1e-15
+    // Chunk length: the truncated reduced system must neglect spike entries below 1e-8
+    // (FP32) or 1e-15 (FP64); the shortest length that does is used.
     const double tol = h->prec == WF_FP32 ? 1e-8 : 1e-15;
-    int target = h->prec == WF_FP32 ? 32 : 64;
-    const int G = line_rows_per_cta(h->prec);
+    static const int bases32[] = {32, 48, 64, 96, 128, 256, 512, 1024, 2048, 8192};
+    static const int bases64[] = {48, 64, 96, 128, 192, 256, 512, 1024, 2048, 8192};
+    const int* bases = h->prec == WF_FP32 ? bases32 : bases64;
     int rc = WF_OK;
-    for (int attempt = 0; attempt < 12; ++attempt) {
+    for (int attempt = 0; attempt < 10; ++attempt) {
         Dir* ds[2] = {&h->dx, &h->dy};
         for (Dir* d : ds) {
-            Chunks ch = make_chunks(d->N, target);
-            while (G * ch.C > 1024) ch = make_chunks(d->N, ch.base * 2);
+            // at most 32 chunks per line (one warp lane or one thread row each); odd lengths
+            // keep the 32 lanes of the x pass on distinct shared-memory banks
+            int base = bases[attempt];
+            const int need = (d->N + 31) / 32;
+            if (base < need) base = need;
+            base |= 1;
+            Chunks ch = make_chunks(d->N, base, p);
             for (Op& o : d->op) o.ch = ch;
         }
         if (h->mem) {
@@ -618,7 +656,6 @@ int wf_create(int nx, int ny, int p, double dt, const wf_params* params, wf_hand
         rc = build_factors(h, tol, &worst);
         if (rc != WF_ETRUNC) break;
         if (h->dx.op[0].ch.C == 1 && h->dy.op[0].ch.C == 1) break;
-        target *= 2;
     }
     if (rc != WF_OK) {
         destroy(h);

@@ -25,13 +25,21 @@ struct Phys {
     int heat_by_fuel;
 };
 
-// Partition of a line of N unknowns into C chunks of length base or base+1
-// (the first `rem` chunks are one longer).
+// Partition of a line of N unknowns into C chunks: chunk k starts at k*base and has
+// length base, except the last one, which has length `last` in [2p, base + 2p)
+// (a single chunk, C = 1, has length N).
 struct Chunks {
-    int N, C, base, rem;
+    int N, C, base, last;
 };
-__host__ __device__ inline int chunk_start(const Chunks& c, int k) { return k * c.base + (k < c.rem ? k : c.rem); }
-__host__ __device__ inline int chunk_len(const Chunks& c, int k) { return c.base + (k < c.rem ? 1 : 0); }
+__host__ __device__ inline int chunk_start(const Chunks& c, int k) { return k * c.base; }
+__host__ __device__ inline int chunk_len(const Chunks& c, int k) { return k < c.C - 1 ? c.base : c.last; }
+__host__ __device__ inline int chunk_of(const Chunks& c, int x) {
+    const int k = x / c.base;
+    return k < c.C - 1 ? k : c.C - 1;
+}
+// Chunk and interface types of the compact factor form: 0 = first, 1 = interior, 2 = last.
+__host__ __device__ inline int chunk_type(const Chunks& c, int k) { return k == 0 ? 0 : (k == c.C - 1 ? 2 : 1); }
+__host__ __device__ inline int iface_type(const Chunks& c, int k) { return k == 0 ? 0 : (k == c.C - 2 ? 2 : 1); }
 
 // Chunked LU of a banded 1-D operator A (half-bandwidth p), truncated-SPIKE form.
 //   lu[r][0..p-1]  multipliers: forward row r subtracts lu[r][i-1] * y[r-i]
@@ -40,11 +48,20 @@ __host__ __device__ inline int chunk_len(const Chunks& c, int k) { return c.base
 //   spk[r][0..p-1] V (right spike of the chunk holding r), spk[r][p..2p-1] W (left spike)
 //   E[k][p][p]     (I - W_{k+1}^top V_k^bottom)^{-1} for the interface between chunks k and k+1
 // Every product is chunk-local: entries coupling two chunks are carried by the spikes.
+//
+// Compact form: with uniform open knots every interior chunk (1 .. C-2) of an operator
+// has bitwise identical factors, so three chunk types suffice whatever N is:
+//   luc[t][o][2p+1], spkc[t][o][2p] for o < mmax (= base + 2p), Ec[t][p][p], t in {0,1,2}.
 struct FactorV {
     Chunks ch;
     const void* lu;
     const void* spk;
     const void* E;
+    int compact;  // 1 if luc/spkc/Ec are valid (interior chunks verified identical)
+    int mmax;
+    const void* luc;
+    const void* spkc;
+    const void* Ec;
 };
 
 // ---- tables and factorisation (FP64, wf_tables.cu) ---------------------------------
@@ -58,6 +75,10 @@ cudaError_t launch_factor(const double* Mb, const double* Kb, const double* Gb, 
                           int N, int p, Chunks ch, double* band64, double* lu64, double* spk64, double* E64,
                           double* work64, double* diag, cudaStream_t s);
 cudaError_t launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s);
+// Compact copies of chunk types 0/1/2 (see FactorV); diag[2] = 1.0 if an interior chunk differs
+// from chunk 1 bit for bit (then the compact form must not be used).
+cudaError_t launch_compact(const double* lu, const double* spk, const double* E, int p, Chunks ch, int mmax,
+                           double* luc, double* spkc, double* Ec, double* diag, cudaStream_t s);
 // out[r][e*q+a] = sum_l B[e][a][l] coef[r][e+l]  (1-D spline factor at Gauss points)
 cudaError_t launch_factor_points(int prec, const double* coef, int rank, int n, int p, const double* B,
                                  void* out, cudaStream_t s);
@@ -100,6 +121,9 @@ struct LineArgs {
 };
 cudaError_t launch_xsolve(int prec, int p, const LineArgs& a, cudaStream_t s);
 cudaError_t launch_ysolve(int prec, int p, const LineArgs& a, cudaStream_t s);
+// compact-factor form (wf_linefast.cu); returns cudaErrorNotSupported when it cannot
+// take the arguments (factors not compact, more than 256 threads, shared memory)
+cudaError_t launch_line_fast(int prec, int p, bool xdir, const LineArgs& a, cudaStream_t s);
 
 // R = Fscale F + c1 (A1 (x) B1) T + c2 (A2 (x) B2) T   (A2 may be NULL)
 struct MatvecArgs {

@@ -1,0 +1,534 @@
+// Chunked line solves (TMA-staged x pass, column-parallel y pass) and the tiled Kronecker matvec.
+//
+// Paper: Sec. 4 ("Cost of directional implicit solves"): each directional system
+// is a set of independent banded 1-D solves (half-bandwidth p) along x or y.
+//
+// Every line is cut into at most 32 chunks; one thread owns one chunk (`base`
+// values, or the last chunk of at most base + 2p values), runs the chunk-local LU
+// substitution with the recurrence in registers, solves the p x p interface
+// systems of truncated SPIKE with its neighbours' boundary values and applies the
+// spike corrections.  LU factors and spikes come from shared memory in their
+// compact form: with uniform open knots every interior chunk has the same factors,
+// so a CTA stages three chunk types (first, interior, last) whatever the length.
+//
+// x pass: one warp per row, one lane per chunk.  The rows of a CTA are contiguous
+// in memory and move with one TMA bulk copy each way (cp.async.bulk with an
+// mbarrier); neighbouring chunks exchange boundary values by warp shuffles.
+// y pass: a CTA owns G columns; lanes of neighbouring columns read and write
+// contiguous runs of G elements per row, 16 loads in flight per thread.
+#include "wf_internal.h"
+
+namespace wf {
+
+namespace {
+
+template <typename P>
+struct FastArgs {
+    int nlines, pitch, mpad, G;
+    Chunks ch;
+    const P* in[2];
+    P* out[2];
+    const P* base[2];
+    const P* premul[2];
+    P prescale[2];
+    const P* luc[2];
+    const P* spkc[2];
+    const P* Ec[2];
+    int* status;
+    P tmax;
+    int tma;  // x pass: rows staged with bulk copies (16-byte aligned rows)
+};
+
+// ---- TMA bulk copies and mbarrier (PTX) ------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// global -> shared, completion signalled on the mbarrier (16-byte aligned, size multiple of 16)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// shared -> global, tracked by the bulk async-group of the issuing thread
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit_and_wait_read() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+constexpr uint32_t kSpinLimit = 1u << 20;  // bounded mbarrier wait; a timeout sets status bit 2
+
+// Chunk-local LU substitution on g[0 .. m) (stride 1) with the factors of one chunk type.
+template <typename P, int PD>
+__device__ __forceinline__ void lu_chunk(P* g, int m, const P* L) {
+    constexpr int W = 2 * PD + 1;
+    P prev[PD];
+#pragma unroll
+    for (int i = 0; i < PD; ++i) prev[i] = P(0);
+#pragma unroll 4
+    for (int o = 0; o < m; ++o) {
+        P x = g[o];
+#pragma unroll
+        for (int i = 0; i < PD; ++i) x -= L[o * W + i] * prev[i];
+#pragma unroll
+        for (int i = PD - 1; i > 0; --i) prev[i] = prev[i - 1];
+        prev[0] = x;
+        g[o] = x;
+    }
+#pragma unroll
+    for (int i = 0; i < PD; ++i) prev[i] = P(0);
+#pragma unroll 4
+    for (int o = m - 1; o >= 0; --o) {
+        P x = g[o];
+#pragma unroll
+        for (int j = 0; j < PD; ++j) x -= L[o * W + PD + 1 + j] * prev[j];
+        x *= L[o * W + PD];
+#pragma unroll
+        for (int j = PD - 1; j > 0; --j) prev[j] = prev[j - 1];
+        prev[0] = x;
+        g[o] = x;
+    }
+}
+
+// Interface values of chunk k from its own boundary values and its neighbours':
+// tn = first PD values of chunk k+1, bp = last PD values of chunk k-1 (truncated SPIKE).
+template <typename P, int PD>
+__device__ __forceinline__ void interface_solve(const Chunks& ch, int k, int mmax, const P* fs, const P* fe,
+                                                const P* own_top, const P* own_bot, const P* nxt_top,
+                                                const P* prv_bot, P* tn, P* bp) {
+    constexpr int S = 2 * PD;
+    const int base = ch.base;
+#pragma unroll
+    for (int q = 0; q < PD; ++q) tn[q] = bp[q] = P(0);
+    if (k + 1 < ch.C) {
+        const P* Wn = fs + chunk_type(ch, k + 1) * mmax * S;
+        const P* E = fe + iface_type(ch, k) * PD * PD;
+        P rhs[PD];
+#pragma unroll
+        for (int q = 0; q < PD; ++q) {
+            P x = nxt_top[q];
+#pragma unroll
+            for (int r = 0; r < PD; ++r) x -= Wn[q * S + PD + r] * own_bot[r];
+            rhs[q] = x;
+        }
+#pragma unroll
+        for (int q = 0; q < PD; ++q) {
+            P x = 0;
+#pragma unroll
+            for (int r = 0; r < PD; ++r) x += E[q * PD + r] * rhs[r];
+            tn[q] = x;
+        }
+    }
+    if (k > 0) {
+        const P* Wk = fs + chunk_type(ch, k) * mmax * S;
+        const P* E = fe + iface_type(ch, k - 1) * PD * PD;
+        const P* Vp = fs + (chunk_type(ch, k - 1) * mmax + base - PD) * S;
+        P rhs[PD], tk[PD];
+#pragma unroll
+        for (int q = 0; q < PD; ++q) {
+            P x = own_top[q];
+#pragma unroll
+            for (int r = 0; r < PD; ++r) x -= Wk[q * S + PD + r] * prv_bot[r];
+            rhs[q] = x;
+        }
+#pragma unroll
+        for (int q = 0; q < PD; ++q) {
+            P x = 0;
+#pragma unroll
+            for (int r = 0; r < PD; ++r) x += E[q * PD + r] * rhs[r];
+            tk[q] = x;
+        }
+#pragma unroll
+        for (int q = 0; q < PD; ++q) {
+            P x = prv_bot[q];
+#pragma unroll
+            for (int r = 0; r < PD; ++r) x -= Vp[q * S + r] * tk[r];
+            bp[q] = x;
+        }
+    }
+}
+
+template <typename P>
+__device__ __forceinline__ void stage_factors(const FastArgs<P>& a, int arr, int n_lu, int n_spk, int n_e, P* fl,
+                                              P* fs, P* fe) {
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const P* __restrict__ g1 = a.luc[arr];
+    const P* __restrict__ g2 = a.spkc[arr];
+    const P* __restrict__ g3 = a.Ec[arr];
+    for (int i = tid; i < n_lu; i += nt) fl[i] = g1[i];
+    for (int i = tid; i < n_spk; i += nt) fs[i] = g2[i];
+    for (int i = tid; i < n_e; i += nt) fe[i] = g3[i];
+}
+
+// x pass.  CTA = G warps; warp w solves row blockIdx.x*G + w, lane k owns chunk k (C <= 32).
+// The G rows are contiguous in memory: one bulk copy stages them, one bulk store writes them back.
+// Chunk lengths are odd, so the 32 lanes of a warp read 32 distinct shared-memory banks.
+template <typename P, int PD>
+__global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
+    constexpr int W = 2 * PD + 1, S = 2 * PD;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const Chunks ch = a.ch;
+    const int N = ch.N, C = ch.C, base = ch.base, G = a.G;
+    const int mmax = base + 2 * PD;
+    const int arr = blockIdx.y;
+    const int j0 = blockIdx.x * G;
+    const int rows = min(G, a.nlines - j0);
+    const size_t row_bytes = (size_t)a.pitch * sizeof(P);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    P* rowbuf = reinterpret_cast<P*>(smem_raw + 128);  // [G][pitch]
+    P* fl = rowbuf + (size_t)G * a.pitch;               // [3][mmax][W]
+    P* fs = fl + 3 * mmax * W;                          // [3][mmax][S]
+    P* fe = fs + 3 * mmax * S;                          // [3][PD*PD]
+    const P* __restrict__ in = a.in[arr];
+    P* out = a.out[arr];
+
+    bool staged = true;
+    if (a.tma) {
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            mbar_fence_init();
+            const uint32_t bytes = (uint32_t)(rows * row_bytes);
+            mbar_expect_tx(bar, bytes);
+            bulk_load(rowbuf, in + (size_t)j0 * a.pitch, bytes, bar);
+        }
+    } else {
+        for (int r = 0; r < rows; ++r)
+            for (int x = tid; x < N; x += blockDim.x) rowbuf[(size_t)r * a.pitch + x] = in[(size_t)(j0 + r) * a.pitch + x];
+    }
+    stage_factors(a, arr, 3 * mmax * W, 3 * mmax * S, 3 * PD * PD, fl, fs, fe);
+    __syncthreads();  // mbarrier initialised, factors staged
+    if (a.tma) {
+        uint32_t it = 0;
+        while (!mbar_try_wait(bar, 0) && ++it < kSpinLimit) {
+        }
+        if (it >= kSpinLimit) staged = false;
+    }
+    if (!staged) {
+        // give the copy in flight a second bounded wait before the shared memory is released
+        uint32_t it = 0;
+        while (!mbar_try_wait(bar, 0) && ++it < kSpinLimit) {
+        }
+        if (tid == 0 && a.status) atomicOr(a.status, 4);
+        return;
+    }
+
+    const bool active = warp < rows && lane < C;
+    const int k = lane;
+    const int m = (k < C - 1) ? base : ch.last;
+    P* g = rowbuf + (size_t)warp * a.pitch + (size_t)k * base;
+    const int t = chunk_type(ch, k < C ? k : 0);
+    if (active) lu_chunk<P, PD>(g, m, fl + t * mmax * W);
+    __syncwarp();
+    P top[PD], bot[PD], nxt_top[PD], prv_bot[PD];
+#pragma unroll
+    for (int q = 0; q < PD; ++q) {
+        top[q] = active ? g[q] : P(0);
+        bot[q] = (active && k + 1 < C) ? g[base - PD + q] : P(0);
+    }
+#pragma unroll
+    for (int q = 0; q < PD; ++q) {
+        nxt_top[q] = __shfl_down_sync(0xffffffffu, top[q], 1);
+        prv_bot[q] = __shfl_up_sync(0xffffffffu, bot[q], 1);
+    }
+    P tn[PD], bp[PD];
+    interface_solve<P, PD>(ch, k < C ? k : 0, mmax, fs, fe, top, bot, nxt_top, prv_bot, tn, bp);
+    if (active) {
+        const P* Sk = fs + t * mmax * S;
+#pragma unroll 4
+        for (int o = 0; o < m; ++o) {
+            P x = g[o];
+#pragma unroll
+            for (int r = 0; r < PD; ++r) x -= Sk[o * S + r] * tn[r] + Sk[o * S + PD + r] * bp[r];
+            g[o] = x;
+        }
+    }
+    if (a.tma) {
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            bulk_store(out + (size_t)j0 * a.pitch, rowbuf, (uint32_t)(rows * row_bytes));
+            bulk_commit_and_wait_read();
+        }
+    } else {
+        __syncthreads();
+        for (int r = 0; r < rows; ++r)
+            for (int x = tid; x < N; x += blockDim.x) out[(size_t)(j0 + r) * a.pitch + x] = rowbuf[(size_t)r * a.pitch + x];
+    }
+}
+
+// y pass.  CTA = G columns x C chunks (blockDim = G*C <= 256); thread tid = k*G + c owns chunk k
+// of column c in its private shared-memory region (odd stride: distinct banks).  Loads are
+// issued in batches of 16 before use so each thread keeps 16 requests in flight.
+template <typename P, int PD>
+__global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
+    constexpr int W = 2 * PD + 1, S = 2 * PD, B = 16;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const Chunks ch = a.ch;
+    const int N = ch.N, C = ch.C, base = ch.base, G = a.G, mpad = a.mpad;
+    const int mmax = base + 2 * PD;
+    P* fl = reinterpret_cast<P*>(smem_raw);  // [3][mmax][W]
+    P* fs = fl + 3 * mmax * W;               // [3][mmax][S]
+    P* fe = fs + 3 * mmax * S;               // [3][PD*PD]
+    P* buf = fe + 3 * PD * PD;               // [nt][mpad]
+    const int arr = blockIdx.y;
+    const int k = tid / G, c = tid - k * G;
+    const int s = k * base;
+    const int m = (k < C - 1) ? base : ch.last;
+    const int t = chunk_type(ch, k);
+    const int line = blockIdx.x * G + c;
+    const bool valid = line < a.nlines;
+    const P* __restrict__ in = a.in[arr];
+    P* out = a.out[arr];
+    P* g = buf + (size_t)tid * mpad;
+
+    stage_factors(a, arr, 3 * mmax * W, 3 * mmax * S, 3 * PD * PD, fl, fs, fe);
+    const P* __restrict__ pre = a.premul[arr];
+    for (int o0 = 0; o0 < m; o0 += B) {
+        P r[B];
+        if (pre) {
+            const P ps = a.prescale[arr];
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                const int row = s + o0 + q;
+                P acc = 0;
+                if (valid && o0 + q < m) {
+#pragma unroll
+                    for (int d = 0; d < W; ++d) {
+                        const int rr = row + d - PD;
+                        if (rr >= 0 && rr < N) acc += pre[(size_t)row * W + d] * in[(size_t)rr * a.pitch + line];
+                    }
+                }
+                r[q] = ps * acc;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < B; ++q)
+                r[q] = (valid && o0 + q < m) ? in[(size_t)(s + o0 + q) * a.pitch + line] : P(0);
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q)
+            if (o0 + q < m) g[o0 + q] = r[q];
+    }
+    __syncthreads();
+    lu_chunk<P, PD>(g, m, fl + t * mmax * W);
+    __syncthreads();
+    const P* gn = buf + (size_t)((k + 1 < C ? k + 1 : k) * G + c) * mpad;
+    const P* gp = buf + (size_t)((k > 0 ? k - 1 : k) * G + c) * mpad + (base - PD);
+    P tn[PD], bp[PD];
+    interface_solve<P, PD>(ch, k, mmax, fs, fe, g, g + (base - PD), gn, gp, tn, bp);
+    if (!valid) return;  // no barrier follows
+    const P* Sk = fs + t * mmax * S;
+    const P* __restrict__ bs = a.base[arr];
+    const bool guard = (a.status != nullptr) && arr == 0;
+    bool bad = false;
+    for (int o0 = 0; o0 < m; o0 += B) {
+        P b[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) b[q] = (bs && o0 + q < m) ? bs[(size_t)(s + o0 + q) * a.pitch + line] : P(0);
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            const int o = o0 + q;
+            if (o < m) {
+                P x = g[o];
+#pragma unroll
+                for (int r = 0; r < PD; ++r) x -= Sk[o * S + r] * tn[r] + Sk[o * S + PD + r] * bp[r];
+                x += b[q];
+                out[(size_t)(s + o) * a.pitch + line] = x;
+                if (guard) bad |= !(fabs((double)x) <= (double)a.tmax);
+            }
+        }
+    }
+    if (guard && bad) atomicOr(a.status, 1);
+}
+
+template <typename P, int PD, bool X>
+cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
+    constexpr int W = 2 * PD + 1, S = 2 * PD;
+    const Chunks& ch = a.f[0].ch;
+    if (ch.C > 32) return cudaErrorNotSupported;
+    const int mmax = ch.base + 2 * PD;
+    const size_t fbytes = ((size_t)3 * mmax * (W + S) + 3 * PD * PD) * sizeof(P);
+    FastArgs<P> f;
+    f.nlines = a.nlines;
+    f.pitch = a.pitch;
+    f.ch = ch;
+    for (int q = 0; q < 2; ++q) {
+        f.in[q] = (const P*)a.in[q];
+        f.out[q] = (P*)a.out[q];
+        f.base[q] = (const P*)a.base[q];
+        f.premul[q] = (const P*)a.premul[q];
+        f.prescale[q] = (P)a.prescale[q];
+        f.luc[q] = (const P*)a.f[q].luc;
+        f.spkc[q] = (const P*)a.f[q].spkc;
+        f.Ec[q] = (const P*)a.f[q].Ec;
+    }
+    f.status = a.status;
+    f.tmax = (P)a.tmax;
+    f.mpad = (ch.base > ch.last ? ch.base : ch.last) | 1;
+    if (X) {
+        // rows per CTA: as many warps as fit 100 KB of staged rows (at least one)
+        const size_t row_bytes = (size_t)a.pitch * sizeof(P);
+        int G = 8;
+        while (G > 1 && 128 + G * row_bytes + fbytes > 100 * 1024) G /= 2;
+        const size_t smem = 128 + G * row_bytes + fbytes;
+        if (smem > 227 * 1024) return cudaErrorNotSupported;
+        bool aligned = (row_bytes % 16 == 0);
+        for (int q = 0; q < a.narr; ++q)
+            aligned = aligned && ((uintptr_t)a.in[q] % 16 == 0) && ((uintptr_t)a.out[q] % 16 == 0);
+        f.G = G;
+        f.tma = aligned ? 1 : 0;
+        auto kern = k_xsolve_warp<P, PD>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((a.nlines + G - 1) / G, a.narr);
+        kern<<<grid, 32 * G, smem, s>>>(f);
+    } else {
+        int G = sizeof(P) == 4 ? 8 : 4;
+        while (G > 1 && G * ch.C > 256) G /= 2;
+        const int nt = G * ch.C;
+        if (nt > 256) return cudaErrorNotSupported;
+        const size_t smem = fbytes + (size_t)nt * f.mpad * sizeof(P);
+        if (smem > 227 * 1024) return cudaErrorNotSupported;
+        f.G = G;
+        f.tma = 0;
+        auto kern = k_ysolve_cols<P, PD>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((a.nlines + G - 1) / G, a.narr);
+        kern<<<grid, nt, smem, s>>>(f);
+    }
+    return cudaGetLastError();
+}
+
+// ---- tiled explicit Kronecker matvec -------------------------------------------------
+// R = Fscale F + c1 (A1^x (x) B1^y) T + c2 (A2^x (x) B2^y) T on TX x TY tiles: the halo of T
+// is staged in shared memory, convolved along x with both x bands, then along y.
+template <typename P, int PD, int TX, int TY, int RY>
+__global__ void __launch_bounds__(TX*(TY / RY)) k_matvec_tile(int Nx, int Ny, int pitch, const P* __restrict__ T,
+                                                          const P* __restrict__ F, P* R, const P* __restrict__ A1,
+                                                          const P* __restrict__ B1, const P* __restrict__ A2,
+                                                          const P* __restrict__ B2, P Fscale, P c1, P c2) {
+    constexpr int W = 2 * PD + 1, HY = TY + 2 * PD, HX = TX + 2 * PD, NTY = TY / RY;
+    __shared__ P h[HY][HX + 1];
+    __shared__ P x1[HY][TX + 1];
+    __shared__ P x2[HY][TX + 1];
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < HY; r += NTY)
+        for (int x = tx; x < HX; x += TX) {
+            const int gj = j0 - PD + r, gi = i0 - PD + x;
+            h[r][x] = (gj >= 0 && gj < Ny && gi >= 0 && gi < Nx) ? T[(size_t)gj * pitch + gi] : P(0);
+        }
+    __syncthreads();
+    const int i = i0 + tx;
+    const bool col_ok = i < Nx;
+    P a1[W], a2[W];
+#pragma unroll
+    for (int d = 0; d < W; ++d) {
+        a1[d] = col_ok ? A1[(size_t)i * W + d] : P(0);
+        a2[d] = (col_ok && A2) ? A2[(size_t)i * W + d] : P(0);
+    }
+    for (int r = ty; r < HY; r += NTY) {
+        P s1 = 0, s2 = 0;
+#pragma unroll
+        for (int d = 0; d < W; ++d) {
+            s1 += a1[d] * h[r][tx + d];
+            s2 += a2[d] * h[r][tx + d];
+        }
+        x1[r][tx] = s1;
+        x2[r][tx] = s2;
+    }
+    __syncthreads();
+    if (!col_ok) return;
+#pragma unroll
+    for (int q = 0; q < RY; ++q) {
+        const int jl = ty * RY + q, j = j0 + jl;
+        if (j >= Ny) break;
+        P r1 = 0, r2 = 0;
+#pragma unroll
+        for (int d = 0; d < W; ++d) {
+            r1 += B1[(size_t)j * W + d] * x1[jl + d][tx];
+            if (A2) r2 += B2[(size_t)j * W + d] * x2[jl + d][tx];
+        }
+        const size_t g = (size_t)j * pitch + i;
+        R[g] = Fscale * F[g] + c1 * r1 + c2 * r2;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_line_fast(int prec, int p, bool xdir, const LineArgs& a, cudaStream_t s) {
+    for (int q = 0; q < a.narr; ++q)
+        if (!a.f[q].compact || a.f[q].ch.base != a.f[0].ch.base || a.f[q].ch.C != a.f[0].ch.C)
+            return cudaErrorNotSupported;
+#define WF_FAST(P, PD) return xdir ? run_fast<P, PD, true>(a, s) : run_fast<P, PD, false>(a, s)
+    if (prec == 0) {
+        switch (p) {
+            case 1: WF_FAST(float, 1);
+            case 2: WF_FAST(float, 2);
+            case 3: WF_FAST(float, 3);
+        }
+    } else {
+        switch (p) {
+            case 1: WF_FAST(double, 1);
+            case 2: WF_FAST(double, 2);
+            case 3: WF_FAST(double, 3);
+        }
+    }
+#undef WF_FAST
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s) {
+    constexpr int TX = 32, TY = 16, RY = 2;
+    dim3 grid((a.Nx + TX - 1) / TX, (a.Ny + TY - 1) / TY), block(TX, TY / RY);
+#define WF_MV(P, PD)                                                                                             \
+    k_matvec_tile<P, PD, TX, TY, RY><<<grid, block, 0, s>>>(a.Nx, a.Ny, a.pitch, (const P*)a.T, (const P*)a.F,   \
+                                                            (P*)a.R, (const P*)a.A1, (const P*)a.B1,             \
+                                                            (const P*)a.A2, (const P*)a.B2, (P)a.Fscale, (P)a.c1, \
+                                                            (P)a.c2)
+    if (prec == 0) {
+        switch (p) {
+            case 1: WF_MV(float, 1); break;
+            case 2: WF_MV(float, 2); break;
+            case 3: WF_MV(float, 3); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (p) {
+            case 1: WF_MV(double, 1); break;
+            case 2: WF_MV(double, 2); break;
+            case 3: WF_MV(double, 3); break;
+            default: return cudaErrorInvalidValue;
+        }
+    }
+#undef WF_MV
+    return cudaGetLastError();
+}
+
+}  // namespace wf

@@ -1,4 +1,4 @@
-// Independent 1-D banded solves along x and along y, and the explicit Kronecker matvec.
+// Independent 1-D banded solves along x and along y (shared-memory form).
 //
 // Paper: Sec. 4 ("Cost of directional implicit solves"): a system
 // (A^x (x) B^y) X = R is solved as N_y independent solves of size N_x with
@@ -151,11 +151,6 @@ __device__ __forceinline__ P spike_correct(const P* __restrict__ sk, P g, const 
     return g;
 }
 
-__device__ __forceinline__ int chunk_of(const Chunks& ch, int x) {
-    const int big = ch.rem * (ch.base + 1);
-    return x < big ? x / (ch.base + 1) : ch.rem + (x - big) / ch.base;
-}
-
 // x pass.  blockIdx.x: group of ROWS rows; blockIdx.y: array.  blockDim.x = ROWS * C.
 template <typename P, int PD, int ROWS>
 __global__ void k_xsolve(const LineArgsT<P> a) {
@@ -265,39 +260,6 @@ __global__ void k_ysolve(const LineArgsT<P> a) {
     if (guard && bad) atomicOr(a.status, 1);
 }
 
-// R = Fscale F + c1 (A1^x (x) B1^y) T + c2 (A2^x (x) B2^y) T, one thread per coefficient.
-template <typename P, int PD>
-__device__ __forceinline__ P kron_apply(int i, int j, int Nx, int Ny, int pitch, const P* __restrict__ T,
-                                        const P* __restrict__ A, const P* __restrict__ B) {
-    constexpr int W = 2 * PD + 1;
-    P r = 0;
-#pragma unroll
-    for (int dl = 0; dl < W; ++dl) {
-        const int jj = j + dl - PD;
-        if (jj < 0 || jj >= Ny) continue;
-        P t = 0;
-#pragma unroll
-        for (int dk = 0; dk < W; ++dk) {
-            const int ii = i + dk - PD;
-            if (ii >= 0 && ii < Nx) t += A[(size_t)i * W + dk] * T[(size_t)jj * pitch + ii];
-        }
-        r += B[(size_t)j * W + dl] * t;
-    }
-    return r;
-}
-
-template <typename P, int PD>
-__global__ void k_matvec(int Nx, int Ny, int pitch, const P* __restrict__ T, const P* __restrict__ F, P* R,
-                         const P* __restrict__ A1, const P* __restrict__ B1, const P* __restrict__ A2,
-                         const P* __restrict__ B2, P Fscale, P c1, P c2) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (i >= Nx) return;
-    P r = c1 * kron_apply<P, PD>(i, j, Nx, Ny, pitch, T, A1, B1);
-    if (A2) r += c2 * kron_apply<P, PD>(i, j, Nx, Ny, pitch, T, A2, B2);
-    R[(size_t)j * pitch + i] = r + Fscale * F[(size_t)j * pitch + i];
-}
-
 template <typename P>
 LineArgsT<P> to_typed(const LineArgs& a, int mpad) {
     LineArgsT<P> t;
@@ -317,7 +279,7 @@ LineArgsT<P> to_typed(const LineArgs& a, int mpad) {
     return t;
 }
 
-inline int mpad_of(const Chunks& ch) { return (ch.base + 1) | 1; }
+inline int mpad_of(const Chunks& ch) { return (ch.base > ch.last ? ch.base : ch.last) | 1; }
 
 template <typename P>
 constexpr int lanes_per_line() { return sizeof(P) == 4 ? 8 : 4; }
@@ -365,8 +327,18 @@ cudaError_t dispatch_line(int prec, int p, const LineArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch_xsolve(int prec, int p, const LineArgs& a, cudaStream_t s) { return dispatch_line<true>(prec, p, a, s); }
+// The compact-factor kernels (wf_linefast.cu) take every operator whose interior chunks are
+// identical and whose lines fit one CTA of 256 threads; everything else runs the kernels above.
+cudaError_t launch_xsolve(int prec, int p, const LineArgs& a, cudaStream_t s) {
+    cudaError_t e = launch_line_fast(prec, p, true, a, s);
+    if (e != cudaErrorNotSupported) return e;
+    cudaGetLastError();
+    return dispatch_line<true>(prec, p, a, s);
+}
 cudaError_t launch_ysolve(int prec, int p, const LineArgs& a, cudaStream_t s) {
+    cudaError_t e = launch_line_fast(prec, p, false, a, s);
+    if (e != cudaErrorNotSupported) return e;
+    cudaGetLastError();
     return dispatch_line<false>(prec, p, a, s);
 }
 
@@ -374,32 +346,7 @@ int line_rows_per_cta(int prec) { return prec == 0 ? 8 : 4; }
 
 size_t line_smem_bytes(int prec, const Chunks& ch) {
     const int G = line_rows_per_cta(prec);
-    return (size_t)G * ch.C * ((ch.base + 1) | 1) * (prec == 0 ? 4 : 8);
-}
-
-cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s) {
-    dim3 grid((a.Nx + 127) / 128, a.Ny);
-#define WF_MV(P, PD)                                                                                        \
-    k_matvec<P, PD><<<grid, 128, 0, s>>>(a.Nx, a.Ny, a.pitch, (const P*)a.T, (const P*)a.F, (P*)a.R,       \
-                                         (const P*)a.A1, (const P*)a.B1, (const P*)a.A2, (const P*)a.B2,     \
-                                         (P)a.Fscale, (P)a.c1, (P)a.c2)
-    if (prec == 0) {
-        switch (p) {
-            case 1: WF_MV(float, 1); break;
-            case 2: WF_MV(float, 2); break;
-            case 3: WF_MV(float, 3); break;
-            default: return cudaErrorInvalidValue;
-        }
-    } else {
-        switch (p) {
-            case 1: WF_MV(double, 1); break;
-            case 2: WF_MV(double, 2); break;
-            case 3: WF_MV(double, 3); break;
-            default: return cudaErrorInvalidValue;
-        }
-    }
-#undef WF_MV
-    return cudaGetLastError();
+    return (size_t)G * ch.C * ((ch.base > ch.last ? ch.base : ch.last) | 1) * (prec == 0 ? 4 : 8);
 }
 
 }  // namespace wf

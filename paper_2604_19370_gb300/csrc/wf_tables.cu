@@ -47,28 +47,33 @@ __global__ void k_gauss(double* xi, double* w, int q) {
     w[i] = 1.0 / ((1.0 - x * x) * dp * dp);  // (2 / ((1-x^2) P_q'^2)) / 2
 }
 
-__device__ inline double knot(int j, int n, int p, double L) {
+// Knot t_j of the open uniform knot vector relative to the start of element e, as
+// (integer) * h: the same bits for every interior element, so the tables, the
+// assembled bands and the chunk factors of interior rows are exactly translation
+// invariant.
+__device__ inline double knot_rel(int j, int e, int n, int p, double h) {
     int m = j - p;
     m = m < 0 ? 0 : (m > n ? n : m);
-    return m == n ? L : m * (L / n);
+    return (double)(m - e) * h;
 }
 
 // Basis values and derivatives at the Gauss points of every element, by the
 // triangular (left/right difference) evaluation of the nonzero B-splines of
-// a knot span.  One thread per (element, point).
+// a knot span, in coordinates relative to the element start.  One thread per
+// (element, point).
 __global__ void k_basis(const double* __restrict__ xi, int q, int n, int p, double L, double* B, double* D) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * q) return;
     const int e = idx / q, a = idx % q;
     const double h = L / n;
     const int span = e + p;
-    const double x = knot(span, n, p, L) + xi[a] * h;
+    const double x = xi[a] * h;  // offset of the point inside element e
     double left[kMaxP + 1], right[kMaxP + 1], Nv[kMaxP + 1], Nm[kMaxP + 1];
     Nv[0] = 1.0;
     Nm[0] = 1.0;
     for (int j = 1; j <= p; ++j) {
-        left[j] = x - knot(span + 1 - j, n, p, L);
-        right[j] = knot(span + j, n, p, L) - x;
+        left[j] = x - knot_rel(span + 1 - j, e, n, p, h);
+        right[j] = knot_rel(span + j, e, n, p, h) - x;
         double saved = 0.0;
         for (int r = 0; r < j; ++r) {
             double tmp = Nv[r] / (right[r + 1] + left[j - r]);
@@ -84,11 +89,11 @@ __global__ void k_basis(const double* __restrict__ xi, int q, int n, int p, doub
         double d = 0.0;
         if (p > 0) {
             if (l >= 1) {
-                double den = knot(i + p, n, p, L) - knot(i, n, p, L);
+                double den = knot_rel(i + p, e, n, p, h) - knot_rel(i, e, n, p, h);
                 if (den > 0.0) d += p * Nm[l - 1] / den;
             }
             if (l <= p - 1) {
-                double den = knot(i + p + 1, n, p, L) - knot(i + 1, n, p, L);
+                double den = knot_rel(i + p + 1, e, n, p, h) - knot_rel(i + 1, e, n, p, h);
                 if (den > 0.0) d -= p * Nm[l] / den;
             }
         }
@@ -264,13 +269,52 @@ __global__ void k_interface(int p, Chunks ch, const double* __restrict__ spk, do
     }
     for (int a = 0; a < p; ++a)
         for (int c = 0; c < p; ++c) E[(size_t)k * p * p + a * p + c] = A[a][p + c];
+    // The reduced system of interface k neglects the bottom of chunk k's left spike
+    // (zero for k = 0) and the top of chunk k+1's right spike (zero for k+1 = C-1).
     double tr = 0.0;
     for (int a = 0; a < p; ++a)
         for (int c = 0; c < p; ++c) {
-            tr = fmax(tr, fabs(spk[(size_t)(s0 + a) * S + c]));                 // top of V_k
-            tr = fmax(tr, fabs(spk[(size_t)(s1 + m1 - p + a) * S + p + c]));    // bottom of W_{k+1}
+            if (k > 0) tr = fmax(tr, fabs(spk[(size_t)(s0 + m0 - p + a) * S + p + c]));
+            if (k + 1 < ch.C - 1) tr = fmax(tr, fabs(spk[(size_t)(s1 + a) * S + c]));
         }
+    (void)m1;
     atomic_max_nonneg(diag + 1, tr);
+}
+
+// Compact factors: chunk types 0 (first), 1 (interior, represented by chunk 1), 2 (last);
+// interface types 0 (k = 0), 1 (interior, interface 1), 2 (k = C-2).  One thread per
+// (row offset o < mmax); thread 0 also copies E and every thread checks interior
+// chunks against chunk 1.
+__global__ void k_compact(const double* __restrict__ lu, const double* __restrict__ spk, const double* __restrict__ E,
+                          int p, Chunks ch, int mmax, double* luc, double* spkc, double* Ec, double* diag) {
+    const int W = 2 * p + 1, S = 2 * p;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o < mmax) {
+        const int src_chunk[3] = {0, ch.C >= 3 ? 1 : 0, ch.C - 1};
+        for (int t = 0; t < 3; ++t) {
+            const int k = src_chunk[t];
+            const bool ok = o < chunk_len(ch, k);
+            const size_t r = (size_t)chunk_start(ch, k) + o;
+            for (int d = 0; d < W; ++d) luc[((size_t)t * mmax + o) * W + d] = ok ? lu[r * W + d] : 0.0;
+            for (int c = 0; c < S; ++c) spkc[((size_t)t * mmax + o) * S + c] = ok ? spk[r * S + c] : 0.0;
+        }
+        bool same = true;
+        for (int k = 2; k + 1 < ch.C && o < ch.base; ++k) {
+            const size_t r1 = (size_t)chunk_start(ch, 1) + o, rk = (size_t)chunk_start(ch, k) + o;
+            for (int d = 0; d < W; ++d) same &= lu[rk * W + d] == lu[r1 * W + d];
+            for (int c = 0; c < S; ++c) same &= spk[rk * S + c] == spk[r1 * S + c];
+        }
+        if (!same) diag[2] = 1.0;
+    }
+    if (o == 0 && ch.C > 1) {
+        const int src_if[3] = {0, ch.C >= 4 ? 1 : 0, ch.C - 2};
+        for (int t = 0; t < 3; ++t)
+            for (int c = 0; c < p * p; ++c) Ec[t * p * p + c] = E[(size_t)src_if[t] * p * p + c];
+        bool same = true;
+        for (int k = 2; k < ch.C - 2; ++k)
+            for (int c = 0; c < p * p; ++c) same &= E[(size_t)k * p * p + c] == E[(size_t)p * p + c];
+        if (!same) diag[2] = 1.0;
+    }
 }
 
 __global__ void k_to_f32(const double* __restrict__ src, float* dst, size_t n) {
@@ -344,6 +388,12 @@ cudaError_t launch_factor(const double* Mb, const double* Kb, const double* Gb, 
         err = cudaGetLastError();
     }
     return err;
+}
+
+cudaError_t launch_compact(const double* lu, const double* spk, const double* E, int p, Chunks ch, int mmax,
+                           double* luc, double* spkc, double* Ec, double* diag, cudaStream_t s) {
+    k_compact<<<blocks(mmax, 64), 64, 0, s>>>(lu, spk, E, p, ch, mmax, luc, spkc, Ec, diag);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s) {
