@@ -103,6 +103,10 @@ struct RhsArgs {
     Phys phys;
 };
 cudaError_t launch_rhs(int prec, int p, const RhsArgs& a, cudaStream_t s);
+// streaming form of the same computation (wf_rhs_stream.cu); cudaErrorNotSupported for
+// a wind variation of rank > 2
+cudaError_t launch_rhs_stream(int prec, int p, const RhsArgs& a, cudaStream_t s);
+cudaError_t launch_rhs_tile(int prec, int p, const RhsArgs& a, cudaStream_t s);  // shared-memory tiles
 int rhs_items_per_dof(int p);  // informational
 
 // ---- line solves and matvec (wf_solve.cu) -------------------------------------------

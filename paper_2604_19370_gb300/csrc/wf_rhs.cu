@@ -339,6 +339,13 @@ cudaError_t run_rhs(const RhsArgs& a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_rhs(int prec, int p, const RhsArgs& a, cudaStream_t s) {
+    cudaError_t e = launch_rhs_stream(prec, p, a, s);
+    if (e != cudaErrorNotSupported) return e;
+    cudaGetLastError();
+    return launch_rhs_tile(prec, p, a, s);
+}
+
+cudaError_t launch_rhs_tile(int prec, int p, const RhsArgs& a, cudaStream_t s) {
     if (prec == 0) {
         switch (p) {
             case 1: return run_rhs<float, 1, 16, 16, 256>(a, s);

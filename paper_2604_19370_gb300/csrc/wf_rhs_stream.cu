@@ -1,0 +1,427 @@
+// Explicit right-hand side by sum-factorised Gauss quadrature, streaming form.
+//
+// Computes exactly what k_rhs (wf_rhs.cu) computes (Eq. termsPR's F tested against
+// every basis function, the fuel increment of the Sec. 7 listing and the
+// increment-form right-hand side R = Rscale F + c1 (A1 (x) B1) T + c2 (A2 (x) B2) T),
+// with a different schedule:
+//
+//   * one warp owns a strip of 32 element columns (lane L <-> element column
+//     X0 - p + L) and walks down a segment of element rows;
+//   * everything the sum factorisation needs lives in registers as sliding
+//     windows over rows: the x-interpolated values (T, dT/dx, phi) of the p+1
+//     coefficient rows an element row uses, the y-test accumulators of the p+1
+//     DOF rows it contributes to, and the x-convolved coefficient rows of the
+//     explicit Kronecker products;
+//   * neighbouring element columns are reached with warp shuffles, so nothing
+//     goes through shared memory;
+//   * a DOF row is finished (x-test contraction, matvec, stores) as soon as the
+//     last element row touching it has been processed.
+//
+// Lanes 0..p-1 only feed their neighbours, so a strip produces 32 - p DOF
+// columns; a segment recomputes p element rows above it.  Both overheads are
+// below 7 % for p = 2.
+#include <math.h>
+
+#include "wf_internal.h"
+
+namespace wf {
+
+namespace {
+
+template <typename P>
+struct PhysS {
+    P K_ign, chiTamb, c_rad, T_amb, T_amb2, C_nld, c_W, T_ig, phi_min, T_a, tau_kf;
+    int heat_by_fuel;
+};
+
+template <typename P>
+__device__ __forceinline__ P expo_s(P x);
+template <>
+__device__ __forceinline__ float expo_s<float>(float x) { return __expf(x); }
+template <>
+__device__ __forceinline__ double expo_s<double>(double x) { return exp(x); }
+
+template <typename P>
+struct StreamArgs {
+    int nx, ny, Nx, Ny, pitch, seg, nstrips;
+    const P* __restrict__ T;
+    const P* __restrict__ phi;
+    P* F;
+    P* Phi;
+    P* R;
+    const P *Bx, *Dx, *By, *Dy, *wx, *wy;
+    int wind_rank;
+    const P *fxq, *gxq, *fyq, *gyq;
+    const P *A1, *B1, *A2, *B2;
+    P Rscale, c1, c2;
+    PhysS<P> c;
+};
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename P>
+__device__ __forceinline__ P col_from(P own, P extra, int lane, int k) {
+    // value of the lane `k` to the right; lanes past 31 read the extra column of lane (lane+k-32)
+    const P down = __shfl_down_sync(FULL, own, k);
+    const P wrap = __shfl_sync(FULL, extra, (lane + k) & 31);
+    return (lane + k < 32) ? down : wrap;
+}
+
+template <typename P, int PD, int WR>
+__global__ void __launch_bounds__(128) k_rhs_stream(const StreamArgs<P> a) {
+    constexpr int Q = PD + 1, NB = PD + 1, W = 2 * PD + 1, NC = 2 * PD + 1;
+    const int lane = threadIdx.x & 31;
+    const int strip = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (strip >= a.nstrips) return;  // whole warp leaves; no block barrier in this kernel
+    const int X0 = strip * (32 - PD);
+    const int ex = X0 - PD + lane;             // element column of this lane; also its DOF column
+    const bool ex_ok = ex >= 0 && ex < a.nx;
+    const bool out_col = lane >= PD && ex < a.Nx;
+    const int cc = ex;                         // coefficient column held by this lane
+    const int cc2 = X0 - PD + 32 + lane;       // extra coefficient column (lanes < 2p are used)
+    const bool cc_ok = cc >= 0 && cc < a.Nx;
+    const bool cc2_ok = cc2 >= 0 && cc2 < a.Nx;
+    const int Y0 = blockIdx.y * a.seg;
+    const int Y1 = min(Y0 + a.seg, a.Ny);
+
+    // per-lane constants: x tables of the element, x bands of the DOF column, wind x-factors
+    P bx[Q][NB], dx[Q][NB];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            bx[q][k] = ex_ok ? a.Bx[(size_t)(ex * Q + q) * NB + k] : P(0);
+            dx[q][k] = ex_ok ? a.Dx[(size_t)(ex * Q + q) * NB + k] : P(0);
+        }
+    P a1[W], a2[W];
+#pragma unroll
+    for (int d = 0; d < W; ++d) {
+        a1[d] = cc_ok ? a.A1[(size_t)cc * W + d] : P(0);
+        a2[d] = (cc_ok && a.A2) ? a.A2[(size_t)cc * W + d] : P(0);
+    }
+    P fxr[WR > 0 ? WR : 1][Q], fyr[WR > 0 ? WR : 1][Q];
+#pragma unroll
+    for (int r = 0; r < WR; ++r)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            fxr[r][q] = ex_ok ? a.fxq[(size_t)r * a.nx * Q + ex * Q + q] : P(0);
+            fyr[r][q] = ex_ok ? a.fyq[(size_t)r * a.nx * Q + ex * Q + q] : P(0);
+        }
+    P wxq[Q], wyq[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        wxq[q] = a.wx[q];
+        wyq[q] = a.wy[q];
+    }
+    // x-test tables of the elements left of this lane: element ex - k, local basis k
+    P tbx[NB][Q], tdx[NB][Q];
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            tbx[k][q] = (k == 0) ? bx[q][0] : __shfl_up_sync(FULL, bx[q][k], k);
+            tdx[k][q] = (k == 0) ? dx[q][0] : __shfl_up_sync(FULL, dx[q][k], k);
+        }
+    // y tables: every interior element row (p <= ey < ny - p) has the same ones
+    const int eyi = a.ny > 2 * PD ? PD : 0;
+    P byi[Q][NB], dyi[Q][NB];
+#pragma unroll
+    for (int b = 0; b < Q; ++b)
+#pragma unroll
+        for (int l = 0; l < NB; ++l) {
+            byi[b][l] = a.By[(size_t)(eyi * Q + b) * NB + l];
+            dyi[b][l] = a.Dy[(size_t)(eyi * Q + b) * NB + l];
+        }
+
+    // sliding windows
+    P xv[NB][Q], xd[NB][Q], xp[NB][Q];  // x-interpolation of coefficient rows ey .. ey+p
+    P acs[NB][Q], acq[NB][Q], acg[NB][Q];  // y-test accumulators of DOF rows ey .. ey+p
+    P cw1[NC], cw2[NC];                 // x-convolved T rows ey-p .. ey+p (matvec)
+#pragma unroll
+    for (int l = 0; l < NB; ++l)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) xv[l][q] = xd[l][q] = xp[l][q] = acs[l][q] = acq[l][q] = acg[l][q] = P(0);
+#pragma unroll
+    for (int d = 0; d < NC; ++d) cw1[d] = cw2[d] = P(0);
+
+    // coefficient row r: the four values this lane contributes (own and extra column of T and phi)
+    struct Row {
+        P t0, t1, f0, f1;
+    };
+    auto fetch_row = [&](int r) {
+        Row w;
+        const bool rok = r >= 0 && r < a.Ny;
+        const size_t o = (size_t)(rok ? r : 0) * a.pitch;
+        w.t0 = (rok && cc_ok) ? a.T[o + cc] : P(0);
+        w.t1 = (rok && cc2_ok && lane < 2 * PD) ? a.T[o + cc2] : P(0);
+        w.f0 = (rok && cc_ok) ? a.phi[o + cc] : P(0);
+        w.f1 = (rok && cc2_ok && lane < 2 * PD) ? a.phi[o + cc2] : P(0);
+        return w;
+    };
+    // x-interpolation of a fetched row and its x-convolutions for the matvec
+    auto process_row = [&](const Row& w, P(&v)[Q], P(&dv)[Q], P(&pv)[Q], P& w1, P& w2) {
+        P ct[NB], cf[NB];
+        ct[0] = w.t0;
+        cf[0] = w.f0;
+#pragma unroll
+        for (int k = 1; k < NB; ++k) {
+            ct[k] = col_from(w.t0, w.t1, lane, k);
+            cf[k] = col_from(w.f0, w.f1, lane, k);
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            P s = 0, sd = 0, sp = 0;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                s += bx[q][k] * ct[k];
+                sd += dx[q][k] * ct[k];
+                sp += bx[q][k] * cf[k];
+            }
+            v[q] = s;
+            dv[q] = sd;
+            pv[q] = sp;
+        }
+        P s1 = a1[PD] * w.t0, s2 = a2[PD] * w.t0;
+#pragma unroll
+        for (int k = 1; k <= PD; ++k) {
+            const P up = __shfl_up_sync(FULL, w.t0, k);
+            s1 += a1[PD - k] * up + a1[PD + k] * ct[k];
+            s2 += a2[PD - k] * up + a2[PD + k] * ct[k];
+        }
+        w1 = s1;
+        w2 = s2;
+    };
+
+    // prologue: rows Y0-2p .. Y0-1 (matvec window), of which Y0-p .. Y0-1 also enter the x window
+    const int ey0 = Y0 - PD;
+#pragma unroll
+    for (int d = 0; d < 2 * PD; ++d) {
+        const int r = Y0 - 2 * PD + d;
+        P v[Q], dv[Q], pv[Q];
+        process_row(fetch_row(r), v, dv, pv, cw1[d], cw2[d]);
+        if (d >= PD) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                xv[d - PD][q] = v[q];
+                xd[d - PD][q] = dv[q];
+                xp[d - PD][q] = pv[q];
+            }
+        }
+    }
+
+    Row nxt = fetch_row(ey0 + PD);
+    for (int ey = ey0; ey < Y1; ++ey) {
+        // new coefficient row ey + p (fetched one iteration ahead), and the fetch of the next one
+        const Row cur = nxt;
+        nxt = fetch_row(ey + PD + 1);
+        process_row(cur, xv[PD], xd[PD], xp[PD], cw1[2 * PD], cw2[2 * PD]);
+        // element (ex, ey): Q x Q points, y-test accumulation into DOF rows ey .. ey+p
+        if (ey >= 0 && ey < a.ny) {
+            P by[Q][NB], dy[Q][NB];
+            const bool interior = ey >= PD && ey < a.ny - PD;
+#pragma unroll
+            for (int b = 0; b < Q; ++b)
+#pragma unroll
+                for (int l = 0; l < NB; ++l) {
+                    by[b][l] = interior ? byi[b][l] : a.By[(size_t)(ey * Q + b) * NB + l];
+                    dy[b][l] = interior ? dyi[b][l] : a.Dy[(size_t)(ey * Q + b) * NB + l];
+                }
+            P gyr[WR > 0 ? WR : 1][Q], gxr[WR > 0 ? WR : 1][Q];
+#pragma unroll
+            for (int r = 0; r < WR; ++r)
+#pragma unroll
+                for (int b = 0; b < Q; ++b) {
+                    gxr[r][b] = a.gxq[(size_t)r * a.ny * Q + ey * Q + b];
+                    gyr[r][b] = a.gyq[(size_t)r * a.ny * Q + ey * Q + b];
+                }
+            if (ex_ok) {
+#pragma unroll
+                for (int b = 0; b < Q; ++b) {
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        P T = 0, Ty = 0, Tx = 0, ph = 0;
+#pragma unroll
+                        for (int l = 0; l < NB; ++l) {
+                            T += by[b][l] * xv[l][q];
+                            Ty += dy[b][l] * xv[l][q];
+                            Tx += by[b][l] * xd[l][q];
+                            ph += by[b][l] * xp[l][q];
+                        }
+                        P bpx = 0, bpy = 0;
+#pragma unroll
+                        for (int r = 0; r < WR; ++r) {
+                            bpx += fxr[r][q] * gxr[r][b];
+                            bpy += fyr[r][q] * gyr[r][b];
+                        }
+                        const PhysS<P>& c = a.c;
+                        const bool burn = (T > c.T_ig) && (ph > c.phi_min);
+                        const P E = burn ? T * expo_s<P>(-c.T_a / T) : P(0);
+                        const P T2 = T * T;
+                        const P rad = c.c_rad * (c.T_amb2 + T2) * (c.T_amb + T) * (c.T_amb - T);
+                        const P heat = c.K_ign * E * (c.heat_by_fuel ? ph : P(1));
+                        const P Wq = wxq[q] * wyq[b];
+                        const P S = Wq * (heat + c.chiTamb + rad - c.c_W * (bpx * Tx + bpy * Ty));
+                        const P qn = -Wq * c.C_nld * T2 * T;
+                        const P QX = qn * Tx, QY = qn * Ty;
+                        const P G = -Wq * c.tau_kf * E * ph;
+#pragma unroll
+                        for (int l = 0; l < NB; ++l) {
+                            acs[l][q] += by[b][l] * S + dy[b][l] * QY;
+                            acq[l][q] += by[b][l] * QX;
+                            acg[l][q] += by[b][l] * G;
+                        }
+                    }
+                }
+            }
+        }
+        // DOF row ey is complete: x-test contraction, matvec, stores
+        if (ey >= Y0) {
+            P Fv = 0, Ph = 0;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    // element ex - k holds DOF column ex as its local basis k
+                    const P s = (k == 0) ? acs[0][q] : __shfl_up_sync(FULL, acs[0][q], k);
+                    const P u = (k == 0) ? acq[0][q] : __shfl_up_sync(FULL, acq[0][q], k);
+                    const P g = (k == 0) ? acg[0][q] : __shfl_up_sync(FULL, acg[0][q], k);
+                    Fv += tbx[k][q] * s + tdx[k][q] * u;
+                    Ph += tbx[k][q] * g;
+                }
+            }
+            if (out_col) {
+                const size_t g = (size_t)ey * a.pitch + ex;
+                if (a.F) a.F[g] = Fv;
+                if (a.Phi) a.Phi[g] = Ph;
+                if (a.R) {
+                    P r1 = 0, r2 = 0;
+#pragma unroll
+                    for (int d = 0; d < W; ++d) {
+                        r1 += a.B1[(size_t)ey * W + d] * cw1[d];
+                        if (a.A2) r2 += a.B2[(size_t)ey * W + d] * cw2[d];
+                    }
+                    a.R[g] = a.Rscale * Fv + a.c1 * r1 + a.c2 * r2;
+                }
+            }
+        }
+        // slide the windows by one row
+#pragma unroll
+        for (int l = 0; l < PD; ++l)
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                xv[l][q] = xv[l + 1][q];
+                xd[l][q] = xd[l + 1][q];
+                xp[l][q] = xp[l + 1][q];
+                acs[l][q] = acs[l + 1][q];
+                acq[l][q] = acq[l + 1][q];
+                acg[l][q] = acg[l + 1][q];
+            }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) acs[PD][q] = acq[PD][q] = acg[PD][q] = P(0);
+#pragma unroll
+        for (int d = 0; d < NC - 1; ++d) {
+            cw1[d] = cw1[d + 1];
+            cw2[d] = cw2[d + 1];
+        }
+    }
+}
+
+template <typename P>
+PhysS<P> to_phys_s(const Phys& c, double tau) {
+    PhysS<P> o;
+    o.K_ign = (P)c.K_ign;
+    o.chiTamb = (P)(c.c_chi * c.T_amb);
+    o.c_rad = (P)c.c_rad;
+    o.T_amb = (P)c.T_amb;
+    o.T_amb2 = (P)(c.T_amb * c.T_amb);
+    o.C_nld = (P)c.C_nld;
+    o.c_W = (P)c.c_W;
+    o.T_ig = (P)c.T_ig;
+    o.phi_min = (P)c.phi_min;
+    o.T_a = (P)c.T_a;
+    o.tau_kf = (P)(tau * c.k_f);
+    o.heat_by_fuel = c.heat_by_fuel;
+    return o;
+}
+
+template <typename P, int PD, int WR>
+cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
+    constexpr int WARPS = 4;
+    StreamArgs<P> a;
+    a.nx = r.nx;
+    a.ny = r.ny;
+    a.Nx = r.Nx;
+    a.Ny = r.Ny;
+    a.pitch = r.pitch;
+    a.nstrips = (r.Nx + (32 - PD) - 1) / (32 - PD);
+    // segment height: about one wave of 2 CTAs per SM (the register budget allows two),
+    // at least 16 rows so the p halo rows stay a small overhead
+    int sms = 152;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const long ctas_x = (a.nstrips + WARPS - 1) / WARPS;
+    int seg = 128;
+    while (seg > 16 && 10 * ctas_x * ((r.Ny + seg - 1) / seg) < 18L * sms) seg /= 2;
+    a.seg = seg;
+    a.T = (const P*)r.T;
+    a.phi = (const P*)r.phi;
+    a.F = (P*)r.F;
+    a.Phi = (P*)r.Phi;
+    a.R = (P*)r.R;
+    a.Bx = (const P*)r.Bx;
+    a.Dx = (const P*)r.Dx;
+    a.By = (const P*)r.By;
+    a.Dy = (const P*)r.Dy;
+    a.wx = (const P*)r.wx;
+    a.wy = (const P*)r.wy;
+    a.wind_rank = r.wind_rank;
+    a.fxq = (const P*)r.fxq;
+    a.gxq = (const P*)r.gxq;
+    a.fyq = (const P*)r.fyq;
+    a.gyq = (const P*)r.gyq;
+    a.A1 = (const P*)r.A1;
+    a.B1 = (const P*)r.B1;
+    a.A2 = (const P*)r.A2;
+    a.B2 = (const P*)r.B2;
+    a.Rscale = (P)r.Rscale;
+    a.c1 = (P)r.c1;
+    a.c2 = (P)r.c2;
+    a.c = to_phys_s<P>(r.phys, r.tau);
+    dim3 grid((a.nstrips + WARPS - 1) / WARPS, (r.Ny + seg - 1) / seg);
+    k_rhs_stream<P, PD, WR><<<grid, 32 * WARPS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename P, int PD>
+cudaError_t by_rank(const RhsArgs& r, cudaStream_t s) {
+    if (sizeof(P) == 8 && PD == 3) return cudaErrorNotSupported;  // its register windows spill: tile form
+    switch (r.wind_rank) {
+        case 0: return run_stream<P, PD, 0>(r, s);
+        case 1: return run_stream<P, PD, 1>(r, s);
+        case 2: return run_stream<P, PD, 2>(r, s);
+    }
+    return cudaErrorNotSupported;
+}
+
+}  // namespace
+
+cudaError_t launch_rhs_stream(int prec, int p, const RhsArgs& r, cudaStream_t s) {
+    if (prec == 0) {
+        switch (p) {
+            case 1: return by_rank<float, 1>(r, s);
+            case 2: return by_rank<float, 2>(r, s);
+            case 3: return by_rank<float, 3>(r, s);
+        }
+    } else {
+        switch (p) {
+            case 1: return by_rank<double, 1>(r, s);
+            case 2: return by_rank<double, 2>(r, s);
+            case 3: return by_rank<double, 3>(r, s);
+        }
+    }
+    return cudaErrorNotSupported;
+}
+
+}  // namespace wf
