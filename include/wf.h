@@ -29,7 +29,7 @@
  *  - The library owns all device memory it allocates and one CUDA stream
  *    per handle (or the caller's stream, see wf_set_stream).
  *  - A handle is not thread-safe: one thread at a time per handle.  The
- *    server object (wf_server_*) is thread-safe.
+ *    server calls (wf_submit, wf_poll, wf_server_stats) are thread-safe.
  */
 #ifndef WF_H
 #define WF_H
@@ -158,6 +158,107 @@ int wf_set_profiling(wf_handle* h, int on);
 int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], int max_k);
 
 /*
+ * ---- batches of scenarios ------------------------------------------------
+ * A batch handle holds `capacity` independent scenarios (slots) of one grid
+ * (nx, ny, p, dt and model parameters shared).  Each slot has its own state,
+ * mean wind (which sets its implicit 1-D operators) and wind variation.  A
+ * wf_step on a batch advances every active slot with one launch per kernel
+ * of the step (the slots are the third grid dimension); inactive slots cost
+ * nothing.  Slots can be filled, activated and drained between steps; the
+ * step graph is not re-captured for that.  wf_create is a batch of capacity
+ * 1 whose slot 0 is active; the single-scenario calls (wf_set_state,
+ * wf_set_wind, wf_get_state) address slot 0.  This extends Sec. 4's
+ * independent line solves across scenarios; the paper runs one scenario.
+ */
+
+/* Create a batch of `capacity` (1..65535) inactive slots, all with the mean wind
+ * of `params`.  Errors as wf_create.  The device memory it holds is reported by
+ * wf_device_bytes. */
+int wf_batch_create(int nx, int ny, int p, double dt, const wf_params* params, int capacity, wf_handle** out);
+
+/* Load slot `slot`: state T, fuel ([Ny][Nx] float64 each), mean wind (wind_x,
+ * wind_y) and wind variation of rank 0..4 (factors as in wf_set_wind, NULL for
+ * rank 0).  A new mean wind refactors the slot's operators on the GPU.  Clears
+ * the slot's guard flag; does not change whether the slot is active.  Waits for
+ * earlier work on the handle's stream.  Errors: WF_EINVAL, WF_ETRUNC,
+ * WF_ESINGULAR, WF_ECUDA. */
+int wf_batch_set_slot(wf_handle* h, int slot, const double* T, const double* fuel, double wind_x, double wind_y,
+                      int wind_rank, const double* wind_factors);
+
+/* Copy slot `slot`'s state into host arrays (either may be NULL); waits.
+ * Errors: WF_EINVAL, WF_ECUDA. */
+int wf_batch_get_slot(wf_handle* h, int slot, double* T, double* fuel);
+
+/* Include (on != 0) or exclude a slot from the following wf_step calls.
+ * Errors: WF_EINVAL. */
+int wf_batch_activate(wf_handle* h, int slot, int on);
+
+/* Waits and writes, per slot, 1 if its guard tripped since the last call (a
+ * temperature non-finite or above 1e5 K) else 0, into status[0 .. capacity-1]
+ * (n >= capacity), and clears the flags.  Errors: WF_EINVAL, WF_ECUDA. */
+int wf_batch_status(wf_handle* h, int* status, int n);
+
+/* Number of slots of a handle (>= 1), or WF_EINVAL. */
+int wf_batch_capacity(const wf_handle* h);
+
+/* Device bytes held by the handle.  Errors: WF_EINVAL. */
+int wf_device_bytes(const wf_handle* h, size_t* bytes);
+
+/*
+ * ---- serving ---------------------------------------------------------------
+ * A server runs fire-scenario requests of any grid size, degree, precision and
+ * step count on one GPU.  A worker thread admits requests, first come first
+ * served, into slots of batch handles (one per class of requests that can share
+ * a launch: same nx, ny, p, dt and parameters apart from the mean wind), creating
+ * a class's handle when the device-memory budget allows; it advances every class
+ * by quanta of at most 25 steps, all classes enqueued before any is waited for,
+ * and retires finished requests.  Requests join and leave running batches at
+ * quantum boundaries (continuous batching); a request's result does not depend
+ * on the other requests it ran beside.  The paper has no serving layer.
+ */
+typedef struct wf_request {
+    int nx, ny, p, steps;        /* grid, degree (1..3), time steps (>= 0) */
+    double dt;                   /* time step (> 0) */
+    wf_params params;            /* precision, scheme, extents, mean wind, model constants */
+    const double* T0;            /* [Ny][Nx] initial temperature: copied by wf_submit */
+    const double* fuel0;         /* [Ny][Nx] initial fuel: copied by wf_submit */
+    int wind_rank;               /* 0..4 */
+    const double* wind_factors;  /* as in wf_set_wind (NULL for rank 0): copied by wf_submit */
+    double* T_out;               /* [Ny][Nx]: written before wf_poll reports completion; */
+    double* fuel_out;            /*   the caller keeps both alive until then */
+} wf_request;
+
+typedef struct wf_result {
+    int status;        /* WF_OK or the request's error (WF_EUNSTABLE, WF_ENOMEM, ...) */
+    double latency_s;  /* submit -> result written */
+    double queue_s;    /* submit -> admitted into a slot */
+    double run_s;      /* admitted -> result written */
+} wf_result;
+
+typedef struct wf_server wf_server;
+
+/* Start a server on the current device with a device-memory budget (bytes) and at
+ * most max_slots (1..4096) slots per class.  Errors: WF_EINVAL, WF_ENOMEM, WF_ECUDA. */
+int wf_server_create(size_t hbm_budget_bytes, int max_slots, wf_server** out);
+
+/* Queue a request; copies its inputs and returns a ticket.  Thread-safe.
+ * Errors: WF_EINVAL. */
+int wf_submit(wf_server* s, const wf_request* req, uint64_t* ticket);
+
+/* WF_PENDING while the request is queued or running; otherwise fills *res (may be
+ * NULL), forgets the ticket and returns the request's status (WF_OK once T_out and
+ * fuel_out hold the result).  WF_ENOTFOUND for an unknown or already reported
+ * ticket.  Thread-safe, never blocks on the GPU. */
+int wf_poll(wf_server* s, uint64_t ticket, wf_result* res);
+
+/* Completed DOF-steps ((nx+p)(ny+p) x steps summed over finished requests), number
+ * of finished requests and device bytes held by the server's batch handles. */
+int wf_server_stats(wf_server* s, double* dof_steps, uint64_t* completed, size_t* hbm_used);
+
+/* Stop the worker (running requests are abandoned) and free everything. */
+void wf_server_destroy(wf_server* s);
+
+/*
  * Advance a caller-owned FP32 state by nsteps time steps without allocating any
  * device memory.  The paper has no counterpart: this exists for callers that
  * cannot call cudaMalloc while they step, e.g. a process whose device memory is
@@ -178,6 +279,7 @@ int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], in
  * limit, nsteps < 0), WF_ECUDA.
  */
 int wf_step_noalloc(wf_handle* h, void* T, void* fuel, int pitch, int nsteps);
+/* (wf_step_noalloc takes single-scenario handles only: capacity 1.) */
 
 /* Free every resource of the handle (NULL is accepted). */
 void wf_destroy(wf_handle* h);

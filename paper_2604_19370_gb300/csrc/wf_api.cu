@@ -7,10 +7,17 @@
 // Each 2-D solve (A^x (x) B^y) X = R runs as an x pass (lines of A^x) and a y pass
 // (lines of B^y), Sec. 4.  The launches of one step are captured once into a CUDA
 // graph and replayed by wf_step.
+//
+// A handle holds S scenario slots of one grid (S = 1 for wf_create).  Every slot owns
+// one block of device memory with the same layout (fields, wind-dependent operator
+// bands and factors, wind tables, guard flag); kernels address slot z at
+// z * sbytes past slot 0 and skip slots whose active flag is 0, so slots can join and
+// leave between steps without re-capturing the graph.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -36,11 +43,10 @@ struct Arena {
     }
 };
 
+// One directional operator of slot 0 (every other slot: same offsets in its block).
 struct Op {
-    double aM = 0, aK = 0, aG = 0;
     bool factored = false;
     bool compact = false;
-    Chunks ch{};
     int mmax = 0;
     double *band64 = nullptr, *lu64 = nullptr, *spk64 = nullptr, *E64 = nullptr;
     void *bandP = nullptr, *luP = nullptr, *spkP = nullptr, *EP = nullptr;
@@ -51,10 +57,21 @@ struct Op {
 struct Dir {
     int n = 0, N = 0;
     double L = 0, h = 0;
+    Chunks ch{};
+    // shared by all slots
     double *B64 = nullptr, *D64 = nullptr;
     void *BP = nullptr, *DP = nullptr, *wP = nullptr;
     double *M64 = nullptr, *K64 = nullptr, *G64 = nullptr;
-    Op op[3];  // 0: M, 1: minus operator (explicit side), 2: plus operator (implicit side)
+    // per slot
+    Op op[3];  // 0: M, 1: -theta A (explicit side, band only), 2: M + theta A (implicit side)
+};
+
+// Host-side settings of one slot.
+struct Slot {
+    double wind_x = 0, wind_y = 0;
+    int wind_rank = 0;
+    bool active = false;
+    double coef[2][3][3] = {};  // [dir][op][aM, aK, aG]
 };
 
 enum SiteId { S_RHS1, S_X1, S_Y1, S_Y2PRE, S_RHS2, S_MV2, S_X2, S_Y3, S_NSITES };
@@ -71,16 +88,25 @@ struct wf_handle {
     cudaStream_t own = nullptr, stream = nullptr;
     void* mem = nullptr;
     size_t mem_bytes = 0;
+    // shared region
     double *gxi = nullptr, *gw = nullptr;
-    Dir dx, dy;
-    void *T = nullptr, *phi = nullptr, *F = nullptr, *Phi = nullptr, *R = nullptr;
-    double* stage = nullptr;  // 2 * Nx * Ny doubles for host transfers
+    double* stage = nullptr;   // 2 * Nx * Ny doubles for host transfers
     double* work64 = nullptr;
-    double* diag = nullptr;   // [2] factorisation diagnostics
+    double* diag = nullptr;    // [4] factorisation diagnostics
+    double* wind64 = nullptr;  // staging of wind factors
+    int* active_dev = nullptr;
+    int* status_out = nullptr;  // [S] gathered guard flags
+    Dir dx, dy;
+    // slot blocks: slot-0 pointers, block stride
+    int S = 1;
+    long long sbytes = 0;
+    void *T = nullptr, *phi = nullptr, *F = nullptr, *Phi = nullptr, *R = nullptr;
     int* status = nullptr;
-    int wind_rank = 0;
     void *fxq = nullptr, *gxq = nullptr, *fyq = nullptr, *gyq = nullptr;
-    double* wind64 = nullptr;
+    std::vector<Slot> slots;
+    std::vector<int> active_host;
+    bool active_dirty = true;
+    int wr = 0;  // wind rank the kernels are launched with (max over slots)
     cudaGraphExec_t g1 = nullptr, g8 = nullptr;
     bool profiling = false;
     std::vector<cudaEvent_t> ev_free;
@@ -95,13 +121,28 @@ struct wf_handle {
 
 namespace {
 
-#define WF_TRY(expr)                               \
-    do {                                           \
-        cudaError_t _e = (expr);                   \
-        if (_e != cudaSuccess) return WF_ECUDA;    \
+#define WF_TRY(expr)                            \
+    do {                                        \
+        cudaError_t _e = (expr);                \
+        if (_e != cudaSuccess) return WF_ECUDA; \
     } while (0)
 
 size_t esize(int prec) { return prec == WF_FP32 ? 4 : 8; }
+
+template <typename T>
+T* at(const wf_handle* h, T* p, int slot) {
+    return p ? reinterpret_cast<T*>(reinterpret_cast<char*>(const_cast<void*>(static_cast<const void*>(p))) +
+                                    (long long)slot * h->sbytes)
+             : p;
+}
+
+Batch batch(const wf_handle* h) {
+    Batch b;
+    b.S = h->S;
+    b.sbytes = h->sbytes;
+    b.active = h->active_dev;
+    return b;
+}
 
 // Chunks of length `base`; the last chunk takes the remainder and is merged into its
 // neighbour when it would be shorter than 2p, so every chunk holds at least 2p rows
@@ -120,22 +161,17 @@ Chunks make_chunks(int N, int base, int p) {
     return c;
 }
 
-void layout(wf_handle* h, Arena& A) {
-    const size_t es = esize(h->prec);
-    const size_t field = (size_t)h->Ny * h->pitch;
-    h->T = A.take<char>(field * es);
-    h->phi = A.take<char>(field * es);
-    h->F = A.take<char>(field * es);
-    h->Phi = A.take<char>(field * es);
-    h->R = A.take<char>(field * es);
+void layout_shared(wf_handle* h, Arena& A) {
     h->stage = A.take<double>(2 * (size_t)h->Nx * h->Ny);
     h->gxi = A.take<double>(16);
     h->gw = A.take<double>(16);
     h->diag = A.take<double>(4);
-    h->status = A.take<int>(4);
+    h->active_dev = A.take<int>(h->S);
+    h->status_out = A.take<int>(h->S);
     const int W = 2 * h->p + 1;
-    int maxN = h->Nx > h->Ny ? h->Nx : h->Ny;
+    const int maxN = h->Nx > h->Ny ? h->Nx : h->Ny;
     h->work64 = A.take<double>((size_t)maxN * W);
+    h->wind64 = A.take<double>((size_t)2 * kMaxRank * (h->Nx + h->Ny));
     Dir* ds[2] = {&h->dx, &h->dy};
     for (Dir* d : ds) {
         const size_t tab = (size_t)d->n * h->q * (h->p + 1);
@@ -153,15 +189,29 @@ void layout(wf_handle* h, Arena& A) {
         d->M64 = A.take<double>((size_t)d->N * W);
         d->K64 = A.take<double>((size_t)d->N * W);
         d->G64 = A.take<double>((size_t)d->N * W);
+    }
+}
+
+// Slot block, laid out relative to its own start (A.base = start of slot 0).
+void layout_slot(wf_handle* h, Arena& A) {
+    const size_t es = esize(h->prec);
+    const size_t field = (size_t)h->Ny * h->pitch;
+    h->T = A.take<char>(field * es);
+    h->phi = A.take<char>(field * es);
+    h->F = A.take<char>(field * es);
+    h->Phi = A.take<char>(field * es);
+    h->R = A.take<char>(field * es);
+    h->status = A.take<int>(4);
+    const int W = 2 * h->p + 1;
+    Dir* ds[2] = {&h->dx, &h->dy};
+    for (Dir* d : ds) {
         for (Op& o : d->op) {
-            // every operator gets FP64 band and factor space (the explicit-side operator's
-            // factors are never used; they exist so one kernel builds every band)
-            const size_t nE = (size_t)(o.ch.C > 1 ? o.ch.C - 1 : 1) * h->p * h->p;
+            const size_t nE = (size_t)(d->ch.C > 1 ? d->ch.C - 1 : 1) * h->p * h->p;
+            o.mmax = d->ch.base + 2 * h->p;
             o.band64 = A.take<double>((size_t)d->N * W);
             o.lu64 = A.take<double>((size_t)d->N * W);
             o.spk64 = A.take<double>((size_t)d->N * 2 * h->p);
             o.E64 = A.take<double>(nE);
-            o.mmax = o.ch.base + 2 * h->p;
             o.luc64 = A.take<double>((size_t)3 * o.mmax * W);
             o.spkc64 = A.take<double>((size_t)3 * o.mmax * 2 * h->p);
             o.Ec64 = A.take<double>((size_t)3 * h->p * h->p);
@@ -189,41 +239,24 @@ void layout(wf_handle* h, Arena& A) {
     h->gxq = A.take<char>(qy * es);
     h->fyq = A.take<char>(qx * es);
     h->gyq = A.take<char>(qy * es);
-    h->wind64 = A.take<double>((size_t)2 * kMaxRank * (h->Nx + h->Ny));
 }
 
-void set_op_coeffs(wf_handle* h) {
+// Operator coefficients of a slot for its mean wind:
+//   x: A_x = C_d K + c_W b_x G + c_chi M;  op1 = -theta A_x (band),  op2 = X_+ = M + theta A_x
+//   y: A_y = C_d K + c_W b_y G;            op1 = -theta A_y (band),  op2 = Y_+ = M + theta A_y
+void set_slot_coeffs(const wf_handle* h, Slot& s) {
     const Phys& c = h->phys;
     const double tau = h->dt;
-    double thx, thy;
-    if (h->prm.scheme == WF_PR) {
-        thx = thy = 0.5 * tau;
-    } else {
-        thx = 0.25 * tau;
-        thy = 0.5 * tau;
-    }
-    // x: A_x = C_d K + c_W b_x G + c_chi M;  op[1] = -theta A_x (band),  op[2] = X_+ = M + theta A_x
-    Op* ox = h->dx.op;
-    ox[0].aM = 1.0;
-    ox[1].aM = -thx * c.c_chi;
-    ox[1].aK = -thx * c.C_d;
-    ox[1].aG = -thx * c.c_W * h->prm.wind_x;
-    ox[2].aM = 1.0 + thx * c.c_chi;
-    ox[2].aK = thx * c.C_d;
-    ox[2].aG = thx * c.c_W * h->prm.wind_x;
-    // y: A_y = C_d K + c_W b_y G;  op[1] = -theta A_y (band),  op[2] = Y_+ = M + theta A_y
-    Op* oy = h->dy.op;
-    oy[0].aM = 1.0;
-    oy[1].aM = 0.0;
-    oy[1].aK = -thy * c.C_d;
-    oy[1].aG = -thy * c.c_W * h->prm.wind_y;
-    oy[2].aM = 1.0;
-    oy[2].aK = thy * c.C_d;
-    oy[2].aG = thy * c.c_W * h->prm.wind_y;
-    for (int k = 0; k < 3; ++k) {
-        ox[k].factored = (k != 1);
-        oy[k].factored = (k != 1);
-    }
+    const double thx = h->prm.scheme == WF_PR ? 0.5 * tau : 0.25 * tau;
+    const double thy = 0.5 * tau;
+    double(*x)[3] = s.coef[0];
+    double(*y)[3] = s.coef[1];
+    x[0][0] = 1.0, x[0][1] = 0.0, x[0][2] = 0.0;
+    x[1][0] = -thx * c.c_chi, x[1][1] = -thx * c.C_d, x[1][2] = -thx * c.c_W * s.wind_x;
+    x[2][0] = 1.0 + thx * c.c_chi, x[2][1] = thx * c.C_d, x[2][2] = thx * c.c_W * s.wind_x;
+    y[0][0] = 1.0, y[0][1] = 0.0, y[0][2] = 0.0;
+    y[1][0] = 0.0, y[1][1] = -thy * c.C_d, y[1][2] = -thy * c.c_W * s.wind_y;
+    y[2][0] = 1.0, y[2][1] = thy * c.C_d, y[2][2] = thy * c.c_W * s.wind_y;
 }
 
 Phys make_phys(const wf_params& p) {
@@ -248,12 +281,12 @@ bool params_ok(const wf_params& p) {
     const double v[] = {p.Lx, p.Ly, p.rho, p.cp};
     for (double x : v)
         if (!(x > 0.0) || !isfinite(x)) return false;
-    const double w[] = {p.kappa, p.sigma, p.eps, p.ch, p.hc, p.cW, p.chi, p.T_amb, p.T_ig, p.delta_x, p.delta_z,
+    const double w[] = {p.kappa, p.sigma, p.eps, p.ch, p.hc, p.cW, p.chi, p.T_amb, p.T_ig, p.delta_x,
                         p.A_r, p.M_ratio, p.T_a, p.heat_scale, p.fuel_rate, p.fuel_thresh, p.thresh_guard,
                         p.wind_x, p.wind_y};
     for (double x : w)
-        if (!isfinite(x) && !(x == INFINITY)) return false;
-    if (!(p.delta_z > 0.0)) return false;
+        if (!isfinite(x)) return false;
+    if (!(p.delta_z > 0.0)) return false;  // may be +inf (no vertical radiation)
     if (p.scheme != WF_PR && p.scheme != WF_STRANG_CN) return false;
     if (p.precision != WF_FP32 && p.precision != WF_FP64) return false;
     if (p.F_timing != WF_F_ONCE && p.F_timing != WF_F_PER_SUBSTEP) return false;
@@ -273,7 +306,6 @@ int build_tables(wf_handle* h) {
             WF_TRY(launch_to_f32(d->D64, (float*)d->DP, tab, s));
         }
     }
-    // weights times element length, per direction, in P
     double w[16];
     WF_TRY(cudaMemcpyAsync(w, h->gw, sizeof(double) * h->q, cudaMemcpyDeviceToHost, s));
     WF_TRY(cudaStreamSynchronize(s));
@@ -287,41 +319,54 @@ int build_tables(wf_handle* h) {
             for (int a = 0; a < h->q; ++a) w64[a] = w[a] * d->h;
             WF_TRY(cudaMemcpyAsync(d->wP, w64, sizeof(double) * h->q, cudaMemcpyHostToDevice, s));
         }
+        WF_TRY(cudaStreamSynchronize(s));  // the host weight arrays go out of scope
     }
-    WF_TRY(cudaStreamSynchronize(s));  // the host weight arrays go out of scope
     return WF_OK;
 }
 
-// returns WF_OK, WF_ESINGULAR or WF_ETRUNC (tolerance tol on the neglected spike entries)
-int build_factors(wf_handle* h, double tol, double* worst) {
+// Bands and chunked factors of every operator of one slot.  Returns WF_OK, WF_ESINGULAR or
+// WF_ETRUNC (neglected spike entries above tol); *worst receives the largest of them.
+int build_factors(wf_handle* h, int slot, double tol, double* worst) {
     cudaStream_t s = h->stream;
-    const int W = 2 * h->p + 1;
+    const int W = 2 * h->p + 1, S2 = 2 * h->p;
     *worst = 0.0;
     Dir* ds[2] = {&h->dx, &h->dy};
-    for (Dir* d : ds) {
-        for (Op& o : d->op) {
+    for (int dd = 0; dd < 2; ++dd) {
+        Dir* d = ds[dd];
+        for (int k = 0; k < 3; ++k) {
+            Op& o = d->op[k];
+            const double* cf = h->slots[slot].coef[dd][k];
             double zero[4] = {0.0, 0.0, 0.0, 0.0};
             WF_TRY(cudaMemcpyAsync(h->diag, zero, sizeof(zero), cudaMemcpyHostToDevice, s));
-            WF_TRY(launch_factor(d->M64, d->K64, d->G64, o.aM, o.aK, o.aG, d->N, h->p, o.ch, o.band64, o.lu64,
-                                 o.spk64, o.E64, h->work64, h->diag, s));
-            WF_TRY(launch_compact(o.lu64, o.spk64, o.E64, h->p, o.ch, o.mmax, o.luc64, o.spkc64, o.Ec64, h->diag, s));
+            WF_TRY(launch_factor(d->M64, d->K64, d->G64, cf[0], cf[1], cf[2], d->N, h->p, d->ch,
+                                 at(h, o.band64, slot), at(h, o.lu64, slot), at(h, o.spk64, slot),
+                                 at(h, o.E64, slot), h->work64, h->diag, s));
+            WF_TRY(launch_compact(at(h, o.lu64, slot), at(h, o.spk64, slot), at(h, o.E64, slot), h->p, d->ch,
+                                  o.mmax, at(h, o.luc64, slot), at(h, o.spkc64, slot), at(h, o.Ec64, slot), h->diag,
+                                  s));
             double dg[4];
             WF_TRY(cudaMemcpyAsync(dg, h->diag, sizeof(dg), cudaMemcpyDeviceToHost, s));
             WF_TRY(cudaStreamSynchronize(s));
             if (o.factored) {
                 if (dg[0] != 0.0) return WF_ESINGULAR;
                 if (dg[1] > *worst) *worst = dg[1];
+                // every slot must agree on the form the kernels read; slot 0 decides at create
+                if (slot == 0)
+                    o.compact = dg[2] == 0.0;
+                else if (o.compact && dg[2] != 0.0)
+                    return WF_ETRUNC;
             }
-            o.compact = o.factored && dg[2] == 0.0;
             if (h->prec != WF_FP32) continue;
-            WF_TRY(launch_to_f32(o.band64, (float*)o.bandP, (size_t)d->N * W, s));
+            const size_t nE = (size_t)(d->ch.C > 1 ? d->ch.C - 1 : 1) * h->p * h->p;
+            WF_TRY(launch_to_f32(at(h, o.band64, slot), (float*)at(h, o.bandP, slot), (size_t)d->N * W, s));
             if (o.factored) {
-                WF_TRY(launch_to_f32(o.lu64, (float*)o.luP, (size_t)d->N * W, s));
-                WF_TRY(launch_to_f32(o.spk64, (float*)o.spkP, (size_t)d->N * 2 * h->p, s));
-                WF_TRY(launch_to_f32(o.E64, (float*)o.EP, (size_t)(o.ch.C > 1 ? o.ch.C - 1 : 1) * h->p * h->p, s));
-                WF_TRY(launch_to_f32(o.luc64, (float*)o.lucP, (size_t)3 * o.mmax * W, s));
-                WF_TRY(launch_to_f32(o.spkc64, (float*)o.spkcP, (size_t)3 * o.mmax * 2 * h->p, s));
-                WF_TRY(launch_to_f32(o.Ec64, (float*)o.EcP, (size_t)3 * h->p * h->p, s));
+                WF_TRY(launch_to_f32(at(h, o.lu64, slot), (float*)at(h, o.luP, slot), (size_t)d->N * W, s));
+                WF_TRY(launch_to_f32(at(h, o.spk64, slot), (float*)at(h, o.spkP, slot), (size_t)d->N * S2, s));
+                WF_TRY(launch_to_f32(at(h, o.E64, slot), (float*)at(h, o.EP, slot), nE, s));
+                WF_TRY(launch_to_f32(at(h, o.luc64, slot), (float*)at(h, o.lucP, slot), (size_t)3 * o.mmax * W, s));
+                WF_TRY(launch_to_f32(at(h, o.spkc64, slot), (float*)at(h, o.spkcP, slot), (size_t)3 * o.mmax * S2,
+                                     s));
+                WF_TRY(launch_to_f32(at(h, o.Ec64, slot), (float*)at(h, o.EcP, slot), (size_t)3 * h->p * h->p, s));
             }
         }
     }
@@ -329,9 +374,11 @@ int build_factors(wf_handle* h, double tol, double* worst) {
     return *worst > tol ? WF_ETRUNC : WF_OK;
 }
 
-FactorV fv(const Op& o) {
+double trunc_tol(const wf_handle* h) { return h->prec == WF_FP32 ? 1e-8 : 1e-15; }
+
+FactorV fv(const Op& o, const Chunks& ch) {
     FactorV f;
-    f.ch = o.ch;
+    f.ch = ch;
     f.lu = o.luP;
     f.spk = o.spkP;
     f.E = o.EP;
@@ -385,7 +432,7 @@ RhsArgs rhs_args(wf_handle* h, const void* T, void* F, void* Phi, void* R, doubl
     a.Dy = h->dy.DP;
     a.wx = h->dx.wP;
     a.wy = h->dy.wP;
-    a.wind_rank = h->wind_rank;
+    a.wind_rank = h->wr;
     a.fxq = h->fxq;
     a.gxq = h->gxq;
     a.fyq = h->fyq;
@@ -399,6 +446,7 @@ RhsArgs rhs_args(wf_handle* h, const void* T, void* F, void* Phi, void* R, doubl
     a.c2 = c2;
     a.tau = h->dt;
     a.phys = h->phys;
+    a.b = batch(h);
     return a;
 }
 
@@ -408,21 +456,32 @@ LineArgs line_args(wf_handle* h, bool xdir) {
     a.nlines = xdir ? h->Ny : h->Nx;
     a.pitch = h->pitch;
     a.tmax = kTmax;
+    a.b = batch(h);
     return a;
 }
 
-void add_line(LineArgs& a, const void* in, void* out, const Op& o, const void* base = nullptr,
+void add_line(LineArgs& a, const void* in, void* out, const Op& o, const Chunks& ch, const void* base = nullptr,
               const void* premul = nullptr, double prescale = 1.0) {
     a.in[a.narr] = in;
     a.out[a.narr] = out;
-    a.f[a.narr] = fv(o);
+    a.f[a.narr] = fv(o, ch);
     a.base[a.narr] = base;
     a.premul[a.narr] = premul;
     a.prescale[a.narr] = prescale;
     a.narr++;
 }
 
-// Enqueue one time step on h->stream.
+cudaError_t upload_active(wf_handle* h) {
+    if (!h->active_dirty) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(h->active_dev, h->active_host.data(), sizeof(int) * h->S, cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(h->stream);  // the host copy may change right after
+    if (e == cudaSuccess) h->active_dirty = false;
+    return e;
+}
+
+// Enqueue one time step of every active slot on h->stream.
 //
 // Every substep is solved for its increment: with X_+ = M + theta A_x and
 // Y_+ = M + theta A_y, the PR systems of Eq. matrixPR are identical to
@@ -439,6 +498,8 @@ cudaError_t enqueue_step(wf_handle* h) {
     const int prec = h->prec, p = h->p;
     Op* X = h->dx.op;
     Op* Y = h->dy.op;
+    const Chunks& cx = h->dx.ch;
+    const Chunks& cy = h->dy.ch;
     cudaError_t e;
     if (h->prm.scheme == WF_PR) {
         const double th = 0.5 * h->dt;
@@ -446,12 +507,12 @@ cudaError_t enqueue_step(wf_handle* h) {
         RhsArgs r1 = rhs_args(h, h->T, once ? h->F : nullptr, h->Phi, h->R, th, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
         if ((e = timed(h, S_RHS1, [&] { return launch_rhs(prec, p, r1, s); })) != cudaSuccess) return e;
         LineArgs x1 = line_args(h, true);
-        add_line(x1, h->R, h->R, X[2]);
-        add_line(x1, h->Phi, h->Phi, X[0]);
+        add_line(x1, h->R, h->R, X[2], cx);
+        add_line(x1, h->Phi, h->Phi, X[0], cx);
         if ((e = timed(h, S_X1, [&] { return launch_xsolve(prec, p, x1, s); })) != cudaSuccess) return e;
         LineArgs y1 = line_args(h, false);
-        add_line(y1, h->R, h->T, Y[0], h->T);
-        if (once) add_line(y1, h->Phi, h->phi, Y[0], h->phi);
+        add_line(y1, h->R, h->T, Y[0], cy, h->T);
+        if (once) add_line(y1, h->Phi, h->phi, Y[0], cy, h->phi);
         if ((e = timed(h, S_Y1, [&] { return launch_ysolve(prec, p, y1, s); })) != cudaSuccess) return e;
         if (once) {
             MatvecArgs mv;
@@ -468,17 +529,18 @@ cudaError_t enqueue_step(wf_handle* h) {
             mv.Fscale = th;
             mv.c1 = 1.0;
             mv.c2 = 1.0;
+            mv.b = batch(h);
             if ((e = timed(h, S_MV2, [&] { return launch_matvec(prec, p, mv, s); })) != cudaSuccess) return e;
         } else {
             RhsArgs r2 = rhs_args(h, h->T, nullptr, nullptr, h->R, th, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
             if ((e = timed(h, S_RHS2, [&] { return launch_rhs(prec, p, r2, s); })) != cudaSuccess) return e;
         }
         LineArgs x2 = line_args(h, true);
-        add_line(x2, h->R, h->R, X[0]);
+        add_line(x2, h->R, h->R, X[0], cx);
         if ((e = timed(h, S_X2, [&] { return launch_xsolve(prec, p, x2, s); })) != cudaSuccess) return e;
         LineArgs y2 = line_args(h, false);
-        add_line(y2, h->R, h->T, Y[2], h->T);
-        if (!once) add_line(y2, h->Phi, h->phi, Y[0], h->phi);
+        add_line(y2, h->R, h->T, Y[2], cy, h->T);
+        if (!once) add_line(y2, h->Phi, h->phi, Y[0], cy, h->phi);
         y2.status = h->status;
         if ((e = timed(h, S_Y3, [&] { return launch_ysolve(prec, p, y2, s); })) != cudaSuccess) return e;
         return cudaSuccess;
@@ -488,23 +550,23 @@ cudaError_t enqueue_step(wf_handle* h) {
     RhsArgs r1 = rhs_args(h, h->T, nullptr, h->Phi, h->R, half, X[1], Y[0], 2.0, nullptr, nullptr, 0.0);
     if ((e = timed(h, S_RHS1, [&] { return launch_rhs(prec, p, r1, s); })) != cudaSuccess) return e;
     LineArgs x1 = line_args(h, true);
-    add_line(x1, h->R, h->R, X[2]);
-    add_line(x1, h->Phi, h->Phi, X[0]);
+    add_line(x1, h->R, h->R, X[2], cx);
+    add_line(x1, h->Phi, h->Phi, X[0], cx);
     if ((e = timed(h, S_X1, [&] { return launch_xsolve(prec, p, x1, s); })) != cudaSuccess) return e;
     LineArgs y1 = line_args(h, false);
-    add_line(y1, h->R, h->T, Y[0], h->T);
+    add_line(y1, h->R, h->T, Y[0], cy, h->T);
     if ((e = timed(h, S_Y1, [&] { return launch_ysolve(prec, p, y1, s); })) != cudaSuccess) return e;
     LineArgs yy = line_args(h, false);
-    add_line(yy, h->T, h->T, Y[2], h->T, Y[1].bandP, 2.0);
+    add_line(yy, h->T, h->T, Y[2], cy, h->T, Y[1].bandP, 2.0);
     if ((e = timed(h, S_Y2PRE, [&] { return launch_ysolve(prec, p, yy, s); })) != cudaSuccess) return e;
     RhsArgs r2 = rhs_args(h, h->T, nullptr, nullptr, h->R, half, X[1], Y[0], 2.0, nullptr, nullptr, 0.0);
     if ((e = timed(h, S_RHS2, [&] { return launch_rhs(prec, p, r2, s); })) != cudaSuccess) return e;
     LineArgs x2 = line_args(h, true);
-    add_line(x2, h->R, h->R, X[2]);
+    add_line(x2, h->R, h->R, X[2], cx);
     if ((e = timed(h, S_X2, [&] { return launch_xsolve(prec, p, x2, s); })) != cudaSuccess) return e;
     LineArgs y2 = line_args(h, false);
-    add_line(y2, h->R, h->T, Y[0], h->T);
-    add_line(y2, h->Phi, h->phi, Y[0], h->phi);
+    add_line(y2, h->R, h->T, Y[0], cy, h->T);
+    add_line(y2, h->Phi, h->phi, Y[0], cy, h->phi);
     y2.status = h->status;
     if ((e = timed(h, S_Y3, [&] { return launch_ysolve(prec, p, y2, s); })) != cudaSuccess) return e;
     return cudaSuccess;
@@ -533,6 +595,14 @@ cudaError_t capture(wf_handle* h, int steps, cudaGraphExec_t* out) {
     return e;
 }
 
+// The kernels are launched with the largest wind rank of any slot (lower ranks have zero factors).
+void refresh_wind_rank(wf_handle* h) {
+    int wr = 0;
+    for (const Slot& s : h->slots) wr = std::max(wr, s.wind_rank);
+    if (wr != h->wr) drop_graphs(h);
+    h->wr = wr;
+}
+
 void destroy(wf_handle* h) {
     if (!h) return;
     drop_graphs(h);
@@ -544,6 +614,66 @@ void destroy(wf_handle* h) {
     if (h->mem) cudaFree(h->mem);
     if (h->own) cudaStreamDestroy(h->own);
     delete h;
+}
+
+int set_slot_state(wf_handle* h, int slot, const double* T, const double* fuel) {
+    const size_t n = (size_t)h->Nx * h->Ny;
+    cudaStream_t s = h->stream;
+    double* st2 = h->stage + n;
+    WF_TRY(cudaMemcpyAsync(h->stage, T, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    WF_TRY(cudaMemcpyAsync(st2, fuel, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    WF_TRY(launch_convert_in(h->prec, h->stage, at(h, h->T, slot), h->Nx, h->Ny, h->pitch, s));
+    WF_TRY(launch_convert_in(h->prec, st2, at(h, h->phi, slot), h->Nx, h->Ny, h->pitch, s));
+    WF_TRY(cudaStreamSynchronize(s));
+    return WF_OK;
+}
+
+int get_slot_state(wf_handle* h, int slot, double* T, double* fuel) {
+    const size_t n = (size_t)h->Nx * h->Ny;
+    cudaStream_t s = h->stream;
+    if (T) {
+        WF_TRY(launch_convert_out(h->prec, at(h, h->T, slot), h->stage, h->Nx, h->Ny, h->pitch, s));
+        WF_TRY(cudaMemcpyAsync(T, h->stage, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    if (fuel) {
+        WF_TRY(launch_convert_out(h->prec, at(h, h->phi, slot), h->stage + n, h->Nx, h->Ny, h->pitch, s));
+        WF_TRY(cudaMemcpyAsync(fuel, h->stage + n, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    WF_TRY(cudaStreamSynchronize(s));
+    return WF_OK;
+}
+
+int set_slot_wind_factors(wf_handle* h, int slot, int rank, const double* factors) {
+    cudaStream_t s = h->stream;
+    const size_t es = esize(h->prec);
+    const size_t qx = (size_t)kMaxRank * h->nx * h->q, qy = (size_t)kMaxRank * h->ny * h->q;
+    // unused ranks hold zeros: the kernels may run with a higher rank than this slot's
+    WF_TRY(cudaMemsetAsync(at(h, h->fxq, slot), 0, qx * es, s));
+    WF_TRY(cudaMemsetAsync(at(h, h->gxq, slot), 0, qy * es, s));
+    WF_TRY(cudaMemsetAsync(at(h, h->fyq, slot), 0, qx * es, s));
+    WF_TRY(cudaMemsetAsync(at(h, h->gyq, slot), 0, qy * es, s));
+    if (rank > 0) {
+        const size_t nx = (size_t)rank * h->Nx, ny = (size_t)rank * h->Ny;
+        WF_TRY(cudaMemcpyAsync(h->wind64, factors, 2 * (nx + ny) * sizeof(double), cudaMemcpyHostToDevice, s));
+        const double* fx = h->wind64;
+        const double* gx = fx + nx;
+        const double* fy = gx + ny;
+        const double* gy = fy + nx;
+        WF_TRY(launch_factor_points(h->prec, fx, rank, h->nx, h->p, h->dx.B64, at(h, h->fxq, slot), s));
+        WF_TRY(launch_factor_points(h->prec, gx, rank, h->ny, h->p, h->dy.B64, at(h, h->gxq, slot), s));
+        WF_TRY(launch_factor_points(h->prec, fy, rank, h->nx, h->p, h->dx.B64, at(h, h->fyq, slot), s));
+        WF_TRY(launch_factor_points(h->prec, gy, rank, h->ny, h->p, h->dy.B64, at(h, h->gyq, slot), s));
+    }
+    WF_TRY(cudaStreamSynchronize(s));
+    h->slots[slot].wind_rank = rank;
+    refresh_wind_rank(h);
+    return WF_OK;
+}
+
+bool factors_finite(const double* f, size_t n) {
+    for (size_t k = 0; k < n; ++k)
+        if (!isfinite(f[k])) return false;
+    return true;
 }
 
 }  // namespace
@@ -581,11 +711,11 @@ int wf_params_default(wf_params* p) {
     return WF_OK;
 }
 
-int wf_create(int nx, int ny, int p, double dt, const wf_params* params, wf_handle** out) {
+int wf_batch_create(int nx, int ny, int p, double dt, const wf_params* params, int capacity, wf_handle** out) {
     if (!out) return WF_EINVAL;
     *out = nullptr;
     if (!params || nx < 1 || ny < 1 || p < 1 || p > kMaxP || !(dt > 0.0) || !isfinite(dt)) return WF_EINVAL;
-    if (nx > (1 << 15) || ny > (1 << 15)) return WF_EINVAL;
+    if (nx > (1 << 15) || ny > (1 << 15) || capacity < 1 || capacity > 65535) return WF_EINVAL;
     if (!params_ok(*params)) return WF_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaFree(0) != cudaSuccess) return WF_ECUDA;
@@ -603,6 +733,7 @@ int wf_create(int nx, int ny, int p, double dt, const wf_params* params, wf_hand
     h->dt = dt;
     h->prm = *params;
     h->phys = make_phys(*params);
+    h->S = capacity;
     h->dx.n = nx;
     h->dx.N = h->Nx;
     h->dx.L = params->Lx;
@@ -611,111 +742,170 @@ int wf_create(int nx, int ny, int p, double dt, const wf_params* params, wf_hand
     h->dy.N = h->Ny;
     h->dy.L = params->Ly;
     h->dy.h = params->Ly / ny;
+    for (Dir* d : {&h->dx, &h->dy})
+        for (int k = 0; k < 3; ++k) d->op[k].factored = (k != 1);
+    h->slots.assign(capacity, Slot());
+    for (Slot& sl : h->slots) {
+        sl.wind_x = params->wind_x;
+        sl.wind_y = params->wind_y;
+        set_slot_coeffs(h, sl);
+    }
+    h->active_host.assign(capacity, 0);
     if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
         destroy(h);
         return WF_ECUDA;
     }
     h->stream = h->own;
-    set_op_coeffs(h);
 
     // Chunk length: the truncated reduced system must neglect spike entries below 1e-8
-    // (FP32) or 1e-15 (FP64); the shortest length that does is used.
-    const double tol = h->prec == WF_FP32 ? 1e-8 : 1e-15;
+    // (FP32) or 1e-15 (FP64); the shortest length that does (for the creation wind) is used.
     static const int bases32[] = {32, 48, 64, 96, 128, 256, 512, 1024, 2048, 8192};
     static const int bases64[] = {48, 64, 96, 128, 192, 256, 512, 1024, 2048, 8192};
     const int* bases = h->prec == WF_FP32 ? bases32 : bases64;
+    const double tol = trunc_tol(h);
     int rc = WF_OK;
+    size_t shared = 0;
     for (int attempt = 0; attempt < 10; ++attempt) {
-        Dir* ds[2] = {&h->dx, &h->dy};
-        for (Dir* d : ds) {
+        for (Dir* d : {&h->dx, &h->dy}) {
             // at most 32 chunks per line (one warp lane or one thread row each); odd lengths
             // keep the 32 lanes of the x pass on distinct shared-memory banks
             int base = bases[attempt];
             const int need = (d->N + 31) / 32;
             if (base < need) base = need;
             base |= 1;
-            Chunks ch = make_chunks(d->N, base, p);
-            for (Op& o : d->op) o.ch = ch;
+            d->ch = make_chunks(d->N, base, p);
         }
         if (h->mem) {
             cudaFree(h->mem);
             h->mem = nullptr;
         }
         Arena A;
-        layout(h, A);
-        h->mem_bytes = A.off + 256;
+        layout_shared(h, A);
+        shared = (A.off + 255) & ~(size_t)255;
+        Arena B;
+        layout_slot(h, B);
+        h->sbytes = (long long)((B.off + 255) & ~(size_t)255);
+        h->mem_bytes = shared + (size_t)h->sbytes * capacity + 256;
         if (cudaMalloc(&h->mem, h->mem_bytes) != cudaSuccess) {
             destroy(h);
             return WF_ENOMEM;
         }
-        Arena B;
-        B.base = reinterpret_cast<char*>(h->mem);
-        layout(h, B);
+        Arena A2;
+        A2.base = reinterpret_cast<char*>(h->mem);
+        layout_shared(h, A2);
+        Arena B2;
+        B2.base = reinterpret_cast<char*>(h->mem) + shared;
+        layout_slot(h, B2);
+        // every slot block starts zeroed (fields, guard flags, unused wind ranks)
+        if (cudaMemsetAsync(B2.base, 0, (size_t)h->sbytes * capacity, h->stream) != cudaSuccess) {
+            rc = WF_ECUDA;
+            break;
+        }
         if ((rc = build_tables(h)) != WF_OK) break;
         double worst = 0.0;
-        rc = build_factors(h, tol, &worst);
+        rc = build_factors(h, 0, tol, &worst);
         if (rc != WF_ETRUNC) break;
-        if (h->dx.op[0].ch.C == 1 && h->dy.op[0].ch.C == 1) break;
+        if (h->dx.ch.C == 1 && h->dy.ch.C == 1) break;
     }
+    for (int sl = 1; sl < capacity && rc == WF_OK; ++sl) {
+        double worst = 0.0;
+        rc = build_factors(h, sl, tol, &worst);
+    }
+    if (rc == WF_OK && (upload_active(h) != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess))
+        rc = WF_ECUDA;
     if (rc != WF_OK) {
         destroy(h);
         return rc;
-    }
-    const size_t field = (size_t)h->Ny * h->pitch;
-    const int prec = h->prec;
-    if (launch_fill(prec, h->T, field, 0.0, h->stream) != cudaSuccess ||
-        launch_fill(prec, h->phi, field, 0.0, h->stream) != cudaSuccess ||
-        launch_fill(prec, h->F, field, 0.0, h->stream) != cudaSuccess ||
-        launch_fill(prec, h->Phi, field, 0.0, h->stream) != cudaSuccess ||
-        launch_fill(prec, h->R, field, 0.0, h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->stream) != cudaSuccess ||
-        cudaStreamSynchronize(h->stream) != cudaSuccess) {
-        destroy(h);
-        return WF_ECUDA;
     }
     *out = h;
     return WF_OK;
 }
 
+int wf_create(int nx, int ny, int p, double dt, const wf_params* params, wf_handle** out) {
+    int rc = wf_batch_create(nx, ny, p, dt, params, 1, out);
+    if (rc != WF_OK) return rc;
+    (*out)->active_host[0] = 1;
+    (*out)->slots[0].active = true;
+    (*out)->active_dirty = true;
+    if (upload_active(*out) != cudaSuccess) {
+        destroy(*out);
+        *out = nullptr;
+        return WF_ECUDA;
+    }
+    return WF_OK;
+}
+
 int wf_set_state(wf_handle* h, const double* T, const double* fuel, size_t n) {
     if (!h || !T || !fuel || n != (size_t)h->Nx * h->Ny) return WF_EINVAL;
-    cudaStream_t s = h->stream;
-    double* st2 = h->stage + n;
-    WF_TRY(cudaMemcpyAsync(h->stage, T, n * sizeof(double), cudaMemcpyHostToDevice, s));
-    WF_TRY(cudaMemcpyAsync(st2, fuel, n * sizeof(double), cudaMemcpyHostToDevice, s));
-    WF_TRY(launch_convert_in(h->prec, h->stage, h->T, h->Nx, h->Ny, h->pitch, s));
-    WF_TRY(launch_convert_in(h->prec, st2, h->phi, h->Nx, h->Ny, h->pitch, s));
-    WF_TRY(cudaStreamSynchronize(s));
-    return WF_OK;
+    return set_slot_state(h, 0, T, fuel);
 }
 
 int wf_set_wind(wf_handle* h, int rank, const double* factors) {
     if (!h || rank < 0 || rank > kMaxRank || (rank > 0 && !factors)) return WF_EINVAL;
-    cudaStream_t s = h->stream;
-    if (rank > 0) {
-        const size_t nx = (size_t)rank * h->Nx, ny = (size_t)rank * h->Ny;
-        const size_t total = 2 * (nx + ny);
-        for (size_t k = 0; k < total; ++k)
-            if (!isfinite(factors[k])) return WF_EINVAL;
-        WF_TRY(cudaMemcpyAsync(h->wind64, factors, total * sizeof(double), cudaMemcpyHostToDevice, s));
-        const double* fx = h->wind64;
-        const double* gx = fx + nx;
-        const double* fy = gx + ny;
-        const double* gy = fy + nx;
-        WF_TRY(launch_factor_points(h->prec, fx, rank, h->nx, h->p, h->dx.B64, h->fxq, s));
-        WF_TRY(launch_factor_points(h->prec, gx, rank, h->ny, h->p, h->dy.B64, h->gxq, s));
-        WF_TRY(launch_factor_points(h->prec, fy, rank, h->nx, h->p, h->dx.B64, h->fyq, s));
-        WF_TRY(launch_factor_points(h->prec, gy, rank, h->ny, h->p, h->dy.B64, h->gyq, s));
-        WF_TRY(cudaStreamSynchronize(s));
+    if (rank > 0 && !factors_finite(factors, 2 * (size_t)rank * (h->Nx + h->Ny))) return WF_EINVAL;
+    return set_slot_wind_factors(h, 0, rank, factors);
+}
+
+int wf_batch_set_slot(wf_handle* h, int slot, const double* T, const double* fuel, double wind_x, double wind_y,
+                      int wind_rank, const double* wind_factors) {
+    if (!h || slot < 0 || slot >= h->S || !T || !fuel) return WF_EINVAL;
+    if (!isfinite(wind_x) || !isfinite(wind_y) || wind_rank < 0 || wind_rank > kMaxRank) return WF_EINVAL;
+    if (wind_rank > 0 && (!wind_factors || !factors_finite(wind_factors, 2 * (size_t)wind_rank * (h->Nx + h->Ny))))
+        return WF_EINVAL;
+    Slot& sl = h->slots[slot];
+    if (sl.wind_x != wind_x || sl.wind_y != wind_y) {
+        sl.wind_x = wind_x;
+        sl.wind_y = wind_y;
+        set_slot_coeffs(h, sl);
+        double worst = 0.0;
+        const int rc = build_factors(h, slot, trunc_tol(h), &worst);
+        if (rc != WF_OK) return rc;
     }
-    if (rank != h->wind_rank) drop_graphs(h);  // the rank is a kernel argument of the captured graph
-    h->wind_rank = rank;
+    int rc = set_slot_wind_factors(h, slot, wind_rank, wind_factors);
+    if (rc != WF_OK) return rc;
+    rc = set_slot_state(h, slot, T, fuel);
+    if (rc != WF_OK) return rc;
+    if (cudaMemsetAsync(at(h, h->status, slot), 0, 4 * sizeof(int), h->stream) != cudaSuccess) return WF_ECUDA;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;
+    return WF_OK;
+}
+
+int wf_batch_get_slot(wf_handle* h, int slot, double* T, double* fuel) {
+    if (!h || slot < 0 || slot >= h->S) return WF_EINVAL;
+    return get_slot_state(h, slot, T, fuel);
+}
+
+int wf_batch_activate(wf_handle* h, int slot, int on) {
+    if (!h || slot < 0 || slot >= h->S) return WF_EINVAL;
+    const int v = on ? 1 : 0;
+    if (h->active_host[slot] != v) {
+        h->active_host[slot] = v;
+        h->slots[slot].active = v != 0;
+        h->active_dirty = true;
+    }
+    return WF_OK;
+}
+
+int wf_batch_status(wf_handle* h, int* status, int n) {
+    if (!h || !status || n < h->S) return WF_EINVAL;
+    WF_TRY(launch_gather_status(h->status, h->sbytes, h->S, h->status_out, 1, h->stream));
+    WF_TRY(cudaMemcpyAsync(status, h->status_out, sizeof(int) * h->S, cudaMemcpyDeviceToHost, h->stream));
+    WF_TRY(cudaStreamSynchronize(h->stream));
+    return WF_OK;
+}
+
+int wf_batch_capacity(const wf_handle* h) { return h ? h->S : WF_EINVAL; }
+
+int wf_device_bytes(const wf_handle* h, size_t* bytes) {
+    if (!h || !bytes) return WF_EINVAL;
+    *bytes = h->mem_bytes;
     return WF_OK;
 }
 
 int wf_step(wf_handle* h, int nsteps) {
     if (!h || nsteps < 0) return WF_EINVAL;
     if (nsteps == 0) return WF_OK;
+    if (upload_active(h) != cudaSuccess) return WF_ECUDA;
     if (h->profiling) {
         for (int k = 0; k < nsteps; ++k)
             if (enqueue_step(h) != cudaSuccess) return WF_ECUDA;
@@ -741,30 +931,17 @@ int wf_step(wf_handle* h, int nsteps) {
 
 int wf_sync(wf_handle* h) {
     if (!h) return WF_EINVAL;
-    int st[4] = {0, 0, 0, 0};
-    WF_TRY(cudaMemcpyAsync(st, h->status, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
-    WF_TRY(cudaStreamSynchronize(h->stream));
-    if (st[0]) {
-        WF_TRY(cudaMemsetAsync(h->status, 0, sizeof(st), h->stream));
-        WF_TRY(cudaStreamSynchronize(h->stream));
-        return WF_EUNSTABLE;
-    }
+    std::vector<int> st(h->S, 0);
+    const int rc = wf_batch_status(h, st.data(), h->S);
+    if (rc != WF_OK) return rc;
+    for (int z = 0; z < h->S; ++z)
+        if (st[z] && h->active_host[z]) return WF_EUNSTABLE;
     return WF_OK;
 }
 
 int wf_get_state(wf_handle* h, double* T, double* fuel, size_t n) {
     if (!h || n != (size_t)h->Nx * h->Ny) return WF_EINVAL;
-    cudaStream_t s = h->stream;
-    if (T) {
-        WF_TRY(launch_convert_out(h->prec, h->T, h->stage, h->Nx, h->Ny, h->pitch, s));
-        WF_TRY(cudaMemcpyAsync(T, h->stage, n * sizeof(double), cudaMemcpyDeviceToHost, s));
-    }
-    if (fuel) {
-        WF_TRY(launch_convert_out(h->prec, h->phi, h->stage + n, h->Nx, h->Ny, h->pitch, s));
-        WF_TRY(cudaMemcpyAsync(fuel, h->stage + n, n * sizeof(double), cudaMemcpyDeviceToHost, s));
-    }
-    WF_TRY(cudaStreamSynchronize(s));
-    return WF_OK;
+    return get_slot_state(h, 0, T, fuel);
 }
 
 int wf_get_dims(const wf_handle* h, int* Nx, int* Ny, int* p, int* precision) {
@@ -852,12 +1029,13 @@ cudaError_t noalloc_scratch(float** out) {
 
 extern "C" int wf_step_noalloc(wf_handle* h, void* T, void* fuel, int pitch, int nsteps) {
     if (!h || !T || !fuel || nsteps < 0) return WF_EINVAL;
-    if (h->prec != WF_FP32) return WF_EINVAL;
+    if (h->prec != WF_FP32 || h->S != 1) return WF_EINVAL;
     if (pitch < h->Nx) return WF_EINVAL;
     if ((size_t)pitch * (size_t)h->Ny > kNoallocMaxElems) return WF_EINVAL;
     if (nsteps == 0) return WF_OK;
     float* scratch = nullptr;
     if (noalloc_scratch(&scratch) != cudaSuccess) return WF_ECUDA;
+    if (upload_active(h) != cudaSuccess) return WF_ECUDA;
     // Run the handle's own step sequence with the caller's state and the static scratch in
     // place of the handle's buffers.  Every scratch element a kernel reads was written earlier
     // in the same step, so nothing needs clearing between calls.

@@ -14,10 +14,31 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace wf {
 
 constexpr int kMaxP = 3;
 constexpr int kMaxRank = 4;
+
+// Scenario batching.  Every per-scenario pointer handed to a kernel addresses scenario 0;
+// scenario z's copy lies z * sbytes bytes further (each scenario owns one block of device
+// memory with the same internal layout).  Launches cover all S scenarios with grid.z = S;
+// a scenario whose active flag is 0 is skipped.
+struct Batch {
+    int S;
+    long long sbytes;
+    const int* active;  // [S] or nullptr (all active)
+};
+#ifdef __CUDACC__
+template <typename T>
+__device__ __forceinline__ T* scene_ptr(T* p, const Batch& b) {
+    return p ? reinterpret_cast<T*>(reinterpret_cast<char*>(const_cast<typename std::remove_const<T>::type*>(p)) +
+                                    (long long)blockIdx.z * b.sbytes)
+             : p;
+}
+__device__ __forceinline__ bool scene_active(const Batch& b) { return !b.active || b.active[blockIdx.z] != 0; }
+#endif
 
 // Normalised model coefficients (equation divided by rho*c_p).
 struct Phys {
@@ -85,6 +106,7 @@ cudaError_t launch_factor_points(int prec, const double* coef, int rank, int n, 
 cudaError_t launch_convert_in(int prec, const double* src, void* dst, int Nx, int Ny, int pitch, cudaStream_t s);
 cudaError_t launch_convert_out(int prec, const void* src, double* dst, int Nx, int Ny, int pitch, cudaStream_t s);
 cudaError_t launch_fill(int prec, void* dst, size_t n, double v, cudaStream_t s);
+cudaError_t launch_gather_status(int* status0, long long sbytes, int S, int* out, int clear, cudaStream_t s);
 
 // ---- quadrature right-hand side (wf_rhs.cu) ---------------------------------------
 struct RhsArgs {
@@ -101,6 +123,7 @@ struct RhsArgs {
     double Rscale, c1, c2;
     double tau;  // full time step (fuel update)
     Phys phys;
+    Batch b;  // per scenario: T, phi, F, Phi, R, A1, B1, A2, B2, fxq, gxq, fyq, gyq
 };
 cudaError_t launch_rhs(int prec, int p, const RhsArgs& a, cudaStream_t s);
 // streaming form of the same computation (wf_rhs_stream.cu); cudaErrorNotSupported for
@@ -122,6 +145,7 @@ struct LineArgs {
     const void* base[2];    // y pass only: out = base + solution (or NULL: out = solution)
     int* status;            // y pass only: guard flag for out[0] (or NULL)
     double tmax;
+    Batch b;  // per scenario: in, out, factors, premul, base, status
 };
 cudaError_t launch_xsolve(int prec, int p, const LineArgs& a, cudaStream_t s);
 cudaError_t launch_ysolve(int prec, int p, const LineArgs& a, cudaStream_t s);
@@ -137,6 +161,7 @@ struct MatvecArgs {
     void* R;
     const void *A1, *B1, *A2, *B2;
     double Fscale, c1, c2;
+    Batch b;  // per scenario: every pointer
 };
 cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s);
 

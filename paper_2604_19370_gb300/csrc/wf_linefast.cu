@@ -37,7 +37,25 @@ struct FastArgs {
     int* status;
     P tmax;
     int tma;  // x pass: rows staged with bulk copies (16-byte aligned rows)
+    Batch b;
 };
+
+template <typename P>
+__device__ __forceinline__ FastArgs<P> scene_args(const FastArgs<P>& a_in) {
+    FastArgs<P> a = a_in;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        a.in[q] = scene_ptr(a.in[q], a.b);
+        a.out[q] = scene_ptr(a.out[q], a.b);
+        a.base[q] = scene_ptr(a.base[q], a.b);
+        a.premul[q] = scene_ptr(a.premul[q], a.b);
+        a.luc[q] = scene_ptr(a.luc[q], a.b);
+        a.spkc[q] = scene_ptr(a.spkc[q], a.b);
+        a.Ec[q] = scene_ptr(a.Ec[q], a.b);
+    }
+    a.status = scene_ptr(a.status, a.b);
+    return a;
+}
 
 // ---- TMA bulk copies and mbarrier (PTX) ------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -187,8 +205,10 @@ __device__ __forceinline__ void stage_factors(const FastArgs<P>& a, int arr, int
 // The G rows are contiguous in memory: one bulk copy stages them, one bulk store writes them back.
 // Chunk lengths are odd, so the 32 lanes of a warp read 32 distinct shared-memory banks.
 template <typename P, int PD>
-__global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
+__global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a_in) {
     constexpr int W = 2 * PD + 1, S = 2 * PD;
+    if (!scene_active(a_in.b)) return;
+    const FastArgs<P> a = scene_args(a_in);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const Chunks ch = a.ch;
@@ -284,8 +304,10 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
 // of column c in its private shared-memory region (odd stride: distinct banks).  Loads are
 // issued in batches of 16 before use so each thread keeps 16 requests in flight.
 template <typename P, int PD>
-__global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
+__global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a_in) {
     constexpr int W = 2 * PD + 1, S = 2 * PD, B = 16;
+    if (!scene_active(a_in.b)) return;
+    const FastArgs<P> a = scene_args(a_in);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nt = blockDim.x, tid = threadIdx.x;
     const Chunks ch = a.ch;
@@ -389,6 +411,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
     }
     f.status = a.status;
     f.tmax = (P)a.tmax;
+    f.b = a.b;
     f.mpad = (ch.base > ch.last ? ch.base : ch.last) | 1;
     if (X) {
         // rows per CTA: as many warps as fit 100 KB of staged rows (at least one)
@@ -397,7 +420,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         while (G > 1 && 128 + G * row_bytes + fbytes > 100 * 1024) G /= 2;
         const size_t smem = 128 + G * row_bytes + fbytes;
         if (smem > 227 * 1024) return cudaErrorNotSupported;
-        bool aligned = (row_bytes % 16 == 0);
+        bool aligned = (row_bytes % 16 == 0) && (a.b.sbytes % 16 == 0);
         for (int q = 0; q < a.narr; ++q)
             aligned = aligned && ((uintptr_t)a.in[q] % 16 == 0) && ((uintptr_t)a.out[q] % 16 == 0);
         f.G = G;
@@ -405,7 +428,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         auto kern = k_xsolve_warp<P, PD>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        dim3 grid((a.nlines + G - 1) / G, a.narr);
+        dim3 grid((a.nlines + G - 1) / G, a.narr, a.b.S);
         kern<<<grid, 32 * G, smem, s>>>(f);
     } else {
         int G = sizeof(P) == 4 ? 8 : 4;
@@ -419,7 +442,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         auto kern = k_ysolve_cols<P, PD>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        dim3 grid((a.nlines + G - 1) / G, a.narr);
+        dim3 grid((a.nlines + G - 1) / G, a.narr, a.b.S);
         kern<<<grid, nt, smem, s>>>(f);
     }
     return cudaGetLastError();
@@ -432,8 +455,17 @@ template <typename P, int PD, int TX, int TY, int RY>
 __global__ void __launch_bounds__(TX*(TY / RY)) k_matvec_tile(int Nx, int Ny, int pitch, const P* __restrict__ T,
                                                           const P* __restrict__ F, P* R, const P* __restrict__ A1,
                                                           const P* __restrict__ B1, const P* __restrict__ A2,
-                                                          const P* __restrict__ B2, P Fscale, P c1, P c2) {
+                                                          const P* __restrict__ B2, P Fscale, P c1, P c2,
+                                                          Batch b) {
     constexpr int W = 2 * PD + 1, HY = TY + 2 * PD, HX = TX + 2 * PD, NTY = TY / RY;
+    if (!scene_active(b)) return;
+    T = scene_ptr(T, b);
+    F = scene_ptr(F, b);
+    R = scene_ptr(R, b);
+    A1 = scene_ptr(A1, b);
+    B1 = scene_ptr(B1, b);
+    A2 = scene_ptr(A2, b);
+    B2 = scene_ptr(B2, b);
     __shared__ P h[HY][HX + 1];
     __shared__ P x1[HY][TX + 1];
     __shared__ P x2[HY][TX + 1];
@@ -506,12 +538,12 @@ cudaError_t launch_line_fast(int prec, int p, bool xdir, const LineArgs& a, cuda
 
 cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s) {
     constexpr int TX = 32, TY = 16, RY = 2;
-    dim3 grid((a.Nx + TX - 1) / TX, (a.Ny + TY - 1) / TY), block(TX, TY / RY);
+    dim3 grid((a.Nx + TX - 1) / TX, (a.Ny + TY - 1) / TY, a.b.S), block(TX, TY / RY);
 #define WF_MV(P, PD)                                                                                             \
     k_matvec_tile<P, PD, TX, TY, RY><<<grid, block, 0, s>>>(a.Nx, a.Ny, a.pitch, (const P*)a.T, (const P*)a.F,   \
                                                             (P*)a.R, (const P*)a.A1, (const P*)a.B1,             \
                                                             (const P*)a.A2, (const P*)a.B2, (P)a.Fscale, (P)a.c1, \
-                                                            (P)a.c2)
+                                                            (P)a.c2, a.b)
     if (prec == 0) {
         switch (p) {
             case 1: WF_MV(float, 1); break;

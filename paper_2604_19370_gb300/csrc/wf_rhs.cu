@@ -76,6 +76,7 @@ struct RhsArgsT {
     const P *A1, *B1, *A2, *B2;
     P Rscale, c1, c2;
     PhysP<P> c;
+    Batch b;
 };
 
 template <typename P, int PD, int TJ, int TI>
@@ -89,8 +90,23 @@ struct RhsShape {
 };
 
 template <typename P, int PD, int TJ, int TI, int NT>
-__global__ void __launch_bounds__(NT) k_rhs(const RhsArgsT<P> a) {
+__global__ void __launch_bounds__(NT) k_rhs(const RhsArgsT<P> a_in) {
     using S_ = RhsShape<P, PD, TJ, TI>;
+    if (!scene_active(a_in.b)) return;
+    RhsArgsT<P> a = a_in;
+    a.T = scene_ptr(a.T, a.b);
+    a.phi = scene_ptr(a.phi, a.b);
+    a.F = scene_ptr(a.F, a.b);
+    a.Phi = scene_ptr(a.Phi, a.b);
+    a.R = scene_ptr(a.R, a.b);
+    a.A1 = scene_ptr(a.A1, a.b);
+    a.B1 = scene_ptr(a.B1, a.b);
+    a.A2 = scene_ptr(a.A2, a.b);
+    a.B2 = scene_ptr(a.B2, a.b);
+    a.fxq = scene_ptr(a.fxq, a.b);
+    a.gxq = scene_ptr(a.gxq, a.b);
+    a.fyq = scene_ptr(a.fyq, a.b);
+    a.gyq = scene_ptr(a.gyq, a.b);
     constexpr int Q = S_::Q, NB = S_::NB, CJ = S_::CJ, CI = S_::CI, EJ = S_::EJ, EI = S_::EI, XI = S_::XI,
                   YJ = S_::YJ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -318,6 +334,7 @@ RhsArgsT<P> to_typed(const RhsArgs& a) {
     t.c1 = (P)a.c1;
     t.c2 = (P)a.c2;
     t.c = to_phys<P>(a.phys, a.tau);
+    t.b = a.b;
     return t;
 }
 
@@ -331,7 +348,7 @@ cudaError_t run_rhs(const RhsArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 grid((a.Nx + TI - 1) / TI, (a.Ny + TJ - 1) / TJ);
+    dim3 grid((a.Nx + TI - 1) / TI, (a.Ny + TJ - 1) / TJ, a.b.S);
     kern<<<grid, NT, S_::bytes, s>>>(to_typed<P>(a));
     return cudaGetLastError();
 }

@@ -55,6 +55,7 @@ struct StreamArgs {
     const P *A1, *B1, *A2, *B2;
     P Rscale, c1, c2;
     PhysS<P> c;
+    Batch b;
 };
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -68,8 +69,23 @@ __device__ __forceinline__ P col_from(P own, P extra, int lane, int k) {
 }
 
 template <typename P, int PD, int WR>
-__global__ void __launch_bounds__(128) k_rhs_stream(const StreamArgs<P> a) {
+__global__ void __launch_bounds__(128) k_rhs_stream(const StreamArgs<P> a_in) {
     constexpr int Q = PD + 1, NB = PD + 1, W = 2 * PD + 1, NC = 2 * PD + 1;
+    if (!scene_active(a_in.b)) return;
+    StreamArgs<P> a = a_in;
+    a.T = scene_ptr(a.T, a.b);
+    a.phi = scene_ptr(a.phi, a.b);
+    a.F = scene_ptr(a.F, a.b);
+    a.Phi = scene_ptr(a.Phi, a.b);
+    a.R = scene_ptr(a.R, a.b);
+    a.A1 = scene_ptr(a.A1, a.b);
+    a.B1 = scene_ptr(a.B1, a.b);
+    a.A2 = scene_ptr(a.A2, a.b);
+    a.B2 = scene_ptr(a.B2, a.b);
+    a.fxq = scene_ptr(a.fxq, a.b);
+    a.gxq = scene_ptr(a.gxq, a.b);
+    a.fyq = scene_ptr(a.fyq, a.b);
+    a.gyq = scene_ptr(a.gyq, a.b);
     const int lane = threadIdx.x & 31;
     const int strip = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (strip >= a.nstrips) return;  // whole warp leaves; no block barrier in this kernel
@@ -363,7 +379,7 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
     }
     const long ctas_x = (a.nstrips + WARPS - 1) / WARPS;
     int seg = 128;
-    while (seg > 16 && 10 * ctas_x * ((r.Ny + seg - 1) / seg) < 18L * sms) seg /= 2;
+    while (seg > 16 && 10 * ctas_x * ((r.Ny + seg - 1) / seg) * r.b.S < 18L * sms) seg /= 2;
     a.seg = seg;
     a.T = (const P*)r.T;
     a.phi = (const P*)r.phi;
@@ -389,7 +405,8 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
     a.c1 = (P)r.c1;
     a.c2 = (P)r.c2;
     a.c = to_phys_s<P>(r.phys, r.tau);
-    dim3 grid((a.nstrips + WARPS - 1) / WARPS, (r.Ny + seg - 1) / seg);
+    a.b = r.b;
+    dim3 grid((a.nstrips + WARPS - 1) / WARPS, (r.Ny + seg - 1) / seg, r.b.S);
     k_rhs_stream<P, PD, WR><<<grid, 32 * WARPS, 0, s>>>(a);
     return cudaGetLastError();
 }

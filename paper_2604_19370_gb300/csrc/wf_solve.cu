@@ -53,7 +53,25 @@ struct LineArgsT {
     const P* base[2];
     int* status;
     P tmax;
+    Batch b;
 };
+
+template <typename P>
+__device__ __forceinline__ LineArgsT<P> scene_line_args(const LineArgsT<P>& a_in) {
+    LineArgsT<P> a = a_in;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        a.in[q] = scene_ptr(a.in[q], a.b);
+        a.out[q] = scene_ptr(a.out[q], a.b);
+        a.f[q].lu = scene_ptr(a.f[q].lu, a.b);
+        a.f[q].spk = scene_ptr(a.f[q].spk, a.b);
+        a.f[q].E = scene_ptr(a.f[q].E, a.b);
+        a.premul[q] = scene_ptr(a.premul[q], a.b);
+        a.base[q] = scene_ptr(a.base[q], a.b);
+    }
+    a.status = scene_ptr(a.status, a.b);
+    return a;
+}
 
 // Forward and backward substitution of one chunk, in place on g (stride 1).
 template <typename P, int PD>
@@ -153,7 +171,9 @@ __device__ __forceinline__ P spike_correct(const P* __restrict__ sk, P g, const 
 
 // x pass.  blockIdx.x: group of ROWS rows; blockIdx.y: array.  blockDim.x = ROWS * C.
 template <typename P, int PD, int ROWS>
-__global__ void k_xsolve(const LineArgsT<P> a) {
+__global__ void k_xsolve(const LineArgsT<P> a_in) {
+    if (!scene_active(a_in.b)) return;
+    const LineArgsT<P> a = scene_line_args(a_in);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     P* buf = reinterpret_cast<P*>(smem_raw);
     const int arr = blockIdx.y;
@@ -199,7 +219,9 @@ __global__ void k_xsolve(const LineArgsT<P> a) {
 
 // y pass.  blockIdx.x: group of COLS columns; blockIdx.y: array.  blockDim.x = COLS * C.
 template <typename P, int PD, int COLS>
-__global__ void k_ysolve(const LineArgsT<P> a) {
+__global__ void k_ysolve(const LineArgsT<P> a_in) {
+    if (!scene_active(a_in.b)) return;
+    const LineArgsT<P> a = scene_line_args(a_in);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     P* buf = reinterpret_cast<P*>(smem_raw);
     constexpr int W = 2 * PD + 1;
@@ -276,6 +298,7 @@ LineArgsT<P> to_typed(const LineArgs& a, int mpad) {
     }
     t.status = a.status;
     t.tmax = (P)a.tmax;
+    t.b = a.b;
     return t;
 }
 
@@ -292,7 +315,7 @@ cudaError_t run_line(const LineArgs& a, cudaStream_t s) {
     const int threads = G * ch.C;
     const size_t smem = (size_t)threads * mpad * sizeof(P);
     if (threads > 1024 || smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-    dim3 grid((a.nlines + G - 1) / G, a.narr);
+    dim3 grid((a.nlines + G - 1) / G, a.narr, a.b.S);
     if (X) {
         auto kern = k_xsolve<P, PD, G>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

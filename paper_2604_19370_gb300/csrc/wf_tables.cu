@@ -350,6 +350,16 @@ __global__ void k_convert_out(const P* __restrict__ src, double* dst, int Nx, in
     dst[idx] = (double)src[(size_t)j * pitch + i];
 }
 
+// Guard flags of S scenarios (each in its own block, sbytes apart) gathered into out[S],
+// and cleared when clear != 0.
+__global__ void k_gather_status(int* status0, long long sbytes, int S, int* out, int clear) {
+    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= S) return;
+    int* st = reinterpret_cast<int*>(reinterpret_cast<char*>(status0) + (long long)z * sbytes);
+    out[z] = st[0];
+    if (clear) st[0] = 0;
+}
+
 template <typename P>
 __global__ void k_fill(P* dst, size_t n, P v) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -428,6 +438,11 @@ cudaError_t launch_convert_out(int prec, const void* src, double* dst, int Nx, i
         k_convert_out<float><<<blocks(cnt, 256), 256, 0, s>>>((const float*)src, dst, Nx, Ny, pitch);
     else
         k_convert_out<double><<<blocks(cnt, 256), 256, 0, s>>>((const double*)src, dst, Nx, Ny, pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_status(int* status0, long long sbytes, int S, int* out, int clear, cudaStream_t s) {
+    k_gather_status<<<blocks(S, 128), 128, 0, s>>>(status0, sbytes, S, out, clear);
     return cudaGetLastError();
 }
 

@@ -42,6 +42,19 @@ class wf_params(ctypes.Structure):
         "scheme", "precision", "F_timing", "scale_heat_by_fuel")]
 
 
+class wf_request(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("p", ctypes.c_int), ("steps", ctypes.c_int),
+                ("dt", ctypes.c_double), ("params", wf_params), ("T0", ctypes.POINTER(ctypes.c_double)),
+                ("fuel0", ctypes.POINTER(ctypes.c_double)), ("wind_rank", ctypes.c_int),
+                ("wind_factors", ctypes.POINTER(ctypes.c_double)), ("T_out", ctypes.POINTER(ctypes.c_double)),
+                ("fuel_out", ctypes.POINTER(ctypes.c_double))]
+
+
+class wf_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double),
+                ("run_s", ctypes.c_double)]
+
+
 class WFError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -72,6 +85,19 @@ def lib() -> ctypes.CDLL:
         L.wf_set_profiling.argtypes = [vp, i]
         L.wf_kernel_times.argtypes = [vp, dp, ctypes.POINTER(i), ctypes.c_void_p, i]
         L.wf_step_noalloc.argtypes = [vp, vp, vp, i, i]
+        L.wf_batch_create.argtypes = [i, i, i, d, ctypes.POINTER(wf_params), i, ctypes.POINTER(vp)]
+        L.wf_batch_set_slot.argtypes = [vp, i, dp, dp, d, d, i, dp]
+        L.wf_batch_get_slot.argtypes = [vp, i, dp, dp]
+        L.wf_batch_activate.argtypes = [vp, i, i]
+        L.wf_batch_status.argtypes = [vp, ctypes.POINTER(i), i]
+        L.wf_batch_capacity.argtypes = [vp]
+        L.wf_device_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+        L.wf_server_create.argtypes = [sz, i, ctypes.POINTER(vp)]
+        L.wf_submit.argtypes = [vp, ctypes.POINTER(wf_request), ctypes.POINTER(ctypes.c_uint64)]
+        L.wf_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(wf_result)]
+        L.wf_server_stats.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(sz)]
+        L.wf_server_destroy.argtypes = [vp]
+        L.wf_server_destroy.restype = None
         L.wf_destroy.argtypes = [vp]
         L.wf_destroy.restype = None
         L.wf_strerror.argtypes = [i]
@@ -193,6 +219,120 @@ def wf_step_noalloc(h, T_dev_ptr: int, fuel_dev_ptr: int, pitch: int, nsteps: in
     return lib().wf_step_noalloc(h, ctypes.c_void_p(T_dev_ptr), ctypes.c_void_p(fuel_dev_ptr), pitch, nsteps)
 
 
+def wf_batch_create(nx: int, ny: int, p: int, dt: float, params: wf_params, capacity: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().wf_batch_create(nx, ny, p, dt, ctypes.byref(params), capacity, ctypes.byref(h)), "wf_batch_create")
+    return h
+
+
+def wf_batch_set_slot(h, slot: int, T, fuel, wind_x: float, wind_y: float, wind_rank: int = 0, factors=None) -> None:
+    Nx, Ny, _, _ = wf_get_dims(h)
+    n = Nx * Ny
+    Ta, Fa = _host(T, n), _host(fuel, n)
+    fa = None if factors is None else np.ascontiguousarray(factors, dtype=np.float64).ravel()
+    _check(lib().wf_batch_set_slot(h, slot, _dptr(Ta), _dptr(Fa), float(wind_x), float(wind_y), wind_rank, _dptr(fa)),
+           "wf_batch_set_slot")
+
+
+def wf_batch_get_slot(h, slot: int) -> Tuple[np.ndarray, np.ndarray]:
+    Nx, Ny, _, _ = wf_get_dims(h)
+    T = np.empty((Ny, Nx))
+    F = np.empty((Ny, Nx))
+    _check(lib().wf_batch_get_slot(h, slot, _dptr(T), _dptr(F)), "wf_batch_get_slot")
+    return T, F
+
+
+def wf_batch_activate(h, slot: int, on: bool) -> None:
+    _check(lib().wf_batch_activate(h, slot, 1 if on else 0), "wf_batch_activate")
+
+
+def wf_batch_status(h) -> np.ndarray:
+    S = wf_batch_capacity(h)
+    st = (ctypes.c_int * S)()
+    _check(lib().wf_batch_status(h, st, S), "wf_batch_status")
+    return np.array(st[:], dtype=np.int32)
+
+
+def wf_batch_capacity(h) -> int:
+    return _check(lib().wf_batch_capacity(h), "wf_batch_capacity")
+
+
+def wf_device_bytes(h) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().wf_device_bytes(h, ctypes.byref(b)), "wf_device_bytes")
+    return b.value
+
+
+def wf_server_create(hbm_budget_bytes: int, max_slots: int) -> ctypes.c_void_p:
+    s = ctypes.c_void_p()
+    _check(lib().wf_server_create(hbm_budget_bytes, max_slots, ctypes.byref(s)), "wf_server_create")
+    return s
+
+
+def wf_server_destroy(s) -> None:
+    if s:
+        lib().wf_server_destroy(s)
+
+
+def wf_server_stats(s):
+    d = ctypes.c_double()
+    c = ctypes.c_uint64()
+    b = ctypes.c_size_t()
+    _check(lib().wf_server_stats(s, ctypes.byref(d), ctypes.byref(c), ctypes.byref(b)), "wf_server_stats")
+    return d.value, c.value, b.value
+
+
+class Server:
+    """Owning wrapper around wf_server: keeps every request's arrays alive until it is polled."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 16):
+        self.s = wf_server_create(hbm_budget_bytes, max_slots)
+        self.live = {}
+
+    def submit(self, sc, steps=None, precision=WF_FP32, scheme=WF_PR, F_timing=WF_F_ONCE) -> int:
+        """Queue scenario `sc` (a scenarios.Scenario); returns its ticket."""
+        prm = wf_params_default(Lx=sc.Lx, Ly=sc.Ly, wind_x=sc.wind[0], wind_y=sc.wind[1], precision=precision,
+                                scheme=scheme, F_timing=F_timing)
+        T0 = np.ascontiguousarray(sc.T0, dtype=np.float64)
+        f0 = np.ascontiguousarray(sc.fuel0, dtype=np.float64)
+        wfac = sc.wind_packed()
+        wfac = None if wfac is None else np.ascontiguousarray(wfac, dtype=np.float64)
+        Tout = np.empty_like(T0)
+        fout = np.empty_like(f0)
+        r = wf_request(nx=sc.nx, ny=sc.ny, p=sc.p, steps=sc.steps if steps is None else steps, dt=sc.dt, params=prm,
+                       T0=_dptr(T0), fuel0=_dptr(f0), wind_rank=sc.wind_rank, wind_factors=_dptr(wfac),
+                       T_out=_dptr(Tout), fuel_out=_dptr(fout))
+        t = ctypes.c_uint64()
+        _check(lib().wf_submit(self.s, ctypes.byref(r), ctypes.byref(t)), "wf_submit")
+        self.live[t.value] = (Tout, fout, T0, f0, wfac)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending; else (status, wf_result, T, fuel)."""
+        res = wf_result()
+        code = lib().wf_poll(self.s, ticket, ctypes.byref(res))
+        if code == WF_PENDING:
+            return None
+        if code == WF_ENOTFOUND:
+            raise WFError(code, "wf_poll")
+        Tout, fout = self.live.pop(ticket)[:2]
+        return code, res, Tout, fout
+
+    def stats(self):
+        return wf_server_stats(self.s)
+
+    def close(self):
+        if self.s:
+            wf_server_destroy(self.s)
+            self.s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def wf_destroy(h) -> None:
     if h:
         lib().wf_destroy(h)
@@ -219,6 +359,51 @@ class Simulation:
 
     def state(self):
         return wf_get_state(self.h)
+
+    def close(self):
+        if self.h:
+            wf_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owning wrapper around a batch handle (capacity scenario slots of one grid)."""
+
+    def __init__(self, nx, ny, p, dt, params: wf_params, capacity: int):
+        self.h = wf_batch_create(nx, ny, p, dt, params, capacity)
+        self.Nx, self.Ny, self.p, self.precision = wf_get_dims(self.h)
+        self.capacity = capacity
+
+    def set_slot(self, slot, T, fuel, wind, wind_rank=0, factors=None):
+        wf_batch_set_slot(self.h, slot, T, fuel, wind[0], wind[1], wind_rank, factors)
+
+    def load_scenario(self, slot, sc, active=True):
+        self.set_slot(slot, sc.T0, sc.fuel0, sc.wind, sc.wind_rank, sc.wind_packed())
+        wf_batch_activate(self.h, slot, active)
+
+    def activate(self, slot, on=True):
+        wf_batch_activate(self.h, slot, on)
+
+    def step(self, n=1):
+        wf_step(self.h, n)
+
+    def status(self):
+        return wf_batch_status(self.h)
+
+    def state(self, slot):
+        return wf_batch_get_slot(self.h, slot)
 
     def close(self):
         if self.h:

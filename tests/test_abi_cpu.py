@@ -75,3 +75,20 @@ def test_no_device_reports_cuda_error(libpath):
     h = ctypes.c_void_p()
     assert L.wf_create(8, 8, 2, 1e-3, ctypes.byref(p), ctypes.byref(h)) == wf.WF_ECUDA
     assert not h.value
+
+
+def test_server_and_batch_argument_checks(libpath):
+    from paper_2604_19370_gb300 import wf
+
+    L = wf.lib()
+    s = ctypes.c_void_p()
+    assert L.wf_server_create(0, 4, ctypes.byref(s)) == wf.WF_EINVAL
+    assert L.wf_server_create(1 << 20, 0, ctypes.byref(s)) == wf.WF_EINVAL
+    assert L.wf_submit(None, None, None) == wf.WF_EINVAL
+    assert L.wf_poll(None, 1, None) == wf.WF_EINVAL
+    L.wf_server_destroy(None)
+    h = ctypes.c_void_p()
+    p = wf.wf_params_default()
+    assert L.wf_batch_create(8, 8, 2, 1e-3, ctypes.byref(p), 0, ctypes.byref(h)) == wf.WF_EINVAL
+    assert L.wf_batch_activate(None, 0, 1) == wf.WF_EINVAL
+    assert L.wf_batch_capacity(None) == wf.WF_EINVAL
