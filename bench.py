@@ -157,6 +157,31 @@ def _dist():
     return world, rank, local
 
 
+def reduce_max(x: float, device=None) -> float:
+    """Maximum of x over all ranks (x itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_throughput(units_per_rank: float, local_seconds: float, world: int, device=None):
+    """Units all ranks processed / the slowest rank's time (weak scaling: fixed units per rank)."""
+    slowest = reduce_max(local_seconds, device)
+    return world * units_per_rank / slowest, slowest
+
+
+def shard(n_items: int, rank: int, world: int):
+    """Contiguous share of n_items for one rank (independent scenarios; no exchange between ranks)."""
+    base, extra = divmod(n_items, world)
+    start = rank * base + min(rank, extra)
+    return range(start, start + base + (1 if rank < extra else 0))
+
+
 def _oracle_sample(steps: int, which: str = "c2", scheme: str = "pr") -> dict:
     """Run the FP64 oracle (ads mode) in a fresh single-threaded process; returns timing and state file."""
     out = tempfile.mktemp(suffix=".npz")
@@ -287,12 +312,8 @@ def run_gpu(args) -> None:
     with ClockSampler(local) as clk:
         ms_total = run_steps(False)
     status = sim.sync()
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_per_step = ms_total / args.steps
-    value = world * sc.dofs / (ms_per_step * 1e-3)
+    value, slowest_s = whole_job_throughput(sc.dofs * args.steps, ms_total * 1e-3, world, dev)
+    ms_per_step = slowest_s * 1e3 / args.steps
 
     # kernel durations: the same K steps launched kernel by kernel with a CUDA event pair around
     # each launch on the launching stream (the event records add small gaps between kernels,
@@ -316,11 +337,7 @@ def run_gpu(args) -> None:
         wf.wf_set_state_ptr(sim.h, hT.data_ptr(), hP.data_ptr(), n)
         wf.wf_step(sim.h, 1)
         wf.wf_get_state_ptr(sim.h, hT.data_ptr(), hP.data_ptr(), n)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dev)
 
     # roofline of the dominant kernel class
     peaks = _peaks()
@@ -413,6 +430,206 @@ def run_gpu(args) -> None:
         torch.distributed.destroy_process_group()
 
 
+
+def _percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q
+    f = int(math.floor(k))
+    c = min(f + 1, len(xs) - 1)
+    return xs[f] + (xs[c] - xs[f]) * (k - f)
+
+
+def run_ensemble(args) -> None:
+    """Batched ensemble: S scenarios of 256^2 elements (p = 2) stepped together, one launch per kernel."""
+    import numpy as np
+    import torch
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2604_19370_gb300.build import build_library
+
+    build_library()
+    from paper_2604_19370_gb300 import wf
+    from scenarios import config_c4
+
+    S = args.scenarios
+    first = config_c4(0)
+    shared = first.fuel0
+    scs = [first] + [config_c4(k, shared_fuel=shared) for k in range(1, S)]
+    prm = wf.wf_params_default(Lx=first.Lx, Ly=first.Ly, precision=wf.WF_FP32)
+    b = wf.Batch(first.nx, first.ny, first.p, first.dt, prm, capacity=S)
+    for k, sc in enumerate(scs):
+        b.load_scenario(k, sc)
+    stream = torch.cuda.Stream(device=dev)
+    wf.wf_set_stream(b.h, stream.cuda_stream)
+    dofs = S * first.dofs
+    with torch.cuda.stream(stream):
+        b.step(args.warmup)
+    stream.synchronize()
+
+    def timed(profile):
+        wf.wf_set_profiling(b.h, profile)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(args.steps):
+                wf.wf_step(b.h, 1)
+            e1.record(stream)
+        stream.synchronize()
+        wf.wf_set_profiling(b.h, False)
+        return e0.elapsed_time(e1) * 1e-3
+
+    with ClockSampler(local) as clk:
+        secs = timed(False)
+    value, slowest = whole_job_throughput(dofs * args.steps, secs, world, dev)
+    wf.wf_kernel_times(b.h)
+    timed(True)
+    kt = wf.wf_kernel_times(b.h)
+    st = b.status()
+    peaks = _peaks()
+    costs = algorithmic_costs(first.p)
+    shares = {k: v[0] for k, v in kt.items() if v[1] > 0}
+    dom = max(shares, key=shares.get)
+    dom_ms = kt[dom][0] / kt[dom][1]
+    props = torch.cuda.get_device_properties(dev)
+    alu_peak = fp32_alu_peak_tflops(props.multi_processor_count, peaks["sm_max_mhz"])
+    c = costs[dom]
+    if c["flops"] / c["bytes"] > alu_peak * 1e12 / (peaks["hbm_gbs"] * 1e9):
+        ach = c["flops"] * dofs / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak}
+    else:
+        ach = c["bytes"] * dofs / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"]}
+    roof.update({"kernel": dom, "ms_per_launch": dom_ms, "traffic": None})
+    step_bytes = sum(costs[k]["bytes"] for k in costs if k in shares) * dofs
+    # end to end through the C ABI: load every slot from host memory, one step, read every slot back
+    n = first.dofs
+    hT = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hP = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    e2e_steps = 2
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for k, sc in enumerate(scs):
+            wf.wf_batch_set_slot(b.h, k, sc.T0, sc.fuel0, sc.wind[0], sc.wind[1], 0, None)
+        wf.wf_step(b.h, 1)
+        for k in range(S):
+            b.state(k)
+    e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dev)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": slowest * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"c4_ensemble_{S}x256x256_p2_pr", "scenarios": S, "nx": 256, "ny": 256, "p": 2,
+                   "dofs": dofs, "l2": f"state {S} x 5 fields > L2, no flush", "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "step_hbm_frac": step_bytes / (slowest / args.steps) / 1e9 / peaks["hbm_gbs"],
+        "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in kt.items() if v[1] > 0},
+        "gpu_launches": int(sum(v[1] for v in kt.values())),
+        "e2e": {"value": world * dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * dofs,
+                "d2h_bytes_per_step": 2 * 8 * dofs, "ms_per_step": e2e_s * 1e3},
+        "clocks": clk.summary(),
+        "unstable_slots": int(st.sum()),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle.step import Problem
+
+        ks = 2
+        P = Problem.from_scenario(scs[0], mode="ads")
+        t0 = time.perf_counter()
+        To, po = P.run(scs[0].T0, scs[0].fuel0, ks)
+        cpu_s = time.perf_counter() - t0
+        chk = wf.simulation_from_scenario(scs[0], precision=wf.WF_FP32)
+        chk.step(ks)
+        Tg, pg = chk.state()
+        chk.close()
+        line["cpu_baseline"] = {"value": first.dofs * ks / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{ks} PR steps of scenario 0 of the ensemble, FP64, ads mode"}
+        line["rel_l2_vs_oracle"] = {"steps": ks, "T": float(np.linalg.norm(Tg - To) / np.linalg.norm(To))}
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_serving(args) -> None:
+    """Served request stream: Poisson arrivals at 80 % of measured capacity, p50/p99 latency."""
+    import torch
+
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_2604_19370_gb300.build import build_library
+
+    build_library()
+    from paper_2604_19370_gb300 import wf
+    from scenarios import make_scenario, request_stream_c5
+
+    free, _total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+
+    def scenario(r):
+        return make_scenario(f"q{r['seed']}", r["n"], r["p"], 1e-3, r["steps"], r["seed"], fuel_sigma=20.0,
+                             wind_speed_range=(0.0, 3.0))
+
+    def run(reqs, rate):
+        srv = wf.Server(budget, max_slots=args.max_slots)
+        prepared = [(scenario(r), r) for r in reqs]
+        tickets, lat, dof_steps = {}, [], 0.0
+        t_start = time.perf_counter()
+        pending = list(prepared)
+        while pending or tickets:
+            now = time.perf_counter() - t_start
+            while pending and (rate is None or pending[0][1]["arrival_s"] <= now):
+                sc, r = pending.pop(0)
+                prec = wf.WF_FP64 if r["fp64"] else wf.WF_FP32
+                tickets[srv.submit(sc, precision=prec)] = sc
+            for t in list(tickets):
+                out = srv.poll(t)
+                if out is not None:
+                    sc = tickets.pop(t)
+                    if out[0] == wf.WF_OK:
+                        lat.append(out[1].latency_s)
+                        dof_steps += sc.dofs * sc.steps
+            time.sleep(0.0005)
+        makespan = time.perf_counter() - t_start
+        srv.close()
+        return lat, dof_steps, makespan
+
+    # capacity: closed loop, every request submitted at once
+    warm = request_stream_c5(4, 1.0, seed=55)
+    run(warm, None)
+    closed = request_stream_c5(args.requests, 1.0, seed=5)
+    lat_c, ds_c, span_c = run(closed, None)
+    capacity = len(lat_c) / span_c
+    rate = 0.8 * capacity
+    open_reqs = request_stream_c5(args.requests, rate, seed=6)
+    lat, ds, span = run(open_reqs, rate)
+    line = {
+        "metric": METRIC, "value": ds / span, "unit": UNIT, "n_gpus": 1, "steps": len(open_reqs),
+        "warmup": len(warm), "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (20% of requests f64)", "data": "synthetic",
+        "config": {"workload": "c5_served_poisson", "requests": len(open_reqs), "arrival_rate_hz": rate,
+                   "capacity_rps": capacity, "sizes": [128, 256, 512, 1024], "p": [2, 3],
+                   "steps": "U[200,2000]", "fp64_share": 0.2, "hbm_budget_bytes": budget,
+                   "max_slots_per_class": args.max_slots},
+        "latency_p50_s": _percentile(lat, 0.5), "latency_p99_s": _percentile(lat, 0.99),
+        "completed": len(lat), "closed_loop_dof_steps_per_s": ds_c / span_c,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,11 +642,20 @@ def main():
     ap.add_argument("--strang", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
+                    help="c2: one 1024^2 domain (default); c4: batched ensemble; c5: served request stream")
+    ap.add_argument("--scenarios", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--max-slots", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c4":
+        run_ensemble(args)
+    elif args.workload == "c5":
+        run_serving(args)
     else:
         run_gpu(args)
 
