@@ -48,12 +48,14 @@ def fp32_alu_peak_tflops(sm_count: int, mhz: float) -> float:
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
 
 
-def algorithmic_costs(p: int) -> dict:
+def algorithmic_costs(p: int, fused_x2: bool = True) -> dict:
     """Algorithmic bytes and flops per DOF of each kernel class (FP32, 4-byte values).
 
     Flops count the sum-factorised quadrature once per element (no halo
     recomputation), one FMA = 2 flops, 30 flops per Gauss point for the
-    pointwise terms (exp and reciprocal counted as one each).
+    pointwise terms (exp and reciprocal counted as one each).  With `fused_x2`
+    the second x pass forms its right-hand side from T* and F itself (no
+    separate matvec launch).
     """
     q = nb = p + 1
     W = 2 * p + 1
@@ -68,7 +70,8 @@ def algorithmic_costs(p: int) -> dict:
         "ysolve_1": dict(bytes=24, flops=2 * (4 * p + 2) * 2),
         # read T*, F; write R
         "matvec_2": dict(bytes=12, flops=2 * 2 * (W * W + W) + 2),
-        "xsolve_2": dict(bytes=8, flops=(4 * p + 1) * 2),
+        "xsolve_2": (dict(bytes=12, flops=2 * 2 * (W * W + W) + 2 + (4 * p + 1) * 2) if fused_x2
+                     else dict(bytes=8, flops=(4 * p + 1) * 2)),
         "ysolve_2": dict(bytes=12, flops=(4 * p + 2) * 2),
     }
 
@@ -341,7 +344,8 @@ def run_gpu(args) -> None:
 
     # roofline of the dominant kernel class
     peaks = _peaks()
-    costs = algorithmic_costs(sc.p if not args.fp64 else sc.p)
+    costs = algorithmic_costs(sc.p, fused_x2=("matvec_2" not in kt or kt["matvec_2"][1] == 0)
+                              and not args.strang)
     es = 8 if args.fp64 else 4
     shares = {k: v[0] for k, v in kt.items() if v[1] > 0}
     dom = max(shares, key=shares.get)

@@ -408,7 +408,13 @@ cudaError_t timed(wf_handle* h, int site, F&& launch) {
     cudaEventRecord(a, h->stream);
     cudaError_t e = launch();
     cudaEventRecord(b, h->stream);
-    h->pending.push_back({site, a, b});
+    if (e == cudaSuccess) h->pending.push_back({site, a, b});
+    else {
+        // nothing launched (or the launch failed): the events time no kernel
+        cudaEventSynchronize(b);
+        h->ev_free.push_back(a);
+        h->ev_free.push_back(b);
+    }
     return e;
 }
 
@@ -514,7 +520,26 @@ cudaError_t enqueue_step(wf_handle* h) {
         add_line(y1, h->R, h->T, Y[0], cy, h->T);
         if (once) add_line(y1, h->Phi, h->phi, Y[0], cy, h->phi);
         if ((e = timed(h, S_Y1, [&] { return launch_ysolve(prec, p, y1, s); })) != cudaSuccess) return e;
+        bool fused = false;
         if (once) {
+            // substep 2 in one x pass: R = th F + (op1_x (x) M^y) T* + (M^x (x) op1_y) T*, then M^x lines
+            LineArgs x2 = line_args(h, true);
+            add_line(x2, nullptr, h->R, X[0], cx);
+            x2.preT = h->T;
+            x2.preF = h->F;
+            x2.preFscale = th;
+            x2.pc1 = 1.0;
+            x2.pc2 = 1.0;
+            x2.pA1 = X[1].bandP;
+            x2.pB1 = Y[0].bandP;
+            x2.pA2 = X[0].bandP;
+            x2.pB2 = Y[1].bandP;
+            e = timed(h, S_X2, [&] { return launch_xsolve(prec, p, x2, s); });
+            if (e == cudaSuccess) fused = true;
+            else if (e != cudaErrorNotSupported) return e;
+            else cudaGetLastError();
+        }
+        if (once && !fused) {
             MatvecArgs mv;
             mv.Nx = h->Nx;
             mv.Ny = h->Ny;
@@ -531,13 +556,15 @@ cudaError_t enqueue_step(wf_handle* h) {
             mv.c2 = 1.0;
             mv.b = batch(h);
             if ((e = timed(h, S_MV2, [&] { return launch_matvec(prec, p, mv, s); })) != cudaSuccess) return e;
-        } else {
+        } else if (!once) {
             RhsArgs r2 = rhs_args(h, h->T, nullptr, nullptr, h->R, th, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
             if ((e = timed(h, S_RHS2, [&] { return launch_rhs(prec, p, r2, s); })) != cudaSuccess) return e;
         }
-        LineArgs x2 = line_args(h, true);
-        add_line(x2, h->R, h->R, X[0], cx);
-        if ((e = timed(h, S_X2, [&] { return launch_xsolve(prec, p, x2, s); })) != cudaSuccess) return e;
+        if (!fused) {
+            LineArgs x2 = line_args(h, true);
+            add_line(x2, h->R, h->R, X[0], cx);
+            if ((e = timed(h, S_X2, [&] { return launch_xsolve(prec, p, x2, s); })) != cudaSuccess) return e;
+        }
         LineArgs y2 = line_args(h, false);
         add_line(y2, h->R, h->T, Y[2], cy, h->T);
         if (!once) add_line(y2, h->Phi, h->phi, Y[0], cy, h->phi);

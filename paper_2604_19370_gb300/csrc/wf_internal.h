@@ -145,7 +145,13 @@ struct LineArgs {
     const void* base[2];    // y pass only: out = base + solution (or NULL: out = solution)
     int* status;            // y pass only: guard flag for out[0] (or NULL)
     double tmax;
-    Batch b;  // per scenario: in, out, factors, premul, base, status
+    Batch b;  // per scenario: in, out, factors, premul, base, status, pre*
+    // x pass only, one array: when preT is set the input line is formed in the kernel as
+    // R = preFscale preF + pc1 (pA1 (x) pB1) preT + pc2 (pA2 (x) pB2) preT  (in[0] unused)
+    const void* preT;
+    const void* preF;
+    double preFscale, pc1, pc2;
+    const void *pA1, *pB1, *pA2, *pB2;
 };
 cudaError_t launch_xsolve(int prec, int p, const LineArgs& a, cudaStream_t s);
 cudaError_t launch_ysolve(int prec, int p, const LineArgs& a, cudaStream_t s);

@@ -38,23 +38,47 @@ struct FastArgs {
     P tmax;
     int tma;  // x pass: rows staged with bulk copies (16-byte aligned rows)
     Batch b;
+    const P* preT;
+    const P* preF;
+    P preFscale, pc1, pc2;
+    const P *pA1, *pB1, *pA2, *pB2;
+};
+
+// Pointers of one array (blockIdx.y) of one scenario (blockIdx.z).  They are selected with
+// conditional moves rather than by indexing the parameter arrays, which would put a copy of
+// the whole argument block in local memory.
+template <typename P>
+struct LineView {
+    const P* in;
+    P* out;
+    const P* base;
+    const P* premul;
+    P prescale;
+    const P *luc, *spkc, *Ec;
+    int* status;
+    const P *preT, *preF, *pA1, *pB1, *pA2, *pB2;
 };
 
 template <typename P>
-__device__ __forceinline__ FastArgs<P> scene_args(const FastArgs<P>& a_in) {
-    FastArgs<P> a = a_in;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        a.in[q] = scene_ptr(a.in[q], a.b);
-        a.out[q] = scene_ptr(a.out[q], a.b);
-        a.base[q] = scene_ptr(a.base[q], a.b);
-        a.premul[q] = scene_ptr(a.premul[q], a.b);
-        a.luc[q] = scene_ptr(a.luc[q], a.b);
-        a.spkc[q] = scene_ptr(a.spkc[q], a.b);
-        a.Ec[q] = scene_ptr(a.Ec[q], a.b);
-    }
-    a.status = scene_ptr(a.status, a.b);
-    return a;
+__device__ __forceinline__ LineView<P> scene_line(const FastArgs<P>& a, int arr) {
+    const bool one = arr != 0;
+    LineView<P> v;
+    v.in = scene_ptr(one ? a.in[1] : a.in[0], a.b);
+    v.out = scene_ptr(one ? a.out[1] : a.out[0], a.b);
+    v.base = scene_ptr(one ? a.base[1] : a.base[0], a.b);
+    v.premul = scene_ptr(one ? a.premul[1] : a.premul[0], a.b);
+    v.prescale = one ? a.prescale[1] : a.prescale[0];
+    v.luc = scene_ptr(one ? a.luc[1] : a.luc[0], a.b);
+    v.spkc = scene_ptr(one ? a.spkc[1] : a.spkc[0], a.b);
+    v.Ec = scene_ptr(one ? a.Ec[1] : a.Ec[0], a.b);
+    v.status = scene_ptr(a.status, a.b);
+    v.preT = scene_ptr(a.preT, a.b);
+    v.preF = scene_ptr(a.preF, a.b);
+    v.pA1 = scene_ptr(a.pA1, a.b);
+    v.pB1 = scene_ptr(a.pB1, a.b);
+    v.pA2 = scene_ptr(a.pA2, a.b);
+    v.pB2 = scene_ptr(a.pB2, a.b);
+    return v;
 }
 
 // ---- TMA bulk copies and mbarrier (PTX) ------------------------------------------------
@@ -100,34 +124,92 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 constexpr uint32_t kSpinLimit = 1u << 20;  // bounded mbarrier wait; a timeout sets status bit 2
 
 // Chunk-local LU substitution on g[0 .. m) (stride 1) with the factors of one chunk type.
+// The values and factors of 8 rows are loaded before the dependent FMA chain runs over
+// them, so shared-memory latency is paid once per 8 rows rather than once per row.
 template <typename P, int PD>
 __device__ __forceinline__ void lu_chunk(P* g, int m, const P* L) {
-    constexpr int W = 2 * PD + 1;
+    constexpr int W = 2 * PD + 1, B = 8;
     P prev[PD];
 #pragma unroll
     for (int i = 0; i < PD; ++i) prev[i] = P(0);
-#pragma unroll 4
-    for (int o = 0; o < m; ++o) {
-        P x = g[o];
+    for (int o0 = 0; o0 < m; o0 += B) {
+        P gv[B], lv[B][PD];
 #pragma unroll
-        for (int i = 0; i < PD; ++i) x -= L[o * W + i] * prev[i];
+        for (int q = 0; q < B; ++q) {
+            const int o = o0 + q < m ? o0 + q : m - 1;
+            gv[q] = g[o];
 #pragma unroll
-        for (int i = PD - 1; i > 0; --i) prev[i] = prev[i - 1];
-        prev[0] = x;
-        g[o] = x;
+            for (int i = 0; i < PD; ++i) lv[q][i] = L[o * W + i];
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            if (o0 + q < m) {
+                P x = gv[q];
+#pragma unroll
+                for (int i = 0; i < PD; ++i) x -= lv[q][i] * prev[i];
+#pragma unroll
+                for (int i = PD - 1; i > 0; --i) prev[i] = prev[i - 1];
+                prev[0] = x;
+                gv[q] = x;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q)
+            if (o0 + q < m) g[o0 + q] = gv[q];
     }
 #pragma unroll
     for (int i = 0; i < PD; ++i) prev[i] = P(0);
-#pragma unroll 4
-    for (int o = m - 1; o >= 0; --o) {
-        P x = g[o];
+    for (int o1 = m; o1 > 0; o1 -= B) {
+        P gv[B], uv[B][PD + 1];
 #pragma unroll
-        for (int j = 0; j < PD; ++j) x -= L[o * W + PD + 1 + j] * prev[j];
-        x *= L[o * W + PD];
+        for (int q = 0; q < B; ++q) {
+            const int o = o1 - 1 - q >= 0 ? o1 - 1 - q : 0;
+            gv[q] = g[o];
 #pragma unroll
-        for (int j = PD - 1; j > 0; --j) prev[j] = prev[j - 1];
-        prev[0] = x;
-        g[o] = x;
+            for (int j = 0; j <= PD; ++j) uv[q][j] = L[o * W + PD + j];
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            if (o1 - 1 - q >= 0) {
+                P x = gv[q];
+#pragma unroll
+                for (int j = 0; j < PD; ++j) x -= uv[q][1 + j] * prev[j];
+                x *= uv[q][0];
+#pragma unroll
+                for (int j = PD - 1; j > 0; --j) prev[j] = prev[j - 1];
+                prev[0] = x;
+                gv[q] = x;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q)
+            if (o1 - 1 - q >= 0) g[o1 - 1 - q] = gv[q];
+    }
+}
+
+// Spike corrections g[o] -= V[o] tn + W[o] bp on g[0 .. m), 8 rows per batch of loads.
+template <typename P, int PD>
+__device__ __forceinline__ void spike_fix(P* g, int m, const P* Sk, const P* tn, const P* bp) {
+    constexpr int S = 2 * PD, B = 8;
+    for (int o0 = 0; o0 < m; o0 += B) {
+        P gv[B], sv[B][S];
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            const int o = o0 + q < m ? o0 + q : m - 1;
+            gv[q] = g[o];
+#pragma unroll
+            for (int c = 0; c < S; ++c) sv[q][c] = Sk[o * S + c];
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            P x = gv[q];
+#pragma unroll
+            for (int r = 0; r < PD; ++r) x -= sv[q][r] * tn[r] + sv[q][PD + r] * bp[r];
+            gv[q] = x;
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q)
+            if (o0 + q < m) g[o0 + q] = gv[q];
     }
 }
 
@@ -190,12 +272,12 @@ __device__ __forceinline__ void interface_solve(const Chunks& ch, int k, int mma
 }
 
 template <typename P>
-__device__ __forceinline__ void stage_factors(const FastArgs<P>& a, int arr, int n_lu, int n_spk, int n_e, P* fl,
-                                              P* fs, P* fe) {
+__device__ __forceinline__ void stage_factors(const LineView<P>& v, int n_lu, int n_spk, int n_e, P* fl, P* fs,
+                                              P* fe) {
     const int nt = blockDim.x, tid = threadIdx.x;
-    const P* __restrict__ g1 = a.luc[arr];
-    const P* __restrict__ g2 = a.spkc[arr];
-    const P* __restrict__ g3 = a.Ec[arr];
+    const P* __restrict__ g1 = v.luc;
+    const P* __restrict__ g2 = v.spkc;
+    const P* __restrict__ g3 = v.Ec;
     for (int i = tid; i < n_lu; i += nt) fl[i] = g1[i];
     for (int i = tid; i < n_spk; i += nt) fs[i] = g2[i];
     for (int i = tid; i < n_e; i += nt) fe[i] = g3[i];
@@ -205,42 +287,59 @@ __device__ __forceinline__ void stage_factors(const FastArgs<P>& a, int arr, int
 // The G rows are contiguous in memory: one bulk copy stages them, one bulk store writes them back.
 // Chunk lengths are odd, so the 32 lanes of a warp read 32 distinct shared-memory banks.
 template <typename P, int PD>
-__global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a_in) {
+__global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
     constexpr int W = 2 * PD + 1, S = 2 * PD;
-    if (!scene_active(a_in.b)) return;
-    const FastArgs<P> a = scene_args(a_in);
+    if (!scene_active(a.b)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const Chunks ch = a.ch;
     const int N = ch.N, C = ch.C, base = ch.base, G = a.G;
     const int mmax = base + 2 * PD;
     const int arr = blockIdx.y;
+    const LineView<P> v = scene_line(a, arr);
     const int j0 = blockIdx.x * G;
     const int rows = min(G, a.nlines - j0);
     const size_t row_bytes = (size_t)a.pitch * sizeof(P);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    P* rowbuf = reinterpret_cast<P*>(smem_raw + 128);  // [G][pitch]
-    P* fl = rowbuf + (size_t)G * a.pitch;               // [3][mmax][W]
-    P* fs = fl + 3 * mmax * W;                          // [3][mmax][S]
-    P* fe = fs + 3 * mmax * S;                          // [3][PD*PD]
-    const P* __restrict__ in = a.in[arr];
-    P* out = a.out[arr];
+    const bool pre = a.preT != nullptr;
+    P* rowbuf = reinterpret_cast<P*>(smem_raw + 128);             // [G][pitch]
+    P* tbuf = rowbuf + (size_t)G * a.pitch;                        // pre: [G + 2p][pitch], rows j0-p ..
+    P* fl = tbuf + (pre ? (size_t)(G + 2 * PD) * a.pitch : 0);     // [3][mmax][W]
+    P* fs = fl + 3 * mmax * W;                                     // [3][mmax][S]
+    P* fe = fs + 3 * mmax * S;                                     // [3][PD*PD]
+    const P* __restrict__ in = pre ? v.preF : v.in;
+    P* out = v.out;
+    // rows of the halo block that exist (pre): lo .. hi-1
+    const int lo = max(0, j0 - PD), hi = min(a.nlines, j0 + rows + PD);
 
     bool staged = true;
+    if (pre) {
+        // halo rows outside the domain read as zero
+        for (int r = j0 - PD; r < j0 + rows + PD; ++r) {
+            if (r >= lo && r < hi) continue;
+            for (int x = tid; x < a.pitch; x += blockDim.x) tbuf[(size_t)(r - (j0 - PD)) * a.pitch + x] = P(0);
+        }
+    }
     if (a.tma) {
         if (tid == 0) {
             mbar_init(bar, 1);
             mbar_fence_init();
             const uint32_t bytes = (uint32_t)(rows * row_bytes);
-            mbar_expect_tx(bar, bytes);
+            const uint32_t tbytes = pre ? (uint32_t)((hi - lo) * row_bytes) : 0u;
+            mbar_expect_tx(bar, bytes + tbytes);
             bulk_load(rowbuf, in + (size_t)j0 * a.pitch, bytes, bar);
+            if (pre) bulk_load(tbuf + (size_t)(lo - (j0 - PD)) * a.pitch, v.preT + (size_t)lo * a.pitch, tbytes, bar);
         }
     } else {
         for (int r = 0; r < rows; ++r)
             for (int x = tid; x < N; x += blockDim.x) rowbuf[(size_t)r * a.pitch + x] = in[(size_t)(j0 + r) * a.pitch + x];
+        if (pre)
+            for (int r = lo; r < hi; ++r)
+                for (int x = tid; x < N; x += blockDim.x)
+                    tbuf[(size_t)(r - (j0 - PD)) * a.pitch + x] = v.preT[(size_t)r * a.pitch + x];
     }
-    stage_factors(a, arr, 3 * mmax * W, 3 * mmax * S, 3 * PD * PD, fl, fs, fe);
-    __syncthreads();  // mbarrier initialised, factors staged
+    stage_factors(v, 3 * mmax * W, 3 * mmax * S, 3 * PD * PD, fl, fs, fe);
+    __syncthreads();  // mbarrier initialised, factors staged, halo zeroed
     if (a.tma) {
         uint32_t it = 0;
         while (!mbar_try_wait(bar, 0) && ++it < kSpinLimit) {
@@ -252,8 +351,43 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a_in) {
         uint32_t it = 0;
         while (!mbar_try_wait(bar, 0) && ++it < kSpinLimit) {
         }
-        if (tid == 0 && a.status) atomicOr(a.status, 4);
+        if (tid == 0 && v.status) atomicOr(v.status, 4);
         return;
+    }
+    if (pre && warp < rows) {
+        // R = preFscale F + pc1 (pA1 (x) pB1) T + pc2 (pA2 (x) pB2) T for this warp's row
+        const int j = j0 + warp;
+        P b1[W], b2[W];
+#pragma unroll
+        for (int d = 0; d < W; ++d) {
+            b1[d] = a.pc1 * v.pB1[(size_t)j * W + d];
+            b2[d] = v.pA2 ? a.pc2 * v.pB2[(size_t)j * W + d] : P(0);
+        }
+        P* rrow = rowbuf + (size_t)warp * a.pitch;
+        for (int x = lane; x < N; x += 32) {
+            P a1v[W], a2v[W];
+#pragma unroll
+            for (int d = 0; d < W; ++d) {
+                a1v[d] = v.pA1[(size_t)x * W + d];
+                a2v[d] = v.pA2 ? v.pA2[(size_t)x * W + d] : P(0);
+            }
+            P acc = a.preFscale * rrow[x];
+#pragma unroll
+            for (int dl = 0; dl < W; ++dl) {
+                const P* trow = tbuf + (size_t)(warp + dl) * a.pitch;
+                P t1 = 0, t2 = 0;
+#pragma unroll
+                for (int dk = 0; dk < W; ++dk) {
+                    const int xx = x + dk - PD;
+                    const P v = (xx >= 0 && xx < N) ? trow[xx] : P(0);
+                    t1 += a1v[dk] * v;
+                    t2 += a2v[dk] * v;
+                }
+                acc += b1[dl] * t1 + b2[dl] * t2;
+            }
+            rrow[x] = acc;
+        }
+        __syncwarp();
     }
 
     const bool active = warp < rows && lane < C;
@@ -276,16 +410,7 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a_in) {
     }
     P tn[PD], bp[PD];
     interface_solve<P, PD>(ch, k < C ? k : 0, mmax, fs, fe, top, bot, nxt_top, prv_bot, tn, bp);
-    if (active) {
-        const P* Sk = fs + t * mmax * S;
-#pragma unroll 4
-        for (int o = 0; o < m; ++o) {
-            P x = g[o];
-#pragma unroll
-            for (int r = 0; r < PD; ++r) x -= Sk[o * S + r] * tn[r] + Sk[o * S + PD + r] * bp[r];
-            g[o] = x;
-        }
-    }
+    if (active) spike_fix<P, PD>(g, m, fs + t * mmax * S, tn, bp);
     if (a.tma) {
         fence_proxy_async_smem();
         __syncthreads();
@@ -304,10 +429,9 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a_in) {
 // of column c in its private shared-memory region (odd stride: distinct banks).  Loads are
 // issued in batches of 16 before use so each thread keeps 16 requests in flight.
 template <typename P, int PD>
-__global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a_in) {
+__global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
     constexpr int W = 2 * PD + 1, S = 2 * PD, B = 16;
-    if (!scene_active(a_in.b)) return;
-    const FastArgs<P> a = scene_args(a_in);
+    if (!scene_active(a.b)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nt = blockDim.x, tid = threadIdx.x;
     const Chunks ch = a.ch;
@@ -324,16 +448,17 @@ __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a_in) {
     const int t = chunk_type(ch, k);
     const int line = blockIdx.x * G + c;
     const bool valid = line < a.nlines;
-    const P* __restrict__ in = a.in[arr];
-    P* out = a.out[arr];
+    const LineView<P> v = scene_line(a, arr);
+    const P* __restrict__ in = v.in;
+    P* out = v.out;
     P* g = buf + (size_t)tid * mpad;
 
-    stage_factors(a, arr, 3 * mmax * W, 3 * mmax * S, 3 * PD * PD, fl, fs, fe);
-    const P* __restrict__ pre = a.premul[arr];
+    stage_factors(v, 3 * mmax * W, 3 * mmax * S, 3 * PD * PD, fl, fs, fe);
+    const P* __restrict__ pre = v.premul;
     for (int o0 = 0; o0 < m; o0 += B) {
         P r[B];
         if (pre) {
-            const P ps = a.prescale[arr];
+            const P ps = v.prescale;
 #pragma unroll
             for (int q = 0; q < B; ++q) {
                 const int row = s + o0 + q;
@@ -365,8 +490,8 @@ __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a_in) {
     interface_solve<P, PD>(ch, k, mmax, fs, fe, g, g + (base - PD), gn, gp, tn, bp);
     if (!valid) return;  // no barrier follows
     const P* Sk = fs + t * mmax * S;
-    const P* __restrict__ bs = a.base[arr];
-    const bool guard = (a.status != nullptr) && arr == 0;
+    const P* __restrict__ bs = v.base;
+    const bool guard = (v.status != nullptr) && arr == 0;
     bool bad = false;
     for (int o0 = 0; o0 < m; o0 += B) {
         P b[B];
@@ -385,7 +510,7 @@ __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a_in) {
             }
         }
     }
-    if (guard && bad) atomicOr(a.status, 1);
+    if (guard && bad) atomicOr(v.status, 1);
 }
 
 template <typename P, int PD, bool X>
@@ -413,16 +538,30 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
     f.tmax = (P)a.tmax;
     f.b = a.b;
     f.mpad = (ch.base > ch.last ? ch.base : ch.last) | 1;
+    f.preT = (const P*)a.preT;
+    f.preF = (const P*)a.preF;
+    f.preFscale = (P)a.preFscale;
+    f.pc1 = (P)a.pc1;
+    f.pc2 = (P)a.pc2;
+    f.pA1 = (const P*)a.pA1;
+    f.pB1 = (const P*)a.pB1;
+    f.pA2 = (const P*)a.pA2;
+    f.pB2 = (const P*)a.pB2;
+    if (!X && a.preT) return cudaErrorNotSupported;
     if (X) {
         // rows per CTA: as many warps as fit 100 KB of staged rows (at least one)
         const size_t row_bytes = (size_t)a.pitch * sizeof(P);
+        const bool pre = a.preT != nullptr;
+        if (pre && a.narr != 1) return cudaErrorNotSupported;
+        auto need = [&](int g) { return 128 + g * row_bytes + (pre ? (g + 2 * PD) * row_bytes : 0) + fbytes; };
         int G = 8;
-        while (G > 1 && 128 + G * row_bytes + fbytes > 100 * 1024) G /= 2;
-        const size_t smem = 128 + G * row_bytes + fbytes;
+        while (G > 1 && need(G) > 100 * 1024) G /= 2;
+        const size_t smem = need(G);
         if (smem > 227 * 1024) return cudaErrorNotSupported;
         bool aligned = (row_bytes % 16 == 0) && (a.b.sbytes % 16 == 0);
         for (int q = 0; q < a.narr; ++q)
-            aligned = aligned && ((uintptr_t)a.in[q] % 16 == 0) && ((uintptr_t)a.out[q] % 16 == 0);
+            aligned = aligned && ((uintptr_t)(pre ? a.preF : a.in[q]) % 16 == 0) && ((uintptr_t)a.out[q] % 16 == 0);
+        if (pre) aligned = aligned && ((uintptr_t)a.preT % 16 == 0);
         f.G = G;
         f.tma = aligned ? 1 : 0;
         auto kern = k_xsolve_warp<P, PD>;

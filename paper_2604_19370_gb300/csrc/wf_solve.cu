@@ -356,6 +356,7 @@ cudaError_t launch_xsolve(int prec, int p, const LineArgs& a, cudaStream_t s) {
     cudaError_t e = launch_line_fast(prec, p, true, a, s);
     if (e != cudaErrorNotSupported) return e;
     cudaGetLastError();
+    if (a.preT) return cudaErrorNotSupported;  // fused input only in the compact-factor kernel
     return dispatch_line<true>(prec, p, a, s);
 }
 cudaError_t launch_ysolve(int prec, int p, const LineArgs& a, cudaStream_t s) {
