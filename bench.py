@@ -76,6 +76,29 @@ def algorithmic_costs(p: int, fused_x2: bool = True) -> dict:
     }
 
 
+def min_step_bytes(scheme_strang: bool) -> int:
+    """Least HBM bytes per DOF of one step (FP32): fields read and written once per pass.
+
+    PR: x1 reads T, phi and writes its two results and F (20); y1 reads and writes two
+    fields (16); x2 reads T*, F and writes its result (12); y2 reads and writes one (8).
+    Strang-CN: 16 + 16 (substep 1) + 8 (y substep) + 12 + 8 (substep 3).
+    """
+    return 60 if scheme_strang else 56
+
+
+def shape_source(args) -> str:
+    return "given" if args.tuning else ("rule" if args.no_autotune else "autotuned")
+
+
+def pick_shapes(wf, h, args, reps: int):
+    """Launch shapes: given on the command line, the launchers' rules, or autotuned on the handle."""
+    if args.tuning:
+        wf.wf_set_tuning(h, [int(v) for v in args.tuning.split(",")])
+    elif not args.no_autotune:
+        wf.wf_autotune(h, reps)
+    return wf.wf_get_tuning(h)
+
+
 def _source_sha(name: str) -> str:
     with open(os.path.join(ROOT, "paper_2604_19370_gb300", "csrc", name), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
@@ -282,6 +305,8 @@ def run_gpu(args) -> None:
     sim = wf.simulation_from_scenario(sc, precision=prec, scheme=scheme)
     stream = torch.cuda.Stream(device=dev)
     wf.wf_set_stream(sim.h, stream.cuda_stream)
+    # launch shapes tuned on this handle (its state is restored afterwards)
+    tuning = pick_shapes(wf, sim.h, args, 3)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     props = torch.cuda.get_device_properties(dev)
 
@@ -399,9 +424,14 @@ def run_gpu(args) -> None:
                    "scheme": "Strang-CN" if args.strang else "PR",
                    "precision": "fp64" if args.fp64 else "fp32 bulk, fp64 1-D factorisation",
                    "l2": "flushed before every timed step (256 MiB write)",
+                   "launch_shapes": {"x_lines_per_cta": tuning[0], "y_lines_per_cta": tuning[1],
+                                     "quadrature_segment_rows": tuning[2], "x_lines_per_warp": tuning[3],
+                                     "source": shape_source(args)},
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
-        "step_hbm_frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / peaks["hbm_gbs"],
+        "step_hbm_frac": min_step_bytes(args.strang) * (es / 4) * sc.dofs / (ms_per_step * 1e-3) / 1e9
+        / peaks["hbm_gbs"],
+        "step_hbm_frac_kernel_bytes": step_bytes / (ms_per_step * 1e-3) / 1e9 / peaks["hbm_gbs"],
         "profiled_ms_per_step": prof_ms_per_step,
         "kernels": kernels,
         "gpu_launches": launches,
@@ -473,6 +503,7 @@ def run_ensemble(args) -> None:
         b.load_scenario(k, sc)
     stream = torch.cuda.Stream(device=dev)
     wf.wf_set_stream(b.h, stream.cuda_stream)
+    tuning = pick_shapes(wf, b.h, args, 2)
     dofs = S * first.dofs
     with torch.cuda.stream(stream):
         b.step(args.warmup)
@@ -534,9 +565,13 @@ def run_ensemble(args) -> None:
         "warmup": args.warmup, "ms_per_step": slowest * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"c4_ensemble_{S}x256x256_p2_pr", "scenarios": S, "nx": 256, "ny": 256, "p": 2,
-                   "dofs": dofs, "l2": f"state {S} x 5 fields > L2, no flush", "parallelism": f"replicas x{world}"},
+                   "dofs": dofs, "l2": f"state {S} x 5 fields > L2, no flush", "parallelism": f"replicas x{world}",
+                   "launch_shapes": {"x_lines_per_cta": tuning[0], "y_lines_per_cta": tuning[1],
+                                     "quadrature_segment_rows": tuning[2], "x_lines_per_warp": tuning[3],
+                                     "source": shape_source(args)}},
         "roofline": roof,
-        "step_hbm_frac": step_bytes / (slowest / args.steps) / 1e9 / peaks["hbm_gbs"],
+        "step_hbm_frac": min_step_bytes(False) * dofs / (slowest / args.steps) / 1e9 / peaks["hbm_gbs"],
+        "step_hbm_frac_kernel_bytes": step_bytes / (slowest / args.steps) / 1e9 / peaks["hbm_gbs"],
         "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in kt.items() if v[1] > 0},
         "gpu_launches": int(sum(v[1] for v in kt.values())),
         "e2e": {"value": world * dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * dofs,
@@ -646,6 +681,8 @@ def main():
     ap.add_argument("--strang", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="launch shapes from the launchers' rules")
+    ap.add_argument("--tuning", default="", help="launch shapes x_cta,y_cta,seg,x_per_warp (skips the autotuner)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
                     help="c2: one 1024^2 domain (default); c4: batched ensemble; c5: served request stream")
     ap.add_argument("--scenarios", type=int, default=256)

@@ -158,6 +158,34 @@ int wf_set_profiling(wf_handle* h, int on);
 int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], int max_k);
 
 /*
+ * Launch-shape autotuner (no counterpart in the paper, whose solver runs on
+ * CPU threads).  Four shapes are tuned (int shape[4]):
+ *   shape[0]  lines per CTA of the x pass (rows staged per CTA; at most
+ *             8 warps' worth),
+ *   shape[1]  lines per CTA of the y pass (columns per CTA, bounded by
+ *             lines x chunks <= 256 threads),
+ *   shape[2]  element rows per segment of the streaming quadrature kernel,
+ *   shape[3]  lines per warp of the x pass (1, 2 or 4; at most 32 / chunks
+ *             per line, which is also the default);
+ * 0 selects the launchers' built-in rule.  wf_autotune times reps steps
+ * (after one warm-up step) of the handle's active slots for each candidate,
+ * keeps for every shape the value whose launches took least device time,
+ * and restores every slot's device state afterwards, so the trajectory is
+ * unchanged.  It needs a temporary device copy of the slot blocks
+ * (S x the per-slot bytes, freed before return; WF_ENOMEM if it cannot be
+ * had), synchronises the handle's stream, drops the captured graphs (they
+ * are captured again by the next wf_step) and discards kernel times
+ * collected under wf_set_profiling.  No active slot: WF_OK, nothing tuned.
+ * Shapes never change the arithmetic of a line or an element.
+ * Errors: WF_EINVAL (reps outside 1..100), WF_ENOMEM, WF_ECUDA.
+ * wf_get_tuning / wf_set_tuning read and write the four values
+ * (wf_set_tuning: each 0..1024, else WF_EINVAL).
+ */
+int wf_autotune(wf_handle* h, int reps);
+int wf_get_tuning(const wf_handle* h, int* shape);
+int wf_set_tuning(wf_handle* h, const int* shape);
+
+/*
  * ---- batches of scenarios ------------------------------------------------
  * A batch handle holds `capacity` independent scenarios (slots) of one grid
  * (nx, ny, p, dt and model parameters shared).  Each slot has its own state,

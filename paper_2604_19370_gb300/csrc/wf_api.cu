@@ -30,6 +30,7 @@ using namespace wf;
 namespace {
 
 constexpr double kTmax = 1e5;  // guard on |T| (K)
+constexpr int kTune = 4;       // tuned launch shapes (wf_autotune)
 
 struct Arena {
     char* base = nullptr;
@@ -58,6 +59,7 @@ struct Dir {
     int n = 0, N = 0;
     double L = 0, h = 0;
     Chunks ch{};
+    ElemTabs itab{};  // host copy of the interior element's tables
     // shared by all slots
     double *B64 = nullptr, *D64 = nullptr;
     void *BP = nullptr, *DP = nullptr, *wP = nullptr;
@@ -100,6 +102,9 @@ struct wf_handle {
     // slot blocks: slot-0 pointers, block stride
     int S = 1;
     long long sbytes = 0;
+    char* slots_mem = nullptr;  // start of slot 0's block
+    int tune[4] = {0, 0, 0, 0};  // x lines per CTA, y lines per CTA, quadrature segment rows,
+                                 // x lines per warp (0: the launchers' rules)
     void *T = nullptr, *phi = nullptr, *F = nullptr, *Phi = nullptr, *R = nullptr;
     int* status = nullptr;
     void *fxq = nullptr, *gxq = nullptr, *fyq = nullptr, *gyq = nullptr;
@@ -320,6 +325,24 @@ int build_tables(wf_handle* h) {
             WF_TRY(cudaMemcpyAsync(d->wP, w64, sizeof(double) * h->q, cudaMemcpyHostToDevice, s));
         }
         WF_TRY(cudaStreamSynchronize(s));  // the host weight arrays go out of scope
+        // interior element p (uniform knots): its tables, read back once
+        ElemTabs& it = d->itab;
+        memset(&it, 0, sizeof(it));
+        for (int a = 0; a < h->q; ++a) it.w[a] = w[a] * d->h;
+        it.ok = d->n > 2 * h->p;
+        if (it.ok) {
+            const int Q = h->q, NB = h->p + 1;
+            double tb[16], td[16];
+            const size_t off = (size_t)h->p * Q * NB;
+            WF_TRY(cudaMemcpyAsync(tb, d->B64 + off, sizeof(double) * Q * NB, cudaMemcpyDeviceToHost, s));
+            WF_TRY(cudaMemcpyAsync(td, d->D64 + off, sizeof(double) * Q * NB, cudaMemcpyDeviceToHost, s));
+            WF_TRY(cudaStreamSynchronize(s));
+            for (int a = 0; a < Q; ++a)
+                for (int k = 0; k < NB; ++k) {
+                    it.B[a][k] = tb[a * NB + k];
+                    it.D[a][k] = td[a * NB + k];
+                }
+        }
     }
     return WF_OK;
 }
@@ -451,6 +474,9 @@ RhsArgs rhs_args(wf_handle* h, const void* T, void* F, void* Phi, void* R, doubl
     a.c1 = c1;
     a.c2 = c2;
     a.tau = h->dt;
+    a.seg = h->tune[2];
+    a.tx = h->dx.itab;
+    a.ty = h->dy.itab;
     a.phys = h->phys;
     a.b = batch(h);
     return a;
@@ -460,6 +486,8 @@ LineArgs line_args(wf_handle* h, bool xdir) {
     LineArgs a;
     memset(&a, 0, sizeof(a));
     a.nlines = xdir ? h->Ny : h->Nx;
+    a.G = xdir ? h->tune[0] : h->tune[1];
+    a.rpw = xdir ? h->tune[3] : 0;
     a.pitch = h->pitch;
     a.tmax = kTmax;
     a.b = batch(h);
@@ -822,6 +850,7 @@ int wf_batch_create(int nx, int ny, int p, double dt, const wf_params* params, i
         layout_shared(h, A2);
         Arena B2;
         B2.base = reinterpret_cast<char*>(h->mem) + shared;
+        h->slots_mem = B2.base;
         layout_slot(h, B2);
         // every slot block starts zeroed (fields, guard flags, unused wind ranks)
         if (cudaMemsetAsync(B2.base, 0, (size_t)h->sbytes * capacity, h->stream) != cudaSuccess) {
@@ -1017,6 +1046,91 @@ int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], in
         h->site_cnt[k] = 0;
     }
     return S_NSITES;
+}
+
+// ---- autotuner ---------------------------------------------------------------------
+//
+// Launch shapes (x lines per CTA, y lines per CTA, rows per quadrature segment) are chosen
+// per handle by timing whole steps of the handle itself: the slot blocks are saved, every
+// candidate runs warm-up + `reps` eager steps with a CUDA event pair around each launch,
+// each parameter takes the value whose launches took least time, and the blocks are
+// restored, so the state after wf_autotune equals the state before it.  Candidate 0 is the
+// launchers' own rule.
+
+int wf_autotune(wf_handle* h, int reps) {
+    if (!h || reps < 1 || reps > 100) return WF_EINVAL;
+    bool any = false;
+    for (int z = 0; z < h->S; ++z) any = any || h->active_host[z];
+    if (!any) return WF_OK;
+    // each row is one candidate run; -1 keeps a shape at its best value so far.  The x lines
+    // per warp are tuned after the x lines per CTA they depend on.
+    constexpr int kRuns = 10;
+    static const int kCands[kRuns][kTune] = {
+        {0, 0, 0, 0},      {32, 32, 128, -1}, {16, 16, 64, -1}, {8, 8, 32, -1}, {4, 4, 16, -1},
+        {2, 2, -1, -1},    {1, 1, -1, -1},    {-1, -1, -1, 1},  {-1, -1, -1, 2}, {-1, -1, -1, 4}};
+    const size_t bytes = (size_t)h->sbytes * h->S;
+    void* snap = nullptr;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;
+    if (cudaMalloc(&snap, bytes) != cudaSuccess) return WF_ENOMEM;
+    int rc = WF_OK;
+    const bool was_profiling = h->profiling;
+    int saved[kTune], best_v[kTune];
+    double best_t[kTune];
+    for (int q = 0; q < kTune; ++q) {
+        saved[q] = best_v[q] = h->tune[q];
+        best_t[q] = 1e300;
+    }
+    if (cudaMemcpyAsync(snap, h->slots_mem, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+        rc = WF_ECUDA;
+    drop_graphs(h);
+    h->profiling = true;
+    double ms[S_NSITES];
+    int cnt[S_NSITES];
+    for (int c = 0; c < kRuns && rc == WF_OK; ++c) {
+        bool fresh[kTune];
+        for (int q = 0; q < kTune; ++q) {
+            fresh[q] = kCands[c][q] >= 0;
+            h->tune[q] = fresh[q] ? kCands[c][q] : best_v[q];
+        }
+        for (int k = 0; k <= reps && rc == WF_OK; ++k) {
+            if (k == 1) wf_kernel_times(h, nullptr, nullptr, nullptr, 0);  // drop the warm-up step
+            if (enqueue_step(h) != cudaSuccess) rc = WF_ECUDA;
+        }
+        if (rc != WF_OK || wf_kernel_times(h, ms, cnt, nullptr, S_NSITES) < 0) {
+            rc = WF_ECUDA;
+            break;
+        }
+        const double tx = ms[S_X1] + ms[S_X2];
+        const double t[kTune] = {tx, ms[S_Y1] + ms[S_Y2PRE] + ms[S_Y3], ms[S_RHS1] + ms[S_RHS2], tx};
+        for (int q = 0; q < kTune; ++q)
+            if (fresh[q] && t[q] < best_t[q]) {
+                best_t[q] = t[q];
+                best_v[q] = h->tune[q];
+            }
+        if (cudaMemcpyAsync(h->slots_mem, snap, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+            rc = WF_ECUDA;
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = WF_ECUDA;
+    cudaFree(snap);
+    h->profiling = was_profiling;
+    for (int q = 0; q < kTune; ++q) h->tune[q] = rc == WF_OK ? best_v[q] : saved[q];
+    drop_graphs(h);
+    return rc;
+}
+
+int wf_get_tuning(const wf_handle* h, int* shape) {
+    if (!h || !shape) return WF_EINVAL;
+    for (int q = 0; q < kTune; ++q) shape[q] = h->tune[q];
+    return WF_OK;
+}
+
+int wf_set_tuning(wf_handle* h, const int* shape) {
+    if (!h || !shape) return WF_EINVAL;
+    for (int q = 0; q < kTune; ++q)
+        if (shape[q] < 0 || shape[q] > 1024) return WF_EINVAL;
+    for (int q = 0; q < kTune; ++q) h->tune[q] = shape[q];
+    drop_graphs(h);
+    return WF_OK;
 }
 
 }  // extern "C"

@@ -109,6 +109,14 @@ cudaError_t launch_fill(int prec, void* dst, size_t n, double v, cudaStream_t s)
 cudaError_t launch_gather_status(int* status0, long long sbytes, int S, int* out, int clear, cudaStream_t s);
 
 // ---- quadrature right-hand side (wf_rhs.cu) ---------------------------------------
+// Tables of an interior element along one direction (uniform open knots: every element
+// p <= e < n - p has the same ones, bitwise, as the device tables), and the Gauss weights.
+struct ElemTabs {
+    int ok;                   // n > 2p (interior elements exist)
+    double B[4][4], D[4][4];  // [Gauss point][local basis], as in the device tables
+    double w[4];              // Gauss weight x element length
+};
+
 struct RhsArgs {
     int nx, ny, Nx, Ny, pitch;
     const void* T;
@@ -122,6 +130,8 @@ struct RhsArgs {
     const void *A1, *B1, *A2, *B2;      // bands along x (A) and y (B) for R; A2 may be NULL
     double Rscale, c1, c2;
     double tau;  // full time step (fuel update)
+    int seg;     // element rows per segment of the streaming kernel (0: the launcher's rule)
+    ElemTabs tx, ty;
     Phys phys;
     Batch b;  // per scenario: T, phi, F, Phi, R, A1, B1, A2, B2, fxq, gxq, fyq, gyq
 };
@@ -134,6 +144,8 @@ int rhs_items_per_dof(int p);  // informational
 
 // ---- line solves and matvec (wf_solve.cu) -------------------------------------------
 struct LineArgs {
+    int G;       // lines per CTA of the compact-factor kernels (0: the launcher's rule; else an upper bound)
+    int rpw;     // x pass: lines per warp (0: as many as the chunks allow; 1, 2: at most that many)
     int nlines;  // number of independent lines
     int pitch;   // row pitch of the fields (elements)
     int narr;    // 1 or 2 arrays (blockIdx.y)

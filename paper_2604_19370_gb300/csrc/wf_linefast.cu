@@ -25,6 +25,7 @@ namespace {
 template <typename P>
 struct FastArgs {
     int nlines, pitch, mpad, G;
+    int lsh;  // x pass: log2 of the lanes per line (5: one line per warp; 4: two; 3: four)
     Chunks ch;
     const P* in[2];
     P* out[2];
@@ -283,7 +284,8 @@ __device__ __forceinline__ void stage_factors(const LineView<P>& v, int n_lu, in
     for (int i = tid; i < n_e; i += nt) fe[i] = g3[i];
 }
 
-// x pass.  CTA = G warps; warp w solves row blockIdx.x*G + w, lane k owns chunk k (C <= 32).
+// x pass.  CTA = G lines; a warp solves 32 / lanes lines, lane k of a line's group owns chunk k
+// (C <= lanes per line).
 // The G rows are contiguous in memory: one bulk copy stages them, one bulk store writes them back.
 // Chunk lengths are odd, so the 32 lanes of a warp read 32 distinct shared-memory banks.
 template <typename P, int PD>
@@ -339,6 +341,14 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
                     tbuf[(size_t)(r - (j0 - PD)) * a.pitch + x] = v.preT[(size_t)r * a.pitch + x];
     }
     stage_factors(v, 3 * mmax * W, 3 * mmax * S, 3 * PD * PD, fl, fs, fe);
+    if (pre) {
+        P* bco = fe + 3 * PD * PD;
+        for (int i = tid; i < rows * W; i += blockDim.x) {
+            const int r = i / W, d = i - r * W;
+            bco[(size_t)r * 2 * W + d] = a.pc1 * v.pB1[(size_t)(j0 + r) * W + d];
+            bco[(size_t)r * 2 * W + W + d] = v.pA2 ? a.pc2 * v.pB2[(size_t)(j0 + r) * W + d] : P(0);
+        }
+    }
     __syncthreads();  // mbarrier initialised, factors staged, halo zeroed
     if (a.tma) {
         uint32_t it = 0;
@@ -354,46 +364,56 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
         if (tid == 0 && v.status) atomicOr(v.status, 4);
         return;
     }
-    if (pre && warp < rows) {
-        // R = preFscale F + pc1 (pA1 (x) pB1) T + pc2 (pA2 (x) pB2) T for this warp's row
-        const int j = j0 + warp;
-        P b1[W], b2[W];
-#pragma unroll
-        for (int d = 0; d < W; ++d) {
-            b1[d] = a.pc1 * v.pB1[(size_t)j * W + d];
-            b2[d] = v.pA2 ? a.pc2 * v.pB2[(size_t)j * W + d] : P(0);
-        }
-        P* rrow = rowbuf + (size_t)warp * a.pitch;
-        for (int x = lane; x < N; x += 32) {
-            P a1v[W], a2v[W];
+    if (pre) {
+        // R = preFscale F + (pA1 (x) pc1 pB1) T + (pA2 (x) pc2 pB2) T, one column per thread:
+        // the x bands of column x are loaded once and applied to the G + 2p staged rows, whose
+        // results pass through a W-row register window that the y bands reduce.
+        const P* __restrict__ bco = fe + 3 * PD * PD;  // [G][2][W], scaled by pc1 / pc2
+        for (int x = tid; x < N; x += blockDim.x) {
+            P a1v[W], a2v[W], w1[W], w2[W];
 #pragma unroll
             for (int d = 0; d < W; ++d) {
                 a1v[d] = v.pA1[(size_t)x * W + d];
                 a2v[d] = v.pA2 ? v.pA2[(size_t)x * W + d] : P(0);
+                w1[d] = P(0);
+                w2[d] = P(0);
             }
-            P acc = a.preFscale * rrow[x];
-#pragma unroll
-            for (int dl = 0; dl < W; ++dl) {
-                const P* trow = tbuf + (size_t)(warp + dl) * a.pitch;
+            for (int r = 0; r < rows + 2 * PD; ++r) {
+                const P* trow = tbuf + (size_t)r * a.pitch;
                 P t1 = 0, t2 = 0;
 #pragma unroll
                 for (int dk = 0; dk < W; ++dk) {
                     const int xx = x + dk - PD;
-                    const P v = (xx >= 0 && xx < N) ? trow[xx] : P(0);
-                    t1 += a1v[dk] * v;
-                    t2 += a2v[dk] * v;
+                    const P val = (xx >= 0 && xx < N) ? trow[xx] : P(0);
+                    t1 += a1v[dk] * val;
+                    t2 += a2v[dk] * val;
                 }
-                acc += b1[dl] * t1 + b2[dl] * t2;
+#pragma unroll
+                for (int d = 0; d + 1 < W; ++d) {
+                    w1[d] = w1[d + 1];
+                    w2[d] = w2[d + 1];
+                }
+                w1[W - 1] = t1;
+                w2[W - 1] = t2;
+                if (r >= 2 * PD) {
+                    const int jl = r - 2 * PD;
+                    const P* bj = bco + (size_t)jl * 2 * W;
+                    P acc = a.preFscale * rowbuf[(size_t)jl * a.pitch + x];
+#pragma unroll
+                    for (int dl = 0; dl < W; ++dl) acc += bj[dl] * w1[dl] + bj[W + dl] * w2[dl];
+                    rowbuf[(size_t)jl * a.pitch + x] = acc;
+                }
             }
-            rrow[x] = acc;
         }
-        __syncwarp();
+        __syncthreads();
     }
 
-    const bool active = warp < rows && lane < C;
-    const int k = lane;
+    // lanes per line: 32 >> (5 - lsh); line r of the CTA = warp * lines-per-warp + lane / lanes
+    const int k = lane & ((1 << a.lsh) - 1);
+    const int r = (warp << (5 - a.lsh)) + (lane >> a.lsh);
+    const bool active = r < rows && k < C;
     const int m = (k < C - 1) ? base : ch.last;
-    P* g = rowbuf + (size_t)warp * a.pitch + (size_t)k * base;
+    P* g = rowbuf + (size_t)(r < rows ? r : 0) * a.pitch + (size_t)k * base;
     const int t = chunk_type(ch, k < C ? k : 0);
     if (active) lu_chunk<P, PD>(g, m, fl + t * mmax * W);
     __syncwarp();
@@ -553,9 +573,19 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         const size_t row_bytes = (size_t)a.pitch * sizeof(P);
         const bool pre = a.preT != nullptr;
         if (pre && a.narr != 1) return cudaErrorNotSupported;
-        auto need = [&](int g) { return 128 + g * row_bytes + (pre ? (g + 2 * PD) * row_bytes : 0) + fbytes; };
-        int G = 8;
-        while (G > 1 && need(G) > 100 * 1024) G /= 2;
+        auto need = [&](int g) {
+            return 128 + g * row_bytes + (pre ? (g + 2 * PD) * row_bytes + (size_t)g * 2 * W * sizeof(P) : 0) + fbytes;
+        };
+        // lines per warp: as many as the chunks allow (C <= 8: four, C <= 16: two), or fewer
+        int lsh = ch.C <= 8 ? 3 : (ch.C <= 16 ? 4 : 5);
+        if (a.rpw == 1) lsh = 5;
+        else if (a.rpw == 2 && lsh < 4) lsh = 4;
+        const int lpw = 1 << (5 - lsh);
+        // lines per CTA: up to 8 warps' worth, fewer when the staged rows need more than 100 KB
+        int G = 8 * lpw;
+        if (a.G > 0 && a.G < G) G = a.G < lpw ? lpw : a.G;
+        G = (G + lpw - 1) / lpw * lpw;
+        while (G > lpw && need(G) > 100 * 1024) G = ((G / 2) + lpw - 1) / lpw * lpw;
         const size_t smem = need(G);
         if (smem > 227 * 1024) return cudaErrorNotSupported;
         bool aligned = (row_bytes % 16 == 0) && (a.b.sbytes % 16 == 0);
@@ -563,14 +593,15 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
             aligned = aligned && ((uintptr_t)(pre ? a.preF : a.in[q]) % 16 == 0) && ((uintptr_t)a.out[q] % 16 == 0);
         if (pre) aligned = aligned && ((uintptr_t)a.preT % 16 == 0);
         f.G = G;
+        f.lsh = lsh;
         f.tma = aligned ? 1 : 0;
         auto kern = k_xsolve_warp<P, PD>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         dim3 grid((a.nlines + G - 1) / G, a.narr, a.b.S);
-        kern<<<grid, 32 * G, smem, s>>>(f);
+        kern<<<grid, 32 * (G / lpw), smem, s>>>(f);
     } else {
-        int G = sizeof(P) == 4 ? 8 : 4;
+        int G = a.G > 0 ? (a.G < 256 ? a.G : 256) : (sizeof(P) == 4 ? 8 : 4);
         while (G > 1 && G * ch.C > 256) G /= 2;
         const int nt = G * ch.C;
         if (nt > 256) return cudaErrorNotSupported;

@@ -15,12 +15,20 @@
 //   * neighbouring element columns are reached with warp shuffles, so nothing
 //     goes through shared memory;
 //   * a DOF row is finished (x-test contraction, matvec, stores) as soon as the
-//     last element row touching it has been processed.
+//     last element row touching it has been processed;
+//   * with uniform knots every element p <= e < n - p has the same B, B' tables, so
+//     strips and element rows away from the boundary take them from the kernel's
+//     parameter block (constant operands of the FMAs, no registers); boundary strips
+//     read their own tables through L1;
+//   * warps take (strip, segment) work items in a flat order, so none idles when the
+//     strips of a row do not fill a CTA.
 //
 // Lanes 0..p-1 only feed their neighbours, so a strip produces 32 - p DOF
 // columns; a segment recomputes p element rows above it.  Both overheads are
 // below 7 % for p = 2.
 #include <math.h>
+
+#include <type_traits>
 
 #include "wf_internal.h"
 
@@ -41,21 +49,32 @@ __device__ __forceinline__ float expo_s<float>(float x) { return __expf(x); }
 template <>
 __device__ __forceinline__ double expo_s<double>(double x) { return exp(x); }
 
+// Tables of an interior element (uniform knots: every element p <= e < n - p has the same
+// ones), carried in the kernel parameters so that the FMAs read them as constant operands.
+template <typename P>
+struct ITab {
+    P bx[4][4], dx[4][4];  // x: [Gauss point][local basis]
+    P by[4][4], dy[4][4];  // y: [Gauss point][local basis]
+    P wx[4], wy[4];        // Gauss weights x element length (every element)
+    int xok, yok;          // the interior tables exist (n > 2p)
+};
+
 template <typename P>
 struct StreamArgs {
-    int nx, ny, Nx, Ny, pitch, seg, nstrips;
+    int nx, ny, Nx, Ny, pitch, seg, nstrips, nsegs;
     const P* __restrict__ T;
     const P* __restrict__ phi;
     P* F;
     P* Phi;
     P* R;
-    const P *Bx, *Dx, *By, *Dy, *wx, *wy;
+    const P *Bx, *Dx, *By, *Dy;
     int wind_rank;
     const P *fxq, *gxq, *fyq, *gyq;
     const P *A1, *B1, *A2, *B2;
     P Rscale, c1, c2;
     PhysS<P> c;
     Batch b;
+    ITab<P> it;
 };
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -68,47 +87,36 @@ __device__ __forceinline__ P col_from(P own, P extra, int lane, int k) {
     return (lane + k < 32) ? down : wrap;
 }
 
-template <typename P, int PD, int WR>
-__global__ void __launch_bounds__(128) k_rhs_stream(const StreamArgs<P> a_in) {
+// -T_a / T: the FP32 path uses the fast divide (about 2 ulp), the FP64 path the exact one
+template <typename P>
+__device__ __forceinline__ P neg_ratio(P a, P t);
+template <>
+__device__ __forceinline__ float neg_ratio<float>(float a, float t) { return -__fdividef(a, t); }
+template <>
+__device__ __forceinline__ double neg_ratio<double>(double a, double t) { return -a / t; }
+
+// One warp: strip of 32 element columns starting at X0 - p, element rows Y0 - p .. Y1 - 1.
+// XI: every element of the strip (and every element feeding its output columns) is interior,
+// so the x tables come from the parameter block.
+template <typename P, int PD, int WR, bool XI>
+__device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<P>& it, int lane, int X0, int Y0,
+                                             int Y1) {
     constexpr int Q = PD + 1, NB = PD + 1, W = 2 * PD + 1, NC = 2 * PD + 1;
-    if (!scene_active(a_in.b)) return;
-    StreamArgs<P> a = a_in;
-    a.T = scene_ptr(a.T, a.b);
-    a.phi = scene_ptr(a.phi, a.b);
-    a.F = scene_ptr(a.F, a.b);
-    a.Phi = scene_ptr(a.Phi, a.b);
-    a.R = scene_ptr(a.R, a.b);
-    a.A1 = scene_ptr(a.A1, a.b);
-    a.B1 = scene_ptr(a.B1, a.b);
-    a.A2 = scene_ptr(a.A2, a.b);
-    a.B2 = scene_ptr(a.B2, a.b);
-    a.fxq = scene_ptr(a.fxq, a.b);
-    a.gxq = scene_ptr(a.gxq, a.b);
-    a.fyq = scene_ptr(a.fyq, a.b);
-    a.gyq = scene_ptr(a.gyq, a.b);
-    const int lane = threadIdx.x & 31;
-    const int strip = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (strip >= a.nstrips) return;  // whole warp leaves; no block barrier in this kernel
-    const int X0 = strip * (32 - PD);
     const int ex = X0 - PD + lane;             // element column of this lane; also its DOF column
-    const bool ex_ok = ex >= 0 && ex < a.nx;
+    const bool ex_ok = XI || (ex >= 0 && ex < a.nx);
     const bool out_col = lane >= PD && ex < a.Nx;
     const int cc = ex;                         // coefficient column held by this lane
     const int cc2 = X0 - PD + 32 + lane;       // extra coefficient column (lanes < 2p are used)
-    const bool cc_ok = cc >= 0 && cc < a.Nx;
-    const bool cc2_ok = cc2 >= 0 && cc2 < a.Nx;
-    const int Y0 = blockIdx.y * a.seg;
-    const int Y1 = min(Y0 + a.seg, a.Ny);
+    const bool cc_ok = XI || (cc >= 0 && cc < a.Nx);
+    const bool cc2_ok = XI || (cc2 >= 0 && cc2 < a.Nx);
 
-    // per-lane constants: x tables of the element, x bands of the DOF column, wind x-factors
-    P bx[Q][NB], dx[Q][NB];
-#pragma unroll
-    for (int q = 0; q < Q; ++q)
-#pragma unroll
-        for (int k = 0; k < NB; ++k) {
-            bx[q][k] = ex_ok ? a.Bx[(size_t)(ex * Q + q) * NB + k] : P(0);
-            dx[q][k] = ex_ok ? a.Dx[(size_t)(ex * Q + q) * NB + k] : P(0);
-        }
+    // x tables: interior strips read the parameter block; boundary strips read the element's
+    // table through L1 at each use (they are a small share of the work; holding them in
+    // registers would raise the register count of every strip)
+    const P* __restrict__ Bxe = a.Bx + (size_t)(ex_ok ? ex : 0) * Q * NB;
+    const P* __restrict__ Dxe = a.Dx + (size_t)(ex_ok ? ex : 0) * Q * NB;
+#define WF_BX(q, k) (XI ? it.bx[q][k] : (ex_ok ? __ldg(Bxe + (q) * NB + (k)) : P(0)))
+#define WF_DX(q, k) (XI ? it.dx[q][k] : (ex_ok ? __ldg(Dxe + (q) * NB + (k)) : P(0)))
     P a1[W], a2[W];
 #pragma unroll
     for (int d = 0; d < W; ++d) {
@@ -123,31 +131,13 @@ __global__ void __launch_bounds__(128) k_rhs_stream(const StreamArgs<P> a_in) {
             fxr[r][q] = ex_ok ? a.fxq[(size_t)r * a.nx * Q + ex * Q + q] : P(0);
             fyr[r][q] = ex_ok ? a.fyq[(size_t)r * a.nx * Q + ex * Q + q] : P(0);
         }
-    P wxq[Q], wyq[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        wxq[q] = a.wx[q];
-        wyq[q] = a.wy[q];
-    }
     // x-test tables of the elements left of this lane: element ex - k, local basis k
-    P tbx[NB][Q], tdx[NB][Q];
-#pragma unroll
-    for (int k = 0; k < NB; ++k)
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            tbx[k][q] = (k == 0) ? bx[q][0] : __shfl_up_sync(FULL, bx[q][k], k);
-            tdx[k][q] = (k == 0) ? dx[q][0] : __shfl_up_sync(FULL, dx[q][k], k);
-        }
-    // y tables: every interior element row (p <= ey < ny - p) has the same ones
-    const int eyi = a.ny > 2 * PD ? PD : 0;
-    P byi[Q][NB], dyi[Q][NB];
-#pragma unroll
-    for (int b = 0; b < Q; ++b)
-#pragma unroll
-        for (int l = 0; l < NB; ++l) {
-            byi[b][l] = a.By[(size_t)(eyi * Q + b) * NB + l];
-            dyi[b][l] = a.Dy[(size_t)(eyi * Q + b) * NB + l];
-        }
+    auto tab_left = [&](const P* tab, int k, int q) {
+        const int e = ex - k;
+        return (e >= 0 && e < a.nx) ? __ldg(tab + ((size_t)e * Q + q) * NB + k) : P(0);
+    };
+#define WF_TBX(k, q) (XI ? it.bx[q][k] : tab_left(a.Bx, k, q))
+#define WF_TDX(k, q) (XI ? it.dx[q][k] : tab_left(a.Dx, k, q))
 
     // sliding windows
     P xv[NB][Q], xd[NB][Q], xp[NB][Q];  // x-interpolation of coefficient rows ey .. ey+p
@@ -189,9 +179,9 @@ __global__ void __launch_bounds__(128) k_rhs_stream(const StreamArgs<P> a_in) {
             P s = 0, sd = 0, sp = 0;
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
-                s += bx[q][k] * ct[k];
-                sd += dx[q][k] * ct[k];
-                sp += bx[q][k] * cf[k];
+                s += WF_BX(q, k) * ct[k];
+                sd += WF_DX(q, k) * ct[k];
+                sp += WF_BX(q, k) * cf[k];
             }
             v[q] = s;
             dv[q] = sd;
@@ -206,6 +196,70 @@ __global__ void __launch_bounds__(128) k_rhs_stream(const StreamArgs<P> a_in) {
         }
         w1 = s1;
         w2 = s2;
+    };
+
+    // one element row: Q x Q points, y-test accumulation into DOF rows ey .. ey+p.
+    // YI: the row is interior and its y tables come from the parameter block.
+    auto element_row = [&](auto yi, int ey) {
+        constexpr bool YI = decltype(yi)::value;
+        P byr[Q][NB], dyr[Q][NB];
+#pragma unroll
+        for (int b = 0; b < Q; ++b)
+#pragma unroll
+            for (int l = 0; l < NB; ++l) {
+                byr[b][l] = YI ? P(0) : a.By[(size_t)(ey * Q + b) * NB + l];
+                dyr[b][l] = YI ? P(0) : a.Dy[(size_t)(ey * Q + b) * NB + l];
+            }
+#define WF_BY(b, l) (YI ? it.by[b][l] : byr[b][l])
+#define WF_DY(b, l) (YI ? it.dy[b][l] : dyr[b][l])
+        P gyr[WR > 0 ? WR : 1][Q], gxr[WR > 0 ? WR : 1][Q];
+#pragma unroll
+        for (int r = 0; r < WR; ++r)
+#pragma unroll
+            for (int b = 0; b < Q; ++b) {
+                gxr[r][b] = a.gxq[(size_t)r * a.ny * Q + ey * Q + b];
+                gyr[r][b] = a.gyq[(size_t)r * a.ny * Q + ey * Q + b];
+            }
+        if (!ex_ok) return;
+        const PhysS<P>& c = a.c;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                P T = 0, Ty = 0, Tx = 0, ph = 0;
+#pragma unroll
+                for (int l = 0; l < NB; ++l) {
+                    T += WF_BY(b, l) * xv[l][q];
+                    Ty += WF_DY(b, l) * xv[l][q];
+                    Tx += WF_BY(b, l) * xd[l][q];
+                    ph += WF_BY(b, l) * xp[l][q];
+                }
+                P bpx = 0, bpy = 0;
+#pragma unroll
+                for (int r = 0; r < WR; ++r) {
+                    bpx += fxr[r][q] * gxr[r][b];
+                    bpy += fyr[r][q] * gyr[r][b];
+                }
+                const bool burn = (T > c.T_ig) && (ph > c.phi_min);
+                const P E = burn ? T * expo_s<P>(neg_ratio<P>(c.T_a, T)) : P(0);
+                const P T2 = T * T;
+                const P rad = c.c_rad * (c.T_amb2 + T2) * (c.T_amb + T) * (c.T_amb - T);
+                const P heat = c.K_ign * E * (c.heat_by_fuel ? ph : P(1));
+                const P Wq = it.wx[q] * it.wy[b];
+                const P S = Wq * (heat + c.chiTamb + rad - c.c_W * (bpx * Tx + bpy * Ty));
+                const P qn = -Wq * c.C_nld * T2 * T;
+                const P QX = qn * Tx, QY = qn * Ty;
+                const P G = -Wq * c.tau_kf * E * ph;
+#pragma unroll
+                for (int l = 0; l < NB; ++l) {
+                    acs[l][q] += WF_BY(b, l) * S + WF_DY(b, l) * QY;
+                    acq[l][q] += WF_BY(b, l) * QX;
+                    acg[l][q] += WF_BY(b, l) * G;
+                }
+            }
+        }
+#undef WF_BY
+#undef WF_DY
     };
 
     // prologue: rows Y0-2p .. Y0-1 (matvec window), of which Y0-p .. Y0-1 also enter the x window
@@ -225,71 +279,17 @@ __global__ void __launch_bounds__(128) k_rhs_stream(const StreamArgs<P> a_in) {
         }
     }
 
+    const int yi_lo = it.yok ? PD : a.ny, yi_hi = a.ny - PD;  // interior element rows [yi_lo, yi_hi)
     Row nxt = fetch_row(ey0 + PD);
     for (int ey = ey0; ey < Y1; ++ey) {
         // new coefficient row ey + p (fetched one iteration ahead), and the fetch of the next one
         const Row cur = nxt;
         nxt = fetch_row(ey + PD + 1);
         process_row(cur, xv[PD], xd[PD], xp[PD], cw1[2 * PD], cw2[2 * PD]);
-        // element (ex, ey): Q x Q points, y-test accumulation into DOF rows ey .. ey+p
-        if (ey >= 0 && ey < a.ny) {
-            P by[Q][NB], dy[Q][NB];
-            const bool interior = ey >= PD && ey < a.ny - PD;
-#pragma unroll
-            for (int b = 0; b < Q; ++b)
-#pragma unroll
-                for (int l = 0; l < NB; ++l) {
-                    by[b][l] = interior ? byi[b][l] : a.By[(size_t)(ey * Q + b) * NB + l];
-                    dy[b][l] = interior ? dyi[b][l] : a.Dy[(size_t)(ey * Q + b) * NB + l];
-                }
-            P gyr[WR > 0 ? WR : 1][Q], gxr[WR > 0 ? WR : 1][Q];
-#pragma unroll
-            for (int r = 0; r < WR; ++r)
-#pragma unroll
-                for (int b = 0; b < Q; ++b) {
-                    gxr[r][b] = a.gxq[(size_t)r * a.ny * Q + ey * Q + b];
-                    gyr[r][b] = a.gyq[(size_t)r * a.ny * Q + ey * Q + b];
-                }
-            if (ex_ok) {
-#pragma unroll
-                for (int b = 0; b < Q; ++b) {
-#pragma unroll
-                    for (int q = 0; q < Q; ++q) {
-                        P T = 0, Ty = 0, Tx = 0, ph = 0;
-#pragma unroll
-                        for (int l = 0; l < NB; ++l) {
-                            T += by[b][l] * xv[l][q];
-                            Ty += dy[b][l] * xv[l][q];
-                            Tx += by[b][l] * xd[l][q];
-                            ph += by[b][l] * xp[l][q];
-                        }
-                        P bpx = 0, bpy = 0;
-#pragma unroll
-                        for (int r = 0; r < WR; ++r) {
-                            bpx += fxr[r][q] * gxr[r][b];
-                            bpy += fyr[r][q] * gyr[r][b];
-                        }
-                        const PhysS<P>& c = a.c;
-                        const bool burn = (T > c.T_ig) && (ph > c.phi_min);
-                        const P E = burn ? T * expo_s<P>(-c.T_a / T) : P(0);
-                        const P T2 = T * T;
-                        const P rad = c.c_rad * (c.T_amb2 + T2) * (c.T_amb + T) * (c.T_amb - T);
-                        const P heat = c.K_ign * E * (c.heat_by_fuel ? ph : P(1));
-                        const P Wq = wxq[q] * wyq[b];
-                        const P S = Wq * (heat + c.chiTamb + rad - c.c_W * (bpx * Tx + bpy * Ty));
-                        const P qn = -Wq * c.C_nld * T2 * T;
-                        const P QX = qn * Tx, QY = qn * Ty;
-                        const P G = -Wq * c.tau_kf * E * ph;
-#pragma unroll
-                        for (int l = 0; l < NB; ++l) {
-                            acs[l][q] += by[b][l] * S + dy[b][l] * QY;
-                            acq[l][q] += by[b][l] * QX;
-                            acg[l][q] += by[b][l] * G;
-                        }
-                    }
-                }
-            }
-        }
+        if (ey >= yi_lo && ey < yi_hi)
+            element_row(std::true_type{}, ey);
+        else if (ey >= 0 && ey < a.ny)
+            element_row(std::false_type{}, ey);
         // DOF row ey is complete: x-test contraction, matvec, stores
         if (ey >= Y0) {
             P Fv = 0, Ph = 0;
@@ -301,8 +301,8 @@ __global__ void __launch_bounds__(128) k_rhs_stream(const StreamArgs<P> a_in) {
                     const P s = (k == 0) ? acs[0][q] : __shfl_up_sync(FULL, acs[0][q], k);
                     const P u = (k == 0) ? acq[0][q] : __shfl_up_sync(FULL, acq[0][q], k);
                     const P g = (k == 0) ? acg[0][q] : __shfl_up_sync(FULL, acg[0][q], k);
-                    Fv += tbx[k][q] * s + tdx[k][q] * u;
-                    Ph += tbx[k][q] * g;
+                    Fv += WF_TBX(k, q) * s + WF_TDX(k, q) * u;
+                    Ph += WF_TBX(k, q) * g;
                 }
             }
             if (out_col) {
@@ -340,6 +340,47 @@ __global__ void __launch_bounds__(128) k_rhs_stream(const StreamArgs<P> a_in) {
             cw2[d] = cw2[d + 1];
         }
     }
+#undef WF_BX
+#undef WF_DX
+#undef WF_TBX
+#undef WF_TDX
+}
+
+// Work item = (strip, segment) of one scenario, flattened so that the warps of a CTA never
+// idle at the end of a row of strips.
+// FP32, p <= 2, wind variation of rank <= 1: three CTAs per SM (at most 168 registers a
+// thread, no spills); the rank-2 form needs more and runs two
+template <typename P, int PD, int WR>
+__global__ void __launch_bounds__(128, (sizeof(P) == 4 && PD <= 2 && WR <= 1) ? 3 : 1)
+    k_rhs_stream(const StreamArgs<P> a_in) {
+    if (!scene_active(a_in.b)) return;
+    StreamArgs<P> a = a_in;
+    a.T = scene_ptr(a.T, a.b);
+    a.phi = scene_ptr(a.phi, a.b);
+    a.F = scene_ptr(a.F, a.b);
+    a.Phi = scene_ptr(a.Phi, a.b);
+    a.R = scene_ptr(a.R, a.b);
+    a.A1 = scene_ptr(a.A1, a.b);
+    a.B1 = scene_ptr(a.B1, a.b);
+    a.A2 = scene_ptr(a.A2, a.b);
+    a.B2 = scene_ptr(a.B2, a.b);
+    a.fxq = scene_ptr(a.fxq, a.b);
+    a.gxq = scene_ptr(a.gxq, a.b);
+    a.fyq = scene_ptr(a.fyq, a.b);
+    a.gyq = scene_ptr(a.gyq, a.b);
+    const int lane = threadIdx.x & 31;
+    const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (item >= a.nstrips * a.nsegs) return;  // whole warp leaves; no block barrier in this kernel
+    const int sg = item / a.nstrips;
+    const int strip = item - sg * a.nstrips;
+    const int X0 = strip * (32 - PD);
+    const int Y0 = sg * a.seg;
+    const int Y1 = min(Y0 + a.seg, a.Ny);
+    const bool xint = a_in.it.xok && X0 >= 2 * PD && X0 + 31 < a.nx;
+    if (xint)
+        stream_strip<P, PD, WR, true>(a, a_in.it, lane, X0, Y0, Y1);
+    else
+        stream_strip<P, PD, WR, false>(a, a_in.it, lane, X0, Y0, Y1);
 }
 
 template <typename P>
@@ -377,9 +418,10 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    const long ctas_x = (a.nstrips + WARPS - 1) / WARPS;
     int seg = 128;
-    while (seg > 16 && 10 * ctas_x * ((r.Ny + seg - 1) / seg) * r.b.S < 18L * sms) seg /= 2;
+    while (seg > 16 && 10 * (((long)a.nstrips * ((r.Ny + seg - 1) / seg) + WARPS - 1) / WARPS) * r.b.S < 18L * sms)
+        seg /= 2;
+    if (r.seg > 0) seg = r.seg;
     a.seg = seg;
     a.T = (const P*)r.T;
     a.phi = (const P*)r.phi;
@@ -390,8 +432,6 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
     a.Dx = (const P*)r.Dx;
     a.By = (const P*)r.By;
     a.Dy = (const P*)r.Dy;
-    a.wx = (const P*)r.wx;
-    a.wy = (const P*)r.wy;
     a.wind_rank = r.wind_rank;
     a.fxq = (const P*)r.fxq;
     a.gxq = (const P*)r.gxq;
@@ -406,7 +446,20 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
     a.c2 = (P)r.c2;
     a.c = to_phys_s<P>(r.phys, r.tau);
     a.b = r.b;
-    dim3 grid((a.nstrips + WARPS - 1) / WARPS, (r.Ny + seg - 1) / seg, r.b.S);
+    a.nsegs = (r.Ny + seg - 1) / seg;
+    for (int i = 0; i < 4; ++i) {
+        for (int j = 0; j < 4; ++j) {
+            a.it.bx[i][j] = (P)r.tx.B[i][j];
+            a.it.dx[i][j] = (P)r.tx.D[i][j];
+            a.it.by[i][j] = (P)r.ty.B[i][j];
+            a.it.dy[i][j] = (P)r.ty.D[i][j];
+        }
+        a.it.wx[i] = (P)r.tx.w[i];
+        a.it.wy[i] = (P)r.ty.w[i];
+    }
+    a.it.xok = r.tx.ok;
+    a.it.yok = r.ty.ok;
+    dim3 grid((unsigned)(((long)a.nstrips * a.nsegs + WARPS - 1) / WARPS), 1, r.b.S);
     k_rhs_stream<P, PD, WR><<<grid, 32 * WARPS, 0, s>>>(a);
     return cudaGetLastError();
 }

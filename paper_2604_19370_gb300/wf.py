@@ -85,6 +85,9 @@ def lib() -> ctypes.CDLL:
         L.wf_set_profiling.argtypes = [vp, i]
         L.wf_kernel_times.argtypes = [vp, dp, ctypes.POINTER(i), ctypes.c_void_p, i]
         L.wf_step_noalloc.argtypes = [vp, vp, vp, i, i]
+        L.wf_autotune.argtypes = [vp, i]
+        L.wf_get_tuning.argtypes = [vp, ctypes.POINTER(i)]
+        L.wf_set_tuning.argtypes = [vp, ctypes.POINTER(i)]
         L.wf_batch_create.argtypes = [i, i, i, d, ctypes.POINTER(wf_params), i, ctypes.POINTER(vp)]
         L.wf_batch_set_slot.argtypes = [vp, i, dp, dp, d, d, i, dp]
         L.wf_batch_get_slot.argtypes = [vp, i, dp, dp]
@@ -212,6 +215,26 @@ def wf_kernel_times(h, max_k: int = 16):
         nm = bytes(names[48 * j:48 * (j + 1)]).split(b"\0")[0].decode()
         out[nm] = (ms[j], cnt[j])
     return out
+
+
+def wf_autotune(h, reps: int = 3) -> Tuple[int, int, int, int]:
+    """Tune the launch shapes of a handle on its active slots.
+
+    Returns (x lines per CTA, y lines per CTA, quadrature segment rows, x lines per warp).
+    """
+    _check(lib().wf_autotune(h, reps), "wf_autotune")
+    return wf_get_tuning(h)
+
+
+def wf_get_tuning(h) -> Tuple[int, int, int, int]:
+    out = (ctypes.c_int * 4)()
+    _check(lib().wf_get_tuning(h, out), "wf_get_tuning")
+    return tuple(int(v) for v in out)
+
+
+def wf_set_tuning(h, shape) -> None:
+    arr = (ctypes.c_int * 4)(*[int(v) for v in shape])
+    _check(lib().wf_set_tuning(h, arr), "wf_set_tuning")
 
 
 def wf_step_noalloc(h, T_dev_ptr: int, fuel_dev_ptr: int, pitch: int, nsteps: int) -> int:

@@ -92,3 +92,12 @@ def test_server_and_batch_argument_checks(libpath):
     assert L.wf_batch_create(8, 8, 2, 1e-3, ctypes.byref(p), 0, ctypes.byref(h)) == wf.WF_EINVAL
     assert L.wf_batch_activate(None, 0, 1) == wf.WF_EINVAL
     assert L.wf_batch_capacity(None) == wf.WF_EINVAL
+
+
+def test_tuning_argument_checks_without_device(libpath):
+    from paper_2604_19370_gb300 import wf
+
+    L = wf.lib()
+    assert L.wf_autotune(None, 1) == wf.WF_EINVAL
+    assert L.wf_get_tuning(None, None) == wf.WF_EINVAL
+    assert L.wf_set_tuning(None, None) == wf.WF_EINVAL
