@@ -26,6 +26,7 @@ template <typename P>
 struct FastArgs {
     int nlines, pitch, mpad, G;
     int lsh;  // x pass: log2 of the lanes per line (5: one line per warp; 4: two; 3: four)
+    int sp;   // x pass: row stride of the staged rows in shared memory (elements)
     Chunks ch;
     const P* in[2];
     P* out[2];
@@ -304,9 +305,10 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
     const size_t row_bytes = (size_t)a.pitch * sizeof(P);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     const bool pre = a.preT != nullptr;
-    P* rowbuf = reinterpret_cast<P*>(smem_raw + 128);             // [G][pitch]
-    P* tbuf = rowbuf + (size_t)G * a.pitch;                        // pre: [G + 2p][pitch], rows j0-p ..
-    P* fl = tbuf + (pre ? (size_t)(G + 2 * PD) * a.pitch : 0);     // [3][mmax][W]
+    const int sp = a.sp;                                           // shared-memory row stride
+    P* rowbuf = reinterpret_cast<P*>(smem_raw + 128);             // [G][sp]
+    P* tbuf = rowbuf + (size_t)G * sp;                             // pre: [G + 2p][sp], rows j0-p ..
+    P* fl = tbuf + (pre ? (size_t)(G + 2 * PD) * sp : 0);          // [3][mmax][W]
     P* fs = fl + 3 * mmax * W;                                     // [3][mmax][S]
     P* fe = fs + 3 * mmax * S;                                     // [3][PD*PD]
     const P* __restrict__ in = pre ? v.preF : v.in;
@@ -319,26 +321,35 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
         // halo rows outside the domain read as zero
         for (int r = j0 - PD; r < j0 + rows + PD; ++r) {
             if (r >= lo && r < hi) continue;
-            for (int x = tid; x < a.pitch; x += blockDim.x) tbuf[(size_t)(r - (j0 - PD)) * a.pitch + x] = P(0);
+            for (int x = tid; x < sp; x += blockDim.x) tbuf[(size_t)(r - (j0 - PD)) * sp + x] = P(0);
         }
     }
     if (a.tma) {
+        // one bulk copy per row (the shared-memory stride differs from the global pitch);
+        // thread 0 arms the barrier with the total, the lanes of warp 0 issue the copies
         if (tid == 0) {
             mbar_init(bar, 1);
             mbar_fence_init();
             const uint32_t bytes = (uint32_t)(rows * row_bytes);
             const uint32_t tbytes = pre ? (uint32_t)((hi - lo) * row_bytes) : 0u;
             mbar_expect_tx(bar, bytes + tbytes);
-            bulk_load(rowbuf, in + (size_t)j0 * a.pitch, bytes, bar);
-            if (pre) bulk_load(tbuf + (size_t)(lo - (j0 - PD)) * a.pitch, v.preT + (size_t)lo * a.pitch, tbytes, bar);
+        }
+        __syncwarp();
+        if (warp == 0) {
+            for (int r = lane; r < rows; r += 32)
+                bulk_load(rowbuf + (size_t)r * sp, in + (size_t)(j0 + r) * a.pitch, (uint32_t)row_bytes, bar);
+            if (pre)
+                for (int r = lo + lane; r < hi; r += 32)
+                    bulk_load(tbuf + (size_t)(r - (j0 - PD)) * sp, v.preT + (size_t)r * a.pitch, (uint32_t)row_bytes,
+                              bar);
         }
     } else {
         for (int r = 0; r < rows; ++r)
-            for (int x = tid; x < N; x += blockDim.x) rowbuf[(size_t)r * a.pitch + x] = in[(size_t)(j0 + r) * a.pitch + x];
+            for (int x = tid; x < N; x += blockDim.x) rowbuf[(size_t)r * sp + x] = in[(size_t)(j0 + r) * a.pitch + x];
         if (pre)
             for (int r = lo; r < hi; ++r)
                 for (int x = tid; x < N; x += blockDim.x)
-                    tbuf[(size_t)(r - (j0 - PD)) * a.pitch + x] = v.preT[(size_t)r * a.pitch + x];
+                    tbuf[(size_t)(r - (j0 - PD)) * sp + x] = v.preT[(size_t)r * a.pitch + x];
     }
     stage_factors(v, 3 * mmax * W, 3 * mmax * S, 3 * PD * PD, fl, fs, fe);
     if (pre) {
@@ -379,7 +390,7 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
                 w2[d] = P(0);
             }
             for (int r = 0; r < rows + 2 * PD; ++r) {
-                const P* trow = tbuf + (size_t)r * a.pitch;
+                const P* trow = tbuf + (size_t)r * sp;
                 P t1 = 0, t2 = 0;
 #pragma unroll
                 for (int dk = 0; dk < W; ++dk) {
@@ -398,10 +409,10 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
                 if (r >= 2 * PD) {
                     const int jl = r - 2 * PD;
                     const P* bj = bco + (size_t)jl * 2 * W;
-                    P acc = a.preFscale * rowbuf[(size_t)jl * a.pitch + x];
+                    P acc = a.preFscale * rowbuf[(size_t)jl * sp + x];
 #pragma unroll
                     for (int dl = 0; dl < W; ++dl) acc += bj[dl] * w1[dl] + bj[W + dl] * w2[dl];
-                    rowbuf[(size_t)jl * a.pitch + x] = acc;
+                    rowbuf[(size_t)jl * sp + x] = acc;
                 }
             }
         }
@@ -413,7 +424,7 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
     const int r = (warp << (5 - a.lsh)) + (lane >> a.lsh);
     const bool active = r < rows && k < C;
     const int m = (k < C - 1) ? base : ch.last;
-    P* g = rowbuf + (size_t)(r < rows ? r : 0) * a.pitch + (size_t)k * base;
+    P* g = rowbuf + (size_t)(r < rows ? r : 0) * sp + (size_t)k * base;
     const int t = chunk_type(ch, k < C ? k : 0);
     if (active) lu_chunk<P, PD>(g, m, fl + t * mmax * W);
     __syncwarp();
@@ -434,14 +445,18 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
     if (a.tma) {
         fence_proxy_async_smem();
         __syncthreads();
-        if (tid == 0) {
-            bulk_store(out + (size_t)j0 * a.pitch, rowbuf, (uint32_t)(rows * row_bytes));
-            bulk_commit_and_wait_read();
+        if (warp == 0) {
+            bool issued = false;
+            for (int r = lane; r < rows; r += 32) {
+                bulk_store(out + (size_t)(j0 + r) * a.pitch, rowbuf + (size_t)r * sp, (uint32_t)row_bytes);
+                issued = true;
+            }
+            if (issued) bulk_commit_and_wait_read();
         }
     } else {
         __syncthreads();
         for (int r = 0; r < rows; ++r)
-            for (int x = tid; x < N; x += blockDim.x) out[(size_t)(j0 + r) * a.pitch + x] = rowbuf[(size_t)r * a.pitch + x];
+            for (int x = tid; x < N; x += blockDim.x) out[(size_t)(j0 + r) * a.pitch + x] = rowbuf[(size_t)r * sp + x];
     }
 }
 
@@ -573,14 +588,22 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         const size_t row_bytes = (size_t)a.pitch * sizeof(P);
         const bool pre = a.preT != nullptr;
         if (pre && a.narr != 1) return cudaErrorNotSupported;
-        auto need = [&](int g) {
-            return 128 + g * row_bytes + (pre ? (g + 2 * PD) * row_bytes + (size_t)g * 2 * W * sizeof(P) : 0) + fbytes;
-        };
         // lines per warp: as many as the chunks allow (C <= 8: four, C <= 16: two), or fewer
         int lsh = ch.C <= 8 ? 3 : (ch.C <= 16 ? 4 : 5);
         if (a.rpw == 1) lsh = 5;
         else if (a.rpw == 2 && lsh < 4) lsh = 4;
         const int lpw = 1 << (5 - lsh);
+        // shared-memory row stride: the lines of a warp start L banks apart (L = lanes per line,
+        // chunk lengths odd), so its lanes hit distinct banks; 16-byte multiple for bulk copies
+        const int L = 32 >> (5 - lsh);
+        const int slots = sizeof(P) == 4 ? 32 : 16;  // bank-width words per wavefront
+        int sp = a.pitch;
+        if (L < slots)
+            while (sp % (2 * L) != L || (sp * sizeof(P)) % 16 != 0) ++sp;
+        const size_t srow = (size_t)sp * sizeof(P);
+        auto need = [&](int g) {
+            return 128 + g * srow + (pre ? (g + 2 * PD) * srow + (size_t)g * 2 * W * sizeof(P) : 0) + fbytes;
+        };
         // lines per CTA: up to 8 warps' worth, fewer when the staged rows need more than 100 KB
         int G = 8 * lpw;
         if (a.G > 0 && a.G < G) G = a.G < lpw ? lpw : a.G;
@@ -594,6 +617,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         if (pre) aligned = aligned && ((uintptr_t)a.preT % 16 == 0);
         f.G = G;
         f.lsh = lsh;
+        f.sp = sp;
         f.tma = aligned ? 1 : 0;
         auto kern = k_xsolve_warp<P, PD>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
