@@ -16,10 +16,12 @@
 //     goes through shared memory;
 //   * a DOF row is finished (x-test contraction, matvec, stores) as soon as the
 //     last element row touching it has been processed;
-//   * with uniform knots every element p <= e < n - p has the same B, B' tables, so
-//     strips and element rows away from the boundary take them from the kernel's
-//     parameter block (constant operands of the FMAs, no registers); boundary strips
-//     read their own tables through L1;
+//   * with uniform knots every element p <= e < n - p has the same B, B' tables; the
+//     rows are cut into a segment of the first 2p DOF rows, interior segments and a
+//     segment of the last 2p, so that a warp on an interior strip and segment touches
+//     interior elements only and takes every table from the kernel's parameter block
+//     (constant operands of the FMAs, no registers); the other warps read their
+//     element's tables through L1;
 //   * warps take (strip, segment) work items in a flat order, so none idles when the
 //     strips of a row do not fill a CTA.
 //
@@ -28,7 +30,6 @@
 // below 7 % for p = 2.
 #include <math.h>
 
-#include <type_traits>
 
 #include "wf_internal.h"
 
@@ -55,13 +56,16 @@ template <typename P>
 struct ITab {
     P bx[4][4], dx[4][4];  // x: [Gauss point][local basis]
     P by[4][4], dy[4][4];  // y: [Gauss point][local basis]
-    P wx[4], wy[4];        // Gauss weights x element length (every element)
+    P wq[4][4];            // Gauss weight products w_y[b] w_x[q] (every element)
+    P wqc[4][4];           // -C_nld w_y[b] w_x[q]
+    P wqg[4][4];           // -tau k_f w_y[b] w_x[q]
     int xok, yok;          // the interior tables exist (n > 2p)
 };
 
 template <typename P>
 struct StreamArgs {
     int nx, ny, Nx, Ny, pitch, seg, nstrips, nsegs;
+    int split;  // segments: [0, 2p), interior pieces of [2p, Ny - 2p), [Ny - 2p, Ny)
     const P* __restrict__ T;
     const P* __restrict__ phi;
     P* F;
@@ -96,8 +100,9 @@ template <>
 __device__ __forceinline__ double neg_ratio<double>(double a, double t) { return -a / t; }
 
 // One warp: strip of 32 element columns starting at X0 - p, element rows Y0 - p .. Y1 - 1.
-// XI: every element of the strip (and every element feeding its output columns) is interior,
-// so the x tables come from the parameter block.
+// XI (fast form): every element the warp touches is interior, so all tables come from the
+// parameter block; otherwise (boundary strips and the boundary segments) they are read
+// through L1.
 template <typename P, int PD, int WR, bool XI>
 __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<P>& it, int lane, int X0, int Y0,
                                              int Y1) {
@@ -198,10 +203,9 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
         w2 = s2;
     };
 
-    // one element row: Q x Q points, y-test accumulation into DOF rows ey .. ey+p.
-    // YI: the row is interior and its y tables come from the parameter block.
-    auto element_row = [&](auto yi, int ey) {
-        constexpr bool YI = decltype(yi)::value;
+    // one element row: Q x Q points, y-test accumulation into DOF rows ey .. ey+p
+    auto element_row = [&](int ey) {
+        constexpr bool YI = XI;
         P byr[Q][NB], dyr[Q][NB];
 #pragma unroll
         for (int b = 0; b < Q; ++b)
@@ -245,11 +249,10 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
                 const P T2 = T * T;
                 const P rad = c.c_rad * (c.T_amb2 + T2) * (c.T_amb + T) * (c.T_amb - T);
                 const P heat = c.K_ign * E * (c.heat_by_fuel ? ph : P(1));
-                const P Wq = it.wx[q] * it.wy[b];
-                const P S = Wq * (heat + c.chiTamb + rad - c.c_W * (bpx * Tx + bpy * Ty));
-                const P qn = -Wq * c.C_nld * T2 * T;
+                const P S = it.wq[b][q] * (heat + c.chiTamb + rad - c.c_W * (bpx * Tx + bpy * Ty));
+                const P qn = it.wqc[b][q] * T2 * T;
                 const P QX = qn * Tx, QY = qn * Ty;
-                const P G = -Wq * c.tau_kf * E * ph;
+                const P G = it.wqg[b][q] * E * ph;
 #pragma unroll
                 for (int l = 0; l < NB; ++l) {
                     acs[l][q] += WF_BY(b, l) * S + WF_DY(b, l) * QY;
@@ -279,17 +282,13 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
         }
     }
 
-    const int yi_lo = it.yok ? PD : a.ny, yi_hi = a.ny - PD;  // interior element rows [yi_lo, yi_hi)
     Row nxt = fetch_row(ey0 + PD);
     for (int ey = ey0; ey < Y1; ++ey) {
         // new coefficient row ey + p (fetched one iteration ahead), and the fetch of the next one
         const Row cur = nxt;
         nxt = fetch_row(ey + PD + 1);
         process_row(cur, xv[PD], xd[PD], xp[PD], cw1[2 * PD], cw2[2 * PD]);
-        if (ey >= yi_lo && ey < yi_hi)
-            element_row(std::true_type{}, ey);
-        else if (ey >= 0 && ey < a.ny)
-            element_row(std::false_type{}, ey);
+        if (XI || (ey >= 0 && ey < a.ny)) element_row(ey);
         // DOF row ey is complete: x-test contraction, matvec, stores
         if (ey >= Y0) {
             P Fv = 0, Ph = 0;
@@ -374,10 +373,25 @@ __global__ void __launch_bounds__(128, (sizeof(P) == 4 && PD <= 2 && WR <= 1) ? 
     const int sg = item / a.nstrips;
     const int strip = item - sg * a.nstrips;
     const int X0 = strip * (32 - PD);
-    const int Y0 = sg * a.seg;
-    const int Y1 = min(Y0 + a.seg, a.Ny);
+    int Y0, Y1;
+    bool yint = false;
+    if (!a.split) {
+        Y0 = sg * a.seg;
+        Y1 = min(Y0 + a.seg, a.Ny);
+    } else if (sg == 0) {
+        Y0 = 0;
+        Y1 = 2 * PD;
+    } else if (sg == a.nsegs - 1) {
+        Y0 = a.Ny - 2 * PD;
+        Y1 = a.Ny;
+    } else {
+        // element rows Y0 - p .. Y1 - 1 all lie in [p, ny - p)
+        Y0 = 2 * PD + (sg - 1) * a.seg;
+        Y1 = min(Y0 + a.seg, a.Ny - 2 * PD);
+        yint = true;
+    }
     const bool xint = a_in.it.xok && X0 >= 2 * PD && X0 + 31 < a.nx;
-    if (xint)
+    if (xint && yint)
         stream_strip<P, PD, WR, true>(a, a_in.it, lane, X0, Y0, Y1);
     else
         stream_strip<P, PD, WR, false>(a, a_in.it, lane, X0, Y0, Y1);
@@ -446,7 +460,11 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
     a.c2 = (P)r.c2;
     a.c = to_phys_s<P>(r.phys, r.tau);
     a.b = r.b;
-    a.nsegs = (r.Ny + seg - 1) / seg;
+    // interior segments need element rows p .. ny-p-1 only: the middle [2p, Ny - 2p) is cut
+    // into pieces, the 2p DOF rows at either end form their own (boundary) segments
+    const int mid = r.Ny - 4 * PD;
+    a.split = (r.tx.ok && r.ty.ok && mid >= 1) ? 1 : 0;
+    a.nsegs = a.split ? 2 + (mid + seg - 1) / seg : (r.Ny + seg - 1) / seg;
     for (int i = 0; i < 4; ++i) {
         for (int j = 0; j < 4; ++j) {
             a.it.bx[i][j] = (P)r.tx.B[i][j];
@@ -454,8 +472,12 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
             a.it.by[i][j] = (P)r.ty.B[i][j];
             a.it.dy[i][j] = (P)r.ty.D[i][j];
         }
-        a.it.wx[i] = (P)r.tx.w[i];
-        a.it.wy[i] = (P)r.ty.w[i];
+        for (int j = 0; j < 4; ++j) {
+            const double wq = r.ty.w[i] * r.tx.w[j];
+            a.it.wq[i][j] = (P)wq;
+            a.it.wqc[i][j] = (P)(-wq * r.phys.C_nld);
+            a.it.wqg[i][j] = (P)(-wq * r.tau * r.phys.k_f);
+        }
     }
     a.it.xok = r.tx.ok;
     a.it.yok = r.ty.ok;
