@@ -125,50 +125,119 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 
 constexpr uint32_t kSpinLimit = 1u << 20;  // bounded mbarrier wait; a timeout sets status bit 2
 
-// Chunk-local LU substitution on g[0 .. m) (stride 1) with the factors of one chunk type.
-// The values and factors of 8 rows are loaded before the dependent FMA chain runs over
-// them, so shared-memory latency is paid once per 8 rows rather than once per row.
+// ---- factors in shared memory ---------------------------------------------------------
+// Each chunk-type row of the compact factors is split into three padded vectors so that one
+// row is one (or two) vector loads:
+//   F[o]: L_1 .. L_p            (multipliers of rows o-1 .. o-p, forward elimination)
+//   U[o]: 1/u_oo, u_o,o+1 .. u_o,o+p   (backward substitution)
+//   S[o]: V_1 .. V_p, W_1 .. W_p  (spike columns)
+template <int PD>
+struct FacW {
+    static constexpr int F = PD == 1 ? 1 : (PD == 2 ? 2 : 4);
+    static constexpr int U = PD == 1 ? 2 : 4;
+    static constexpr int S = PD == 1 ? 2 : (PD == 2 ? 4 : 8);
+};
+__host__ __device__ constexpr int round4(int n) { return (n + 3) & ~3; }
+// elements of the staged factors of 3 chunk types with mmax rows (each part 16-byte aligned)
+template <int PD>
+__host__ __device__ constexpr int fac_elems(int mmax) {
+    return round4(3 * mmax * FacW<PD>::F) + round4(3 * mmax * FacW<PD>::U) + round4(3 * mmax * FacW<PD>::S) +
+           round4(3 * PD * PD);
+}
 template <typename P, int PD>
-__device__ __forceinline__ void lu_chunk(P* g, int m, const P* L) {
-    constexpr int W = 2 * PD + 1, B = 8;
+struct FacSmem {
+    P *F, *U, *S, *E;
+    __device__ __forceinline__ FacSmem(P* base, int mmax) {
+        F = base;
+        U = F + round4(3 * mmax * FacW<PD>::F);
+        S = U + round4(3 * mmax * FacW<PD>::U);
+        E = S + round4(3 * mmax * FacW<PD>::S);
+    }
+    __device__ __forceinline__ P* end() const { return E + round4(3 * PD * PD); }
+};
+
+// N consecutive values from a shared-memory row aligned to min(16, N * sizeof(P)) bytes
+template <typename P, int N>
+__device__ __forceinline__ void ldv(const P* p, P (&o)[N]) {
+    if constexpr (sizeof(P) == 4 && N % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < N; i += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(p + i);
+            o[i] = v.x;
+            o[i + 1] = v.y;
+            o[i + 2] = v.z;
+            o[i + 3] = v.w;
+        }
+    } else if constexpr (sizeof(P) == 4 && N == 2) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+    } else if constexpr (sizeof(P) == 8 && N % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < N; i += 2) {
+            const double2 v = *reinterpret_cast<const double2*>(p + i);
+            o[i] = v.x;
+            o[i + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) o[i] = p[i];
+    }
+}
+
+// Forward elimination of one batch of B rows o0 .. o0+B-1 (< m) held in registers.
+template <typename P, int PD, int B>
+__device__ __forceinline__ void forward_batch(P (&x)[B], int o0, int m, const P* F, P (&prev)[PD]) {
+    constexpr int NF = FacW<PD>::F;
+    P lv[B][NF];
+#pragma unroll
+    for (int q = 0; q < B; ++q) ldv<P, NF>(F + (o0 + q < m ? o0 + q : m - 1) * NF, lv[q]);
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        if (o0 + q < m) {
+            P y = x[q];
+#pragma unroll
+            for (int i = 0; i < PD; ++i) y -= lv[q][i] * prev[i];
+#pragma unroll
+            for (int i = PD - 1; i > 0; --i) prev[i] = prev[i - 1];
+            prev[0] = y;
+            x[q] = y;
+        }
+    }
+}
+
+// Chunk-local forward elimination on g[0 .. m) in shared memory, 8 rows per batch of loads.
+template <typename P, int PD>
+__device__ __forceinline__ void lu_forward(P* g, int m, const P* F) {
+    constexpr int B = 8;
     P prev[PD];
 #pragma unroll
     for (int i = 0; i < PD; ++i) prev[i] = P(0);
     for (int o0 = 0; o0 < m; o0 += B) {
-        P gv[B], lv[B][PD];
+        P gv[B];
 #pragma unroll
-        for (int q = 0; q < B; ++q) {
-            const int o = o0 + q < m ? o0 + q : m - 1;
-            gv[q] = g[o];
-#pragma unroll
-            for (int i = 0; i < PD; ++i) lv[q][i] = L[o * W + i];
-        }
-#pragma unroll
-        for (int q = 0; q < B; ++q) {
-            if (o0 + q < m) {
-                P x = gv[q];
-#pragma unroll
-                for (int i = 0; i < PD; ++i) x -= lv[q][i] * prev[i];
-#pragma unroll
-                for (int i = PD - 1; i > 0; --i) prev[i] = prev[i - 1];
-                prev[0] = x;
-                gv[q] = x;
-            }
-        }
+        for (int q = 0; q < B; ++q) gv[q] = g[o0 + q < m ? o0 + q : m - 1];
+        forward_batch<P, PD, B>(gv, o0, m, F, prev);
 #pragma unroll
         for (int q = 0; q < B; ++q)
             if (o0 + q < m) g[o0 + q] = gv[q];
     }
+}
+
+// Chunk-local backward substitution on g[0 .. m), 8 rows per batch of loads.
+template <typename P, int PD>
+__device__ __forceinline__ void lu_backward(P* g, int m, const P* U) {
+    constexpr int B = 8, NU = FacW<PD>::U;
+    P prev[PD];
 #pragma unroll
     for (int i = 0; i < PD; ++i) prev[i] = P(0);
     for (int o1 = m; o1 > 0; o1 -= B) {
-        P gv[B], uv[B][PD + 1];
+        P gv[B], uv[B][NU];
 #pragma unroll
         for (int q = 0; q < B; ++q) {
             const int o = o1 - 1 - q >= 0 ? o1 - 1 - q : 0;
             gv[q] = g[o];
-#pragma unroll
-            for (int j = 0; j <= PD; ++j) uv[q][j] = L[o * W + PD + j];
+            ldv<P, NU>(U + o * NU, uv[q]);
         }
 #pragma unroll
         for (int q = 0; q < B; ++q) {
@@ -192,15 +261,14 @@ __device__ __forceinline__ void lu_chunk(P* g, int m, const P* L) {
 // Spike corrections g[o] -= V[o] tn + W[o] bp on g[0 .. m), 8 rows per batch of loads.
 template <typename P, int PD>
 __device__ __forceinline__ void spike_fix(P* g, int m, const P* Sk, const P* tn, const P* bp) {
-    constexpr int S = 2 * PD, B = 8;
+    constexpr int B = 8, NS = FacW<PD>::S;
     for (int o0 = 0; o0 < m; o0 += B) {
-        P gv[B], sv[B][S];
+        P gv[B], sv[B][NS];
 #pragma unroll
         for (int q = 0; q < B; ++q) {
             const int o = o0 + q < m ? o0 + q : m - 1;
             gv[q] = g[o];
-#pragma unroll
-            for (int c = 0; c < S; ++c) sv[q][c] = Sk[o * S + c];
+            ldv<P, NS>(Sk + o * NS, sv[q]);
         }
 #pragma unroll
         for (int q = 0; q < B; ++q) {
@@ -221,7 +289,7 @@ template <typename P, int PD>
 __device__ __forceinline__ void interface_solve(const Chunks& ch, int k, int mmax, const P* fs, const P* fe,
                                                 const P* own_top, const P* own_bot, const P* nxt_top,
                                                 const P* prv_bot, P* tn, P* bp) {
-    constexpr int S = 2 * PD;
+    constexpr int S = FacW<PD>::S;  // row stride of the staged spikes
     const int base = ch.base;
 #pragma unroll
     for (int q = 0; q < PD; ++q) tn[q] = bp[q] = P(0);
@@ -273,16 +341,30 @@ __device__ __forceinline__ void interface_solve(const Chunks& ch, int k, int mma
     }
 }
 
-template <typename P>
-__device__ __forceinline__ void stage_factors(const LineView<P>& v, int n_lu, int n_spk, int n_e, P* fl, P* fs,
-                                              P* fe) {
+// Compact factors (global, [3][mmax][2p+1], [3][mmax][2p], [3][p*p]) into the padded
+// shared-memory layout of FacSmem; padding entries are zero.
+template <typename P, int PD>
+__device__ __forceinline__ void stage_factors(const LineView<P>& v, int mmax, const FacSmem<P, PD>& fm) {
+    constexpr int W = 2 * PD + 1, S2 = 2 * PD;
+    constexpr int NF = FacW<PD>::F, NU = FacW<PD>::U, NS = FacW<PD>::S;
     const int nt = blockDim.x, tid = threadIdx.x;
     const P* __restrict__ g1 = v.luc;
     const P* __restrict__ g2 = v.spkc;
     const P* __restrict__ g3 = v.Ec;
-    for (int i = tid; i < n_lu; i += nt) fl[i] = g1[i];
-    for (int i = tid; i < n_spk; i += nt) fs[i] = g2[i];
-    for (int i = tid; i < n_e; i += nt) fe[i] = g3[i];
+    const int rows = 3 * mmax;
+    for (int i = tid; i < rows * NF; i += nt) {
+        const int r = i / NF, c = i - r * NF;
+        fm.F[i] = c < PD ? g1[r * W + c] : P(0);
+    }
+    for (int i = tid; i < rows * NU; i += nt) {
+        const int r = i / NU, c = i - r * NU;
+        fm.U[i] = c <= PD ? g1[r * W + PD + c] : P(0);
+    }
+    for (int i = tid; i < rows * NS; i += nt) {
+        const int r = i / NS, c = i - r * NS;
+        fm.S[i] = c < S2 ? g2[r * S2 + c] : P(0);
+    }
+    for (int i = tid; i < 3 * PD * PD; i += nt) fm.E[i] = g3[i];
 }
 
 // x pass.  CTA = G lines; a warp solves 32 / lanes lines, lane k of a line's group owns chunk k
@@ -291,7 +373,7 @@ __device__ __forceinline__ void stage_factors(const LineView<P>& v, int n_lu, in
 // Chunk lengths are odd, so the 32 lanes of a warp read 32 distinct shared-memory banks.
 template <typename P, int PD>
 __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
-    constexpr int W = 2 * PD + 1, S = 2 * PD;
+    constexpr int W = 2 * PD + 1;
     if (!scene_active(a.b)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -308,9 +390,7 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
     const int sp = a.sp;                                           // shared-memory row stride
     P* rowbuf = reinterpret_cast<P*>(smem_raw + 128);             // [G][sp]
     P* tbuf = rowbuf + (size_t)G * sp;                             // pre: [G + 2p][sp], rows j0-p ..
-    P* fl = tbuf + (pre ? (size_t)(G + 2 * PD) * sp : 0);          // [3][mmax][W]
-    P* fs = fl + 3 * mmax * W;                                     // [3][mmax][S]
-    P* fe = fs + 3 * mmax * S;                                     // [3][PD*PD]
+    const FacSmem<P, PD> fm(tbuf + (pre ? (size_t)(G + 2 * PD) * sp : 0), mmax);  // factors, then pre: bands
     const P* __restrict__ in = pre ? v.preF : v.in;
     P* out = v.out;
     // rows of the halo block that exist (pre): lo .. hi-1
@@ -351,9 +431,9 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
                 for (int x = tid; x < N; x += blockDim.x)
                     tbuf[(size_t)(r - (j0 - PD)) * sp + x] = v.preT[(size_t)r * a.pitch + x];
     }
-    stage_factors(v, 3 * mmax * W, 3 * mmax * S, 3 * PD * PD, fl, fs, fe);
+    stage_factors<P, PD>(v, mmax, fm);
     if (pre) {
-        P* bco = fe + 3 * PD * PD;
+        P* bco = fm.end();
         for (int i = tid; i < rows * W; i += blockDim.x) {
             const int r = i / W, d = i - r * W;
             bco[(size_t)r * 2 * W + d] = a.pc1 * v.pB1[(size_t)(j0 + r) * W + d];
@@ -379,7 +459,7 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
         // R = preFscale F + (pA1 (x) pc1 pB1) T + (pA2 (x) pc2 pB2) T, one column per thread:
         // the x bands of column x are loaded once and applied to the G + 2p staged rows, whose
         // results pass through a W-row register window that the y bands reduce.
-        const P* __restrict__ bco = fe + 3 * PD * PD;  // [G][2][W], scaled by pc1 / pc2
+        const P* __restrict__ bco = fm.end();  // [G][2][W], scaled by pc1 / pc2
         for (int x = tid; x < N; x += blockDim.x) {
             P a1v[W], a2v[W], w1[W], w2[W];
 #pragma unroll
@@ -426,7 +506,10 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
     const int m = (k < C - 1) ? base : ch.last;
     P* g = rowbuf + (size_t)(r < rows ? r : 0) * sp + (size_t)k * base;
     const int t = chunk_type(ch, k < C ? k : 0);
-    if (active) lu_chunk<P, PD>(g, m, fl + t * mmax * W);
+    if (active) {
+        lu_forward<P, PD>(g, m, fm.F + t * mmax * FacW<PD>::F);
+        lu_backward<P, PD>(g, m, fm.U + t * mmax * FacW<PD>::U);
+    }
     __syncwarp();
     P top[PD], bot[PD], nxt_top[PD], prv_bot[PD];
 #pragma unroll
@@ -440,8 +523,8 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
         prv_bot[q] = __shfl_up_sync(0xffffffffu, bot[q], 1);
     }
     P tn[PD], bp[PD];
-    interface_solve<P, PD>(ch, k < C ? k : 0, mmax, fs, fe, top, bot, nxt_top, prv_bot, tn, bp);
-    if (active) spike_fix<P, PD>(g, m, fs + t * mmax * S, tn, bp);
+    interface_solve<P, PD>(ch, k < C ? k : 0, mmax, fm.S, fm.E, top, bot, nxt_top, prv_bot, tn, bp);
+    if (active) spike_fix<P, PD>(g, m, fm.S + t * mmax * FacW<PD>::S, tn, bp);
     if (a.tma) {
         fence_proxy_async_smem();
         __syncthreads();
@@ -461,21 +544,21 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
 }
 
 // y pass.  CTA = G columns x C chunks (blockDim = G*C <= 256); thread tid = k*G + c owns chunk k
-// of column c in its private shared-memory region (odd stride: distinct banks).  Loads are
-// issued in batches of 16 before use so each thread keeps 16 requests in flight.
+// of column c in its private shared-memory strip (odd stride: distinct banks).  The column values
+// are loaded 16 rows at a time and eliminated forward as they arrive, so the strip is written
+// once before the backward sweep; the increment base is added on the final store.
 template <typename P, int PD>
 __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
-    constexpr int W = 2 * PD + 1, S = 2 * PD, B = 16;
+    constexpr int W = 2 * PD + 1, B = 16;
+    constexpr int NF = FacW<PD>::F, NU = FacW<PD>::U, NS = FacW<PD>::S;
     if (!scene_active(a.b)) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nt = blockDim.x, tid = threadIdx.x;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int tid = threadIdx.x;
     const Chunks ch = a.ch;
     const int N = ch.N, C = ch.C, base = ch.base, G = a.G, mpad = a.mpad;
     const int mmax = base + 2 * PD;
-    P* fl = reinterpret_cast<P*>(smem_raw);  // [3][mmax][W]
-    P* fs = fl + 3 * mmax * W;               // [3][mmax][S]
-    P* fe = fs + 3 * mmax * S;               // [3][PD*PD]
-    P* buf = fe + 3 * PD * PD;               // [nt][mpad]
+    const FacSmem<P, PD> fm(reinterpret_cast<P*>(smem_raw), mmax);
+    P* buf = fm.end();  // [nt][mpad]
     const int arr = blockIdx.y;
     const int k = tid / G, c = tid - k * G;
     const int s = k * base;
@@ -484,12 +567,17 @@ __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
     const int line = blockIdx.x * G + c;
     const bool valid = line < a.nlines;
     const LineView<P> v = scene_line(a, arr);
-    const P* __restrict__ in = v.in;
-    P* out = v.out;
+    const size_t pitch = (size_t)a.pitch;
+    const P* __restrict__ src = v.in + (size_t)s * pitch + (valid ? line : 0);
     P* g = buf + (size_t)tid * mpad;
 
-    stage_factors(v, 3 * mmax * W, 3 * mmax * S, 3 * PD * PD, fl, fs, fe);
+    stage_factors<P, PD>(v, mmax, fm);
+    __syncthreads();
     const P* __restrict__ pre = v.premul;
+    const P* Fk = fm.F + t * mmax * NF;
+    P prev[PD];
+#pragma unroll
+    for (int i = 0; i < PD; ++i) prev[i] = P(0);
     for (int o0 = 0; o0 < m; o0 += B) {
         P r[B];
         if (pre) {
@@ -502,46 +590,52 @@ __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
 #pragma unroll
                     for (int d = 0; d < W; ++d) {
                         const int rr = row + d - PD;
-                        if (rr >= 0 && rr < N) acc += pre[(size_t)row * W + d] * in[(size_t)rr * a.pitch + line];
+                        if (rr >= 0 && rr < N) acc += pre[(size_t)row * W + d] * v.in[(size_t)rr * pitch + line];
                     }
                 }
                 r[q] = ps * acc;
             }
         } else {
 #pragma unroll
-            for (int q = 0; q < B; ++q)
-                r[q] = (valid && o0 + q < m) ? in[(size_t)(s + o0 + q) * a.pitch + line] : P(0);
+            for (int q = 0; q < B; ++q) r[q] = (valid && o0 + q < m) ? src[(size_t)(o0 + q) * pitch] : P(0);
         }
+        forward_batch<P, PD, B>(r, o0, m, Fk, prev);
 #pragma unroll
         for (int q = 0; q < B; ++q)
             if (o0 + q < m) g[o0 + q] = r[q];
     }
-    __syncthreads();
-    lu_chunk<P, PD>(g, m, fl + t * mmax * W);
+    lu_backward<P, PD>(g, m, fm.U + t * mmax * NU);
     __syncthreads();
     const P* gn = buf + (size_t)((k + 1 < C ? k + 1 : k) * G + c) * mpad;
     const P* gp = buf + (size_t)((k > 0 ? k - 1 : k) * G + c) * mpad + (base - PD);
     P tn[PD], bp[PD];
-    interface_solve<P, PD>(ch, k, mmax, fs, fe, g, g + (base - PD), gn, gp, tn, bp);
+    interface_solve<P, PD>(ch, k, mmax, fm.S, fm.E, g, g + (base - PD), gn, gp, tn, bp);
     if (!valid) return;  // no barrier follows
-    const P* Sk = fs + t * mmax * S;
-    const P* __restrict__ bs = v.base;
+    const P* Sk = fm.S + t * mmax * NS;
+    const P* __restrict__ bs = v.base ? v.base + (size_t)s * pitch + line : nullptr;
+    P* dst = v.out + (size_t)s * pitch + line;
     const bool guard = (v.status != nullptr) && arr == 0;
+    const P tmax = a.tmax;
     bool bad = false;
-    for (int o0 = 0; o0 < m; o0 += B) {
-        P b[B];
+    constexpr int B2 = 8;  // rows per batch of the final pass (spikes need NS registers a row)
+    for (int o0 = 0; o0 < m; o0 += B2) {
+        P b[B2], gv[B2], sv[B2][NS];
 #pragma unroll
-        for (int q = 0; q < B; ++q) b[q] = (bs && o0 + q < m) ? bs[(size_t)(s + o0 + q) * a.pitch + line] : P(0);
+        for (int q = 0; q < B2; ++q) {
+            const int o = o0 + q < m ? o0 + q : m - 1;
+            b[q] = (bs && o0 + q < m) ? bs[(size_t)(o0 + q) * pitch] : P(0);
+            gv[q] = g[o];
+            ldv<P, NS>(Sk + o * NS, sv[q]);
+        }
 #pragma unroll
-        for (int q = 0; q < B; ++q) {
-            const int o = o0 + q;
-            if (o < m) {
-                P x = g[o];
+        for (int q = 0; q < B2; ++q) {
+            if (o0 + q < m) {
+                P x = gv[q];
 #pragma unroll
-                for (int r = 0; r < PD; ++r) x -= Sk[o * S + r] * tn[r] + Sk[o * S + PD + r] * bp[r];
+                for (int r = 0; r < PD; ++r) x -= sv[q][r] * tn[r] + sv[q][PD + r] * bp[r];
                 x += b[q];
-                out[(size_t)(s + o) * a.pitch + line] = x;
-                if (guard) bad |= !(fabs((double)x) <= (double)a.tmax);
+                dst[(size_t)(o0 + q) * pitch] = x;
+                bad |= !(fabs(x) <= tmax);  // also catches NaN
             }
         }
     }
@@ -550,11 +644,11 @@ __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
 
 template <typename P, int PD, bool X>
 cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
-    constexpr int W = 2 * PD + 1, S = 2 * PD;
+    constexpr int W = 2 * PD + 1;
     const Chunks& ch = a.f[0].ch;
     if (ch.C > 32) return cudaErrorNotSupported;
     const int mmax = ch.base + 2 * PD;
-    const size_t fbytes = ((size_t)3 * mmax * (W + S) + 3 * PD * PD) * sizeof(P);
+    const size_t fbytes = (size_t)fac_elems<PD>(mmax) * sizeof(P);
     FastArgs<P> f;
     f.nlines = a.nlines;
     f.pitch = a.pitch;
