@@ -1063,11 +1063,14 @@ int wf_autotune(wf_handle* h, int reps) {
     for (int z = 0; z < h->S; ++z) any = any || h->active_host[z];
     if (!any) return WF_OK;
     // each row is one candidate run; -1 keeps a shape at its best value so far.  The x lines
-    // per warp are tuned after the x lines per CTA they depend on.
-    constexpr int kRuns = 10;
+    // per warp are tuned after the x lines per CTA they depend on; segment heights also take
+    // values between the powers of two, because the number of (strip, segment) work items
+    // against the resident warps decides how full the last wave is.
+    constexpr int kRuns = 15;
     static const int kCands[kRuns][kTune] = {
-        {0, 0, 0, 0},      {32, 32, 128, -1}, {16, 16, 64, -1}, {8, 8, 32, -1}, {4, 4, 16, -1},
-        {2, 2, -1, -1},    {1, 1, -1, -1},    {-1, -1, -1, 1},  {-1, -1, -1, 2}, {-1, -1, -1, 4}};
+        {0, 0, 0, 0},      {32, 32, 128, -1}, {16, 16, 64, -1},  {8, 8, 32, -1},    {4, 4, 16, -1},
+        {2, 2, 96, -1},    {1, 1, 48, -1},    {-1, -1, 40, 1},   {-1, -1, 24, 2},   {-1, -1, 20, 4},
+        {-1, -1, 80, -1},  {-1, -1, 28, -1},  {-1, -1, 21, -1},  {-1, -1, 56, -1},  {-1, -1, 12, -1}};
     const size_t bytes = (size_t)h->sbytes * h->S;
     void* snap = nullptr;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;

@@ -16,6 +16,8 @@
 // mbarrier); neighbouring chunks exchange boundary values by warp shuffles.
 // y pass: a CTA owns G columns; lanes of neighbouring columns read and write
 // contiguous runs of G elements per row, 16 loads in flight per thread.
+#include <type_traits>
+
 #include "wf_internal.h"
 
 namespace wf {
@@ -27,6 +29,7 @@ struct FastArgs {
     int nlines, pitch, mpad, G;
     int lsh;  // x pass: log2 of the lanes per line (5: one line per warp; 4: two; 3: four)
     int sp;   // x pass: row stride of the staged rows in shared memory (elements)
+    int tsp;  // x pass with preT: row stride of the staged T* rows (data at column offset 4)
     Chunks ch;
     const P* in[2];
     P* out[2];
@@ -185,101 +188,125 @@ __device__ __forceinline__ void ldv(const P* p, P (&o)[N]) {
     }
 }
 
-// Forward elimination of one batch of B rows o0 .. o0+B-1 (< m) held in registers.
+// Forward elimination of B consecutive rows held in registers; F points at the first row's
+// factors.  prev[i] holds the result i+1 rows above.
 template <typename P, int PD, int B>
-__device__ __forceinline__ void forward_batch(P (&x)[B], int o0, int m, const P* F, P (&prev)[PD]) {
+__device__ __forceinline__ void fwd_rows(P (&x)[B], const P* F, P (&prev)[PD]) {
     constexpr int NF = FacW<PD>::F;
     P lv[B][NF];
 #pragma unroll
-    for (int q = 0; q < B; ++q) ldv<P, NF>(F + (o0 + q < m ? o0 + q : m - 1) * NF, lv[q]);
+    for (int q = 0; q < B; ++q) ldv<P, NF>(F + q * NF, lv[q]);
 #pragma unroll
     for (int q = 0; q < B; ++q) {
-        if (o0 + q < m) {
-            P y = x[q];
+        P y = x[q];
 #pragma unroll
-            for (int i = 0; i < PD; ++i) y -= lv[q][i] * prev[i];
+        for (int i = 0; i < PD; ++i) y -= lv[q][i] * prev[i];
 #pragma unroll
-            for (int i = PD - 1; i > 0; --i) prev[i] = prev[i - 1];
-            prev[0] = y;
-            x[q] = y;
-        }
+        for (int i = PD - 1; i > 0; --i) prev[i] = prev[i - 1];
+        prev[0] = y;
+        x[q] = y;
     }
 }
 
-// Chunk-local forward elimination on g[0 .. m) in shared memory, 8 rows per batch of loads.
+// Backward substitution of B consecutive rows going up: x[q] is row top - q, U points at the
+// factors of row top.  prev[j] holds the result j+1 rows below.
+template <typename P, int PD, int B>
+__device__ __forceinline__ void bwd_rows(P (&x)[B], const P* U, P (&prev)[PD]) {
+    constexpr int NU = FacW<PD>::U;
+    P uv[B][NU];
+#pragma unroll
+    for (int q = 0; q < B; ++q) ldv<P, NU>(U - q * NU, uv[q]);
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        P y = x[q];
+#pragma unroll
+        for (int j = 0; j < PD; ++j) y -= uv[q][1 + j] * prev[j];
+        y *= uv[q][0];
+#pragma unroll
+        for (int j = PD - 1; j > 0; --j) prev[j] = prev[j - 1];
+        prev[0] = y;
+        x[q] = y;
+    }
+}
+
+// Chunk-local forward elimination on g[0 .. m) in shared memory: batches of 8 rows whose loads
+// are issued before the dependent FMA chain, then the remaining rows one by one.
 template <typename P, int PD>
 __device__ __forceinline__ void lu_forward(P* g, int m, const P* F) {
-    constexpr int B = 8;
+    constexpr int B = 8, NF = FacW<PD>::F;
     P prev[PD];
 #pragma unroll
     for (int i = 0; i < PD; ++i) prev[i] = P(0);
-    for (int o0 = 0; o0 < m; o0 += B) {
+    int o = 0;
+    for (; o + B <= m; o += B) {
         P gv[B];
 #pragma unroll
-        for (int q = 0; q < B; ++q) gv[q] = g[o0 + q < m ? o0 + q : m - 1];
-        forward_batch<P, PD, B>(gv, o0, m, F, prev);
+        for (int q = 0; q < B; ++q) gv[q] = g[o + q];
+        fwd_rows<P, PD, B>(gv, F + o * NF, prev);
 #pragma unroll
-        for (int q = 0; q < B; ++q)
-            if (o0 + q < m) g[o0 + q] = gv[q];
+        for (int q = 0; q < B; ++q) g[o + q] = gv[q];
+    }
+    for (; o < m; ++o) {
+        P gv[1] = {g[o]};
+        fwd_rows<P, PD, 1>(gv, F + o * NF, prev);
+        g[o] = gv[0];
     }
 }
 
-// Chunk-local backward substitution on g[0 .. m), 8 rows per batch of loads.
+// Chunk-local backward substitution on g[0 .. m), from row m-1 up, in the same batches.
 template <typename P, int PD>
 __device__ __forceinline__ void lu_backward(P* g, int m, const P* U) {
     constexpr int B = 8, NU = FacW<PD>::U;
     P prev[PD];
 #pragma unroll
     for (int i = 0; i < PD; ++i) prev[i] = P(0);
-    for (int o1 = m; o1 > 0; o1 -= B) {
-        P gv[B], uv[B][NU];
+    int top = m - 1;
+    for (; top - B + 1 >= 0; top -= B) {
+        P gv[B];
 #pragma unroll
-        for (int q = 0; q < B; ++q) {
-            const int o = o1 - 1 - q >= 0 ? o1 - 1 - q : 0;
-            gv[q] = g[o];
-            ldv<P, NU>(U + o * NU, uv[q]);
-        }
+        for (int q = 0; q < B; ++q) gv[q] = g[top - q];
+        bwd_rows<P, PD, B>(gv, U + top * NU, prev);
 #pragma unroll
-        for (int q = 0; q < B; ++q) {
-            if (o1 - 1 - q >= 0) {
-                P x = gv[q];
-#pragma unroll
-                for (int j = 0; j < PD; ++j) x -= uv[q][1 + j] * prev[j];
-                x *= uv[q][0];
-#pragma unroll
-                for (int j = PD - 1; j > 0; --j) prev[j] = prev[j - 1];
-                prev[0] = x;
-                gv[q] = x;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < B; ++q)
-            if (o1 - 1 - q >= 0) g[o1 - 1 - q] = gv[q];
+        for (int q = 0; q < B; ++q) g[top - q] = gv[q];
+    }
+    for (; top >= 0; --top) {
+        P gv[1] = {g[top]};
+        bwd_rows<P, PD, 1>(gv, U + top * NU, prev);
+        g[top] = gv[0];
     }
 }
 
-// Spike corrections g[o] -= V[o] tn + W[o] bp on g[0 .. m), 8 rows per batch of loads.
+// Spike corrections of B consecutive rows: x[q] -= V tn + W bp with the spikes of row q at Sk.
+template <typename P, int PD, int B>
+__device__ __forceinline__ void spike_rows(P (&x)[B], const P* Sk, const P* tn, const P* bp) {
+    constexpr int NS = FacW<PD>::S;
+    P sv[B][NS];
+#pragma unroll
+    for (int q = 0; q < B; ++q) ldv<P, NS>(Sk + q * NS, sv[q]);
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+#pragma unroll
+        for (int r = 0; r < PD; ++r) x[q] -= sv[q][r] * tn[r] + sv[q][PD + r] * bp[r];
+    }
+}
+
+// Spike corrections on g[0 .. m) in shared memory.
 template <typename P, int PD>
 __device__ __forceinline__ void spike_fix(P* g, int m, const P* Sk, const P* tn, const P* bp) {
     constexpr int B = 8, NS = FacW<PD>::S;
-    for (int o0 = 0; o0 < m; o0 += B) {
-        P gv[B], sv[B][NS];
+    int o = 0;
+    for (; o + B <= m; o += B) {
+        P gv[B];
 #pragma unroll
-        for (int q = 0; q < B; ++q) {
-            const int o = o0 + q < m ? o0 + q : m - 1;
-            gv[q] = g[o];
-            ldv<P, NS>(Sk + o * NS, sv[q]);
-        }
+        for (int q = 0; q < B; ++q) gv[q] = g[o + q];
+        spike_rows<P, PD, B>(gv, Sk + o * NS, tn, bp);
 #pragma unroll
-        for (int q = 0; q < B; ++q) {
-            P x = gv[q];
-#pragma unroll
-            for (int r = 0; r < PD; ++r) x -= sv[q][r] * tn[r] + sv[q][PD + r] * bp[r];
-            gv[q] = x;
-        }
-#pragma unroll
-        for (int q = 0; q < B; ++q)
-            if (o0 + q < m) g[o0 + q] = gv[q];
+        for (int q = 0; q < B; ++q) g[o + q] = gv[q];
+    }
+    for (; o < m; ++o) {
+        P gv[1] = {g[o]};
+        spike_rows<P, PD, 1>(gv, Sk + o * NS, tn, bp);
+        g[o] = gv[0];
     }
 }
 
@@ -389,8 +416,12 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
     const bool pre = a.preT != nullptr;
     const int sp = a.sp;                                           // shared-memory row stride
     P* rowbuf = reinterpret_cast<P*>(smem_raw + 128);             // [G][sp]
-    P* tbuf = rowbuf + (size_t)G * sp;                             // pre: [G + 2p][sp], rows j0-p ..
-    const FacSmem<P, PD> fm(tbuf + (pre ? (size_t)(G + 2 * PD) * sp : 0), mmax);  // factors, then pre: bands
+    // pre: T* rows j0-p .. j0+G+p-1 at stride tsp, values at column offset HO, zero halo columns
+    // on either side so that the column sweep needs no bounds checks
+    constexpr int HO = 4;
+    const int tsp = a.tsp;
+    P* tbuf = rowbuf + (size_t)G * sp;
+    const FacSmem<P, PD> fm(tbuf + (pre ? (size_t)(G + 2 * PD) * tsp : 0), mmax);  // factors, then pre: bands
     const P* __restrict__ in = pre ? v.preF : v.in;
     P* out = v.out;
     // rows of the halo block that exist (pre): lo .. hi-1
@@ -398,10 +429,14 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
 
     bool staged = true;
     if (pre) {
-        // halo rows outside the domain read as zero
+        // halo rows outside the domain read as zero; so do the PD columns left of every row
         for (int r = j0 - PD; r < j0 + rows + PD; ++r) {
-            if (r >= lo && r < hi) continue;
-            for (int x = tid; x < sp; x += blockDim.x) tbuf[(size_t)(r - (j0 - PD)) * sp + x] = P(0);
+            P* row = tbuf + (size_t)(r - (j0 - PD)) * tsp;
+            if (r >= lo && r < hi) {
+                if (tid < PD) row[HO - PD + tid] = P(0);
+            } else {
+                for (int x = tid; x < tsp; x += blockDim.x) row[x] = P(0);
+            }
         }
     }
     if (a.tma) {
@@ -420,8 +455,8 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
                 bulk_load(rowbuf + (size_t)r * sp, in + (size_t)(j0 + r) * a.pitch, (uint32_t)row_bytes, bar);
             if (pre)
                 for (int r = lo + lane; r < hi; r += 32)
-                    bulk_load(tbuf + (size_t)(r - (j0 - PD)) * sp, v.preT + (size_t)r * a.pitch, (uint32_t)row_bytes,
-                              bar);
+                    bulk_load(tbuf + (size_t)(r - (j0 - PD)) * tsp + HO, v.preT + (size_t)r * a.pitch,
+                              (uint32_t)row_bytes, bar);
         }
     } else {
         for (int r = 0; r < rows; ++r)
@@ -429,7 +464,7 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
         if (pre)
             for (int r = lo; r < hi; ++r)
                 for (int x = tid; x < N; x += blockDim.x)
-                    tbuf[(size_t)(r - (j0 - PD)) * sp + x] = v.preT[(size_t)r * a.pitch + x];
+                    tbuf[(size_t)(r - (j0 - PD)) * tsp + HO + x] = v.preT[(size_t)r * a.pitch + x];
     }
     stage_factors<P, PD>(v, mmax, fm);
     if (pre) {
@@ -456,6 +491,10 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
         return;
     }
     if (pre) {
+        // the PD columns right of every staged row read as zero (they may hold row padding)
+        for (int r = lo; r < hi; ++r)
+            if (tid < PD) tbuf[(size_t)(r - (j0 - PD)) * tsp + HO + N + tid] = P(0);
+        __syncthreads();
         // R = preFscale F + (pA1 (x) pc1 pB1) T + (pA2 (x) pc2 pB2) T, one column per thread:
         // the x bands of column x are loaded once and applied to the G + 2p staged rows, whose
         // results pass through a W-row register window that the y bands reduce.
@@ -469,16 +508,17 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
                 w1[d] = P(0);
                 w2[d] = P(0);
             }
+            const P* tcol = tbuf + HO - PD + x;
+            P* rcol = rowbuf + x;
             for (int r = 0; r < rows + 2 * PD; ++r) {
-                const P* trow = tbuf + (size_t)r * sp;
                 P t1 = 0, t2 = 0;
 #pragma unroll
                 for (int dk = 0; dk < W; ++dk) {
-                    const int xx = x + dk - PD;
-                    const P val = (xx >= 0 && xx < N) ? trow[xx] : P(0);
+                    const P val = tcol[dk];
                     t1 += a1v[dk] * val;
                     t2 += a2v[dk] * val;
                 }
+                tcol += tsp;
 #pragma unroll
                 for (int d = 0; d + 1 < W; ++d) {
                     w1[d] = w1[d + 1];
@@ -487,12 +527,12 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
                 w1[W - 1] = t1;
                 w2[W - 1] = t2;
                 if (r >= 2 * PD) {
-                    const int jl = r - 2 * PD;
-                    const P* bj = bco + (size_t)jl * 2 * W;
-                    P acc = a.preFscale * rowbuf[(size_t)jl * sp + x];
+                    const P* bj = bco + (size_t)(r - 2 * PD) * 2 * W;
+                    P acc = a.preFscale * *rcol;
 #pragma unroll
                     for (int dl = 0; dl < W; ++dl) acc += bj[dl] * w1[dl] + bj[W + dl] * w2[dl];
-                    rowbuf[(size_t)jl * sp + x] = acc;
+                    *rcol = acc;
+                    rcol += sp;
                 }
             }
         }
@@ -546,10 +586,11 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
 // y pass.  CTA = G columns x C chunks (blockDim = G*C <= 256); thread tid = k*G + c owns chunk k
 // of column c in its private shared-memory strip (odd stride: distinct banks).  The column values
 // are loaded 16 rows at a time and eliminated forward as they arrive, so the strip is written
-// once before the backward sweep; the increment base is added on the final store.
+// once before the backward sweep; the increment base is added on the final store.  Threads of
+// columns past the last line solve a copy of the last line and store nothing.
 template <typename P, int PD>
 __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
-    constexpr int W = 2 * PD + 1, B = 16;
+    constexpr int W = 2 * PD + 1, B = 16, B2 = 8;
     constexpr int NF = FacW<PD>::F, NU = FacW<PD>::U, NS = FacW<PD>::S;
     if (!scene_active(a.b)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -564,11 +605,11 @@ __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
     const int s = k * base;
     const int m = (k < C - 1) ? base : ch.last;
     const int t = chunk_type(ch, k);
-    const int line = blockIdx.x * G + c;
-    const bool valid = line < a.nlines;
+    const int line_raw = blockIdx.x * G + c;
+    const bool valid = line_raw < a.nlines;
+    const int line = valid ? line_raw : a.nlines - 1;
     const LineView<P> v = scene_line(a, arr);
     const size_t pitch = (size_t)a.pitch;
-    const P* __restrict__ src = v.in + (size_t)s * pitch + (valid ? line : 0);
     P* g = buf + (size_t)tid * mpad;
 
     stage_factors<P, PD>(v, mmax, fm);
@@ -578,31 +619,39 @@ __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
     P prev[PD];
 #pragma unroll
     for (int i = 0; i < PD; ++i) prev[i] = P(0);
-    for (int o0 = 0; o0 < m; o0 += B) {
-        P r[B];
-        if (pre) {
-            const P ps = v.prescale;
+    if (pre) {
+        // right-hand side prescale (premul band (x) I) in: rows s .. s+m-1 of the product
+        const P ps = v.prescale;
+        for (int o = 0; o < m; ++o) {
+            const int row = s + o;
+            P acc = 0;
 #pragma unroll
-            for (int q = 0; q < B; ++q) {
-                const int row = s + o0 + q;
-                P acc = 0;
-                if (valid && o0 + q < m) {
-#pragma unroll
-                    for (int d = 0; d < W; ++d) {
-                        const int rr = row + d - PD;
-                        if (rr >= 0 && rr < N) acc += pre[(size_t)row * W + d] * v.in[(size_t)rr * pitch + line];
-                    }
-                }
-                r[q] = ps * acc;
+            for (int d = 0; d < W; ++d) {
+                const int rr = row + d - PD;
+                if (rr >= 0 && rr < N) acc += pre[(size_t)row * W + d] * v.in[(size_t)rr * pitch + line];
             }
-        } else {
-#pragma unroll
-            for (int q = 0; q < B; ++q) r[q] = (valid && o0 + q < m) ? src[(size_t)(o0 + q) * pitch] : P(0);
+            P x[1] = {ps * acc};
+            fwd_rows<P, PD, 1>(x, Fk + o * NF, prev);
+            g[o] = x[0];
         }
-        forward_batch<P, PD, B>(r, o0, m, Fk, prev);
+    } else {
+        const P* __restrict__ src = v.in + (size_t)s * pitch + line;
+        int o = 0;
+        for (; o + B <= m; o += B) {
+            P r[B];
 #pragma unroll
-        for (int q = 0; q < B; ++q)
-            if (o0 + q < m) g[o0 + q] = r[q];
+            for (int q = 0; q < B; ++q) r[q] = src[q * pitch];
+            src += B * pitch;
+            fwd_rows<P, PD, B>(r, Fk + o * NF, prev);
+#pragma unroll
+            for (int q = 0; q < B; ++q) g[o + q] = r[q];
+        }
+        for (; o < m; ++o) {
+            P r[1] = {*src};
+            src += pitch;
+            fwd_rows<P, PD, 1>(r, Fk + o * NF, prev);
+            g[o] = r[0];
+        }
     }
     lu_backward<P, PD>(g, m, fm.U + t * mmax * NU);
     __syncthreads();
@@ -614,32 +663,31 @@ __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
     const P* Sk = fm.S + t * mmax * NS;
     const P* __restrict__ bs = v.base ? v.base + (size_t)s * pitch + line : nullptr;
     P* dst = v.out + (size_t)s * pitch + line;
-    const bool guard = (v.status != nullptr) && arr == 0;
     const P tmax = a.tmax;
     bool bad = false;
-    constexpr int B2 = 8;  // rows per batch of the final pass (spikes need NS registers a row)
-    for (int o0 = 0; o0 < m; o0 += B2) {
-        P b[B2], gv[B2], sv[B2][NS];
+    // final rows: spike correction, increment base, store, guard
+    auto finish = [&](auto nrows, int o) {
+        constexpr int R = decltype(nrows)::value;
+        P x[R], bv[R];
 #pragma unroll
-        for (int q = 0; q < B2; ++q) {
-            const int o = o0 + q < m ? o0 + q : m - 1;
-            b[q] = (bs && o0 + q < m) ? bs[(size_t)(o0 + q) * pitch] : P(0);
-            gv[q] = g[o];
-            ldv<P, NS>(Sk + o * NS, sv[q]);
+        for (int q = 0; q < R; ++q) {
+            x[q] = g[o + q];
+            bv[q] = bs ? bs[(size_t)q * pitch] : P(0);
         }
+        spike_rows<P, PD, R>(x, Sk + o * NS, tn, bp);
 #pragma unroll
-        for (int q = 0; q < B2; ++q) {
-            if (o0 + q < m) {
-                P x = gv[q];
-#pragma unroll
-                for (int r = 0; r < PD; ++r) x -= sv[q][r] * tn[r] + sv[q][PD + r] * bp[r];
-                x += b[q];
-                dst[(size_t)(o0 + q) * pitch] = x;
-                bad |= !(fabs(x) <= tmax);  // also catches NaN
-            }
+        for (int q = 0; q < R; ++q) {
+            const P y = x[q] + bv[q];
+            dst[(size_t)q * pitch] = y;
+            bad |= !(fabs(y) <= tmax);  // also catches NaN
         }
-    }
-    if (guard && bad) atomicOr(v.status, 1);
+        if (bs) bs += R * pitch;
+        dst += R * pitch;
+    };
+    int o = 0;
+    for (; o + B2 <= m; o += B2) finish(std::integral_constant<int, B2>{}, o);
+    for (; o < m; ++o) finish(std::integral_constant<int, 1>{}, o);
+    if (bad && v.status != nullptr && arr == 0) atomicOr(v.status, 1);
 }
 
 template <typename P, int PD, bool X>
@@ -695,8 +743,10 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         if (L < slots)
             while (sp % (2 * L) != L || (sp * sizeof(P)) % 16 != 0) ++sp;
         const size_t srow = (size_t)sp * sizeof(P);
+        const int tsp = pre ? round4(4 + a.pitch + PD) : 0;  // staged T* rows: 4 left, PD right halo
+        const size_t trow = (size_t)tsp * sizeof(P);
         auto need = [&](int g) {
-            return 128 + g * srow + (pre ? (g + 2 * PD) * srow + (size_t)g * 2 * W * sizeof(P) : 0) + fbytes;
+            return 128 + g * srow + (pre ? (g + 2 * PD) * trow + (size_t)g * 2 * W * sizeof(P) : 0) + fbytes;
         };
         // lines per CTA: up to 8 warps' worth, fewer when the staged rows need more than 100 KB
         int G = 8 * lpw;
@@ -712,6 +762,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         f.G = G;
         f.lsh = lsh;
         f.sp = sp;
+        f.tsp = tsp;
         f.tma = aligned ? 1 : 0;
         auto kern = k_xsolve_warp<P, PD>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

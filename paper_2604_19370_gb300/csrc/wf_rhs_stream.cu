@@ -40,15 +40,10 @@ namespace {
 template <typename P>
 struct PhysS {
     P K_ign, chiTamb, c_rad, T_amb, T_amb2, C_nld, c_W, T_ig, phi_min, T_a, tau_kf;
+    P K0;    // c_chi T_amb + c_rad T_amb^4: the constant part of the point source
+    P Ta_l2; // T_a log2(e)
     int heat_by_fuel;
 };
-
-template <typename P>
-__device__ __forceinline__ P expo_s(P x);
-template <>
-__device__ __forceinline__ float expo_s<float>(float x) { return __expf(x); }
-template <>
-__device__ __forceinline__ double expo_s<double>(double x) { return exp(x); }
 
 // Tables of an interior element (uniform knots: every element p <= e < n - p has the same
 // ones), carried in the kernel parameters so that the FMAs read them as constant operands.
@@ -59,6 +54,11 @@ struct ITab {
     P wq[4][4];            // Gauss weight products w_y[b] w_x[q] (every element)
     P wqc[4][4];           // -C_nld w_y[b] w_x[q]
     P wqg[4][4];           // -tau k_f w_y[b] w_x[q]
+    // interior y-test tables with the point weights folded in, [b][q][l]:
+    P ys[4][4][4];         // B_l(y_b) w_bq               (point source)
+    P yd[4][4][4];         // B_l'(y_b) w_bq (-C_nld)     (T^3 dT/dy against dB/dy)
+    P yq[4][4][4];         // B_l(y_b) w_bq (-C_nld)      (T^3 dT/dx, tested later against dB/dx)
+    P yg[4][4][4];         // B_l(y_b) w_bq (-tau k_f)    (fuel)
     int xok, yok;          // the interior tables exist (n > 2p)
 };
 
@@ -91,13 +91,20 @@ __device__ __forceinline__ P col_from(P own, P extra, int lane, int k) {
     return (lane + k < 32) ? down : wrap;
 }
 
-// -T_a / T: the FP32 path uses the fast divide (about 2 ulp), the FP64 path the exact one
+// exp(-T_a / T).  FP32: 2^(-T_a log2(e) / T) with the fast divide and the hardware base-2
+// exponential (PTX ex2.approx, relative error about 2^-22); FP64: exp of the exact quotient.
 template <typename P>
-__device__ __forceinline__ P neg_ratio(P a, P t);
+__device__ __forceinline__ P arrhenius(const PhysS<P>& c, P T);
 template <>
-__device__ __forceinline__ float neg_ratio<float>(float a, float t) { return -__fdividef(a, t); }
+__device__ __forceinline__ float arrhenius<float>(const PhysS<float>& c, float T) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-__fdividef(c.Ta_l2, T)));
+    return y;
+}
 template <>
-__device__ __forceinline__ double neg_ratio<double>(double a, double t) { return -a / t; }
+__device__ __forceinline__ double arrhenius<double>(const PhysS<double>& c, double T) {
+    return exp(-c.T_a / T);
+}
 
 // One warp: strip of 32 element columns starting at X0 - p, element rows Y0 - p .. Y1 - 1.
 // XI (fast form): every element the warp touches is interior, so all tables come from the
@@ -244,20 +251,30 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
                     bpx += fxr[r][q] * gxr[r][b];
                     bpy += fyr[r][q] * gyr[r][b];
                 }
+                // point source: K_ign E (+ c_chi T_amb + c_rad (T_amb^4 - T^4)) - c_W b'.grad T
                 const bool burn = (T > c.T_ig) && (ph > c.phi_min);
-                const P E = burn ? T * expo_s<P>(neg_ratio<P>(c.T_a, T)) : P(0);
-                const P T2 = T * T;
-                const P rad = c.c_rad * (c.T_amb2 + T2) * (c.T_amb + T) * (c.T_amb - T);
-                const P heat = c.K_ign * E * (c.heat_by_fuel ? ph : P(1));
-                const P S = it.wq[b][q] * (heat + c.chiTamb + rad - c.c_W * (bpx * Tx + bpy * Ty));
-                const P qn = it.wqc[b][q] * T2 * T;
-                const P QX = qn * Tx, QY = qn * Ty;
-                const P G = it.wqg[b][q] * E * ph;
+                const P E = burn ? T * arrhenius<P>(c, T) : P(0);
+                const P T2 = T * T, T3 = T2 * T;
+                const P EP = E * ph;
+                const P src = (c.heat_by_fuel ? c.K_ign * EP : c.K_ign * E) + (c.K0 - c.c_rad * (T2 * T2)) -
+                              c.c_W * (bpx * Tx + bpy * Ty);
+                const P t3x = T3 * Tx, t3y = T3 * Ty;
+                if constexpr (YI) {
 #pragma unroll
-                for (int l = 0; l < NB; ++l) {
-                    acs[l][q] += WF_BY(b, l) * S + WF_DY(b, l) * QY;
-                    acq[l][q] += WF_BY(b, l) * QX;
-                    acg[l][q] += WF_BY(b, l) * G;
+                    for (int l = 0; l < NB; ++l) {
+                        acs[l][q] += it.ys[b][q][l] * src + it.yd[b][q][l] * t3y;
+                        acq[l][q] += it.yq[b][q][l] * t3x;
+                        acg[l][q] += it.yg[b][q][l] * EP;
+                    }
+                } else {
+                    const P S = it.wq[b][q] * src, QX = it.wqc[b][q] * t3x, QY = it.wqc[b][q] * t3y;
+                    const P G = it.wqg[b][q] * EP;
+#pragma unroll
+                    for (int l = 0; l < NB; ++l) {
+                        acs[l][q] += WF_BY(b, l) * S + WF_DY(b, l) * QY;
+                        acq[l][q] += WF_BY(b, l) * QX;
+                        acg[l][q] += WF_BY(b, l) * G;
+                    }
                 }
             }
         }
@@ -347,10 +364,9 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
 
 // Work item = (strip, segment) of one scenario, flattened so that the warps of a CTA never
 // idle at the end of a row of strips.
-// FP32, p <= 2, wind variation of rank <= 1: three CTAs per SM (at most 168 registers a
-// thread, no spills); the rank-2 form needs more and runs two
+// FP32, p <= 2: three CTAs per SM (at most 168 registers a thread, no spills)
 template <typename P, int PD, int WR>
-__global__ void __launch_bounds__(128, (sizeof(P) == 4 && PD <= 2 && WR <= 1) ? 3 : 1)
+__global__ void __launch_bounds__(128, (sizeof(P) == 4 && PD <= 2) ? 3 : 1)
     k_rhs_stream(const StreamArgs<P> a_in) {
     if (!scene_active(a_in.b)) return;
     StreamArgs<P> a = a_in;
@@ -411,6 +427,8 @@ PhysS<P> to_phys_s(const Phys& c, double tau) {
     o.phi_min = (P)c.phi_min;
     o.T_a = (P)c.T_a;
     o.tau_kf = (P)(tau * c.k_f);
+    o.K0 = (P)(c.c_chi * c.T_amb + c.c_rad * c.T_amb * c.T_amb * c.T_amb * c.T_amb);
+    o.Ta_l2 = (P)(c.T_a * 1.4426950408889634074);  // log2(e)
     o.heat_by_fuel = c.heat_by_fuel;
     return o;
 }
@@ -477,6 +495,12 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
             a.it.wq[i][j] = (P)wq;
             a.it.wqc[i][j] = (P)(-wq * r.phys.C_nld);
             a.it.wqg[i][j] = (P)(-wq * r.tau * r.phys.k_f);
+            for (int l = 0; l < 4; ++l) {
+                a.it.ys[i][j][l] = (P)(r.ty.B[i][l] * wq);
+                a.it.yd[i][j][l] = (P)(r.ty.D[i][l] * wq * -r.phys.C_nld);
+                a.it.yq[i][j][l] = (P)(r.ty.B[i][l] * wq * -r.phys.C_nld);
+                a.it.yg[i][j][l] = (P)(r.ty.B[i][l] * wq * -(r.tau * r.phys.k_f));
+            }
         }
     }
     a.it.xok = r.tx.ok;

@@ -56,7 +56,7 @@ def test_autotune_keeps_state_and_parity(wf):
     T0, p0 = sim.state()
     shape = wf.wf_autotune(sim.h, 2)
     assert shape[0] in (0, 32, 16, 8, 4, 2, 1) and shape[1] in (0, 32, 16, 8, 4, 2, 1)
-    assert shape[2] in (0, 128, 64, 32, 16) and shape[3] in (0, 1, 2, 4)
+    assert shape[2] in (0, 128, 96, 80, 64, 56, 48, 40, 32, 28, 24, 21, 20, 16, 12) and shape[3] in (0, 1, 2, 4)
     T1, p1 = sim.state()
     assert np.array_equal(T0, T1) and np.array_equal(p0, p1)
     sim.step(4)
