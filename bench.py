@@ -306,7 +306,7 @@ def run_gpu(args) -> None:
     stream = torch.cuda.Stream(device=dev)
     wf.wf_set_stream(sim.h, stream.cuda_stream)
     # launch shapes tuned on this handle (its state is restored afterwards)
-    tuning = pick_shapes(wf, sim.h, args, 3)
+    tuning = pick_shapes(wf, sim.h, args, 6)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     props = torch.cuda.get_device_properties(dev)
 
@@ -426,6 +426,7 @@ def run_gpu(args) -> None:
                    "l2": "flushed before every timed step (256 MiB write)",
                    "launch_shapes": {"x_lines_per_cta": tuning[0], "y_lines_per_cta": tuning[1],
                                      "quadrature_segment_rows": tuning[2], "x_lines_per_warp": tuning[3],
+                                     "x2_lines_per_cta": tuning[4],
                                      "source": shape_source(args)},
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
@@ -503,7 +504,7 @@ def run_ensemble(args) -> None:
         b.load_scenario(k, sc)
     stream = torch.cuda.Stream(device=dev)
     wf.wf_set_stream(b.h, stream.cuda_stream)
-    tuning = pick_shapes(wf, b.h, args, 2)
+    tuning = pick_shapes(wf, b.h, args, 3)
     dofs = S * first.dofs
     with torch.cuda.stream(stream):
         b.step(args.warmup)
@@ -568,6 +569,7 @@ def run_ensemble(args) -> None:
                    "dofs": dofs, "l2": f"state {S} x 5 fields > L2, no flush", "parallelism": f"replicas x{world}",
                    "launch_shapes": {"x_lines_per_cta": tuning[0], "y_lines_per_cta": tuning[1],
                                      "quadrature_segment_rows": tuning[2], "x_lines_per_warp": tuning[3],
+                                     "x2_lines_per_cta": tuning[4],
                                      "source": shape_source(args)}},
         "roofline": roof,
         "step_hbm_frac": min_step_bytes(False) * dofs / (slowest / args.steps) / 1e9 / peaks["hbm_gbs"],
@@ -682,7 +684,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="launch shapes from the launchers' rules")
-    ap.add_argument("--tuning", default="", help="launch shapes x_cta,y_cta,seg,x_per_warp (skips the autotuner)")
+    ap.add_argument("--tuning", default="", help="launch shapes x_cta,y_cta,seg,x_per_warp,x2_cta (skips the autotuner)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
                     help="c2: one 1024^2 domain (default); c4: batched ensemble; c5: served request stream")
     ap.add_argument("--scenarios", type=int, default=256)

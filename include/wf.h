@@ -159,14 +159,16 @@ int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], in
 
 /*
  * Launch-shape autotuner (no counterpart in the paper, whose solver runs on
- * CPU threads).  Four shapes are tuned (int shape[4]):
- *   shape[0]  lines per CTA of the x pass (rows staged per CTA; at most
- *             8 warps' worth),
+ * CPU threads).  Five shapes are tuned (int shape[5]):
+ *   shape[0]  lines per CTA of the first x pass of a step (rows staged per
+ *             CTA; at most 8 warps' worth),
  *   shape[1]  lines per CTA of the y pass (columns per CTA, bounded by
  *             lines x chunks <= 256 threads),
  *   shape[2]  element rows per segment of the streaming quadrature kernel,
- *   shape[3]  lines per warp of the x pass (1, 2 or 4; at most 32 / chunks
- *             per line, which is also the default);
+ *   shape[3]  lines per warp of the x passes (1, 2 or 4; at most 32 / chunks
+ *             per line, which is also the default),
+ *   shape[4]  lines per CTA of the second x pass (which, for Peaceman-Rachford
+ *             with one F per step, also forms its right-hand side);
  * 0 selects the launchers' built-in rule.  wf_autotune times reps steps
  * (after one warm-up step) of the handle's active slots for each candidate,
  * keeps for every shape the value whose launches took least device time,
@@ -178,7 +180,7 @@ int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], in
  * collected under wf_set_profiling.  No active slot: WF_OK, nothing tuned.
  * Shapes never change the arithmetic of a line or an element.
  * Errors: WF_EINVAL (reps outside 1..100), WF_ENOMEM, WF_ECUDA.
- * wf_get_tuning / wf_set_tuning read and write the four values
+ * wf_get_tuning / wf_set_tuning read and write the five values
  * (wf_set_tuning: each 0..1024, else WF_EINVAL).
  */
 int wf_autotune(wf_handle* h, int reps);

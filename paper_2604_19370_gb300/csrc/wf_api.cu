@@ -30,7 +30,7 @@ using namespace wf;
 namespace {
 
 constexpr double kTmax = 1e5;  // guard on |T| (K)
-constexpr int kTune = 4;       // tuned launch shapes (wf_autotune)
+constexpr int kTune = 5;       // tuned launch shapes (wf_autotune)
 
 struct Arena {
     char* base = nullptr;
@@ -103,8 +103,9 @@ struct wf_handle {
     int S = 1;
     long long sbytes = 0;
     char* slots_mem = nullptr;  // start of slot 0's block
-    int tune[4] = {0, 0, 0, 0};  // x lines per CTA, y lines per CTA, quadrature segment rows,
-                                 // x lines per warp (0: the launchers' rules)
+    int tune[5] = {0, 0, 0, 0, 0};  // x lines per CTA (first x pass), y lines per CTA, quadrature
+                                    // segment rows, x lines per warp, x lines per CTA of the
+                                    // second x pass (0: the launchers' rules)
     void *T = nullptr, *phi = nullptr, *F = nullptr, *Phi = nullptr, *R = nullptr;
     int* status = nullptr;
     void *fxq = nullptr, *gxq = nullptr, *fyq = nullptr, *gyq = nullptr;
@@ -482,11 +483,13 @@ RhsArgs rhs_args(wf_handle* h, const void* T, void* F, void* Phi, void* R, doubl
     return a;
 }
 
-LineArgs line_args(wf_handle* h, bool xdir) {
+// xsite: 1 or 2 for the first or second x pass of a step, 0 for a y pass
+LineArgs line_args(wf_handle* h, int xsite) {
+    const bool xdir = xsite != 0;
     LineArgs a;
     memset(&a, 0, sizeof(a));
     a.nlines = xdir ? h->Ny : h->Nx;
-    a.G = xdir ? h->tune[0] : h->tune[1];
+    a.G = xsite == 1 ? h->tune[0] : (xsite == 2 ? h->tune[4] : h->tune[1]);
     a.rpw = xdir ? h->tune[3] : 0;
     a.pitch = h->pitch;
     a.tmax = kTmax;
@@ -540,18 +543,18 @@ cudaError_t enqueue_step(wf_handle* h) {
         const bool once = h->prm.F_timing == WF_F_ONCE;
         RhsArgs r1 = rhs_args(h, h->T, once ? h->F : nullptr, h->Phi, h->R, th, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
         if ((e = timed(h, S_RHS1, [&] { return launch_rhs(prec, p, r1, s); })) != cudaSuccess) return e;
-        LineArgs x1 = line_args(h, true);
+        LineArgs x1 = line_args(h, 1);
         add_line(x1, h->R, h->R, X[2], cx);
         add_line(x1, h->Phi, h->Phi, X[0], cx);
         if ((e = timed(h, S_X1, [&] { return launch_xsolve(prec, p, x1, s); })) != cudaSuccess) return e;
-        LineArgs y1 = line_args(h, false);
+        LineArgs y1 = line_args(h, 0);
         add_line(y1, h->R, h->T, Y[0], cy, h->T);
         if (once) add_line(y1, h->Phi, h->phi, Y[0], cy, h->phi);
         if ((e = timed(h, S_Y1, [&] { return launch_ysolve(prec, p, y1, s); })) != cudaSuccess) return e;
         bool fused = false;
         if (once) {
             // substep 2 in one x pass: R = th F + (op1_x (x) M^y) T* + (M^x (x) op1_y) T*, then M^x lines
-            LineArgs x2 = line_args(h, true);
+            LineArgs x2 = line_args(h, 2);
             add_line(x2, nullptr, h->R, X[0], cx);
             x2.preT = h->T;
             x2.preF = h->F;
@@ -589,11 +592,11 @@ cudaError_t enqueue_step(wf_handle* h) {
             if ((e = timed(h, S_RHS2, [&] { return launch_rhs(prec, p, r2, s); })) != cudaSuccess) return e;
         }
         if (!fused) {
-            LineArgs x2 = line_args(h, true);
+            LineArgs x2 = line_args(h, 2);
             add_line(x2, h->R, h->R, X[0], cx);
             if ((e = timed(h, S_X2, [&] { return launch_xsolve(prec, p, x2, s); })) != cudaSuccess) return e;
         }
-        LineArgs y2 = line_args(h, false);
+        LineArgs y2 = line_args(h, 0);
         add_line(y2, h->R, h->T, Y[2], cy, h->T);
         if (!once) add_line(y2, h->Phi, h->phi, Y[0], cy, h->phi);
         y2.status = h->status;
@@ -604,22 +607,22 @@ cudaError_t enqueue_step(wf_handle* h) {
     const double half = 0.5 * h->dt;
     RhsArgs r1 = rhs_args(h, h->T, nullptr, h->Phi, h->R, half, X[1], Y[0], 2.0, nullptr, nullptr, 0.0);
     if ((e = timed(h, S_RHS1, [&] { return launch_rhs(prec, p, r1, s); })) != cudaSuccess) return e;
-    LineArgs x1 = line_args(h, true);
+    LineArgs x1 = line_args(h, 1);
     add_line(x1, h->R, h->R, X[2], cx);
     add_line(x1, h->Phi, h->Phi, X[0], cx);
     if ((e = timed(h, S_X1, [&] { return launch_xsolve(prec, p, x1, s); })) != cudaSuccess) return e;
-    LineArgs y1 = line_args(h, false);
+    LineArgs y1 = line_args(h, 0);
     add_line(y1, h->R, h->T, Y[0], cy, h->T);
     if ((e = timed(h, S_Y1, [&] { return launch_ysolve(prec, p, y1, s); })) != cudaSuccess) return e;
-    LineArgs yy = line_args(h, false);
+    LineArgs yy = line_args(h, 0);
     add_line(yy, h->T, h->T, Y[2], cy, h->T, Y[1].bandP, 2.0);
     if ((e = timed(h, S_Y2PRE, [&] { return launch_ysolve(prec, p, yy, s); })) != cudaSuccess) return e;
     RhsArgs r2 = rhs_args(h, h->T, nullptr, nullptr, h->R, half, X[1], Y[0], 2.0, nullptr, nullptr, 0.0);
     if ((e = timed(h, S_RHS2, [&] { return launch_rhs(prec, p, r2, s); })) != cudaSuccess) return e;
-    LineArgs x2 = line_args(h, true);
+    LineArgs x2 = line_args(h, 2);
     add_line(x2, h->R, h->R, X[2], cx);
     if ((e = timed(h, S_X2, [&] { return launch_xsolve(prec, p, x2, s); })) != cudaSuccess) return e;
-    LineArgs y2 = line_args(h, false);
+    LineArgs y2 = line_args(h, 0);
     add_line(y2, h->R, h->T, Y[0], cy, h->T);
     add_line(y2, h->Phi, h->phi, Y[0], cy, h->phi);
     y2.status = h->status;
@@ -1063,14 +1066,15 @@ int wf_autotune(wf_handle* h, int reps) {
     for (int z = 0; z < h->S; ++z) any = any || h->active_host[z];
     if (!any) return WF_OK;
     // each row is one candidate run; -1 keeps a shape at its best value so far.  The x lines
-    // per warp are tuned after the x lines per CTA they depend on; segment heights also take
+    // per warp (both x passes) are tuned after the x lines per CTA they depend on; segment heights also take
     // values between the powers of two, because the number of (strip, segment) work items
     // against the resident warps decides how full the last wave is.
     constexpr int kRuns = 15;
     static const int kCands[kRuns][kTune] = {
-        {0, 0, 0, 0},      {32, 32, 128, -1}, {16, 16, 64, -1},  {8, 8, 32, -1},    {4, 4, 16, -1},
-        {2, 2, 96, -1},    {1, 1, 48, -1},    {-1, -1, 40, 1},   {-1, -1, 24, 2},   {-1, -1, 20, 4},
-        {-1, -1, 80, -1},  {-1, -1, 28, -1},  {-1, -1, 21, -1},  {-1, -1, 56, -1},  {-1, -1, 12, -1}};
+        {0, 0, 0, 0, 0},       {32, 32, 128, -1, 32}, {16, 16, 64, -1, 16}, {8, 8, 32, -1, 8},
+        {4, 4, 16, -1, 4},     {2, 2, 96, -1, 2},     {1, 1, 48, -1, 1},    {-1, -1, 40, 1, -1},
+        {-1, -1, 24, 2, -1},   {-1, -1, 20, 4, -1},   {-1, -1, 80, -1, -1}, {-1, -1, 28, -1, -1},
+        {-1, -1, 21, -1, -1},  {-1, -1, 56, -1, -1},  {-1, -1, 12, -1, -1}};
     const size_t bytes = (size_t)h->sbytes * h->S;
     void* snap = nullptr;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;
@@ -1103,8 +1107,8 @@ int wf_autotune(wf_handle* h, int reps) {
             rc = WF_ECUDA;
             break;
         }
-        const double tx = ms[S_X1] + ms[S_X2];
-        const double t[kTune] = {tx, ms[S_Y1] + ms[S_Y2PRE] + ms[S_Y3], ms[S_RHS1] + ms[S_RHS2], tx};
+        const double t[kTune] = {ms[S_X1], ms[S_Y1] + ms[S_Y2PRE] + ms[S_Y3], ms[S_RHS1] + ms[S_RHS2],
+                                 ms[S_X1] + ms[S_X2], ms[S_X2]};
         for (int q = 0; q < kTune; ++q)
             if (fresh[q] && t[q] < best_t[q]) {
                 best_t[q] = t[q];

@@ -495,11 +495,29 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
         for (int r = lo; r < hi; ++r)
             if (tid < PD) tbuf[(size_t)(r - (j0 - PD)) * tsp + HO + N + tid] = P(0);
         __syncthreads();
-        // R = preFscale F + (pA1 (x) pc1 pB1) T + (pA2 (x) pc2 pB2) T, one column per thread:
-        // the x bands of column x are loaded once and applied to the G + 2p staged rows, whose
-        // results pass through a W-row register window that the y bands reduce.
+        // R = preFscale F + (pA1 (x) pc1 pB1) T + (pA2 (x) pc2 pB2) T.  Work item = one column and
+        // a group of rh output rows: the x bands of the column are loaded once and applied to the
+        // rh + 2p staged rows the group needs, whose results pass through a W-row register window
+        // that the y bands reduce.  The number of row groups nh balances N * nh items over the
+        // CTA's threads against the 2p rows each group re-reads.
         const P* __restrict__ bco = fm.end();  // [G][2][W], scaled by pc1 / pc2
-        for (int x = tid; x < N; x += blockDim.x) {
+        const int nt = blockDim.x;
+        int nh = 1, rh = rows;
+        {
+            long best = (long)((N + nt - 1) / nt) * (rows + 2 * PD);
+            for (int cand = 2; cand <= 8 && cand <= rows; cand *= 2) {
+                const int h = (rows + cand - 1) / cand;
+                const long cost = (long)((N * cand + nt - 1) / nt) * (h + 2 * PD);
+                if (cost < best) {
+                    best = cost;
+                    nh = cand;
+                    rh = h;
+                }
+            }
+        }
+        for (int item = tid; item < N * nh; item += nt) {
+            const int grp = item / N, x = item - grp * N;
+            const int r0 = grp * rh, r1 = min(rows, r0 + rh);
             P a1v[W], a2v[W], w1[W], w2[W];
 #pragma unroll
             for (int d = 0; d < W; ++d) {
@@ -508,9 +526,9 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
                 w1[d] = P(0);
                 w2[d] = P(0);
             }
-            const P* tcol = tbuf + HO - PD + x;
-            P* rcol = rowbuf + x;
-            for (int r = 0; r < rows + 2 * PD; ++r) {
+            const P* tcol = tbuf + (size_t)r0 * tsp + HO - PD + x;
+            P* rcol = rowbuf + (size_t)r0 * sp + x;
+            for (int r = r0; r < r1 + 2 * PD; ++r) {
                 P t1 = 0, t2 = 0;
 #pragma unroll
                 for (int dk = 0; dk < W; ++dk) {
@@ -526,7 +544,7 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
                 }
                 w1[W - 1] = t1;
                 w2[W - 1] = t2;
-                if (r >= 2 * PD) {
+                if (r >= r0 + 2 * PD) {
                     const P* bj = bco + (size_t)(r - 2 * PD) * 2 * W;
                     P acc = a.preFscale * *rcol;
 #pragma unroll

@@ -217,23 +217,24 @@ def wf_kernel_times(h, max_k: int = 16):
     return out
 
 
-def wf_autotune(h, reps: int = 3) -> Tuple[int, int, int, int]:
+def wf_autotune(h, reps: int = 3) -> Tuple[int, int, int, int, int]:
     """Tune the launch shapes of a handle on its active slots.
 
-    Returns (x lines per CTA, y lines per CTA, quadrature segment rows, x lines per warp).
+    Returns (x lines per CTA, y lines per CTA, quadrature segment rows, x lines per warp,
+    second-x-pass lines per CTA).
     """
     _check(lib().wf_autotune(h, reps), "wf_autotune")
     return wf_get_tuning(h)
 
 
-def wf_get_tuning(h) -> Tuple[int, int, int, int]:
-    out = (ctypes.c_int * 4)()
+def wf_get_tuning(h) -> Tuple[int, int, int, int, int]:
+    out = (ctypes.c_int * 5)()
     _check(lib().wf_get_tuning(h, out), "wf_get_tuning")
     return tuple(int(v) for v in out)
 
 
 def wf_set_tuning(h, shape) -> None:
-    arr = (ctypes.c_int * 4)(*[int(v) for v in shape])
+    arr = (ctypes.c_int * 5)(*[int(v) for v in shape])
     _check(lib().wf_set_tuning(h, arr), "wf_set_tuning")
 
 
