@@ -1093,11 +1093,13 @@ int wf_autotune(wf_handle* h, int reps) {
     h->profiling = true;
     double ms[S_NSITES];
     int cnt[S_NSITES];
-    for (int c = 0; c < kRuns && rc == WF_OK; ++c) {
+    // two sweeps over the candidates; each shape keeps the least time any sweep measured for it
+    for (int c = 0; c < 2 * kRuns && rc == WF_OK; ++c) {
+        const int cand = c % kRuns;
         bool fresh[kTune];
         for (int q = 0; q < kTune; ++q) {
-            fresh[q] = kCands[c][q] >= 0;
-            h->tune[q] = fresh[q] ? kCands[c][q] : best_v[q];
+            fresh[q] = kCands[cand][q] >= 0;
+            h->tune[q] = fresh[q] ? kCands[cand][q] : best_v[q];
         }
         for (int k = 0; k <= reps && rc == WF_OK; ++k) {
             if (k == 1) wf_kernel_times(h, nullptr, nullptr, nullptr, 0);  // drop the warm-up step

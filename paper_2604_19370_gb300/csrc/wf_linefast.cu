@@ -286,7 +286,7 @@ __device__ __forceinline__ void spike_rows(P (&x)[B], const P* Sk, const P* tn, 
 #pragma unroll
     for (int q = 0; q < B; ++q) {
 #pragma unroll
-        for (int r = 0; r < PD; ++r) x[q] -= sv[q][r] * tn[r] + sv[q][PD + r] * bp[r];
+        for (int r = 0; r < PD; ++r) x[q] = fma(-sv[q][r], tn[r], fma(-sv[q][PD + r], bp[r], x[q]));
     }
 }
 
@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
                     const P* bj = bco + (size_t)(r - 2 * PD) * 2 * W;
                     P acc = a.preFscale * *rcol;
 #pragma unroll
-                    for (int dl = 0; dl < W; ++dl) acc += bj[dl] * w1[dl] + bj[W + dl] * w2[dl];
+                    for (int dl = 0; dl < W; ++dl) acc = fma(bj[dl], w1[dl], fma(bj[W + dl], w2[dl], acc));
                     *rcol = acc;
                     rcol += sp;
                 }

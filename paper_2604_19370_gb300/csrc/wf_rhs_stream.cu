@@ -203,8 +203,8 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
 #pragma unroll
         for (int k = 1; k <= PD; ++k) {
             const P up = __shfl_up_sync(FULL, w.t0, k);
-            s1 += a1[PD - k] * up + a1[PD + k] * ct[k];
-            s2 += a2[PD - k] * up + a2[PD + k] * ct[k];
+            s1 = fma(a1[PD - k], up, fma(a1[PD + k], ct[k], s1));
+            s2 = fma(a2[PD - k], up, fma(a2[PD + k], ct[k], s2));
         }
         w1 = s1;
         w2 = s2;
@@ -256,13 +256,13 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
                 const P E = burn ? T * arrhenius<P>(c, T) : P(0);
                 const P T2 = T * T, T3 = T2 * T;
                 const P EP = E * ph;
-                const P src = (c.heat_by_fuel ? c.K_ign * EP : c.K_ign * E) + (c.K0 - c.c_rad * (T2 * T2)) -
-                              c.c_W * (bpx * Tx + bpy * Ty);
+                P src = fma(c.K_ign, c.heat_by_fuel ? EP : E, fma(-c.c_rad, T2 * T2, c.K0));
+                if (WR > 0) src = fma(-c.c_W, fma(bpx, Tx, bpy * Ty), src);
                 const P t3x = T3 * Tx, t3y = T3 * Ty;
                 if constexpr (YI) {
 #pragma unroll
                     for (int l = 0; l < NB; ++l) {
-                        acs[l][q] += it.ys[b][q][l] * src + it.yd[b][q][l] * t3y;
+                        acs[l][q] = fma(it.ys[b][q][l], src, fma(it.yd[b][q][l], t3y, acs[l][q]));
                         acq[l][q] += it.yq[b][q][l] * t3x;
                         acg[l][q] += it.yg[b][q][l] * EP;
                     }
@@ -271,7 +271,7 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
                     const P G = it.wqg[b][q] * EP;
 #pragma unroll
                     for (int l = 0; l < NB; ++l) {
-                        acs[l][q] += WF_BY(b, l) * S + WF_DY(b, l) * QY;
+                        acs[l][q] = fma(WF_BY(b, l), S, fma(WF_DY(b, l), QY, acs[l][q]));
                         acq[l][q] += WF_BY(b, l) * QX;
                         acg[l][q] += WF_BY(b, l) * G;
                     }
@@ -317,7 +317,7 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
                     const P s = (k == 0) ? acs[0][q] : __shfl_up_sync(FULL, acs[0][q], k);
                     const P u = (k == 0) ? acq[0][q] : __shfl_up_sync(FULL, acq[0][q], k);
                     const P g = (k == 0) ? acg[0][q] : __shfl_up_sync(FULL, acg[0][q], k);
-                    Fv += WF_TBX(k, q) * s + WF_TDX(k, q) * u;
+                    Fv = fma(WF_TBX(k, q), s, fma(WF_TDX(k, q), u, Fv));
                     Ph += WF_TBX(k, q) * g;
                 }
             }
@@ -332,7 +332,7 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
                         r1 += a.B1[(size_t)ey * W + d] * cw1[d];
                         if (a.A2) r2 += a.B2[(size_t)ey * W + d] * cw2[d];
                     }
-                    a.R[g] = a.Rscale * Fv + a.c1 * r1 + a.c2 * r2;
+                    a.R[g] = fma(a.Rscale, Fv, fma(a.c1, r1, a.c2 * r2));
                 }
             }
         }
