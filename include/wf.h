@@ -169,10 +169,10 @@ int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], in
  *             per line, which is also the default),
  *   shape[4]  lines per CTA of the second x pass (which, for Peaceman-Rachford
  *             with one F per step, also forms its right-hand side);
- * 0 selects the launchers' built-in rule.  wf_autotune times reps steps
- * (after one warm-up step) of the handle's active slots for each candidate,
- * in two sweeps over the candidate list, and keeps for every shape the value
- * whose launches took least device time,
+ * 0 selects the launchers' built-in rule.  wf_autotune tunes one shape at a
+ * time (two sweeps, the others held at their best values): for each
+ * candidate it times reps steps (after one warm-up step) of the handle's
+ * active slots and keeps the value whose step took least device time,
  * and restores every slot's device state afterwards, so the trajectory is
  * unchanged.  It needs a temporary device copy of the slot blocks
  * (S x the per-slot bytes, freed before return; WF_ENOMEM if it cannot be

@@ -344,6 +344,13 @@ int build_tables(wf_handle* h) {
                     it.D[a][k] = td[a * NB + k];
                 }
         }
+        // an interior row of the mass matrix (assembled from the same element tables)
+        const int W = 2 * h->p + 1;
+        if (d->N >= 4 * h->p + 1) {
+            WF_TRY(cudaMemcpyAsync(it.Mb, d->M64 + (size_t)(2 * h->p) * W, sizeof(double) * W,
+                                   cudaMemcpyDeviceToHost, s));
+            WF_TRY(cudaStreamSynchronize(s));
+        }
     }
     return WF_OK;
 }
@@ -1053,76 +1060,81 @@ int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], in
 
 // ---- autotuner ---------------------------------------------------------------------
 //
-// Launch shapes (x lines per CTA, y lines per CTA, rows per quadrature segment) are chosen
-// per handle by timing whole steps of the handle itself: the slot blocks are saved, every
-// candidate runs warm-up + `reps` eager steps with a CUDA event pair around each launch,
-// each parameter takes the value whose launches took least time, and the blocks are
-// restored, so the state after wf_autotune equals the state before it.  Candidate 0 is the
-// launchers' own rule.
+// Launch shapes are chosen per handle by timing whole steps of the handle itself: the slot
+// blocks are saved, every candidate runs warm-up + `reps` eager steps with a CUDA event pair
+// around each launch, and the blocks are restored after each candidate, so the state after
+// wf_autotune equals the state before it.  Value 0 of each shape is the launchers' own rule.
 
 int wf_autotune(wf_handle* h, int reps) {
     if (!h || reps < 1 || reps > 100) return WF_EINVAL;
     bool any = false;
     for (int z = 0; z < h->S; ++z) any = any || h->active_host[z];
     if (!any) return WF_OK;
-    // each row is one candidate run; -1 keeps a shape at its best value so far.  The x lines
-    // per warp (both x passes) are tuned after the x lines per CTA they depend on; segment heights also take
-    // values between the powers of two, because the number of (strip, segment) work items
-    // against the resident warps decides how full the last wave is.
-    constexpr int kRuns = 15;
-    static const int kCands[kRuns][kTune] = {
-        {0, 0, 0, 0, 0},       {32, 32, 128, -1, 32}, {16, 16, 64, -1, 16}, {8, 8, 32, -1, 8},
-        {4, 4, 16, -1, 4},     {2, 2, 96, -1, 2},     {1, 1, 48, -1, 1},    {-1, -1, 40, 1, -1},
-        {-1, -1, 24, 2, -1},   {-1, -1, 20, 4, -1},   {-1, -1, 80, -1, -1}, {-1, -1, 28, -1, -1},
-        {-1, -1, 21, -1, -1},  {-1, -1, 56, -1, -1},  {-1, -1, 12, -1, -1}};
+    // Coordinate search: one shape at a time, in launch order, the others held at their best
+    // values; a candidate is judged by the device time of the whole step, because a shape
+    // also changes what the next kernel finds in L2.  Two sweeps.  Segment heights include
+    // values between the powers of two: the number of (strip, segment) work items against
+    // the resident warps decides how full the last wave is.
+    static const int kSeg[] = {0, 128, 96, 80, 64, 56, 48, 40, 32, 28, 24, 21, 20, 16, 12};
+    static const int kLines[] = {0, 32, 16, 8, 4, 2, 1};
+    static const int kRpw[] = {0, 1, 2, 4};
+    struct Axis {
+        int q;
+        const int* v;
+        int n;
+    };
+    const Axis order[] = {{2, kSeg, (int)(sizeof(kSeg) / sizeof(int))},
+                          {0, kLines, (int)(sizeof(kLines) / sizeof(int))},
+                          {3, kRpw, (int)(sizeof(kRpw) / sizeof(int))},
+                          {1, kLines, (int)(sizeof(kLines) / sizeof(int))},
+                          {4, kLines, (int)(sizeof(kLines) / sizeof(int))}};
     const size_t bytes = (size_t)h->sbytes * h->S;
     void* snap = nullptr;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;
     if (cudaMalloc(&snap, bytes) != cudaSuccess) return WF_ENOMEM;
     int rc = WF_OK;
     const bool was_profiling = h->profiling;
-    int saved[kTune], best_v[kTune];
-    double best_t[kTune];
-    for (int q = 0; q < kTune; ++q) {
-        saved[q] = best_v[q] = h->tune[q];
-        best_t[q] = 1e300;
-    }
+    int saved[kTune], best[kTune];
+    for (int q = 0; q < kTune; ++q) saved[q] = best[q] = h->tune[q];
     if (cudaMemcpyAsync(snap, h->slots_mem, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
         rc = WF_ECUDA;
     drop_graphs(h);
     h->profiling = true;
     double ms[S_NSITES];
     int cnt[S_NSITES];
-    // two sweeps over the candidates; each shape keeps the least time any sweep measured for it
-    for (int c = 0; c < 2 * kRuns && rc == WF_OK; ++c) {
-        const int cand = c % kRuns;
-        bool fresh[kTune];
-        for (int q = 0; q < kTune; ++q) {
-            fresh[q] = kCands[cand][q] >= 0;
-            h->tune[q] = fresh[q] ? kCands[cand][q] : best_v[q];
-        }
-        for (int k = 0; k <= reps && rc == WF_OK; ++k) {
+    // device time of reps steps (after one warm-up step) with the shapes in h->tune
+    auto measure = [&](double* t) -> int {
+        for (int k = 0; k <= reps; ++k) {
             if (k == 1) wf_kernel_times(h, nullptr, nullptr, nullptr, 0);  // drop the warm-up step
-            if (enqueue_step(h) != cudaSuccess) rc = WF_ECUDA;
+            if (enqueue_step(h) != cudaSuccess) return WF_ECUDA;
         }
-        if (rc != WF_OK || wf_kernel_times(h, ms, cnt, nullptr, S_NSITES) < 0) {
-            rc = WF_ECUDA;
-            break;
-        }
-        const double t[kTune] = {ms[S_X1], ms[S_Y1] + ms[S_Y2PRE] + ms[S_Y3], ms[S_RHS1] + ms[S_RHS2],
-                                 ms[S_X1] + ms[S_X2], ms[S_X2]};
-        for (int q = 0; q < kTune; ++q)
-            if (fresh[q] && t[q] < best_t[q]) {
-                best_t[q] = t[q];
-                best_v[q] = h->tune[q];
-            }
+        if (wf_kernel_times(h, ms, cnt, nullptr, S_NSITES) < 0) return WF_ECUDA;
+        *t = 0.0;
+        for (int k = 0; k < S_NSITES; ++k) *t += ms[k];
         if (cudaMemcpyAsync(h->slots_mem, snap, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
-            rc = WF_ECUDA;
-    }
+            return WF_ECUDA;
+        return WF_OK;
+    };
+    for (int sweep = 0; sweep < 2 && rc == WF_OK; ++sweep)
+        for (const Axis& ax : order) {
+            double best_t = 1e300;
+            int best_v = best[ax.q];
+            for (int i = 0; i < ax.n && rc == WF_OK; ++i) {
+                for (int q = 0; q < kTune; ++q) h->tune[q] = best[q];
+                h->tune[ax.q] = ax.v[i];
+                double t = 0.0;
+                rc = measure(&t);
+                if (rc == WF_OK && t < best_t) {
+                    best_t = t;
+                    best_v = ax.v[i];
+                }
+            }
+            best[ax.q] = best_v;
+        }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = WF_ECUDA;
     cudaFree(snap);
     h->profiling = was_profiling;
-    for (int q = 0; q < kTune; ++q) h->tune[q] = rc == WF_OK ? best_v[q] : saved[q];
+    for (int q = 0; q < kTune; ++q) h->tune[q] = rc == WF_OK ? best[q] : saved[q];
     drop_graphs(h);
     return rc;
 }

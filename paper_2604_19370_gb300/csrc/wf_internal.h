@@ -115,6 +115,7 @@ struct ElemTabs {
     int ok;                   // n > 2p (interior elements exist)
     double B[4][4], D[4][4];  // [Gauss point][local basis], as in the device tables
     double w[4];              // Gauss weight x element length
+    double Mb[8];             // band of an interior row of the 1-D mass matrix (rows 2p .. N-1-2p)
 };
 
 struct RhsArgs {

@@ -59,6 +59,9 @@ struct ITab {
     P yd[4][4][4];         // B_l'(y_b) w_bq (-C_nld)     (T^3 dT/dy against dB/dy)
     P yq[4][4][4];         // B_l(y_b) w_bq (-C_nld)      (T^3 dT/dx, tested later against dB/dx)
     P yg[4][4][4];         // B_l(y_b) w_bq (-tau k_f)    (fuel)
+    // interior rows of the 1-D mass matrices (rows 2p .. N-1-2p are all equal): the x band
+    // A2 = M^x of the second explicit product and the y band B1 = M^y of the first
+    P mbx[8], mby[8];
     int xok, yok;          // the interior tables exist (n > 2p)
 };
 
@@ -129,12 +132,18 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
     const P* __restrict__ Dxe = a.Dx + (size_t)(ex_ok ? ex : 0) * Q * NB;
 #define WF_BX(q, k) (XI ? it.bx[q][k] : (ex_ok ? __ldg(Bxe + (q) * NB + (k)) : P(0)))
 #define WF_DX(q, k) (XI ? it.dx[q][k] : (ex_ok ? __ldg(Dxe + (q) * NB + (k)) : P(0)))
-    P a1[W], a2[W];
+    // x bands of the DOF column (A1 per scenario; A2 = M^x, from the parameter block on interior
+    // strips), and, on interior strips, the y band B2 of the interior DOF rows (per scenario)
+    // (the rank-2 wind form keeps the general code here: it has no registers to spare)
+    constexpr bool HB2 = XI && WR < 2;
+    P a1[W], a2r[W], b2i[W];
 #pragma unroll
     for (int d = 0; d < W; ++d) {
         a1[d] = cc_ok ? a.A1[(size_t)cc * W + d] : P(0);
-        a2[d] = (cc_ok && a.A2) ? a.A2[(size_t)cc * W + d] : P(0);
+        a2r[d] = (!HB2 && cc_ok && a.A2) ? a.A2[(size_t)cc * W + d] : P(0);
+        b2i[d] = (HB2 && a.A2) ? a.B2[(size_t)(2 * PD) * W + d] : P(0);
     }
+#define WF_A2(d) (HB2 ? it.mbx[d] : a2r[d])
     P fxr[WR > 0 ? WR : 1][Q], fyr[WR > 0 ? WR : 1][Q];
 #pragma unroll
     for (int r = 0; r < WR; ++r)
@@ -199,12 +208,12 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
             dv[q] = sd;
             pv[q] = sp;
         }
-        P s1 = a1[PD] * w.t0, s2 = a2[PD] * w.t0;
+        P s1 = a1[PD] * w.t0, s2 = WF_A2(PD) * w.t0;
 #pragma unroll
         for (int k = 1; k <= PD; ++k) {
             const P up = __shfl_up_sync(FULL, w.t0, k);
             s1 = fma(a1[PD - k], up, fma(a1[PD + k], ct[k], s1));
-            s2 = fma(a2[PD - k], up, fma(a2[PD + k], ct[k], s2));
+            s2 = fma(WF_A2(PD - k), up, fma(WF_A2(PD + k), ct[k], s2));
         }
         w1 = s1;
         w2 = s2;
@@ -327,10 +336,18 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
                 if (a.Phi) a.Phi[g] = Ph;
                 if (a.R) {
                     P r1 = 0, r2 = 0;
+                    if constexpr (HB2) {
 #pragma unroll
-                    for (int d = 0; d < W; ++d) {
-                        r1 += a.B1[(size_t)ey * W + d] * cw1[d];
-                        if (a.A2) r2 += a.B2[(size_t)ey * W + d] * cw2[d];
+                        for (int d = 0; d < W; ++d) {
+                            r1 = fma(it.mby[d], cw1[d], r1);
+                            r2 = fma(b2i[d], cw2[d], r2);
+                        }
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < W; ++d) {
+                            r1 += a.B1[(size_t)ey * W + d] * cw1[d];
+                            if (a.A2) r2 += a.B2[(size_t)ey * W + d] * cw2[d];
+                        }
                     }
                     a.R[g] = fma(a.Rscale, Fv, fma(a.c1, r1, a.c2 * r2));
                 }
@@ -360,6 +377,7 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
 #undef WF_DX
 #undef WF_TBX
 #undef WF_TDX
+#undef WF_A2
 }
 
 // Work item = (strip, segment) of one scenario, flattened so that the warps of a CTA never
@@ -502,6 +520,10 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
                 a.it.yg[i][j][l] = (P)(r.ty.B[i][l] * wq * -(r.tau * r.phys.k_f));
             }
         }
+    }
+    for (int d = 0; d < 8; ++d) {
+        a.it.mbx[d] = (P)r.tx.Mb[d];
+        a.it.mby[d] = (P)r.ty.Mb[d];
     }
     a.it.xok = r.tx.ok;
     a.it.yok = r.ty.ok;
