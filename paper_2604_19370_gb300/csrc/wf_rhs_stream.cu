@@ -380,11 +380,11 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
 #undef WF_A2
 }
 
-// Work item = (strip, segment) of one scenario, flattened so that the warps of a CTA never
-// idle at the end of a row of strips.
-// FP32, p <= 2: three CTAs per SM (at most 168 registers a thread, no spills)
+// Work item = (strip, segment) of one scenario, flattened, interior segments first and the
+// short boundary segments last, so that they fill the tail of the launch.  One warp per CTA, so that a warp slot frees as soon as its own item ends.  FP32, p <= 2:
+// twelve warps per SM (at most 168 registers a thread, no spills).
 template <typename P, int PD, int WR>
-__global__ void __launch_bounds__(128, (sizeof(P) == 4 && PD <= 2) ? 3 : 1)
+__global__ void __launch_bounds__(32, (sizeof(P) == 4 && PD <= 2) ? 12 : 1)
     k_rhs_stream(const StreamArgs<P> a_in) {
     if (!scene_active(a_in.b)) return;
     StreamArgs<P> a = a_in;
@@ -412,17 +412,17 @@ __global__ void __launch_bounds__(128, (sizeof(P) == 4 && PD <= 2) ? 3 : 1)
     if (!a.split) {
         Y0 = sg * a.seg;
         Y1 = min(Y0 + a.seg, a.Ny);
-    } else if (sg == 0) {
-        Y0 = 0;
-        Y1 = 2 * PD;
-    } else if (sg == a.nsegs - 1) {
-        Y0 = a.Ny - 2 * PD;
-        Y1 = a.Ny;
-    } else {
-        // element rows Y0 - p .. Y1 - 1 all lie in [p, ny - p)
-        Y0 = 2 * PD + (sg - 1) * a.seg;
+    } else if (sg < a.nsegs - 2) {
+        // interior segments first (the long items), element rows Y0 - p .. Y1 - 1 in [p, ny - p)
+        Y0 = 2 * PD + sg * a.seg;
         Y1 = min(Y0 + a.seg, a.Ny - 2 * PD);
         yint = true;
+    } else if (sg == a.nsegs - 2) {
+        Y0 = 0;
+        Y1 = 2 * PD;
+    } else {
+        Y0 = a.Ny - 2 * PD;
+        Y1 = a.Ny;
     }
     const bool xint = a_in.it.xok && X0 >= 2 * PD && X0 + 31 < a.nx;
     if (xint && yint)
@@ -453,7 +453,7 @@ PhysS<P> to_phys_s(const Phys& c, double tau) {
 
 template <typename P, int PD, int WR>
 cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
-    constexpr int WARPS = 4;
+    constexpr int WARPS = 1;
     StreamArgs<P> a;
     a.nx = r.nx;
     a.ny = r.ny;
@@ -461,16 +461,15 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
     a.Ny = r.Ny;
     a.pitch = r.pitch;
     a.nstrips = (r.Nx + (32 - PD) - 1) / (32 - PD);
-    // segment height: about one wave of 2 CTAs per SM (the register budget allows two),
-    // at least 16 rows so the p halo rows stay a small overhead
+    // segment height: the largest power of two from 128 down to 16 that still gives every
+    // resident warp (twelve per SM) an item
     int sms = 152;
     {
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     int seg = 128;
-    while (seg > 16 && 10 * (((long)a.nstrips * ((r.Ny + seg - 1) / seg) + WARPS - 1) / WARPS) * r.b.S < 18L * sms)
-        seg /= 2;
+    while (seg > 16 && (long)a.nstrips * ((r.Ny + seg - 1) / seg) * r.b.S < 12L * sms) seg /= 2;
     if (r.seg > 0) seg = r.seg;
     a.seg = seg;
     a.T = (const P*)r.T;
