@@ -22,6 +22,12 @@ tau/4 (F^{n+1/2} + F^n) -> tau/2 F(T^n), tau/4 (F^{n+1} + F^{n+1/2}) -> tau/2 F(
     (M^x (x) Y(tau/2,+)) T**     = (M^x (x) Y(tau/2,-)) T*
     (X(tau/4,+) (x) M^y) T^{n+1} = (X(tau/4,-) (x) M^y) T** + tau/2 F(T**)
 
+Explicit L2 projection (the explicit dynamics of Sec. 6, the scheme the Sec. 7
+listing runs; the comparator of the convergence study): every term at T^n,
+    (M^x (x) M^y) T^{n+1} = (M^x (x) M^y) T^n - tau (A_x (x) M^y + M^x (x) A_y) T^n + tau F(T^n)
+with A_x = C_d K^x + c_W b_x G^x + c_chi M^x and A_y = C_d K^y + c_W b_y G^y, written
+with the operators above as (X(tau,-) (x) M^y) T + (M^x (x) Y(tau,-)) T - (M^x (x) M^y) T.
+
 Fuel (listing "compute_rhs"): (M^x (x) M^y) phi^{n+1} = Phi(T^n, phi^n), once
 per step with the full tau; phi^n is the fuel seen by every F of the step.
 
@@ -57,7 +63,7 @@ class Problem:
 
     def __init__(self, nx, ny, p, Lx, Ly, dt, wind=(0.0, 0.0), wind_factors=None, prm: Params = None,
                  scheme: str = "pr", mode: str = "direct"):
-        assert scheme in ("pr", "strang")
+        assert scheme in ("pr", "strang", "explicit")
         assert mode in ("direct", "ads")
         self.prm = prm if prm is not None else Params()
         self.c = derived_constants(self.prm)
@@ -139,6 +145,8 @@ class Problem:
 
     # ---- schemes -----------------------------------------------------------------
     def step(self, T, phi):
+        if self.scheme == "explicit":
+            return self.explicit_step(T, phi)
         return self.pr_step(T, phi) if self.scheme == "pr" else self.strang_step(T, phi)
 
     def pr_step(self, T, phi):
@@ -163,6 +171,13 @@ class Problem:
         Tn = self.solve(("x", qx, 1.0), self.apply(("x", qx, -1.0), Tss) + 0.5 * tau * F3)
         phin = self.solve(("m",), Phi)
         return Tn, phin
+
+    def explicit_step(self, T, phi):
+        tau = self.dt
+        F, Phi = self.load(T, phi)
+        R = (self.apply(("x", tau, -1.0), T) + self.apply(("y", tau, -1.0), T) - self.apply(("m",), T)
+             + tau * F)
+        return self.solve(("m",), R), self.solve(("m",), Phi)
 
     def run(self, T, phi, steps):
         T = np.array(T, dtype=np.float64)

@@ -4,7 +4,8 @@
   'direct' equals a dense numpy solve of the same system on tiny grids.
 * Closed-form decay of discrete eigenmodes (pure diffusion, F off): one PR step
   multiplies v_x (x) v_y by (1 - th C_d l_y)(1 - th C_d l_x) / ((1 + th C_d l_x)(1 + th C_d l_y)),
-  th = tau/2; one Strang step by [(1 - tau C_d l_x/4)/(1 + tau C_d l_x/4)]^2 (1 - tau C_d l_y/2)/(1 + tau C_d l_y/2).
+  th = tau/2; one Strang step by [(1 - tau C_d l_x/4)/(1 + tau C_d l_x/4)]^2 (1 - tau C_d l_y/2)/(1 + tau C_d l_y/2);
+  one explicit L2-projection step by 1 - tau C_d (l_x + l_y).
 * A spatially uniform state follows the scalar recurrences derived from the schemes
   (source recomputed from raw Table constants, not from the oracle).
 * The ambient state T = T_amb is steady for any wind and fuel.
@@ -42,6 +43,12 @@ def _uniform_pr(T, phi, prm, tau):
     return Tn, phi * (1 - tau * 3e2 * r)
 
 
+def _uniform_explicit(T, phi, prm, tau):
+    c_chi = prm.chi / (prm.rho * prm.cp)
+    s, r = _raw_s(T, phi, prm)
+    return T - tau * c_chi * T + tau * s, phi * (1 - tau * 3e2 * r)
+
+
 def _uniform_strang(T, phi, prm, tau):
     c_chi = prm.chi / (prm.rho * prm.cp)
     q = tau / 4
@@ -56,7 +63,7 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("scheme", ["pr", "strang"])
+@pytest.mark.parametrize("scheme", ["pr", "strang", "explicit"])
 @pytest.mark.parametrize("p,n", [(2, 1), (2, 6), (3, 5), (3, 13)])
 def test_ads_equals_direct(scheme, p, n):
     sc = make_scenario("t", n, p, 1e-3, 3, 11 + n, wind=(1.2, -0.4), fuel_sigma=1.0)
@@ -93,7 +100,7 @@ def test_eigenmode_decay_pr_and_strang(mode, p):
     dt = 0.8  # large enough that the factors differ visibly from 1
     prm = _diffusion_only()
     C_d = prm.kappa / (prm.rho * prm.cp)
-    for scheme in ("pr", "strang"):
+    for scheme in ("pr", "strang", "explicit"):
         P = Problem(nx, ny, p, Lx, Ly, dt, prm=prm, scheme=scheme, mode=mode)
         lx, Vx = sla.eigh(P.Kx.toarray(), P.Mx.toarray())
         ly, Vy = sla.eigh(P.Ky.toarray(), P.My.toarray())
@@ -104,6 +111,8 @@ def test_eigenmode_decay_pr_and_strang(mode, p):
                 th = dt / 2
                 rho = ((1 - th * C_d * ly[ky]) * (1 - th * C_d * lx[kx])
                        / ((1 + th * C_d * lx[kx]) * (1 + th * C_d * ly[ky])))
+            elif scheme == "explicit":
+                rho = 1 - dt * C_d * (lx[kx] + ly[ky])
             else:
                 ax = (1 - dt * C_d * lx[kx] / 4) / (1 + dt * C_d * lx[kx] / 4)
                 ay = (1 - dt * C_d * ly[ky] / 2) / (1 + dt * C_d * ly[ky] / 2)
@@ -111,7 +120,7 @@ def test_eigenmode_decay_pr_and_strang(mode, p):
             assert _rel(T1, rho * T0) < 1e-12, (scheme, kx, ky)
 
 
-@pytest.mark.parametrize("scheme", ["pr", "strang"])
+@pytest.mark.parametrize("scheme", ["pr", "strang", "explicit"])
 @pytest.mark.parametrize("T,phi", [(1000.0, 0.8), (1000.0, 0.1), (500.0, 0.9), (1400.0, 0.2 + 5e-7)])
 def test_uniform_state_recurrence(scheme, T, phi):
     sc = make_scenario("u", 5, 2, 2e-3, 1, 3, wind=(1.0, 0.5))  # wind and its perturbation on
@@ -119,13 +128,13 @@ def test_uniform_state_recurrence(scheme, T, phi):
     P = Problem.from_scenario(sc, prm=prm, scheme=scheme, mode="direct")
     shape = sc.T0.shape
     Tn, pn = P.step(np.full(shape, T), np.full(shape, phi))
-    f = _uniform_pr if scheme == "pr" else _uniform_strang
+    f = {"pr": _uniform_pr, "strang": _uniform_strang, "explicit": _uniform_explicit}[scheme]
     Te, pe = f(T, phi, prm, sc.dt)
     assert np.abs(Tn / Te - 1).max() < 1e-12
     assert np.abs(pn / pe - 1).max() < 1e-12
 
 
-@pytest.mark.parametrize("scheme", ["pr", "strang"])
+@pytest.mark.parametrize("scheme", ["pr", "strang", "explicit"])
 def test_ambient_state_is_steady(scheme):
     sc = make_scenario("a", 8, 3, 1e-3, 1, 21, wind=(2.0, -1.0))
     P = Problem.from_scenario(sc, scheme=scheme, mode="ads")
@@ -133,7 +142,7 @@ def test_ambient_state_is_steady(scheme):
     assert np.abs(T / 300.0 - 1).max() < 1e-12
 
 
-@pytest.mark.parametrize("scheme", ["pr", "strang"])
+@pytest.mark.parametrize("scheme", ["pr", "strang", "explicit"])
 def test_heat_content_conserved_without_sources(scheme):
     # linear and T^3 diffusion on, every source and the wind off
     prm = Params(chi=0.0, heat_scale=0.0, delta_z=1e300)
@@ -147,7 +156,7 @@ def test_heat_content_conserved_without_sources(scheme):
     assert np.abs(T - sc.T0).max() > 1e-3  # the state did evolve
 
 
-@pytest.mark.parametrize("scheme", ["pr", "strang"])
+@pytest.mark.parametrize("scheme", ["pr", "strang", "explicit"])
 def test_mirror_symmetry_of_verification_problem(scheme):
     sc = make_scenario("v", 12, 2, 1e-3, 1, 9, wind=(0.0, 0.0), uniform_fuel=1.0, centred_ignition=True)
     P = Problem.from_scenario(sc, scheme=scheme, mode="ads")
