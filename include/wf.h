@@ -56,6 +56,8 @@ extern "C" {
 /* ---- choices ----------------------------------------------------------- */
 #define WF_PR 0              /* Peaceman-Rachford, Sec. 3.1 */
 #define WF_STRANG_CN 1       /* Strang splitting + Crank-Nicolson, Sec. 3.2 */
+#define WF_EXPLICIT 2        /* explicit L2 projection: every term at T^n, mass solves (the
+                                explicit dynamics of Sec. 6, the scheme the Sec. 7 listing runs) */
 #define WF_FP32 0            /* FP32 quadrature and substitution, FP64 1-D factorisation */
 #define WF_FP64 1            /* everything in FP64 (verification mode) */
 #define WF_F_ONCE 0          /* PR: F(T^n, phi^n) used in both substeps (default) */
@@ -75,7 +77,7 @@ typedef struct wf_params {
     double rho, cp, kappa, sigma, eps, ch, hc, cW, chi, T_amb, T_ig, delta_x, delta_z;
     double A_r, M_ratio, T_a, heat_scale, fuel_rate, fuel_thresh, thresh_guard;
     double wind_x, wind_y;
-    int scheme;              /* WF_PR | WF_STRANG_CN */
+    int scheme;              /* WF_PR | WF_STRANG_CN | WF_EXPLICIT */
     int precision;           /* WF_FP32 | WF_FP64 */
     int F_timing;            /* WF_F_ONCE | WF_F_PER_SUBSTEP (PR only) */
     int scale_heat_by_fuel;  /* 0 (default) or 1 */

@@ -3,6 +3,7 @@
 // The step sequences follow the schemes of the paper:
 //   Peaceman-Rachford, Sec. 3.1 Eq. matrixPR (one explicit F per step, or per substep);
 //   Strang + Crank-Nicolson, Sec. 3.2 Eq. matrixCN;
+//   explicit L2 projection (the explicit dynamics of Sec. 6), every term at T^n;
 //   fuel: explicit Euler L2 projection of the Sec. 7 listing, (M^x (x) M^y) phi^{n+1} = Phi.
 // Each 2-D solve (A^x (x) B^y) X = R runs as an x pass (lines of A^x) and a y pass
 // (lines of B^y), Sec. 4.  The launches of one step are captured once into a CUDA
@@ -253,8 +254,10 @@ void layout_slot(wf_handle* h, Arena& A) {
 void set_slot_coeffs(const wf_handle* h, Slot& s) {
     const Phys& c = h->phys;
     const double tau = h->dt;
-    const double thx = h->prm.scheme == WF_PR ? 0.5 * tau : 0.25 * tau;
-    const double thy = 0.5 * tau;
+    // explicit: the "-theta A" operators carry the full tau (the "+" side is not used)
+    const bool ex = h->prm.scheme == WF_EXPLICIT;
+    const double thx = ex ? tau : (h->prm.scheme == WF_PR ? 0.5 * tau : 0.25 * tau);
+    const double thy = ex ? tau : 0.5 * tau;
     double(*x)[3] = s.coef[0];
     double(*y)[3] = s.coef[1];
     x[0][0] = 1.0, x[0][1] = 0.0, x[0][2] = 0.0;
@@ -293,7 +296,7 @@ bool params_ok(const wf_params& p) {
     for (double x : w)
         if (!isfinite(x)) return false;
     if (!(p.delta_z > 0.0)) return false;  // may be +inf (no vertical radiation)
-    if (p.scheme != WF_PR && p.scheme != WF_STRANG_CN) return false;
+    if (p.scheme != WF_PR && p.scheme != WF_STRANG_CN && p.scheme != WF_EXPLICIT) return false;
     if (p.precision != WF_FP32 && p.precision != WF_FP64) return false;
     if (p.F_timing != WF_F_ONCE && p.F_timing != WF_F_PER_SUBSTEP) return false;
     return true;
@@ -545,6 +548,21 @@ cudaError_t enqueue_step(wf_handle* h) {
     const Chunks& cx = h->dx.ch;
     const Chunks& cy = h->dy.ch;
     cudaError_t e;
+    if (h->prm.scheme == WF_EXPLICIT) {
+        // (M^x (x) M^y)(T^{n+1} - T^n) = tau F - tau (A_x (x) M^y) T^n - tau (M^x (x) A_y) T^n
+        RhsArgs r1 = rhs_args(h, h->T, nullptr, h->Phi, h->R, h->dt, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
+        if ((e = timed(h, S_RHS1, [&] { return launch_rhs(prec, p, r1, s); })) != cudaSuccess) return e;
+        LineArgs x1 = line_args(h, 1);
+        add_line(x1, h->R, h->R, X[0], cx);
+        add_line(x1, h->Phi, h->Phi, X[0], cx);
+        if ((e = timed(h, S_X1, [&] { return launch_xsolve(prec, p, x1, s); })) != cudaSuccess) return e;
+        LineArgs y1 = line_args(h, 0);
+        add_line(y1, h->R, h->T, Y[0], cy, h->T);
+        add_line(y1, h->Phi, h->phi, Y[0], cy, h->phi);
+        y1.status = h->status;
+        if ((e = timed(h, S_Y3, [&] { return launch_ysolve(prec, p, y1, s); })) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
     if (h->prm.scheme == WF_PR) {
         const double th = 0.5 * h->dt;
         const bool once = h->prm.F_timing == WF_F_ONCE;

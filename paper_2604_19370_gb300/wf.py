@@ -28,6 +28,7 @@ WF_ETRUNC = -7
 WF_ENOTFOUND = -8
 WF_PR = 0
 WF_STRANG_CN = 1
+WF_EXPLICIT = 2
 WF_FP32 = 0
 WF_FP64 = 1
 WF_F_ONCE = 0

@@ -34,10 +34,10 @@ def _batch_params(wf, sc, prec, scheme):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-@pytest.mark.parametrize("scheme", ["pr", "strang"])
+@pytest.mark.parametrize("scheme", ["pr", "strang", "explicit"])
 def test_batch_slots_equal_single_runs(wf, prec, scheme):
     P = wf.WF_FP32 if prec == "fp32" else wf.WF_FP64
-    code = wf.WF_PR if scheme == "pr" else wf.WF_STRANG_CN
+    code = {"pr": wf.WF_PR, "strang": wf.WF_STRANG_CN, "explicit": wf.WF_EXPLICIT}[scheme]
     scs = _scenarios(40, 2, 5, 700)
     steps = 4
     b = wf.Batch(scs[0].nx, scs[0].ny, 2, 1e-3, _batch_params(wf, scs[0], P, code), capacity=6)
