@@ -160,6 +160,33 @@ int wf_set_profiling(wf_handle* h, int on);
 int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], int max_k);
 
 /*
+ * Manufactured-solution forcing for the convergence study of Sec. 6 ("Stability
+ * and order of the time integration scheme").  With m != NULL every
+ * right-hand side of a step gains the load vector of
+ *   f = u_t - C_d lap u + c_W b.grad u + c_chi u
+ *       - [c_chi T_amb + c_rad (T_amb^4 - u^4) + C_nld (u^3 lap u + 3 u^2 |grad u|^2)]
+ * evaluated at the exact solution
+ *   u*(x, y, t) = base + sum_{k < nmodes} amp[k] (1 - cos(2 pi kx[k] x / Lx))
+ *                                        (1 - cos(2 pi ky[k] y / Ly)) exp(-lambda[k] t)
+ * (the paper: base 300, modes (80, 1, 1, 3), (30, 2, 1, 5), (110, 2, 2, 1.5) on
+ * [0, 100]^2), at the start time of the step, scaled like the scheme's F; the
+ * time starts at t0 and advances by dt every step (kept on the device).  The
+ * model's combustion and wind variation are not part of f: run the study with
+ * heat_scale = 0 and no wind variation.  m == NULL switches the forcing off.
+ * Single-scenario handles only.  Captured graphs are dropped.
+ * Errors: WF_EINVAL (batch handle, nmodes outside 0..4, non-finite values),
+ * WF_ECUDA.  wf_get_time reads the current time (waits for the stream).
+ */
+typedef struct wf_mms {
+    int nmodes;
+    double amp[4], kx[4], ky[4], lambda[4];
+    double base;
+    double t0;
+} wf_mms;
+int wf_set_mms(wf_handle* h, const wf_mms* m);
+int wf_get_time(wf_handle* h, double* t);
+
+/*
  * Launch-shape autotuner (no counterpart in the paper, whose solver runs on
  * CPU threads).  Five shapes are tuned (int shape[5]):
  *   shape[0]  lines per CTA of the first x pass of a step (rows staged per

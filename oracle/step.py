@@ -28,6 +28,9 @@ listing runs; the comparator of the convergence study): every term at T^n,
 with A_x = C_d K^x + c_W b_x G^x + c_chi M^x and A_y = C_d K^y + c_W b_y G^y, written
 with the operators above as (X(tau,-) (x) M^y) T + (M^x (x) Y(tau,-)) T - (M^x (x) M^y) T.
 
+With a manufactured solution (oracle.mms), its forcing load vector, evaluated at the start
+time of the step, is added to every F of the step.
+
 Fuel (listing "compute_rhs"): (M^x (x) M^y) phi^{n+1} = Phi(T^n, phi^n), once
 per step with the full tau; phi^n is the fuel seen by every F of the step.
 
@@ -62,7 +65,7 @@ class Problem:
     """A grid, its operators and the scheme settings; `step` advances (T, phi) by one time step."""
 
     def __init__(self, nx, ny, p, Lx, Ly, dt, wind=(0.0, 0.0), wind_factors=None, prm: Params = None,
-                 scheme: str = "pr", mode: str = "direct"):
+                 scheme: str = "pr", mode: str = "direct", forcing=None, t0: float = 0.0):
         assert scheme in ("pr", "strang", "explicit")
         assert mode in ("direct", "ads")
         self.prm = prm if prm is not None else Params()
@@ -75,6 +78,10 @@ class Problem:
         self.wind_factors = wind_factors
         self.scheme = scheme
         self.mode = mode
+        # manufactured-solution forcing (oracle.mms.Manufactured) added to every F of a step,
+        # evaluated at the step's start time self.t
+        self.forcing = forcing
+        self.t = float(t0)
         self.Mx, self.Kx, self.Gx = matrices_1d(self.tx)
         self.My, self.Ky, self.Gy = matrices_1d(self.ty)
         self._ops = {}
@@ -141,13 +148,21 @@ class Problem:
         return sla.solve_banded((p, p), to_banded(A, p), Y.T).T  # along x: every row
 
     def load(self, T, phi):
-        return load_vectors(self.tx, self.ty, T, phi, self.prm, self.dt, self.wind_factors)
+        F, Phi = load_vectors(self.tx, self.ty, T, phi, self.prm, self.dt, self.wind_factors)
+        if self.forcing is not None:
+            F = F + self.forcing.load(self.tx, self.ty, self.t, self.c, self.wind)
+        return F, Phi
 
     # ---- schemes -----------------------------------------------------------------
     def step(self, T, phi):
         if self.scheme == "explicit":
-            return self.explicit_step(T, phi)
-        return self.pr_step(T, phi) if self.scheme == "pr" else self.strang_step(T, phi)
+            out = self.explicit_step(T, phi)
+        elif self.scheme == "pr":
+            out = self.pr_step(T, phi)
+        else:
+            out = self.strang_step(T, phi)
+        self.t += self.dt
+        return out
 
     def pr_step(self, T, phi):
         th = 0.5 * self.dt

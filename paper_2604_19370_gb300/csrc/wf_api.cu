@@ -104,6 +104,9 @@ struct wf_handle {
     int S = 1;
     long long sbytes = 0;
     char* slots_mem = nullptr;  // start of slot 0's block
+    bool mms_on = false;       // manufactured-solution forcing (wf_set_mms)
+    MmsArgs mms{};
+    double* tdev = nullptr;    // device: start time of the next step (advanced only with forcing)
     int tune[5] = {0, 0, 0, 0, 0};  // x lines per CTA (first x pass), y lines per CTA, quadrature
                                     // segment rows, x lines per warp, x lines per CTA of the
                                     // second x pass (0: the launchers' rules)
@@ -175,6 +178,7 @@ void layout_shared(wf_handle* h, Arena& A) {
     h->diag = A.take<double>(4);
     h->active_dev = A.take<int>(h->S);
     h->status_out = A.take<int>(h->S);
+    h->tdev = A.take<double>(1);
     const int W = 2 * h->p + 1;
     const int maxN = h->Nx > h->Ny ? h->Nx : h->Ny;
     h->work64 = A.take<double>((size_t)maxN * W);
@@ -540,7 +544,23 @@ cudaError_t upload_active(wf_handle* h) {
 //   (X_+ (x) M^y) (T^{n+1} - T**) = tau/2 F(T**) - 2 theta_x (A_x (x) M^y) T**
 // Rounding errors then scale with the increment instead of the temperature,
 // which keeps the FP32 path accurate through the inverse mass matrices.
+// quadrature launch, then (with a manufactured solution) its forcing: out1 += s1 int f B,
+// out2 += s2 int f B
+cudaError_t rhs_and_forcing(wf_handle* h, const RhsArgs& r, void* out1, double s1, void* out2, double s2) {
+    cudaError_t e = launch_rhs(h->prec, h->p, r, h->stream);
+    if (e != cudaSuccess || !h->mms_on) return e;
+    return launch_forcing(h->prec, h->mms, out1, s1, out2, s2, h->stream);
+}
+
+cudaError_t enqueue_step_body(wf_handle* h);
+
 cudaError_t enqueue_step(wf_handle* h) {
+    cudaError_t e = enqueue_step_body(h);
+    if (e == cudaSuccess && h->mms_on) e = launch_advance_time(h->tdev, h->dt, h->stream);
+    return e;
+}
+
+cudaError_t enqueue_step_body(wf_handle* h) {
     cudaStream_t s = h->stream;
     const int prec = h->prec, p = h->p;
     Op* X = h->dx.op;
@@ -551,7 +571,8 @@ cudaError_t enqueue_step(wf_handle* h) {
     if (h->prm.scheme == WF_EXPLICIT) {
         // (M^x (x) M^y)(T^{n+1} - T^n) = tau F - tau (A_x (x) M^y) T^n - tau (M^x (x) A_y) T^n
         RhsArgs r1 = rhs_args(h, h->T, nullptr, h->Phi, h->R, h->dt, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
-        if ((e = timed(h, S_RHS1, [&] { return launch_rhs(prec, p, r1, s); })) != cudaSuccess) return e;
+        auto l1 = [&] { return rhs_and_forcing(h, r1, h->R, h->dt, nullptr, 0.0); };
+        if ((e = timed(h, S_RHS1, l1)) != cudaSuccess) return e;
         LineArgs x1 = line_args(h, 1);
         add_line(x1, h->R, h->R, X[0], cx);
         add_line(x1, h->Phi, h->Phi, X[0], cx);
@@ -567,7 +588,8 @@ cudaError_t enqueue_step(wf_handle* h) {
         const double th = 0.5 * h->dt;
         const bool once = h->prm.F_timing == WF_F_ONCE;
         RhsArgs r1 = rhs_args(h, h->T, once ? h->F : nullptr, h->Phi, h->R, th, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
-        if ((e = timed(h, S_RHS1, [&] { return launch_rhs(prec, p, r1, s); })) != cudaSuccess) return e;
+        auto l1 = [&] { return rhs_and_forcing(h, r1, h->R, th, once ? h->F : nullptr, 1.0); };
+        if ((e = timed(h, S_RHS1, l1)) != cudaSuccess) return e;
         LineArgs x1 = line_args(h, 1);
         add_line(x1, h->R, h->R, X[2], cx);
         add_line(x1, h->Phi, h->Phi, X[0], cx);
@@ -614,7 +636,8 @@ cudaError_t enqueue_step(wf_handle* h) {
             if ((e = timed(h, S_MV2, [&] { return launch_matvec(prec, p, mv, s); })) != cudaSuccess) return e;
         } else if (!once) {
             RhsArgs r2 = rhs_args(h, h->T, nullptr, nullptr, h->R, th, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
-            if ((e = timed(h, S_RHS2, [&] { return launch_rhs(prec, p, r2, s); })) != cudaSuccess) return e;
+            auto l2 = [&] { return rhs_and_forcing(h, r2, h->R, th, nullptr, 0.0); };
+            if ((e = timed(h, S_RHS2, l2)) != cudaSuccess) return e;
         }
         if (!fused) {
             LineArgs x2 = line_args(h, 2);
@@ -631,7 +654,8 @@ cudaError_t enqueue_step(wf_handle* h) {
     // Strang / Crank-Nicolson
     const double half = 0.5 * h->dt;
     RhsArgs r1 = rhs_args(h, h->T, nullptr, h->Phi, h->R, half, X[1], Y[0], 2.0, nullptr, nullptr, 0.0);
-    if ((e = timed(h, S_RHS1, [&] { return launch_rhs(prec, p, r1, s); })) != cudaSuccess) return e;
+    auto l1 = [&] { return rhs_and_forcing(h, r1, h->R, half, nullptr, 0.0); };
+    if ((e = timed(h, S_RHS1, l1)) != cudaSuccess) return e;
     LineArgs x1 = line_args(h, 1);
     add_line(x1, h->R, h->R, X[2], cx);
     add_line(x1, h->Phi, h->Phi, X[0], cx);
@@ -643,7 +667,8 @@ cudaError_t enqueue_step(wf_handle* h) {
     add_line(yy, h->T, h->T, Y[2], cy, h->T, Y[1].bandP, 2.0);
     if ((e = timed(h, S_Y2PRE, [&] { return launch_ysolve(prec, p, yy, s); })) != cudaSuccess) return e;
     RhsArgs r2 = rhs_args(h, h->T, nullptr, nullptr, h->R, half, X[1], Y[0], 2.0, nullptr, nullptr, 0.0);
-    if ((e = timed(h, S_RHS2, [&] { return launch_rhs(prec, p, r2, s); })) != cudaSuccess) return e;
+    auto l2 = [&] { return rhs_and_forcing(h, r2, h->R, half, nullptr, 0.0); };
+    if ((e = timed(h, S_RHS2, l2)) != cudaSuccess) return e;
     LineArgs x2 = line_args(h, 2);
     add_line(x2, h->R, h->R, X[2], cx);
     if ((e = timed(h, S_X2, [&] { return launch_xsolve(prec, p, x2, s); })) != cudaSuccess) return e;
@@ -1155,6 +1180,69 @@ int wf_autotune(wf_handle* h, int reps) {
     for (int q = 0; q < kTune; ++q) h->tune[q] = rc == WF_OK ? best[q] : saved[q];
     drop_graphs(h);
     return rc;
+}
+
+int wf_set_mms(wf_handle* h, const wf_mms* m) {
+    if (!h) return WF_EINVAL;
+    if (!m) {
+        h->mms_on = false;
+        drop_graphs(h);
+        return WF_OK;
+    }
+    if (h->S != 1 || m->nmodes < 0 || m->nmodes > 4) return WF_EINVAL;
+    for (int k = 0; k < m->nmodes; ++k)
+        if (!isfinite(m->amp[k]) || !isfinite(m->kx[k]) || !isfinite(m->ky[k]) || !isfinite(m->lambda[k]))
+            return WF_EINVAL;
+    if (!isfinite(m->base) || !isfinite(m->t0)) return WF_EINVAL;
+    MmsArgs& a = h->mms;
+    memset(&a, 0, sizeof(a));
+    a.nmodes = m->nmodes;
+    for (int k = 0; k < m->nmodes; ++k) {
+        a.amp[k] = m->amp[k];
+        a.kx[k] = m->kx[k];
+        a.ky[k] = m->ky[k];
+        a.lambda[k] = m->lambda[k];
+    }
+    a.base = m->base;
+    a.Lx = h->dx.L;
+    a.Ly = h->dy.L;
+    a.hx = h->dx.h;
+    a.hy = h->dy.h;
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.Nx = h->Nx;
+    a.Ny = h->Ny;
+    a.pitch = h->pitch;
+    a.p = h->p;
+    a.q = h->q;
+    a.Bx = h->dx.B64;
+    a.By = h->dy.B64;
+    WF_TRY(cudaMemcpyAsync(a.xi, h->gxi, sizeof(double) * h->q, cudaMemcpyDeviceToHost, h->stream));
+    WF_TRY(cudaMemcpyAsync(a.w, h->gw, sizeof(double) * h->q, cudaMemcpyDeviceToHost, h->stream));
+    const Phys& c = h->phys;
+    a.C_d = c.C_d;
+    a.c_W = c.c_W;
+    a.c_chi = c.c_chi;
+    a.T_amb = c.T_amb;
+    a.T_amb4 = c.T_amb * c.T_amb * c.T_amb * c.T_amb;
+    a.c_rad = c.c_rad;
+    a.C_nld = c.C_nld;
+    a.wind_x = h->slots[0].wind_x;
+    a.wind_y = h->slots[0].wind_y;
+    a.t = h->tdev;
+    const double t0 = m->t0;
+    WF_TRY(cudaMemcpyAsync(h->tdev, &t0, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    WF_TRY(cudaStreamSynchronize(h->stream));  // t0 and the node arrays are host locals
+    h->mms_on = true;
+    drop_graphs(h);
+    return WF_OK;
+}
+
+int wf_get_time(wf_handle* h, double* t) {
+    if (!h || !t) return WF_EINVAL;
+    WF_TRY(cudaMemcpyAsync(t, h->tdev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    WF_TRY(cudaStreamSynchronize(h->stream));
+    return WF_OK;
 }
 
 int wf_get_tuning(const wf_handle* h, int* shape) {

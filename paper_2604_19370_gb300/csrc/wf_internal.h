@@ -143,6 +143,22 @@ cudaError_t launch_rhs_stream(int prec, int p, const RhsArgs& a, cudaStream_t s)
 cudaError_t launch_rhs_tile(int prec, int p, const RhsArgs& a, cudaStream_t s);  // shared-memory tiles
 int rhs_items_per_dof(int p);  // informational
 
+// ---- manufactured-solution forcing (wf_mms.cu) --------------------------------------
+struct MmsArgs {
+    int nmodes;
+    double amp[4], kx[4], ky[4], lambda[4], base;  // u* = base + sum amp (1-cos)(1-cos) exp(-lambda t)
+    double Lx, Ly, hx, hy;
+    int nx, ny, Nx, Ny, pitch, p, q;
+    const double *Bx, *By;  // FP64 basis tables [n][q][p+1]
+    double xi[8], w[8];     // Gauss nodes and weights on [0, 1]
+    double C_d, c_W, c_chi, T_amb, T_amb4, c_rad, C_nld, wind_x, wind_y;
+    const double* t;        // device: start time of the step being enqueued
+};
+// out1 += s1 * int f B_i B_j, and out2 += s2 * the same when out2 is not NULL
+cudaError_t launch_forcing(int prec, const MmsArgs& a, void* out1, double s1, void* out2, double s2,
+                           cudaStream_t s);
+cudaError_t launch_advance_time(double* t, double dt, cudaStream_t s);
+
 // ---- line solves and matvec (wf_solve.cu) -------------------------------------------
 struct LineArgs {
     int G;       // lines per CTA of the compact-factor kernels (0: the launcher's rule; else an upper bound)

@@ -65,6 +65,12 @@ class WFError(RuntimeError):
 _lib = None
 
 
+class wf_mms(ctypes.Structure):
+    _fields_ = [("nmodes", ctypes.c_int), ("amp", ctypes.c_double * 4), ("kx", ctypes.c_double * 4),
+                ("ky", ctypes.c_double * 4), ("lambda_", ctypes.c_double * 4), ("base", ctypes.c_double),
+                ("t0", ctypes.c_double)]
+
+
 def lib() -> ctypes.CDLL:
     """Load libwf.so (raises if it was not built)."""
     global _lib
@@ -87,6 +93,8 @@ def lib() -> ctypes.CDLL:
         L.wf_kernel_times.argtypes = [vp, dp, ctypes.POINTER(i), ctypes.c_void_p, i]
         L.wf_step_noalloc.argtypes = [vp, vp, vp, i, i]
         L.wf_autotune.argtypes = [vp, i]
+        L.wf_set_mms.argtypes = [vp, ctypes.POINTER(wf_mms)]
+        L.wf_get_time.argtypes = [vp, ctypes.POINTER(d)]
         L.wf_get_tuning.argtypes = [vp, ctypes.POINTER(i)]
         L.wf_set_tuning.argtypes = [vp, ctypes.POINTER(i)]
         L.wf_batch_create.argtypes = [i, i, i, d, ctypes.POINTER(wf_params), i, ctypes.POINTER(vp)]
@@ -216,6 +224,26 @@ def wf_kernel_times(h, max_k: int = 16):
         nm = bytes(names[48 * j:48 * (j + 1)]).split(b"\0")[0].decode()
         out[nm] = (ms[j], cnt[j])
     return out
+
+
+def wf_set_mms(h, modes=None, base: float = 300.0, t0: float = 0.0) -> None:
+    """Manufactured-solution forcing: modes = [(amp, kx, ky, lambda), ...] (at most 4); None: off."""
+    if modes is None:
+        _check(lib().wf_set_mms(h, None), "wf_set_mms")
+        return
+    m = wf_mms()
+    m.nmodes = len(modes)
+    for k, (a, kx, ky, lam) in enumerate(modes):
+        m.amp[k], m.kx[k], m.ky[k], m.lambda_[k] = a, kx, ky, lam
+    m.base = base
+    m.t0 = t0
+    _check(lib().wf_set_mms(h, ctypes.byref(m)), "wf_set_mms")
+
+
+def wf_get_time(h) -> float:
+    t = ctypes.c_double()
+    _check(lib().wf_get_time(h, ctypes.byref(t)), "wf_get_time")
+    return t.value
 
 
 def wf_autotune(h, reps: int = 3) -> Tuple[int, int, int, int, int]:

@@ -101,3 +101,11 @@ def test_tuning_argument_checks_without_device(libpath):
     assert L.wf_autotune(None, 1) == wf.WF_EINVAL
     assert L.wf_get_tuning(None, None) == wf.WF_EINVAL
     assert L.wf_set_tuning(None, None) == wf.WF_EINVAL
+
+
+def test_mms_argument_checks_without_device(libpath):
+    from paper_2604_19370_gb300 import wf
+
+    L = wf.lib()
+    assert L.wf_set_mms(None, None) == wf.WF_EINVAL
+    assert L.wf_get_time(None, None) == wf.WF_EINVAL
