@@ -160,6 +160,19 @@ int wf_set_profiling(wf_handle* h, int on);
 int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], int max_k);
 
 /*
+ * Change the mean wind b (m/s) of a slot between steps (slot 0 for a handle of
+ * wf_create), keeping its state: the runs of Sec. 7 change the wind direction
+ * part-way (the Gran Canaria run: a south-westerly, then a westerly wind).  The
+ * slot's implicit operators and their chunked factors are rebuilt on the GPU
+ * (FP64); the call waits for the handle's stream first.  Captured step graphs
+ * stay valid (they address the factors, not their values).
+ * Errors: WF_EINVAL, WF_ESINGULAR / WF_ETRUNC (the new operators cannot be
+ * factored with the chunk length chosen at creation; the slot keeps its
+ * previous wind), WF_ECUDA.
+ */
+int wf_set_mean_wind(wf_handle* h, int slot, double wind_x, double wind_y);
+
+/*
  * Manufactured-solution forcing for the convergence study of Sec. 6 ("Stability
  * and order of the time integration scheme").  With m != NULL every
  * right-hand side of a step gains the load vector of

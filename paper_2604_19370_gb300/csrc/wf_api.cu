@@ -955,6 +955,33 @@ int wf_set_wind(wf_handle* h, int rank, const double* factors) {
     return set_slot_wind_factors(h, 0, rank, factors);
 }
 
+int wf_set_mean_wind(wf_handle* h, int slot, double wind_x, double wind_y) {
+    if (!h || slot < 0 || slot >= h->S || !isfinite(wind_x) || !isfinite(wind_y)) return WF_EINVAL;
+    Slot& sl = h->slots[slot];
+    if (sl.wind_x == wind_x && sl.wind_y == wind_y) return WF_OK;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;  // steps in flight use the factors
+    const double old_x = sl.wind_x, old_y = sl.wind_y;
+    sl.wind_x = wind_x;
+    sl.wind_y = wind_y;
+    set_slot_coeffs(h, sl);
+    double worst = 0.0;
+    int rc = build_factors(h, slot, trunc_tol(h), &worst);
+    if (rc != WF_OK) {
+        // keep the slot usable: back to the previous wind (whose factors were valid)
+        sl.wind_x = old_x;
+        sl.wind_y = old_y;
+        set_slot_coeffs(h, sl);
+        const int rc2 = build_factors(h, slot, trunc_tol(h), &worst);
+        return rc2 == WF_OK ? rc : rc2;
+    }
+    if (h->mms_on && slot == 0) {
+        h->mms.wind_x = wind_x;
+        h->mms.wind_y = wind_y;
+        drop_graphs(h);  // the forcing launch carries the wind by value
+    }
+    return WF_OK;
+}
+
 int wf_batch_set_slot(wf_handle* h, int slot, const double* T, const double* fuel, double wind_x, double wind_y,
                       int wind_rank, const double* wind_factors) {
     if (!h || slot < 0 || slot >= h->S || !T || !fuel) return WF_EINVAL;

@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
         L.wf_step_noalloc.argtypes = [vp, vp, vp, i, i]
         L.wf_autotune.argtypes = [vp, i]
         L.wf_set_mms.argtypes = [vp, ctypes.POINTER(wf_mms)]
+        L.wf_set_mean_wind.argtypes = [vp, i, d, d]
         L.wf_get_time.argtypes = [vp, ctypes.POINTER(d)]
         L.wf_get_tuning.argtypes = [vp, ctypes.POINTER(i)]
         L.wf_set_tuning.argtypes = [vp, ctypes.POINTER(i)]
@@ -224,6 +225,10 @@ def wf_kernel_times(h, max_k: int = 16):
         nm = bytes(names[48 * j:48 * (j + 1)]).split(b"\0")[0].decode()
         out[nm] = (ms[j], cnt[j])
     return out
+
+
+def wf_set_mean_wind(h, wind_x: float, wind_y: float, slot: int = 0) -> None:
+    _check(lib().wf_set_mean_wind(h, slot, wind_x, wind_y), "wf_set_mean_wind")
 
 
 def wf_set_mms(h, modes=None, base: float = 300.0, t0: float = 0.0) -> None:

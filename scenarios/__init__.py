@@ -19,3 +19,4 @@ from .generate import (  # noqa: F401
     request_stream_c5,
     element_size,
 )
+from .fuelmap import FUEL_MAP_SCALE, fuel_from_map, read_fuel_csv, sample_fuel_map  # noqa: F401,E402

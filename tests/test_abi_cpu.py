@@ -109,3 +109,10 @@ def test_mms_argument_checks_without_device(libpath):
     L = wf.lib()
     assert L.wf_set_mms(None, None) == wf.WF_EINVAL
     assert L.wf_get_time(None, None) == wf.WF_EINVAL
+
+
+def test_mean_wind_argument_checks_without_device(libpath):
+    from paper_2604_19370_gb300 import wf
+
+    L = wf.lib()
+    assert L.wf_set_mean_wind(None, 0, 1.0, 0.0) == wf.WF_EINVAL
