@@ -76,14 +76,20 @@ def algorithmic_costs(p: int, fused_x2: bool = True) -> dict:
     }
 
 
-def min_step_bytes(scheme_strang: bool) -> int:
+def min_step_bytes(scheme: str) -> int:
     """Least HBM bytes per DOF of one step (FP32): fields read and written once per pass.
 
     PR: x1 reads T, phi and writes its two results and F (20); y1 reads and writes two
     fields (16); x2 reads T*, F and writes its result (12); y2 reads and writes one (8).
     Strang-CN: 16 + 16 (substep 1) + 8 (y substep) + 12 + 8 (substep 3).
+    Explicit: x reads T, phi and writes two results (16); y reads them and the bases T, phi
+    and writes two fields (24).
     """
-    return 60 if scheme_strang else 56
+    return {"pr": 56, "strang": 60, "explicit": 40}[scheme]
+
+
+def scheme_of(args) -> str:
+    return "strang" if args.strang else ("explicit" if args.explicit else "pr")
 
 
 def shape_source(args) -> str:
@@ -301,7 +307,7 @@ def run_gpu(args) -> None:
         sc = make_scenario(f"n{args.nx}", args.nx, args.p, 1e-3, 1, 2001, fuel_sigma=20.0,
                            wind_speed_range=(0.0, 3.0))
     prec = wf.WF_FP64 if args.fp64 else wf.WF_FP32
-    scheme = wf.WF_STRANG_CN if args.strang else wf.WF_PR
+    scheme = {"pr": wf.WF_PR, "strang": wf.WF_STRANG_CN, "explicit": wf.WF_EXPLICIT}[scheme_of(args)]
     sim = wf.simulation_from_scenario(sc, precision=prec, scheme=scheme)
     stream = torch.cuda.Stream(device=dev)
     wf.wf_set_stream(sim.h, stream.cuda_stream)
@@ -370,7 +376,10 @@ def run_gpu(args) -> None:
     # roofline of the dominant kernel class
     peaks = _peaks()
     costs = algorithmic_costs(sc.p, fused_x2=("matvec_2" not in kt or kt["matvec_2"][1] == 0)
-                              and not args.strang)
+                              and scheme_of(args) == "pr")
+    if scheme_of(args) == "explicit":
+        costs["rhs_quadrature_1"]["bytes"] = 16  # no F stored
+        costs["ysolve_2"]["bytes"] = 24  # two arrays with their bases
     es = 8 if args.fp64 else 4
     shares = {k: v[0] for k, v in kt.items() if v[1] > 0}
     dom = max(shares, key=shares.get)
@@ -419,9 +428,9 @@ def run_gpu(args) -> None:
         "vs_baseline": None,
         "dtype": "f64" if args.fp64 else "f32",
         "data": "synthetic",
-        "config": {"workload": f"c2_{sc.nx}x{sc.ny}_p{sc.p}_{'strang' if args.strang else 'pr'}",
+        "config": {"workload": f"c2_{sc.nx}x{sc.ny}_p{sc.p}_{scheme_of(args)}",
                    "nx": sc.nx, "ny": sc.ny, "p": sc.p, "dofs": sc.dofs,
-                   "scheme": "Strang-CN" if args.strang else "PR",
+                   "scheme": {"pr": "PR", "strang": "Strang-CN", "explicit": "explicit L2 projection"}[scheme_of(args)],
                    "precision": "fp64" if args.fp64 else "fp32 bulk, fp64 1-D factorisation",
                    "l2": "flushed before every timed step (256 MiB write)",
                    "launch_shapes": {"x_lines_per_cta": tuning[0], "y_lines_per_cta": tuning[1],
@@ -430,7 +439,7 @@ def run_gpu(args) -> None:
                                      "source": shape_source(args)},
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
-        "step_hbm_frac": min_step_bytes(args.strang) * (es / 4) * sc.dofs / (ms_per_step * 1e-3) / 1e9
+        "step_hbm_frac": min_step_bytes(scheme_of(args)) * (es / 4) * sc.dofs / (ms_per_step * 1e-3) / 1e9
         / peaks["hbm_gbs"],
         "step_hbm_frac_kernel_bytes": step_bytes / (ms_per_step * 1e-3) / 1e9 / peaks["hbm_gbs"],
         "profiled_ms_per_step": prof_ms_per_step,
@@ -445,7 +454,7 @@ def run_gpu(args) -> None:
     # oracle baseline on a bounded sample (rank 0, N=1) and the rel-L2 of this path on the same steps
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ks = args.cpu_steps
-        res = _oracle_sample(ks, scheme="strang" if args.strang else "pr")
+        res = _oracle_sample(ks, scheme=scheme_of(args))
         d = np.load(res["state"])
         os.unlink(res["state"])
         chk = wf.simulation_from_scenario(sc, precision=prec, scheme=scheme)
@@ -456,7 +465,8 @@ def run_gpu(args) -> None:
         rla = float(np.linalg.norm(Tg - d["T"]) / np.linalg.norm(d["T"] - 300.0))
         rlp = float(np.linalg.norm(pg - d["phi"]) / np.linalg.norm(d["phi"]))
         line["cpu_baseline"] = {"value": sc.dofs * ks / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{ks} PR steps of the same 1026^2-DOF workload, FP64, ads mode"}
+                                "sample": f"{ks} {scheme_of(args)} steps of the same 1026^2-DOF workload, FP64, "
+                                          "ads mode"}
         line["rel_l2_vs_oracle"] = {"steps": ks, "T": rl, "T_minus_Tamb": rla, "phi": rlp}
     sim.close()
     if rank == 0:
@@ -572,7 +582,7 @@ def run_ensemble(args) -> None:
                                      "x2_lines_per_cta": tuning[4],
                                      "source": shape_source(args)}},
         "roofline": roof,
-        "step_hbm_frac": min_step_bytes(False) * dofs / (slowest / args.steps) / 1e9 / peaks["hbm_gbs"],
+        "step_hbm_frac": min_step_bytes("pr") * dofs / (slowest / args.steps) / 1e9 / peaks["hbm_gbs"],
         "step_hbm_frac_kernel_bytes": step_bytes / (slowest / args.steps) / 1e9 / peaks["hbm_gbs"],
         "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in kt.items() if v[1] > 0},
         "gpu_launches": int(sum(v[1] for v in kt.values())),
@@ -681,6 +691,7 @@ def main():
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--strang", action="store_true")
+    ap.add_argument("--explicit", action="store_true", help="explicit L2-projection scheme (the comparator)")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="launch shapes from the launchers' rules")
