@@ -65,6 +65,13 @@ struct ITab {
     int xok, yok;          // the interior tables exist (n > 2p)
 };
 
+// Tables of the FP32 fast form with the values of Gauss points q = 2j and 2j+1 side by side, so
+// that one packed FMA (two FP32 lanes per instruction) serves both points.
+struct ITabPairs {
+    float2 bx[4][2], dx[4][2];                                  // [k][j]: (B_k(x_2j), B_k(x_2j+1))
+    float2 ys[4][4][2], yd[4][4][2], yq[4][4][2], yg[4][4][2];  // [b][l][j], as ITab's y-test tables
+};
+
 template <typename P>
 struct StreamArgs {
     int nx, ny, Nx, Ny, pitch, seg, nstrips, nsegs;
@@ -82,6 +89,7 @@ struct StreamArgs {
     PhysS<P> c;
     Batch b;
     ITab<P> it;
+    ITabPairs pr;
 };
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -380,6 +388,303 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
 #undef WF_A2
 }
 
+// ---- FP32 fast form with packed pairs ---------------------------------------------------
+// The computation of stream_strip<float, PD, WR, true> with the Gauss points q = 2j and 2j+1
+// of each element row carried side by side in float2 values: interpolation, point source
+// and y-test accumulation use packed FMAs (__ffma2_rn: two FP32 FMAs in one instruction),
+// which halves the issue slots of that arithmetic; an odd last point stays scalar.  Only
+// interior strips and segments take this form, so every table is a constant.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+template <int PD, int WR>
+__device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, const ITab<float>& it,
+                                                   const ITabPairs& pt, int lane, int X0, int Y0, int Y1) {
+    using P = float;
+    constexpr int Q = PD + 1, NB = PD + 1, W = 2 * PD + 1, NC = 2 * PD + 1;
+    constexpr int QP = Q / 2, QS = Q % 2, QPm = QP > 0 ? QP : 1, WRm = WR > 0 ? WR : 1;
+    const int ex = X0 - PD + lane;             // element column of this lane; also its DOF column
+    const bool out_col = lane >= PD;
+    const int cc = ex;                         // coefficient column held by this lane
+    const int cc2 = X0 - PD + 32 + lane;       // extra coefficient column (lanes < 2p are used)
+    constexpr bool HB2 = WR < 2;
+    P a1[W], a2r[W], b2i[W];
+#pragma unroll
+    for (int d = 0; d < W; ++d) {
+        a1[d] = a.A1[(size_t)cc * W + d];
+        a2r[d] = (!HB2 && a.A2) ? a.A2[(size_t)cc * W + d] : P(0);
+        b2i[d] = (HB2 && a.A2) ? a.B2[(size_t)(2 * PD) * W + d] : P(0);
+    }
+#define WF_A2(d) (HB2 ? it.mbx[d] : a2r[d])
+    float2 fx2[WRm][QPm], fy2[WRm][QPm];
+    P fxs[WRm], fys[WRm];
+#pragma unroll
+    for (int r = 0; r < WR; ++r) {
+        const P* fxp = a.fxq + (size_t)r * a.nx * Q + (size_t)ex * Q;
+        const P* fyp = a.fyq + (size_t)r * a.nx * Q + (size_t)ex * Q;
+#pragma unroll
+        for (int j = 0; j < QP; ++j) {
+            fx2[r][j] = make_float2(fxp[2 * j], fxp[2 * j + 1]);
+            fy2[r][j] = make_float2(fyp[2 * j], fyp[2 * j + 1]);
+        }
+        fxs[r] = QS ? fxp[Q - 1] : P(0);
+        fys[r] = QS ? fyp[Q - 1] : P(0);
+    }
+
+    // sliding windows: x-interpolated coefficient rows ey .. ey+p, y-test accumulators of DOF rows
+    // ey .. ey+p (pairs of Gauss points and the odd last point), x-convolved T rows for the matvec
+    float2 xv2[NB][QPm], xd2[NB][QPm], xp2[NB][QPm], as2[NB][QPm], aq2[NB][QPm], ag2[NB][QPm];
+    P xvs[NB], xds[NB], xps[NB], ass[NB], aqs[NB], ags[NB];
+    P cw1[NC], cw2[NC];
+#pragma unroll
+    for (int l = 0; l < NB; ++l) {
+#pragma unroll
+        for (int j = 0; j < QPm; ++j) xv2[l][j] = xd2[l][j] = xp2[l][j] = as2[l][j] = aq2[l][j] = ag2[l][j] = f2(0.f);
+        xvs[l] = xds[l] = xps[l] = ass[l] = aqs[l] = ags[l] = P(0);
+    }
+#pragma unroll
+    for (int d = 0; d < NC; ++d) cw1[d] = cw2[d] = P(0);
+
+    struct Row {
+        P t0, t1, f0, f1;
+    };
+    // rows Y0 - 2p .. Y1 + p all exist on an interior segment
+    auto fetch_row = [&](int r) {
+        Row w;
+        const size_t o = (size_t)r * a.pitch;
+        w.t0 = a.T[o + cc];
+        w.t1 = lane < 2 * PD ? a.T[o + cc2] : P(0);
+        w.f0 = a.phi[o + cc];
+        w.f1 = lane < 2 * PD ? a.phi[o + cc2] : P(0);
+        return w;
+    };
+    auto process_row = [&](const Row& w, float2(&v)[QPm], float2(&dv)[QPm], float2(&pv)[QPm], P& vs, P& dvs,
+                           P& pvs, P& w1, P& w2) {
+        P ct[NB], cf[NB];
+        ct[0] = w.t0;
+        cf[0] = w.f0;
+#pragma unroll
+        for (int k = 1; k < NB; ++k) {
+            ct[k] = col_from(w.t0, w.t1, lane, k);
+            cf[k] = col_from(w.f0, w.f1, lane, k);
+        }
+#pragma unroll
+        for (int j = 0; j < QP; ++j) {
+            float2 s = mul2(pt.bx[0][j], f2(ct[0])), sd = mul2(pt.dx[0][j], f2(ct[0])), sp = mul2(pt.bx[0][j], f2(cf[0]));
+#pragma unroll
+            for (int k = 1; k < NB; ++k) {
+                s = fma2(pt.bx[k][j], f2(ct[k]), s);
+                sd = fma2(pt.dx[k][j], f2(ct[k]), sd);
+                sp = fma2(pt.bx[k][j], f2(cf[k]), sp);
+            }
+            v[j] = s;
+            dv[j] = sd;
+            pv[j] = sp;
+        }
+        if (QS) {
+            P s = 0, sd = 0, sp = 0;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                s += it.bx[Q - 1][k] * ct[k];
+                sd += it.dx[Q - 1][k] * ct[k];
+                sp += it.bx[Q - 1][k] * cf[k];
+            }
+            vs = s;
+            dvs = sd;
+            pvs = sp;
+        }
+        P s1 = a1[PD] * w.t0, s2 = WF_A2(PD) * w.t0;
+#pragma unroll
+        for (int k = 1; k <= PD; ++k) {
+            const P up = __shfl_up_sync(FULL, w.t0, k);
+            s1 = fma(a1[PD - k], up, fma(a1[PD + k], ct[k], s1));
+            s2 = fma(WF_A2(PD - k), up, fma(WF_A2(PD + k), ct[k], s2));
+        }
+        w1 = s1;
+        w2 = s2;
+    };
+
+    const PhysS<P>& c = a.c;
+    auto element_row = [&](int ey) {
+        P gyr[WRm][Q], gxr[WRm][Q];
+#pragma unroll
+        for (int r = 0; r < WR; ++r)
+#pragma unroll
+            for (int b = 0; b < Q; ++b) {
+                gxr[r][b] = a.gxq[(size_t)r * a.ny * Q + ey * Q + b];
+                gyr[r][b] = a.gyq[(size_t)r * a.ny * Q + ey * Q + b];
+            }
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+#pragma unroll
+            for (int j = 0; j < QP; ++j) {
+                float2 T = mul2(f2(it.by[b][0]), xv2[0][j]), Ty = mul2(f2(it.dy[b][0]), xv2[0][j]);
+                float2 Tx = mul2(f2(it.by[b][0]), xd2[0][j]), ph = mul2(f2(it.by[b][0]), xp2[0][j]);
+#pragma unroll
+                for (int l = 1; l < NB; ++l) {
+                    T = fma2(f2(it.by[b][l]), xv2[l][j], T);
+                    Ty = fma2(f2(it.dy[b][l]), xv2[l][j], Ty);
+                    Tx = fma2(f2(it.by[b][l]), xd2[l][j], Tx);
+                    ph = fma2(f2(it.by[b][l]), xp2[l][j], ph);
+                }
+                float2 bpx = f2(0.f), bpy = f2(0.f);
+#pragma unroll
+                for (int r = 0; r < WR; ++r) {
+                    bpx = fma2(fx2[r][j], f2(gxr[r][b]), bpx);
+                    bpy = fma2(fy2[r][j], f2(gyr[r][b]), bpy);
+                }
+                const bool bx0 = (T.x > c.T_ig) && (ph.x > c.phi_min);
+                const bool bx1 = (T.y > c.T_ig) && (ph.y > c.phi_min);
+                const float2 E = make_float2(bx0 ? T.x * arrhenius<P>(c, T.x) : P(0),
+                                             bx1 ? T.y * arrhenius<P>(c, T.y) : P(0));
+                const float2 T2 = mul2(T, T);
+                const float2 T3 = mul2(T2, T);
+                const float2 EP = mul2(E, ph);
+                float2 src = fma2(f2(c.K_ign), c.heat_by_fuel ? EP : E, fma2(f2(-c.c_rad), mul2(T2, T2), f2(c.K0)));
+                if (WR > 0) src = fma2(f2(-c.c_W), fma2(bpx, Tx, mul2(bpy, Ty)), src);
+                const float2 t3x = mul2(T3, Tx), t3y = mul2(T3, Ty);
+#pragma unroll
+                for (int l = 0; l < NB; ++l) {
+                    as2[l][j] = fma2(pt.ys[b][l][j], src, fma2(pt.yd[b][l][j], t3y, as2[l][j]));
+                    aq2[l][j] = fma2(pt.yq[b][l][j], t3x, aq2[l][j]);
+                    ag2[l][j] = fma2(pt.yg[b][l][j], EP, ag2[l][j]);
+                }
+            }
+            if (QS) {
+                constexpr int q = Q - 1;
+                P T = 0, Ty = 0, Tx = 0, ph = 0;
+#pragma unroll
+                for (int l = 0; l < NB; ++l) {
+                    T += it.by[b][l] * xvs[l];
+                    Ty += it.dy[b][l] * xvs[l];
+                    Tx += it.by[b][l] * xds[l];
+                    ph += it.by[b][l] * xps[l];
+                }
+                P bpx = 0, bpy = 0;
+#pragma unroll
+                for (int r = 0; r < WR; ++r) {
+                    bpx += fxs[r] * gxr[r][b];
+                    bpy += fys[r] * gyr[r][b];
+                }
+                const bool burn = (T > c.T_ig) && (ph > c.phi_min);
+                const P E = burn ? T * arrhenius<P>(c, T) : P(0);
+                const P T2 = T * T, T3 = T2 * T;
+                const P EP = E * ph;
+                P src = fma(c.K_ign, c.heat_by_fuel ? EP : E, fma(-c.c_rad, T2 * T2, c.K0));
+                if (WR > 0) src = fma(-c.c_W, fma(bpx, Tx, bpy * Ty), src);
+                const P t3x = T3 * Tx, t3y = T3 * Ty;
+#pragma unroll
+                for (int l = 0; l < NB; ++l) {
+                    ass[l] = fma(it.ys[b][q][l], src, fma(it.yd[b][q][l], t3y, ass[l]));
+                    aqs[l] = fma(it.yq[b][q][l], t3x, aqs[l]);
+                    ags[l] = fma(it.yg[b][q][l], EP, ags[l]);
+                }
+            }
+        }
+    };
+
+    // prologue: rows Y0-2p .. Y0-1 (matvec window), of which Y0-p .. Y0-1 also enter the x window
+    const int ey0 = Y0 - PD;
+#pragma unroll
+    for (int d = 0; d < 2 * PD; ++d) {
+        const int r = Y0 - 2 * PD + d;
+        float2 v[QPm], dv[QPm], pv[QPm];
+        P vs = 0, dvs = 0, pvs = 0;
+        process_row(fetch_row(r), v, dv, pv, vs, dvs, pvs, cw1[d], cw2[d]);
+        if (d >= PD) {
+#pragma unroll
+            for (int j = 0; j < QP; ++j) {
+                xv2[d - PD][j] = v[j];
+                xd2[d - PD][j] = dv[j];
+                xp2[d - PD][j] = pv[j];
+            }
+            xvs[d - PD] = vs;
+            xds[d - PD] = dvs;
+            xps[d - PD] = pvs;
+        }
+    }
+
+    Row nxt = fetch_row(ey0 + PD);
+    for (int ey = ey0; ey < Y1; ++ey) {
+        const Row cur = nxt;
+        nxt = fetch_row(ey + PD + 1);
+        process_row(cur, xv2[PD], xd2[PD], xp2[PD], xvs[PD], xds[PD], xps[PD], cw1[2 * PD], cw2[2 * PD]);
+        element_row(ey);
+        if (ey >= Y0) {
+            // x-test contraction: element ex - k holds DOF column ex as its local basis k
+            float2 Fv2 = f2(0.f), Ph2 = f2(0.f);
+            P Fv = 0, Ph = 0;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+#pragma unroll
+                for (int j = 0; j < QP; ++j) {
+                    float2 sv = as2[0][j], uv = aq2[0][j], gv = ag2[0][j];
+                    if (k > 0) {
+                        sv = make_float2(__shfl_up_sync(FULL, sv.x, k), __shfl_up_sync(FULL, sv.y, k));
+                        uv = make_float2(__shfl_up_sync(FULL, uv.x, k), __shfl_up_sync(FULL, uv.y, k));
+                        gv = make_float2(__shfl_up_sync(FULL, gv.x, k), __shfl_up_sync(FULL, gv.y, k));
+                    }
+                    Fv2 = fma2(pt.bx[k][j], sv, fma2(pt.dx[k][j], uv, Fv2));
+                    Ph2 = fma2(pt.bx[k][j], gv, Ph2);
+                }
+                if (QS) {
+                    const P sv = (k == 0) ? ass[0] : __shfl_up_sync(FULL, ass[0], k);
+                    const P uv = (k == 0) ? aqs[0] : __shfl_up_sync(FULL, aqs[0], k);
+                    const P gv = (k == 0) ? ags[0] : __shfl_up_sync(FULL, ags[0], k);
+                    Fv = fma(it.bx[Q - 1][k], sv, fma(it.dx[Q - 1][k], uv, Fv));
+                    Ph = fma(it.bx[Q - 1][k], gv, Ph);
+                }
+            }
+            Fv += Fv2.x + Fv2.y;
+            Ph += Ph2.x + Ph2.y;
+            if (out_col) {
+                const size_t g = (size_t)ey * a.pitch + ex;
+                if (a.F) a.F[g] = Fv;
+                if (a.Phi) a.Phi[g] = Ph;
+                if (a.R) {
+                    P r1 = 0, r2 = 0;
+#pragma unroll
+                    for (int d = 0; d < W; ++d) {
+                        r1 = fma(it.mby[d], cw1[d], r1);
+                        if (HB2) r2 = fma(b2i[d], cw2[d], r2);
+                        else if (a.A2) r2 += a.B2[(size_t)ey * W + d] * cw2[d];
+                    }
+                    a.R[g] = fma(a.Rscale, Fv, fma(a.c1, r1, a.c2 * r2));
+                }
+            }
+        }
+        // slide the windows by one row
+#pragma unroll
+        for (int l = 0; l < PD; ++l) {
+#pragma unroll
+            for (int j = 0; j < QPm; ++j) {
+                xv2[l][j] = xv2[l + 1][j];
+                xd2[l][j] = xd2[l + 1][j];
+                xp2[l][j] = xp2[l + 1][j];
+                as2[l][j] = as2[l + 1][j];
+                aq2[l][j] = aq2[l + 1][j];
+                ag2[l][j] = ag2[l + 1][j];
+            }
+            xvs[l] = xvs[l + 1];
+            xds[l] = xds[l + 1];
+            xps[l] = xps[l + 1];
+            ass[l] = ass[l + 1];
+            aqs[l] = aqs[l + 1];
+            ags[l] = ags[l + 1];
+        }
+#pragma unroll
+        for (int j = 0; j < QPm; ++j) as2[PD][j] = aq2[PD][j] = ag2[PD][j] = f2(0.f);
+        ass[PD] = aqs[PD] = ags[PD] = P(0);
+#pragma unroll
+        for (int d = 0; d < NC - 1; ++d) {
+            cw1[d] = cw1[d + 1];
+            cw2[d] = cw2[d + 1];
+        }
+    }
+#undef WF_A2
+}
+
 // Work item = (strip, segment) of one scenario, flattened, interior segments first and the
 // short boundary segments last, so that they fill the tail of the launch.  One warp per CTA, so that a warp slot frees as soon as its own item ends.  FP32, p <= 2:
 // twelve warps per SM (at most 168 registers a thread, no spills).
@@ -425,9 +730,12 @@ __global__ void __launch_bounds__(32, (sizeof(P) == 4 && PD <= 2) ? 12 : 1)
         Y1 = a.Ny;
     }
     const bool xint = a_in.it.xok && X0 >= 2 * PD && X0 + 31 < a.nx;
-    if (xint && yint)
-        stream_strip<P, PD, WR, true>(a, a_in.it, lane, X0, Y0, Y1);
-    else
+    if (xint && yint) {
+        if constexpr (sizeof(P) == 4)
+            stream_strip_pairs<PD, WR>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1);
+        else
+            stream_strip<P, PD, WR, true>(a, a_in.it, lane, X0, Y0, Y1);
+    } else
         stream_strip<P, PD, WR, false>(a, a_in.it, lane, X0, Y0, Y1);
 }
 
@@ -520,6 +828,21 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
             }
         }
     }
+    for (int k = 0; k < 4; ++k)
+        for (int j = 0; j < 2; ++j) {
+            const int q0 = 2 * j, q1 = 2 * j + 1;
+            a.pr.bx[k][j] = make_float2((float)r.tx.B[q0][k], (float)r.tx.B[q1][k]);
+            a.pr.dx[k][j] = make_float2((float)r.tx.D[q0][k], (float)r.tx.D[q1][k]);
+            for (int b = 0; b < 4; ++b) {
+                const double w0 = r.ty.w[b] * r.tx.w[q0], w1 = r.ty.w[b] * r.tx.w[q1];
+                const double Bb = r.ty.B[b][k], Db = r.ty.D[b][k];
+                const double cn = -r.phys.C_nld, cg = -(r.tau * r.phys.k_f);
+                a.pr.ys[b][k][j] = make_float2((float)(Bb * w0), (float)(Bb * w1));
+                a.pr.yd[b][k][j] = make_float2((float)(Db * w0 * cn), (float)(Db * w1 * cn));
+                a.pr.yq[b][k][j] = make_float2((float)(Bb * w0 * cn), (float)(Bb * w1 * cn));
+                a.pr.yg[b][k][j] = make_float2((float)(Bb * w0 * cg), (float)(Bb * w1 * cg));
+            }
+        }
     for (int d = 0; d < 8; ++d) {
         a.it.mbx[d] = (P)r.tx.Mb[d];
         a.it.mby[d] = (P)r.ty.Mb[d];
