@@ -89,6 +89,9 @@ struct wf_handle {
     wf_params prm;
     Phys phys;
     cudaStream_t own = nullptr, stream = nullptr;
+    // second stream: the quadrature's boundary items run there beside its interior items
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void* mem = nullptr;
     size_t mem_bytes = 0;
     // shared region
@@ -490,6 +493,9 @@ RhsArgs rhs_args(wf_handle* h, const void* T, void* F, void* Phi, void* R, doubl
     a.c2 = c2;
     a.tau = h->dt;
     a.seg = h->tune[2];
+    a.aux = h->aux;
+    a.ev_fork = h->ev_fork;
+    a.ev_join = h->ev_join;
     a.tx = h->dx.itab;
     a.ty = h->dy.itab;
     a.phys = h->phys;
@@ -721,6 +727,9 @@ void destroy(wf_handle* h) {
     for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
     if (h->mem) cudaFree(h->mem);
     if (h->own) cudaStreamDestroy(h->own);
+    if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
 }
 
@@ -859,7 +868,10 @@ int wf_batch_create(int nx, int ny, int p, double dt, const wf_params* params, i
         set_slot_coeffs(h, sl);
     }
     h->active_host.assign(capacity, 0);
-    if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         destroy(h);
         return WF_ECUDA;
     }

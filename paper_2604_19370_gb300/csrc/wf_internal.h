@@ -132,6 +132,10 @@ struct RhsArgs {
     double Rscale, c1, c2;
     double tau;  // full time step (fuel update)
     int seg;     // element rows per segment of the streaming kernel (0: the launcher's rule)
+    // second stream and fork/join events of the handle: the quadrature's boundary items run
+    // there, beside its interior items (NULL: one stream)
+    cudaStream_t aux;
+    cudaEvent_t ev_fork, ev_join;
     ElemTabs tx, ty;
     Phys phys;
     Batch b;  // per scenario: T, phi, F, Phi, R, A1, B1, A2, B2, fxq, gxq, fyq, gyq

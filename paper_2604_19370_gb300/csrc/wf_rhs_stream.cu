@@ -76,6 +76,7 @@ template <typename P>
 struct StreamArgs {
     int nx, ny, Nx, Ny, pitch, seg, nstrips, nsegs;
     int split;  // segments: [0, 2p), interior pieces of [2p, Ny - 2p), [Ny - 2p, Ny)
+    int s_lo, s_hi;  // interior strips (every element interior): s_lo <= strip < s_hi
     const P* __restrict__ T;
     const P* __restrict__ phi;
     P* F;
@@ -685,12 +686,20 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
 #undef WF_A2
 }
 
-// Work item = (strip, segment) of one scenario, flattened, interior segments first and the
-// short boundary segments last, so that they fill the tail of the launch.  One warp per CTA, so that a warp slot frees as soon as its own item ends.  FP32, p <= 2:
-// twelve warps per SM (at most 168 registers a thread, no spills).
-template <typename P, int PD, int WR>
-__global__ void __launch_bounds__(32, (sizeof(P) == 4 && PD <= 2) ? 12 : 1)
-    k_rhs_stream(const StreamArgs<P> a_in) {
+// Work items = (strip, segment) of one scenario.  MODE 2: every item, interior segments first and
+// the short boundary segments last, each warp taking the fast or the general form.  With
+// FP32 the items are split between two launches whose register budgets differ: MODE 0 runs the
+// interior items (interior strip x interior segment: the fast form, which needs few registers,
+// so sixteen one-warp CTAs fit an SM, fourteen with a rank-2 wind variation) and MODE 1 the
+// rest (the general form, twelve per SM).  One warp per CTA, so that a warp slot frees as soon
+// as its own item ends.
+template <typename P, int PD, int WR, int MODE>
+struct RhsOcc {
+    static constexpr int value = sizeof(P) != 4 || PD > 2 ? 1 : (MODE == 0 ? (WR == 2 ? 14 : 16) : 12);
+};
+
+template <typename P, int PD, int WR, int MODE>
+__global__ void __launch_bounds__(32, RhsOcc<P, PD, WR, MODE>::value) k_rhs_stream(const StreamArgs<P> a_in) {
     if (!scene_active(a_in.b)) return;
     StreamArgs<P> a = a_in;
     a.T = scene_ptr(a.T, a.b);
@@ -708,9 +717,31 @@ __global__ void __launch_bounds__(32, (sizeof(P) == 4 && PD <= 2) ? 12 : 1)
     a.gyq = scene_ptr(a.gyq, a.b);
     const int lane = threadIdx.x & 31;
     const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (item >= a.nstrips * a.nsegs) return;  // whole warp leaves; no block barrier in this kernel
-    const int sg = item / a.nstrips;
-    const int strip = item - sg * a.nstrips;
+    const int nsi = a.s_hi - a.s_lo;          // interior strips
+    const int nseg_in = a.split ? a.nsegs - 2 : 0;  // interior segments (listed first)
+    int sg, strip;
+    if (MODE == 0) {
+        if (item >= nsi * nseg_in) return;  // whole warp leaves; no block barrier in this kernel
+        sg = item / nsi;
+        strip = a.s_lo + (item - sg * nsi);
+    } else if (MODE == 1) {
+        const int nb = a.nstrips - nsi;      // boundary strips: [0, s_lo) and [s_hi, nstrips)
+        const int first = nb * nseg_in;      // boundary strips x interior segments, then every
+        if (item < first) {                  // strip x the two boundary segments
+            sg = item / nb;
+            const int bs = item - sg * nb;
+            strip = bs < a.s_lo ? bs : a.s_hi + (bs - a.s_lo);
+        } else {
+            const int g = item - first;
+            if (g >= 2 * a.nstrips) return;
+            sg = nseg_in + g / a.nstrips;
+            strip = g - (g / a.nstrips) * a.nstrips;
+        }
+    } else {
+        if (item >= a.nstrips * a.nsegs) return;
+        sg = item / a.nstrips;
+        strip = item - sg * a.nstrips;
+    }
     const int X0 = strip * (32 - PD);
     int Y0, Y1;
     bool yint = false;
@@ -730,13 +761,14 @@ __global__ void __launch_bounds__(32, (sizeof(P) == 4 && PD <= 2) ? 12 : 1)
         Y1 = a.Ny;
     }
     const bool xint = a_in.it.xok && X0 >= 2 * PD && X0 + 31 < a.nx;
-    if (xint && yint) {
+    if (MODE != 1 && xint && yint) {
         if constexpr (sizeof(P) == 4)
             stream_strip_pairs<PD, WR>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1);
         else
             stream_strip<P, PD, WR, true>(a, a_in.it, lane, X0, Y0, Y1);
-    } else
+    } else if (MODE != 0) {
         stream_strip<P, PD, WR, false>(a, a_in.it, lane, X0, Y0, Y1);
+    }
 }
 
 template <typename P>
@@ -808,6 +840,22 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
     const int mid = r.Ny - 4 * PD;
     a.split = (r.tx.ok && r.ty.ok && mid >= 1) ? 1 : 0;
     a.nsegs = a.split ? 2 + (mid + seg - 1) / seg : (r.Ny + seg - 1) / seg;
+    // interior strips: X0 = s (32 - p) >= 2p and X0 + 31 < nx (a contiguous range of s)
+    a.s_lo = a.s_hi = 0;
+    if (r.tx.ok) {
+        int lo = -1, hi = -1;
+        for (int st = 0; st < a.nstrips; ++st) {
+            const int X0 = st * (32 - PD);
+            if (X0 >= 2 * PD && X0 + 31 < r.nx) {
+                if (lo < 0) lo = st;
+                hi = st + 1;
+            }
+        }
+        if (lo >= 0) {
+            a.s_lo = lo;
+            a.s_hi = hi;
+        }
+    }
     for (int i = 0; i < 4; ++i) {
         for (int j = 0; j < 4; ++j) {
             a.it.bx[i][j] = (P)r.tx.B[i][j];
@@ -849,8 +897,32 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
     }
     a.it.xok = r.tx.ok;
     a.it.yok = r.ty.ok;
-    dim3 grid((unsigned)(((long)a.nstrips * a.nsegs + WARPS - 1) / WARPS), 1, r.b.S);
-    k_rhs_stream<P, PD, WR><<<grid, 32 * WARPS, 0, s>>>(a);
+    const long n_fast = (long)(a.s_hi - a.s_lo) * (a.split ? a.nsegs - 2 : 0);
+    const long n_all = (long)a.nstrips * a.nsegs;
+    if (sizeof(P) == 4 && n_fast > 0) {
+        // interior items in one launch, the rest in a second (their register budgets differ);
+        // with the handle's second stream the two run side by side and join before returning
+        cudaError_t e;
+        const bool fork = r.aux && r.ev_fork && r.ev_join;
+        cudaStream_t s1 = fork ? r.aux : s;
+        if (fork) {
+            if ((e = cudaEventRecord(r.ev_fork, s)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(r.aux, r.ev_fork, 0)) != cudaSuccess) return e;
+        }
+        dim3 g1((unsigned)((n_all - n_fast + WARPS - 1) / WARPS), 1, r.b.S);
+        k_rhs_stream<P, PD, WR, 1><<<g1, 32 * WARPS, 0, s1>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        dim3 g0((unsigned)((n_fast + WARPS - 1) / WARPS), 1, r.b.S);
+        k_rhs_stream<P, PD, WR, 0><<<g0, 32 * WARPS, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (fork) {
+            if ((e = cudaEventRecord(r.ev_join, r.aux)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(s, r.ev_join, 0)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    dim3 grid((unsigned)((n_all + WARPS - 1) / WARPS), 1, r.b.S);
+    k_rhs_stream<P, PD, WR, 2><<<grid, 32 * WARPS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
