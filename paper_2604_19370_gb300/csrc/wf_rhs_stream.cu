@@ -690,12 +690,13 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
 // the short boundary segments last, each warp taking the fast or the general form.  With
 // FP32 the items are split between two launches whose register budgets differ: MODE 0 runs the
 // interior items (interior strip x interior segment: the fast form, which needs few registers,
-// so sixteen one-warp CTAs fit an SM, fourteen with a rank-2 wind variation) and MODE 1 the
+// so twenty one-warp CTAs fit an SM without wind variation, sixteen with rank 1, fourteen with
+// rank 2) and MODE 1 the
 // rest (the general form, twelve per SM).  One warp per CTA, so that a warp slot frees as soon
 // as its own item ends.
 template <typename P, int PD, int WR, int MODE>
 struct RhsOcc {
-    static constexpr int value = sizeof(P) != 4 || PD > 2 ? 1 : (MODE == 0 ? (WR == 2 ? 14 : 16) : 12);
+    static constexpr int value = sizeof(P) != 4 || PD > 2 ? 1 : (MODE == 0 ? (WR == 2 ? 14 : (WR == 1 ? 16 : 20)) : 12);
 };
 
 template <typename P, int PD, int WR, int MODE>
