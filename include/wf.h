@@ -200,6 +200,14 @@ int wf_set_mms(wf_handle* h, const wf_mms* m);
 int wf_get_time(wf_handle* h, double* t);
 
 /*
+ * Number of time-step kernels the library has launched in this process (every
+ * handle, eager launches and graph captures alike; a replayed graph launches
+ * again the kernels it captured).  For measurement: the difference over eager
+ * steps is the number of kernels one step launches.  Errors: WF_EINVAL.
+ */
+int wf_launch_count(unsigned long long* n);
+
+/*
  * Launch-shape autotuner (no counterpart in the paper, whose solver runs on
  * CPU threads).  Five shapes are tuned (int shape[5]):
  *   shape[0]  lines per CTA of the first x pass of a step (rows staged per

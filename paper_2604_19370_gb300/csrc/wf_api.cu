@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -131,6 +132,11 @@ struct wf_handle {
     double site_ms[S_NSITES] = {0};
     int site_cnt[S_NSITES] = {0};
 };
+
+namespace wf {
+std::atomic<unsigned long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+}  // namespace wf
 
 namespace {
 
@@ -1281,6 +1287,12 @@ int wf_get_time(wf_handle* h, double* t) {
     if (!h || !t) return WF_EINVAL;
     WF_TRY(cudaMemcpyAsync(t, h->tdev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     WF_TRY(cudaStreamSynchronize(h->stream));
+    return WF_OK;
+}
+
+int wf_launch_count(unsigned long long* n) {
+    if (!n) return WF_EINVAL;
+    *n = wf::g_launches.load(std::memory_order_relaxed);
     return WF_OK;
 }
 

@@ -141,6 +141,8 @@ struct RhsArgs {
     Batch b;  // per scenario: T, phi, F, Phi, R, A1, B1, A2, B2, fxq, gxq, fyq, gyq
 };
 cudaError_t launch_rhs(int prec, int p, const RhsArgs& a, cudaStream_t s);
+// process-wide count of the time-step kernels launched (wf_launch_count)
+void count_launches(int n);
 // streaming form of the same computation (wf_rhs_stream.cu); cudaErrorNotSupported for
 // a wind variation of rank > 2
 cudaError_t launch_rhs_stream(int prec, int p, const RhsArgs& a, cudaStream_t s);

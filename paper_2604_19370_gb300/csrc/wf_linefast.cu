@@ -787,6 +787,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         dim3 grid((a.nlines + G - 1) / G, a.narr, a.b.S);
         kern<<<grid, 32 * (G / lpw), smem, s>>>(f);
+        count_launches(1);
     } else {
         int G = a.G > 0 ? (a.G < 256 ? a.G : 256) : (sizeof(P) == 4 ? 8 : 4);
         while (G > 1 && G * ch.C > 256) G /= 2;
@@ -801,6 +802,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         dim3 grid((a.nlines + G - 1) / G, a.narr, a.b.S);
         kern<<<grid, nt, smem, s>>>(f);
+        count_launches(1);
     }
     return cudaGetLastError();
 }
@@ -917,6 +919,7 @@ cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s) 
         }
     }
 #undef WF_MV
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -84,11 +84,13 @@ cudaError_t launch_forcing(int prec, const MmsArgs& a, void* out1, double s1, vo
         k_forcing<float><<<grid, block, 0, s>>>(a, (float*)out1, (float)s1, (float*)out2, (float)s2);
     else
         k_forcing<double><<<grid, block, 0, s>>>(a, (double*)out1, s1, (double*)out2, s2);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_advance_time(double* t, double dt, cudaStream_t s) {
     k_advance_time<<<1, 32, 0, s>>>(t, dt);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -350,6 +350,7 @@ cudaError_t run_rhs(const RhsArgs& a, cudaStream_t s) {
     }
     dim3 grid((a.Nx + TI - 1) / TI, (a.Ny + TJ - 1) / TJ, a.b.S);
     kern<<<grid, NT, S_::bytes, s>>>(to_typed<P>(a));
+    count_launches(1);
     return cudaGetLastError();
 }
 

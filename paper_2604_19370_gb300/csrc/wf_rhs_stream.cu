@@ -913,9 +913,11 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
         dim3 g1((unsigned)((n_all - n_fast + WARPS - 1) / WARPS), 1, r.b.S);
         k_rhs_stream<P, PD, WR, 1><<<g1, 32 * WARPS, 0, s1>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        count_launches(1);
         dim3 g0((unsigned)((n_fast + WARPS - 1) / WARPS), 1, r.b.S);
         k_rhs_stream<P, PD, WR, 0><<<g0, 32 * WARPS, 0, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        count_launches(1);
         if (fork) {
             if ((e = cudaEventRecord(r.ev_join, r.aux)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(s, r.ev_join, 0)) != cudaSuccess) return e;
@@ -924,6 +926,7 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
     }
     dim3 grid((unsigned)((n_all + WARPS - 1) / WARPS), 1, r.b.S);
     k_rhs_stream<P, PD, WR, 2><<<grid, 32 * WARPS, 0, s>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 

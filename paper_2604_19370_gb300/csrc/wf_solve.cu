@@ -327,6 +327,7 @@ cudaError_t run_line(const LineArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         kern<<<grid, threads, smem, s>>>(to_typed<P>(a, mpad));
     }
+    count_launches(1);
     return cudaGetLastError();
 }
 

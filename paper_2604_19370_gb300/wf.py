@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
         L.wf_kernel_times.argtypes = [vp, dp, ctypes.POINTER(i), ctypes.c_void_p, i]
         L.wf_step_noalloc.argtypes = [vp, vp, vp, i, i]
         L.wf_autotune.argtypes = [vp, i]
+        L.wf_launch_count.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
         L.wf_set_mms.argtypes = [vp, ctypes.POINTER(wf_mms)]
         L.wf_set_mean_wind.argtypes = [vp, i, d, d]
         L.wf_get_time.argtypes = [vp, ctypes.POINTER(d)]
@@ -249,6 +250,12 @@ def wf_get_time(h) -> float:
     t = ctypes.c_double()
     _check(lib().wf_get_time(h, ctypes.byref(t)), "wf_get_time")
     return t.value
+
+
+def wf_launch_count() -> int:
+    n = ctypes.c_ulonglong()
+    _check(lib().wf_launch_count(ctypes.byref(n)), "wf_launch_count")
+    return int(n.value)
 
 
 def wf_autotune(h, reps: int = 3) -> Tuple[int, int, int, int, int]:

@@ -116,3 +116,11 @@ def test_mean_wind_argument_checks_without_device(libpath):
 
     L = wf.lib()
     assert L.wf_set_mean_wind(None, 0, 1.0, 0.0) == wf.WF_EINVAL
+
+
+def test_launch_counter_without_device(libpath):
+    from paper_2604_19370_gb300 import wf
+
+    L = wf.lib()
+    assert L.wf_launch_count(None) == wf.WF_EINVAL
+    assert wf.wf_launch_count() >= 0
