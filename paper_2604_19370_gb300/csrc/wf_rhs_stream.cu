@@ -20,8 +20,9 @@
 //     rows are cut into a segment of the first 2p DOF rows, interior segments and a
 //     segment of the last 2p, so that a warp on an interior strip and segment touches
 //     interior elements only and takes every table from the kernel's parameter block
-//     (constant operands of the FMAs, no registers); the other warps read their
-//     element's tables through L1;
+//     (constant operands of the FMAs, no registers); in FP32 a warp on a boundary strip
+//     of an interior segment holds its element's x tables in registers, and the warps of
+//     the boundary segments read their element's tables through L1;
 //   * warps take (strip, segment) work items in a flat order, so none idles when the
 //     strips of a row do not fill a CTA.
 //
@@ -77,6 +78,7 @@ struct StreamArgs {
     int nx, ny, Nx, Ny, pitch, seg, nstrips, nsegs;
     int split;  // segments: [0, 2p), interior pieces of [2p, Ny - 2p), [Ny - 2p, Ny)
     int s_lo, s_hi;  // interior strips (every element interior): s_lo <= strip < s_hi
+    int seg_b, nseg_b;  // interior segments of the boundary strips: their own height and count
     const P* __restrict__ T;
     const P* __restrict__ phi;
     P* F;
@@ -394,43 +396,74 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
 // of each element row carried side by side in float2 values: interpolation, point source
 // and y-test accumulation use packed FMAs (__ffma2_rn: two FP32 FMAs in one instruction),
 // which halves the issue slots of that arithmetic; an odd last point stays scalar.  Only
-// interior strips and segments take this form, so every table is a constant.
+// interior segments take this form, so the y tables are constants; so are the x tables on
+// interior strips (XB false), while on the strips that reach the x boundary (XB) each lane
+// holds its own element's x tables in registers.
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
-template <int PD, int WR>
+template <int PD, int WR, bool XB>
 __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, const ITab<float>& it,
                                                    const ITabPairs& pt, int lane, int X0, int Y0, int Y1) {
     using P = float;
     constexpr int Q = PD + 1, NB = PD + 1, W = 2 * PD + 1, NC = 2 * PD + 1;
     constexpr int QP = Q / 2, QS = Q % 2, QPm = QP > 0 ? QP : 1, WRm = WR > 0 ? WR : 1;
     const int ex = X0 - PD + lane;             // element column of this lane; also its DOF column
-    const bool out_col = lane >= PD;
     const int cc = ex;                         // coefficient column held by this lane
     const int cc2 = X0 - PD + 32 + lane;       // extra coefficient column (lanes < 2p are used)
-    constexpr bool HB2 = WR < 2;
+    // XB (strips that reach the x boundary): lanes outside [0, nx) carry zero tables, the first
+    // and last p element columns their own ones; every lane holds its element's x tables in
+    // registers.  Otherwise every element is interior and the tables are constants.
+    const bool ex_ok = !XB || (ex >= 0 && ex < a.nx);
+    const bool cc_ok = !XB || (cc >= 0 && cc < a.Nx);
+    const bool cc2_ok = !XB || (cc2 >= 0 && cc2 < a.Nx);
+    const bool out_col = lane >= PD && (!XB || ex < a.Nx);
+    float2 rbx[XB ? NB : 1][QPm], rdx[XB ? NB : 1][QPm];
+    P rbs[XB ? NB : 1], rds[XB ? NB : 1];
+    if constexpr (XB) {
+        const P* Be = a.Bx + (size_t)(ex_ok ? ex : 0) * Q * NB;
+        const P* De = a.Dx + (size_t)(ex_ok ? ex : 0) * Q * NB;
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+#pragma unroll
+            for (int j = 0; j < QP; ++j) {
+                rbx[k][j] = ex_ok ? make_float2(Be[(2 * j) * NB + k], Be[(2 * j + 1) * NB + k]) : f2(0.f);
+                rdx[k][j] = ex_ok ? make_float2(De[(2 * j) * NB + k], De[(2 * j + 1) * NB + k]) : f2(0.f);
+            }
+            rbs[k] = (QS && ex_ok) ? Be[(Q - 1) * NB + k] : P(0);
+            rds[k] = (QS && ex_ok) ? De[(Q - 1) * NB + k] : P(0);
+        }
+    }
+#define WF_PBX(k, j) (XB ? rbx[XB ? k : 0][j] : pt.bx[k][j])
+#define WF_PDX(k, j) (XB ? rdx[XB ? k : 0][j] : pt.dx[k][j])
+#define WF_SBX(k) (XB ? rbs[XB ? k : 0] : it.bx[Q - 1][k])
+#define WF_SDX(k) (XB ? rds[XB ? k : 0] : it.dx[Q - 1][k])
+    // x bands of the DOF column: A1 per scenario; A2 = M^x from the constants where every column
+    // is interior and the rank-2 wind form needs no registers for it.  Segments of this form are
+    // interior in y, so the y band of B2 is its interior row.
+    constexpr bool A2C = !XB && WR < 2;
     P a1[W], a2r[W], b2i[W];
 #pragma unroll
     for (int d = 0; d < W; ++d) {
-        a1[d] = a.A1[(size_t)cc * W + d];
-        a2r[d] = (!HB2 && a.A2) ? a.A2[(size_t)cc * W + d] : P(0);
-        b2i[d] = (HB2 && a.A2) ? a.B2[(size_t)(2 * PD) * W + d] : P(0);
+        a1[d] = cc_ok ? a.A1[(size_t)cc * W + d] : P(0);
+        a2r[d] = (!A2C && cc_ok && a.A2) ? a.A2[(size_t)cc * W + d] : P(0);
+        b2i[d] = a.A2 ? a.B2[(size_t)(2 * PD) * W + d] : P(0);
     }
-#define WF_A2(d) (HB2 ? it.mbx[d] : a2r[d])
+#define WF_A2(d) (A2C ? it.mbx[d] : a2r[d])
     float2 fx2[WRm][QPm], fy2[WRm][QPm];
     P fxs[WRm], fys[WRm];
 #pragma unroll
     for (int r = 0; r < WR; ++r) {
-        const P* fxp = a.fxq + (size_t)r * a.nx * Q + (size_t)ex * Q;
-        const P* fyp = a.fyq + (size_t)r * a.nx * Q + (size_t)ex * Q;
+        const P* fxp = a.fxq + (size_t)r * a.nx * Q + (size_t)(ex_ok ? ex : 0) * Q;
+        const P* fyp = a.fyq + (size_t)r * a.nx * Q + (size_t)(ex_ok ? ex : 0) * Q;
 #pragma unroll
         for (int j = 0; j < QP; ++j) {
-            fx2[r][j] = make_float2(fxp[2 * j], fxp[2 * j + 1]);
-            fy2[r][j] = make_float2(fyp[2 * j], fyp[2 * j + 1]);
+            fx2[r][j] = ex_ok ? make_float2(fxp[2 * j], fxp[2 * j + 1]) : f2(0.f);
+            fy2[r][j] = ex_ok ? make_float2(fyp[2 * j], fyp[2 * j + 1]) : f2(0.f);
         }
-        fxs[r] = QS ? fxp[Q - 1] : P(0);
-        fys[r] = QS ? fyp[Q - 1] : P(0);
+        fxs[r] = (QS && ex_ok) ? fxp[Q - 1] : P(0);
+        fys[r] = (QS && ex_ok) ? fyp[Q - 1] : P(0);
     }
 
     // sliding windows: x-interpolated coefficient rows ey .. ey+p, y-test accumulators of DOF rows
@@ -454,10 +487,10 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
     auto fetch_row = [&](int r) {
         Row w;
         const size_t o = (size_t)r * a.pitch;
-        w.t0 = a.T[o + cc];
-        w.t1 = lane < 2 * PD ? a.T[o + cc2] : P(0);
-        w.f0 = a.phi[o + cc];
-        w.f1 = lane < 2 * PD ? a.phi[o + cc2] : P(0);
+        w.t0 = cc_ok ? a.T[o + cc] : P(0);
+        w.t1 = (cc2_ok && lane < 2 * PD) ? a.T[o + cc2] : P(0);
+        w.f0 = cc_ok ? a.phi[o + cc] : P(0);
+        w.f1 = (cc2_ok && lane < 2 * PD) ? a.phi[o + cc2] : P(0);
         return w;
     };
     auto process_row = [&](const Row& w, float2(&v)[QPm], float2(&dv)[QPm], float2(&pv)[QPm], P& vs, P& dvs,
@@ -472,12 +505,13 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
         }
 #pragma unroll
         for (int j = 0; j < QP; ++j) {
-            float2 s = mul2(pt.bx[0][j], f2(ct[0])), sd = mul2(pt.dx[0][j], f2(ct[0])), sp = mul2(pt.bx[0][j], f2(cf[0]));
+            float2 s = mul2(WF_PBX(0, j), f2(ct[0])), sd = mul2(WF_PDX(0, j), f2(ct[0]));
+            float2 sp = mul2(WF_PBX(0, j), f2(cf[0]));
 #pragma unroll
             for (int k = 1; k < NB; ++k) {
-                s = fma2(pt.bx[k][j], f2(ct[k]), s);
-                sd = fma2(pt.dx[k][j], f2(ct[k]), sd);
-                sp = fma2(pt.bx[k][j], f2(cf[k]), sp);
+                s = fma2(WF_PBX(k, j), f2(ct[k]), s);
+                sd = fma2(WF_PDX(k, j), f2(ct[k]), sd);
+                sp = fma2(WF_PBX(k, j), f2(cf[k]), sp);
             }
             v[j] = s;
             dv[j] = sd;
@@ -487,9 +521,9 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
             P s = 0, sd = 0, sp = 0;
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
-                s += it.bx[Q - 1][k] * ct[k];
-                sd += it.dx[Q - 1][k] * ct[k];
-                sp += it.bx[Q - 1][k] * cf[k];
+                s += WF_SBX(k) * ct[k];
+                sd += WF_SDX(k) * ct[k];
+                sp += WF_SBX(k) * cf[k];
             }
             vs = s;
             dvs = sd;
@@ -507,8 +541,10 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
     };
 
     const PhysS<P>& c = a.c;
-    auto element_row = [&](int ey) {
-        P gyr[WRm][Q], gxr[WRm][Q];
+    // wind factors of element row ey, loaded before the row's x interpolation so that their
+    // latency is hidden behind it
+    P gyr[WRm][Q], gxr[WRm][Q];
+    auto load_wind_row = [&](int ey) {
 #pragma unroll
         for (int r = 0; r < WR; ++r)
 #pragma unroll
@@ -516,6 +552,8 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
                 gxr[r][b] = a.gxq[(size_t)r * a.ny * Q + ey * Q + b];
                 gyr[r][b] = a.gyq[(size_t)r * a.ny * Q + ey * Q + b];
             }
+    };
+    auto element_row = [&]() {
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
 #pragma unroll
@@ -610,35 +648,36 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
     for (int ey = ey0; ey < Y1; ++ey) {
         const Row cur = nxt;
         nxt = fetch_row(ey + PD + 1);
+        load_wind_row(ey);
         process_row(cur, xv2[PD], xd2[PD], xp2[PD], xvs[PD], xds[PD], xps[PD], cw1[2 * PD], cw2[2 * PD]);
-        element_row(ey);
+        element_row();
         if (ey >= Y0) {
-            // x-test contraction: element ex - k holds DOF column ex as its local basis k
-            float2 Fv2 = f2(0.f), Ph2 = f2(0.f);
+            // x-test contraction: each lane first folds its own element's contributions to its
+            // local basis functions k (with its own x tables), then DOF column ex gathers local
+            // basis k of element ex - k from the lane k to its left
             P Fv = 0, Ph = 0;
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
+                float2 C2 = mul2(WF_PDX(k, 0), aq2[0][0]);
+                C2 = fma2(WF_PBX(k, 0), as2[0][0], C2);
+                float2 G2 = mul2(WF_PBX(k, 0), ag2[0][0]);
 #pragma unroll
-                for (int j = 0; j < QP; ++j) {
-                    float2 sv = as2[0][j], uv = aq2[0][j], gv = ag2[0][j];
-                    if (k > 0) {
-                        sv = make_float2(__shfl_up_sync(FULL, sv.x, k), __shfl_up_sync(FULL, sv.y, k));
-                        uv = make_float2(__shfl_up_sync(FULL, uv.x, k), __shfl_up_sync(FULL, uv.y, k));
-                        gv = make_float2(__shfl_up_sync(FULL, gv.x, k), __shfl_up_sync(FULL, gv.y, k));
-                    }
-                    Fv2 = fma2(pt.bx[k][j], sv, fma2(pt.dx[k][j], uv, Fv2));
-                    Ph2 = fma2(pt.bx[k][j], gv, Ph2);
+                for (int j = 1; j < QP; ++j) {
+                    C2 = fma2(WF_PBX(k, j), as2[0][j], fma2(WF_PDX(k, j), aq2[0][j], C2));
+                    G2 = fma2(WF_PBX(k, j), ag2[0][j], G2);
                 }
+                P Ck = C2.x + C2.y, Gk = G2.x + G2.y;
                 if (QS) {
-                    const P sv = (k == 0) ? ass[0] : __shfl_up_sync(FULL, ass[0], k);
-                    const P uv = (k == 0) ? aqs[0] : __shfl_up_sync(FULL, aqs[0], k);
-                    const P gv = (k == 0) ? ags[0] : __shfl_up_sync(FULL, ags[0], k);
-                    Fv = fma(it.bx[Q - 1][k], sv, fma(it.dx[Q - 1][k], uv, Fv));
-                    Ph = fma(it.bx[Q - 1][k], gv, Ph);
+                    Ck = fma(WF_SBX(k), ass[0], fma(WF_SDX(k), aqs[0], Ck));
+                    Gk = fma(WF_SBX(k), ags[0], Gk);
                 }
+                if (k > 0) {
+                    Ck = __shfl_up_sync(FULL, Ck, k);
+                    Gk = __shfl_up_sync(FULL, Gk, k);
+                }
+                Fv += Ck;
+                Ph += Gk;
             }
-            Fv += Fv2.x + Fv2.y;
-            Ph += Ph2.x + Ph2.y;
             if (out_col) {
                 const size_t g = (size_t)ey * a.pitch + ex;
                 if (a.F) a.F[g] = Fv;
@@ -648,8 +687,7 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
 #pragma unroll
                     for (int d = 0; d < W; ++d) {
                         r1 = fma(it.mby[d], cw1[d], r1);
-                        if (HB2) r2 = fma(b2i[d], cw2[d], r2);
-                        else if (a.A2) r2 += a.B2[(size_t)ey * W + d] * cw2[d];
+                        r2 = fma(b2i[d], cw2[d], r2);
                     }
                     a.R[g] = fma(a.Rscale, Fv, fma(a.c1, r1, a.c2 * r2));
                 }
@@ -684,16 +722,21 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
         }
     }
 #undef WF_A2
+#undef WF_PBX
+#undef WF_PDX
+#undef WF_SBX
+#undef WF_SDX
 }
 
 // Work items = (strip, segment) of one scenario.  MODE 2: every item, interior segments first and
 // the short boundary segments last, each warp taking the fast or the general form.  With
 // FP32 the items are split between two launches whose register budgets differ: MODE 0 runs the
-// interior items (interior strip x interior segment: the fast form, which needs few registers,
-// so twenty one-warp CTAs fit an SM without wind variation, sixteen with rank 1, fourteen with
-// rank 2) and MODE 1 the
-// rest (the general form, twelve per SM).  One warp per CTA, so that a warp slot frees as soon
-// as its own item ends.
+// interior items (interior strip x interior segment: the packed form with constant tables,
+// which needs few registers, so twenty one-warp CTAs fit an SM without wind variation, sixteen
+// with rank 1, fourteen with rank 2) and MODE 1 the rest, twelve per SM: the boundary strips
+// of the interior segments in the packed form with x tables in registers (on segments of
+// their own, shorter height) and the boundary segments in the general form.  One warp per
+// CTA, so that a warp slot frees as soon as its own item ends.
 template <typename P, int PD, int WR, int MODE>
 struct RhsOcc {
     static constexpr int value = sizeof(P) != 4 || PD > 2 ? 1 : (MODE == 0 ? (WR == 2 ? 14 : (WR == 1 ? 16 : 20)) : 12);
@@ -720,28 +763,32 @@ __global__ void __launch_bounds__(32, RhsOcc<P, PD, WR, MODE>::value) k_rhs_stre
     const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int nsi = a.s_hi - a.s_lo;          // interior strips
     const int nseg_in = a.split ? a.nsegs - 2 : 0;  // interior segments (listed first)
-    int sg, strip;
+    // item -> strip and segment; segments: 0 .. nseg_in-1 interior (height seg), nseg_in the
+    // first 2p DOF rows, nseg_in+1 the last 2p (split), or plain pieces of height seg
+    int sg, strip, seg = a.seg;
     if (MODE == 0) {
         if (item >= nsi * nseg_in) return;  // whole warp leaves; no block barrier in this kernel
         sg = item / nsi;
         strip = a.s_lo + (item - sg * nsi);
     } else if (MODE == 1) {
         const int nb = a.nstrips - nsi;      // boundary strips: [0, s_lo) and [s_hi, nstrips)
-        const int first = nb * nseg_in;      // boundary strips x interior segments, then every
-        if (item < first) {                  // strip x the two boundary segments
+        const int first = nb * a.nseg_b;     // boundary strips x interior segments of height
+        if (item < first) {                  // seg_b, then every strip x the two boundary segments
             sg = item / nb;
             const int bs = item - sg * nb;
             strip = bs < a.s_lo ? bs : a.s_hi + (bs - a.s_lo);
+            seg = a.seg_b;
         } else {
             const int g = item - first;
             if (g >= 2 * a.nstrips) return;
-            sg = nseg_in + g / a.nstrips;
+            sg = -1 - g / a.nstrips;         // -1: first 2p rows, -2: last 2p rows
             strip = g - (g / a.nstrips) * a.nstrips;
         }
     } else {
         if (item >= a.nstrips * a.nsegs) return;
         sg = item / a.nstrips;
         strip = item - sg * a.nstrips;
+        if (a.split && sg >= nseg_in) sg = nseg_in - 1 - sg;  // nseg_in -> -1, nseg_in+1 -> -2
     }
     const int X0 = strip * (32 - PD);
     int Y0, Y1;
@@ -749,12 +796,12 @@ __global__ void __launch_bounds__(32, RhsOcc<P, PD, WR, MODE>::value) k_rhs_stre
     if (!a.split) {
         Y0 = sg * a.seg;
         Y1 = min(Y0 + a.seg, a.Ny);
-    } else if (sg < a.nsegs - 2) {
-        // interior segments first (the long items), element rows Y0 - p .. Y1 - 1 in [p, ny - p)
-        Y0 = 2 * PD + sg * a.seg;
-        Y1 = min(Y0 + a.seg, a.Ny - 2 * PD);
+    } else if (sg >= 0) {
+        // interior segments (the long items), element rows Y0 - p .. Y1 - 1 in [p, ny - p)
+        Y0 = 2 * PD + sg * seg;
+        Y1 = min(Y0 + seg, a.Ny - 2 * PD);
         yint = true;
-    } else if (sg == a.nsegs - 2) {
+    } else if (sg == -1) {
         Y0 = 0;
         Y1 = 2 * PD;
     } else {
@@ -762,13 +809,21 @@ __global__ void __launch_bounds__(32, RhsOcc<P, PD, WR, MODE>::value) k_rhs_stre
         Y1 = a.Ny;
     }
     const bool xint = a_in.it.xok && X0 >= 2 * PD && X0 + 31 < a.nx;
-    if (MODE != 1 && xint && yint) {
-        if constexpr (sizeof(P) == 4)
-            stream_strip_pairs<PD, WR>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1);
+    if constexpr (sizeof(P) == 4) {
+        // FP32: interior strips of interior segments with constant tables (MODE 0), the other
+        // strips of interior segments with x tables in registers, boundary segments general.
+        // MODE 2 runs in FP32 only where no strip is interior.
+        if (MODE == 0)
+            stream_strip_pairs<PD, WR, false>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1);
+        else if (yint)
+            stream_strip_pairs<PD, WR, true>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1);
         else
+            stream_strip<P, PD, WR, false>(a, a_in.it, lane, X0, Y0, Y1);
+    } else {
+        if (xint && yint)
             stream_strip<P, PD, WR, true>(a, a_in.it, lane, X0, Y0, Y1);
-    } else if (MODE != 0) {
-        stream_strip<P, PD, WR, false>(a, a_in.it, lane, X0, Y0, Y1);
+        else
+            stream_strip<P, PD, WR, false>(a, a_in.it, lane, X0, Y0, Y1);
     }
 }
 
@@ -900,6 +955,16 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
     a.it.yok = r.ty.ok;
     const long n_fast = (long)(a.s_hi - a.s_lo) * (a.split ? a.nsegs - 2 : 0);
     const long n_all = (long)a.nstrips * a.nsegs;
+    // the boundary strips' interior segments run beside the interior launch, few of them: they
+    // take shorter segments (down to 8 rows) so that four items per SM exist
+    {
+        const int nb = a.nstrips - (a.s_hi - a.s_lo);
+        int sb = seg;
+        while (sb / 2 >= 8 && (long)nb * ((mid + sb - 1) / sb) * r.b.S < 4L * sms) sb /= 2;
+        a.seg_b = sb;
+        a.nseg_b = a.split ? (mid + sb - 1) / sb : 0;
+    }
+    const long n_side = (long)(a.nstrips - (a.s_hi - a.s_lo)) * a.nseg_b + 2L * a.nstrips;
     if (sizeof(P) == 4 && n_fast > 0) {
         // interior items in one launch, the rest in a second (their register budgets differ);
         // with the handle's second stream the two run side by side and join before returning
@@ -910,7 +975,7 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
             if ((e = cudaEventRecord(r.ev_fork, s)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(r.aux, r.ev_fork, 0)) != cudaSuccess) return e;
         }
-        dim3 g1((unsigned)((n_all - n_fast + WARPS - 1) / WARPS), 1, r.b.S);
+        dim3 g1((unsigned)((n_side + WARPS - 1) / WARPS), 1, r.b.S);
         k_rhs_stream<P, PD, WR, 1><<<g1, 32 * WARPS, 0, s1>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         count_launches(1);
