@@ -434,7 +434,7 @@ def run_gpu(args) -> None:
                    "l2": "flushed before every timed step (256 MiB write)",
                    "launch_shapes": {"x_lines_per_cta": tuning[0], "y_lines_per_cta": tuning[1],
                                      "quadrature_segment_rows": tuning[2], "x_lines_per_warp": tuning[3],
-                                     "x2_lines_per_cta": tuning[4],
+                                     "x2_lines_per_cta": tuning[4], "x2_rhs": tuning[5],
                                      "source": shape_source(args)},
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
@@ -580,7 +580,7 @@ def run_ensemble(args) -> None:
                    "dofs": dofs, "l2": f"state {S} x 5 fields > L2, no flush", "parallelism": f"replicas x{world}",
                    "launch_shapes": {"x_lines_per_cta": tuning[0], "y_lines_per_cta": tuning[1],
                                      "quadrature_segment_rows": tuning[2], "x_lines_per_warp": tuning[3],
-                                     "x2_lines_per_cta": tuning[4],
+                                     "x2_lines_per_cta": tuning[4], "x2_rhs": tuning[5],
                                      "source": shape_source(args)}},
         "roofline": roof,
         "step_hbm_frac": min_step_bytes("pr") * dofs / (slowest / args.steps) / 1e9 / peaks["hbm_gbs"],
@@ -696,7 +696,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="launch shapes from the launchers' rules")
-    ap.add_argument("--tuning", default="", help="launch shapes x_cta,y_cta,seg,x_per_warp,x2_cta (skips the autotuner)")
+    ap.add_argument("--tuning", default="", help="launch shapes x_cta,y_cta,seg,x_per_warp,x2_cta,x2_rhs (skips the autotuner)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
                     help="c2: one 1024^2 domain (default); c4: batched ensemble; c5: served request stream")
     ap.add_argument("--scenarios", type=int, default=256)

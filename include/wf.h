@@ -209,7 +209,7 @@ int wf_launch_count(unsigned long long* n);
 
 /*
  * Launch-shape autotuner (no counterpart in the paper, whose solver runs on
- * CPU threads).  Five shapes are tuned (int shape[5]):
+ * CPU threads).  Six shapes are tuned (int shape[6]):
  *   shape[0]  lines per CTA of the first x pass of a step (rows staged per
  *             CTA; at most 8 warps' worth),
  *   shape[1]  lines per CTA of the y pass (columns per CTA, bounded by
@@ -217,9 +217,13 @@ int wf_launch_count(unsigned long long* n);
  *   shape[2]  element rows per segment of the streaming quadrature kernel,
  *   shape[3]  lines per warp of the x passes (1, 2 or 4; at most 32 / chunks
  *             per line, which is also the default),
- *   shape[4]  lines per CTA of the second x pass (which, for Peaceman-Rachford
- *             with one F per step, also forms its right-hand side);
- * 0 selects the launchers' built-in rule.  wf_autotune tunes one shape at a
+ *   shape[4]  lines per CTA of the second x pass,
+ *   shape[5]  where Peaceman-Rachford with one F per step forms the right-hand
+ *             side of its second x pass: 1 inside that pass (from staged rows
+ *             of T* and F), 2 in a tiled matvec kernel before it (one more
+ *             pass over R, but every thread busy on short lines);
+ * 0 selects the launchers' built-in rule (for shape[5]: inside the pass).
+ * Both schedules of shape[5] perform the same operations in the same order.  wf_autotune tunes one shape at a
  * time (two sweeps, the others held at their best values): for each
  * candidate it times reps steps (after one warm-up step) of the handle's
  * active slots and keeps the value whose step took least device time,
@@ -231,8 +235,8 @@ int wf_launch_count(unsigned long long* n);
  * collected under wf_set_profiling.  No active slot: WF_OK, nothing tuned.
  * Shapes never change the arithmetic of a line or an element.
  * Errors: WF_EINVAL (reps outside 1..100), WF_ENOMEM, WF_ECUDA.
- * wf_get_tuning / wf_set_tuning read and write the five values
- * (wf_set_tuning: each 0..1024, else WF_EINVAL).
+ * wf_get_tuning / wf_set_tuning read and write the six values
+ * (wf_set_tuning: shape[0..4] each 0..1024, shape[5] 0..2, else WF_EINVAL).
  */
 int wf_autotune(wf_handle* h, int reps);
 int wf_get_tuning(const wf_handle* h, int* shape);

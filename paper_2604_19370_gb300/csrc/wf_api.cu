@@ -32,7 +32,7 @@ using namespace wf;
 namespace {
 
 constexpr double kTmax = 1e5;  // guard on |T| (K)
-constexpr int kTune = 5;       // tuned launch shapes (wf_autotune)
+constexpr int kTune = 6;       // tuned launch shapes (wf_autotune)
 
 struct Arena {
     char* base = nullptr;
@@ -111,9 +111,10 @@ struct wf_handle {
     bool mms_on = false;       // manufactured-solution forcing (wf_set_mms)
     MmsArgs mms{};
     double* tdev = nullptr;    // device: start time of the next step (advanced only with forcing)
-    int tune[5] = {0, 0, 0, 0, 0};  // x lines per CTA (first x pass), y lines per CTA, quadrature
-                                    // segment rows, x lines per warp, x lines per CTA of the
-                                    // second x pass (0: the launchers' rules)
+    int tune[kTune] = {0, 0, 0, 0, 0, 0};  // x lines per CTA (first x pass), y lines per CTA,
+                                           // quadrature segment rows, x lines per warp, x lines
+                                           // per CTA of the second x pass, its right-hand side
+                                           // (1 fused, 2 separate matvec) (0: the launchers' rules)
     void *T = nullptr, *phi = nullptr, *F = nullptr, *Phi = nullptr, *R = nullptr;
     int* status = nullptr;
     void *fxq = nullptr, *gxq = nullptr, *fyq = nullptr, *gyq = nullptr;
@@ -611,7 +612,7 @@ cudaError_t enqueue_step_body(wf_handle* h) {
         if (once) add_line(y1, h->Phi, h->phi, Y[0], cy, h->phi);
         if ((e = timed(h, S_Y1, [&] { return launch_ysolve(prec, p, y1, s); })) != cudaSuccess) return e;
         bool fused = false;
-        if (once) {
+        if (once && h->tune[5] != 2) {
             // substep 2 in one x pass: R = th F + (op1_x (x) M^y) T* + (M^x (x) op1_y) T*, then M^x lines
             LineArgs x2 = line_args(h, 2);
             add_line(x2, nullptr, h->R, X[0], cx);
@@ -1166,6 +1167,7 @@ int wf_autotune(wf_handle* h, int reps) {
     static const int kSeg[] = {0, 128, 96, 80, 64, 56, 48, 40, 32, 28, 24, 21, 20, 16, 12};
     static const int kLines[] = {0, 32, 16, 8, 4, 2, 1};
     static const int kRpw[] = {0, 1, 2, 4};
+    static const int kFuse[] = {0, 2};
     struct Axis {
         int q;
         const int* v;
@@ -1175,7 +1177,8 @@ int wf_autotune(wf_handle* h, int reps) {
                           {0, kLines, (int)(sizeof(kLines) / sizeof(int))},
                           {3, kRpw, (int)(sizeof(kRpw) / sizeof(int))},
                           {1, kLines, (int)(sizeof(kLines) / sizeof(int))},
-                          {4, kLines, (int)(sizeof(kLines) / sizeof(int))}};
+                          {4, kLines, (int)(sizeof(kLines) / sizeof(int))},
+                          {5, kFuse, (int)(sizeof(kFuse) / sizeof(int))}};
     const size_t bytes = (size_t)h->sbytes * h->S;
     void* snap = nullptr;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;
@@ -1305,7 +1308,7 @@ int wf_get_tuning(const wf_handle* h, int* shape) {
 int wf_set_tuning(wf_handle* h, const int* shape) {
     if (!h || !shape) return WF_EINVAL;
     for (int q = 0; q < kTune; ++q)
-        if (shape[q] < 0 || shape[q] > 1024) return WF_EINVAL;
+        if (shape[q] < 0 || shape[q] > (q == 5 ? 2 : 1024)) return WF_EINVAL;
     for (int q = 0; q < kTune; ++q) h->tune[q] = shape[q];
     drop_graphs(h);
     return WF_OK;

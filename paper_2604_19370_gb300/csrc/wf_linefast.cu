@@ -1,4 +1,5 @@
-// Chunked line solves (TMA-staged x pass, column-parallel y pass) and the tiled Kronecker matvec.
+// Chunked line solves (TMA-staged x pass, column-parallel y pass) and the streaming Kronecker
+// matvec.
 //
 // Paper: Sec. 4 ("Cost of directional implicit solves"): each directional system
 // is a set of independent banded 1-D solves (half-bandwidth p) along x or y.
@@ -16,8 +17,6 @@
 // mbarrier); neighbouring chunks exchange boundary values by warp shuffles.
 // y pass: a CTA owns G columns; lanes of neighbouring columns read and write
 // contiguous runs of G elements per row, 16 loads in flight per thread.
-#include <type_traits>
-
 #include "wf_internal.h"
 
 namespace wf {
@@ -398,7 +397,7 @@ __device__ __forceinline__ void stage_factors(const LineView<P>& v, int mmax, co
 // (C <= lanes per line).
 // The G rows are contiguous in memory: one bulk copy stages them, one bulk store writes them back.
 // Chunk lengths are odd, so the 32 lanes of a warp read 32 distinct shared-memory banks.
-template <typename P, int PD>
+template <typename P, int PD, bool PRE>
 __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
     constexpr int W = 2 * PD + 1;
     if (!scene_active(a.b)) return;
@@ -413,7 +412,7 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
     const int rows = min(G, a.nlines - j0);
     const size_t row_bytes = (size_t)a.pitch * sizeof(P);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    const bool pre = a.preT != nullptr;
+    constexpr bool pre = PRE;
     const int sp = a.sp;                                           // shared-memory row stride
     P* rowbuf = reinterpret_cast<P*>(smem_raw + 128);             // [G][sp]
     // pre: T* rows j0-p .. j0+G+p-1 at stride tsp, values at column offset HO, zero halo columns
@@ -503,8 +502,9 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
         const P* __restrict__ bco = fm.end();  // [G][2][W], scaled by pc1 / pc2
         const int nt = blockDim.x;
         int nh = 1, rh = rows;
+        long best;
         {
-            long best = (long)((N + nt - 1) / nt) * (rows + 2 * PD);
+            best = (long)((N + nt - 1) / nt) * (rows + 2 * PD);
             for (int cand = 2; cand <= 8 && cand <= rows; cand *= 2) {
                 const int h = (rows + cand - 1) / cand;
                 const long cost = (long)((N * cand + nt - 1) / nt) * (h + 2 * PD);
@@ -515,9 +515,14 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
                 }
             }
         }
-        for (int item = tid; item < N * nh; item += nt) {
-            const int grp = item / N, x = item - grp * N;
-            const int r0 = grp * rh, r1 = min(rows, r0 + rh);
+        // alternatively every thread takes an equal run of L (column, row) pairs in column-major
+        // order (at most L / rows + 2 column pieces): no ragged last round when N is just above
+        // a multiple of the thread count
+        const long total = (long)N * rows;
+        const long L = (total + nt - 1) / nt;
+        const bool flat = L + 2 * PD * (L / rows + 2) < best;
+        // rows r0 .. r1-1 of column x
+        auto column_run = [&](int x, int r0, int r1) {
             P a1v[W], a2v[W], w1[W], w2[W];
 #pragma unroll
             for (int d = 0; d < W; ++d) {
@@ -552,6 +557,21 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
                     *rcol = acc;
                     rcol += sp;
                 }
+            }
+        };
+        if (flat) {
+            long s0 = (long)tid * L;
+            const long s1 = min(total, s0 + L);
+            while (s0 < s1) {
+                const int x = (int)(s0 / rows), r0 = (int)(s0 - (long)x * rows);
+                const int r1 = (int)min((long)rows, (long)r0 + (s1 - s0));
+                column_run(x, r0, r1);
+                s0 += r1 - r0;
+            }
+        } else {
+            for (int item = tid; item < N * nh; item += nt) {
+                const int grp = item / N, x = item - grp * N;
+                column_run(x, grp * rh, min(rows, grp * rh + rh));
             }
         }
         __syncthreads();
@@ -782,7 +802,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         f.sp = sp;
         f.tsp = tsp;
         f.tma = aligned ? 1 : 0;
-        auto kern = k_xsolve_warp<P, PD>;
+        auto kern = pre ? k_xsolve_warp<P, PD, true> : k_xsolve_warp<P, PD, false>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         dim3 grid((a.nlines + G - 1) / G, a.narr, a.b.S);
@@ -807,17 +827,24 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// ---- tiled explicit Kronecker matvec -------------------------------------------------
-// R = Fscale F + c1 (A1^x (x) B1^y) T + c2 (A2^x (x) B2^y) T on TX x TY tiles: the halo of T
-// is staged in shared memory, convolved along x with both x bands, then along y.
-template <typename P, int PD, int TX, int TY, int RY>
-__global__ void __launch_bounds__(TX*(TY / RY)) k_matvec_tile(int Nx, int Ny, int pitch, const P* __restrict__ T,
-                                                          const P* __restrict__ F, P* R, const P* __restrict__ A1,
-                                                          const P* __restrict__ B1, const P* __restrict__ A2,
-                                                          const P* __restrict__ B2, P Fscale, P c1, P c2,
-                                                          Batch b) {
-    constexpr int W = 2 * PD + 1, HY = TY + 2 * PD, HX = TX + 2 * PD, NTY = TY / RY;
+// ---- streaming explicit Kronecker matvec ---------------------------------------------
+// R = Fscale F + c1 (A1^x (x) B1^y) T + c2 (A2^x (x) B2^y) T.  A warp owns 32 columns (lane L
+// <-> column X0 - p + L; lanes p .. 31-p are outputs) and RS output rows: it issues every load
+// of its RS + 2p rows of T and RS rows of F first, x-convolves each row with neighbours'
+// values taken by shuffles, and reduces the y bands from registers.  No shared memory, no
+// barriers, every warp independent.  Values outside the domain are zeros, and the operations
+// (and their order) are those of the right-hand side fused into the x pass.
+template <typename P, int PD, int RS>
+__global__ void __launch_bounds__(128) k_matvec_stream(int Nx, int Ny, int pitch, const P* __restrict__ T,
+                                                       const P* __restrict__ F, P* R, const P* __restrict__ A1,
+                                                       const P* __restrict__ B1, const P* __restrict__ A2,
+                                                       const P* __restrict__ B2, P Fscale, P c1, P c2, Batch b,
+                                                       int nstrips, int nsegs) {
+    constexpr int W = 2 * PD + 1, NR = RS + 2 * PD;
     if (!scene_active(b)) return;
+    const int lane = threadIdx.x & 31;
+    const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (item >= nstrips * nsegs) return;  // whole warp
     T = scene_ptr(T, b);
     F = scene_ptr(F, b);
     R = scene_ptr(R, b);
@@ -825,49 +852,64 @@ __global__ void __launch_bounds__(TX*(TY / RY)) k_matvec_tile(int Nx, int Ny, in
     B1 = scene_ptr(B1, b);
     A2 = scene_ptr(A2, b);
     B2 = scene_ptr(B2, b);
-    __shared__ P h[HY][HX + 1];
-    __shared__ P x1[HY][TX + 1];
-    __shared__ P x2[HY][TX + 1];
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    for (int r = ty; r < HY; r += NTY)
-        for (int x = tx; x < HX; x += TX) {
-            const int gj = j0 - PD + r, gi = i0 - PD + x;
-            h[r][x] = (gj >= 0 && gj < Ny && gi >= 0 && gi < Nx) ? T[(size_t)gj * pitch + gi] : P(0);
-        }
-    __syncthreads();
-    const int i = i0 + tx;
-    const bool col_ok = i < Nx;
-    P a1[W], a2[W];
+    const int sg = item / nstrips, st = item - sg * nstrips;
+    const int x = st * (32 - 2 * PD) - PD + lane;  // this lane's column
+    const bool xok = x >= 0 && x < Nx;
+    const bool out = lane >= PD && lane < 32 - PD && x < Nx;
+    const int j0 = sg * RS;  // first output row
+    P tv[NR], fv[RS];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int r = j0 - PD + i;
+        tv[i] = (xok && r >= 0 && r < Ny) ? T[(size_t)r * pitch + x] : P(0);
+    }
+#pragma unroll
+    for (int i = 0; i < RS; ++i) {
+        const int r = j0 + i;
+        fv[i] = (out && r < Ny) ? F[(size_t)r * pitch + x] : P(0);
+    }
+    P a1v[W], a2v[W];
 #pragma unroll
     for (int d = 0; d < W; ++d) {
-        a1[d] = col_ok ? A1[(size_t)i * W + d] : P(0);
-        a2[d] = (col_ok && A2) ? A2[(size_t)i * W + d] : P(0);
+        a1v[d] = out ? A1[(size_t)x * W + d] : P(0);
+        a2v[d] = (out && A2) ? A2[(size_t)x * W + d] : P(0);
     }
-    for (int r = ty; r < HY; r += NTY) {
-        P s1 = 0, s2 = 0;
+    // x-convolution of every row (outputs lanes read lanes lane - p .. lane + p)
+    P w1[NR], w2[NR];
 #pragma unroll
-        for (int d = 0; d < W; ++d) {
-            s1 += a1[d] * h[r][tx + d];
-            s2 += a2[d] * h[r][tx + d];
+    for (int i = 0; i < NR; ++i) {
+        P t1 = 0, t2 = 0;
+#pragma unroll
+        for (int dk = 0; dk < W; ++dk) {
+            const P val = (dk == PD) ? tv[i] : __shfl_sync(0xffffffffu, tv[i], (lane - PD + dk) & 31);
+            t1 += a1v[dk] * val;
+            t2 += a2v[dk] * val;
         }
-        x1[r][tx] = s1;
-        x2[r][tx] = s2;
+        w1[i] = t1;
+        w2[i] = t2;
     }
-    __syncthreads();
-    if (!col_ok) return;
+    if (!out) return;
+    // y bands: rows 2p .. Ny-2p-1 all equal row 2p (held in registers), the others loaded
+    const bool has_yi = Ny > 4 * PD;
+    P b1i[W], b2i[W];
 #pragma unroll
-    for (int q = 0; q < RY; ++q) {
-        const int jl = ty * RY + q, j = j0 + jl;
+    for (int d = 0; d < W; ++d) {
+        b1i[d] = has_yi ? c1 * B1[(size_t)(2 * PD) * W + d] : P(0);
+        b2i[d] = (has_yi && A2) ? c2 * B2[(size_t)(2 * PD) * W + d] : P(0);
+    }
+#pragma unroll
+    for (int o = 0; o < RS; ++o) {
+        const int j = j0 + o;
         if (j >= Ny) break;
-        P r1 = 0, r2 = 0;
+        const bool yi = has_yi && j >= 2 * PD && j < Ny - 2 * PD;
+        P acc = Fscale * fv[o];
 #pragma unroll
-        for (int d = 0; d < W; ++d) {
-            r1 += B1[(size_t)j * W + d] * x1[jl + d][tx];
-            if (A2) r2 += B2[(size_t)j * W + d] * x2[jl + d][tx];
+        for (int dl = 0; dl < W; ++dl) {
+            const P b1 = yi ? b1i[dl] : c1 * B1[(size_t)j * W + dl];
+            const P b2 = yi ? b2i[dl] : (A2 ? c2 * B2[(size_t)j * W + dl] : P(0));
+            acc = fma(b1, w1[o + dl], fma(b2, w2[o + dl], acc));
         }
-        const size_t g = (size_t)j * pitch + i;
-        R[g] = Fscale * F[g] + c1 * r1 + c2 * r2;
+        R[(size_t)j * pitch + x] = acc;
     }
 }
 
@@ -896,26 +938,27 @@ cudaError_t launch_line_fast(int prec, int p, bool xdir, const LineArgs& a, cuda
 }
 
 cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s) {
-    constexpr int TX = 32, TY = 16, RY = 2;
-    dim3 grid((a.Nx + TX - 1) / TX, (a.Ny + TY - 1) / TY, a.b.S), block(TX, TY / RY);
-#define WF_MV(P, PD)                                                                                             \
-    k_matvec_tile<P, PD, TX, TY, RY><<<grid, block, 0, s>>>(a.Nx, a.Ny, a.pitch, (const P*)a.T, (const P*)a.F,   \
-                                                            (P*)a.R, (const P*)a.A1, (const P*)a.B1,             \
-                                                            (const P*)a.A2, (const P*)a.B2, (P)a.Fscale, (P)a.c1, \
-                                                            (P)a.c2, a.b)
+    constexpr int RS = 16, WARPS = 4;
+    if (p < 1 || p > 3) return cudaErrorInvalidValue;
+    const int nstrips = (a.Nx + (32 - 2 * p) - 1) / (32 - 2 * p), nsegs = (a.Ny + RS - 1) / RS;
+    const long items = (long)nstrips * nsegs;
+    dim3 grid((unsigned)((items + WARPS - 1) / WARPS), 1, a.b.S), block(32 * WARPS);
+#define WF_MV(P, PD)                                                                                         \
+    k_matvec_stream<P, PD, RS><<<grid, block, 0, s>>>(a.Nx, a.Ny, a.pitch, (const P*)a.T, (const P*)a.F,     \
+                                                      (P*)a.R, (const P*)a.A1, (const P*)a.B1, (const P*)a.A2, \
+                                                      (const P*)a.B2, (P)a.Fscale, (P)a.c1, (P)a.c2, a.b,      \
+                                                      nstrips, nsegs)
     if (prec == 0) {
         switch (p) {
             case 1: WF_MV(float, 1); break;
             case 2: WF_MV(float, 2); break;
             case 3: WF_MV(float, 3); break;
-            default: return cudaErrorInvalidValue;
         }
     } else {
         switch (p) {
             case 1: WF_MV(double, 1); break;
             case 2: WF_MV(double, 2); break;
             case 3: WF_MV(double, 3); break;
-            default: return cudaErrorInvalidValue;
         }
     }
 #undef WF_MV

@@ -258,24 +258,28 @@ def wf_launch_count() -> int:
     return int(n.value)
 
 
-def wf_autotune(h, reps: int = 3) -> Tuple[int, int, int, int, int]:
+def wf_autotune(h, reps: int = 3) -> Tuple[int, int, int, int, int, int]:
     """Tune the launch shapes of a handle on its active slots.
 
     Returns (x lines per CTA, y lines per CTA, quadrature segment rows, x lines per warp,
-    second-x-pass lines per CTA).
+    second-x-pass lines per CTA, second-x-pass right-hand side: 1 fused, 2 separate matvec).
+    0 is the launchers' rule.
     """
     _check(lib().wf_autotune(h, reps), "wf_autotune")
     return wf_get_tuning(h)
 
 
-def wf_get_tuning(h) -> Tuple[int, int, int, int, int]:
-    out = (ctypes.c_int * 5)()
+def wf_get_tuning(h) -> Tuple[int, int, int, int, int, int]:
+    out = (ctypes.c_int * 6)()
     _check(lib().wf_get_tuning(h, out), "wf_get_tuning")
     return tuple(int(v) for v in out)
 
 
 def wf_set_tuning(h, shape) -> None:
-    arr = (ctypes.c_int * 5)(*[int(v) for v in shape])
+    vals = [int(v) for v in shape]
+    if len(vals) != 6:
+        raise ValueError("wf_set_tuning: six values")
+    arr = (ctypes.c_int * 6)(*vals)
     _check(lib().wf_set_tuning(h, arr), "wf_set_tuning")
 
 

@@ -1,8 +1,9 @@
 """Launch-shape autotuner: shapes change the schedule, never the arithmetic.
 
 * every launch shape (x lines per CTA, y lines per CTA, quadrature segment rows,
-  x lines per warp, second-x-pass lines per CTA) gives bit-for-bit the trajectory of the launchers' own rule, single and batched,
-  FP32 and FP64, PR and Strang;
+  x lines per warp, second-x-pass lines per CTA, second-x-pass right-hand side fused or in a
+  separate matvec) gives bit-for-bit the trajectory of the launchers' own rule, single and
+  batched, FP32 and FP64, PR and Strang;
 * wf_autotune leaves the device state exactly as it found it and picks shapes
   from its candidate lists;
 * the tuned handle then matches the FP64 oracle within the parity bar.
@@ -15,8 +16,8 @@ from scenarios import make_scenario
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(0, 0, 0, 0, 0), (1, 1, 16, 1, 2), (8, 32, 128, 2, 1), (2, 4, 32, 4, 32), (4, 2, 64, 0, 8),
-          (32, 8, 16, 4, 16)]
+SHAPES = [(0, 0, 0, 0, 0, 0), (1, 1, 16, 1, 2, 2), (8, 32, 128, 2, 1, 1), (2, 4, 32, 4, 32, 2),
+          (4, 2, 64, 0, 8, 0), (32, 8, 16, 4, 16, 2)]
 
 
 @pytest.fixture(scope="module")
@@ -58,7 +59,7 @@ def test_autotune_keeps_state_and_parity(wf):
     shape = wf.wf_autotune(sim.h, 2)
     assert shape[0] in (0, 32, 16, 8, 4, 2, 1) and shape[1] in (0, 32, 16, 8, 4, 2, 1)
     assert shape[2] in (0, 128, 96, 80, 64, 56, 48, 40, 32, 28, 24, 21, 20, 16, 12) and shape[3] in (0, 1, 2, 4)
-    assert shape[4] in (0, 32, 16, 8, 4, 2, 1)
+    assert shape[4] in (0, 32, 16, 8, 4, 2, 1) and shape[5] in (0, 2)
     T1, p1 = sim.state()
     assert np.array_equal(T0, T1) and np.array_equal(p0, p1)
     sim.step(4)
@@ -99,6 +100,8 @@ def test_tuning_argument_checks(wf):
     sim = _sim(wf, sc, wf.WF_FP32, wf.WF_PR)
     L = wf.lib()
     assert L.wf_autotune(sim.h, 0) == wf.WF_EINVAL
-    bad = (wf.ctypes.c_int * 5)(1, -1, 0, 0, 0)
+    bad = (wf.ctypes.c_int * 6)(1, -1, 0, 0, 0, 0)
+    assert L.wf_set_tuning(sim.h, bad) == wf.WF_EINVAL
+    bad = (wf.ctypes.c_int * 6)(0, 0, 0, 0, 0, 3)
     assert L.wf_set_tuning(sim.h, bad) == wf.WF_EINVAL
     sim.close()
