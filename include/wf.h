@@ -224,9 +224,11 @@ int wf_launch_count(unsigned long long* n);
  *             pass over R, but every thread busy on short lines);
  * 0 selects the launchers' built-in rule (for shape[5]: inside the pass).
  * Both schedules of shape[5] perform the same operations in the same order.  wf_autotune tunes one shape at a
- * time (two sweeps, the others held at their best values): for each
- * candidate it times reps steps (after one warm-up step) of the handle's
- * active slots and keeps the value whose step took least device time,
+ * time (two sweeps, the others held at their best values): each candidate
+ * is timed in three rounds (the candidates in alternating order, so that a
+ * drift of the clocks favours none), each round reps steps (after one
+ * warm-up step) of the handle's active slots; the value whose fastest round
+ * took least device time is kept,
  * and restores every slot's device state afterwards, so the trajectory is
  * unchanged.  It needs a temporary device copy of the slot blocks
  * (S x the per-slot bytes, freed before return; WF_ENOMEM if it cannot be

@@ -1150,9 +1150,9 @@ int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], in
 // ---- autotuner ---------------------------------------------------------------------
 //
 // Launch shapes are chosen per handle by timing whole steps of the handle itself: the slot
-// blocks are saved, every candidate runs warm-up + `reps` eager steps with a CUDA event pair
-// around each launch, and the blocks are restored after each candidate, so the state after
-// wf_autotune equals the state before it.  Value 0 of each shape is the launchers' own rule.
+// blocks are saved, every candidate runs warm-up + `reps` eager steps timed by one CUDA event
+// pair, and the blocks are restored after each candidate, so the state after wf_autotune
+// equals the state before it.  Value 0 of each shape is the launchers' own rule.
 
 int wf_autotune(wf_handle* h, int reps) {
     if (!h || reps < 1 || reps > 100) return WF_EINVAL;
@@ -1181,6 +1181,9 @@ int wf_autotune(wf_handle* h, int reps) {
                           {5, kFuse, (int)(sizeof(kFuse) / sizeof(int))}};
     const size_t bytes = (size_t)h->sbytes * h->S;
     void* snap = nullptr;
+    // the slots' activity flags reach the device lazily (at the next step): send them now, or
+    // freshly loaded slots would be timed as inactive
+    if (upload_active(h) != cudaSuccess) return WF_ECUDA;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;
     if (cudaMalloc(&snap, bytes) != cudaSuccess) return WF_ENOMEM;
     int rc = WF_OK;
@@ -1189,41 +1192,65 @@ int wf_autotune(wf_handle* h, int reps) {
     for (int q = 0; q < kTune; ++q) saved[q] = best[q] = h->tune[q];
     if (cudaMemcpyAsync(snap, h->slots_mem, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
         rc = WF_ECUDA;
+    // the start time of the forcing, which every step advances
+    double t_start = 0.0;
+    if (h->mms_on && cudaMemcpy(&t_start, h->tdev, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = WF_ECUDA;
     drop_graphs(h);
-    h->profiling = true;
-    double ms[S_NSITES];
-    int cnt[S_NSITES];
-    // device time of reps steps (after one warm-up step) with the shapes in h->tune
+    h->profiling = false;
+    wf_kernel_times(h, nullptr, nullptr, nullptr, 0);  // discard kernel times collected so far
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess) rc = WF_ECUDA;
+    // device time of reps steps (after one warm-up step) with the shapes in h->tune, replayed from
+    // a captured one-step graph as wf_step runs them, under one event pair
     auto measure = [&](double* t) -> int {
-        for (int k = 0; k <= reps; ++k) {
-            if (k == 1) wf_kernel_times(h, nullptr, nullptr, nullptr, 0);  // drop the warm-up step
-            if (enqueue_step(h) != cudaSuccess) return WF_ECUDA;
-        }
-        if (wf_kernel_times(h, ms, cnt, nullptr, S_NSITES) < 0) return WF_ECUDA;
-        *t = 0.0;
-        for (int k = 0; k < S_NSITES; ++k) *t += ms[k];
+        cudaGraphExec_t ge = nullptr;
+        if (capture(h, 1, &ge) != cudaSuccess) return WF_ECUDA;
+        int r = WF_OK;
+        if (cudaGraphLaunch(ge, h->stream) != cudaSuccess || cudaEventRecord(ev0, h->stream) != cudaSuccess)
+            r = WF_ECUDA;
+        for (int k = 0; k < reps && r == WF_OK; ++k)
+            if (cudaGraphLaunch(ge, h->stream) != cudaSuccess) r = WF_ECUDA;
+        if (r == WF_OK && (cudaEventRecord(ev1, h->stream) != cudaSuccess || cudaEventSynchronize(ev1) != cudaSuccess))
+            r = WF_ECUDA;
+        float ms = 0.f;
+        if (r == WF_OK && cudaEventElapsedTime(&ms, ev0, ev1) != cudaSuccess) r = WF_ECUDA;
+        cudaGraphExecDestroy(ge);
+        if (r != WF_OK) return r;
+        *t = ms;
         if (cudaMemcpyAsync(h->slots_mem, snap, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+            return WF_ECUDA;
+        if (h->mms_on &&
+            cudaMemcpyAsync(h->tdev, &t_start, sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
             return WF_ECUDA;
         return WF_OK;
     };
+    // Each axis is timed in three rounds, the candidates in alternating order, and a candidate
+    // keeps its fastest round: a slow drift of the clocks under the sustained load (power
+    // capping) then favours no position in the list.
+    constexpr int kRounds = 3, kMaxCand = 16;
     for (int sweep = 0; sweep < 2 && rc == WF_OK; ++sweep)
         for (const Axis& ax : order) {
-            double best_t = 1e300;
-            int best_v = best[ax.q];
-            for (int i = 0; i < ax.n && rc == WF_OK; ++i) {
-                for (int q = 0; q < kTune; ++q) h->tune[q] = best[q];
-                h->tune[ax.q] = ax.v[i];
-                double t = 0.0;
-                rc = measure(&t);
-                if (rc == WF_OK && t < best_t) {
-                    best_t = t;
-                    best_v = ax.v[i];
+            double tmin[kMaxCand];
+            for (int i = 0; i < ax.n; ++i) tmin[i] = 1e300;
+            for (int round = 0; round < kRounds && rc == WF_OK; ++round)
+                for (int n = 0; n < ax.n && rc == WF_OK; ++n) {
+                    const int i = (round & 1) ? ax.n - 1 - n : n;
+                    for (int q = 0; q < kTune; ++q) h->tune[q] = best[q];
+                    h->tune[ax.q] = ax.v[i];
+                    double t = 0.0;
+                    rc = measure(&t);
+                    if (rc == WF_OK && t < tmin[i]) tmin[i] = t;
                 }
-            }
-            best[ax.q] = best_v;
+            int bi = -1;
+            for (int i = 0; i < ax.n; ++i)
+                if (bi < 0 || tmin[i] < tmin[bi]) bi = i;
+            if (bi >= 0) best[ax.q] = ax.v[bi];
         }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = WF_ECUDA;
     cudaFree(snap);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
     h->profiling = was_profiling;
     for (int q = 0; q < kTune; ++q) h->tune[q] = rc == WF_OK ? best[q] : saved[q];
     drop_graphs(h);

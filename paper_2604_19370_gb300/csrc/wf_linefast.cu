@@ -857,16 +857,28 @@ __global__ void __launch_bounds__(128) k_matvec_stream(int Nx, int Ny, int pitch
     const bool xok = x >= 0 && x < Nx;
     const bool out = lane >= PD && lane < 32 - PD && x < Nx;
     const int j0 = sg * RS;  // first output row
+    // interior segment: every T row it reads exists and every output row has the interior
+    // y bands (rows 2p .. Ny-2p-1 of a band all equal row 2p), so no row needs a guard
+    const bool yint = j0 >= 2 * PD && j0 + RS + 2 * PD <= Ny;
     P tv[NR], fv[RS];
+    if (yint) {
+        const P* tp = T + (size_t)(j0 - PD) * pitch + (xok ? x : 0);
+        const P* fp = F + (size_t)j0 * pitch + (xok ? x : 0);
 #pragma unroll
-    for (int i = 0; i < NR; ++i) {
-        const int r = j0 - PD + i;
-        tv[i] = (xok && r >= 0 && r < Ny) ? T[(size_t)r * pitch + x] : P(0);
-    }
+        for (int i = 0; i < NR; ++i) tv[i] = xok ? tp[(size_t)i * pitch] : P(0);
 #pragma unroll
-    for (int i = 0; i < RS; ++i) {
-        const int r = j0 + i;
-        fv[i] = (out && r < Ny) ? F[(size_t)r * pitch + x] : P(0);
+        for (int i = 0; i < RS; ++i) fv[i] = out ? fp[(size_t)i * pitch] : P(0);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int r = j0 - PD + i;
+            tv[i] = (xok && r >= 0 && r < Ny) ? T[(size_t)r * pitch + x] : P(0);
+        }
+#pragma unroll
+        for (int i = 0; i < RS; ++i) {
+            const int r = j0 + i;
+            fv[i] = (out && r < Ny) ? F[(size_t)r * pitch + x] : P(0);
+        }
     }
     P a1v[W], a2v[W];
 #pragma unroll
@@ -889,24 +901,32 @@ __global__ void __launch_bounds__(128) k_matvec_stream(int Nx, int Ny, int pitch
         w2[i] = t2;
     }
     if (!out) return;
-    // y bands: rows 2p .. Ny-2p-1 all equal row 2p (held in registers), the others loaded
-    const bool has_yi = Ny > 4 * PD;
-    P b1i[W], b2i[W];
+    if (yint) {
+        P b1i[W], b2i[W];
 #pragma unroll
-    for (int d = 0; d < W; ++d) {
-        b1i[d] = has_yi ? c1 * B1[(size_t)(2 * PD) * W + d] : P(0);
-        b2i[d] = (has_yi && A2) ? c2 * B2[(size_t)(2 * PD) * W + d] : P(0);
+        for (int d = 0; d < W; ++d) {
+            b1i[d] = c1 * B1[(size_t)(2 * PD) * W + d];
+            b2i[d] = A2 ? c2 * B2[(size_t)(2 * PD) * W + d] : P(0);
+        }
+        P* rp = R + (size_t)j0 * pitch + x;
+#pragma unroll
+        for (int o = 0; o < RS; ++o) {
+            P acc = Fscale * fv[o];
+#pragma unroll
+            for (int dl = 0; dl < W; ++dl) acc = fma(b1i[dl], w1[o + dl], fma(b2i[dl], w2[o + dl], acc));
+            rp[(size_t)o * pitch] = acc;
+        }
+        return;
     }
 #pragma unroll
     for (int o = 0; o < RS; ++o) {
         const int j = j0 + o;
         if (j >= Ny) break;
-        const bool yi = has_yi && j >= 2 * PD && j < Ny - 2 * PD;
         P acc = Fscale * fv[o];
 #pragma unroll
         for (int dl = 0; dl < W; ++dl) {
-            const P b1 = yi ? b1i[dl] : c1 * B1[(size_t)j * W + dl];
-            const P b2 = yi ? b2i[dl] : (A2 ? c2 * B2[(size_t)j * W + dl] : P(0));
+            const P b1 = c1 * B1[(size_t)j * W + dl];
+            const P b2 = A2 ? c2 * B2[(size_t)j * W + dl] : P(0);
             acc = fma(b1, w1[o + dl], fma(b2, w2[o + dl], acc));
         }
         R[(size_t)j * pitch + x] = acc;

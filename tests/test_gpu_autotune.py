@@ -105,3 +105,18 @@ def test_tuning_argument_checks(wf):
     bad = (wf.ctypes.c_int * 6)(0, 0, 0, 0, 0, 3)
     assert L.wf_set_tuning(sim.h, bad) == wf.WF_EINVAL
     sim.close()
+
+
+def test_autotune_keeps_forcing_time(wf):
+    # every step advances the manufactured solution's time; the tuner's steps must not
+    sc = make_scenario("mt", 40, 2, 1e-3, 1, 94)
+    sim = _sim(wf, sc, wf.WF_FP64, wf.WF_PR)
+    wf.wf_set_mms(sim.h, [(10.0, 1.0, 1.0, 0.5)], 300.0, 0.25)
+    sim.step(2)
+    t0 = wf.wf_get_time(sim.h)
+    T0, _ = sim.state()
+    wf.wf_autotune(sim.h, 1)
+    assert wf.wf_get_time(sim.h) == t0
+    T1, _ = sim.state()
+    assert np.array_equal(T0, T1)
+    sim.close()
