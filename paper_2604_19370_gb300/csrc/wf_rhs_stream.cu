@@ -30,6 +30,7 @@
 // columns; a segment recomputes p element rows above it.  Both overheads are
 // below 7 % for p = 2.
 #include <math.h>
+#include <stdint.h>
 
 
 #include "wf_internal.h"
@@ -405,7 +406,8 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 
 template <int PD, int WR, bool XB>
 __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, const ITab<float>& it,
-                                                   const ITabPairs& pt, int lane, int X0, int Y0, int Y1) {
+                                                   const ITabPairs& pt, int lane, int X0, int Y0, int Y1,
+                                                   float* wsm) {
     using P = float;
     constexpr int Q = PD + 1, NB = PD + 1, W = 2 * PD + 1, NC = 2 * PD + 1;
     constexpr int QP = Q / 2, QS = Q % 2, QPm = QP > 0 ? QP : 1, WRm = WR > 0 ? WR : 1;
@@ -541,16 +543,27 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
     };
 
     const PhysS<P>& c = a.c;
-    // wind factors of element row ey, loaded before the row's x interpolation so that their
-    // latency is hidden behind it
+    // wind factors of the element rows Y0-p .. Y1-1, staged in this warp's shared memory when the
+    // item starts ([r][row][b], x factors then y factors): the rows are then read with short
+    // latency, before the row's x interpolation
+    const int ey0 = Y0 - PD, nrow = Y1 - ey0;
+    if (WR > 0) {
+        for (int i = lane; i < WR * nrow * Q; i += 32) {
+            const int r = i / (nrow * Q), k = i - r * nrow * Q;
+            const size_t g = (size_t)r * a.ny * Q + (size_t)ey0 * Q + k;
+            wsm[i] = a.gxq[g];
+            wsm[WR * nrow * Q + i] = a.gyq[g];
+        }
+        __syncwarp();
+    }
     P gyr[WRm][Q], gxr[WRm][Q];
     auto load_wind_row = [&](int ey) {
 #pragma unroll
         for (int r = 0; r < WR; ++r)
 #pragma unroll
             for (int b = 0; b < Q; ++b) {
-                gxr[r][b] = a.gxq[(size_t)r * a.ny * Q + ey * Q + b];
-                gyr[r][b] = a.gyq[(size_t)r * a.ny * Q + ey * Q + b];
+                gxr[r][b] = wsm[(r * nrow + (ey - ey0)) * Q + b];
+                gyr[r][b] = wsm[WR * nrow * Q + (r * nrow + (ey - ey0)) * Q + b];
             }
     };
     auto element_row = [&]() {
@@ -624,7 +637,6 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
     };
 
     // prologue: rows Y0-2p .. Y0-1 (matvec window), of which Y0-p .. Y0-1 also enter the x window
-    const int ey0 = Y0 - PD;
 #pragma unroll
     for (int d = 0; d < 2 * PD; ++d) {
         const int r = Y0 - 2 * PD + d;
@@ -744,6 +756,7 @@ struct RhsOcc {
 
 template <typename P, int PD, int WR, int MODE>
 __global__ void __launch_bounds__(32, RhsOcc<P, PD, WR, MODE>::value) k_rhs_stream(const StreamArgs<P> a_in) {
+    extern __shared__ float wind_rows[];  // FP32 packed form: the item's wind factors
     if (!scene_active(a_in.b)) return;
     StreamArgs<P> a = a_in;
     a.T = scene_ptr(a.T, a.b);
@@ -814,9 +827,9 @@ __global__ void __launch_bounds__(32, RhsOcc<P, PD, WR, MODE>::value) k_rhs_stre
         // strips of interior segments with x tables in registers, boundary segments general.
         // MODE 2 runs in FP32 only where no strip is interior.
         if (MODE == 0)
-            stream_strip_pairs<PD, WR, false>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1);
+            stream_strip_pairs<PD, WR, false>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1, wind_rows);
         else if (yint)
-            stream_strip_pairs<PD, WR, true>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1);
+            stream_strip_pairs<PD, WR, true>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1, wind_rows);
         else
             stream_strip<P, PD, WR, false>(a, a_in.it, lane, X0, Y0, Y1);
     } else {
@@ -845,6 +858,22 @@ PhysS<P> to_phys_s(const Phys& c, double tau) {
     o.Ta_l2 = (P)(c.T_a * 1.4426950408889634074);  // log2(e)
     o.heat_by_fuel = c.heat_by_fuel;
     return o;
+}
+
+// Dynamic shared memory of a launch whose packed-form items span at most seg + p element rows:
+// 2 WR (p+1) wind factors per row (none in FP64 or without wind variation); above the default
+// 48 KB the kernel is opted in to more; SIZE_MAX if it cannot be had.
+template <typename P, int PD, int WR, int MODE>
+size_t wind_smem(int seg) {
+    if (sizeof(P) != 4 || WR == 0) return 0;
+    const size_t bytes = (size_t)2 * WR * (PD + 1) * (seg + PD) * sizeof(float);
+    if (bytes > 48 * 1024) {
+        if (bytes > 227 * 1024) return SIZE_MAX;
+        if (cudaFuncSetAttribute(k_rhs_stream<P, PD, WR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes) != cudaSuccess)
+            return SIZE_MAX;
+    }
+    return bytes;
 }
 
 template <typename P, int PD, int WR>
@@ -975,12 +1004,14 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
             if ((e = cudaEventRecord(r.ev_fork, s)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(r.aux, r.ev_fork, 0)) != cudaSuccess) return e;
         }
+        const size_t wb0 = wind_smem<P, PD, WR, 0>(a.seg), wb1 = wind_smem<P, PD, WR, 1>(a.seg_b);
+        if (wb0 == SIZE_MAX || wb1 == SIZE_MAX) return cudaErrorInvalidValue;
         dim3 g1((unsigned)((n_side + WARPS - 1) / WARPS), 1, r.b.S);
-        k_rhs_stream<P, PD, WR, 1><<<g1, 32 * WARPS, 0, s1>>>(a);
+        k_rhs_stream<P, PD, WR, 1><<<g1, 32 * WARPS, wb1, s1>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         count_launches(1);
         dim3 g0((unsigned)((n_fast + WARPS - 1) / WARPS), 1, r.b.S);
-        k_rhs_stream<P, PD, WR, 0><<<g0, 32 * WARPS, 0, s>>>(a);
+        k_rhs_stream<P, PD, WR, 0><<<g0, 32 * WARPS, wb0, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         count_launches(1);
         if (fork) {
@@ -990,7 +1021,9 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
         return cudaSuccess;
     }
     dim3 grid((unsigned)((n_all + WARPS - 1) / WARPS), 1, r.b.S);
-    k_rhs_stream<P, PD, WR, 2><<<grid, 32 * WARPS, 0, s>>>(a);
+    const size_t wb2 = wind_smem<P, PD, WR, 2>(a.seg);
+    if (wb2 == SIZE_MAX) return cudaErrorInvalidValue;
+    k_rhs_stream<P, PD, WR, 2><<<grid, 32 * WARPS, wb2, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
