@@ -69,8 +69,9 @@ def algorithmic_costs(p: int, fused_x2: bool = True) -> dict:
         # two arrays: read solve input and base, write result
         "ysolve_1": dict(bytes=24, flops=2 * (4 * p + 2) * 2),
         # read T*, F; write R
-        "matvec_2": dict(bytes=12, flops=2 * 2 * (W * W + W) + 2),
-        "xsolve_2": (dict(bytes=12, flops=2 * 2 * (W * W + W) + 2 + (4 * p + 1) * 2) if fused_x2
+        # sum-factorised: both x bands (W taps each) on T, both y bands on the results, scale F
+        "matvec_2": dict(bytes=12, flops=2 * (2 * W) * 2 + 2),
+        "xsolve_2": (dict(bytes=12, flops=2 * (2 * W) * 2 + 2 + (4 * p + 1) * 2) if fused_x2
                      else dict(bytes=8, flops=(4 * p + 1) * 2)),
         "ysolve_2": dict(bytes=12, flops=(4 * p + 2) * 2),
     }
