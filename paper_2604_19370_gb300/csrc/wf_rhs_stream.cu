@@ -32,6 +32,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 
 #include "wf_internal.h"
 
@@ -43,6 +45,7 @@ template <typename P>
 struct PhysS {
     P K_ign, chiTamb, c_rad, T_amb, T_amb2, C_nld, c_W, T_ig, phi_min, T_a, tau_kf;
     P K0;    // c_chi T_amb + c_rad T_amb^4: the constant part of the point source
+    P T_ig_lo;  // T_ig (1 - 1e-5): below it no point of an element row can ignite
     P Ta_l2; // T_a log2(e)
     int heat_by_fuel;
 };
@@ -566,19 +569,24 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
                 gyr[r][b] = wsm[WR * nrow * Q + (r * nrow + (ey - ey0)) * Q + b];
             }
     };
-    auto element_row = [&]() {
+    // one element row.  HOT: some point may exceed the ignition temperature, so the reaction term
+    // is evaluated point by point; otherwise it is zero at every point (E = 0: no reaction source,
+    // no fuel change), which is exactly what the point-by-point test would give
+    auto element_row_body = [&](auto hot_c) {
+        constexpr bool HOT = decltype(hot_c)::value;
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
 #pragma unroll
             for (int j = 0; j < QP; ++j) {
                 float2 T = mul2(f2(it.by[b][0]), xv2[0][j]), Ty = mul2(f2(it.dy[b][0]), xv2[0][j]);
-                float2 Tx = mul2(f2(it.by[b][0]), xd2[0][j]), ph = mul2(f2(it.by[b][0]), xp2[0][j]);
+                float2 Tx = mul2(f2(it.by[b][0]), xd2[0][j]), ph = f2(0.f);
+                if (HOT) ph = mul2(f2(it.by[b][0]), xp2[0][j]);
 #pragma unroll
                 for (int l = 1; l < NB; ++l) {
                     T = fma2(f2(it.by[b][l]), xv2[l][j], T);
                     Ty = fma2(f2(it.dy[b][l]), xv2[l][j], Ty);
                     Tx = fma2(f2(it.by[b][l]), xd2[l][j], Tx);
-                    ph = fma2(f2(it.by[b][l]), xp2[l][j], ph);
+                    if (HOT) ph = fma2(f2(it.by[b][l]), xp2[l][j], ph);
                 }
                 float2 bpx = f2(0.f), bpy = f2(0.f);
 #pragma unroll
@@ -586,21 +594,25 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
                     bpx = fma2(fx2[r][j], f2(gxr[r][b]), bpx);
                     bpy = fma2(fy2[r][j], f2(gyr[r][b]), bpy);
                 }
-                const bool bx0 = (T.x > c.T_ig) && (ph.x > c.phi_min);
-                const bool bx1 = (T.y > c.T_ig) && (ph.y > c.phi_min);
-                const float2 E = make_float2(bx0 ? T.x * arrhenius<P>(c, T.x) : P(0),
-                                             bx1 ? T.y * arrhenius<P>(c, T.y) : P(0));
                 const float2 T2 = mul2(T, T);
                 const float2 T3 = mul2(T2, T);
-                const float2 EP = mul2(E, ph);
-                float2 src = fma2(f2(c.K_ign), c.heat_by_fuel ? EP : E, fma2(f2(-c.c_rad), mul2(T2, T2), f2(c.K0)));
+                float2 src = fma2(f2(-c.c_rad), mul2(T2, T2), f2(c.K0));
+                float2 EP = f2(0.f);
+                if (HOT) {
+                    const bool bx0 = (T.x > c.T_ig) && (ph.x > c.phi_min);
+                    const bool bx1 = (T.y > c.T_ig) && (ph.y > c.phi_min);
+                    const float2 E = make_float2(bx0 ? T.x * arrhenius<P>(c, T.x) : P(0),
+                                                 bx1 ? T.y * arrhenius<P>(c, T.y) : P(0));
+                    EP = mul2(E, ph);
+                    src = fma2(f2(c.K_ign), c.heat_by_fuel ? EP : E, src);
+                }
                 if (WR > 0) src = fma2(f2(-c.c_W), fma2(bpx, Tx, mul2(bpy, Ty)), src);
                 const float2 t3x = mul2(T3, Tx), t3y = mul2(T3, Ty);
 #pragma unroll
                 for (int l = 0; l < NB; ++l) {
                     as2[l][j] = fma2(pt.ys[b][l][j], src, fma2(pt.yd[b][l][j], t3y, as2[l][j]));
                     aq2[l][j] = fma2(pt.yq[b][l][j], t3x, aq2[l][j]);
-                    ag2[l][j] = fma2(pt.yg[b][l][j], EP, ag2[l][j]);
+                    if (HOT) ag2[l][j] = fma2(pt.yg[b][l][j], EP, ag2[l][j]);
                 }
             }
             if (QS) {
@@ -611,7 +623,7 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
                     T += it.by[b][l] * xvs[l];
                     Ty += it.dy[b][l] * xvs[l];
                     Tx += it.by[b][l] * xds[l];
-                    ph += it.by[b][l] * xps[l];
+                    if (HOT) ph += it.by[b][l] * xps[l];
                 }
                 P bpx = 0, bpy = 0;
 #pragma unroll
@@ -619,21 +631,41 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
                     bpx += fxs[r] * gxr[r][b];
                     bpy += fys[r] * gyr[r][b];
                 }
-                const bool burn = (T > c.T_ig) && (ph > c.phi_min);
-                const P E = burn ? T * arrhenius<P>(c, T) : P(0);
                 const P T2 = T * T, T3 = T2 * T;
-                const P EP = E * ph;
-                P src = fma(c.K_ign, c.heat_by_fuel ? EP : E, fma(-c.c_rad, T2 * T2, c.K0));
+                P src = fma(-c.c_rad, T2 * T2, c.K0);
+                P EP = P(0);
+                if (HOT) {
+                    const bool burn = (T > c.T_ig) && (ph > c.phi_min);
+                    const P E = burn ? T * arrhenius<P>(c, T) : P(0);
+                    EP = E * ph;
+                    src = fma(c.K_ign, c.heat_by_fuel ? EP : E, src);
+                }
                 if (WR > 0) src = fma(-c.c_W, fma(bpx, Tx, bpy * Ty), src);
                 const P t3x = T3 * Tx, t3y = T3 * Ty;
 #pragma unroll
                 for (int l = 0; l < NB; ++l) {
                     ass[l] = fma(it.ys[b][q][l], src, fma(it.yd[b][q][l], t3y, ass[l]));
                     aqs[l] = fma(it.yq[b][q][l], t3x, aqs[l]);
-                    ags[l] = fma(it.yg[b][q][l], EP, ags[l]);
+                    if (HOT) ags[l] = fma(it.yg[b][q][l], EP, ags[l]);
                 }
             }
         }
+    };
+
+    auto element_row = [&]() {
+        // largest x-interpolated T of the element's coefficient rows: the y interpolation, with
+        // nonnegative basis values summing to one, cannot exceed it at any point
+        P m = QS ? xvs[0] : xv2[0][0].x;
+#pragma unroll
+        for (int l = 0; l < NB; ++l) {
+#pragma unroll
+            for (int j = 0; j < QP; ++j) m = fmaxf(m, fmaxf(xv2[l][j].x, xv2[l][j].y));
+            if (QS) m = fmaxf(m, xvs[l]);
+        }
+        if (__any_sync(FULL, m > c.T_ig_lo))
+            element_row_body(std::true_type{});
+        else
+            element_row_body(std::false_type{});
     };
 
     // prologue: rows Y0-2p .. Y0-1 (matvec window), of which Y0-p .. Y0-1 also enter the x window
@@ -744,14 +776,14 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
 // the short boundary segments last, each warp taking the fast or the general form.  With
 // FP32 the items are split between two launches whose register budgets differ: MODE 0 runs the
 // interior items (interior strip x interior segment: the packed form with constant tables,
-// which needs few registers, so twenty one-warp CTAs fit an SM without wind variation, sixteen
-// with rank 1, fourteen with rank 2) and MODE 1 the rest, twelve per SM: the boundary strips
+// which needs few registers, so sixteen one-warp CTAs fit an SM) and MODE 1 the rest, twelve
+// per SM: the boundary strips
 // of the interior segments in the packed form with x tables in registers (on segments of
 // their own, shorter height) and the boundary segments in the general form.  One warp per
 // CTA, so that a warp slot frees as soon as its own item ends.
 template <typename P, int PD, int WR, int MODE>
 struct RhsOcc {
-    static constexpr int value = sizeof(P) != 4 || PD > 2 ? 1 : (MODE == 0 ? (WR == 2 ? 14 : (WR == 1 ? 16 : 20)) : 12);
+    static constexpr int value = sizeof(P) != 4 || PD > 2 ? 1 : (MODE == 0 ? 16 : 12);
 };
 
 template <typename P, int PD, int WR, int MODE>
@@ -851,6 +883,7 @@ PhysS<P> to_phys_s(const Phys& c, double tau) {
     o.C_nld = (P)c.C_nld;
     o.c_W = (P)c.c_W;
     o.T_ig = (P)c.T_ig;
+    o.T_ig_lo = (P)(c.T_ig * (1.0 - 1e-5));
     o.phi_min = (P)c.phi_min;
     o.T_a = (P)c.T_a;
     o.tau_kf = (P)(tau * c.k_f);

@@ -229,3 +229,20 @@ def test_wind_change_between_steps(wf):
     sc0 = dataclasses.replace(sc, wind_rank=0)
     To, po = oracle_run(sc0, 3, T0=T1, phi0=p1)
     assert rel(T, To) <= 1e-10
+
+
+@pytest.mark.parametrize("wind", [(0.0, 0.0), (1.3, -0.6)])
+def test_fp32_hot_rows(wf, wind):
+    # 700 K with three coefficient rows partly at 1100 K: only the element rows whose window holds
+    # a hot row can reach the ignition temperature (800 K), so warps of the FP32 quadrature take
+    # the form that skips the reaction term next to warps that evaluate it point by point.  One
+    # step from these values keeps every Gauss point far from the threshold (the oracle's result
+    # does not move when T_ig moves by 1e-3 K), while the reaction changes T by about 1 %.
+    sc = make_scenario("ign", 96, 2, 1e-3, 1, 611, wind=wind, fuel_sigma=3.0)
+    rng = np.random.default_rng(612)
+    T0 = np.full(sc.T0.shape, 700.0)
+    for r in (20, 47, 71):
+        T0[r, rng.random(T0.shape[1]) < 0.3] = 1100.0
+    T, phi = gpu_run(wf, sc, 1, wf.WF_FP32, T0=T0)
+    To, po = oracle_run(sc, 1, T0=T0)
+    assert rel(T, To) <= 1e-5 and rel(phi, po) <= 1e-5
