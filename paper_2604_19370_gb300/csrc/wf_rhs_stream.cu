@@ -255,8 +255,19 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
                 gxr[r][b] = a.gxq[(size_t)r * a.ny * Q + ey * Q + b];
                 gyr[r][b] = a.gyq[(size_t)r * a.ny * Q + ey * Q + b];
             }
-        if (!ex_ok) return;
         const PhysS<P>& c = a.c;
+        // no point of the row can reach the ignition temperature unless the largest x-interpolated
+        // T of its coefficient rows does (nonnegative y basis values summing to one): one warp
+        // vote decides whether the reaction term is evaluated point by point or is zero everywhere
+        P m = P(-1e30);
+#pragma unroll
+        for (int l = 0; l < NB; ++l)
+#pragma unroll
+            for (int q = 0; q < Q; ++q) m = xv[l][q] > m ? xv[l][q] : m;
+        const bool hot = __any_sync(FULL, ex_ok && m > c.T_ig_lo);
+        if (!ex_ok) return;
+        auto points = [&](auto hot_c) {
+        constexpr bool HOT = decltype(hot_c)::value;
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
 #pragma unroll
@@ -267,7 +278,7 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
                     T += WF_BY(b, l) * xv[l][q];
                     Ty += WF_DY(b, l) * xv[l][q];
                     Tx += WF_BY(b, l) * xd[l][q];
-                    ph += WF_BY(b, l) * xp[l][q];
+                    if (HOT) ph += WF_BY(b, l) * xp[l][q];
                 }
                 P bpx = 0, bpy = 0;
 #pragma unroll
@@ -276,11 +287,15 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
                     bpy += fyr[r][q] * gyr[r][b];
                 }
                 // point source: K_ign E (+ c_chi T_amb + c_rad (T_amb^4 - T^4)) - c_W b'.grad T
-                const bool burn = (T > c.T_ig) && (ph > c.phi_min);
-                const P E = burn ? T * arrhenius<P>(c, T) : P(0);
                 const P T2 = T * T, T3 = T2 * T;
-                const P EP = E * ph;
-                P src = fma(c.K_ign, c.heat_by_fuel ? EP : E, fma(-c.c_rad, T2 * T2, c.K0));
+                P src = fma(-c.c_rad, T2 * T2, c.K0);
+                P EP = P(0);
+                if (HOT) {
+                    const bool burn = (T > c.T_ig) && (ph > c.phi_min);
+                    const P E = burn ? T * arrhenius<P>(c, T) : P(0);
+                    EP = E * ph;
+                    src = fma(c.K_ign, c.heat_by_fuel ? EP : E, src);
+                }
                 if (WR > 0) src = fma(-c.c_W, fma(bpx, Tx, bpy * Ty), src);
                 const P t3x = T3 * Tx, t3y = T3 * Ty;
                 if constexpr (YI) {
@@ -288,7 +303,7 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
                     for (int l = 0; l < NB; ++l) {
                         acs[l][q] = fma(it.ys[b][q][l], src, fma(it.yd[b][q][l], t3y, acs[l][q]));
                         acq[l][q] += it.yq[b][q][l] * t3x;
-                        acg[l][q] += it.yg[b][q][l] * EP;
+                        if (HOT) acg[l][q] += it.yg[b][q][l] * EP;
                     }
                 } else {
                     const P S = it.wq[b][q] * src, QX = it.wqc[b][q] * t3x, QY = it.wqc[b][q] * t3y;
@@ -297,11 +312,16 @@ __device__ __forceinline__ void stream_strip(const StreamArgs<P>& a, const ITab<
                     for (int l = 0; l < NB; ++l) {
                         acs[l][q] = fma(WF_BY(b, l), S, fma(WF_DY(b, l), QY, acs[l][q]));
                         acq[l][q] += WF_BY(b, l) * QX;
-                        acg[l][q] += WF_BY(b, l) * G;
+                        if (HOT) acg[l][q] += WF_BY(b, l) * G;
                     }
                 }
             }
         }
+        };
+        if (hot)
+            points(std::true_type{});
+        else
+            points(std::false_type{});
 #undef WF_BY
 #undef WF_DY
     };
