@@ -313,7 +313,7 @@ def run_gpu(args) -> None:
     stream = torch.cuda.Stream(device=dev)
     wf.wf_set_stream(sim.h, stream.cuda_stream)
     # launch shapes tuned on this handle (its state is restored afterwards)
-    tuning = pick_shapes(wf, sim.h, args, 10)
+    tuning = pick_shapes(wf, sim.h, args, 40)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     props = torch.cuda.get_device_properties(dev)
 
@@ -514,7 +514,7 @@ def run_ensemble(args) -> None:
         b.load_scenario(k, sc)
     stream = torch.cuda.Stream(device=dev)
     wf.wf_set_stream(b.h, stream.cuda_stream)
-    tuning = pick_shapes(wf, b.h, args, 6)
+    tuning = pick_shapes(wf, b.h, args, 12)
     dofs = S * first.dofs
     with torch.cuda.stream(stream):
         b.step(args.warmup)

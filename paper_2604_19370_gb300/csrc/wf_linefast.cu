@@ -623,12 +623,12 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
 
 // y pass.  CTA = G columns x C chunks (blockDim = G*C <= 256); thread tid = k*G + c owns chunk k
 // of column c in its private shared-memory strip (odd stride: distinct banks).  The column values
-// are loaded 16 rows at a time and eliminated forward as they arrive, so the strip is written
+// are loaded 16 or 32 rows at a time and eliminated forward as they arrive, so the strip is written
 // once before the backward sweep; the increment base is added on the final store.  Threads of
 // columns past the last line solve a copy of the last line and store nothing.
-template <typename P, int PD>
+template <typename P, int PD, int B>
 __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
-    constexpr int W = 2 * PD + 1, B = 16, B2 = 8;
+    constexpr int W = 2 * PD + 1, B2 = 8;
     constexpr int NF = FacW<PD>::F, NU = FacW<PD>::U, NS = FacW<PD>::S;
     if (!scene_active(a.b)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -817,10 +817,15 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         if (smem > 227 * 1024) return cudaErrorNotSupported;
         f.G = G;
         f.tma = 0;
-        auto kern = k_ysolve_cols<P, PD>;
+        // rows loaded per batch: 32 when the launch leaves at most two CTAs per SM (its threads then
+        // wait on load latency, and more loads in flight pay), else 16 (fewer registers, more CTAs)
+        dim3 grid((a.nlines + G - 1) / G, a.narr, a.b.S);
+        int sms = 152, dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const bool wide = (long)grid.x * grid.y * grid.z <= 2L * sms;
+        auto kern = wide ? k_ysolve_cols<P, PD, 32> : k_ysolve_cols<P, PD, 16>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        dim3 grid((a.nlines + G - 1) / G, a.narr, a.b.S);
         kern<<<grid, nt, smem, s>>>(f);
         count_launches(1);
     }
