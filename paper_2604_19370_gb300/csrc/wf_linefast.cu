@@ -834,7 +834,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
 
 // ---- streaming explicit Kronecker matvec ---------------------------------------------
 // R = Fscale F + c1 (A1^x (x) B1^y) T + c2 (A2^x (x) B2^y) T.  A warp owns 32 columns (lane L
-// <-> column X0 - p + L; lanes p .. 31-p are outputs) and RS output rows: it issues every load
+// <-> column X0 - p + L; lanes p .. 31-p are outputs) and RS (8) output rows: it issues every load
 // of its RS + 2p rows of T and RS rows of F first, x-convolves each row with neighbours'
 // values taken by shuffles, and reduces the y bands from registers.  No shared memory, no
 // barriers, every warp independent.  Values outside the domain are zeros, and the operations
@@ -963,7 +963,7 @@ cudaError_t launch_line_fast(int prec, int p, bool xdir, const LineArgs& a, cuda
 }
 
 cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s) {
-    constexpr int RS = 16, WARPS = 4;
+    constexpr int RS = 8, WARPS = 4;
     if (p < 1 || p > 3) return cudaErrorInvalidValue;
     const int nstrips = (a.Nx + (32 - 2 * p) - 1) / (32 - 2 * p), nsegs = (a.Ny + RS - 1) / RS;
     const long items = (long)nstrips * nsegs;
