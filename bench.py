@@ -361,19 +361,24 @@ def run_gpu(args) -> None:
     if sim.sync() != wf.WF_OK:
         status = wf.WF_EUNSTABLE
 
-    # end to end through the C ABI with pinned host buffers: set state, one step, read state
+    # end to end through the C ABI with pinned host buffers: set state, one step, read state; the
+    # host arrays are in the handle's working precision (float32 calls for the FP32 path)
     n = sc.dofs
-    hT = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    hP = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hdt = torch.float64 if args.fp64 else torch.float32
+    es = 8 if args.fp64 else 4
+    hT = torch.empty(n, dtype=hdt, pin_memory=True)
+    hP = torch.empty(n, dtype=hdt, pin_memory=True)
     hT.numpy()[:] = sc.T0.ravel()
     hP.numpy()[:] = sc.fuel0.ravel()
+    set_ptr = wf.wf_set_state_ptr if args.fp64 else wf.wf_set_state_f32_ptr
+    get_ptr = wf.wf_get_state_ptr if args.fp64 else wf.wf_get_state_f32_ptr
     e2e_steps = max(3, min(args.steps, 20))
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        wf.wf_set_state_ptr(sim.h, hT.data_ptr(), hP.data_ptr(), n)
+        set_ptr(sim.h, hT.data_ptr(), hP.data_ptr(), n)
         wf.wf_step(sim.h, 1)
-        wf.wf_get_state_ptr(sim.h, hT.data_ptr(), hP.data_ptr(), n)
+        get_ptr(sim.h, hT.data_ptr(), hP.data_ptr(), n)
     e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dev)
 
     # roofline of the dominant kernel class
@@ -445,8 +450,9 @@ def run_gpu(args) -> None:
         "profiled_ms_per_step": prof_ms_per_step,
         "kernels": kernels,
         "gpu_launches": launches,
-        "e2e": {"value": world * sc.dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n,
-                "d2h_bytes_per_step": 2 * 8 * n, "ms_per_step": e2e_s * 1e3},
+        "e2e": {"value": world * sc.dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * es * n,
+                "d2h_bytes_per_step": 2 * es * n, "ms_per_step": e2e_s * 1e3,
+                "host_dtype": "float64" if args.fp64 else "float32"},
         "clocks": clk.summary(),
         "status": wf.wf_strerror(status),
     }
@@ -560,18 +566,22 @@ def run_ensemble(args) -> None:
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"]}
     roof.update({"kernel": dom, "ms_per_launch": dom_ms, "traffic": None})
     step_bytes = sum(costs[k]["bytes"] for k in costs if k in shares) * dofs
-    # end to end through the C ABI: load every slot from host memory, one step, read every slot back
+    # end to end through the C ABI: every slot's state from pinned float32 host arrays in one call,
+    # one step, every slot's state back in one call
     n = first.dofs
-    hT = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    hP = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    e2e_steps = 2
+    hT = torch.empty(S * n, dtype=torch.float32, pin_memory=True)
+    hP = torch.empty(S * n, dtype=torch.float32, pin_memory=True)
+    for k, sc in enumerate(scs):
+        hT.numpy()[k * n:(k + 1) * n] = sc.T0.ravel()
+        hP.numpy()[k * n:(k + 1) * n] = sc.fuel0.ravel()
+    wf.wf_batch_states_ptr(b.h, hT.data_ptr(), hP.data_ptr(), S * n, True, True)  # staging allocated here
+    e2e_steps = 5
+    torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for k, sc in enumerate(scs):
-            wf.wf_batch_set_slot(b.h, k, sc.T0, sc.fuel0, sc.wind[0], sc.wind[1], 0, None)
+        wf.wf_batch_states_ptr(b.h, hT.data_ptr(), hP.data_ptr(), S * n, True, True)
         wf.wf_step(b.h, 1)
-        for k in range(S):
-            b.state(k)
+        wf.wf_batch_states_ptr(b.h, hT.data_ptr(), hP.data_ptr(), S * n, True, False)
     e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -588,8 +598,8 @@ def run_ensemble(args) -> None:
         "step_hbm_frac_kernel_bytes": step_bytes / (slowest / args.steps) / 1e9 / peaks["hbm_gbs"],
         "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in kt.items() if v[1] > 0},
         "gpu_launches": ens_launches,
-        "e2e": {"value": world * dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * dofs,
-                "d2h_bytes_per_step": 2 * 8 * dofs, "ms_per_step": e2e_s * 1e3},
+        "e2e": {"value": world * dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * dofs,
+                "d2h_bytes_per_step": 2 * 4 * dofs, "ms_per_step": e2e_s * 1e3, "host_dtype": "float32"},
         "clocks": clk.summary(),
         "unstable_slots": int(st.sum()),
     }

@@ -107,6 +107,15 @@ int wf_create(int nx, int ny, int p, double dt, const wf_params* params, wf_hand
 int wf_set_state(wf_handle* h, const double* T, const double* fuel, size_t n);
 
 /*
+ * wf_set_state with float32 host arrays (n = Nx*Ny values each, [Ny][Nx]):
+ * half the bytes over the host link for a handle that computes in FP32
+ * (an FP64 handle widens them).  The arrays are the caller's; pinned
+ * memory makes the copy asynchronous to the host.  Same waiting and
+ * errors as wf_set_state.
+ */
+int wf_set_state_f32(wf_handle* h, const float* T, const float* fuel, size_t n);
+
+/*
  * Set the explicit, spatially varying part b'(x, y) of the wind:
  *   b'_x(x,y) = sum_r fx_r(x) gx_r(y),  b'_y(x,y) = sum_r fy_r(x) gy_r(y),
  * r < rank (0..4), each factor a 1-D spline of the handle's degree and
@@ -137,6 +146,13 @@ int wf_sync(wf_handle* h);
  * Errors: WF_EINVAL, WF_ECUDA.
  */
 int wf_get_state(wf_handle* h, double* T, double* fuel, size_t n);
+
+/*
+ * wf_get_state into float32 host arrays (n = Nx*Ny values each; either
+ * may be NULL).  An FP64 handle's state is rounded to float32.  Same
+ * waiting and errors as wf_get_state.
+ */
+int wf_get_state_f32(wf_handle* h, float* T, float* fuel, size_t n);
 
 /* Grid sizes of a handle (any pointer may be NULL).  Errors: WF_EINVAL. */
 int wf_get_dims(const wf_handle* h, int* Nx, int* Ny, int* p, int* precision);
@@ -275,6 +291,23 @@ int wf_batch_set_slot(wf_handle* h, int slot, const double* T, const double* fue
 /* Copy slot `slot`'s state into host arrays (either may be NULL); waits.
  * Errors: WF_EINVAL, WF_ECUDA. */
 int wf_batch_get_slot(wf_handle* h, int slot, double* T, double* fuel);
+
+/*
+ * Every slot's state in one call: T and fuel are host arrays of
+ * n = S*Nx*Ny values each, slot-major ([S][Ny][Nx]), float64 or (the _f32
+ * calls) float32; one copy per field and one conversion over all slots,
+ * through a device staging area that the first call allocates (2*n values
+ * of the host type) and the handle keeps.  Slots' winds, activity and
+ * guard flags are untouched.  The get calls wait for enqueued work; either
+ * array may be NULL to skip it.  The arrays are the caller's (pinned memory
+ * makes the copies asynchronous to the host).
+ * Errors: WF_EINVAL (NULL handle or set array, n != S*Nx*Ny), WF_ENOMEM
+ * (staging), WF_ECUDA.
+ */
+int wf_batch_set_states(wf_handle* h, const double* T, const double* fuel, size_t n);
+int wf_batch_set_states_f32(wf_handle* h, const float* T, const float* fuel, size_t n);
+int wf_batch_get_states(wf_handle* h, double* T, double* fuel, size_t n);
+int wf_batch_get_states_f32(wf_handle* h, float* T, float* fuel, size_t n);
 
 /* Include (on != 0) or exclude a slot from the following wf_step calls.
  * Errors: WF_EINVAL. */

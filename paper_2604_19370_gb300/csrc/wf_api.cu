@@ -98,6 +98,8 @@ struct wf_handle {
     // shared region
     double *gxi = nullptr, *gw = nullptr;
     double* stage = nullptr;   // 2 * Nx * Ny doubles for host transfers
+    void* bstage = nullptr;    // whole-batch host transfers (allocated on first use)
+    size_t bstage_bytes = 0;
     double* work64 = nullptr;
     double* diag = nullptr;    // [4] factorisation diagnostics
     double* wind64 = nullptr;  // staging of wind factors
@@ -727,6 +729,7 @@ void refresh_wind_rank(wf_handle* h) {
 void destroy(wf_handle* h) {
     if (!h) return;
     drop_graphs(h);
+    if (h->bstage) cudaFree(h->bstage);
     for (auto& pnd : h->pending) {
         cudaEventDestroy(pnd.a);
         cudaEventDestroy(pnd.b);
@@ -740,28 +743,54 @@ void destroy(wf_handle* h) {
     delete h;
 }
 
-int set_slot_state(wf_handle* h, int slot, const double* T, const double* fuel) {
-    const size_t n = (size_t)h->Nx * h->Ny;
+// Host state of one slot in or out: FP64 or FP32 host arrays [Ny][Nx], staged on the device and
+// converted to or from the slot's pitched fields.  T travels on the handle's stream and the fuel on
+// its second stream, so that one field's conversion overlaps the other's copy.
+int set_slot_state(wf_handle* h, int slot, const void* T, const void* fuel, int host32 = 0) {
+    const size_t n = (size_t)h->Nx * h->Ny, es = host32 ? sizeof(float) : sizeof(double);
     cudaStream_t s = h->stream;
-    double* st2 = h->stage + n;
-    WF_TRY(cudaMemcpyAsync(h->stage, T, n * sizeof(double), cudaMemcpyHostToDevice, s));
-    WF_TRY(cudaMemcpyAsync(st2, fuel, n * sizeof(double), cudaMemcpyHostToDevice, s));
-    WF_TRY(launch_convert_in(h->prec, h->stage, at(h, h->T, slot), h->Nx, h->Ny, h->pitch, s));
-    WF_TRY(launch_convert_in(h->prec, st2, at(h, h->phi, slot), h->Nx, h->Ny, h->pitch, s));
+    const bool two = h->aux && h->ev_fork && h->ev_join;
+    cudaStream_t s2 = two ? h->aux : s;
+    char* st1 = reinterpret_cast<char*>(h->stage);
+    char* st2 = st1 + n * es;
+    if (two) {
+        WF_TRY(cudaEventRecord(h->ev_fork, s));
+        WF_TRY(cudaStreamWaitEvent(s2, h->ev_fork, 0));
+    }
+    WF_TRY(cudaMemcpyAsync(st1, T, n * es, cudaMemcpyHostToDevice, s));
+    WF_TRY(cudaMemcpyAsync(st2, fuel, n * es, cudaMemcpyHostToDevice, s2));
+    WF_TRY(launch_convert_in(h->prec, st1, host32, at(h, h->T, slot), h->Nx, h->Ny, h->pitch, s));
+    WF_TRY(launch_convert_in(h->prec, st2, host32, at(h, h->phi, slot), h->Nx, h->Ny, h->pitch, s2));
+    if (two) {
+        WF_TRY(cudaEventRecord(h->ev_join, s2));
+        WF_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
+    }
     WF_TRY(cudaStreamSynchronize(s));
     return WF_OK;
 }
 
-int get_slot_state(wf_handle* h, int slot, double* T, double* fuel) {
-    const size_t n = (size_t)h->Nx * h->Ny;
+int get_slot_state(wf_handle* h, int slot, void* T, void* fuel, int host32 = 0) {
+    const size_t n = (size_t)h->Nx * h->Ny, es = host32 ? sizeof(float) : sizeof(double);
     cudaStream_t s = h->stream;
+    const bool two = h->aux && h->ev_fork && h->ev_join && T && fuel;
+    cudaStream_t s2 = two ? h->aux : s;
+    char* st1 = reinterpret_cast<char*>(h->stage);
+    char* st2 = st1 + n * es;
+    if (two) {
+        WF_TRY(cudaEventRecord(h->ev_fork, s));
+        WF_TRY(cudaStreamWaitEvent(s2, h->ev_fork, 0));
+    }
     if (T) {
-        WF_TRY(launch_convert_out(h->prec, at(h, h->T, slot), h->stage, h->Nx, h->Ny, h->pitch, s));
-        WF_TRY(cudaMemcpyAsync(T, h->stage, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        WF_TRY(launch_convert_out(h->prec, at(h, h->T, slot), st1, host32, h->Nx, h->Ny, h->pitch, s));
+        WF_TRY(cudaMemcpyAsync(T, st1, n * es, cudaMemcpyDeviceToHost, s));
     }
     if (fuel) {
-        WF_TRY(launch_convert_out(h->prec, at(h, h->phi, slot), h->stage + n, h->Nx, h->Ny, h->pitch, s));
-        WF_TRY(cudaMemcpyAsync(fuel, h->stage + n, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        WF_TRY(launch_convert_out(h->prec, at(h, h->phi, slot), st2, host32, h->Nx, h->Ny, h->pitch, s2));
+        WF_TRY(cudaMemcpyAsync(fuel, st2, n * es, cudaMemcpyDeviceToHost, s2));
+    }
+    if (two) {
+        WF_TRY(cudaEventRecord(h->ev_join, s2));
+        WF_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
     }
     WF_TRY(cudaStreamSynchronize(s));
     return WF_OK;
@@ -968,6 +997,11 @@ int wf_set_state(wf_handle* h, const double* T, const double* fuel, size_t n) {
     return set_slot_state(h, 0, T, fuel);
 }
 
+int wf_set_state_f32(wf_handle* h, const float* T, const float* fuel, size_t n) {
+    if (!h || !T || !fuel || n != (size_t)h->Nx * h->Ny) return WF_EINVAL;
+    return set_slot_state(h, 0, T, fuel, 1);
+}
+
 int wf_set_wind(wf_handle* h, int rank, const double* factors) {
     if (!h || rank < 0 || rank > kMaxRank || (rank > 0 && !factors)) return WF_EINVAL;
     if (rank > 0 && !factors_finite(factors, 2 * (size_t)rank * (h->Nx + h->Ny))) return WF_EINVAL;
@@ -1028,6 +1062,79 @@ int wf_batch_set_slot(wf_handle* h, int slot, const double* T, const double* fue
 int wf_batch_get_slot(wf_handle* h, int slot, double* T, double* fuel) {
     if (!h || slot < 0 || slot >= h->S) return WF_EINVAL;
     return get_slot_state(h, slot, T, fuel);
+}
+
+// Every slot's state in or out in one call: host arrays [S][Ny][Nx] per field, one copy per field
+// through a staging area allocated on the first call (kept with the handle), one conversion
+// kernel per field over all slots.  T on the handle's stream, fuel on its second stream.
+static int batch_states(wf_handle* h, const void* Tin, const void* Fin, void* Tout, void* Fout, size_t n,
+                        int host32) {
+    const size_t per = (size_t)h->Nx * h->Ny;
+    if (n != per * (size_t)h->S) return WF_EINVAL;
+    const size_t es = host32 ? sizeof(float) : sizeof(double);
+    const size_t need = 2 * n * es;
+    if (h->bstage_bytes < need) {
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;
+        if (h->bstage) cudaFree(h->bstage);
+        h->bstage = nullptr;
+        h->bstage_bytes = 0;
+        if (cudaMalloc(&h->bstage, need) != cudaSuccess) return WF_ENOMEM;
+        h->bstage_bytes = need;
+    }
+    char* st1 = reinterpret_cast<char*>(h->bstage);
+    char* st2 = st1 + n * es;
+    cudaStream_t s = h->stream;
+    const bool two = h->aux && h->ev_fork && h->ev_join;
+    cudaStream_t s2 = two ? h->aux : s;
+    const bool in = Tin != nullptr;
+    if (two) {
+        WF_TRY(cudaEventRecord(h->ev_fork, s));
+        WF_TRY(cudaStreamWaitEvent(s2, h->ev_fork, 0));
+    }
+    struct Field {
+        const void* src;
+        void* dst;
+        void* dev;
+        char* st;
+        cudaStream_t st_s;
+    } f[2] = {{Tin, Tout, h->T, st1, s}, {Fin, Fout, h->phi, st2, s2}};
+    for (const Field& q : f) {
+        if (in) {
+            WF_TRY(cudaMemcpyAsync(q.st, q.src, n * es, cudaMemcpyHostToDevice, q.st_s));
+            WF_TRY(launch_convert_batch(1, h->prec, q.st, host32, at(h, q.dev, 0), h->sbytes, h->S, h->Nx, h->Ny,
+                                        h->pitch, q.st_s));
+        } else if (q.dst) {
+            WF_TRY(launch_convert_batch(0, h->prec, q.st, host32, at(h, q.dev, 0), h->sbytes, h->S, h->Nx, h->Ny,
+                                        h->pitch, q.st_s));
+            WF_TRY(cudaMemcpyAsync(q.dst, q.st, n * es, cudaMemcpyDeviceToHost, q.st_s));
+        }
+    }
+    if (two) {
+        WF_TRY(cudaEventRecord(h->ev_join, s2));
+        WF_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
+    }
+    WF_TRY(cudaStreamSynchronize(s));
+    return WF_OK;
+}
+
+int wf_batch_set_states(wf_handle* h, const double* T, const double* fuel, size_t n) {
+    if (!h || !T || !fuel) return WF_EINVAL;
+    return batch_states(h, T, fuel, nullptr, nullptr, n, 0);
+}
+
+int wf_batch_set_states_f32(wf_handle* h, const float* T, const float* fuel, size_t n) {
+    if (!h || !T || !fuel) return WF_EINVAL;
+    return batch_states(h, T, fuel, nullptr, nullptr, n, 1);
+}
+
+int wf_batch_get_states(wf_handle* h, double* T, double* fuel, size_t n) {
+    if (!h) return WF_EINVAL;
+    return batch_states(h, nullptr, nullptr, T, fuel, n, 0);
+}
+
+int wf_batch_get_states_f32(wf_handle* h, float* T, float* fuel, size_t n) {
+    if (!h) return WF_EINVAL;
+    return batch_states(h, nullptr, nullptr, T, fuel, n, 1);
 }
 
 int wf_batch_activate(wf_handle* h, int slot, int on) {
@@ -1097,6 +1204,11 @@ int wf_sync(wf_handle* h) {
 int wf_get_state(wf_handle* h, double* T, double* fuel, size_t n) {
     if (!h || n != (size_t)h->Nx * h->Ny) return WF_EINVAL;
     return get_slot_state(h, 0, T, fuel);
+}
+
+int wf_get_state_f32(wf_handle* h, float* T, float* fuel, size_t n) {
+    if (!h || n != (size_t)h->Nx * h->Ny) return WF_EINVAL;
+    return get_slot_state(h, 0, T, fuel, 1);
 }
 
 int wf_get_dims(const wf_handle* h, int* Nx, int* Ny, int* p, int* precision) {

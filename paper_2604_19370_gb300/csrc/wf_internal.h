@@ -103,8 +103,16 @@ cudaError_t launch_compact(const double* lu, const double* spk, const double* E,
 // out[r][e*q+a] = sum_l B[e][a][l] coef[r][e+l]  (1-D spline factor at Gauss points)
 cudaError_t launch_factor_points(int prec, const double* coef, int rank, int n, int p, const double* B,
                                  void* out, cudaStream_t s);
-cudaError_t launch_convert_in(int prec, const double* src, void* dst, int Nx, int Ny, int pitch, cudaStream_t s);
-cudaError_t launch_convert_out(int prec, const void* src, double* dst, int Nx, int Ny, int pitch, cudaStream_t s);
+// host layout [Ny][Nx] in FP64 (host32 = 0) or FP32 (host32 = 1) <-> device [Ny][pitch] in the
+// handle's precision (padding columns written as zeros)
+cudaError_t launch_convert_in(int prec, const void* src, int host32, void* dst, int Nx, int Ny, int pitch,
+                              cudaStream_t s);
+cudaError_t launch_convert_out(int prec, const void* src, void* dst, int host32, int Nx, int Ny, int pitch,
+                               cudaStream_t s);
+// every slot at once (dir_in 1: staged host arrays [S][Ny][Nx] -> slot fields field0 + z * sbytes;
+// 0: the reverse)
+cudaError_t launch_convert_batch(int dir_in, int prec, const void* host_stage, int host32, void* field0,
+                                 long long sbytes, int S, int Nx, int Ny, int pitch, cudaStream_t s);
 cudaError_t launch_fill(int prec, void* dst, size_t n, double v, cudaStream_t s);
 cudaError_t launch_gather_status(int* status0, long long sbytes, int S, int* out, int clear, cudaStream_t s);
 

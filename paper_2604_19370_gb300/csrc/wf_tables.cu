@@ -334,20 +334,41 @@ __global__ void k_factor_points(const double* __restrict__ coef, int rank, int n
     out[idx] = (P)v;
 }
 
-template <typename P>
-__global__ void k_convert_in(const double* __restrict__ src, P* dst, int Nx, int Ny, int pitch) {
+template <typename P, typename H>
+__global__ void k_convert_in(const H* __restrict__ src, P* dst, int Nx, int Ny, int pitch) {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)Ny * pitch) return;
     const int j = (int)(idx / pitch), i = (int)(idx % pitch);
     dst[idx] = (i < Nx) ? (P)src[(size_t)j * Nx + i] : (P)0;
 }
 
-template <typename P>
-__global__ void k_convert_out(const P* __restrict__ src, double* dst, int Nx, int Ny, int pitch) {
+// every slot of a batch at once: blockIdx.z = slot, host arrays [S][Ny][Nx], slot fields sbytes apart
+template <typename P, typename H>
+__global__ void k_convert_in_batch(const H* __restrict__ src, P* dst0, long long sbytes, int Nx, int Ny, int pitch) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)Ny * pitch) return;
+    const int z = blockIdx.z;
+    P* dst = reinterpret_cast<P*>(reinterpret_cast<char*>(dst0) + (long long)z * sbytes);
+    const int j = (int)(idx / pitch), i = (int)(idx % pitch);
+    dst[idx] = (i < Nx) ? (P)src[(size_t)z * Nx * Ny + (size_t)j * Nx + i] : (P)0;
+}
+
+template <typename P, typename H>
+__global__ void k_convert_out_batch(const P* src0, H* dst, long long sbytes, int Nx, int Ny, int pitch) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)Ny * Nx) return;
+    const int z = blockIdx.z;
+    const P* src = reinterpret_cast<const P*>(reinterpret_cast<const char*>(src0) + (long long)z * sbytes);
+    const int j = (int)(idx / Nx), i = (int)(idx % Nx);
+    dst[(size_t)z * Nx * Ny + idx] = (H)src[(size_t)j * pitch + i];
+}
+
+template <typename P, typename H>
+__global__ void k_convert_out(const P* __restrict__ src, H* dst, int Nx, int Ny, int pitch) {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)Ny * Nx) return;
     const int j = (int)(idx / Nx), i = (int)(idx % Nx);
-    dst[idx] = (double)src[(size_t)j * pitch + i];
+    dst[idx] = (H)src[(size_t)j * pitch + i];
 }
 
 // Guard flags of S scenarios (each in its own block, sbytes apart) gathered into out[S],
@@ -423,21 +444,47 @@ cudaError_t launch_factor_points(int prec, const double* coef, int rank, int n, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_convert_in(int prec, const double* src, void* dst, int Nx, int Ny, int pitch, cudaStream_t s) {
+cudaError_t launch_convert_in(int prec, const void* src, int host32, void* dst, int Nx, int Ny, int pitch,
+                              cudaStream_t s) {
     const size_t cnt = (size_t)Ny * pitch;
-    if (prec == 0)
-        k_convert_in<float><<<blocks(cnt, 256), 256, 0, s>>>(src, (float*)dst, Nx, Ny, pitch);
-    else
-        k_convert_in<double><<<blocks(cnt, 256), 256, 0, s>>>(src, (double*)dst, Nx, Ny, pitch);
+    if (prec == 0) {
+        if (host32) k_convert_in<float, float><<<blocks(cnt, 256), 256, 0, s>>>((const float*)src, (float*)dst, Nx, Ny, pitch);
+        else k_convert_in<float, double><<<blocks(cnt, 256), 256, 0, s>>>((const double*)src, (float*)dst, Nx, Ny, pitch);
+    } else {
+        if (host32) k_convert_in<double, float><<<blocks(cnt, 256), 256, 0, s>>>((const float*)src, (double*)dst, Nx, Ny, pitch);
+        else k_convert_in<double, double><<<blocks(cnt, 256), 256, 0, s>>>((const double*)src, (double*)dst, Nx, Ny, pitch);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_convert_out(int prec, const void* src, double* dst, int Nx, int Ny, int pitch, cudaStream_t s) {
+cudaError_t launch_convert_batch(int dir_in, int prec, const void* host_stage, int host32, void* field0,
+                                 long long sbytes, int S, int Nx, int Ny, int pitch, cudaStream_t s) {
+    const size_t cnt = dir_in ? (size_t)Ny * pitch : (size_t)Ny * Nx;
+    dim3 g(blocks(cnt, 256), 1, S);
+#define WF_CB(P, H)                                                                                        \
+    if (dir_in)                                                                                            \
+        k_convert_in_batch<P, H><<<g, 256, 0, s>>>((const H*)host_stage, (P*)field0, sbytes, Nx, Ny, pitch); \
+    else                                                                                                   \
+        k_convert_out_batch<P, H><<<g, 256, 0, s>>>((const P*)field0, (H*)host_stage, sbytes, Nx, Ny, pitch)
+    if (prec == 0) {
+        if (host32) { WF_CB(float, float); } else { WF_CB(float, double); }
+    } else {
+        if (host32) { WF_CB(double, float); } else { WF_CB(double, double); }
+    }
+#undef WF_CB
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_out(int prec, const void* src, void* dst, int host32, int Nx, int Ny, int pitch,
+                               cudaStream_t s) {
     const size_t cnt = (size_t)Ny * Nx;
-    if (prec == 0)
-        k_convert_out<float><<<blocks(cnt, 256), 256, 0, s>>>((const float*)src, dst, Nx, Ny, pitch);
-    else
-        k_convert_out<double><<<blocks(cnt, 256), 256, 0, s>>>((const double*)src, dst, Nx, Ny, pitch);
+    if (prec == 0) {
+        if (host32) k_convert_out<float, float><<<blocks(cnt, 256), 256, 0, s>>>((const float*)src, (float*)dst, Nx, Ny, pitch);
+        else k_convert_out<float, double><<<blocks(cnt, 256), 256, 0, s>>>((const float*)src, (double*)dst, Nx, Ny, pitch);
+    } else {
+        if (host32) k_convert_out<double, float><<<blocks(cnt, 256), 256, 0, s>>>((const double*)src, (float*)dst, Nx, Ny, pitch);
+        else k_convert_out<double, double><<<blocks(cnt, 256), 256, 0, s>>>((const double*)src, (double*)dst, Nx, Ny, pitch);
+    }
     return cudaGetLastError();
 }
 

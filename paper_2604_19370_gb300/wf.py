@@ -80,13 +80,20 @@ def lib() -> ctypes.CDLL:
         L = ctypes.CDLL(LIB_PATH)
         vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
         dp = ctypes.POINTER(ctypes.c_double)
+        fp = ctypes.POINTER(ctypes.c_float)
         L.wf_params_default.argtypes = [ctypes.POINTER(wf_params)]
         L.wf_create.argtypes = [i, i, i, d, ctypes.POINTER(wf_params), ctypes.POINTER(vp)]
         L.wf_set_state.argtypes = [vp, dp, dp, sz]
+        L.wf_set_state_f32.argtypes = [vp, fp, fp, sz]
         L.wf_set_wind.argtypes = [vp, i, dp]
         L.wf_step.argtypes = [vp, i]
         L.wf_sync.argtypes = [vp]
         L.wf_get_state.argtypes = [vp, dp, dp, sz]
+        L.wf_get_state_f32.argtypes = [vp, fp, fp, sz]
+        L.wf_batch_set_states.argtypes = [vp, dp, dp, sz]
+        L.wf_batch_set_states_f32.argtypes = [vp, fp, fp, sz]
+        L.wf_batch_get_states.argtypes = [vp, dp, dp, sz]
+        L.wf_batch_get_states_f32.argtypes = [vp, fp, fp, sz]
         L.wf_get_dims.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
         L.wf_set_stream.argtypes = [vp, vp]
         L.wf_set_profiling.argtypes = [vp, i]
@@ -178,6 +185,24 @@ def wf_set_state_ptr(h, T_ptr: int, fuel_ptr: int, n: int) -> None:
     _check(lib().wf_set_state(h, ctypes.cast(T_ptr, dp), ctypes.cast(fuel_ptr, dp), n), "wf_set_state")
 
 
+def wf_set_state_f32(h, T, fuel) -> None:
+    """wf_set_state with float32 host arrays (half the bytes over the host link)."""
+    Nx, Ny, _, _ = wf_get_dims(h)
+    n = Nx * Ny
+    Ta = np.ascontiguousarray(T, dtype=np.float32).ravel()
+    Fa = np.ascontiguousarray(fuel, dtype=np.float32).ravel()
+    if Ta.size != n or Fa.size != n:
+        raise ValueError(f"wf_set_state_f32: expected {n} values per field")
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(lib().wf_set_state_f32(h, Ta.ctypes.data_as(fp), Fa.ctypes.data_as(fp), n), "wf_set_state_f32")
+
+
+def wf_set_state_f32_ptr(h, T_ptr: int, fuel_ptr: int, n: int) -> None:
+    """Same call with raw float32 host addresses (e.g. pinned buffers owned by the caller)."""
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(lib().wf_set_state_f32(h, ctypes.cast(T_ptr, fp), ctypes.cast(fuel_ptr, fp), n), "wf_set_state_f32")
+
+
 def wf_set_wind(h, rank: int, factors=None) -> None:
     arr = None if factors is None else np.ascontiguousarray(factors, dtype=np.float64).ravel()
     _check(lib().wf_set_wind(h, rank, _dptr(arr)), "wf_set_wind")
@@ -206,6 +231,29 @@ def wf_get_state(h) -> Tuple[np.ndarray, np.ndarray]:
 def wf_get_state_ptr(h, T_ptr: int, fuel_ptr: int, n: int) -> None:
     dp = ctypes.POINTER(ctypes.c_double)
     _check(lib().wf_get_state(h, ctypes.cast(T_ptr, dp), ctypes.cast(fuel_ptr, dp), n), "wf_get_state")
+
+
+def wf_get_state_f32(h) -> Tuple[np.ndarray, np.ndarray]:
+    Nx, Ny, _, _ = wf_get_dims(h)
+    T = np.empty((Ny, Nx), dtype=np.float32)
+    F = np.empty((Ny, Nx), dtype=np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(lib().wf_get_state_f32(h, T.ctypes.data_as(fp), F.ctypes.data_as(fp), Nx * Ny), "wf_get_state_f32")
+    return T, F
+
+
+def wf_get_state_f32_ptr(h, T_ptr: int, fuel_ptr: int, n: int) -> None:
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(lib().wf_get_state_f32(h, ctypes.cast(T_ptr, fp), ctypes.cast(fuel_ptr, fp), n), "wf_get_state_f32")
+
+
+def wf_batch_states_ptr(h, T_ptr: int, fuel_ptr: int, n: int, f32: bool, set_: bool) -> None:
+    """Every slot's state in (set_) or out through raw host addresses ([S][Ny][Nx] per field)."""
+    tp = ctypes.POINTER(ctypes.c_float if f32 else ctypes.c_double)
+    name = ("wf_batch_set_states" if set_ else "wf_batch_get_states") + ("_f32" if f32 else "")
+    fn = getattr(lib(), name)
+    _check(fn(h, ctypes.cast(T_ptr, tp) if T_ptr else None, ctypes.cast(fuel_ptr, tp) if fuel_ptr else None, n),
+           name)
 
 
 def wf_set_stream(h, stream_ptr: Optional[int]) -> None:

@@ -61,6 +61,12 @@ def test_argument_validation_without_device(libpath):
     assert L.wf_step(None, 1) == wf.WF_EINVAL
     assert L.wf_sync(None) == wf.WF_EINVAL
     assert L.wf_get_dims(None, None, None, None, None) == wf.WF_EINVAL
+    assert L.wf_set_state_f32(None, None, None, 0) == wf.WF_EINVAL
+    assert L.wf_get_state_f32(None, None, None, 0) == wf.WF_EINVAL
+    assert L.wf_batch_set_states(None, None, None, 0) == wf.WF_EINVAL
+    assert L.wf_batch_set_states_f32(None, None, None, 0) == wf.WF_EINVAL
+    assert L.wf_batch_get_states(None, None, None, 0) == wf.WF_EINVAL
+    assert L.wf_batch_get_states_f32(None, None, None, 0) == wf.WF_EINVAL
     L.wf_destroy(None)
 
 

@@ -92,3 +92,40 @@ def test_batch_guard_is_per_slot(wf):
     assert list(st) == [0, 1, 0]
     assert not b.status().any()  # cleared by the call
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_whole_batch_state_io(wf, prec):
+    # one call for every slot's state (float64 and float32 host arrays) equals slot-by-slot transfers
+    scs = _scenarios(40, 2, 3, 800)
+    P = wf.WF_FP32 if prec == "fp32" else wf.WF_FP64
+    prm = _batch_params(wf, scs[0], P, wf.WF_PR)
+    a = wf.Batch(40, 40, 2, 1e-3, prm, capacity=3)
+    b = wf.Batch(40, 40, 2, 1e-3, prm, capacity=3)
+    for i, sc in enumerate(scs):
+        a.load_scenario(i, sc)
+        b.load_scenario(i, sc)
+    n = scs[0].T0.size
+    T32 = np.stack([sc.T0 for sc in scs]).astype(np.float32).ravel()
+    F32 = np.stack([sc.fuel0 for sc in scs]).astype(np.float32).ravel()
+    for i, sc in enumerate(scs):  # same values through the per-slot float64 call
+        wf.wf_batch_set_slot(a.h, i, T32[i * n:(i + 1) * n].astype(np.float64),
+                             F32[i * n:(i + 1) * n].astype(np.float64), sc.wind[0], sc.wind[1],
+                             sc.wind_rank, sc.wind_packed())
+    wf.wf_batch_states_ptr(b.h, T32.ctypes.data, F32.ctypes.data, 3 * n, True, True)
+    a.step(2)
+    b.step(2)
+    T64 = np.empty(3 * n)
+    F64 = np.empty(3 * n)
+    wf.wf_batch_states_ptr(b.h, T64.ctypes.data, F64.ctypes.data, 3 * n, False, False)
+    To32 = np.empty(3 * n, dtype=np.float32)
+    wf.wf_batch_states_ptr(b.h, To32.ctypes.data, 0, 3 * n, True, False)
+    for i in range(3):
+        Ta, Fa = a.state(i)
+        assert np.array_equal(T64[i * n:(i + 1) * n], Ta.ravel()), i
+        assert np.array_equal(F64[i * n:(i + 1) * n], Fa.ravel()), i
+        assert np.array_equal(To32[i * n:(i + 1) * n], Ta.ravel().astype(np.float32)), i
+    with pytest.raises(wf.WFError):
+        wf.wf_batch_states_ptr(b.h, T64.ctypes.data, F64.ctypes.data, 3 * n - 1, False, True)
+    a.close()
+    b.close()

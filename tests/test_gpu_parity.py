@@ -246,3 +246,27 @@ def test_fp32_hot_rows(wf, wind):
     T, phi = gpu_run(wf, sc, 1, wf.WF_FP32, T0=T0)
     To, po = oracle_run(sc, 1, T0=T0)
     assert rel(T, To) <= 1e-5 and rel(phi, po) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_state_io_f32_matches_f64(wf, prec):
+    # the float32 state calls carry the same values as the float64 ones: set from float32 values
+    # (exactly representable in both), step, read both ways
+    sc = make_scenario("io", 60, 2, 1e-3, 1, 71, wind=(0.7, -0.4), fuel_sigma=3.0)
+    P = wf.WF_FP32 if prec == "fp32" else wf.WF_FP64
+    T0 = sc.T0.astype(np.float32)
+    F0 = sc.fuel0.astype(np.float32)
+    a = wf.simulation_from_scenario(sc, precision=P)
+    b = wf.simulation_from_scenario(sc, precision=P)
+    wf.wf_set_state(a.h, T0.astype(np.float64), F0.astype(np.float64))
+    wf.wf_set_state_f32(b.h, T0, F0)
+    a.step(3)
+    b.step(3)
+    Ta, Fa = wf.wf_get_state(a.h)
+    Tb, Fb = wf.wf_get_state(b.h)
+    assert np.array_equal(Ta, Tb) and np.array_equal(Fa, Fb)
+    T32, F32 = wf.wf_get_state_f32(b.h)
+    assert T32.dtype == np.float32
+    assert np.array_equal(T32, Tb.astype(np.float32)) and np.array_equal(F32, Fb.astype(np.float32))
+    a.close()
+    b.close()
