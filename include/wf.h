@@ -236,7 +236,7 @@ int wf_launch_count(unsigned long long* n);
  *   shape[4]  lines per CTA of the second x pass,
  *   shape[5]  where Peaceman-Rachford with one F per step forms the right-hand
  *             side of its second x pass: 1 inside that pass (from staged rows
- *             of T* and F), 2 in a tiled matvec kernel before it (one more
+ *             of T* and F), 2 in a streaming matvec kernel before it (one more
  *             pass over R, but every thread busy on short lines);
  * 0 selects the launchers' built-in rule (for shape[5]: inside the pass).
  * Both schedules of shape[5] perform the same operations in the same order.  wf_autotune tunes one shape at a

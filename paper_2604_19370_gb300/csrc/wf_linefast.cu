@@ -16,7 +16,7 @@
 // in memory and move with one TMA bulk copy each way (cp.async.bulk with an
 // mbarrier); neighbouring chunks exchange boundary values by warp shuffles.
 // y pass: a CTA owns G columns; lanes of neighbouring columns read and write
-// contiguous runs of G elements per row, 16 loads in flight per thread.
+// contiguous runs of G elements per row, 16 or 32 loads in flight per thread.
 #include "wf_internal.h"
 
 namespace wf {
