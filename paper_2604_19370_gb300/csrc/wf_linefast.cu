@@ -834,7 +834,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
 
 // ---- streaming explicit Kronecker matvec ---------------------------------------------
 // R = Fscale F + c1 (A1^x (x) B1^y) T + c2 (A2^x (x) B2^y) T.  A warp owns 32 columns (lane L
-// <-> column X0 - p + L; lanes p .. 31-p are outputs) and RS (8) output rows: it issues every load
+// <-> column X0 - p + L; lanes p .. 31-p are outputs) and RS output rows: it issues every load
 // of its RS + 2p rows of T and RS rows of F first, x-convolves each row with neighbours'
 // values taken by shuffles, and reduces the y bands from registers.  No shared memory, no
 // barriers, every warp independent.  Values outside the domain are zeros, and the operations
@@ -963,16 +963,18 @@ cudaError_t launch_line_fast(int prec, int p, bool xdir, const LineArgs& a, cuda
 }
 
 cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s) {
-    constexpr int RS = 8, WARPS = 4;
+    // output rows per warp item: 8 for p <= 2; 16 for p = 3, whose 2p-row halo would otherwise
+    // nearly double the rows a warp loads
+    constexpr int WARPS = 4;
     if (p < 1 || p > 3) return cudaErrorInvalidValue;
-    const int nstrips = (a.Nx + (32 - 2 * p) - 1) / (32 - 2 * p), nsegs = (a.Ny + RS - 1) / RS;
+    const int rs = p > 2 ? 16 : 8;
+    const int nstrips = (a.Nx + (32 - 2 * p) - 1) / (32 - 2 * p), nsegs = (a.Ny + rs - 1) / rs;
     const long items = (long)nstrips * nsegs;
     dim3 grid((unsigned)((items + WARPS - 1) / WARPS), 1, a.b.S), block(32 * WARPS);
-#define WF_MV(P, PD)                                                                                         \
-    k_matvec_stream<P, PD, RS><<<grid, block, 0, s>>>(a.Nx, a.Ny, a.pitch, (const P*)a.T, (const P*)a.F,     \
-                                                      (P*)a.R, (const P*)a.A1, (const P*)a.B1, (const P*)a.A2, \
-                                                      (const P*)a.B2, (P)a.Fscale, (P)a.c1, (P)a.c2, a.b,      \
-                                                      nstrips, nsegs)
+#define WF_MV(P, PD)                                                                                          \
+    k_matvec_stream<P, PD, (PD > 2 ? 16 : 8)><<<grid, block, 0, s>>>(                                         \
+        a.Nx, a.Ny, a.pitch, (const P*)a.T, (const P*)a.F, (P*)a.R, (const P*)a.A1, (const P*)a.B1,           \
+        (const P*)a.A2, (const P*)a.B2, (P)a.Fscale, (P)a.c1, (P)a.c2, a.b, nstrips, nsegs)
     if (prec == 0) {
         switch (p) {
             case 1: WF_MV(float, 1); break;

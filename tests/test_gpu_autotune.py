@@ -51,6 +51,25 @@ def test_shapes_do_not_change_results(wf, prec, scheme):
             assert np.array_equal(T, ref[0]) and np.array_equal(phi, ref[1]), shape
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_shapes_do_not_change_results_cubic(wf, prec):
+    # p = 3: the matvec's taller items and the fused right-hand side give the same bits
+    P = wf.WF_FP32 if prec == "fp32" else wf.WF_FP64
+    sc = make_scenario("shape3", 120, 3, 1e-3, 1, 95, wind=(-0.9, 1.1), fuel_sigma=3.0)
+    ref = None
+    for shape in [(0, 0, 0, 0, 0, 0), (8, 16, 32, 2, 4, 2), (1, 4, 16, 1, 2, 1), (4, 2, 64, 0, 8, 2)]:
+        sim = _sim(wf, sc, P, wf.WF_PR)
+        wf.wf_set_tuning(sim.h, shape)
+        sim.step(4)
+        assert sim.sync() == wf.WF_OK
+        T, phi = sim.state()
+        sim.close()
+        if ref is None:
+            ref = (T, phi)
+        else:
+            assert np.array_equal(T, ref[0]) and np.array_equal(phi, ref[1]), shape
+
+
 def test_autotune_keeps_state_and_parity(wf):
     sc = make_scenario("tune", 96, 2, 1e-3, 1, 92, wind=(0.8, 0.4), fuel_sigma=3.0)
     sim = _sim(wf, sc, wf.WF_FP32, wf.WF_PR)
