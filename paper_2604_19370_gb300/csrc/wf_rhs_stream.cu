@@ -1047,7 +1047,7 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
         a.nseg_b = a.split ? (mid + sb - 1) / sb : 0;
     }
     const long n_side = (long)(a.nstrips - (a.s_hi - a.s_lo)) * a.nseg_b + 2L * a.nstrips;
-    if (sizeof(P) == 4 && n_fast > 0) {
+    if constexpr (sizeof(P) == 4) if (n_fast > 0) {
         // interior items in one launch, the rest in a second (their register budgets differ);
         // with the handle's second stream the two run side by side and join before returning
         cudaError_t e;
@@ -1083,13 +1083,16 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
 
 template <typename P, int PD>
 cudaError_t by_rank(const RhsArgs& r, cudaStream_t s) {
-    if (sizeof(P) == 8 && PD == 3) return cudaErrorNotSupported;  // its register windows spill: tile form
-    switch (r.wind_rank) {
-        case 0: return run_stream<P, PD, 0>(r, s);
-        case 1: return run_stream<P, PD, 1>(r, s);
-        case 2: return run_stream<P, PD, 2>(r, s);
+    if constexpr (sizeof(P) == 8 && PD == 3) {
+        return cudaErrorNotSupported;  // its register windows spill: tile form
+    } else {
+        switch (r.wind_rank) {
+            case 0: return run_stream<P, PD, 0>(r, s);
+            case 1: return run_stream<P, PD, 1>(r, s);
+            case 2: return run_stream<P, PD, 2>(r, s);
+        }
+        return cudaErrorNotSupported;
     }
-    return cudaErrorNotSupported;
 }
 
 }  // namespace
