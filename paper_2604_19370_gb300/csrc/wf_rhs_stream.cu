@@ -1047,31 +1047,34 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
         a.nseg_b = a.split ? (mid + sb - 1) / sb : 0;
     }
     const long n_side = (long)(a.nstrips - (a.s_hi - a.s_lo)) * a.nseg_b + 2L * a.nstrips;
-    if constexpr (sizeof(P) == 4) if (n_fast > 0) {
-        // interior items in one launch, the rest in a second (their register budgets differ);
-        // with the handle's second stream the two run side by side and join before returning
-        cudaError_t e;
-        const bool fork = r.aux && r.ev_fork && r.ev_join;
-        cudaStream_t s1 = fork ? r.aux : s;
-        if (fork) {
-            if ((e = cudaEventRecord(r.ev_fork, s)) != cudaSuccess) return e;
-            if ((e = cudaStreamWaitEvent(r.aux, r.ev_fork, 0)) != cudaSuccess) return e;
+    // FP32 only (FP64 runs every item in one launch): split launches when interior items exist
+    if constexpr (sizeof(P) == 4) {
+        if (n_fast > 0) {
+            // interior items in one launch, the rest in a second (their register budgets differ);
+            // with the handle's second stream the two run side by side and join before returning
+            cudaError_t e;
+            const bool fork = r.aux && r.ev_fork && r.ev_join;
+            cudaStream_t s1 = fork ? r.aux : s;
+            if (fork) {
+                if ((e = cudaEventRecord(r.ev_fork, s)) != cudaSuccess) return e;
+                if ((e = cudaStreamWaitEvent(r.aux, r.ev_fork, 0)) != cudaSuccess) return e;
+            }
+            const size_t wb0 = wind_smem<P, PD, WR, 0>(a.seg), wb1 = wind_smem<P, PD, WR, 1>(a.seg_b);
+            if (wb0 == SIZE_MAX || wb1 == SIZE_MAX) return cudaErrorInvalidValue;
+            dim3 g1((unsigned)((n_side + WARPS - 1) / WARPS), 1, r.b.S);
+            k_rhs_stream<P, PD, WR, 1><<<g1, 32 * WARPS, wb1, s1>>>(a);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            count_launches(1);
+            dim3 g0((unsigned)((n_fast + WARPS - 1) / WARPS), 1, r.b.S);
+            k_rhs_stream<P, PD, WR, 0><<<g0, 32 * WARPS, wb0, s>>>(a);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            count_launches(1);
+            if (fork) {
+                if ((e = cudaEventRecord(r.ev_join, r.aux)) != cudaSuccess) return e;
+                if ((e = cudaStreamWaitEvent(s, r.ev_join, 0)) != cudaSuccess) return e;
+            }
+            return cudaSuccess;
         }
-        const size_t wb0 = wind_smem<P, PD, WR, 0>(a.seg), wb1 = wind_smem<P, PD, WR, 1>(a.seg_b);
-        if (wb0 == SIZE_MAX || wb1 == SIZE_MAX) return cudaErrorInvalidValue;
-        dim3 g1((unsigned)((n_side + WARPS - 1) / WARPS), 1, r.b.S);
-        k_rhs_stream<P, PD, WR, 1><<<g1, 32 * WARPS, wb1, s1>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        count_launches(1);
-        dim3 g0((unsigned)((n_fast + WARPS - 1) / WARPS), 1, r.b.S);
-        k_rhs_stream<P, PD, WR, 0><<<g0, 32 * WARPS, wb0, s>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        count_launches(1);
-        if (fork) {
-            if ((e = cudaEventRecord(r.ev_join, r.aux)) != cudaSuccess) return e;
-            if ((e = cudaStreamWaitEvent(s, r.ev_join, 0)) != cudaSuccess) return e;
-        }
-        return cudaSuccess;
     }
     dim3 grid((unsigned)((n_all + WARPS - 1) / WARPS), 1, r.b.S);
     const size_t wb2 = wind_smem<P, PD, WR, 2>(a.seg);
