@@ -1272,7 +1272,7 @@ int wf_autotune(wf_handle* h, int reps) {
     for (int z = 0; z < h->S; ++z) any = any || h->active_host[z];
     if (!any) return WF_OK;
     // Coordinate search: one shape at a time, in launch order, the others held at their best
-    // values; a candidate is judged by the device time of the whole step, because a shape
+    // values; a candidate is rated by the device time of the whole step, because a shape
     // also changes what the next kernel finds in L2.  Two sweeps.  Segment heights include
     // values between the powers of two: the number of (strip, segment) work items against
     // the resident warps decides how full the last wave is.
