@@ -134,11 +134,26 @@ int wf_set_wind(wf_handle* h, int rank, const double* factors);
 int wf_step(wf_handle* h, int nsteps);
 
 /*
- * Wait for all enqueued work and report device status: WF_EUNSTABLE if a
- * temperature became non-finite or exceeded 1e5 K since the last
- * wf_sync, WF_OK otherwise.  The status flag is cleared by the call.
+ * Wait for all enqueued work and report device status since the last
+ * wf_sync: WF_ETIMEOUT if a bounded device wait gave up in any slot (the
+ * output of that step is invalid for every slot of the handle: a CTA that
+ * gives up leaves its lines unsolved), else WF_EUNSTABLE if an active
+ * slot's temperature became non-finite or exceeded 1e5 K, else WF_OK.
+ * The flags are cleared by the call.  No counterpart in the paper.
  */
 int wf_sync(wf_handle* h);
+
+/*
+ * Limit of every bounded wait inside the library's kernels (the staging
+ * barrier of the x pass, the arrival counters of the persistent step), in
+ * seconds of the GPU's global timer: 0..60, default 1.  A wait that reaches
+ * it gives up, drains its copies in flight, sets the timeout bit of its
+ * slot and returns, so the device stays usable and wf_sync reports
+ * WF_ETIMEOUT.  0 gives up without waiting (for tests of that path).
+ * Captured step graphs are dropped.  Errors: WF_EINVAL.  No counterpart
+ * in the paper.
+ */
+int wf_set_wait_limit(wf_handle* h, double seconds);
 
 /*
  * Wait for enqueued work and copy the state into host arrays T and fuel
@@ -313,9 +328,14 @@ int wf_batch_get_states_f32(wf_handle* h, float* T, float* fuel, size_t n);
  * Errors: WF_EINVAL. */
 int wf_batch_activate(wf_handle* h, int slot, int on);
 
-/* Waits and writes, per slot, 1 if its guard tripped since the last call (a
- * temperature non-finite or above 1e5 K) else 0, into status[0 .. capacity-1]
- * (n >= capacity), and clears the flags.  Errors: WF_EINVAL, WF_ECUDA. */
+/* Waits and writes, per slot, its flag word since the last call into
+ * status[0 .. capacity-1] (n >= capacity), and clears the flags:
+ *   WF_STATUS_UNSTABLE  a temperature became non-finite or exceeded 1e5 K;
+ *   WF_STATUS_TIMEOUT   a bounded device wait gave up (the step's output is
+ *                       invalid for every slot of the handle);
+ * 0 when neither happened.  Errors: WF_EINVAL, WF_ECUDA. */
+#define WF_STATUS_UNSTABLE 1
+#define WF_STATUS_TIMEOUT 4
 int wf_batch_status(wf_handle* h, int* status, int n);
 
 /* Number of slots of a handle (>= 1), or WF_EINVAL. */
@@ -323,6 +343,15 @@ int wf_batch_capacity(const wf_handle* h);
 
 /* Device bytes held by the handle.  Errors: WF_EINVAL. */
 int wf_device_bytes(const wf_handle* h, size_t* bytes);
+
+/* Upper bound of the device bytes wf_batch_create would allocate for these
+ * arguments (the largest layout over every chunk length the creation may
+ * settle on), computed on the host without touching the device: lets a
+ * caller admit work by memory budget before allocating.  The whole-batch
+ * state calls' staging (2 x capacity x Nx x Ny host-type values, allocated
+ * on their first use) is not included.  Errors: WF_EINVAL (as
+ * wf_batch_create's argument checks).  No counterpart in the paper. */
+int wf_batch_bytes(int nx, int ny, int p, double dt, const wf_params* params, int capacity, size_t* bytes);
 
 /*
  * ---- serving ---------------------------------------------------------------
@@ -396,7 +425,8 @@ void wf_server_destroy(wf_server* s);
  * Work is enqueued on the handle's stream (wf_set_stream) without waiting; use
  * wf_sync to wait and read the guard status.  No CUDA graph is used.
  * Errors: WF_EINVAL (NULL pointer, FP64 handle, pitch < Nx, pitch * Ny above the
- * limit, nsteps < 0), WF_ECUDA.
+ * limit, nsteps < 0, manufactured-solution forcing switched on: its clock belongs
+ * to the handle's own state), WF_ECUDA.
  */
 int wf_step_noalloc(wf_handle* h, void* T, void* fuel, int pitch, int nsteps);
 /* (wf_step_noalloc takes single-scenario handles only: capacity 1.) */

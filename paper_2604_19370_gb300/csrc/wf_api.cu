@@ -110,6 +110,7 @@ struct wf_handle {
     int S = 1;
     long long sbytes = 0;
     char* slots_mem = nullptr;  // start of slot 0's block
+    long long wait_ns = 1000000000LL;  // limit of every bounded device wait (wf_set_wait_limit)
     bool mms_on = false;       // manufactured-solution forcing (wf_set_mms)
     MmsArgs mms{};
     double* tdev = nullptr;    // device: start time of the next step (advanced only with forcing)
@@ -522,6 +523,8 @@ LineArgs line_args(wf_handle* h, int xsite) {
     a.rpw = xdir ? h->tune[3] : 0;
     a.pitch = h->pitch;
     a.tmax = kTmax;
+    a.tstatus = h->status;
+    a.wait_ns = h->wait_ns;
     a.b = batch(h);
     return a;
 }
@@ -864,17 +867,45 @@ int wf_params_default(wf_params* p) {
     return WF_OK;
 }
 
-int wf_batch_create(int nx, int ny, int p, double dt, const wf_params* params, int capacity, wf_handle** out) {
-    if (!out) return WF_EINVAL;
-    *out = nullptr;
-    if (!params || nx < 1 || ny < 1 || p < 1 || p > kMaxP || !(dt > 0.0) || !isfinite(dt)) return WF_EINVAL;
-    if (nx > (1 << 15) || ny > (1 << 15) || capacity < 1 || capacity > 65535) return WF_EINVAL;
-    if (!params_ok(*params)) return WF_EINVAL;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaFree(0) != cudaSuccess) return WF_ECUDA;
+namespace {
 
-    wf_handle* h = new (std::nothrow) wf_handle();
-    if (!h) return WF_ENOMEM;
+bool create_args_ok(int nx, int ny, int p, double dt, const wf_params* params, int capacity) {
+    if (!params || nx < 1 || ny < 1 || p < 1 || p > kMaxP || !(dt > 0.0) || !isfinite(dt)) return false;
+    if (nx > (1 << 15) || ny > (1 << 15) || capacity < 1 || capacity > 65535) return false;
+    return params_ok(*params);
+}
+
+// Chunk lengths tried at creation, shortest first: the truncated reduced system must neglect spike
+// entries below 1e-8 (FP32) or 1e-15 (FP64), and the shortest length that does is kept.
+constexpr int kBaseTries = 10;
+const int kBases32[kBaseTries] = {32, 48, 64, 96, 128, 256, 512, 1024, 2048, 8192};
+const int kBases64[kBaseTries] = {48, 64, 96, 128, 192, 256, 512, 1024, 2048, 8192};
+
+// Chunks of both directions for creation attempt `attempt`: at most 32 chunks per line (one warp
+// lane or one thread row each); odd lengths keep the 32 lanes of the x pass on distinct banks.
+void set_chunks(wf_handle* h, int attempt) {
+    const int* bases = h->prec == WF_FP32 ? kBases32 : kBases64;
+    for (Dir* d : {&h->dx, &h->dy}) {
+        int base = bases[attempt];
+        const int need = (d->N + 31) / 32;
+        if (base < need) base = need;
+        base |= 1;
+        d->ch = make_chunks(d->N, base, h->p);
+    }
+}
+
+// Shared-region and per-slot byte counts of the handle's layout for its current chunks.
+void layout_sizes(wf_handle* h, size_t* shared, long long* sbytes) {
+    Arena A;
+    layout_shared(h, A);
+    *shared = (A.off + 255) & ~(size_t)255;
+    Arena B;
+    layout_slot(h, B);
+    *sbytes = (long long)((B.off + 255) & ~(size_t)255);
+}
+
+// Host fields of a new handle (no device work).
+void init_fields(wf_handle* h, int nx, int ny, int p, double dt, const wf_params* params, int capacity) {
     h->nx = nx;
     h->ny = ny;
     h->p = p;
@@ -897,6 +928,36 @@ int wf_batch_create(int nx, int ny, int p, double dt, const wf_params* params, i
     h->dy.h = params->Ly / ny;
     for (Dir* d : {&h->dx, &h->dy})
         for (int k = 0; k < 3; ++k) d->op[k].factored = (k != 1);
+}
+
+}  // namespace
+
+int wf_batch_bytes(int nx, int ny, int p, double dt, const wf_params* params, int capacity, size_t* bytes) {
+    if (!bytes || !create_args_ok(nx, ny, p, dt, params, capacity)) return WF_EINVAL;
+    wf_handle h;
+    init_fields(&h, nx, ny, p, dt, params, capacity);
+    size_t most = 0;
+    for (int attempt = 0; attempt < kBaseTries; ++attempt) {
+        set_chunks(&h, attempt);
+        size_t shared = 0;
+        long long sb = 0;
+        layout_sizes(&h, &shared, &sb);
+        most = std::max(most, shared + (size_t)sb * capacity + 256);
+    }
+    *bytes = most;
+    return WF_OK;
+}
+
+int wf_batch_create(int nx, int ny, int p, double dt, const wf_params* params, int capacity, wf_handle** out) {
+    if (!out) return WF_EINVAL;
+    *out = nullptr;
+    if (!create_args_ok(nx, ny, p, dt, params, capacity)) return WF_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaFree(0) != cudaSuccess) return WF_ECUDA;
+
+    wf_handle* h = new (std::nothrow) wf_handle();
+    if (!h) return WF_ENOMEM;
+    init_fields(h, nx, ny, p, dt, params, capacity);
     h->slots.assign(capacity, Slot());
     for (Slot& sl : h->slots) {
         sl.wind_x = params->wind_x;
@@ -913,34 +974,18 @@ int wf_batch_create(int nx, int ny, int p, double dt, const wf_params* params, i
     }
     h->stream = h->own;
 
-    // Chunk length: the truncated reduced system must neglect spike entries below 1e-8
-    // (FP32) or 1e-15 (FP64); the shortest length that does (for the creation wind) is used.
-    static const int bases32[] = {32, 48, 64, 96, 128, 256, 512, 1024, 2048, 8192};
-    static const int bases64[] = {48, 64, 96, 128, 192, 256, 512, 1024, 2048, 8192};
-    const int* bases = h->prec == WF_FP32 ? bases32 : bases64;
+    // Chunk length: the shortest of the tried lengths whose neglected spike entries stay below
+    // the truncation tolerance (for the creation wind).
     const double tol = trunc_tol(h);
     int rc = WF_OK;
     size_t shared = 0;
-    for (int attempt = 0; attempt < 10; ++attempt) {
-        for (Dir* d : {&h->dx, &h->dy}) {
-            // at most 32 chunks per line (one warp lane or one thread row each); odd lengths
-            // keep the 32 lanes of the x pass on distinct shared-memory banks
-            int base = bases[attempt];
-            const int need = (d->N + 31) / 32;
-            if (base < need) base = need;
-            base |= 1;
-            d->ch = make_chunks(d->N, base, p);
-        }
+    for (int attempt = 0; attempt < kBaseTries; ++attempt) {
+        set_chunks(h, attempt);
         if (h->mem) {
             cudaFree(h->mem);
             h->mem = nullptr;
         }
-        Arena A;
-        layout_shared(h, A);
-        shared = (A.off + 255) & ~(size_t)255;
-        Arena B;
-        layout_slot(h, B);
-        h->sbytes = (long long)((B.off + 255) & ~(size_t)255);
+        layout_sizes(h, &shared, &h->sbytes);
         h->mem_bytes = shared + (size_t)h->sbytes * capacity + 256;
         if (cudaMalloc(&h->mem, h->mem_bytes) != cudaSuccess) {
             destroy(h);
@@ -1196,8 +1241,22 @@ int wf_sync(wf_handle* h) {
     std::vector<int> st(h->S, 0);
     const int rc = wf_batch_status(h, st.data(), h->S);
     if (rc != WF_OK) return rc;
+    // a bounded wait that gave up leaves some lines of that launch unsolved: every slot's
+    // result of the step is suspect, so the timeout outranks the per-slot guard
     for (int z = 0; z < h->S; ++z)
-        if (st[z] && h->active_host[z]) return WF_EUNSTABLE;
+        if (st[z] & WF_STATUS_TIMEOUT) return WF_ETIMEOUT;
+    for (int z = 0; z < h->S; ++z)
+        if ((st[z] & WF_STATUS_UNSTABLE) && h->active_host[z]) return WF_EUNSTABLE;
+    return WF_OK;
+}
+
+int wf_set_wait_limit(wf_handle* h, double seconds) {
+    if (!h || !(seconds >= 0.0) || seconds > 60.0) return WF_EINVAL;
+    const long long ns = (long long)(seconds * 1e9);
+    if (ns != h->wait_ns) {
+        h->wait_ns = ns;
+        drop_graphs(h);  // the limit travels in the kernels' arguments
+    }
     return WF_OK;
 }
 
@@ -1491,6 +1550,9 @@ cudaError_t noalloc_scratch(float** out) {
 extern "C" int wf_step_noalloc(wf_handle* h, void* T, void* fuel, int pitch, int nsteps) {
     if (!h || !T || !fuel || nsteps < 0) return WF_EINVAL;
     if (h->prec != WF_FP32 || h->S != 1) return WF_EINVAL;
+    // the manufactured-solution forcing keeps its clock in the handle: stepping caller-owned
+    // arrays would advance it for steps the handle itself never took
+    if (h->mms_on) return WF_EINVAL;
     if (pitch < h->Nx) return WF_EINVAL;
     if ((size_t)pitch * (size_t)h->Ny > kNoallocMaxElems) return WF_EINVAL;
     if (nsteps == 0) return WF_OK;

@@ -187,6 +187,8 @@ struct LineArgs {
     double prescale[2];     // y pass only: factor of that band
     const void* base[2];    // y pass only: out = base + solution (or NULL: out = solution)
     int* status;            // y pass only: guard flag for out[0] (or NULL)
+    int* tstatus;           // x pass: flag word whose bit 4 records a bounded wait that gave up
+    long long wait_ns;      // limit of a bounded device wait (ns of %globaltimer; 0: give up at once)
     double tmax;
     Batch b;  // per scenario: in, out, factors, premul, base, status, pre*
     // x pass only, one array: when preT is set the input line is formed in the kernel as

@@ -39,6 +39,8 @@ struct FastArgs {
     const P* spkc[2];
     const P* Ec[2];
     int* status;
+    int* tstatus;       // x pass: bit 4 set when the staging wait gave up
+    long long wait_ns;  // x pass: limit of the staging wait
     P tmax;
     int tma;  // x pass: rows staged with bulk copies (16-byte aligned rows)
     Batch b;
@@ -60,6 +62,7 @@ struct LineView {
     P prescale;
     const P *luc, *spkc, *Ec;
     int* status;
+    int* tstatus;
     const P *preT, *preF, *pA1, *pB1, *pA2, *pB2;
 };
 
@@ -76,6 +79,7 @@ __device__ __forceinline__ LineView<P> scene_line(const FastArgs<P>& a, int arr)
     v.spkc = scene_ptr(one ? a.spkc[1] : a.spkc[0], a.b);
     v.Ec = scene_ptr(one ? a.Ec[1] : a.Ec[0], a.b);
     v.status = scene_ptr(a.status, a.b);
+    v.tstatus = scene_ptr(a.tstatus, a.b);
     v.preT = scene_ptr(a.preT, a.b);
     v.preF = scene_ptr(a.preF, a.b);
     v.pA1 = scene_ptr(a.pA1, a.b);
@@ -125,7 +129,29 @@ __device__ __forceinline__ void bulk_commit_and_wait_read() {
 }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-constexpr uint32_t kSpinLimit = 1u << 20;  // bounded mbarrier wait; a timeout sets status bit 2
+// Bounded mbarrier waits.  The first wait on a staging barrier gives up after the handle's wait
+// limit (ns of the SM's global timer) and sets bit 4 of the slot's flag word; the kernel then
+// drains the copies still in flight with a second wait of kDrainPolls polls (each try_wait may
+// suspend the thread for a while), so that no copy lands in shared memory after the CTA exits.
+constexpr uint32_t kDrainPolls = 1u << 20;
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// true once the barrier's phase `parity` completed; false if limit_ns passed first (limit 0: no poll)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit_ns) {
+    if (limit_ns <= 0) return false;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15u) == 15u && (long long)(global_ns() - t0) > limit_ns) return false;
+    }
+}
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kDrainPolls; ++it)
+        if (mbar_try_wait(bar, parity)) return;
+}
 
 // ---- factors in shared memory ---------------------------------------------------------
 // Each chunk-type row of the compact factors is split into three padded vectors so that one
@@ -475,18 +501,12 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
         }
     }
     __syncthreads();  // mbarrier initialised, factors staged, halo zeroed
-    if (a.tma) {
-        uint32_t it = 0;
-        while (!mbar_try_wait(bar, 0) && ++it < kSpinLimit) {
-        }
-        if (it >= kSpinLimit) staged = false;
-    }
+    if (a.tma) staged = mbar_wait_bounded(bar, 0, a.wait_ns);
     if (!staged) {
-        // give the copy in flight a second bounded wait before the shared memory is released
-        uint32_t it = 0;
-        while (!mbar_try_wait(bar, 0) && ++it < kSpinLimit) {
-        }
-        if (tid == 0 && v.status) atomicOr(v.status, 4);
+        // drain the copies in flight before the shared memory is released; the step's output is
+        // not valid (bit 4 invalidates it for the whole handle)
+        mbar_drain(bar, 0);
+        if (tid == 0 && v.tstatus) atomicOr(v.tstatus, 4);
         return;
     }
     if (pre) {
@@ -750,6 +770,8 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         f.Ec[q] = (const P*)a.f[q].Ec;
     }
     f.status = a.status;
+    f.tstatus = a.tstatus;
+    f.wait_ns = a.wait_ns;
     f.tmax = (P)a.tmax;
     f.b = a.b;
     f.mpad = (ch.base > ch.last ? ch.base : ch.last) | 1;

@@ -115,16 +115,17 @@ void finish(wf_server* s, const std::shared_ptr<Req>& q, int status) {
 }
 
 // Create a class handle sized to the free budget (capacity up to max_slots); nullptr if none fits.
+// The capacity is chosen from the handle's computed size before anything is allocated, so the
+// budget is never overshot, not even for a moment.
 std::unique_ptr<Class> make_class(wf_server* s, const ClassKey& key, const wf_request& r) {
     for (int cap = s->max_slots; cap >= 1; cap /= 2) {
+        size_t need = 0;
+        if (wf_batch_bytes(r.nx, r.ny, r.p, r.dt, &r.params, cap, &need) != WF_OK) return nullptr;
+        if (s->used + need > s->budget) continue;
         wf_handle* h = nullptr;
         if (wf_batch_create(r.nx, r.ny, r.p, r.dt, &r.params, cap, &h) != WF_OK) continue;
         size_t bytes = 0;
         wf_device_bytes(h, &bytes);
-        if (s->used + bytes > s->budget) {
-            wf_destroy(h);
-            continue;
-        }
         auto c = std::make_unique<Class>();
         c->key = key;
         c->h = h;

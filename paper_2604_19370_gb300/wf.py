@@ -33,6 +33,8 @@ WF_FP32 = 0
 WF_FP64 = 1
 WF_F_ONCE = 0
 WF_F_PER_SUBSTEP = 1
+WF_STATUS_UNSTABLE = 1
+WF_STATUS_TIMEOUT = 4
 
 
 class wf_params(ctypes.Structure):
@@ -113,6 +115,8 @@ def lib() -> ctypes.CDLL:
         L.wf_batch_status.argtypes = [vp, ctypes.POINTER(i), i]
         L.wf_batch_capacity.argtypes = [vp]
         L.wf_device_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+        L.wf_batch_bytes.argtypes = [i, i, i, d, ctypes.POINTER(wf_params), i, ctypes.POINTER(sz)]
+        L.wf_set_wait_limit.argtypes = [vp, d]
         L.wf_server_create.argtypes = [sz, i, ctypes.POINTER(vp)]
         L.wf_submit.argtypes = [vp, ctypes.POINTER(wf_request), ctypes.POINTER(ctypes.c_uint64)]
         L.wf_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(wf_result)]
@@ -378,6 +382,17 @@ def wf_device_bytes(h) -> int:
     b = ctypes.c_size_t()
     _check(lib().wf_device_bytes(h, ctypes.byref(b)), "wf_device_bytes")
     return b.value
+
+
+def wf_batch_bytes(nx: int, ny: int, p: int, dt: float, params: wf_params, capacity: int) -> int:
+    """Upper bound of the device bytes a batch handle with these arguments allocates (host-only)."""
+    b = ctypes.c_size_t()
+    _check(lib().wf_batch_bytes(nx, ny, p, dt, ctypes.byref(params), capacity, ctypes.byref(b)), "wf_batch_bytes")
+    return b.value
+
+
+def wf_set_wait_limit(h, seconds: float) -> None:
+    _check(lib().wf_set_wait_limit(h, float(seconds)), "wf_set_wait_limit")
 
 
 def wf_server_create(hbm_budget_bytes: int, max_slots: int) -> ctypes.c_void_p:

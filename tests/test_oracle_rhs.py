@@ -101,3 +101,26 @@ def test_params_match_paper_table(repo_root):
     assert abs(prm.delta_x - 3.5e-2 / eps) < 1e-15 and abs(prm.delta_z - 1.5 * eps) < 1e-15
     assert prm.heat_scale == float(vals["heat_scale"]) and prm.fuel_rate == float(vals["fuel_rate"])
     assert prm.fuel_thresh == float(vals["fuel_thresh"]) and prm.T_a == float(vals["T_a"])
+
+
+def test_source_terms_match_hand_table(repo_root):
+    # s(T, phi), the reaction rate E and the fuel rate against values worked by hand from the
+    # Table constants (tests/golden/source_values.txt): catches a dropped or mis-signed term, a
+    # wrong constant or a wrong threshold on either side of T_ig and of the fuel threshold
+    from oracle.physics import derived_constants, source_terms
+
+    rows = []
+    with open(f"{repo_root}/tests/golden/source_values.txt") as f:
+        for line in f:
+            line = line.split("#")[0].split()
+            if len(line) == 6:
+                rows.append([float(v) for v in line])
+    assert len(rows) == 9
+    prm = Params()
+    kf = derived_constants(prm)["k_f"]
+    for T, phi, delta, s_ref, E_ref, rate_ref in rows:
+        s, E, _ = source_terms(np.array([T]), np.array([phi]), prm)
+        assert abs(s[0] - s_ref) <= 1e-13 * abs(s_ref), (T, phi)
+        assert abs(E[0] - E_ref) <= 1e-13 * max(abs(E_ref), 1.0), (T, phi)
+        assert (E[0] > 0) == bool(delta)
+        assert abs(-kf * E[0] * phi - rate_ref) <= 1e-13 * max(abs(rate_ref), 1.0), (T, phi)

@@ -17,7 +17,11 @@ from scenarios import make_scenario
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_step_matches_regular_step():
+# Nx = 92 here.  Nx + 5: rows of 388 bytes, not a multiple of 16, so the x pass stages its rows
+# with plain loads; Nx + 8: 400-byte rows (16-byte multiple, unlike the handle's own 96-element
+# pitch), so the x pass stages them with bulk copies at a shared-memory stride of its own.
+@pytest.mark.parametrize("extra", [5, 8])
+def test_noalloc_step_matches_regular_step(extra):
     wf = need_gpu()
     import torch
 
@@ -25,7 +29,7 @@ def test_noalloc_step_matches_regular_step():
     ref = wf.simulation_from_scenario(sc, precision=wf.WF_FP32)
     alt = wf.simulation_from_scenario(sc, precision=wf.WF_FP32)
     Nx, Ny = sc.Nx, sc.Ny
-    pitch = Nx + 5  # any pitch >= Nx
+    pitch = Nx + extra  # any pitch >= Nx
     T = torch.zeros((Ny, pitch), dtype=torch.float32, device="cuda")
     P = torch.zeros((Ny, pitch), dtype=torch.float32, device="cuda")
     T[:, :Nx] = torch.from_numpy(sc.T0.astype(np.float32))
@@ -44,6 +48,10 @@ def test_noalloc_step_matches_regular_step():
     assert wf.wf_step_noalloc(alt.h, T.data_ptr(), P.data_ptr(), Nx - 1, 1) == wf.WF_EINVAL
     assert wf.wf_step_noalloc(alt.h, T.data_ptr(), P.data_ptr(), (1 << 19) // Ny + 1, 1) == wf.WF_EINVAL
     assert wf.wf_step_noalloc(alt.h, 0, P.data_ptr(), pitch, 1) == wf.WF_EINVAL
+    # the manufactured-solution clock belongs to the handle's own trajectory
+    wf.wf_set_mms(alt.h, [(10.0, 1, 1, 1.0)])
+    assert wf.wf_step_noalloc(alt.h, T.data_ptr(), P.data_ptr(), pitch, 1) == wf.WF_EINVAL
+    wf.wf_set_mms(alt.h, None)
     ref.close()
     alt.close()
     big = make_scenario("noalloc_fp64", 20, 2, 1e-3, 1, 3, wind=(0.0, 0.0))
