@@ -431,6 +431,17 @@ void wf_server_destroy(wf_server* s);
 int wf_step_noalloc(wf_handle* h, void* T, void* fuel, int pitch, int nsteps);
 /* (wf_step_noalloc takes single-scenario handles only: capacity 1.) */
 
+/*
+ * Measure this GPU's rate of plain fused multiply-adds (TFLOP/s, one FMA =
+ * 2 flops) in `precision` (WF_FP32: the faster of scalar and packed-pair
+ * FMAs; WF_FP64): every SM runs independent FMA chains for a few ms,
+ * timed with CUDA events, best of three.  The roofline denominator of the
+ * quadrature and the line solves, which use these pipes, not tensor cores.
+ * Allocates and frees a small device buffer and a stream; synchronises.
+ * Errors: WF_EINVAL, WF_ENOMEM, WF_ECUDA.  No counterpart in the paper.
+ */
+int wf_measure_fma_peak(int precision, double* tflops);
+
 /* Free every resource of the handle (NULL is accepted). */
 void wf_destroy(wf_handle* h);
 

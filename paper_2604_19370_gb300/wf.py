@@ -117,6 +117,7 @@ def lib() -> ctypes.CDLL:
         L.wf_device_bytes.argtypes = [vp, ctypes.POINTER(sz)]
         L.wf_batch_bytes.argtypes = [i, i, i, d, ctypes.POINTER(wf_params), i, ctypes.POINTER(sz)]
         L.wf_set_wait_limit.argtypes = [vp, d]
+        L.wf_measure_fma_peak.argtypes = [i, dp]
         L.wf_server_create.argtypes = [sz, i, ctypes.POINTER(vp)]
         L.wf_submit.argtypes = [vp, ctypes.POINTER(wf_request), ctypes.POINTER(ctypes.c_uint64)]
         L.wf_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(wf_result)]
@@ -389,6 +390,13 @@ def wf_batch_bytes(nx: int, ny: int, p: int, dt: float, params: wf_params, capac
     b = ctypes.c_size_t()
     _check(lib().wf_batch_bytes(nx, ny, p, dt, ctypes.byref(params), capacity, ctypes.byref(b)), "wf_batch_bytes")
     return b.value
+
+
+def wf_measure_fma_peak(precision: int) -> float:
+    """Measured FMA rate of this GPU in TFLOP/s (WF_FP32 or WF_FP64)."""
+    t = ctypes.c_double()
+    _check(lib().wf_measure_fma_peak(precision, ctypes.byref(t)), "wf_measure_fma_peak")
+    return t.value
 
 
 def wf_set_wait_limit(h, seconds: float) -> None:
