@@ -22,7 +22,7 @@ OUT = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(OUT, "libwf.so")
 
-SOURCES = ["wf_tables.cu", "wf_rhs.cu", "wf_rhs_stream.cu", "wf_solve.cu", "wf_linefast.cu", "wf_api.cu", "wf_server.cu", "wf_mms.cu", "wf_probe.cu"]
+SOURCES = ["wf_tables.cu", "wf_rhs.cu", "wf_rhs_stream.cu", "wf_solve.cu", "wf_linefast.cu", "wf_api.cu", "wf_server.cu", "wf_mms.cu", "wf_probe.cu", "wf_persist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

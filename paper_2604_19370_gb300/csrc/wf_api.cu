@@ -32,7 +32,7 @@ using namespace wf;
 namespace {
 
 constexpr double kTmax = 1e5;  // guard on |T| (K)
-constexpr int kTune = 6;       // tuned launch shapes (wf_autotune)
+constexpr int kTune = 8;       // tuned launch shapes (wf_autotune)
 
 struct Arena {
     char* base = nullptr;
@@ -78,9 +78,10 @@ struct Slot {
     double coef[2][3][3] = {};  // [dir][op][aM, aK, aG]
 };
 
-enum SiteId { S_RHS1, S_X1, S_Y1, S_Y2PRE, S_RHS2, S_MV2, S_X2, S_Y3, S_NSITES };
+enum SiteId { S_RHS1, S_X1, S_Y1, S_Y2PRE, S_RHS2, S_MV2, S_X2, S_Y3, S_PERSIST, S_NSITES };
 const char* kSiteNames[S_NSITES] = {"rhs_quadrature_1", "xsolve_1", "ysolve_1", "ysolve_y_substep",
-                                    "rhs_quadrature_2", "matvec_2", "xsolve_2", "ysolve_2"};
+                                    "rhs_quadrature_2", "matvec_2", "xsolve_2", "ysolve_2",
+                                    "step_persistent"};
 
 }  // namespace
 
@@ -114,10 +115,20 @@ struct wf_handle {
     bool mms_on = false;       // manufactured-solution forcing (wf_set_mms)
     MmsArgs mms{};
     double* tdev = nullptr;    // device: start time of the next step (advanced only with forcing)
-    int tune[kTune] = {0, 0, 0, 0, 0, 0};  // x lines per CTA (first x pass), y lines per CTA,
+    int tune[kTune] = {0, 0, 0, 0, 0, 0, 0, 0};  // x lines per CTA (first x pass), y lines per CTA,
                                            // quadrature segment rows, x lines per warp, x lines
                                            // per CTA of the second x pass, its right-hand side
-                                           // (1 fused, 2 separate matvec) (0: the launchers' rules)
+                                           // (1 fused, 2 separate matvec), step form (1 per-pass
+                                           // launches, 2 persistent), slots per group of the
+                                           // persistent order (0: the launchers' rules)
+    // persistent step: work items, ticket / abort / item count, arrival counters (allocated on
+    // first use); the item list is rebuilt when the active slots or the shapes change
+    int4* p_items = nullptr;
+    int* p_ctl = nullptr;
+    int* p_cnt = nullptr;
+    size_t p_items_cap = 0, p_cnt_cap = 0;
+    bool p_dirty = true;
+    bool noalloc_run = false;  // wf_step_noalloc in progress: per-pass launches only
     void *T = nullptr, *phi = nullptr, *F = nullptr, *Phi = nullptr, *R = nullptr;
     int* status = nullptr;
     void *fxq = nullptr, *gxq = nullptr, *fyq = nullptr, *gyq = nullptr;
@@ -542,6 +553,7 @@ void add_line(LineArgs& a, const void* in, void* out, const Op& o, const Chunks&
 
 cudaError_t upload_active(wf_handle* h) {
     if (!h->active_dirty) return cudaSuccess;
+    h->p_dirty = true;  // the persistent item list holds the active slots
     cudaError_t e = cudaMemcpyAsync(h->active_dev, h->active_host.data(), sizeof(int) * h->S, cudaMemcpyHostToDevice,
                                     h->stream);
     if (e != cudaSuccess) return e;
@@ -571,6 +583,126 @@ cudaError_t rhs_and_forcing(wf_handle* h, const RhsArgs& r, void* out1, double s
 }
 
 cudaError_t enqueue_step_body(wf_handle* h);
+void drop_graphs(wf_handle* h);
+
+// The persistent step (one launch per step over every active slot) takes PR with one F per step
+// in FP32 (p <= 2, wind rank <= 2, no manufactured forcing); tuning value 6 picks it (2) or the
+// per-pass launches (1); the rule (0) takes it whenever it applies.
+bool use_persist(const wf_handle* h) {
+    if (h->noalloc_run || h->prm.scheme != WF_PR || h->prm.F_timing != WF_F_ONCE || h->mms_on) return false;
+    if (!persist_supported(h->prec, h->p, h->wr)) return false;
+    return h->tune[6] != 1;
+}
+
+// Arguments of the persistent step: those of the per-pass launches of the same step.
+void persist_args(wf_handle* h, PersistHost* ph) {
+    Op* X = h->dx.op;
+    Op* Y = h->dy.op;
+    const Chunks& cx = h->dx.ch;
+    const Chunks& cy = h->dy.ch;
+    const double th = 0.5 * h->dt;
+    memset(ph, 0, sizeof(*ph));
+    ph->prec = h->prec;
+    ph->p = h->p;
+    ph->q = rhs_args(h, h->T, h->F, h->Phi, h->R, th, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
+    ph->x1 = line_args(h, 1);
+    add_line(ph->x1, h->R, h->R, X[2], cx);
+    add_line(ph->x1, h->Phi, h->Phi, X[0], cx);
+    ph->y1 = line_args(h, 0);
+    add_line(ph->y1, h->R, h->T, Y[0], cy, h->T);
+    add_line(ph->y1, h->Phi, h->phi, Y[0], cy, h->phi);
+    MatvecArgs& mv = ph->mv;
+    mv.Nx = h->Nx;
+    mv.Ny = h->Ny;
+    mv.pitch = h->pitch;
+    mv.T = h->T;
+    mv.F = h->F;
+    mv.R = h->R;
+    mv.A1 = X[1].bandP;
+    mv.B1 = Y[0].bandP;
+    mv.A2 = X[0].bandP;
+    mv.B2 = Y[1].bandP;
+    mv.Fscale = th;
+    mv.c1 = 1.0;
+    mv.c2 = 1.0;
+    mv.b = batch(h);
+    ph->x2 = line_args(h, 2);
+    add_line(ph->x2, h->R, h->R, X[0], cx);
+    ph->y2 = line_args(h, 0);
+    add_line(ph->y2, h->R, h->T, Y[2], cy, h->T);
+    ph->y2.status = h->status;
+    ph->seg = h->tune[2];
+    ph->xG = h->tune[0];
+    ph->yG = h->tune[1];
+    ph->nslots = h->S;
+    ph->nslots_cap = h->S;
+    ph->wait_ns = h->wait_ns;
+    ph->status = h->status;
+    ph->items = h->p_items;
+    ph->nitems = h->p_ctl ? h->p_ctl + 2 : nullptr;
+    ph->ctl = h->p_ctl;
+    ph->cnt = h->p_cnt;
+}
+
+// Slots per group of the persistent order: about six groups are live at once; their fields (five
+// per slot) should take at most about half of the L2 cache.
+int persist_group(const wf_handle* h) {
+    if (h->tune[7] > 0) return h->tune[7];
+    int dev = 0, l2 = 126 << 20;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    const double slot = 5.0 * h->Ny * h->pitch * esize(h->prec);
+    const int g = (int)(0.5 * l2 / (6.0 * slot));
+    return std::max(1, std::min(g, h->S));
+}
+
+// Allocate the persistent buffers and upload the item list of the active slots when needed.
+// Must run outside stream capture (it allocates and synchronises).  Returns WF_OK when the
+// step uses the per-pass launches.
+int prepare_persist(wf_handle* h) {
+    if (!use_persist(h) || !h->p_dirty) return WF_OK;
+    PersistHost ph;
+    persist_args(h, &ph);
+    PersistPlan plan;
+    cudaError_t e = persist_step(ph, &plan, false, h->stream);
+    if (e == cudaErrorNotSupported) {
+        cudaGetLastError();
+        h->tune[6] = 1;  // this handle's arguments do not fit the persistent form
+        return WF_OK;
+    }
+    if (e != cudaSuccess) return WF_ECUDA;
+    std::vector<int> act;
+    for (int z = 0; z < h->S; ++z)
+        if (h->active_host[z]) act.push_back(z);
+    const size_t need_items = std::max<size_t>(1, act.size() * (size_t)plan.items_per_slot);
+    const size_t need_cnt = (size_t)h->S * plan.cstride;
+    if (need_items > h->p_items_cap || need_cnt > h->p_cnt_cap || !h->p_ctl) {
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;
+        if (h->p_items) cudaFree(h->p_items);
+        if (h->p_cnt) cudaFree(h->p_cnt);
+        if (h->p_ctl) cudaFree(h->p_ctl);
+        h->p_items = nullptr;
+        h->p_cnt = nullptr;
+        h->p_ctl = nullptr;
+        h->p_items_cap = h->p_cnt_cap = 0;
+        // room for every slot active, so that slots joining later need no reallocation
+        const size_t cap_items = std::max(need_items, (size_t)h->S * plan.items_per_slot);
+        if (cudaMalloc(&h->p_items, cap_items * sizeof(int4)) != cudaSuccess ||
+            cudaMalloc(&h->p_cnt, need_cnt * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&h->p_ctl, 4 * sizeof(int)) != cudaSuccess)
+            return WF_ENOMEM;
+        h->p_items_cap = cap_items;
+        h->p_cnt_cap = need_cnt;
+        drop_graphs(h);  // captured graphs hold the old buffers
+    }
+    std::vector<int4> items(need_items);
+    const int n = persist_items(plan, act.data(), (int)act.size(), persist_group(h), items.data(), (int)need_items);
+    if ((size_t)n > need_items) return WF_ECUDA;
+    WF_TRY(cudaMemcpyAsync(h->p_items, items.data(), sizeof(int4) * std::max(n, 1), cudaMemcpyHostToDevice, h->stream));
+    WF_TRY(cudaMemcpyAsync(h->p_ctl + 2, &n, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    WF_TRY(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
+    h->p_dirty = false;
+    return WF_OK;
+}
 
 cudaError_t enqueue_step(wf_handle* h) {
     cudaError_t e = enqueue_step_body(h);
@@ -601,6 +733,11 @@ cudaError_t enqueue_step_body(wf_handle* h) {
         y1.status = h->status;
         if ((e = timed(h, S_Y3, [&] { return launch_ysolve(prec, p, y1, s); })) != cudaSuccess) return e;
         return cudaSuccess;
+    }
+    if (h->prm.scheme == WF_PR && use_persist(h) && h->p_ctl) {
+        PersistHost ph;
+        persist_args(h, &ph);
+        return timed(h, S_PERSIST, [&] { return persist_step(ph, nullptr, true, s); });
     }
     if (h->prm.scheme == WF_PR) {
         const double th = 0.5 * h->dt;
@@ -702,9 +839,11 @@ void drop_graphs(wf_handle* h) {
     if (h->g1) cudaGraphExecDestroy(h->g1);
     if (h->g8) cudaGraphExecDestroy(h->g8);
     h->g1 = h->g8 = nullptr;
+    h->p_dirty = true;  // shapes or wind rank may have changed the persistent plan
 }
 
 cudaError_t capture(wf_handle* h, int steps, cudaGraphExec_t* out) {
+    if (prepare_persist(h) != WF_OK) return cudaErrorMemoryAllocation;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return e;
@@ -733,6 +872,9 @@ void destroy(wf_handle* h) {
     if (!h) return;
     drop_graphs(h);
     if (h->bstage) cudaFree(h->bstage);
+    if (h->p_items) cudaFree(h->p_items);
+    if (h->p_cnt) cudaFree(h->p_cnt);
+    if (h->p_ctl) cudaFree(h->p_ctl);
     for (auto& pnd : h->pending) {
         cudaEventDestroy(pnd.a);
         cudaEventDestroy(pnd.b);
@@ -1214,9 +1356,17 @@ int wf_step(wf_handle* h, int nsteps) {
     if (nsteps == 0) return WF_OK;
     if (upload_active(h) != cudaSuccess) return WF_ECUDA;
     if (h->profiling) {
+        const int rc = prepare_persist(h);
+        if (rc != WF_OK) return rc;
         for (int k = 0; k < nsteps; ++k)
             if (enqueue_step(h) != cudaSuccess) return WF_ECUDA;
         return WF_OK;
+    }
+    if (h->g1 && h->p_dirty && use_persist(h)) {
+        // the active slots changed: new item list (same buffers, so the graphs stay valid unless
+        // prepare_persist had to reallocate them)
+        const int rc = prepare_persist(h);
+        if (rc != WF_OK) return rc;
     }
     if (!h->g1) {
         if (capture(h, 1, &h->g1) != cudaSuccess) {
@@ -1339,12 +1489,18 @@ int wf_autotune(wf_handle* h, int reps) {
     static const int kLines[] = {0, 32, 16, 8, 4, 2, 1};
     static const int kRpw[] = {0, 1, 2, 4};
     static const int kFuse[] = {0, 2};
+    static const int kMode[] = {1, 2};
+    static const int kGroup[] = {0, 1, 2, 4, 8, 16, 32, 64};
     struct Axis {
         int q;
         const int* v;
         int n;
     };
-    const Axis order[] = {{2, kSeg, (int)(sizeof(kSeg) / sizeof(int))},
+    const bool pers = persist_supported(h->prec, h->p, h->wr) && h->prm.scheme == WF_PR &&
+                      h->prm.F_timing == WF_F_ONCE && !h->mms_on;
+    const Axis order[] = {{6, kMode, pers ? 2 : 0},
+                          {7, kGroup, pers && h->S > 1 ? (int)(sizeof(kGroup) / sizeof(int)) : 0},
+                          {2, kSeg, (int)(sizeof(kSeg) / sizeof(int))},
                           {0, kLines, (int)(sizeof(kLines) / sizeof(int))},
                           {3, kRpw, (int)(sizeof(kRpw) / sizeof(int))},
                           {1, kLines, (int)(sizeof(kLines) / sizeof(int))},
@@ -1506,7 +1662,7 @@ int wf_get_tuning(const wf_handle* h, int* shape) {
 int wf_set_tuning(wf_handle* h, const int* shape) {
     if (!h || !shape) return WF_EINVAL;
     for (int q = 0; q < kTune; ++q)
-        if (shape[q] < 0 || shape[q] > (q == 5 ? 2 : 1024)) return WF_EINVAL;
+        if (shape[q] < 0 || shape[q] > (q == 5 || q == 6 ? 2 : 1024)) return WF_EINVAL;
     for (int q = 0; q < kTune; ++q) h->tune[q] = shape[q];
     drop_graphs(h);
     return WF_OK;
@@ -1571,7 +1727,9 @@ extern "C" int wf_step_noalloc(wf_handle* h, void* T, void* fuel, int pitch, int
     h->R = scratch + 2 * kNoallocMaxElems;
     h->pitch = pitch;
     cudaError_t e = cudaSuccess;
+    h->noalloc_run = true;  // the persistent step's buffers may not exist yet: per-pass launches
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = enqueue_step(h);
+    h->noalloc_run = false;
     h->T = save[0];
     h->phi = save[1];
     h->F = save[2];

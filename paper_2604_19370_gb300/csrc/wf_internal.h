@@ -216,6 +216,37 @@ struct MatvecArgs {
 };
 cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s);
 
+// ---- persistent step (wf_persist.cu) ------------------------------------------------
+// One launch per Peaceman-Rachford step (one F per step, FP32, p <= 2, wind rank <= 2) over the
+// (phase, slot, tile) items of every active slot, listed by persist_items; the arguments are those
+// of the per-pass launches of the same step.
+struct PersistHost {
+    int prec, p;
+    RhsArgs q;                // quadrature: F, Phi, R (substep 1)
+    LineArgs x1, y1, x2, y2;  // x1 and y1 with two arrays (R, Phi), x2 and y2 with one
+    MatvecArgs mv;            // substep-2 right-hand side
+    int seg, xG, yG;          // quadrature segment rows, x lines and y columns per tile (0: rule)
+    int nslots;               // active slots (for the segment rule)
+    int nslots_cap;           // slot capacity of the handle (counter blocks)
+    long long wait_ns;
+    int* status;              // slot-0 flag word
+    const int4* items;        // device: work items, *nitems of them
+    const int* nitems;
+    int* ctl;                 // device: ticket, abort flag
+    int* cnt;                 // device: nslots_cap x cstride arrival counters
+};
+struct PersistPlan {
+    int nq8, nmv8, nxg, nyg, narr1, cstride, items_per_slot, seg, xG, yG;
+    size_t smem;
+};
+bool persist_supported(int prec, int p, int wind_rank);
+// plan (and, with launch, enqueue: counter reset + one kernel) of one step; cudaErrorNotSupported
+// when the persistent form cannot take these arguments
+cudaError_t persist_step(const PersistHost& h, PersistPlan* plan, bool launch, cudaStream_t s);
+// work items of one step for the given active slots, groups of gs slots in wavefront order;
+// returns the count (entries past cap are not written)
+int persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs, int4* out, int cap);
+
 // launch-shape helpers shared with the host driver
 int line_rows_per_cta(int prec);
 size_t line_smem_bytes(int prec, const Chunks& ch);

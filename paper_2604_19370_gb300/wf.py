@@ -218,9 +218,9 @@ def wf_step(h, nsteps: int) -> None:
 
 
 def wf_sync(h) -> int:
-    """Returns the status code (WF_OK or WF_EUNSTABLE); raises on other errors."""
+    """Returns the status code (WF_OK, WF_EUNSTABLE or WF_ETIMEOUT); raises on other errors."""
     code = lib().wf_sync(h)
-    if code < 0 and code != WF_EUNSTABLE:
+    if code < 0 and code not in (WF_EUNSTABLE, WF_ETIMEOUT):
         raise WFError(code, "wf_sync")
     return code
 
@@ -311,28 +311,37 @@ def wf_launch_count() -> int:
     return int(n.value)
 
 
-def wf_autotune(h, reps: int = 3) -> Tuple[int, int, int, int, int, int]:
+def wf_autotune(h, reps: int = 3) -> Tuple[int, ...]:
     """Tune the launch shapes of a handle on its active slots.
 
-    Returns (x lines per CTA, y lines per CTA, quadrature segment rows, x lines per warp,
-    second-x-pass lines per CTA, second-x-pass right-hand side: 1 fused, 2 separate matvec).
-    0 is the launchers' rule.
+    Returns the eight tuning values (see wf_get_tuning); 0 is the launchers' rule.
     """
     _check(lib().wf_autotune(h, reps), "wf_autotune")
     return wf_get_tuning(h)
 
 
-def wf_get_tuning(h) -> Tuple[int, int, int, int, int, int]:
-    out = (ctypes.c_int * 6)()
+#: names of the eight tuning values of wf_get_tuning / wf_set_tuning
+TUNING_NAMES = ("x_lines_per_cta", "y_lines_per_cta", "quadrature_segment_rows", "x_lines_per_warp",
+                "x2_lines_per_cta", "x2_rhs", "step_form", "persistent_group_slots")
+
+
+def wf_get_tuning(h) -> Tuple[int, ...]:
+    """(x lines per CTA, y lines per CTA, quadrature segment rows, x lines per warp, second-x-pass
+    lines per CTA, second-x-pass right-hand side (1 fused, 2 separate matvec), step form (1 per-pass
+    launches, 2 persistent), slots per group of the persistent order)."""
+    out = (ctypes.c_int * 8)()
     _check(lib().wf_get_tuning(h, out), "wf_get_tuning")
     return tuple(int(v) for v in out)
 
 
 def wf_set_tuning(h, shape) -> None:
+    """Set the tuning values (six values leave the last two at 0, the rule)."""
     vals = [int(v) for v in shape]
-    if len(vals) != 6:
-        raise ValueError("wf_set_tuning: six values")
-    arr = (ctypes.c_int * 6)(*vals)
+    if len(vals) == 6:
+        vals += [0, 0]
+    if len(vals) != 8:
+        raise ValueError("wf_set_tuning: six or eight values")
+    arr = (ctypes.c_int * 8)(*vals)
     _check(lib().wf_set_tuning(h, arr), "wf_set_tuning")
 
 
