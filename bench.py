@@ -1,25 +1,29 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 ADS wildfire time step.
 
-Workload (one time step = one "step"): 1024 x 1024 elements, quadratic
-B-splines (1026 x 1026 = 1,052,676 DOFs), Peaceman-Rachford, FP32 bulk with
-FP64 1-D factorisations, seeded synthetic terrain (fuel smoothed over 20
-elements, wind speed U[0,3] in a random direction plus a 10 % smooth
-variation).  The state is resident on the GPU; the L2 cache is flushed (a
-256 MiB write) before every timed step, so every step reads its inputs from
-HBM.  Each rank runs its own replica: one domain's x and y passes each need
-whole lines, so the single domain is not split across GPUs.
+Default workload (one "step" = one Peaceman-Rachford time step of every scenario): the batched
+ensemble of 256 scenarios of 256 x 256 elements of quadratic B-splines (258 x 258 = 66,564
+DOFs each, 17.04 M in all), each with a seeded mean wind (direction U[0, 2 pi), speed U[0, 3])
+and ignition point, sharing one seeded fuel field; FP32 bulk with FP64 1-D factorisations; one
+batch handle stepped by the launch form and shapes the autotuner picks (one persistent launch
+per step over every slot, or one launch per pass).  The state (five fields per slot, ~380 MB)
+is larger than the L2 cache, so no flush is needed between steps.  Each rank of a multi-GPU run
+steps its own contiguous share of the scenarios (independent problems, no collective).
 
-Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-instead, on a bounded sample of the same workload.
+The same JSON line carries, as extra keys, the single-instance FP64 path on the 1024^2 domain
+(value, ms/step, error against the FP64 oracle on the same steps) and the served request
+stream (Poisson arrivals at 0.8 x the measured capacity; p50/p99 latency, aggregate
+DOF-steps/s).  --workload c2 / c3 / c5 print those configurations as lines of their own;
+--impl reference times the FP64 CPU oracle on a bounded sample of the workload.
 """
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import math
+import multiprocessing as mp
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -31,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "ADS DOF-steps/s & HBM roofline frac, FP32 vs FP64 @ rel-L2; serving p50/p99"
 UNIT = "DOF-steps/s"
 L2_FLUSH_BYTES = 256 << 20
-FP64_NOMINAL_TFLOPS = 1.25
+T_AMB = 300.0
 
 
 def _peaks():
@@ -43,38 +47,50 @@ def _peaks():
         return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, src="fallback")
 
 
-def fp32_alu_peak_tflops(sm_count: int, mhz: float) -> float:
-    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
-    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+def alu_peak(wf, fp64: bool, sm_count: int, mhz: float):
+    """FMA rate of this GPU (TFLOP/s), measured by the library's probe; the derivation if it fails."""
+    try:
+        v = wf.wf_measure_fma_peak(wf.WF_FP64 if fp64 else wf.WF_FP32)
+        return v, ("measured: FMA chains on every SM (wf_measure_fma_peak), "
+                   + ("FP64" if fp64 else "FP32, faster of scalar and packed-pair FMAs"))
+    except Exception:
+        if fp64:
+            return 1.25, "nominal FP64 rate (probe failed)"
+        return sm_count * 128 * 2 * mhz * 1e6 / 1e12, "derived from SM count and clock (probe failed)"
 
 
-def algorithmic_costs(p: int, fused_x2: bool = True) -> dict:
-    """Algorithmic bytes and flops per DOF of each kernel class (FP32, 4-byte values).
+def algorithmic_costs(p: int, fused_x2: bool = False) -> dict:
+    """Algorithmic bytes and flops per DOF of each kernel class of a PR step (FP32 values).
 
-    Flops count the sum-factorised quadrature once per element (no halo
-    recomputation), one FMA = 2 flops, 30 flops per Gauss point for the
-    pointwise terms (exp and reciprocal counted as one each).  With `fused_x2`
-    the second x pass forms its right-hand side from T* and F itself (no
-    separate matvec launch).
+    Flops count fused multiply-adds (2 flops each) of the sum-factorised method, once per DOF:
+    the quadrature interpolates T, dT/dx (x) and T, dT/dx, dT/dy (y) from p+1 coefficients,
+    2q(p+1) + 3q^2(p+1); the fuel q(p+1) + q^2(p+1); tests them against the basis functions at
+    the same cost (the mirror); 6 per Gauss point for the point source; and forms R with two
+    Kronecker products, 4W + 1 (W = 2p+1: an x and a y band each, plus the scaled F).  A line
+    solve is 4p + 1 per value (p forward, p + 1 backward, 2p spike), + 1 where an increment base
+    is added.  Bytes: each field read or written once by its pass.
     """
     q = nb = p + 1
     W = 2 * p + 1
-    fma = 3 * q * nb + 4 * q * q * nb + 4 * q * q * nb + 3 * q * nb + 2 * (W * W + W)
-    rhs_flops = 2 * fma + 30 * q * q
-    return {
-        # read T, phi; write F, Phi, R
-        "rhs_quadrature_1": dict(bytes=20, flops=rhs_flops),
-        # two arrays (R with X_+, Phi with M^x): read + write each
-        "xsolve_1": dict(bytes=16, flops=2 * (4 * p + 1) * 2),
-        # two arrays: read solve input and base, write result
-        "ysolve_1": dict(bytes=24, flops=2 * (4 * p + 2) * 2),
-        # read T*, F; write R
-        # sum-factorised: both x bands (W taps each) on T, both y bands on the results, scale F
-        "matvec_2": dict(bytes=12, flops=2 * (2 * W) * 2 + 2),
-        "xsolve_2": (dict(bytes=12, flops=2 * (2 * W) * 2 + 2 + (4 * p + 1) * 2) if fused_x2
-                     else dict(bytes=8, flops=(4 * p + 1) * 2)),
-        "ysolve_2": dict(bytes=12, flops=(4 * p + 2) * 2),
+    interp = 2 * q * nb + 3 * q * q * nb
+    fuel = q * nb + q * q * nb
+    quad = interp + fuel + (interp + fuel) + 6 * q * q + (4 * W + 1)
+    line = 4 * p + 1
+    mv = 4 * W + 1
+    c = {
+        "rhs_quadrature_1": dict(bytes=20, flops=2 * quad),          # read T, phi; write F, Phi, R
+        "xsolve_1": dict(bytes=16, flops=2 * 2 * line),               # R and Phi in and out
+        "ysolve_1": dict(bytes=24, flops=2 * 2 * (line + 1)),         # R, Phi, bases T, phi in; T, phi out
+        "matvec_2": dict(bytes=12, flops=2 * mv),                     # T*, F in; R out
+        "xsolve_2": (dict(bytes=12, flops=2 * (mv + line)) if fused_x2 else dict(bytes=8, flops=2 * line)),
+        "ysolve_2": dict(bytes=12, flops=2 * (line + 1)),             # R, base T* in; T out
     }
+    step_flops = c["rhs_quadrature_1"]["flops"] + c["xsolve_1"]["flops"] + c["ysolve_1"]["flops"] + \
+        2 * mv + 2 * line + c["ysolve_2"]["flops"]
+    # one persistent launch is one whole step: the method's minimum bytes (each pass reads and
+    # writes its fields once, the quadrature's R and Phi consumed by the first x pass: 56 B)
+    c["step_persistent"] = dict(bytes=56, flops=step_flops)
+    return c
 
 
 def min_step_bytes(scheme: str) -> int:
@@ -87,6 +103,29 @@ def min_step_bytes(scheme: str) -> int:
     and writes two fields (24).
     """
     return {"pr": 56, "strang": 60, "explicit": 40}[scheme]
+
+
+def roofline(kernel: str, ms: float, dofs: int, costs: dict, es: int, hbm_gbs: float, hbm_src: str,
+             alu: float, alu_src: str, traffic=None) -> dict:
+    """Achieved rate of one kernel against its bound: min(HBM x AI, ALU peak) decides which."""
+    c = costs.get(kernel, dict(bytes=0, flops=0))
+    b = c["bytes"] * (es / 4) * dofs
+    fl = c["flops"] * dofs
+    ai = fl / max(b, 1)
+    balance = alu * 1e12 / (hbm_gbs * 1e9)
+    if ai > balance:
+        ach = fl / (ms * 1e-3) / 1e12
+        r = {"bound": "alu", "achieved": ach, "peak": alu, "unit": "TFLOP/s", "frac": ach / alu,
+             "peak_source": alu_src + " (of measured)"}
+    else:
+        ach = b / (ms * 1e-3) / 1e9
+        r = {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs,
+             "peak_source": f"{hbm_src} copy bandwidth (of {hbm_src})"}
+    r.update({"kernel": kernel, "ms_per_launch": ms, "algorithmic_bytes_per_launch": b,
+              "algorithmic_flops_per_launch": fl, "arithmetic_intensity": ai, "traffic": traffic,
+              "hbm_frac_of_algorithmic_bytes": b / (ms * 1e-3) / 1e9 / hbm_gbs,
+              "alu_frac_of_algorithmic_flops": fl / (ms * 1e-3) / 1e12 / alu})
+    return r
 
 
 def scheme_of(args) -> str:
@@ -107,18 +146,20 @@ def pick_shapes(wf, h, args, reps: int):
 
 
 def _source_sha(name: str) -> str:
+    import hashlib
+
     with open(os.path.join(ROOT, "paper_2604_19370_gb300", "csrc", name), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def _traffic_record(kernel_site: str):
+def _traffic_record(kernel_site: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        r = rec[kernel_site]
-        if r["source_sha"] != _source_sha(r["source"]):
+        r = rec[workload][kernel_site]
+        if any(r["source_sha"].get(s) != _source_sha(s) for s in r["source_sha"]):
             return None
         return float(r["dram_bytes_per_launch"])
     except Exception:
@@ -215,51 +256,94 @@ def shard(n_items: int, rank: int, world: int):
     return range(start, start + base + (1 if rank < extra else 0))
 
 
-def _oracle_sample(steps: int, which: str = "c2", scheme: str = "pr") -> dict:
-    """Run the FP64 oracle (ads mode) in a fresh single-threaded process; returns timing and state file."""
-    out = tempfile.mktemp(suffix=".npz")
-    code = f"""
-import os, sys, time, json
-sys.path.insert(0, {ROOT!r})
-import numpy as np
-from scenarios import config_c2
-from oracle.step import Problem
-sc = config_c2()
-P = Problem.from_scenario(sc, scheme={scheme!r}, mode='ads')
-T, phi = sc.T0.copy(), sc.fuel0.copy()
-t0 = time.perf_counter()
-for _ in range({steps}):
-    T, phi = P.step(T, phi)
-dt = time.perf_counter() - t0
-np.savez({out!r}, T=T, phi=phi)
-print(json.dumps(dict(seconds=dt, dofs=sc.dofs)))
-"""
-    env = dict(os.environ)
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
-        env[k] = "1"
-    env["CUDA_VISIBLE_DEVICES"] = ""
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    res = json.loads(r.stdout.strip().splitlines()[-1])
-    res["state"] = out
-    res["steps"] = steps
-    return res
+def cpu_info() -> dict:
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
 
+
+# ---- the FP64 CPU oracle (test infrastructure; timed here as the baseline) ------------------
+
+def _oracle_worker(job):
+    """One process: the oracle (ads mode) on one scenario; returns wall-clock marks and the state."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    sys.path.insert(0, ROOT)
+    from oracle.step import Problem
+    from scenarios import config_c2, config_c4
+
+    kind, idx, warm, steps, scheme, keep = job
+    if kind == "c4":
+        shared = config_c4(0).fuel0
+        sc = config_c4(idx, shared_fuel=shared)
+    else:
+        sc = config_c2()
+    P = Problem.from_scenario(sc, scheme=scheme, mode="ads")
+    T, phi = sc.T0.copy(), sc.fuel0.copy()
+    for _ in range(warm):
+        T, phi = P.step(T, phi)
+    t0 = time.time()
+    for _ in range(steps):
+        T, phi = P.step(T, phi)
+    t1 = time.time()
+    return dict(t0=t0, t1=t1, dofs=sc.dofs, steps=steps, T=T if keep else None, phi=phi if keep else None)
+
+
+def oracle_runs(jobs, procs: int):
+    """Run oracle jobs in a pool of `procs` fresh processes (spawned: no GPU state is inherited)."""
+    ctx = mp.get_context("spawn")
+    env_save = {k: os.environ.get(k) for k in ("CUDA_VISIBLE_DEVICES",)}
+    os.environ["CUDA_VISIBLE_DEVICES"] = ""
+    try:
+        with ctx.Pool(procs) as pool:
+            return pool.map(_oracle_worker, jobs)
+    finally:
+        for k, v in env_save.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def oracle_throughput(results) -> float:
+    start = min(r["t0"] for r in results)
+    end = max(r["t1"] for r in results)
+    return sum(r["dofs"] * r["steps"] for r in results) / (end - start)
+
+
+def errors_vs_oracle(T, phi, To, po) -> dict:
+    import numpy as np
+
+    return {"T": float(np.linalg.norm(T - To) / np.linalg.norm(To)),
+            "T_minus_Tamb": float(np.linalg.norm(T - To) / np.linalg.norm(To - T_AMB)),
+            "max_abs_T_over_max_T_minus_Tamb": float(np.abs(T - To).max() / np.abs(To - T_AMB).max()),
+            "phi": float(np.linalg.norm(phi - po) / np.linalg.norm(po)),
+            "max_abs_phi": float(np.abs(phi - po).max())}
+
+
+# ---- the reference arm -----------------------------------------------------------------------
 
 def run_reference(args) -> None:
+    """The FP64 CPU oracle on the machine's host cores, on a bounded sample of the default workload.
+
+    One step of this arm is one PR step of as many ensemble scenarios as there are cores (one
+    per process); W warm-up steps are run first and exactly K steps are timed.
+    """
     world, rank, _ = _dist()
     if rank != 0:
         return
-    from scenarios import config_c2
-
-    sc = config_c2()
-    # each oracle step takes seconds: warm-up and timed steps are capped to a bounded sample
-    nsteps = min(args.warmup + args.steps, 24)
-    res = _oracle_sample(nsteps)
-    sec_per_step = res["seconds"] / nsteps
-    value = sc.dofs / sec_per_step
-    os.unlink(res["state"])
+    procs = os.cpu_count() or 1
+    res = oracle_runs([("c4", k, args.warmup, args.steps, "pr", False) for k in range(procs)], procs)
+    value = oracle_throughput(res)
+    wall = max(r["t1"] for r in res) - min(r["t0"] for r in res)
+    dofs = res[0]["dofs"]
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -268,23 +352,26 @@ def run_reference(args) -> None:
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": sec_per_step * 1e3,
+        "ms_per_step": wall * 1e3 / args.steps,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "c2_1024x1024_p2_pr", "nx": 1024, "ny": 1024, "p": 2, "dofs": sc.dofs,
-                   "scheme": "PR", "impl": "FP64 CPU oracle, ads mode (1-D banded solves)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{nsteps} PR steps of the 1026^2-DOF workload (FP64, ads mode)"},
+        "config": {"workload": "c4_ensemble_256x256x256_p2_pr", "nx": 256, "ny": 256, "p": 2,
+                   "scenarios_sampled": procs, "dofs_per_scenario": dofs, "scheme": "PR",
+                   "impl": "FP64 CPU oracle, ads mode (1-D banded solves), one scenario per process"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                         "sample": f"{args.steps} timed PR steps (after {args.warmup}) of {procs} scenarios of the "
+                                   "256-scenario ensemble, one per process", **cpu_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args) -> None:
-    import numpy as np
+# ---- GPU workloads ---------------------------------------------------------------------------
+
+def _setup_gpu():
     import torch
 
     world, rank, local = _dist()
@@ -294,37 +381,217 @@ def run_gpu(args) -> None:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
     from paper_2604_19370_gb300.build import build_library
 
     build_library()
     from paper_2604_19370_gb300 import wf
+
+    return wf, dev, world, rank, local
+
+
+def _kernel_table(kt: dict) -> dict:
+    shares = {k: v[0] for k, v in kt.items() if v[1] > 0}
+    tot = sum(shares.values()) or 1.0
+    return {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / tot} for k, v in kt.items() if v[1] > 0}
+
+
+def run_ensemble(args) -> None:
+    """Batched ensemble: S scenarios of 256^2 elements (p = 2) in one batch handle."""
+    import numpy as np
+    import torch
+
+    wf, dev, world, rank, local = _setup_gpu()
+    from scenarios import config_c4
+
+    S_all = args.scenarios
+    mine = list(shard(S_all, rank, world))
+    first = config_c4(0)
+    shared = first.fuel0
+    scs = [config_c4(k, shared_fuel=shared) for k in mine]
+    S = len(scs)
+    prm = wf.wf_params_default(Lx=first.Lx, Ly=first.Ly, precision=wf.WF_FP32)
+    b = wf.Batch(first.nx, first.ny, first.p, first.dt, prm, capacity=S)
+    for k, sc in enumerate(scs):
+        b.load_scenario(k, sc)
+    stream = torch.cuda.Stream(device=dev)
+    wf.wf_set_stream(b.h, stream.cuda_stream)
+    tuning = pick_shapes(wf, b.h, args, 12)
+    dofs = S * first.dofs
+    with torch.cuda.stream(stream):
+        b.step(args.warmup)
+    stream.synchronize()
+    if wf.wf_sync(b.h) != wf.WF_OK:
+        raise RuntimeError("ensemble unstable or timed out during warm-up")
+
+    def timed(profile):
+        wf.wf_set_profiling(b.h, profile)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(args.steps):
+                wf.wf_step(b.h, 1)
+            e1.record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize(dev)
+        wf.wf_set_profiling(b.h, False)
+        return e0.elapsed_time(e1) * 1e-3
+
+    # timed region: K steps replayed from the step graph (the production launch path)
+    with ClockSampler(local) as clk:
+        secs = timed(False)
+    status = wf.wf_sync(b.h)
+    value, slowest = whole_job_throughput(dofs * args.steps, secs, world, dev)
+    ms_per_step = slowest * 1e3 / args.steps
+    # per-kernel device times: the same K steps launched directly, an event pair around each launch
+    wf.wf_kernel_times(b.h)
+    n0 = wf.wf_launch_count()
+    prof_s = timed(True)
+    launches = wf.wf_launch_count() - n0
+    kt = wf.wf_kernel_times(b.h)
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    alu, alu_src = alu_peak(wf, False, props.multi_processor_count, peaks["sm_max_mhz"])
+    costs = algorithmic_costs(first.p, fused_x2=tuning[5] != 2)
+    ktab = _kernel_table(kt)
+    dom = max(ktab, key=lambda k: ktab[k]["share"])
+    workload = f"c4_ensemble_{S_all}x256x256_p2_pr"
+    roof = roofline(dom, ktab[dom]["ms_per_launch"], dofs, costs, 4, peaks["hbm_gbs"], peaks["src"], alu, alu_src,
+                    _traffic_record(dom, "c4_ensemble_256x256x256_p2_pr") if S_all == 256 else None)
+    step_flops = costs["step_persistent"]["flops"] * dofs
+    # end to end through the C ABI: every slot's state from pinned float32 host arrays in one call,
+    # one step, every slot's state back in one call
+    n = first.dofs
+    hT = torch.empty(S * n, dtype=torch.float32, pin_memory=True)
+    hP = torch.empty(S * n, dtype=torch.float32, pin_memory=True)
+    for k, sc in enumerate(scs):
+        hT.numpy()[k * n:(k + 1) * n] = sc.T0.ravel()
+        hP.numpy()[k * n:(k + 1) * n] = sc.fuel0.ravel()
+    wf.wf_batch_states_ptr(b.h, hT.data_ptr(), hP.data_ptr(), S * n, True, True)  # staging allocated here
+    e2e_steps = 5
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        wf.wf_batch_states_ptr(b.h, hT.data_ptr(), hP.data_ptr(), S * n, True, True)
+        wf.wf_step(b.h, 1)
+        wf.wf_batch_states_ptr(b.h, hT.data_ptr(), hP.data_ptr(), S * n, True, False)
+    e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dev)
+    b.close()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload, "scenarios": S_all, "scenarios_per_rank": S, "nx": 256, "ny": 256,
+                   "p": 2, "dofs": S_all * first.dofs, "scheme": "PR",
+                   "precision": "fp32 bulk, fp64 1-D factorisation",
+                   "l2": f"state of {S} slots x 5 fields (~{5 * S * 258 * 288 * 4 / 2**20:.0f} MiB) > L2, no flush",
+                   "parallelism": f"scenarios sharded over {world} rank(s), no collective",
+                   "launch_shapes": {**{k: v for k, v in zip(wf.TUNING_NAMES, tuning)}, "source": shape_source(args)}},
+        "roofline": roof,
+        "step_roofline": {"hbm_frac_of_min_bytes": min_step_bytes("pr") * dofs / (ms_per_step * 1e-3) / 1e9
+                          / peaks["hbm_gbs"],
+                          "alu_frac": step_flops / (ms_per_step * 1e-3) / 1e12 / alu,
+                          "min_bytes_per_dof": min_step_bytes("pr"),
+                          "flops_per_dof": costs["step_persistent"]["flops"]},
+        "profiled_ms_per_step": prof_s * 1e3 / args.steps,
+        "kernels": ktab,
+        "gpu_launches": launches,
+        "e2e": {"value": world * dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * dofs,
+                "d2h_bytes_per_step": 2 * 4 * dofs, "ms_per_step": e2e_s * 1e3, "host_dtype": "float32"},
+        "clocks": clk.summary(),
+        "status": wf.wf_strerror(status),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle: one core on scenario 0 (its state also checks this path), then every core on
+        # as many scenarios at once
+        ks = args.cpu_steps
+        procs = os.cpu_count() or 1
+        one = oracle_runs([("c4", 0, 0, ks, "pr", True)], 1)[0]
+        allc = oracle_runs([("c4", k, 0, ks, "pr", False) for k in range(procs)], procs)
+        chk = wf.simulation_from_scenario(scs[0], precision=wf.WF_FP32)
+        wf.wf_set_tuning(chk.h, tuning)
+        chk.step(ks)
+        Tg, pg = chk.state()
+        chk.close()
+        line["cpu_baseline"] = {"value": oracle_throughput(allc), "unit": UNIT, "cores": procs, "kind": "oracle",
+                                "sample": f"{ks} PR steps of each of {procs} ensemble scenarios, one per process "
+                                          "(FP64, ads mode)",
+                                "single_core_value": oracle_throughput([one]),
+                                "single_core_sample": f"{ks} PR steps of scenario 0", **cpu_info()}
+        line["rel_l2_vs_oracle"] = {"steps": ks, "scenario": 0, **errors_vs_oracle(Tg, pg, one["T"], one["phi"])}
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["fp64_single_instance"] = fp64_c2_extra(wf, dev, args)
+        line["serving"] = run_serving(args, wf=wf, as_extra=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def fp64_c2_extra(wf, dev, args) -> dict:
+    """The single-instance FP64 path on the 1024^2 domain: device throughput and oracle error."""
+    import torch
+
     from scenarios import config_c2
 
-    sc = config_c2(p=args.p) if args.nx == 1024 else None
-    if sc is None:
-        from scenarios import make_scenario
+    sc = config_c2()
+    sim = wf.simulation_from_scenario(sc, precision=wf.WF_FP64)
+    stream = torch.cuda.Stream(device=dev)
+    wf.wf_set_stream(sim.h, stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        sim.step(3)
+    stream.synchronize()
+    K = 10
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with torch.cuda.stream(stream):
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            wf.wf_step(sim.h, 1)
+            ev[k][1].record(stream)
+    stream.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / K
+    st = sim.sync()
+    sim.close()
+    out = {"workload": "c2_1024x1024_p2_pr_fp64", "value": sc.dofs / (ms * 1e-3), "unit": UNIT,
+           "ms_per_step": ms, "steps": K, "l2": "flushed before every timed step (256 MiB write)",
+           "status": wf.wf_strerror(st)}
+    if not args.no_cpu_baseline:
+        ks = 2
+        o = oracle_runs([("c2", 0, 0, ks, "pr", True)], 1)[0]
+        chk = wf.simulation_from_scenario(sc, precision=wf.WF_FP64)
+        chk.step(ks)
+        Tg, pg = chk.state()
+        chk.close()
+        out["rel_l2_vs_oracle"] = {"steps": ks, **errors_vs_oracle(Tg, pg, o["T"], o["phi"])}
+    return out
 
-        sc = make_scenario(f"n{args.nx}", args.nx, args.p, 1e-3, 1, 2001, fuel_sigma=20.0,
-                           wind_speed_range=(0.0, 3.0))
+
+def run_single(args) -> None:
+    """One domain: c2 (1024^2, p = 2) or c3 (4096^2, p = 3, two fuel classes, gaps, three ignitions)."""
+    import torch
+
+    wf, dev, world, rank, local = _setup_gpu()
+    from scenarios import config_c2, config_c3
+
+    sc = config_c3() if args.workload == "c3" else config_c2(p=args.p)
     prec = wf.WF_FP64 if args.fp64 else wf.WF_FP32
     scheme = {"pr": wf.WF_PR, "strang": wf.WF_STRANG_CN, "explicit": wf.WF_EXPLICIT}[scheme_of(args)]
     sim = wf.simulation_from_scenario(sc, precision=prec, scheme=scheme)
     stream = torch.cuda.Stream(device=dev)
     wf.wf_set_stream(sim.h, stream.cuda_stream)
-    # launch shapes tuned on this handle (its state is restored afterwards)
-    tuning = pick_shapes(wf, sim.h, args, 40)
+    tuning = pick_shapes(wf, sim.h, args, 40 if args.workload == "c2" else 6)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    props = torch.cuda.get_device_properties(dev)
-
-    # warm-up: captures the graphs, settles clocks
     with torch.cuda.stream(stream):
         sim.step(args.warmup)
     stream.synchronize()
     if sim.sync() != wf.WF_OK:
         raise RuntimeError("unstable during warm-up")
 
-    def run_steps(profile: bool, sampler=None):
+    def run_steps(profile: bool):
         """K steps, L2 flushed before each, CUDA events around each step on the launching stream."""
         wf.wf_set_profiling(sim.h, profile)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -343,26 +610,17 @@ def run_gpu(args) -> None:
         wf.wf_set_profiling(sim.h, False)
         return float(sum(a.elapsed_time(b) for a, b in ev))
 
-    # timed region: K steps replayed from the step's CUDA graph (the production launch path)
     with ClockSampler(local) as clk:
         ms_total = run_steps(False)
     status = sim.sync()
     value, slowest_s = whole_job_throughput(sc.dofs * args.steps, ms_total * 1e-3, world, dev)
     ms_per_step = slowest_s * 1e3 / args.steps
-
-    # kernel durations: the same K steps launched kernel by kernel with a CUDA event pair around
-    # each launch on the launching stream (the event records add small gaps between kernels,
-    # which is why this pass is not the one that gives the step time)
-    wf.wf_kernel_times(sim.h)  # reset
+    wf.wf_kernel_times(sim.h)
     n0 = wf.wf_launch_count()
     prof_ms_per_step = run_steps(True) / args.steps
-    launches = wf.wf_launch_count() - n0  # kernels of the same K steps (the graph replays them)
+    launches = wf.wf_launch_count() - n0
     kt = wf.wf_kernel_times(sim.h)
-    if sim.sync() != wf.WF_OK:
-        status = wf.WF_EUNSTABLE
-
-    # end to end through the C ABI with pinned host buffers: set state, one step, read state; the
-    # host arrays are in the handle's working precision (float32 calls for the FP32 path)
+    # end to end through the C ABI with pinned host buffers in the working precision
     n = sc.dofs
     hdt = torch.float64 if args.fp64 else torch.float32
     es = 8 if args.fp64 else 4
@@ -380,75 +638,33 @@ def run_gpu(args) -> None:
         wf.wf_step(sim.h, 1)
         get_ptr(sim.h, hT.data_ptr(), hP.data_ptr(), n)
     e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dev)
-
-    # roofline of the dominant kernel class
     peaks = _peaks()
-    costs = algorithmic_costs(sc.p, fused_x2=("matvec_2" not in kt or kt["matvec_2"][1] == 0)
-                              and scheme_of(args) == "pr")
+    props = torch.cuda.get_device_properties(dev)
+    alu, alu_src = alu_peak(wf, args.fp64, props.multi_processor_count, peaks["sm_max_mhz"])
+    costs = algorithmic_costs(sc.p, fused_x2=tuning[5] != 2 and scheme_of(args) == "pr")
     if scheme_of(args) == "explicit":
         costs["rhs_quadrature_1"]["bytes"] = 16  # no F stored
         costs["ysolve_2"]["bytes"] = 24  # two arrays with their bases
-    es = 8 if args.fp64 else 4
-    shares = {k: v[0] for k, v in kt.items() if v[1] > 0}
-    dom = max(shares, key=shares.get)
-    dom_ms = kt[dom][0] / kt[dom][1]
-    c = costs.get(dom, dict(bytes=0, flops=0))
-    bytes_per_launch = c["bytes"] * (es / 4) * sc.dofs
-    flops_per_launch = c["flops"] * sc.dofs
-    sm_count = props.multi_processor_count
-    if args.fp64:
-        alu_peak = FP64_NOMINAL_TFLOPS
-        alu_src = "nominal FP64 rate of a GB300 (1.25 TFLOP/s)"
-    else:
-        alu_peak = fp32_alu_peak_tflops(sm_count, peaks["sm_max_mhz"])
-        alu_src = f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {peaks['sm_max_mhz']:.0f} MHz"
-    balance = alu_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
-    ai = flops_per_launch / max(bytes_per_launch, 1)
-    if ai > balance:
-        achieved = flops_per_launch / (dom_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "peak_source": alu_src}
-    else:
-        achieved = bytes_per_launch / (dom_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peaks['src']} copy bandwidth"}
-    tr = _traffic_record(dom)
-    roof.update({"kernel": dom, "ms_per_launch": dom_ms, "algorithmic_bytes_per_launch": bytes_per_launch,
-                 "algorithmic_flops_per_launch": flops_per_launch, "traffic": tr})
-    # whole-step HBM view: algorithmic bytes of all kernels of the step over the step time
-    step_bytes = sum(costs[k]["bytes"] for k in costs if k in shares) * (es / 4) * sc.dofs
-    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / sum(shares.values())}
-               for k, v in kt.items() if v[1] > 0}
-
+    ktab = _kernel_table(kt)
+    dom = max(ktab, key=lambda k: ktab[k]["share"])
+    wname = f"{args.workload}_{sc.nx}x{sc.ny}_p{sc.p}_{scheme_of(args)}"
+    roof = roofline(dom, ktab[dom]["ms_per_launch"], sc.dofs, costs, es, peaks["hbm_gbs"], peaks["src"], alu, alu_src,
+                    _traffic_record(dom, wname) if not args.fp64 else None)
     line = {
-        "metric": METRIC,
-        "value": value,
-        "unit": UNIT,
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": ms_per_step,
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f64" if args.fp64 else "f32",
-        "data": "synthetic",
-        "config": {"workload": f"c2_{sc.nx}x{sc.ny}_p{sc.p}_{scheme_of(args)}",
-                   "nx": sc.nx, "ny": sc.ny, "p": sc.p, "dofs": sc.dofs,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.fp64 else "f32", "data": "synthetic",
+        "config": {"workload": wname, "nx": sc.nx, "ny": sc.ny, "p": sc.p, "dofs": sc.dofs,
                    "scheme": {"pr": "PR", "strang": "Strang-CN", "explicit": "explicit L2 projection"}[scheme_of(args)],
                    "precision": "fp64" if args.fp64 else "fp32 bulk, fp64 1-D factorisation",
                    "l2": "flushed before every timed step (256 MiB write)",
-                   "launch_shapes": {"x_lines_per_cta": tuning[0], "y_lines_per_cta": tuning[1],
-                                     "quadrature_segment_rows": tuning[2], "x_lines_per_warp": tuning[3],
-                                     "x2_lines_per_cta": tuning[4], "x2_rhs": tuning[5],
-                                     "source": shape_source(args)},
+                   "launch_shapes": {**{k: v for k, v in zip(wf.TUNING_NAMES, tuning)}, "source": shape_source(args)},
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "step_hbm_frac": min_step_bytes(scheme_of(args)) * (es / 4) * sc.dofs / (ms_per_step * 1e-3) / 1e9
         / peaks["hbm_gbs"],
-        "step_hbm_frac_kernel_bytes": step_bytes / (ms_per_step * 1e-3) / 1e9 / peaks["hbm_gbs"],
         "profiled_ms_per_step": prof_ms_per_step,
-        "kernels": kernels,
+        "kernels": ktab,
         "gpu_launches": launches,
         "e2e": {"value": world * sc.dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * es * n,
                 "d2h_bytes_per_step": 2 * es * n, "ms_per_step": e2e_s * 1e3,
@@ -456,30 +672,22 @@ def run_gpu(args) -> None:
         "clocks": clk.summary(),
         "status": wf.wf_strerror(status),
     }
-
-    # oracle baseline on a bounded sample (rank 0, N=1) and the rel-L2 of this path on the same steps
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "c2":
         ks = args.cpu_steps
-        res = _oracle_sample(ks, scheme=scheme_of(args))
-        d = np.load(res["state"])
-        os.unlink(res["state"])
+        o = oracle_runs([("c2", 0, 0, ks, scheme_of(args), True)], 1)[0]
         chk = wf.simulation_from_scenario(sc, precision=prec, scheme=scheme)
         chk.step(ks)
         Tg, pg = chk.state()
         chk.close()
-        rl = float(np.linalg.norm(Tg - d["T"]) / np.linalg.norm(d["T"]))
-        rla = float(np.linalg.norm(Tg - d["T"]) / np.linalg.norm(d["T"] - 300.0))
-        rlp = float(np.linalg.norm(pg - d["phi"]) / np.linalg.norm(d["phi"]))
-        line["cpu_baseline"] = {"value": sc.dofs * ks / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+        line["cpu_baseline"] = {"value": oracle_throughput([o]), "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{ks} {scheme_of(args)} steps of the same 1026^2-DOF workload, FP64, "
-                                          "ads mode"}
-        line["rel_l2_vs_oracle"] = {"steps": ks, "T": rl, "T_minus_Tamb": rla, "phi": rlp}
+                                          "ads mode (one domain: one core)", **cpu_info()}
+        line["rel_l2_vs_oracle"] = {"steps": ks, **errors_vs_oracle(Tg, pg, o["T"], o["phi"])}
     sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
-
 
 
 def _percentile(xs, q):
@@ -492,151 +700,15 @@ def _percentile(xs, q):
     return xs[f] + (xs[c] - xs[f]) * (k - f)
 
 
-def run_ensemble(args) -> None:
-    """Batched ensemble: S scenarios of 256^2 elements (p = 2) stepped together, one launch per kernel."""
-    import numpy as np
-    import torch
-
-    world, rank, local = _dist()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    from paper_2604_19370_gb300.build import build_library
-
-    build_library()
-    from paper_2604_19370_gb300 import wf
-    from scenarios import config_c4
-
-    S = args.scenarios
-    first = config_c4(0)
-    shared = first.fuel0
-    scs = [first] + [config_c4(k, shared_fuel=shared) for k in range(1, S)]
-    prm = wf.wf_params_default(Lx=first.Lx, Ly=first.Ly, precision=wf.WF_FP32)
-    b = wf.Batch(first.nx, first.ny, first.p, first.dt, prm, capacity=S)
-    for k, sc in enumerate(scs):
-        b.load_scenario(k, sc)
-    stream = torch.cuda.Stream(device=dev)
-    wf.wf_set_stream(b.h, stream.cuda_stream)
-    tuning = pick_shapes(wf, b.h, args, 12)
-    dofs = S * first.dofs
-    with torch.cuda.stream(stream):
-        b.step(args.warmup)
-    stream.synchronize()
-
-    def timed(profile):
-        wf.wf_set_profiling(b.h, profile)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize(dev)
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-            for _ in range(args.steps):
-                wf.wf_step(b.h, 1)
-            e1.record(stream)
-        stream.synchronize()
-        wf.wf_set_profiling(b.h, False)
-        return e0.elapsed_time(e1) * 1e-3
-
-    with ClockSampler(local) as clk:
-        secs = timed(False)
-    value, slowest = whole_job_throughput(dofs * args.steps, secs, world, dev)
-    wf.wf_kernel_times(b.h)
-    n0 = wf.wf_launch_count()
-    timed(True)
-    ens_launches = wf.wf_launch_count() - n0
-    kt = wf.wf_kernel_times(b.h)
-    st = b.status()
-    peaks = _peaks()
-    costs = algorithmic_costs(first.p)
-    shares = {k: v[0] for k, v in kt.items() if v[1] > 0}
-    dom = max(shares, key=shares.get)
-    dom_ms = kt[dom][0] / kt[dom][1]
-    props = torch.cuda.get_device_properties(dev)
-    alu_peak = fp32_alu_peak_tflops(props.multi_processor_count, peaks["sm_max_mhz"])
-    c = costs[dom]
-    if c["flops"] / c["bytes"] > alu_peak * 1e12 / (peaks["hbm_gbs"] * 1e9):
-        ach = c["flops"] * dofs / (dom_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak}
-    else:
-        ach = c["bytes"] * dofs / (dom_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"]}
-    roof.update({"kernel": dom, "ms_per_launch": dom_ms, "traffic": None})
-    step_bytes = sum(costs[k]["bytes"] for k in costs if k in shares) * dofs
-    # end to end through the C ABI: every slot's state from pinned float32 host arrays in one call,
-    # one step, every slot's state back in one call
-    n = first.dofs
-    hT = torch.empty(S * n, dtype=torch.float32, pin_memory=True)
-    hP = torch.empty(S * n, dtype=torch.float32, pin_memory=True)
-    for k, sc in enumerate(scs):
-        hT.numpy()[k * n:(k + 1) * n] = sc.T0.ravel()
-        hP.numpy()[k * n:(k + 1) * n] = sc.fuel0.ravel()
-    wf.wf_batch_states_ptr(b.h, hT.data_ptr(), hP.data_ptr(), S * n, True, True)  # staging allocated here
-    e2e_steps = 5
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        wf.wf_batch_states_ptr(b.h, hT.data_ptr(), hP.data_ptr(), S * n, True, True)
-        wf.wf_step(b.h, 1)
-        wf.wf_batch_states_ptr(b.h, hT.data_ptr(), hP.data_ptr(), S * n, True, False)
-    e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dev)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": slowest * 1e3 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"c4_ensemble_{S}x256x256_p2_pr", "scenarios": S, "nx": 256, "ny": 256, "p": 2,
-                   "dofs": dofs, "l2": f"state {S} x 5 fields > L2, no flush", "parallelism": f"replicas x{world}",
-                   "launch_shapes": {"x_lines_per_cta": tuning[0], "y_lines_per_cta": tuning[1],
-                                     "quadrature_segment_rows": tuning[2], "x_lines_per_warp": tuning[3],
-                                     "x2_lines_per_cta": tuning[4], "x2_rhs": tuning[5],
-                                     "source": shape_source(args)}},
-        "roofline": roof,
-        "step_hbm_frac": min_step_bytes("pr") * dofs / (slowest / args.steps) / 1e9 / peaks["hbm_gbs"],
-        "step_hbm_frac_kernel_bytes": step_bytes / (slowest / args.steps) / 1e9 / peaks["hbm_gbs"],
-        "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in kt.items() if v[1] > 0},
-        "gpu_launches": ens_launches,
-        "e2e": {"value": world * dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * dofs,
-                "d2h_bytes_per_step": 2 * 4 * dofs, "ms_per_step": e2e_s * 1e3, "host_dtype": "float32"},
-        "clocks": clk.summary(),
-        "unstable_slots": int(st.sum()),
-    }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle.step import Problem
-
-        ks = 2
-        P = Problem.from_scenario(scs[0], mode="ads")
-        t0 = time.perf_counter()
-        To, po = P.run(scs[0].T0, scs[0].fuel0, ks)
-        cpu_s = time.perf_counter() - t0
-        chk = wf.simulation_from_scenario(scs[0], precision=wf.WF_FP32)
-        chk.step(ks)
-        Tg, pg = chk.state()
-        chk.close()
-        line["cpu_baseline"] = {"value": first.dofs * ks / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{ks} PR steps of scenario 0 of the ensemble, FP64, ads mode"}
-        line["rel_l2_vs_oracle"] = {"steps": ks, "T": float(np.linalg.norm(Tg - To) / np.linalg.norm(To))}
-    b.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
-
-
-def run_serving(args) -> None:
+def run_serving(args, wf=None, as_extra: bool = False):
     """Served request stream: Poisson arrivals at 80 % of measured capacity, p50/p99 latency."""
     import torch
 
     world, rank, local = _dist()
     if rank != 0:
-        return
-    torch.cuda.set_device(local)
-    from paper_2604_19370_gb300.build import build_library
-
-    build_library()
-    from paper_2604_19370_gb300 import wf
+        return None
+    if wf is None:
+        wf, _, world, rank, local = _setup_gpu()
     from scenarios import make_scenario, request_stream_c5
 
     free, _total = torch.cuda.mem_get_info()
@@ -649,7 +721,7 @@ def run_serving(args) -> None:
     def run(reqs, rate):
         srv = wf.Server(budget, max_slots=args.max_slots)
         prepared = [(scenario(r), r) for r in reqs]
-        tickets, lat, dof_steps = {}, [], 0.0
+        tickets, lat, dof_steps, fails = {}, [], 0.0, 0
         t_start = time.perf_counter()
         pending = list(prepared)
         while pending or tickets:
@@ -665,53 +737,62 @@ def run_serving(args) -> None:
                     if out[0] == wf.WF_OK:
                         lat.append(out[1].latency_s)
                         dof_steps += sc.dofs * sc.steps
+                    else:
+                        fails += 1
             time.sleep(0.0005)
         makespan = time.perf_counter() - t_start
         srv.close()
-        return lat, dof_steps, makespan
+        return lat, dof_steps, makespan, fails
 
-    # capacity: closed loop, every request submitted at once
     warm = request_stream_c5(4, 1.0, seed=55)
     run(warm, None)
     closed = request_stream_c5(args.requests, 1.0, seed=5)
-    lat_c, ds_c, span_c = run(closed, None)
+    lat_c, ds_c, span_c, _ = run(closed, None)
     capacity = len(lat_c) / span_c
     rate = 0.8 * capacity
     open_reqs = request_stream_c5(args.requests, rate, seed=6)
-    lat, ds, span = run(open_reqs, rate)
+    lat, ds, span, fails = run(open_reqs, rate)
+    res = {"workload": "c5_served_poisson", "requests": len(open_reqs), "arrival_rate_hz": rate,
+           "capacity_rps": capacity, "sizes": [128, 256, 512, 1024], "p": [2, 3], "steps": "U[200,2000]",
+           "fp64_share": 0.2, "hbm_budget_bytes": budget, "max_slots_per_class": args.max_slots,
+           "latency_p50_s": _percentile(lat, 0.5), "latency_p99_s": _percentile(lat, 0.99),
+           "completed": len(lat), "failed": fails, "value": ds / span, "unit": UNIT,
+           "closed_loop_dof_steps_per_s": ds_c / span_c}
+    if as_extra:
+        return res
     line = {
         "metric": METRIC, "value": ds / span, "unit": UNIT, "n_gpus": 1, "steps": len(open_reqs),
         "warmup": len(warm), "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (20% of requests f64)", "data": "synthetic",
-        "config": {"workload": "c5_served_poisson", "requests": len(open_reqs), "arrival_rate_hz": rate,
-                   "capacity_rps": capacity, "sizes": [128, 256, 512, 1024], "p": [2, 3],
-                   "steps": "U[200,2000]", "fp64_share": 0.2, "hbm_budget_bytes": budget,
-                   "max_slots_per_class": args.max_slots},
-        "latency_p50_s": _percentile(lat, 0.5), "latency_p99_s": _percentile(lat, 0.99),
-        "completed": len(lat), "closed_loop_dof_steps_per_s": ds_c / span_c,
+        "config": {k: v for k, v in res.items() if k not in ("value", "unit", "latency_p50_s", "latency_p99_s",
+                                                              "completed", "failed", "closed_loop_dof_steps_per_s")},
+        "latency_p50_s": res["latency_p50_s"], "latency_p99_s": res["latency_p99_s"],
+        "completed": res["completed"], "failed": fails, "closed_loop_dof_steps_per_s": res["closed_loop_dof_steps_per_s"],
     }
     print(json.dumps(line), flush=True)
+    return res
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--workload", default="c4", choices=["c2", "c3", "c4", "c5"],
+                    help="c4: batched 256-scenario ensemble (default); c2: one 1024^2 domain; c3: one 4096^2 cubic "
+                         "domain; c5: served request stream")
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--strang", action="store_true")
     ap.add_argument("--explicit", action="store_true", help="explicit L2-projection scheme (the comparator)")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="c4 line without the FP64 and serving extra keys")
     ap.add_argument("--no-autotune", action="store_true", help="launch shapes from the launchers' rules")
-    ap.add_argument("--tuning", default="", help="launch shapes x_cta,y_cta,seg,x_per_warp,x2_cta,x2_rhs (skips the autotuner)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
-                    help="c2: one 1024^2 domain (default); c4: batched ensemble; c5: served request stream")
+    ap.add_argument("--tuning", default="", help="the eight tuning values of wf_set_tuning (skips the autotuner)")
     ap.add_argument("--scenarios", type=int, default=256)
-    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--max-slots", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -723,7 +804,7 @@ def main():
     elif args.workload == "c5":
         run_serving(args)
     else:
-        run_gpu(args)
+        run_single(args)
 
 
 if __name__ == "__main__":

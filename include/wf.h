@@ -240,11 +240,13 @@ int wf_launch_count(unsigned long long* n);
 
 /*
  * Launch-shape autotuner (no counterpart in the paper, whose solver runs on
- * CPU threads).  Six shapes are tuned (int shape[6]):
+ * CPU threads).  Eight values are tuned (int shape[8]):
  *   shape[0]  lines per CTA of the first x pass of a step (rows staged per
- *             CTA; at most 8 warps' worth),
+ *             CTA; at most 8 warps' worth); lines per tile of both x passes of
+ *             the persistent step,
  *   shape[1]  lines per CTA of the y pass (columns per CTA, bounded by
- *             lines x chunks <= 256 threads),
+ *             lines x chunks <= 256 threads); columns per tile of the
+ *             persistent step's y passes,
  *   shape[2]  element rows per segment of the streaming quadrature kernel,
  *   shape[3]  lines per warp of the x passes (1, 2 or 4; at most 32 / chunks
  *             per line, which is also the default),
@@ -253,8 +255,17 @@ int wf_launch_count(unsigned long long* n);
  *             side of its second x pass: 1 inside that pass (from staged rows
  *             of T* and F), 2 in a streaming matvec kernel before it (one more
  *             pass over R, but every thread busy on short lines);
- * 0 selects the launchers' built-in rule (for shape[5]: inside the pass).
- * Both schedules of shape[5] perform the same operations in the same order.  wf_autotune tunes one shape at a
+ *   shape[6]  step form: 1 one launch per pass (six or seven per step), 2 one
+ *             persistent launch per step over every active slot (Peaceman-
+ *             Rachford with one F per step, FP32, p <= 2, wind rank <= 2,
+ *             no manufactured forcing; elsewhere the per-pass form runs);
+ *   shape[7]  slots per group of the persistent step's work order (the order
+ *             keeps about six groups' fields live, sized for the L2 cache);
+ * 0 selects the built-in rule (shape[5]: inside the pass; shape[6]: the
+ * persistent step where it applies).
+ * Every value changes the schedule only: both right-hand-side placements and
+ * both step forms perform the same operations in the same order, so the
+ * results are the same bits.  wf_autotune tunes one value at a
  * time (two sweeps, the others held at their best values): each candidate
  * is timed in three rounds (the candidates in alternating order, so that a
  * drift of the clocks favours none), each round reps steps (after one
@@ -266,10 +277,10 @@ int wf_launch_count(unsigned long long* n);
  * had), synchronises the handle's stream, drops the captured graphs (they
  * are captured again by the next wf_step) and discards kernel times
  * collected under wf_set_profiling.  No active slot: WF_OK, nothing tuned.
- * Shapes never change the arithmetic of a line or an element.
  * Errors: WF_EINVAL (reps outside 1..100), WF_ENOMEM, WF_ECUDA.
- * wf_get_tuning / wf_set_tuning read and write the six values
- * (wf_set_tuning: shape[0..4] each 0..1024, shape[5] 0..2, else WF_EINVAL).
+ * wf_get_tuning / wf_set_tuning read and write the eight values
+ * (wf_set_tuning: shape[5] and shape[6] 0..2, the others 0..1024, else
+ * WF_EINVAL).
  */
 int wf_autotune(wf_handle* h, int reps);
 int wf_get_tuning(const wf_handle* h, int* shape);

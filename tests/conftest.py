@@ -16,3 +16,19 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def repo_root():
     return ROOT
+
+
+def pytest_collection_modifyitems(session, config, items):
+    # the all-steps parity tests need minutes of oracle work: start it in background processes
+    # now, so that it runs while the other tests run
+    if any("test_gpu_zlong" in it.nodeid for it in items):
+        try:
+            import torch
+
+            if not torch.cuda.is_available():
+                return
+        except Exception:
+            return
+        import long_oracle
+
+        long_oracle.start()

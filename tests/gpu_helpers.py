@@ -24,6 +24,58 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
+T_AMB = 300.0
+
+#: parity bars of the CUDA path against the FP64 oracle, per precision:
+#:   rel   relative L2 of T and of phi over the coefficient vectors;
+#:   dT    max |T - To| / max |To - T_amb| (element by element, against the fire's departure from
+#:         ambient, which the background would otherwise hide in the relative L2);
+#:   dphi  max |phi - phi_o| (fuel is in [0, 1]).
+BARS = {"fp64": dict(rel=1e-10, dT=1e-10, dphi=1e-10), "fp32": dict(rel=1e-4, dT=1e-4, dphi=1e-5)}
+
+
+def parity_errors(T, phi, To, po):
+    T, phi, To, po = (np.asarray(a, dtype=np.float64) for a in (T, phi, To, po))
+    dev = max(float(np.abs(To - T_AMB).max()), 1e-300)
+    return dict(rel_T=rel(T, To), rel_phi=rel(phi, po), dT=float(np.abs(T - To).max()) / dev,
+                dphi=float(np.abs(phi - po).max()))
+
+
+def assert_parity(T, phi, To, po, prec, rel_bar=None):
+    """Element-wise and relative-L2 parity of (T, phi) with the oracle's (To, po) at the bars of `prec`."""
+    b = BARS[prec]
+    e = parity_errors(T, phi, To, po)
+    rb = b["rel"] if rel_bar is None else rel_bar
+    assert e["rel_T"] <= rb and e["rel_phi"] <= rb, e
+    assert e["dT"] <= b["dT"], e
+    assert e["dphi"] <= b["dphi"], e
+    return e
+
+
+def window(sc, e0x, e0y, n):
+    """The scenario restricted to n x n elements starting at element (e0x, e0y): same element size,
+    the window's temperature, fuel and wind-factor coefficients (its edges become domain edges)."""
+    import dataclasses
+
+    N = n + sc.p
+    h = sc.Lx / sc.nx
+    cut = lambda a: a[e0y:e0y + N, e0x:e0x + N].copy()  # noqa: E731
+    kw = {}
+    if sc.wind_rank:
+        kw = dict(fx=sc.fx[:, e0x:e0x + N].copy(), gx=sc.gx[:, e0y:e0y + N].copy(),
+                  fy=sc.fy[:, e0x:e0x + N].copy(), gy=sc.gy[:, e0y:e0y + N].copy())
+    return dataclasses.replace(sc, name=sc.name + "_window", nx=n, ny=n, Lx=n * h, Ly=n * h,
+                               T0=cut(sc.T0), fuel0=cut(sc.fuel0), **kw)
+
+
+def fire_window(sc, n, margin=8):
+    """Origin (e0x, e0y) of an n x n element window centred on the hottest coefficient."""
+    j, i = np.unravel_index(np.argmax(sc.T0), sc.T0.shape)
+    e0x = int(np.clip(i - n // 2, margin, sc.nx - n - margin))
+    e0y = int(np.clip(j - n // 2, margin, sc.ny - n - margin))
+    return e0x, e0y
+
+
 def oracle_run(sc, steps, scheme="pr", F_timing="once", prm=None, T0=None, phi0=None):
     prm = prm if prm is not None else Params(F_timing=F_timing)
     P = Problem.from_scenario(sc, prm=prm, scheme=scheme, mode="ads")

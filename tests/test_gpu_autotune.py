@@ -11,7 +11,7 @@
 import numpy as np
 import pytest
 
-from gpu_helpers import need_gpu, oracle_run, rel
+from gpu_helpers import assert_parity, need_gpu, oracle_run, rel
 from scenarios import make_scenario
 
 pytestmark = pytest.mark.gpu
@@ -37,7 +37,8 @@ def test_shapes_do_not_change_results(wf, prec, scheme):
     # rectangular, several chunks per line and several quadrature segments
     sc = make_scenario("shape", 150, 2, 1e-3, 1, 91, wind=(1.2, -0.7), fuel_sigma=3.0)
     ref = None
-    for shape in SHAPES:
+    # every shape in both step forms (per-pass launches; the persistent launch where it applies)
+    for shape in [tuple(s6) + (form, 0) for s6 in SHAPES for form in (1, 2)]:
         sim = _sim(wf, sc, P, code)
         wf.wf_set_tuning(sim.h, shape)
         assert wf.wf_get_tuning(sim.h) == shape
@@ -79,6 +80,7 @@ def test_autotune_keeps_state_and_parity(wf):
     assert shape[0] in (0, 32, 16, 8, 4, 2, 1) and shape[1] in (0, 32, 16, 8, 4, 2, 1)
     assert shape[2] in (0, 128, 96, 80, 64, 56, 48, 40, 32, 28, 24, 21, 20, 16, 12) and shape[3] in (0, 1, 2, 4)
     assert shape[4] in (0, 32, 16, 8, 4, 2, 1) and shape[5] in (0, 2)
+    assert shape[6] in (0, 1, 2) and shape[7] in (0, 1, 2, 4, 8, 16, 32, 64)
     T1, p1 = sim.state()
     assert np.array_equal(T0, T1) and np.array_equal(p0, p1)
     sim.step(4)
@@ -86,7 +88,7 @@ def test_autotune_keeps_state_and_parity(wf):
     T, phi = sim.state()
     sim.close()
     To, po = oracle_run(sc, 6)
-    assert rel(T, To) <= 1e-5 and rel(phi, po) <= 1e-5
+    assert_parity(T, phi, To, po, "fp32", rel_bar=1e-5)
 
 
 def test_autotune_batch_keeps_every_slot(wf):
@@ -119,9 +121,11 @@ def test_tuning_argument_checks(wf):
     sim = _sim(wf, sc, wf.WF_FP32, wf.WF_PR)
     L = wf.lib()
     assert L.wf_autotune(sim.h, 0) == wf.WF_EINVAL
-    bad = (wf.ctypes.c_int * 6)(1, -1, 0, 0, 0, 0)
+    bad = (wf.ctypes.c_int * 8)(1, -1, 0, 0, 0, 0, 0, 0)
     assert L.wf_set_tuning(sim.h, bad) == wf.WF_EINVAL
-    bad = (wf.ctypes.c_int * 6)(0, 0, 0, 0, 0, 3)
+    bad = (wf.ctypes.c_int * 8)(0, 0, 0, 0, 0, 3, 0, 0)
+    assert L.wf_set_tuning(sim.h, bad) == wf.WF_EINVAL
+    bad = (wf.ctypes.c_int * 8)(0, 0, 0, 0, 0, 0, 3, 0)
     assert L.wf_set_tuning(sim.h, bad) == wf.WF_EINVAL
     sim.close()
 

@@ -9,7 +9,7 @@ parity bar of the FP64 oracle.
 import numpy as np
 import pytest
 
-from gpu_helpers import gpu_run, need_gpu, oracle_run, rel
+from gpu_helpers import assert_parity, gpu_run, need_gpu, oracle_run, rel
 from scenarios import make_scenario
 
 pytestmark = pytest.mark.gpu
@@ -52,7 +52,7 @@ def test_batch_slots_equal_single_runs(wf, prec, scheme):
     # one slot against the oracle
     To, po = oracle_run(scs[2], steps, scheme=scheme)
     Tb, pb = b.state(2)
-    assert rel(Tb, To) <= (1e-10 if prec == "fp64" else 1e-5)
+    assert_parity(Tb, pb, To, po, prec, rel_bar=1e-10 if prec == "fp64" else 1e-5)
     # the unused slot stayed zero
     Tz, pz = b.state(5)
     assert not Tz.any() and not pz.any()

@@ -18,7 +18,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from gpu_helpers import gpu_run, need_gpu, oracle_run, rel
+from gpu_helpers import assert_parity, gpu_run, need_gpu, oracle_run, rel
 from scenarios import config_c3
 
 pytestmark = pytest.mark.gpu
@@ -67,7 +67,7 @@ def test_c3_sampled_window(wf, c3):
     pg = phi[e0y:e0y + N, e0x:e0x + N][inner]
     # the window holds the ignition: the reaction term is exercised
     assert Tg.max() > 800.0
-    assert rel(Tg, To[inner]) <= 1e-5 and rel(pg, po[inner]) <= 1e-5
+    assert_parity(Tg, pg, To[inner], po[inner], "fp32", rel_bar=1e-5)
 
 
 def test_c3_uniform_state_every_dof(wf, c3):

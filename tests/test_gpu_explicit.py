@@ -8,7 +8,7 @@ after a few steps; shapes cover several chunks per line, ragged tails and p = 1,
 import numpy as np
 import pytest
 
-from gpu_helpers import gpu_run, need_gpu, oracle_run, rel
+from gpu_helpers import assert_parity, gpu_run, need_gpu, oracle_run
 from scenarios import config_c1, make_scenario
 from test_gpu_parity import _rect
 
@@ -27,7 +27,7 @@ def test_c1_explicit(wf, prec, tol):
     P = wf.WF_FP64 if prec == "fp64" else wf.WF_FP32
     T, phi = gpu_run(wf, sc, steps, P, scheme=wf.WF_EXPLICIT)
     To, po = oracle_run(sc, steps, scheme="explicit")
-    assert rel(T, To) <= tol and rel(phi, po) <= tol
+    assert_parity(T, phi, To, po, prec, rel_bar=tol)
 
 
 @pytest.mark.parametrize("nx,ny,p", [(1, 1, 2), (37, 29, 2), (23, 41, 3), (150, 70, 2), (130, 5, 1)])
@@ -37,7 +37,7 @@ def test_shapes_explicit_fp64(wf, nx, ny, p):
     T0 = sc.T0 + 500.0 * np.random.default_rng(nx + 7 * ny).random(sc.T0.shape)
     T, phi = gpu_run(wf, sc, sc.steps, wf.WF_FP64, scheme=wf.WF_EXPLICIT, T0=T0)
     To, po = oracle_run(sc, sc.steps, scheme="explicit", T0=T0)
-    assert rel(T, To) <= 1e-10 and rel(phi, po) <= 1e-10
+    assert_parity(T, phi, To, po, "fp64")
 
 
 def test_explicit_uniform_state(wf):

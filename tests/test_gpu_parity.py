@@ -1,9 +1,11 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Bars (stated by the target of this build):
-  FP64 path: relative L2 of T and of phi <= 1e-10 after all steps;
-  FP32 path: relative L2 of T <= 1e-4, and the 800 K isotherm within one
-  element (symmetric Hausdorff distance over elements, Chebyshev metric).
+Bars (gpu_helpers.BARS):
+  FP64 path: relative L2 of T and of phi <= 1e-10 after all steps, and element by element
+  max |T - To| <= 1e-10 max |To - T_amb|, max |phi - phi_o| <= 1e-10;
+  FP32 path: relative L2 of T <= 1e-4, max |T - To| <= 1e-4 max |To - T_amb|,
+  max |phi - phi_o| <= 1e-5, and the 800 K isotherm within one element
+  (symmetric Hausdorff distance over elements, Chebyshev metric).
 Cases span several tiles (16 x 16 coefficient tiles of the quadrature
 kernel) with ragged tails, several chunks per line (32 coefficients per
 chunk in FP32, 64 in FP64), p = 1, 2, 3, non-square grids, the smallest
@@ -12,7 +14,7 @@ grids (one element) and the full 1024 x 1024 workload for a few steps.
 import numpy as np
 import pytest
 
-from gpu_helpers import gpu_run, hausdorff_elements, isotherm_elements, need_gpu, oracle_run, rel
+from gpu_helpers import assert_parity, gpu_run, hausdorff_elements, isotherm_elements, need_gpu, oracle_run, rel
 from oracle.physics import Params
 from scenarios import config_c1, config_c2, make_scenario
 
@@ -28,18 +30,28 @@ def test_c1_fp64_pr(wf):
     sc = config_c1()
     T, phi = gpu_run(wf, sc, sc.steps, wf.WF_FP64)
     To, po = oracle_run(sc, sc.steps)
-    assert rel(T, To) <= 1e-10
-    assert rel(phi, po) <= 1e-10
+    assert_parity(T, phi, To, po, "fp64")
 
 
 def test_c1_fp32_pr(wf):
     sc = config_c1()
-    T, phi = gpu_run(wf, sc, sc.steps, wf.WF_FP32)
-    To, po = oracle_run(sc, sc.steps)
-    assert rel(T, To) <= 1e-4
-    # the C1 ignition sits on thin fuel: by step 100 the fire has died in both runs (empty sets match)
-    iso_g = isotherm_elements(T, sc.nx, sc.p, sc.Lx)
-    iso_o = isotherm_elements(To, sc.nx, sc.p, sc.Lx)
+    # the C1 ignition sits on thin fuel: its 800 K front exists for about 40 steps (3 elements at
+    # step 20) and has died by step 100; the isotherm is compared while it exists, the state after
+    # all steps
+    sim = wf.simulation_from_scenario(sc, precision=wf.WF_FP32)
+    sim.step(20)
+    T20, _ = sim.state()
+    sim.step(sc.steps - 20)
+    assert sim.sync() == wf.WF_OK
+    T, phi = sim.state()
+    sim.close()
+    P = oracle_run(sc, 20)
+    To20 = P[0]
+    To, po = oracle_run(sc, sc.steps - 20, T0=P[0], phi0=P[1])
+    assert_parity(T, phi, To, po, "fp32")
+    iso_g = isotherm_elements(T20, sc.nx, sc.p, sc.Lx)
+    iso_o = isotherm_elements(To20, sc.nx, sc.p, sc.Lx)
+    assert len(iso_o) > 0
     assert hausdorff_elements(iso_g, iso_o) <= 1
 
 
@@ -52,7 +64,7 @@ def test_ring_of_fire_fp32_isotherm(wf):
     sc = _ring(64, 60)
     T, phi = gpu_run(wf, sc, sc.steps, wf.WF_FP32)
     To, po = oracle_run(sc, sc.steps)
-    assert rel(T, To) <= 1e-4
+    assert_parity(T, phi, To, po, "fp32")
     iso_g = isotherm_elements(T, sc.nx, sc.p, sc.Lx)
     iso_o = isotherm_elements(To, sc.nx, sc.p, sc.Lx)
     assert len(iso_o) > 0
@@ -75,9 +87,7 @@ def test_c1_strang(wf, prec, tol):
     steps = 40
     T, phi = gpu_run(wf, sc, steps, wf.WF_FP64 if prec == "fp64" else wf.WF_FP32, scheme=wf.WF_STRANG_CN)
     To, po = oracle_run(sc, steps, scheme="strang")
-    assert rel(T, To) <= tol
-    if prec == "fp64":
-        assert rel(phi, po) <= tol
+    assert_parity(T, phi, To, po, prec, rel_bar=tol)
 
 
 def test_pr_f_per_substep_fp64(wf):
@@ -85,7 +95,7 @@ def test_pr_f_per_substep_fp64(wf):
     steps = 30
     T, phi = gpu_run(wf, sc, steps, wf.WF_FP64, F_timing=wf.WF_F_PER_SUBSTEP)
     To, po = oracle_run(sc, steps, F_timing="per_substep")
-    assert rel(T, To) <= 1e-10 and rel(phi, po) <= 1e-10
+    assert_parity(T, phi, To, po, "fp64")
 
 
 SHAPES = [(1, 1, 2), (2, 3, 1), (1, 4, 3), (37, 29, 2), (23, 41, 3), (150, 70, 2), (70, 150, 3), (130, 5, 1),
@@ -101,7 +111,7 @@ def test_shapes_fp64(wf, nx, ny, p, scheme):
     code = wf.WF_PR if scheme == "pr" else wf.WF_STRANG_CN
     T, phi = gpu_run(wf, sc, sc.steps, wf.WF_FP64, scheme=code, T0=T0)
     To, po = oracle_run(sc, sc.steps, scheme=scheme, T0=T0)
-    assert rel(T, To) <= 1e-10 and rel(phi, po) <= 1e-10
+    assert_parity(T, phi, To, po, "fp64")
 
 
 @pytest.mark.parametrize("nx,ny,p", SHAPES)
@@ -110,7 +120,7 @@ def test_shapes_fp32(wf, nx, ny, p):
                nx, ny)
     T, phi = gpu_run(wf, sc, sc.steps, wf.WF_FP32)
     To, po = oracle_run(sc, sc.steps)
-    assert rel(T, To) <= 1e-5 and rel(phi, po) <= 1e-5
+    assert_parity(T, phi, To, po, "fp32", rel_bar=1e-5)
 
 
 def _rect(sc, nx, ny):
@@ -130,20 +140,17 @@ def test_full_size_fp32_pr_two_steps(wf):
     sc = config_c2()
     T, phi = gpu_run(wf, sc, 2, wf.WF_FP32)
     To, po = oracle_run(sc, 2)
-    assert rel(T, To) <= 1e-5 and rel(phi, po) <= 1e-5
-    # sampled pointwise check of the hottest region
-    j, i = np.unravel_index(np.argmax(To), To.shape)
-    assert abs(T[j, i] - To[j, i]) <= 1e-4 * To[j, i]
+    assert_parity(T, phi, To, po, "fp32", rel_bar=1e-5)
 
 
 def test_full_size_fp64_one_step_and_strang_fp32(wf):
     sc = config_c2()
     T, phi = gpu_run(wf, sc, 1, wf.WF_FP64)
     To, po = oracle_run(sc, 1)
-    assert rel(T, To) <= 1e-10 and rel(phi, po) <= 1e-10
+    assert_parity(T, phi, To, po, "fp64")
     T, phi = gpu_run(wf, sc, 1, wf.WF_FP32, scheme=wf.WF_STRANG_CN)
     To, po = oracle_run(sc, 1, scheme="strang")
-    assert rel(T, To) <= 1e-5
+    assert_parity(T, phi, To, po, "fp32", rel_bar=1e-5)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -228,7 +235,7 @@ def test_wind_change_between_steps(wf):
 
     sc0 = dataclasses.replace(sc, wind_rank=0)
     To, po = oracle_run(sc0, 3, T0=T1, phi0=p1)
-    assert rel(T, To) <= 1e-10
+    assert_parity(T, phi, To, po, "fp64")
 
 
 @pytest.mark.parametrize("wind", [(0.0, 0.0), (1.3, -0.6)])
@@ -245,7 +252,7 @@ def test_fp32_hot_rows(wf, wind):
         T0[r, rng.random(T0.shape[1]) < 0.3] = 1100.0
     T, phi = gpu_run(wf, sc, 1, wf.WF_FP32, T0=T0)
     To, po = oracle_run(sc, 1, T0=T0)
-    assert rel(T, To) <= 1e-5 and rel(phi, po) <= 1e-5
+    assert_parity(T, phi, To, po, "fp32", rel_bar=1e-5)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])

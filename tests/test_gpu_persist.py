@@ -11,7 +11,7 @@ the step reports WF_ETIMEOUT, nothing hangs, and the handle steps normally after
 import numpy as np
 import pytest
 
-from gpu_helpers import need_gpu, oracle_run, rel
+from gpu_helpers import assert_parity, need_gpu, oracle_run
 from scenarios import make_scenario
 
 pytestmark = pytest.mark.gpu
@@ -99,9 +99,7 @@ def test_persistent_against_oracle(wf):
     _, out = _run(wf, [sc], sc.steps, PERSIST)
     T, phi = out[0]
     To, po = oracle_run(sc, sc.steps)
-    assert rel(T, To) <= 1e-5 and rel(phi, po) <= 1e-5
-    dT = np.abs(T - To).max() / np.abs(To - 300.0).max()
-    assert dT <= 1e-4
+    assert_parity(T, phi, To, po, "fp32", rel_bar=1e-5)
 
 
 @pytest.mark.parametrize("k", [1, 4])

@@ -11,7 +11,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from gpu_helpers import gpu_run, need_gpu, oracle_run, rel
+from gpu_helpers import assert_parity, gpu_run, need_gpu, oracle_run
 from oracle.step import Problem
 from scenarios import fuel_from_map, gaussian_blur, make_scenario, read_fuel_csv
 
@@ -45,7 +45,7 @@ def test_two_wind_phases(wf, prec, tol):
     T, phi = sim.state()
     sim.close()
     To, po = _oracle_two_phase(sc, k, m)
-    assert rel(T, To) <= tol and rel(phi, po) <= tol
+    assert_parity(T, phi, To, po, prec, rel_bar=tol)
 
 
 def test_two_wind_phases_in_a_batch_slot(wf):
@@ -80,5 +80,5 @@ def test_fuel_from_csv_raster(wf, tmp_path):
     sc = dataclasses.replace(sc, fuel0=fuel)
     T, phi = gpu_run(wf, sc, 12, wf.WF_FP64)
     To, po = oracle_run(sc, 12)
-    assert rel(T, To) <= 1e-10 and rel(phi, po) <= 1e-10
+    assert_parity(T, phi, To, po, "fp64")
     assert set(np.unique(np.round(fuel, 6))) <= {0.3 * 0.725, 0.725}

@@ -1,0 +1,105 @@
+"""Parity after all steps at full size: the 1024^2 domain for its 1000 steps (FP64 and FP32) and
+sampled members of the 256-scenario ensemble for their 2000 steps, in the launch configuration
+the bench times (steps replayed from the step graph; the ensemble in one batch handle).
+
+The oracle runs on a window of elements around each fire (tests/long_oracle.py; the windowing is
+pinned against a full-domain run in tests/test_oracle_window.py), started in background
+processes at collection; the comparison covers the window's interior, at the fire's hottest
+phase and after the last step, with the element-wise bars of the parity tests.  Outside the
+window the GPU state must have stayed ambient.  The 800 K isotherm of the FP32 run must lie
+within one element of the oracle's while the front exists.
+"""
+import numpy as np
+import pytest
+
+import long_oracle
+from gpu_helpers import T_AMB, assert_parity, hausdorff_elements, isotherm_elements, need_gpu, parity_errors
+from scenarios import config_c2, config_c4
+
+pytestmark = pytest.mark.gpu
+
+EDGE = 16  # coefficients left out at each edge of a window
+
+
+@pytest.fixture(scope="module")
+def wf():
+    return need_gpu()
+
+
+def _cut(a, origin, n, p):
+    e0x, e0y = origin
+    N = n + p
+    return a[e0y:e0y + N, e0x:e0x + N]
+
+
+def _inner(a, n, p):
+    N = n + p
+    return a[EDGE:N - EDGE, EDGE:N - EDGE]
+
+
+def _outside_ambient(T, origin, n, p, tol):
+    e0x, e0y = origin
+    N = n + p
+    mask = np.ones(T.shape, dtype=bool)
+    mask[e0y:e0y + N, e0x:e0x + N] = False
+    return float(np.abs(T[mask] - T_AMB).max()) <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_c2_all_steps(wf, prec):
+    sc = config_c2()
+    assert sc.steps == 1000
+    ref = long_oracle.result("c2")
+    org, n = ref["origin"], ref["n"]
+    sim = wf.simulation_from_scenario(sc, precision=wf.WF_FP64 if prec == "fp64" else wf.WF_FP32)
+    done = 0
+    for snap in (150, 1000):
+        sim.step(snap - done)
+        done = snap
+        assert sim.sync() == wf.WF_OK
+        T, phi = sim.state()
+        To, po = ref[snap]
+        Tg, pg = _cut(T, org, n, sc.p), _cut(phi, org, n, sc.p)
+        assert_parity(_inner(Tg, n, sc.p), _inner(pg, n, sc.p), _inner(To, n, sc.p), _inner(po, n, sc.p), prec)
+        assert _outside_ambient(T, org, n, sc.p, 1e-9 if prec == "fp64" else 1e-3), snap
+        if snap == 150:
+            assert To.max() > 1500.0  # the fire burns inside the window
+            if prec == "fp32":
+                L = n * sc.Lx / sc.nx
+                iso_o = isotherm_elements(To, n, sc.p, L)
+                iso_g = isotherm_elements(np.array(Tg), n, sc.p, L)
+                assert len(iso_o) > 0
+                assert hausdorff_elements(iso_g, iso_o) <= 1
+    sim.close()
+
+
+def test_c4_all_steps_sampled_members(wf):
+    S = 256
+    first = config_c4(0)
+    shared = first.fuel0
+    scs = [first] + [config_c4(k, shared_fuel=shared) for k in range(1, S)]
+    assert first.steps == 2000
+    prm = wf.wf_params_default(Lx=first.Lx, Ly=first.Ly, precision=wf.WF_FP32)
+    b = wf.Batch(first.nx, first.ny, first.p, first.dt, prm, capacity=S)
+    try:
+        for k, sc in enumerate(scs):
+            b.load_scenario(k, sc)
+        wf.wf_autotune(b.h, 1)
+        done = 0
+        for snap in (100, 2000):
+            b.step(snap - done)
+            done = snap
+            assert wf.wf_sync(b.h) == wf.WF_OK
+            for name, k in (("c4_0", 0), ("c4_178", 178)):
+                ref = long_oracle.result(name)
+                org, n = ref["origin"], ref["n"]
+                T, phi = b.state(k)
+                To, po = ref[snap]
+                Tg, pg = _cut(T, org, n, 2), _cut(phi, org, n, 2)
+                assert_parity(_inner(Tg, n, 2), _inner(pg, n, 2), _inner(To, n, 2), _inner(po, n, 2), "fp32")
+                assert _outside_ambient(T, org, n, 2, 1e-3), (name, snap)
+        for k in range(S):
+            T, _ = b.state(k)
+            assert np.all(np.isfinite(T)) and np.abs(T).max() < 1e5, k
+    finally:
+        b.close()
