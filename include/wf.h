@@ -349,6 +349,18 @@ int wf_batch_activate(wf_handle* h, int slot, int on);
 #define WF_STATUS_TIMEOUT 4
 int wf_batch_status(wf_handle* h, int* status, int n);
 
+/* Step budget of a slot: it takes part in at most `steps` more steps
+ * (counted on the device at the end of each step it takes part in), then
+ * every launch skips it until a budget is set again, so that one
+ * wf_step(h, n) with n at least the largest budget advances every slot by
+ * its own count; steps < 0 removes the budget (the default: unlimited),
+ * 0 stops the slot now.  Independent of wf_batch_activate (a slot steps when
+ * it is active and its budget is not spent).  Waits for the handle's
+ * stream.  The first budget set on a handle drops its captured graphs.
+ * Errors: WF_EINVAL, WF_ECUDA.  No counterpart in the paper: it lets a
+ * server run one quantum for slots with different step counts left. */
+int wf_batch_set_budget(wf_handle* h, int slot, int steps);
+
 /* Number of slots of a handle (>= 1), or WF_EINVAL. */
 int wf_batch_capacity(const wf_handle* h);
 

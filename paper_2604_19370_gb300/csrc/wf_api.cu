@@ -105,6 +105,8 @@ struct wf_handle {
     double* diag = nullptr;    // [4] factorisation diagnostics
     double* wind64 = nullptr;  // staging of wind factors
     int* active_dev = nullptr;
+    int* budget_dev = nullptr;  // [S] step budgets (wf_batch_set_budget; -1: unlimited)
+    bool budget_on = false;     // some budget was set: the step spends them
     int* status_out = nullptr;  // [S] gathered guard flags
     Dir dx, dy;
     // slot blocks: slot-0 pointers, block stride
@@ -175,6 +177,7 @@ Batch batch(const wf_handle* h) {
     b.S = h->S;
     b.sbytes = h->sbytes;
     b.active = h->active_dev;
+    b.budget = h->budget_on ? h->budget_dev : nullptr;
     return b;
 }
 
@@ -201,6 +204,7 @@ void layout_shared(wf_handle* h, Arena& A) {
     h->gw = A.take<double>(16);
     h->diag = A.take<double>(4);
     h->active_dev = A.take<int>(h->S);
+    h->budget_dev = A.take<int>(h->S);
     h->status_out = A.take<int>(h->S);
     h->tdev = A.take<double>(1);
     const int W = 2 * h->p + 1;
@@ -642,6 +646,8 @@ void persist_args(wf_handle* h, PersistHost* ph) {
     ph->nitems = h->p_ctl ? h->p_ctl + 2 : nullptr;
     ph->ctl = h->p_ctl;
     ph->cnt = h->p_cnt;
+    ph->active = h->active_dev;
+    ph->budget = h->budget_on ? h->budget_dev : nullptr;
 }
 
 // Slots per group of the persistent order: about six groups are live at once; their fields (five
@@ -705,8 +711,12 @@ int prepare_persist(wf_handle* h) {
 }
 
 cudaError_t enqueue_step(wf_handle* h) {
+    const bool persistent = h->prm.scheme == WF_PR && use_persist(h) && h->p_ctl;
     cudaError_t e = enqueue_step_body(h);
     if (e == cudaSuccess && h->mms_on) e = launch_advance_time(h->tdev, h->dt, h->stream);
+    // step budgets: the persistent kernel spends them itself when a slot's last item ends
+    if (e == cudaSuccess && h->budget_on && !persistent)
+        e = launch_step_budget(h->active_dev, h->budget_dev, h->S, h->stream);
     return e;
 }
 
@@ -1140,8 +1150,9 @@ int wf_batch_create(int nx, int ny, int p, double dt, const wf_params* params, i
         B2.base = reinterpret_cast<char*>(h->mem) + shared;
         h->slots_mem = B2.base;
         layout_slot(h, B2);
-        // every slot block starts zeroed (fields, guard flags, unused wind ranks)
-        if (cudaMemsetAsync(B2.base, 0, (size_t)h->sbytes * capacity, h->stream) != cudaSuccess) {
+        // every slot block starts zeroed (fields, guard flags, unused wind ranks); no budgets
+        if (cudaMemsetAsync(B2.base, 0, (size_t)h->sbytes * capacity, h->stream) != cudaSuccess ||
+            cudaMemsetAsync(h->budget_dev, 0xff, sizeof(int) * capacity, h->stream) != cudaSuccess) {
             rc = WF_ECUDA;
             break;
         }
@@ -1340,6 +1351,18 @@ int wf_batch_status(wf_handle* h, int* status, int n) {
     WF_TRY(launch_gather_status(h->status, h->sbytes, h->S, h->status_out, 1, h->stream));
     WF_TRY(cudaMemcpyAsync(status, h->status_out, sizeof(int) * h->S, cudaMemcpyDeviceToHost, h->stream));
     WF_TRY(cudaStreamSynchronize(h->stream));
+    return WF_OK;
+}
+
+int wf_batch_set_budget(wf_handle* h, int slot, int steps) {
+    if (!h || slot < 0 || slot >= h->S) return WF_EINVAL;
+    const int v = steps < 0 ? -1 : steps;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;  // steps in flight spend budgets
+    WF_TRY(cudaMemcpy(h->budget_dev + slot, &v, sizeof(int), cudaMemcpyHostToDevice));
+    if (!h->budget_on) {
+        h->budget_on = true;
+        drop_graphs(h);  // every launch now reads and spends budgets
+    }
     return WF_OK;
 }
 

@@ -24,11 +24,12 @@ constexpr int kMaxRank = 4;
 // Scenario batching.  Every per-scenario pointer handed to a kernel addresses scenario 0;
 // scenario z's copy lies z * sbytes bytes further (each scenario owns one block of device
 // memory with the same internal layout).  Launches cover all S scenarios with grid.z = S;
-// a scenario whose active flag is 0 is skipped.
+// a scenario whose active flag is 0, or whose step budget is spent (0), is skipped.
 struct Batch {
     int S;
     long long sbytes;
     const int* active;  // [S] or nullptr (all active)
+    const int* budget;  // [S] step budgets (negative: unlimited) or nullptr (none)
 };
 #ifdef __CUDACC__
 template <typename T>
@@ -37,7 +38,9 @@ __device__ __forceinline__ T* scene_ptr(T* p, const Batch& b) {
                                     (long long)blockIdx.z * b.sbytes)
              : p;
 }
-__device__ __forceinline__ bool scene_active(const Batch& b) { return !b.active || b.active[blockIdx.z] != 0; }
+__device__ __forceinline__ bool scene_active(const Batch& b) {
+    return (!b.active || b.active[blockIdx.z] != 0) && (!b.budget || b.budget[blockIdx.z] != 0);
+}
 #endif
 
 // Normalised model coefficients (equation divided by rho*c_p).
@@ -115,6 +118,9 @@ cudaError_t launch_convert_batch(int dir_in, int prec, const void* host_stage, i
                                  long long sbytes, int S, int Nx, int Ny, int pitch, cudaStream_t s);
 cudaError_t launch_fill(int prec, void* dst, size_t n, double v, cudaStream_t s);
 cudaError_t launch_gather_status(int* status0, long long sbytes, int S, int* out, int clear, cudaStream_t s);
+// end of a step: every active slot with a positive budget spends one step (at zero the slot is
+// skipped by every kernel until its budget is set again)
+cudaError_t launch_step_budget(const int* active, int* budget, int S, cudaStream_t s);
 
 // ---- quadrature right-hand side (wf_rhs.cu) ---------------------------------------
 // Tables of an interior element along one direction (uniform open knots: every element
@@ -234,6 +240,8 @@ struct PersistHost {
     const int* nitems;
     int* ctl;                 // device: ticket, abort flag
     int* cnt;                 // device: nslots_cap x cstride arrival counters
+    const int* active;        // device: per-slot activity flags (an inactive slot's items are skipped)
+    int* budget;              // device: per-slot step budgets, or NULL (a spent budget, 0, skips too)
 };
 struct PersistPlan {
     int nq8, nmv8, nxg, nyg, narr1, cstride, items_per_slot, seg, xG, yG;

@@ -51,7 +51,7 @@ enum { PH_Q = 0, PH_X1 = 1, PH_Y1 = 2, PH_MV = 3, PH_X2 = 4, PH_Y2 = 5, PH_N = 6
 
 // Offsets (ints) of one slot's arrival counters.
 struct CntLayout {
-    int qseg, x1, y1col, mvseg, x2, stride;
+    int qseg, x1, y1col, mvseg, x2, done, stride;
 };
 
 template <typename P>
@@ -78,6 +78,9 @@ struct PersistArgs {
     CntLayout cl;
     long long wait_ns;
     int* status;  // slot 0's flag word (slot z: z * sbytes further)
+    const int* active;  // per-slot activity flags: an inactive slot's items are skipped
+    int* budget;        // per-slot step budgets (NULL: none); a spent one (0) skips the slot too
+    int items_per_slot;
 };
 
 template <typename T>
@@ -485,7 +488,13 @@ __global__ void __launch_bounds__(kPT, 2) k_step_persist(const __grid_constant__
         const long long off = (long long)z * A.sbytes;
         int* cnt = A.cnt + (size_t)z * A.cl.stride;
         int* slot_status = shift(A.status, off);
-        if (!s_abort) {
+        // the slot's activity (flag and unspent budget) is read when an item starts; the budget changes
+        // only after every item of the slot has finished (below), so all of a slot's items agree
+        if (tid == 0) s_dep = ld_relaxed(A.active + z) != 0 && (!A.budget || ld_relaxed(A.budget + z) != 0);
+        __syncthreads();
+        const bool live = s_dep != 0;
+        __syncthreads();  // s_dep is written again by the dependency checks below
+        if (!s_abort && live) {
             if (ph == PH_Q || ph == PH_MV) {
                 // eight independent warp tiles (d.z: the first); no barrier inside
                 const int w = d.z + warp;
@@ -551,6 +560,14 @@ __global__ void __launch_bounds__(kPT, 2) k_step_persist(const __grid_constant__
             }
         }
         __syncthreads();  // s_item, s_key and shared memory are reused by the next item
+        if (tid == 0 && live && !s_abort) {
+            // the slot's last item of the step spends one step of its budget
+            const int old = atomicAdd(cnt + A.cl.done, 1);
+            if (old == A.items_per_slot - 1 && A.budget) {
+                const int b = A.budget[z];
+                if (b > 0) A.budget[z] = b - 1;
+            }
+        }
     }
 }
 
@@ -663,7 +680,8 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     cl.y1col = cl.x1 + 2;
     cl.mvseg = cl.y1col + A.nyg;
     cl.x2 = cl.mvseg + A.mv_nsegs;
-    cl.stride = (cl.x2 + 1 + 31) & ~31;  // 128-byte blocks per slot
+    cl.done = cl.x2 + 1;
+    cl.stride = (cl.done + 1 + 31) & ~31;  // 128-byte blocks per slot
     A.cl = cl;
     size_t smem = std::max(std::max(sx1, sx2), std::max(sy1, sy2));
     smem = std::max(smem, (size_t)(kPT / 32) * A.wsm_floats * sizeof(float));
@@ -693,6 +711,9 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     A.cnt = h.cnt;
     A.wait_ns = h.wait_ns;
     A.status = h.status;
+    A.active = h.active;
+    A.budget = h.budget;
+    A.items_per_slot = plan->items_per_slot;
     // every counter of this step starts at zero (ticket, abort flag, arrival counters)
     e = cudaMemsetAsync(h.ctl, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;

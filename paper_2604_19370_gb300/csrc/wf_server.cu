@@ -1,28 +1,36 @@
 // Serving: a request loop over batch handles with continuous batching.
 //
-// Requests (one fire scenario each: grid, degree, time step, step count, model
-// parameters, initial state and wind) are grouped into classes that can share a
-// launch: same nx, ny, p, dt and parameters apart from the mean wind.  Every class
-// owns one batch handle (wf_batch_create) with its own stream.  A worker thread:
-//   1. admits queued requests into free slots of their class, creating the class's
-//      handle when the device-memory budget allows it (first come, first served);
-//   2. advances every class with active slots by one quantum of steps (the smallest
-//      remaining step count of its slots, at most kQuantum), all classes enqueued
-//      before any is waited for, so their kernels overlap on the GPU;
-//   3. retires finished slots: copies the state into the request's output arrays,
-//      frees the slot and records the latency.
-// New requests therefore join running batches at quantum boundaries, and a slot's
-// result does not depend on which other slots ran beside it (each slot is computed
+// Requests (one fire scenario each: grid, degree, time step, step count, model parameters,
+// initial state and wind) are grouped into classes that can share a launch: same nx, ny, p, dt
+// and parameters apart from the mean wind.  A class owns pools: batch handles (wf_batch_create)
+// of growing capacity, each with its own stream and event.  The worker thread never waits on
+// the GPU:
+//   - a pool is idle or runs one quantum (wf_step of at most kQuantum steps, an event recorded
+//     behind it); completion is polled with cudaEventQuery, so pools of every class run side by
+//     side on the device and a slow class delays no other;
+//   - every slot carries its request's step count as its budget (wf_batch_set_budget), so a
+//     quantum advances each slot by min(quantum, its remaining steps): a request with few steps
+//     left no longer shortens the quantum of the others;
+//   - queued requests are admitted (first come, first served) into free slots of idle pools of
+//     their class; a class with no free slot gets a new pool when the memory budget allows it,
+//     its capacity set by the class's queued demand and checked with wf_batch_bytes before
+//     anything is allocated; a class that did not fit is not retried until memory is freed;
+//   - a pool's finished slots are retired as soon as its quantum completes: the state is copied
+//     into the request's arrays, the slot freed and the latency recorded.
+// New requests therefore join running work at quantum boundaries of their own class, and a
+// slot's result does not depend on which other slots ran beside it (each slot is computed
 // independently inside every launch).
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <vector>
 
@@ -31,7 +39,7 @@
 
 namespace {
 
-constexpr int kQuantum = 25;  // steps per scheduling round
+constexpr int kQuantum = 25;  // steps per quantum of a pool
 
 using Clock = std::chrono::steady_clock;
 
@@ -52,18 +60,28 @@ struct ClassKey {
     bool operator<(const ClassKey& o) const { return memcmp(this, &o, sizeof(ClassKey)) < 0; }
 };
 
-struct Class {
-    ClassKey key;
+struct Pool {
     wf_handle* h = nullptr;
     cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
     size_t bytes = 0;
     std::vector<std::shared_ptr<Req>> slot;  // nullptr: free
-    Clock::time_point last_used;
-    int active() const {
+    bool running = false;
+    int quantum = 0;
+    int used() const {
         int n = 0;
-        for (auto& s : slot) n += s != nullptr;
+        for (auto& q : slot) n += q != nullptr;
         return n;
     }
+    int free_slot() const {
+        for (int k = 0; k < (int)slot.size(); ++k)
+            if (!slot[k]) return k;
+        return -1;
+    }
+};
+
+struct Class {
+    std::vector<std::unique_ptr<Pool>> pools;
 };
 
 ClassKey key_of(const wf_request& r) {
@@ -94,8 +112,9 @@ struct wf_server {
     std::thread worker;
     // worker-owned
     std::deque<std::shared_ptr<Req>> queue;
-    std::map<ClassKey, std::unique_ptr<Class>> classes;
-    size_t used = 0;
+    std::map<ClassKey, Class> classes;
+    std::set<ClassKey> blocked;  // classes that did not fit; retried once memory is freed
+    std::atomic<size_t> used{0};  // device bytes of every pool (read by wf_server_stats)
     // statistics
     double dof_steps = 0.0;
     uint64_t completed = 0;
@@ -114,152 +133,189 @@ void finish(wf_server* s, const std::shared_ptr<Req>& q, int status) {
     }
 }
 
-// Create a class handle sized to the free budget (capacity up to max_slots); nullptr if none fits.
-// The capacity is chosen from the handle's computed size before anything is allocated, so the
-// budget is never overshot, not even for a moment.
-std::unique_ptr<Class> make_class(wf_server* s, const ClassKey& key, const wf_request& r) {
-    for (int cap = s->max_slots; cap >= 1; cap /= 2) {
+int pow2ceil(int n) {
+    int c = 1;
+    while (c < n) c <<= 1;
+    return c;
+}
+
+// A new pool for `key` of capacity at most `want` (halved until its computed size fits the free
+// budget; nothing is allocated before it does); nullptr if not even one slot fits.
+std::unique_ptr<Pool> make_pool(wf_server* s, const wf_request& r, int want) {
+    for (int cap = std::min(want, s->max_slots); cap >= 1; cap /= 2) {
         size_t need = 0;
         if (wf_batch_bytes(r.nx, r.ny, r.p, r.dt, &r.params, cap, &need) != WF_OK) return nullptr;
         if (s->used + need > s->budget) continue;
         wf_handle* h = nullptr;
         if (wf_batch_create(r.nx, r.ny, r.p, r.dt, &r.params, cap, &h) != WF_OK) continue;
-        size_t bytes = 0;
-        wf_device_bytes(h, &bytes);
-        auto c = std::make_unique<Class>();
-        c->key = key;
-        c->h = h;
-        c->bytes = bytes;
-        c->slot.assign(cap, nullptr);
-        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) == cudaSuccess)
-            wf_set_stream(h, c->stream);
-        c->last_used = Clock::now();
-        s->used += bytes;
-        return c;
+        auto pl = std::make_unique<Pool>();
+        pl->h = h;
+        wf_device_bytes(h, &pl->bytes);
+        pl->slot.assign(cap, nullptr);
+        if (cudaStreamCreateWithFlags(&pl->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->ev, cudaEventDisableTiming) != cudaSuccess) {
+            if (pl->stream) cudaStreamDestroy(pl->stream);
+            wf_destroy(h);
+            return nullptr;
+        }
+        wf_set_stream(h, pl->stream);
+        s->used += pl->bytes;
+        return pl;
     }
     return nullptr;
 }
 
-void drop_class(wf_server* s, std::map<ClassKey, std::unique_ptr<Class>>::iterator it) {
-    Class* c = it->second.get();
-    s->used -= c->bytes;
-    wf_set_stream(c->h, nullptr);
-    wf_destroy(c->h);
-    if (c->stream) cudaStreamDestroy(c->stream);
-    s->classes.erase(it);
+void drop_pool(wf_server* s, std::unique_ptr<Pool>& pl) {
+    s->used -= pl->bytes;
+    wf_set_stream(pl->h, nullptr);
+    wf_destroy(pl->h);
+    if (pl->ev) cudaEventDestroy(pl->ev);
+    if (pl->stream) cudaStreamDestroy(pl->stream);
+    pl.reset();
+    s->blocked.clear();  // memory was freed: classes that did not fit may now
 }
 
-// Admit queued requests (in arrival order) into free slots.
-void admit(wf_server* s) {
+// Drop every idle, empty pool (of any class); true if one was dropped.
+bool drop_idle_pools(wf_server* s) {
+    bool any = false;
+    for (auto& kv : s->classes) {
+        auto& v = kv.second.pools;
+        for (auto& pl : v)
+            if (pl && !pl->running && pl->used() == 0) {
+                drop_pool(s, pl);
+                any = true;
+            }
+        v.erase(std::remove(v.begin(), v.end(), nullptr), v.end());
+    }
+    return any;
+}
+
+bool any_pool(const wf_server* s) {
+    for (auto& kv : s->classes)
+        if (!kv.second.pools.empty()) return true;
+    return false;
+}
+
+// Put request q into slot k of the idle pool pl.
+int place(Pool* pl, int k, const std::shared_ptr<Req>& q) {
+    int rc = wf_batch_set_slot(pl->h, k, q->T0.data(), q->fuel0.data(), q->r.params.wind_x, q->r.params.wind_y,
+                               q->r.wind_rank, q->r.wind_rank > 0 ? q->wind.data() : nullptr);
+    if (rc == WF_OK) rc = wf_batch_set_budget(pl->h, k, q->r.steps);
+    if (rc == WF_OK) rc = wf_batch_activate(pl->h, k, 1);
+    if (rc != WF_OK) return rc;
+    pl->slot[k] = q;
+    q->t_admit = Clock::now();
+    return WF_OK;
+}
+
+// Admit queued requests in arrival order into free slots of idle pools; true if any was.
+bool admit(wf_server* s) {
+    bool progress = false;
+    std::map<ClassKey, int> demand;  // queued requests per class
+    for (auto& q : s->queue) demand[key_of(q->r)] += 1;
     for (auto it = s->queue.begin(); it != s->queue.end();) {
         std::shared_ptr<Req> q = *it;
         const ClassKey key = key_of(q->r);
-        auto ci = s->classes.find(key);
-        if (ci == s->classes.end()) {
-            auto c = make_class(s, key, q->r);
-            if (!c) {
-                // free idle classes of other shapes, then retry once
-                for (auto jt = s->classes.begin(); jt != s->classes.end();) {
-                    auto nx = std::next(jt);
-                    if (jt->second->active() == 0) drop_class(s, jt);
-                    jt = nx;
-                }
-                c = make_class(s, key, q->r);
-            }
-            if (!c) {
-                if (s->classes.empty()) {  // nothing else holds memory: the request can never fit
-                    finish(s, q, WF_ENOMEM);
-                    it = s->queue.erase(it);
-                    continue;
-                }
-                ++it;  // wait for running classes to drain
-                continue;
-            }
-            ci = s->classes.emplace(key, std::move(c)).first;
-        }
-        Class* c = ci->second.get();
-        int slot = -1;
-        for (int k = 0; k < (int)c->slot.size(); ++k)
-            if (!c->slot[k]) {
-                slot = k;
+        Class& c = s->classes[key];
+        Pool* target = nullptr;
+        int k = -1;
+        bool any_free = false;
+        for (auto& pl : c.pools) {
+            const int f = pl->free_slot();
+            if (f < 0) continue;
+            any_free = true;
+            if (!pl->running) {
+                target = pl.get();
+                k = f;
                 break;
             }
-        if (slot < 0) {
-            ++it;
+        }
+        if (!target && !any_free && !s->blocked.count(key)) {
+            // no free slot in the class: a new pool sized by the class's queued demand
+            auto pl = make_pool(s, q->r, pow2ceil(std::max(1, demand[key])));
+            if (!pl && drop_idle_pools(s)) pl = make_pool(s, q->r, pow2ceil(std::max(1, demand[key])));
+            if (pl) {
+                c.pools.push_back(std::move(pl));
+                target = c.pools.back().get();
+                k = 0;
+            } else if (!any_pool(s)) {
+                // nothing else holds memory: the request can never fit
+                finish(s, q, WF_ENOMEM);
+                demand[key] -= 1;
+                it = s->queue.erase(it);
+                progress = true;
+                continue;
+            } else {
+                s->blocked.insert(key);
+            }
+        }
+        if (!target) {
+            ++it;  // waits for a slot of its class (or for memory)
             continue;
         }
-        const int rc = wf_batch_set_slot(c->h, slot, q->T0.data(), q->fuel0.data(), q->r.params.wind_x,
-                                         q->r.params.wind_y, q->r.wind_rank,
-                                         q->r.wind_rank > 0 ? q->wind.data() : nullptr);
-        if (rc != WF_OK) {
-            finish(s, q, rc);
-            it = s->queue.erase(it);
-            continue;
-        }
-        wf_batch_activate(c->h, slot, 1);
-        c->slot[slot] = q;
-        c->last_used = Clock::now();
-        q->t_admit = Clock::now();
+        const int rc = place(target, k, q);
+        if (rc != WF_OK) finish(s, q, rc);
+        demand[key] -= 1;
         it = s->queue.erase(it);
+        progress = true;
+    }
+    return progress;
+}
+
+// A pool's quantum completed: read the slots' flags, retire the finished slots.
+void complete(wf_server* s, Pool* pl) {
+    pl->running = false;
+    std::vector<int> st(pl->slot.size(), 0);
+    const int rc = wf_batch_status(pl->h, st.data(), (int)st.size());
+    bool timeout = false;
+    for (int v : st) timeout = timeout || (v & WF_STATUS_TIMEOUT);
+    for (int k = 0; k < (int)pl->slot.size(); ++k) {
+        std::shared_ptr<Req> q = pl->slot[k];
+        if (!q) continue;
+        bool release = true;
+        if (rc != WF_OK) {
+            finish(s, q, WF_ECUDA);
+        } else if (timeout) {
+            finish(s, q, WF_ETIMEOUT);  // the launch's output is invalid for every slot
+        } else if (st[k] & WF_STATUS_UNSTABLE) {
+            finish(s, q, WF_EUNSTABLE);
+        } else {
+            q->remaining -= std::min(pl->quantum, q->remaining);
+            if (q->remaining <= 0)
+                finish(s, q, wf_batch_get_slot(pl->h, k, q->r.T_out, q->r.fuel_out));
+            else
+                release = false;
+        }
+        if (release) {
+            wf_batch_activate(pl->h, k, 0);
+            pl->slot[k] = nullptr;
+        }
     }
 }
 
-// One scheduling round over every class with active slots.
-void run_round(wf_server* s) {
-    std::vector<std::pair<Class*, int>> stepped;
-    for (auto& kv : s->classes) {
-        Class* c = kv.second.get();
-        int quantum = kQuantum;
-        bool any = false;
-        for (auto& q : c->slot)
-            if (q) {
-                quantum = std::min(quantum, q->remaining);
-                any = true;
-            }
-        if (!any) continue;
-        if (quantum > 0 && wf_step(c->h, quantum) == WF_OK) stepped.push_back({c, quantum});
-        else stepped.push_back({c, -1});
-    }
-    for (auto& cs : stepped) {
-        Class* c = cs.first;
-        const int n = cs.second;
-        std::vector<int> st(c->slot.size(), 0);
-        const int rc = wf_batch_status(c->h, st.data(), (int)st.size());  // waits for the class's stream
-        for (int k = 0; k < (int)c->slot.size(); ++k) {
-            std::shared_ptr<Req> q = c->slot[k];
-            if (!q) continue;
-            bool release = false;
-            if (n < 0 || rc != WF_OK) {
-                finish(s, q, WF_ECUDA);
-                release = true;
-            } else if (st[k]) {
-                finish(s, q, WF_EUNSTABLE);
-                release = true;
-            } else {
-                q->remaining -= n;
-                if (q->remaining <= 0) {
-                    const int g = wf_batch_get_slot(c->h, k, q->r.T_out, q->r.fuel_out);
-                    finish(s, q, g);
-                    release = true;
-                }
-            }
-            if (release) {
-                wf_batch_activate(c->h, k, 0);
-                c->slot[k] = nullptr;
-            }
-        }
-        c->last_used = Clock::now();
-    }
+// Start the next quantum of an idle pool with work; every slot runs its own budget.
+// 1: started, 0: nothing to run, -1: the launch failed.
+int launch(Pool* pl) {
+    int most = 0;
+    for (auto& q : pl->slot)
+        if (q) most = std::max(most, q->remaining);
+    if (most <= 0) return 0;
+    const int n = std::min(kQuantum, most);
+    if (wf_step(pl->h, n) != WF_OK || cudaEventRecord(pl->ev, pl->stream) != cudaSuccess) return -1;
+    pl->quantum = n;
+    pl->running = true;
+    return 1;
 }
 
 void worker_main(wf_server* s) {
     cudaSetDevice(s->device);
     for (;;) {
+        bool busy = false;
+        for (auto& kv : s->classes)
+            for (auto& pl : kv.second.pools) busy = busy || pl->running;
         {
             std::unique_lock<std::mutex> lock(s->mu);
-            bool idle = s->queue.empty();
-            for (auto& kv : s->classes) idle = idle && kv.second->active() == 0;
-            if (idle && s->incoming.empty() && !s->stop)
+            if (!busy && s->queue.empty() && s->incoming.empty() && !s->stop)
                 s->cv.wait_for(lock, std::chrono::milliseconds(50));
             if (s->stop) break;
             while (!s->incoming.empty()) {
@@ -267,17 +323,45 @@ void worker_main(wf_server* s) {
                 s->incoming.pop_front();
             }
         }
-        const size_t before = s->queue.size();
-        admit(s);
-        bool any_active = false;
-        for (auto& kv : s->classes) any_active = any_active || kv.second->active() > 0;
-        if (any_active)
-            run_round(s);
-        else if (!s->queue.empty() && s->queue.size() == before)
-            std::this_thread::sleep_for(std::chrono::milliseconds(1));  // waiting for memory to free up
+        bool progress = false;
+        // 1. quanta that completed
+        for (auto& kv : s->classes)
+            for (auto& pl : kv.second.pools) {
+                if (!pl->running) continue;
+                const cudaError_t e = cudaEventQuery(pl->ev);
+                if (e == cudaErrorNotReady) continue;
+                if (e != cudaSuccess) cudaGetLastError();
+                complete(s, pl.get());
+                progress = true;
+            }
+        // 2. admissions into idle pools
+        progress = admit(s) || progress;
+        // 3. the next quantum of every idle pool with work
+        for (auto& kv : s->classes)
+            for (auto& pl : kv.second.pools) {
+                if (pl->running || pl->used() == 0) continue;
+                const int lr = launch(pl.get());
+                if (lr > 0) {
+                    progress = true;
+                } else if (lr < 0) {
+                    // the launch failed: fail the pool's requests
+                    for (int k = 0; k < (int)pl->slot.size(); ++k)
+                        if (pl->slot[k]) {
+                            finish(s, pl->slot[k], WF_ECUDA);
+                            wf_batch_activate(pl->h, k, 0);
+                            pl->slot[k] = nullptr;
+                        }
+                }
+            }
+        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
-    // shut down: drop every class
-    while (!s->classes.empty()) drop_class(s, s->classes.begin());
+    // shut down: wait for the device, drop every pool
+    for (auto& kv : s->classes)
+        for (auto& pl : kv.second.pools) {
+            if (pl->running) cudaEventSynchronize(pl->ev);
+            drop_pool(s, pl);
+        }
+    s->classes.clear();
 }
 
 }  // namespace

@@ -381,6 +381,15 @@ __global__ void k_gather_status(int* status0, long long sbytes, int S, int* out,
     if (clear) st[0] = 0;
 }
 
+// Per-slot step budgets (end of a step): an active slot with a positive budget spends one step of
+// it; at zero the slot is skipped until its budget is set again; a negative budget is unlimited.
+__global__ void k_step_budget(const int* active, int* budget, int S) {
+    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= S || !active[z]) return;
+    const int b = budget[z];
+    if (b > 0) budget[z] = b - 1;
+}
+
 template <typename P>
 __global__ void k_fill(P* dst, size_t n, P v) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -490,6 +499,12 @@ cudaError_t launch_convert_out(int prec, const void* src, void* dst, int host32,
 
 cudaError_t launch_gather_status(int* status0, long long sbytes, int S, int* out, int clear, cudaStream_t s) {
     k_gather_status<<<blocks(S, 128), 128, 0, s>>>(status0, sbytes, S, out, clear);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_budget(const int* active, int* budget, int S, cudaStream_t s) {
+    k_step_budget<<<blocks(S, 128), 128, 0, s>>>(active, budget, S);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -112,6 +112,7 @@ def lib() -> ctypes.CDLL:
         L.wf_batch_set_slot.argtypes = [vp, i, dp, dp, d, d, i, dp]
         L.wf_batch_get_slot.argtypes = [vp, i, dp, dp]
         L.wf_batch_activate.argtypes = [vp, i, i]
+        L.wf_batch_set_budget.argtypes = [vp, i, i]
         L.wf_batch_status.argtypes = [vp, ctypes.POINTER(i), i]
         L.wf_batch_capacity.argtypes = [vp]
         L.wf_device_bytes.argtypes = [vp, ctypes.POINTER(sz)]
@@ -375,6 +376,10 @@ def wf_batch_get_slot(h, slot: int) -> Tuple[np.ndarray, np.ndarray]:
 
 def wf_batch_activate(h, slot: int, on: bool) -> None:
     _check(lib().wf_batch_activate(h, slot, 1 if on else 0), "wf_batch_activate")
+
+
+def wf_batch_set_budget(h, slot: int, steps: int) -> None:
+    _check(lib().wf_batch_set_budget(h, slot, steps), "wf_batch_set_budget")
 
 
 def wf_batch_status(h) -> np.ndarray:

@@ -83,3 +83,58 @@ def test_server_zero_steps_and_bad_requests(wf):
             r = srv.poll(t)
             time.sleep(0.01)
         assert r is not None and r[0] == wf.WF_ENOMEM
+
+
+def test_served_results_against_oracle(wf):
+    # a sample of served requests, FP32 and FP64, checked element by element against the oracle
+    from gpu_helpers import assert_parity, oracle_run
+
+    reqs = [(make_scenario("so0", 48, 2, 1e-3, 17, 801, wind=(1.0, -0.5), fuel_sigma=3.0), "fp32"),
+            (make_scenario("so1", 48, 2, 1e-3, 9, 802, wind=(-2.0, 0.7), fuel_sigma=3.0), "fp32"),
+            (make_scenario("so2", 36, 2, 1e-3, 11, 803, wind=(0.4, 1.9), fuel_sigma=3.0), "fp64"),
+            (make_scenario("so3", 30, 3, 1e-3, 6, 804, wind=(0.0, 0.0), fuel_sigma=3.0), "fp64")]
+    code = {"fp32": wf.WF_FP32, "fp64": wf.WF_FP64}
+    out = {}
+    with wf.Server(1 << 30, max_slots=4) as srv:
+        tickets = {srv.submit(sc, precision=code[prec]): i for i, (sc, prec) in enumerate(reqs)}
+        t0 = time.time()
+        while tickets and time.time() - t0 < 120:
+            for t in list(tickets):
+                r = srv.poll(t)
+                if r is not None:
+                    out[tickets.pop(t)] = r
+            time.sleep(0.002)
+        assert not tickets
+    for i, (sc, prec) in enumerate(reqs):
+        st, res, T, phi = out[i]
+        assert st == wf.WF_OK
+        To, po = oracle_run(sc, sc.steps)
+        assert_parity(T, phi, To, po, prec, rel_bar=1e-10 if prec == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_step_budgets_give_each_slot_its_own_count(wf, form):
+    # one wf_step(n) with per-slot budgets advances each slot by min(n, its budget); in both step
+    # forms; a slot re-armed afterwards continues from where it stopped
+    scs = [make_scenario(f"bg{i}", 64, 2, 1e-3, 1, 820 + i, wind=((1.0, 0.5), (0.0, -1.0), (2.0, 2.0))[i],
+                         fuel_sigma=3.0) for i in range(3)]
+    counts = [3, 8, 5]
+    prm = wf.wf_params_default(Lx=scs[0].Lx, Ly=scs[0].Ly, wind_x=1.0, wind_y=0.5, precision=wf.WF_FP32)
+    b = wf.Batch(64, 64, 2, 1e-3, prm, capacity=3)
+    wf.wf_set_tuning(b.h, (0, 0, 0, 0, 0, 0, form, 0))
+    for i, sc in enumerate(scs):
+        b.load_scenario(i, sc)
+        wf.wf_batch_set_budget(b.h, i, counts[i])
+    b.step(10)
+    assert wf.wf_sync(b.h) == wf.WF_OK
+    got = [b.state(i) for i in range(3)]
+    wf.wf_batch_set_budget(b.h, 0, 2)
+    wf.wf_batch_activate(b.h, 0, True)
+    b.step(4)
+    T0b, _ = b.state(0)
+    b.close()
+    for i, sc in enumerate(scs):
+        T, phi = gpu_run(wf, sc, counts[i], wf.WF_FP32)
+        assert np.array_equal(got[i][0], T) and np.array_equal(got[i][1], phi), i
+    T, _ = gpu_run(wf, scs[0], counts[0] + 2, wf.WF_FP32)
+    assert np.array_equal(T0b, T)
