@@ -721,7 +721,7 @@ def run_serving(args, wf=None, as_extra: bool = False):
     def run(reqs, rate):
         srv = wf.Server(budget, max_slots=args.max_slots)
         prepared = [(scenario(r), r) for r in reqs]
-        tickets, lat, dof_steps, fails = {}, [], 0.0, 0
+        tickets, lat, dof_steps, fails = {}, [], 0.0, {}
         t_start = time.perf_counter()
         pending = list(prepared)
         while pending or tickets:
@@ -738,7 +738,7 @@ def run_serving(args, wf=None, as_extra: bool = False):
                         lat.append(out[1].latency_s)
                         dof_steps += sc.dofs * sc.steps
                     else:
-                        fails += 1
+                        fails[wf.wf_strerror(out[0])] = fails.get(wf.wf_strerror(out[0]), 0) + 1
             time.sleep(0.0005)
         makespan = time.perf_counter() - t_start
         srv.close()
@@ -756,7 +756,7 @@ def run_serving(args, wf=None, as_extra: bool = False):
            "capacity_rps": capacity, "sizes": [128, 256, 512, 1024], "p": [2, 3], "steps": "U[200,2000]",
            "fp64_share": 0.2, "hbm_budget_bytes": budget, "max_slots_per_class": args.max_slots,
            "latency_p50_s": _percentile(lat, 0.5), "latency_p99_s": _percentile(lat, 0.99),
-           "completed": len(lat), "failed": fails, "value": ds / span, "unit": UNIT,
+           "completed": len(lat), "failed": sum(fails.values()), "failures": fails, "value": ds / span, "unit": UNIT,
            "closed_loop_dof_steps_per_s": ds_c / span_c}
     if as_extra:
         return res
@@ -767,7 +767,8 @@ def run_serving(args, wf=None, as_extra: bool = False):
         "config": {k: v for k, v in res.items() if k not in ("value", "unit", "latency_p50_s", "latency_p99_s",
                                                               "completed", "failed", "closed_loop_dof_steps_per_s")},
         "latency_p50_s": res["latency_p50_s"], "latency_p99_s": res["latency_p99_s"],
-        "completed": res["completed"], "failed": fails, "closed_loop_dof_steps_per_s": res["closed_loop_dof_steps_per_s"],
+        "completed": res["completed"], "failed": res["failed"], "failures": fails,
+        "closed_loop_dof_steps_per_s": res["closed_loop_dof_steps_per_s"],
     }
     print(json.dumps(line), flush=True)
     return res
