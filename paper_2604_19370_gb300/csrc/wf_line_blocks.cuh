@@ -380,11 +380,12 @@ __device__ __forceinline__ void interface_solve(const Chunks& ch, int k, int mma
 
 // Compact factors (global, [3][mmax][2p+1], [3][mmax][2p], [3][p*p]) into the padded
 // shared-memory layout of FacSmem; padding entries are zero.
+// (threads tid of nt stage the factors; the CTA's threads by default)
 template <typename P, int PD>
-__device__ __forceinline__ void stage_factors(const LineView<P>& v, int mmax, const FacSmem<P, PD>& fm) {
+__device__ __forceinline__ void stage_factors(const LineView<P>& v, int mmax, const FacSmem<P, PD>& fm, int tid,
+                                              int nt) {
     constexpr int W = 2 * PD + 1, S2 = 2 * PD;
     constexpr int NF = FacW<PD>::F, NU = FacW<PD>::U, NS = FacW<PD>::S;
-    const int nt = blockDim.x, tid = threadIdx.x;
     const P* __restrict__ g1 = v.luc;
     const P* __restrict__ g2 = v.spkc;
     const P* __restrict__ g3 = v.Ec;
@@ -402,6 +403,10 @@ __device__ __forceinline__ void stage_factors(const LineView<P>& v, int mmax, co
         fm.S[i] = c < S2 ? g2[r * S2 + c] : P(0);
     }
     for (int i = tid; i < 3 * PD * PD; i += nt) fm.E[i] = g3[i];
+}
+template <typename P, int PD>
+__device__ __forceinline__ void stage_factors(const LineView<P>& v, int mmax, const FacSmem<P, PD>& fm) {
+    stage_factors<P, PD>(v, mmax, fm, threadIdx.x, blockDim.x);
 }
 
 }  // namespace

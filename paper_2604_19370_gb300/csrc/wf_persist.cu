@@ -45,7 +45,9 @@ namespace wf {
 
 namespace {
 
-constexpr int kPT = 256;  // threads per CTA of the persistent kernel
+constexpr int kAW = 8;                 // A warps per CTA: quadrature and matvec warp tiles
+constexpr int kBT = 256;               // B threads per CTA: x and y line tiles (named barrier 1)
+constexpr int kPT = kAW * 32 + kBT;    // threads per CTA (one CTA per SM)
 
 enum { PH_Q = 0, PH_X1 = 1, PH_Y1 = 2, PH_MV = 3, PH_X2 = 4, PH_Y2 = 5, PH_N = 6 };
 
@@ -71,9 +73,12 @@ struct PersistArgs {
     int nxg, nyg;  // row groups of the x passes, column groups of the y passes
     int vec;       // rows 16-byte aligned: stage x lines with 16-byte loads
     int wsm_floats;  // per-warp shared memory of the quadrature (wind factors)
-    const int4* items;
-    const int* nitems;
-    int* ctl;  // [0] ticket, [1] abort flag
+    int bsmem;       // bytes of the B threads' shared memory (the A warps' follows)
+    const int4* itemsA;  // stream A: quadrature and matvec warp tiles
+    const int4* itemsB;  // stream B: x and y line tiles
+    const int* nA;
+    const int* nB;
+    int* ctl;  // [0] ticket of stream A, [1] abort flag, [2] ticket of stream B
     int* cnt;  // slot z's counters at cnt + z * cl.stride
     CntLayout cl;
     long long wait_ns;
@@ -143,6 +148,9 @@ __device__ bool wait_count(const PersistArgs<P>& A, const int* c, int target, in
     return false;
 }
 
+// barrier of the B threads (the x and y line tiles); the A warps never take part
+__device__ __forceinline__ void bsync() { asm volatile("bar.sync 1, %0;" ::"n"(kBT) : "memory"); }
+
 __device__ __forceinline__ void arrive(int* c) {
     __threadfence();
     atomicAdd(c, 1);
@@ -208,8 +216,8 @@ __device__ __forceinline__ int q_seg_of(const StreamArgs<P>& q, int r) {
 // shared memory are not those of this (slot, operator).
 template <typename P, int PD>
 __device__ void x_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int arr, int j0, unsigned char* smem,
-                       bool restage) {
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x;
+                       bool restage, int tid, int nt) {
+    const int warp = tid >> 5, lane = tid & 31;
     const Chunks ch = a.ch;
     const int N = ch.N, C = ch.C, base = ch.base, G = a.G;
     const int mmax = base + 2 * PD;
@@ -233,8 +241,8 @@ __device__ void x_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int
             rowbuf[(size_t)r * sp + x] = __ldcg(v.in + (size_t)(j0 + r) * pitch + x);
         }
     }
-    if (restage) stage_factors<P, PD>(v, mmax, fm);
-    __syncthreads();
+    if (restage) stage_factors<P, PD>(v, mmax, fm, tid, nt);
+    bsync();
     const int k = lane & ((1 << a.lsh) - 1);
     const int r = (warp << (5 - a.lsh)) + (lane >> a.lsh);
     const bool active = r < rows && k < C;
@@ -260,7 +268,7 @@ __device__ void x_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int
     P tn[PD], bp[PD];
     interface_solve<P, PD>(ch, k < C ? k : 0, mmax, fm.S, fm.E, top, bot, nxt_top, prv_bot, tn, bp);
     if (active) spike_fix<P, PD>(g, m, fm.S + t * mmax * FacW<PD>::S, tn, bp);
-    __syncthreads();
+    bsync();
     if (sizeof(P) == 4 && A.vec) {
         const int n4 = (N + 3) >> 2;
         for (int i = tid; i < rows * n4; i += nt) {
@@ -279,10 +287,9 @@ __device__ void x_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int
 // ---- y-line tile (G columns x C chunks of threads): the operations of k_ysolve_cols ----------
 template <typename P, int PD, int B>
 __device__ void y_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int arr, int cg, unsigned char* smem,
-                       bool restage) {
+                       bool restage, int tid, int nt) {
     constexpr int B2 = 8;
     constexpr int NF = FacW<PD>::F, NU = FacW<PD>::U, NS = FacW<PD>::S;
-    const int tid = threadIdx.x;
     const Chunks ch = a.ch;
     const int C = ch.C, base = ch.base, G = a.G, mpad = a.mpad;
     const int mmax = base + 2 * PD;
@@ -300,8 +307,8 @@ __device__ void y_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int
     const LineView<P> v = line_at(a, arr, off);
     const size_t pitch = (size_t)a.pitch;
     P* g = buf + (size_t)(thr ? tid : 0) * mpad;
-    if (restage) stage_factors<P, PD>(v, mmax, fm);
-    __syncthreads();
+    if (restage) stage_factors<P, PD>(v, mmax, fm, tid, nt);
+    bsync();
     if (thr) {
         const P* Fk = fm.F + t * mmax * NF;
         P prev[PD];
@@ -326,7 +333,7 @@ __device__ void y_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int
         }
         lu_backward<P, PD>(g, m, fm.U + t * mmax * NU);
     }
-    __syncthreads();
+    bsync();
     if (!valid) return;  // no barrier follows in this tile
     const P* gn = buf + (size_t)((k + 1 < C ? k + 1 : k) * G + c) * mpad;
     const P* gp = buf + (size_t)((k > 0 ? k - 1 : k) * G + c) * mpad + (base - PD);
@@ -461,114 +468,157 @@ struct MvRows {
 };
 
 // ---- the kernel ----------------------------------------------------------------------------
+// One CTA of kAW + kBT / 32 warps per SM.  The first kAW warps ("A") each claim single
+// quadrature or matvec warp tiles from stream A, without any CTA barrier; the other kBT threads
+// ("B", synchronised by named barrier 1) claim x and y line tiles from stream B.  The two streams
+// are subsequences of one dependency-respecting order (the wavefront), so the launch makes
+// progress; inside every SM the ALU-heavy quadrature of one group of slots runs beside the
+// memory-bound line passes of older groups.
+
+// a slot takes part in this step: active and its step budget not spent
+template <typename P>
+__device__ __forceinline__ bool slot_live(const PersistArgs<P>& A, int z) {
+    return ld_relaxed(A.active + z) != 0 && (!A.budget || ld_relaxed(A.budget + z) != 0);
+}
+
+// an item of slot z finished; the slot's last item of the step spends one step of its budget
+// (every item of the slot has then started, so all of them saw the same budget)
+template <typename P>
+__device__ __forceinline__ void slot_done(const PersistArgs<P>& A, int* cnt, int z) {
+    const int old = atomicAdd(cnt + A.cl.done, 1);
+    if (old == A.items_per_slot - 1 && A.budget) {
+        const int b = A.budget[z];
+        if (b > 0) A.budget[z] = b - 1;
+    }
+}
+
 template <int PD, int WR>
-__global__ void __launch_bounds__(kPT, 2) k_step_persist(const __grid_constant__ PersistArgs<float> A) {
+__device__ void a_loop(const PersistArgs<float>& A, int lane, float* wsm) {
     using P = float;
     constexpr int RS = MvRows<PD>::value;
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ int s_item, s_abort, s_key, s_dep;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nitems = *A.nitems;
+    const int n = *A.nA;
+    int next = 0;
+    if (lane == 0) next = atomicAdd(A.ctl + 0, 1);
+    next = __shfl_sync(0xffffffffu, next, 0);
+    for (;;) {
+        const int it = next;
+        if (it >= n) break;
+        int go = 0;
+        const int4 d = A.itemsA[it];
+        const int z = d.y, w = d.z;
+        int* cnt = A.cnt + (size_t)z * A.cl.stride;
+        int* slot_status = shift(A.status, (long long)z * A.sbytes);
+        if (lane == 0) {
+            next = atomicAdd(A.ctl + 0, 1);  // fetched while this tile runs
+            go = (!ld_relaxed(A.ctl + 1) ? 1 : 0) | (slot_live(A, z) ? 2 : 0);
+        }
+        next = __shfl_sync(0xffffffffu, next, 0);
+        go = __shfl_sync(0xffffffffu, go, 0);
+        if (!(go & 2)) continue;  // the slot does not take part (no count)
+        if (go & 1) {
+            if (d.x == PH_Q) {
+                q_tile<PD, WR>(A, z, w, wsm);
+                __syncwarp();
+                if (lane == 0) arrive(cnt + A.cl.qseg + w / A.q.nstrips);
+            } else {
+                // columns (with halo) of this strip: wait for the Y1 column groups covering them
+                const int st = w % A.mv_nstrips;
+                const int xlo = max(0, st * (32 - 2 * PD) - PD), xhi = min(A.Nx - 1, st * (32 - 2 * PD) - PD + 31);
+                int ok = 1;
+                if (lane == 0)
+                    for (int gq = xlo / A.y1.G; gq <= xhi / A.y1.G && ok; ++gq)
+                        ok = wait_count(A, cnt + A.cl.y1col + gq, 1, slot_status) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                __syncwarp();  // orders the other lanes' loads after lane 0's acquire
+                if (ok) {
+                    mv_tile<P, PD, RS>(A, z, w);
+                    __syncwarp();
+                    if (lane == 0) arrive(cnt + A.cl.mvseg + w / A.mv_nstrips);
+                }
+            }
+        }
+        if (lane == 0) slot_done(A, cnt, z);
+    }
+}
+
+template <int PD>
+__device__ void b_loop(const PersistArgs<float>& A, int tid, unsigned char* smem, int* sh) {
+    using P = float;
+    constexpr int RS = MvRows<PD>::value;
+    int& s_item = sh[0];
+    int& s_live = sh[1];
+    int& s_dep = sh[2];
+    int& s_key = sh[3];
+    const int n = *A.nB;
     int next = 0;
     if (tid == 0) {
-        next = atomicAdd(A.ctl, 1);
+        next = atomicAdd(A.ctl + 2, 1);
         s_key = -1;
     }
     for (;;) {
         if (tid == 0) {
             s_item = next;
-            if (next < nitems) next = atomicAdd(A.ctl, 1);  // fetched while this item runs
-            s_abort = ld_relaxed(A.ctl + 1);
+            if (next < n) next = atomicAdd(A.ctl + 2, 1);  // fetched while this tile runs
         }
-        __syncthreads();
+        bsync();
         const int it = s_item;
-        if (it >= nitems) break;
-        const int4 d = A.items[it];
-        const int ph = d.x, z = d.y;
-        const long long off = (long long)z * A.sbytes;
+        if (it >= n) break;
+        const int4 d = A.itemsB[it];
+        const int ph = d.x, z = d.y, arr = d.z, tile = d.w;
         int* cnt = A.cnt + (size_t)z * A.cl.stride;
-        int* slot_status = shift(A.status, off);
-        // the slot's activity (flag and unspent budget) is read when an item starts; the budget changes
-        // only after every item of the slot has finished (below), so all of a slot's items agree
-        if (tid == 0) s_dep = ld_relaxed(A.active + z) != 0 && (!A.budget || ld_relaxed(A.budget + z) != 0);
-        __syncthreads();
-        const bool live = s_dep != 0;
-        __syncthreads();  // s_dep is written again by the dependency checks below
-        if (!s_abort && live) {
-            if (ph == PH_Q || ph == PH_MV) {
-                // eight independent warp tiles (d.z: the first); no barrier inside
-                const int w = d.z + warp;
-                if (ph == PH_Q) {
-                    if (w < A.nq) {
-                        q_tile<PD, WR>(A, z, w, reinterpret_cast<float*>(smem) + (size_t)warp * A.wsm_floats);
-                        __syncwarp();
-                        if (lane == 0) arrive(cnt + A.cl.qseg + w / A.q.nstrips);
+        int* slot_status = shift(A.status, (long long)z * A.sbytes);
+        const FastArgs<P>& a = ph == PH_X1 ? A.x1 : (ph == PH_Y1 ? A.y1 : (ph == PH_X2 ? A.x2 : A.y2));
+        if (tid == 0) {
+            const bool live = slot_live(A, z);
+            bool ok = live && !ld_relaxed(A.ctl + 1);
+            if (ok) {
+                if (ph == PH_X1 || ph == PH_X2) {
+                    const int j0 = tile * a.G, j1 = min(a.nlines, j0 + a.G) - 1;
+                    if (ph == PH_X1) {
+                        for (int s = q_seg_of<P, PD>(A.q, j0); s <= q_seg_of<P, PD>(A.q, j1) && ok; ++s)
+                            ok = wait_count(A, cnt + A.cl.qseg + s, A.q.nstrips, slot_status);
+                    } else {
+                        for (int s = j0 / RS; s <= j1 / RS && ok; ++s)
+                            ok = wait_count(A, cnt + A.cl.mvseg + s, A.mv_nstrips, slot_status);
                     }
-                } else if (w < A.mv_nstrips * A.mv_nsegs) {
-                    // columns (with halo) of this strip: wait for the Y1 column groups covering them
-                    const int st = w % A.mv_nstrips;
-                    const int xlo = max(0, st * (32 - 2 * PD) - PD), xhi = min(A.Nx - 1, st * (32 - 2 * PD) - PD + 31);
-                    bool ok = true;
-                    if (lane == 0)
-                        for (int gq = xlo / A.y1.G; gq <= xhi / A.y1.G && ok; ++gq)
-                            ok = wait_count(A, cnt + A.cl.y1col + gq, 1, slot_status);
-                    ok = __shfl_sync(0xffffffffu, ok, 0);
-                    if (ok) {
-                        mv_tile<P, PD, RS>(A, z, w);
-                        __syncwarp();
-                        if (lane == 0) arrive(cnt + A.cl.mvseg + w / A.mv_nstrips);
-                    }
+                } else if (ph == PH_Y1) {
+                    ok = wait_count(A, cnt + A.cl.x1 + arr, A.nxg, slot_status);
+                } else {
+                    ok = wait_count(A, cnt + A.cl.x2, A.nxg, slot_status);
                 }
-                if (tid == 0) s_key = -1;  // the quadrature's wind rows overwrite the staged factors
+            }
+            s_live = live ? 1 : 0;
+            s_dep = ok ? 1 : 0;
+        }
+        const int key = (z << 4) | (ph << 1) | arr;  // ph <= 5: bits 1..3
+        const bool restage = s_key != key;          // read before thread 0 updates it below
+        bsync();
+        if (s_dep) {
+            if (ph == PH_X1 || ph == PH_X2) {
+                x_tile<P, PD>(A, a, z, arr, tile * a.G, smem, restage, tid, kBT);
+                bsync();
+                if (tid == 0) arrive(cnt + (ph == PH_X1 ? A.cl.x1 + arr : A.cl.x2));
             } else {
-                const int arr = d.z, tile = d.w;
-                const FastArgs<P>& a = ph == PH_X1 ? A.x1 : (ph == PH_Y1 ? A.y1 : (ph == PH_X2 ? A.x2 : A.y2));
-                // dependencies, checked by thread 0 for the whole CTA
-                if (tid == 0) {
-                    bool ok = true;
-                    if (ph == PH_X1 || ph == PH_X2) {
-                        const int j0 = tile * a.G, j1 = min(a.nlines, j0 + a.G) - 1;
-                        if (ph == PH_X1) {
-                            for (int s = q_seg_of<P, PD>(A.q, j0); s <= q_seg_of<P, PD>(A.q, j1) && ok; ++s)
-                                ok = wait_count(A, cnt + A.cl.qseg + s, A.q.nstrips, slot_status);
-                        } else {
-                            for (int s = j0 / RS; s <= j1 / RS && ok; ++s)
-                                ok = wait_count(A, cnt + A.cl.mvseg + s, A.mv_nstrips, slot_status);
-                        }
-                    } else if (ph == PH_Y1) {
-                        ok = wait_count(A, cnt + A.cl.x1 + arr, A.nxg, slot_status);
-                    } else {
-                        ok = wait_count(A, cnt + A.cl.x2, A.nxg, slot_status);
-                    }
-                    s_dep = ok ? 1 : 0;  // not s_abort: other threads may still be reading that
-                }
-                const int key = (z << 3) | (ph << 1) | arr;
-                const bool restage = s_key != key;  // read before any thread updates it below
-                __syncthreads();
-                if (s_dep) {
-                    if (ph == PH_X1 || ph == PH_X2) {
-                        x_tile<P, PD>(A, a, z, arr, tile * a.G, smem, restage);
-                        __syncthreads();
-                        if (tid == 0) arrive(cnt + (ph == PH_X1 ? A.cl.x1 + arr : A.cl.x2));
-                    } else {
-                        y_tile<P, PD, 16>(A, a, z, arr, tile, smem, restage);
-                        __syncthreads();
-                        if (tid == 0 && ph == PH_Y1 && arr == 0) arrive(cnt + A.cl.y1col + tile);
-                    }
-                    if (tid == 0) s_key = key;
-                }
+                y_tile<P, PD, 16>(A, a, z, arr, tile, smem, restage, tid, kBT);
+                bsync();
+                if (tid == 0 && ph == PH_Y1 && arr == 0) arrive(cnt + A.cl.y1col + tile);
             }
+            if (tid == 0) s_key = key;
         }
-        __syncthreads();  // s_item, s_key and shared memory are reused by the next item
-        if (tid == 0 && live && !s_abort) {
-            // the slot's last item of the step spends one step of its budget
-            const int old = atomicAdd(cnt + A.cl.done, 1);
-            if (old == A.items_per_slot - 1 && A.budget) {
-                const int b = A.budget[z];
-                if (b > 0) A.budget[z] = b - 1;
-            }
-        }
+        if (tid == 0 && s_live) slot_done(A, cnt, z);
+        bsync();  // s_item, s_key and the shared memory are reused by the next tile
     }
+}
+
+template <int PD, int WR>
+__global__ void __launch_bounds__(kPT, 1) k_step_persist(const __grid_constant__ PersistArgs<float> A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int sh[4];
+    const int tid = threadIdx.x;
+    if (tid < kAW * 32)
+        a_loop<PD, WR>(A, tid & 31, reinterpret_cast<float*>(smem + A.bsmem) + (size_t)(tid >> 5) * A.wsm_floats);
+    else
+        b_loop<PD>(A, tid - kAW * 32, smem, sh);
 }
 
 // ---- host side -----------------------------------------------------------------------------
@@ -616,16 +666,16 @@ bool fill_line(const LineArgs& la, bool xdir, int G_req, FastArgs<P>& f, size_t*
         int sp = la.pitch;
         if (L < slots)
             while (sp % (2 * L) != L || (sp * sizeof(P)) % 16 != 0) ++sp;
-        int G = (kPT / 32) * lpw;
+        int G = (kBT / 32) * lpw;
         if (G_req > 0 && G_req < G) G = (G_req + lpw - 1) / lpw * lpw;
         f.G = G;
         f.lsh = lsh;
         f.sp = sp;
         *smem = (size_t)G * sp * sizeof(P) + fbytes;
     } else {
-        int G = G_req > 0 ? G_req : 256;
-        while (G > 1 && G * ch.C > kPT) G /= 2;
-        if (G * ch.C > kPT) return false;
+        int G = G_req > 0 ? G_req : kBT;
+        while (G > 1 && G * ch.C > kBT) G /= 2;
+        if (G * ch.C > kBT) return false;
         f.G = G;
         *smem = fbytes + (size_t)G * ch.C * f.mpad * sizeof(P);
     }
@@ -641,7 +691,7 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     // give every CTA work
     const int nstrips = (h.q.Nx + (32 - PD) - 1) / (32 - PD);
     int seg = 64;
-    while (seg > 16 && (long)nstrips * ((h.q.Ny + seg - 1) / seg) * h.nslots < 16L * sms) seg /= 2;
+    while (seg > 16 && (long)nstrips * ((h.q.Ny + seg - 1) / seg) * h.nslots < (long)kAW * 2 * sms) seg /= 2;
     if (h.seg > 0) seg = h.seg;
     fill_stream_args<float, PD>(h.q, seg, A.q);
     size_t sx1 = 0, sy1 = 0, sx2 = 0, sy2 = 0;
@@ -683,16 +733,19 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     cl.done = cl.x2 + 1;
     cl.stride = (cl.done + 1 + 31) & ~31;  // 128-byte blocks per slot
     A.cl = cl;
-    size_t smem = std::max(std::max(sx1, sx2), std::max(sy1, sy2));
-    smem = std::max(smem, (size_t)(kPT / 32) * A.wsm_floats * sizeof(float));
-    if (smem > 110 * 1024) return cudaErrorNotSupported;  // two CTAs per SM
-    plan->nq8 = (A.nq + 7) / 8;
-    plan->nmv8 = (A.mv_nstrips * A.mv_nsegs + 7) / 8;
+    // shared memory: the B threads' line tiles, then each A warp's wind rows
+    const size_t bsm = (std::max(std::max(sx1, sx2), std::max(sy1, sy2)) + 127) & ~(size_t)127;
+    A.bsmem = (int)bsm;
+    const size_t smem = bsm + (size_t)kAW * A.wsm_floats * sizeof(float);
+    if (smem > 220 * 1024) return cudaErrorNotSupported;
+    plan->nq = A.nq;
+    plan->nmv = A.mv_nstrips * A.mv_nsegs;
     plan->nxg = A.nxg;
     plan->nyg = A.nyg;
     plan->narr1 = h.x1.narr;
     plan->cstride = cl.stride;
-    plan->items_per_slot = plan->nq8 + 2 * A.nxg + 2 * A.nyg + plan->nmv8 + A.nxg + A.nyg;
+    plan->itemsA_per_slot = plan->nq + plan->nmv;
+    plan->itemsB_per_slot = 2 * A.nxg + 2 * A.nyg + A.nxg + A.nyg;
     plan->seg = seg;
     plan->xG = A.x1.G;
     plan->yG = A.y1.G;
@@ -705,17 +758,19 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorNotSupported;
-    A.items = h.items;
-    A.nitems = h.nitems;
+    A.itemsA = h.itemsA;
+    A.itemsB = h.itemsB;
+    A.nA = h.ctl + 4;
+    A.nB = h.ctl + 5;
     A.ctl = h.ctl;
     A.cnt = h.cnt;
     A.wait_ns = h.wait_ns;
     A.status = h.status;
     A.active = h.active;
     A.budget = h.budget;
-    A.items_per_slot = plan->items_per_slot;
-    // every counter of this step starts at zero (ticket, abort flag, arrival counters)
-    e = cudaMemsetAsync(h.ctl, 0, 2 * sizeof(int), s);
+    A.items_per_slot = plan->itemsA_per_slot + plan->itemsB_per_slot;
+    // every counter of this step starts at zero (tickets, abort flag, arrival counters)
+    e = cudaMemsetAsync(h.ctl, 0, 4 * sizeof(int), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h.cnt, 0, (size_t)h.nslots_cap * cl.stride * sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -751,14 +806,20 @@ cudaError_t persist_step(const PersistHost& h, PersistPlan* plan, bool launch, c
     return cudaErrorNotSupported;
 }
 
-// Wavefront order of the work items over groups of `gs` active slots (see the top of the file).
-int persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs, int4* out, int cap) {
+// Wavefront order of the work items over groups of `gs` active slots (see the top of the file),
+// split into stream A (quadrature and matvec warp tiles) and stream B (x and y line tiles).
+void persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs, int4* outA, int capA, int* nA,
+                   int4* outB, int capB, int* nB) {
     if (gs < 1) gs = 1;
     const int ngroups = (nslots + gs - 1) / gs;
-    int n = 0;
-    auto put = [&](int ph, int z, int a, int b) {
-        if (n < cap) out[n] = make_int4(ph, z, a, b);
-        ++n;
+    int na = 0, nb = 0;
+    auto putA = [&](int ph, int z, int w) {
+        if (na < capA) outA[na] = make_int4(ph, z, w, 0);
+        ++na;
+    };
+    auto putB = [&](int ph, int z, int a, int b) {
+        if (nb < capB) outB[nb] = make_int4(ph, z, a, b);
+        ++nb;
     };
     for (int t = 0; t < ngroups + PH_N - 1; ++t)
         for (int ph = 0; ph < PH_N; ++ph) {
@@ -768,29 +829,30 @@ int persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs,
                 const int z = slots[k];
                 switch (ph) {
                     case PH_Q:
-                        for (int i = 0; i < plan.nq8; ++i) put(PH_Q, z, 8 * i, 0);
+                        for (int i = 0; i < plan.nq; ++i) putA(PH_Q, z, i);
                         break;
                     case PH_X1:
                         for (int arr = 0; arr < plan.narr1; ++arr)
-                            for (int i = 0; i < plan.nxg; ++i) put(PH_X1, z, arr, i);
+                            for (int i = 0; i < plan.nxg; ++i) putB(PH_X1, z, arr, i);
                         break;
                     case PH_Y1:
                         for (int arr = 0; arr < plan.narr1; ++arr)
-                            for (int i = 0; i < plan.nyg; ++i) put(PH_Y1, z, arr, i);
+                            for (int i = 0; i < plan.nyg; ++i) putB(PH_Y1, z, arr, i);
                         break;
                     case PH_MV:
-                        for (int i = 0; i < plan.nmv8; ++i) put(PH_MV, z, 8 * i, 0);
+                        for (int i = 0; i < plan.nmv; ++i) putA(PH_MV, z, i);
                         break;
                     case PH_X2:
-                        for (int i = 0; i < plan.nxg; ++i) put(PH_X2, z, 0, i);
+                        for (int i = 0; i < plan.nxg; ++i) putB(PH_X2, z, 0, i);
                         break;
                     case PH_Y2:
-                        for (int i = 0; i < plan.nyg; ++i) put(PH_Y2, z, 0, i);
+                        for (int i = 0; i < plan.nyg; ++i) putB(PH_Y2, z, 0, i);
                         break;
                 }
             }
         }
-    return n;
+    *nA = na;
+    *nB = nb;
 }
 
 }  // namespace wf
