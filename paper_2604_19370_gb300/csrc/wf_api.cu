@@ -125,8 +125,7 @@ struct wf_handle {
                                            // persistent order (0: the launchers' rules)
     // persistent step: work items, ticket / abort / item count, arrival counters (allocated on
     // first use); the item list is rebuilt when the active slots or the shapes change
-    int4* p_items = nullptr;   // stream A items, then stream B items at p_items + p_capA
-    size_t p_capA = 0;
+    int4* p_items = nullptr;
     int* p_ctl = nullptr;
     int* p_cnt = nullptr;
     size_t p_items_cap = 0, p_cnt_cap = 0;
@@ -643,8 +642,7 @@ void persist_args(wf_handle* h, PersistHost* ph) {
     ph->nslots_cap = h->S;
     ph->wait_ns = h->wait_ns;
     ph->status = h->status;
-    ph->itemsA = h->p_items;
-    ph->itemsB = h->p_items ? h->p_items + h->p_capA : nullptr;
+    ph->items = h->p_items;
     ph->ctl = h->p_ctl;
     ph->cnt = h->p_cnt;
     ph->active = h->active_dev;
@@ -681,10 +679,9 @@ int prepare_persist(wf_handle* h) {
     for (int z = 0; z < h->S; ++z)
         if (h->active_host[z]) act.push_back(z);
     // room for every slot active, so that slots joining later need no reallocation
-    const size_t capA = std::max<size_t>(1, (size_t)h->S * plan.itemsA_per_slot);
-    const size_t capB = std::max<size_t>(1, (size_t)h->S * plan.itemsB_per_slot);
+    const size_t cap = std::max<size_t>(1, (size_t)h->S * plan.items_per_slot);
     const size_t need_cnt = (size_t)h->S * plan.cstride;
-    if (capA + capB > h->p_items_cap || capA != h->p_capA || need_cnt > h->p_cnt_cap || !h->p_ctl) {
+    if (cap > h->p_items_cap || need_cnt > h->p_cnt_cap || !h->p_ctl) {
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;
         if (h->p_items) cudaFree(h->p_items);
         if (h->p_cnt) cudaFree(h->p_cnt);
@@ -692,23 +689,20 @@ int prepare_persist(wf_handle* h) {
         h->p_items = nullptr;
         h->p_cnt = nullptr;
         h->p_ctl = nullptr;
-        h->p_items_cap = h->p_cnt_cap = h->p_capA = 0;
-        if (cudaMalloc(&h->p_items, (capA + capB) * sizeof(int4)) != cudaSuccess ||
+        h->p_items_cap = h->p_cnt_cap = 0;
+        if (cudaMalloc(&h->p_items, cap * sizeof(int4)) != cudaSuccess ||
             cudaMalloc(&h->p_cnt, need_cnt * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&h->p_ctl, 8 * sizeof(int)) != cudaSuccess)
+            cudaMalloc(&h->p_ctl, 4 * sizeof(int)) != cudaSuccess)
             return WF_ENOMEM;
-        h->p_items_cap = capA + capB;
-        h->p_capA = capA;
+        h->p_items_cap = cap;
         h->p_cnt_cap = need_cnt;
         drop_graphs(h);  // captured graphs hold the old buffers
     }
-    std::vector<int4> items(capA + capB);
-    int n[2] = {0, 0};
-    persist_items(plan, act.data(), (int)act.size(), persist_group(h), items.data(), (int)capA, &n[0],
-                  items.data() + capA, (int)capB, &n[1]);
-    if ((size_t)n[0] > capA || (size_t)n[1] > capB) return WF_ECUDA;
-    WF_TRY(cudaMemcpyAsync(h->p_items, items.data(), sizeof(int4) * (capA + capB), cudaMemcpyHostToDevice, h->stream));
-    WF_TRY(cudaMemcpyAsync(h->p_ctl + 4, n, sizeof(n), cudaMemcpyHostToDevice, h->stream));
+    std::vector<int4> items(cap);
+    const int n = persist_items(plan, act.data(), (int)act.size(), persist_group(h), items.data(), (int)cap);
+    if ((size_t)n > cap) return WF_ECUDA;
+    WF_TRY(cudaMemcpyAsync(h->p_items, items.data(), sizeof(int4) * std::max(n, 1), cudaMemcpyHostToDevice, h->stream));
+    WF_TRY(cudaMemcpyAsync(h->p_ctl + 2, &n, sizeof(int), cudaMemcpyHostToDevice, h->stream));
     WF_TRY(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
     h->p_dirty = false;
     return WF_OK;

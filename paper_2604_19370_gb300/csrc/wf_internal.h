@@ -236,25 +236,23 @@ struct PersistHost {
     int nslots_cap;           // slot capacity of the handle (counter blocks)
     long long wait_ns;
     int* status;              // slot-0 flag word
-    const int4* itemsA;       // device: stream A work items (quadrature, matvec warp tiles)
-    const int4* itemsB;       // device: stream B work items (x and y line tiles)
-    int* ctl;                 // device: [0] ticket A, [1] abort, [2] ticket B, [4] items A, [5] items B
+    const int4* items;        // device: work items (warp tiles) in their order
+    int* ctl;                 // device: [0] ticket, [1] abort flag, [2] number of items
     int* cnt;                 // device: nslots_cap x cstride arrival counters
     const int* active;        // device: per-slot activity flags (an inactive slot's items are skipped)
     int* budget;              // device: per-slot step budgets, or NULL (a spent budget, 0, skips too)
 };
 struct PersistPlan {
-    int nq, nmv, nxg, nyg, narr1, cstride, itemsA_per_slot, itemsB_per_slot, seg, xG, yG;
+    int nq, nmv, nxg, nyg, narr1, cstride, items_per_slot, seg, xG, yG;
     size_t smem;
 };
 bool persist_supported(int prec, int p, int wind_rank);
 // plan (and, with launch, enqueue: counter reset + one kernel) of one step; cudaErrorNotSupported
 // when the persistent form cannot take these arguments
 cudaError_t persist_step(const PersistHost& h, PersistPlan* plan, bool launch, cudaStream_t s);
-// work items of one step for the given active slots, groups of gs slots in wavefront order, in
-// the two streams; *nA, *nB receive the counts (entries past the capacities are not written)
-void persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs, int4* outA, int capA, int* nA,
-                   int4* outB, int capB, int* nB);
+// work items of one step for the given active slots, groups of gs slots in wavefront order;
+// returns the count (entries past cap are not written)
+int persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs, int4* out, int cap);
 
 // launch-shape helpers shared with the host driver
 int line_rows_per_cta(int prec);

@@ -1,25 +1,26 @@
 // Persistent step kernel: one launch runs a whole Peaceman-Rachford step (one F per step) of
-// every active slot of a batch handle.
+// every active slot of a batch handle.  Every warp is a worker that claims single warp tiles.
 //
 // Paper: Sec. 3.1 Eq. matrixPR (the two substeps), Sec. 4 (every directional solve is a set
 // of independent 1-D line solves, which is what lets one launch cover a whole pass of a whole
 // batch), Sec. 7 listing "compute_rhs" (the quadrature and the fuel update).
 //
 // The step of one slot is six passes, each a set of independent tiles:
-//   Q   quadrature: F, Phi and the substep-1 right-hand side R, in (strip, segment) warp tiles
-//   X1  x lines of R with X_+ and of Phi with M^x, in groups of rows
-//   Y1  y lines (R -> T*, Phi -> phi^{n+1}, increment bases added), in groups of columns
-//   MV  substep-2 right-hand side R = theta F + (A_x (x) M^y) T* + (M^x (x) A_y) T*, warp tiles
-//   X2  x lines of R with M^x, in groups of rows
-//   Y2  y lines with Y_+ (R -> T^{n+1}, base T*), guard, in groups of columns
+//   Q   quadrature: F, Phi and the substep-1 right-hand side R, in (strip, segment) tiles
+//   X1  x lines of R with X_+ and of Phi with M^x, a warp's lines per tile (one lane per chunk)
+//   Y1  y lines (R -> T*, Phi -> phi^{n+1}, increment bases added), 32 / C columns per tile
+//       (one thread per chunk of a column)
+//   MV  substep-2 right-hand side R = theta F + (A_x (x) M^y) T* + (M^x (x) A_y) T*
+//   X2  x lines of R with M^x
+//   Y2  y lines with Y_+ (R -> T^{n+1}, base T*), guard
 // The arithmetic of every tile is that of the per-pass kernels (the same device functions or
 // the same operations in the same order), so both paths give the same bits.
 //
 // Work items (phase, slot, tile) are listed by the host in a wavefront over groups of slots:
 // at "time" t the list holds Q of group t, X1 of group t-1, ..., Y2 of group t-5, so the
 // intermediate fields of about six groups are live at once (sized to stay in L2), and
-// consecutive items are independent.  A CTA claims the next item from a ticket counter (the
-// next ticket is fetched while the current item runs) and, before touching its inputs, waits
+// consecutive items are independent.  A warp claims the next tile from a ticket counter (the
+// next ticket is fetched while the current tile runs) and, before touching its inputs, waits
 // for the arrival counters of the tiles it reads:
 //   X1 rows     <- the Q segments that cover them (every strip)
 //   Y1 columns  <- every X1 row group of its array
@@ -28,8 +29,8 @@
 //   Y2 columns  <- every X2 row group
 // A tile waits only for tiles with smaller tickets, which are running or done when it is
 // claimed, so the launch always makes progress whatever the number of resident CTAs.
-// Producers release (stores, barrier, fence, counter add); consumers acquire (ld.acquire on
-// the counter, barrier) and read data produced in this launch through L2 (ld.global.cg),
+// Producers release (stores, __syncwarp, fence, counter add); consumers acquire (ld.acquire on
+// the counter, __syncwarp) and read data produced in this launch through L2 (ld.global.cg),
 // never through the read-only path.  Every wait is bounded by the handle's wait limit (the
 // SM's global timer); a wait that gives up sets the slot's timeout bit and the launch-wide
 // abort flag, after which every remaining item is skipped, so a failure costs one limit.
@@ -45,9 +46,7 @@ namespace wf {
 
 namespace {
 
-constexpr int kAW = 8;                 // A warps per CTA: quadrature and matvec warp tiles
-constexpr int kBT = 256;               // B threads per CTA: x and y line tiles (named barrier 1)
-constexpr int kPT = kAW * 32 + kBT;    // threads per CTA (one CTA per SM)
+constexpr int kPT = 256;  // threads per CTA (two CTAs per SM: sixteen warps, 128 registers each)
 
 enum { PH_Q = 0, PH_X1 = 1, PH_Y1 = 2, PH_MV = 3, PH_X2 = 4, PH_Y2 = 5, PH_N = 6 };
 
@@ -73,12 +72,10 @@ struct PersistArgs {
     int nxg, nyg;  // row groups of the x passes, column groups of the y passes
     int vec;       // rows 16-byte aligned: stage x lines with 16-byte loads
     int wsm_floats;  // per-warp shared memory of the quadrature (wind factors)
-    int bsmem;       // bytes of the B threads' shared memory (the A warps' follows)
-    const int4* itemsA;  // stream A: quadrature and matvec warp tiles
-    const int4* itemsB;  // stream B: x and y line tiles
-    const int* nA;
-    const int* nB;
-    int* ctl;  // [0] ticket of stream A, [1] abort flag, [2] ticket of stream B
+    int warp_smem;   // bytes of shared memory of each warp (its tiles' rows, factors, wind rows)
+    const int4* items;
+    const int* nitems;
+    int* ctl;  // [0] ticket, [1] abort flag
     int* cnt;  // slot z's counters at cnt + z * cl.stride
     CntLayout cl;
     long long wait_ns;
@@ -147,9 +144,6 @@ __device__ bool wait_count(const PersistArgs<P>& A, const int* c, int target, in
     if (slot_status) atomicOr(slot_status, WF_STATUS_TIMEOUT);
     return false;
 }
-
-// barrier of the B threads (the x and y line tiles); the A warps never take part
-__device__ __forceinline__ void bsync() { asm volatile("bar.sync 1, %0;" ::"n"(kBT) : "memory"); }
 
 __device__ __forceinline__ void arrive(int* c) {
     __threadfence();
@@ -242,7 +236,7 @@ __device__ void x_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int
         }
     }
     if (restage) stage_factors<P, PD>(v, mmax, fm, tid, nt);
-    bsync();
+    __syncwarp();
     const int k = lane & ((1 << a.lsh) - 1);
     const int r = (warp << (5 - a.lsh)) + (lane >> a.lsh);
     const bool active = r < rows && k < C;
@@ -268,7 +262,7 @@ __device__ void x_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int
     P tn[PD], bp[PD];
     interface_solve<P, PD>(ch, k < C ? k : 0, mmax, fm.S, fm.E, top, bot, nxt_top, prv_bot, tn, bp);
     if (active) spike_fix<P, PD>(g, m, fm.S + t * mmax * FacW<PD>::S, tn, bp);
-    bsync();
+    __syncwarp();
     if (sizeof(P) == 4 && A.vec) {
         const int n4 = (N + 3) >> 2;
         for (int i = tid; i < rows * n4; i += nt) {
@@ -308,7 +302,7 @@ __device__ void y_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int
     const size_t pitch = (size_t)a.pitch;
     P* g = buf + (size_t)(thr ? tid : 0) * mpad;
     if (restage) stage_factors<P, PD>(v, mmax, fm, tid, nt);
-    bsync();
+    __syncwarp();
     if (thr) {
         const P* Fk = fm.F + t * mmax * NF;
         P prev[PD];
@@ -333,7 +327,7 @@ __device__ void y_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int
         }
         lu_backward<P, PD>(g, m, fm.U + t * mmax * NU);
     }
-    bsync();
+    __syncwarp();
     if (!valid) return;  // no barrier follows in this tile
     const P* gn = buf + (size_t)((k + 1 < C ? k + 1 : k) * G + c) * mpad;
     const P* gp = buf + (size_t)((k > 0 ? k - 1 : k) * G + c) * mpad + (base - PD);
@@ -468,12 +462,11 @@ struct MvRows {
 };
 
 // ---- the kernel ----------------------------------------------------------------------------
-// One CTA of kAW + kBT / 32 warps per SM.  The first kAW warps ("A") each claim single
-// quadrature or matvec warp tiles from stream A, without any CTA barrier; the other kBT threads
-// ("B", synchronised by named barrier 1) claim x and y line tiles from stream B.  The two streams
-// are subsequences of one dependency-respecting order (the wavefront), so the launch makes
-// progress; inside every SM the ALU-heavy quadrature of one group of slots runs beside the
-// memory-bound line passes of older groups.
+// Every warp is a worker: it claims the next tile of the ticket order (any pass), waits for the
+// tiles it reads, runs it in its own shared-memory region and signals its arrival; nothing but
+// __syncwarp synchronises threads, so sixteen warps per SM work on whatever is ready and the
+// ALU-heavy quadrature tiles of one group of slots run beside the memory-bound line tiles of
+// older groups.
 
 // a slot takes part in this step: active and its step budget not spent
 template <typename P>
@@ -481,8 +474,8 @@ __device__ __forceinline__ bool slot_live(const PersistArgs<P>& A, int z) {
     return ld_relaxed(A.active + z) != 0 && (!A.budget || ld_relaxed(A.budget + z) != 0);
 }
 
-// an item of slot z finished; the slot's last item of the step spends one step of its budget
-// (every item of the slot has then started, so all of them saw the same budget)
+// a tile of slot z finished; the slot's last tile of the step spends one step of its budget
+// (every tile of the slot has then started, so all of them saw the same budget)
 template <typename P>
 __device__ __forceinline__ void slot_done(const PersistArgs<P>& A, int* cnt, int z) {
     const int old = atomicAdd(cnt + A.cl.done, 1);
@@ -493,87 +486,34 @@ __device__ __forceinline__ void slot_done(const PersistArgs<P>& A, int* cnt, int
 }
 
 template <int PD, int WR>
-__device__ void a_loop(const PersistArgs<float>& A, int lane, float* wsm) {
+__global__ void __launch_bounds__(kPT, 2) k_step_persist(const __grid_constant__ PersistArgs<float> A) {
     using P = float;
     constexpr int RS = MvRows<PD>::value;
-    const int n = *A.nA;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char* wsm = smem + (size_t)warp * A.warp_smem;
+    const int n = *A.nitems;
+    int key = -1;  // (slot, pass, array) whose factors sit in this warp's shared memory
     int next = 0;
-    if (lane == 0) next = atomicAdd(A.ctl + 0, 1);
+    if (lane == 0) next = atomicAdd(A.ctl, 1);
     next = __shfl_sync(0xffffffffu, next, 0);
     for (;;) {
         const int it = next;
         if (it >= n) break;
+        const int4 d = A.items[it];
+        const int ph = d.x, z = d.y;
+        int* cnt = A.cnt + (size_t)z * A.cl.stride;
+        int* slot_status = shift(A.status, (long long)z * A.sbytes);
         int go = 0;
-        const int4 d = A.itemsA[it];
-        const int z = d.y, w = d.z;
-        int* cnt = A.cnt + (size_t)z * A.cl.stride;
-        int* slot_status = shift(A.status, (long long)z * A.sbytes);
         if (lane == 0) {
-            next = atomicAdd(A.ctl + 0, 1);  // fetched while this tile runs
-            go = (!ld_relaxed(A.ctl + 1) ? 1 : 0) | (slot_live(A, z) ? 2 : 0);
-        }
-        next = __shfl_sync(0xffffffffu, next, 0);
-        go = __shfl_sync(0xffffffffu, go, 0);
-        if (!(go & 2)) continue;  // the slot does not take part (no count)
-        if (go & 1) {
-            if (d.x == PH_Q) {
-                q_tile<PD, WR>(A, z, w, wsm);
-                __syncwarp();
-                if (lane == 0) arrive(cnt + A.cl.qseg + w / A.q.nstrips);
-            } else {
-                // columns (with halo) of this strip: wait for the Y1 column groups covering them
-                const int st = w % A.mv_nstrips;
-                const int xlo = max(0, st * (32 - 2 * PD) - PD), xhi = min(A.Nx - 1, st * (32 - 2 * PD) - PD + 31);
-                int ok = 1;
-                if (lane == 0)
-                    for (int gq = xlo / A.y1.G; gq <= xhi / A.y1.G && ok; ++gq)
-                        ok = wait_count(A, cnt + A.cl.y1col + gq, 1, slot_status) ? 1 : 0;
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                __syncwarp();  // orders the other lanes' loads after lane 0's acquire
-                if (ok) {
-                    mv_tile<P, PD, RS>(A, z, w);
-                    __syncwarp();
-                    if (lane == 0) arrive(cnt + A.cl.mvseg + w / A.mv_nstrips);
-                }
-            }
-        }
-        if (lane == 0) slot_done(A, cnt, z);
-    }
-}
-
-template <int PD>
-__device__ void b_loop(const PersistArgs<float>& A, int tid, unsigned char* smem, int* sh) {
-    using P = float;
-    constexpr int RS = MvRows<PD>::value;
-    int& s_item = sh[0];
-    int& s_live = sh[1];
-    int& s_dep = sh[2];
-    int& s_key = sh[3];
-    const int n = *A.nB;
-    int next = 0;
-    if (tid == 0) {
-        next = atomicAdd(A.ctl + 2, 1);
-        s_key = -1;
-    }
-    for (;;) {
-        if (tid == 0) {
-            s_item = next;
-            if (next < n) next = atomicAdd(A.ctl + 2, 1);  // fetched while this tile runs
-        }
-        bsync();
-        const int it = s_item;
-        if (it >= n) break;
-        const int4 d = A.itemsB[it];
-        const int ph = d.x, z = d.y, arr = d.z, tile = d.w;
-        int* cnt = A.cnt + (size_t)z * A.cl.stride;
-        int* slot_status = shift(A.status, (long long)z * A.sbytes);
-        const FastArgs<P>& a = ph == PH_X1 ? A.x1 : (ph == PH_Y1 ? A.y1 : (ph == PH_X2 ? A.x2 : A.y2));
-        if (tid == 0) {
+            next = atomicAdd(A.ctl, 1);  // fetched while this tile runs
             const bool live = slot_live(A, z);
             bool ok = live && !ld_relaxed(A.ctl + 1);
+            // the tiles this one reads
             if (ok) {
                 if (ph == PH_X1 || ph == PH_X2) {
-                    const int j0 = tile * a.G, j1 = min(a.nlines, j0 + a.G) - 1;
+                    const FastArgs<P>& a = ph == PH_X1 ? A.x1 : A.x2;
+                    const int j0 = d.w * a.G, j1 = min(a.nlines, j0 + a.G) - 1;
                     if (ph == PH_X1) {
                         for (int s = q_seg_of<P, PD>(A.q, j0); s <= q_seg_of<P, PD>(A.q, j1) && ok; ++s)
                             ok = wait_count(A, cnt + A.cl.qseg + s, A.q.nstrips, slot_status);
@@ -582,43 +522,52 @@ __device__ void b_loop(const PersistArgs<float>& A, int tid, unsigned char* smem
                             ok = wait_count(A, cnt + A.cl.mvseg + s, A.mv_nstrips, slot_status);
                     }
                 } else if (ph == PH_Y1) {
-                    ok = wait_count(A, cnt + A.cl.x1 + arr, A.nxg, slot_status);
-                } else {
+                    ok = wait_count(A, cnt + A.cl.x1 + d.z, A.nxg, slot_status);
+                } else if (ph == PH_Y2) {
                     ok = wait_count(A, cnt + A.cl.x2, A.nxg, slot_status);
+                } else if (ph == PH_MV) {
+                    const int st = d.z % A.mv_nstrips;
+                    const int xlo = max(0, st * (32 - 2 * PD) - PD), xhi = min(A.Nx - 1, st * (32 - 2 * PD) - PD + 31);
+                    for (int gq = xlo / A.y1.G; gq <= xhi / A.y1.G && ok; ++gq)
+                        ok = wait_count(A, cnt + A.cl.y1col + gq, 1, slot_status);
                 }
             }
-            s_live = live ? 1 : 0;
-            s_dep = ok ? 1 : 0;
+            go = (live ? 2 : 0) | (ok ? 1 : 0);
         }
-        const int key = (z << 4) | (ph << 1) | arr;  // ph <= 5: bits 1..3
-        const bool restage = s_key != key;          // read before thread 0 updates it below
-        bsync();
-        if (s_dep) {
-            if (ph == PH_X1 || ph == PH_X2) {
-                x_tile<P, PD>(A, a, z, arr, tile * a.G, smem, restage, tid, kBT);
-                bsync();
-                if (tid == 0) arrive(cnt + (ph == PH_X1 ? A.cl.x1 + arr : A.cl.x2));
+        next = __shfl_sync(0xffffffffu, next, 0);
+        go = __shfl_sync(0xffffffffu, go, 0);
+        __syncwarp();  // orders the other lanes' loads after lane 0's acquire
+        if (!(go & 2)) continue;  // the slot does not take part in this step (not counted)
+        if (go & 1) {
+            if (ph == PH_Q) {
+                q_tile<PD, WR>(A, z, d.z, reinterpret_cast<float*>(wsm));
+                key = -1;  // the wind rows overwrite the staged factors
+                __syncwarp();
+                if (lane == 0) arrive(cnt + A.cl.qseg + d.z / A.q.nstrips);
+            } else if (ph == PH_MV) {
+                mv_tile<P, PD, RS>(A, z, d.z);
+                __syncwarp();
+                if (lane == 0) arrive(cnt + A.cl.mvseg + d.z / A.mv_nstrips);
             } else {
-                y_tile<P, PD, 16>(A, a, z, arr, tile, smem, restage, tid, kBT);
-                bsync();
-                if (tid == 0 && ph == PH_Y1 && arr == 0) arrive(cnt + A.cl.y1col + tile);
+                const int arr = d.z, tile = d.w;
+                const int k2 = (z << 4) | (ph << 1) | arr;  // ph <= 5: bits 1..3
+                if (ph == PH_X1 || ph == PH_X2) {
+                    const FastArgs<P>& a = ph == PH_X1 ? A.x1 : A.x2;
+                    x_tile<P, PD>(A, a, z, arr, tile * a.G, wsm, k2 != key, lane, 32);
+                    __syncwarp();
+                    if (lane == 0) arrive(cnt + (ph == PH_X1 ? A.cl.x1 + arr : A.cl.x2));
+                } else {
+                    const FastArgs<P>& a = ph == PH_Y1 ? A.y1 : A.y2;
+                    y_tile<P, PD, 16>(A, a, z, arr, tile, wsm, k2 != key, lane, 32);
+                    __syncwarp();
+                    if (lane == 0 && ph == PH_Y1 && arr == 0) arrive(cnt + A.cl.y1col + tile);
+                }
+                key = k2;
             }
-            if (tid == 0) s_key = key;
         }
-        if (tid == 0 && s_live) slot_done(A, cnt, z);
-        bsync();  // s_item, s_key and the shared memory are reused by the next tile
+        if (lane == 0) slot_done(A, cnt, z);
+        __syncwarp();  // the warp's shared memory is reused by its next tile
     }
-}
-
-template <int PD, int WR>
-__global__ void __launch_bounds__(kPT, 1) k_step_persist(const __grid_constant__ PersistArgs<float> A) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ int sh[4];
-    const int tid = threadIdx.x;
-    if (tid < kAW * 32)
-        a_loop<PD, WR>(A, tid & 31, reinterpret_cast<float*>(smem + A.bsmem) + (size_t)(tid >> 5) * A.wsm_floats);
-    else
-        b_loop<PD>(A, tid - kAW * 32, smem, sh);
 }
 
 // ---- host side -----------------------------------------------------------------------------
@@ -666,16 +615,17 @@ bool fill_line(const LineArgs& la, bool xdir, int G_req, FastArgs<P>& f, size_t*
         int sp = la.pitch;
         if (L < slots)
             while (sp % (2 * L) != L || (sp * sizeof(P)) % 16 != 0) ++sp;
-        int G = (kBT / 32) * lpw;
-        if (G_req > 0 && G_req < G) G = (G_req + lpw - 1) / lpw * lpw;
+        const int G = lpw;  // a tile is one warp's lines
+        (void)G_req;
         f.G = G;
         f.lsh = lsh;
         f.sp = sp;
         *smem = (size_t)G * sp * sizeof(P) + fbytes;
     } else {
-        int G = G_req > 0 ? G_req : kBT;
-        while (G > 1 && G * ch.C > kBT) G /= 2;
-        if (G * ch.C > kBT) return false;
+        // a tile is one warp: G columns x C chunks of threads
+        int G = 32 / ch.C;
+        if (G_req > 0 && G_req < G) G = G_req;
+        if (G < 1) return false;
         f.G = G;
         *smem = fbytes + (size_t)G * ch.C * f.mpad * sizeof(P);
     }
@@ -691,7 +641,7 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     // give every CTA work
     const int nstrips = (h.q.Nx + (32 - PD) - 1) / (32 - PD);
     int seg = 64;
-    while (seg > 16 && (long)nstrips * ((h.q.Ny + seg - 1) / seg) * h.nslots < (long)kAW * 2 * sms) seg /= 2;
+    while (seg > 16 && (long)nstrips * ((h.q.Ny + seg - 1) / seg) * h.nslots < 16L * sms) seg /= 2;
     if (h.seg > 0) seg = h.seg;
     fill_stream_args<float, PD>(h.q, seg, A.q);
     size_t sx1 = 0, sy1 = 0, sx2 = 0, sy2 = 0;
@@ -733,19 +683,21 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     cl.done = cl.x2 + 1;
     cl.stride = (cl.done + 1 + 31) & ~31;  // 128-byte blocks per slot
     A.cl = cl;
-    // shared memory: the B threads' line tiles, then each A warp's wind rows
-    const size_t bsm = (std::max(std::max(sx1, sx2), std::max(sy1, sy2)) + 127) & ~(size_t)127;
-    A.bsmem = (int)bsm;
-    const size_t smem = bsm + (size_t)kAW * A.wsm_floats * sizeof(float);
-    if (smem > 220 * 1024) return cudaErrorNotSupported;
+    // shared memory of each warp: the largest of its tiles' needs (line rows and factors, or the
+    // quadrature's wind rows)
+    size_t wsm = std::max(std::max(sx1, sx2), std::max(sy1, sy2));
+    wsm = std::max(wsm, (size_t)A.wsm_floats * sizeof(float));
+    wsm = (wsm + 127) & ~(size_t)127;
+    A.warp_smem = (int)wsm;
+    const size_t smem = (size_t)(kPT / 32) * wsm;
+    if (smem > 110 * 1024) return cudaErrorNotSupported;  // two CTAs per SM
     plan->nq = A.nq;
     plan->nmv = A.mv_nstrips * A.mv_nsegs;
     plan->nxg = A.nxg;
     plan->nyg = A.nyg;
     plan->narr1 = h.x1.narr;
     plan->cstride = cl.stride;
-    plan->itemsA_per_slot = plan->nq + plan->nmv;
-    plan->itemsB_per_slot = 2 * A.nxg + 2 * A.nyg + A.nxg + A.nyg;
+    plan->items_per_slot = plan->nq + plan->nmv + 2 * A.nxg + 2 * A.nyg + A.nxg + A.nyg;
     plan->seg = seg;
     plan->xG = A.x1.G;
     plan->yG = A.y1.G;
@@ -758,19 +710,17 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorNotSupported;
-    A.itemsA = h.itemsA;
-    A.itemsB = h.itemsB;
-    A.nA = h.ctl + 4;
-    A.nB = h.ctl + 5;
+    A.items = h.items;
+    A.nitems = h.ctl + 2;
     A.ctl = h.ctl;
     A.cnt = h.cnt;
     A.wait_ns = h.wait_ns;
     A.status = h.status;
     A.active = h.active;
     A.budget = h.budget;
-    A.items_per_slot = plan->itemsA_per_slot + plan->itemsB_per_slot;
-    // every counter of this step starts at zero (tickets, abort flag, arrival counters)
-    e = cudaMemsetAsync(h.ctl, 0, 4 * sizeof(int), s);
+    A.items_per_slot = plan->items_per_slot;
+    // every counter of this step starts at zero (ticket, abort flag, arrival counters)
+    e = cudaMemsetAsync(h.ctl, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h.cnt, 0, (size_t)h.nslots_cap * cl.stride * sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -806,20 +756,14 @@ cudaError_t persist_step(const PersistHost& h, PersistPlan* plan, bool launch, c
     return cudaErrorNotSupported;
 }
 
-// Wavefront order of the work items over groups of `gs` active slots (see the top of the file),
-// split into stream A (quadrature and matvec warp tiles) and stream B (x and y line tiles).
-void persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs, int4* outA, int capA, int* nA,
-                   int4* outB, int capB, int* nB) {
+// Wavefront order of the work items over groups of `gs` active slots (see the top of the file).
+int persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs, int4* out, int cap) {
     if (gs < 1) gs = 1;
     const int ngroups = (nslots + gs - 1) / gs;
-    int na = 0, nb = 0;
-    auto putA = [&](int ph, int z, int w) {
-        if (na < capA) outA[na] = make_int4(ph, z, w, 0);
-        ++na;
-    };
-    auto putB = [&](int ph, int z, int a, int b) {
-        if (nb < capB) outB[nb] = make_int4(ph, z, a, b);
-        ++nb;
+    int n = 0;
+    auto put = [&](int ph, int z, int a, int b) {
+        if (n < cap) out[n] = make_int4(ph, z, a, b);
+        ++n;
     };
     for (int t = 0; t < ngroups + PH_N - 1; ++t)
         for (int ph = 0; ph < PH_N; ++ph) {
@@ -829,30 +773,29 @@ void persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs
                 const int z = slots[k];
                 switch (ph) {
                     case PH_Q:
-                        for (int i = 0; i < plan.nq; ++i) putA(PH_Q, z, i);
+                        for (int i = 0; i < plan.nq; ++i) put(PH_Q, z, i, 0);
                         break;
                     case PH_X1:
                         for (int arr = 0; arr < plan.narr1; ++arr)
-                            for (int i = 0; i < plan.nxg; ++i) putB(PH_X1, z, arr, i);
+                            for (int i = 0; i < plan.nxg; ++i) put(PH_X1, z, arr, i);
                         break;
                     case PH_Y1:
                         for (int arr = 0; arr < plan.narr1; ++arr)
-                            for (int i = 0; i < plan.nyg; ++i) putB(PH_Y1, z, arr, i);
+                            for (int i = 0; i < plan.nyg; ++i) put(PH_Y1, z, arr, i);
                         break;
                     case PH_MV:
-                        for (int i = 0; i < plan.nmv; ++i) putA(PH_MV, z, i);
+                        for (int i = 0; i < plan.nmv; ++i) put(PH_MV, z, i, 0);
                         break;
                     case PH_X2:
-                        for (int i = 0; i < plan.nxg; ++i) putB(PH_X2, z, 0, i);
+                        for (int i = 0; i < plan.nxg; ++i) put(PH_X2, z, 0, i);
                         break;
                     case PH_Y2:
-                        for (int i = 0; i < plan.nyg; ++i) putB(PH_Y2, z, 0, i);
+                        for (int i = 0; i < plan.nyg; ++i) put(PH_Y2, z, 0, i);
                         break;
                 }
             }
         }
-    *nA = na;
-    *nB = nb;
+    return n;
 }
 
 }  // namespace wf
