@@ -589,13 +589,15 @@ cudaError_t rhs_and_forcing(wf_handle* h, const RhsArgs& r, void* out1, double s
 cudaError_t enqueue_step_body(wf_handle* h);
 void drop_graphs(wf_handle* h);
 
-// The persistent step (one launch per step over every active slot) takes PR with one F per step
-// in FP32 (p <= 2, wind rank <= 2, no manufactured forcing); tuning value 6 picks it (2) or the
-// per-pass launches (1); the rule (0) takes it whenever it applies.
+// The persistent form (the quadrature launch, then one launch over every pass and active slot)
+// takes PR with one F per step; tuning value 6 picks it (2) or the per-pass launches (1); the
+// rule (0) takes it for batches (two slots or more), where its work order keeps each group of
+// slots' fields in L2 from one pass to the next.
 bool use_persist(const wf_handle* h) {
-    if (h->noalloc_run || h->prm.scheme != WF_PR || h->prm.F_timing != WF_F_ONCE || h->mms_on) return false;
+    if (h->noalloc_run || h->prm.scheme != WF_PR || h->prm.F_timing != WF_F_ONCE) return false;
     if (!persist_supported(h->prec, h->p, h->wr)) return false;
-    return h->tune[6] != 1;
+    if (h->tune[6] == 0) return h->S >= 2;
+    return h->tune[6] == 2;
 }
 
 // Arguments of the persistent step: those of the per-pass launches of the same step.
@@ -608,7 +610,6 @@ void persist_args(wf_handle* h, PersistHost* ph) {
     memset(ph, 0, sizeof(*ph));
     ph->prec = h->prec;
     ph->p = h->p;
-    ph->q = rhs_args(h, h->T, h->F, h->Phi, h->R, th, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
     ph->x1 = line_args(h, 1);
     add_line(ph->x1, h->R, h->R, X[2], cx);
     add_line(ph->x1, h->Phi, h->Phi, X[0], cx);
@@ -635,10 +636,8 @@ void persist_args(wf_handle* h, PersistHost* ph) {
     ph->y2 = line_args(h, 0);
     add_line(ph->y2, h->R, h->T, Y[2], cy, h->T);
     ph->y2.status = h->status;
-    ph->seg = h->tune[2];
     ph->xG = h->tune[0];
     ph->yG = h->tune[1];
-    ph->nslots = h->S;
     ph->nslots_cap = h->S;
     ph->wait_ns = h->wait_ns;
     ph->status = h->status;
@@ -649,14 +648,14 @@ void persist_args(wf_handle* h, PersistHost* ph) {
     ph->budget = h->budget_on ? h->budget_dev : nullptr;
 }
 
-// Slots per group of the persistent order: about six groups are live at once; their fields (five
+// Slots per group of the persistent order: about five groups are live at once; their fields (five
 // per slot) should take at most about half of the L2 cache.
 int persist_group(const wf_handle* h) {
     if (h->tune[7] > 0) return h->tune[7];
     int dev = 0, l2 = 126 << 20;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
     const double slot = 5.0 * h->Ny * h->pitch * esize(h->prec);
-    const int g = (int)(0.5 * l2 / (6.0 * slot));
+    const int g = (int)(0.5 * l2 / (5.0 * slot));
     return std::max(1, std::min(g, h->S));
 }
 
@@ -743,6 +742,11 @@ cudaError_t enqueue_step_body(wf_handle* h) {
         return cudaSuccess;
     }
     if (h->prm.scheme == WF_PR && use_persist(h) && h->p_ctl) {
+        // the quadrature (and forcing) as in the per-pass form, then one launch for the rest
+        const double th = 0.5 * h->dt;
+        RhsArgs r1 = rhs_args(h, h->T, h->F, h->Phi, h->R, th, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
+        auto l1 = [&] { return rhs_and_forcing(h, r1, h->R, th, h->F, 1.0); };
+        if ((e = timed(h, S_RHS1, l1)) != cudaSuccess) return e;
         PersistHost ph;
         persist_args(h, &ph);
         return timed(h, S_PERSIST, [&] { return persist_step(ph, nullptr, true, s); });
@@ -1518,7 +1522,7 @@ int wf_autotune(wf_handle* h, int reps) {
         int n;
     };
     const bool pers = persist_supported(h->prec, h->p, h->wr) && h->prm.scheme == WF_PR &&
-                      h->prm.F_timing == WF_F_ONCE && !h->mms_on;
+                      h->prm.F_timing == WF_F_ONCE;
     const Axis order[] = {{6, kMode, pers ? 2 : 0},
                           {7, kGroup, pers && h->S > 1 ? (int)(sizeof(kGroup) / sizeof(int)) : 0},
                           {2, kSeg, (int)(sizeof(kSeg) / sizeof(int))},

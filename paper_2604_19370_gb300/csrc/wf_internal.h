@@ -222,21 +222,19 @@ struct MatvecArgs {
 };
 cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s);
 
-// ---- persistent step (wf_persist.cu) ------------------------------------------------
-// One launch per Peaceman-Rachford step (one F per step, FP32, p <= 2, wind rank <= 2) over the
-// (phase, slot, tile) items of every active slot, listed by persist_items; the arguments are those
-// of the per-pass launches of the same step.
+// ---- persistent line passes (wf_persist.cu) -----------------------------------------
+// After the quadrature launch of a Peaceman-Rachford step (one F per step), one launch runs the
+// step's x, y and matvec passes for every active slot, over the (pass, slot, tile) items listed
+// by persist_items; the arguments are those of the per-pass launches of the same step.
 struct PersistHost {
     int prec, p;
-    RhsArgs q;                // quadrature: F, Phi, R (substep 1)
     LineArgs x1, y1, x2, y2;  // x1 and y1 with two arrays (R, Phi), x2 and y2 with one
     MatvecArgs mv;            // substep-2 right-hand side
-    int seg, xG, yG;          // quadrature segment rows, x lines and y columns per tile (0: rule)
-    int nslots;               // slots (for the segment rule)
+    int xG, yG;               // x lines and y columns per tile (0: rule)
     int nslots_cap;           // slot capacity of the handle (counter blocks)
     long long wait_ns;
     int* status;              // slot-0 flag word
-    const int4* items;        // device: work items (warp tiles) in their order
+    const int4* items;        // device: work items in their order
     int* ctl;                 // device: [0] ticket, [1] abort flag, [2] number of items
     int* cnt;                 // device: nslots_cap x cstride arrival counters
     const int* active;        // device: per-slot activity flags (an inactive slot's items are skipped)

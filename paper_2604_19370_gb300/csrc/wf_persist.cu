@@ -1,36 +1,36 @@
-// Persistent step kernel: one launch runs a whole Peaceman-Rachford step (one F per step) of
-// every active slot of a batch handle.  Every warp is a worker that claims single warp tiles.
+// Persistent line passes: after the quadrature launch of a Peaceman-Rachford step (one F per
+// step), one launch runs the rest of the step for every active slot of a batch handle.
 //
 // Paper: Sec. 3.1 Eq. matrixPR (the two substeps), Sec. 4 (every directional solve is a set
-// of independent 1-D line solves, which is what lets one launch cover a whole pass of a whole
-// batch), Sec. 7 listing "compute_rhs" (the quadrature and the fuel update).
+// of independent 1-D line solves, which is what lets one launch cover every pass of a whole
+// batch).
 //
-// The step of one slot is six passes, each a set of independent tiles:
-//   Q   quadrature: F, Phi and the substep-1 right-hand side R, in (strip, segment) tiles
-//   X1  x lines of R with X_+ and of Phi with M^x, a warp's lines per tile (one lane per chunk)
-//   Y1  y lines (R -> T*, Phi -> phi^{n+1}, increment bases added), 32 / C columns per tile
-//       (one thread per chunk of a column)
-//   MV  substep-2 right-hand side R = theta F + (A_x (x) M^y) T* + (M^x (x) A_y) T*
-//   X2  x lines of R with M^x
-//   Y2  y lines with Y_+ (R -> T^{n+1}, base T*), guard
+// After the quadrature (F, Phi and the substep-1 right-hand side R of every slot), the step of
+// one slot is five passes, each a set of independent tiles:
+//   X1  x lines of R with X_+ and of Phi with M^x, in groups of rows
+//   Y1  y lines (R -> T*, Phi -> phi^{n+1}, increment bases added), in groups of columns
+//   MV  substep-2 right-hand side R = theta F + (A_x (x) M^y) T* + (M^x (x) A_y) T*, eight warp
+//       tiles per item
+//   X2  x lines of R with M^x, in groups of rows
+//   Y2  y lines with Y_+ (R -> T^{n+1}, base T*), guard, in groups of columns
 // The arithmetic of every tile is that of the per-pass kernels (the same device functions or
-// the same operations in the same order), so both paths give the same bits.
+// the same operations in the same order), so both step forms give the same bits.
 //
-// Work items (phase, slot, tile) are listed by the host in a wavefront over groups of slots:
-// at "time" t the list holds Q of group t, X1 of group t-1, ..., Y2 of group t-5, so the
-// intermediate fields of about six groups are live at once (sized to stay in L2), and
-// consecutive items are independent.  A warp claims the next tile from a ticket counter (the
-// next ticket is fetched while the current tile runs) and, before touching its inputs, waits
-// for the arrival counters of the tiles it reads:
-//   X1 rows     <- the Q segments that cover them (every strip)
+// Work items (pass, slot, tile) are listed by the host in a wavefront over groups of slots: at
+// "time" t the list holds X1 of group t, Y1 of group t-1, ..., Y2 of group t-4, so the fields of
+// about five groups are live at once (sized to stay in the L2 cache: a slot's intermediate
+// fields go from one pass to the next through L2, not HBM), and consecutive items are
+// independent.  A CTA claims the next item from a ticket counter (the next ticket is fetched
+// while the current item runs) and, before touching its inputs, waits for the arrival counters
+// of the tiles it reads:
 //   Y1 columns  <- every X1 row group of its array
 //   MV strip    <- the Y1 column groups that cover its columns and halo
 //   X2 rows     <- the MV segments that cover them (every strip)
 //   Y2 columns  <- every X2 row group
 // A tile waits only for tiles with smaller tickets, which are running or done when it is
 // claimed, so the launch always makes progress whatever the number of resident CTAs.
-// Producers release (stores, __syncwarp, fence, counter add); consumers acquire (ld.acquire on
-// the counter, __syncwarp) and read data produced in this launch through L2 (ld.global.cg),
+// Producers release (stores, barrier, fence, counter add); consumers acquire (ld.acquire on
+// the counter, barrier) and read data produced in this launch through L2 (ld.global.cg),
 // never through the read-only path.  Every wait is bounded by the handle's wait limit (the
 // SM's global timer); a wait that gives up sets the slot's timeout bit and the launch-wide
 // abort flag, after which every remaining item is skipped, so a failure costs one limit.
@@ -40,24 +40,22 @@
 
 #include "wf.h"
 #include "wf_line_blocks.cuh"
-#include "wf_rhs_stream.cuh"
 
 namespace wf {
 
 namespace {
 
-constexpr int kPT = 256;  // threads per CTA (two CTAs per SM: sixteen warps, 128 registers each)
+constexpr int kPT = 256;  // threads per CTA
 
-enum { PH_Q = 0, PH_X1 = 1, PH_Y1 = 2, PH_MV = 3, PH_X2 = 4, PH_Y2 = 5, PH_N = 6 };
+enum { PH_X1 = 0, PH_Y1 = 1, PH_MV = 2, PH_X2 = 3, PH_Y2 = 4, PH_N = 5 };
 
 // Offsets (ints) of one slot's arrival counters.
 struct CntLayout {
-    int qseg, x1, y1col, mvseg, x2, done, stride;
+    int x1, y1col, mvseg, x2, done, stride;
 };
 
 template <typename P>
 struct PersistArgs {
-    StreamArgs<P> q;  // quadrature (slot-0 pointers)
     FastArgs<P> x1, y1, x2, y2;
     // substep-2 right-hand side
     const P* mT;
@@ -68,11 +66,8 @@ struct PersistArgs {
     int mv_nstrips, mv_nsegs;
     long long sbytes;
     int Nx, Ny, pitch;
-    int nq;        // Q warp tiles per slot (nstrips * nsegs of the quadrature)
     int nxg, nyg;  // row groups of the x passes, column groups of the y passes
     int vec;       // rows 16-byte aligned: stage x lines with 16-byte loads
-    int wsm_floats;  // per-warp shared memory of the quadrature (wind factors)
-    int warp_smem;   // bytes of shared memory of each warp (its tiles' rows, factors, wind rows)
     const int4* items;
     const int* nitems;
     int* ctl;  // [0] ticket, [1] abort flag
@@ -150,60 +145,6 @@ __device__ __forceinline__ void arrive(int* c) {
     atomicAdd(c, 1);
 }
 
-// ---- quadrature tile (one warp) -----------------------------------------------------------
-template <int PD, int WR>
-__device__ void q_tile(const PersistArgs<float>& A, int z, int w, float* wsm) {
-    const int lane = threadIdx.x & 31;
-    const long long off = (long long)z * A.sbytes;
-    StreamArgs<float> a = A.q;
-    a.T = shift(a.T, off);
-    a.phi = shift(a.phi, off);
-    a.F = shift(a.F, off);
-    a.Phi = shift(a.Phi, off);
-    a.R = shift(a.R, off);
-    a.A1 = shift(a.A1, off);
-    a.B1 = shift(a.B1, off);
-    a.A2 = shift(a.A2, off);
-    a.B2 = shift(a.B2, off);
-    a.fxq = shift(a.fxq, off);
-    a.gxq = shift(a.gxq, off);
-    a.fyq = shift(a.fyq, off);
-    a.gyq = shift(a.gyq, off);
-    const int sg = w / a.nstrips, strip = w - sg * a.nstrips;
-    const int X0 = strip * (32 - PD);
-    int Y0, Y1;
-    bool yint = false;
-    if (!a.split) {
-        Y0 = sg * a.seg;
-        Y1 = min(Y0 + a.seg, a.Ny);
-    } else if (sg == 0) {
-        Y0 = 0;
-        Y1 = 2 * PD;
-    } else if (sg == a.nsegs - 1) {
-        Y0 = a.Ny - 2 * PD;
-        Y1 = a.Ny;
-    } else {
-        Y0 = 2 * PD + (sg - 1) * a.seg;
-        Y1 = min(Y0 + a.seg, a.Ny - 2 * PD);
-        yint = true;
-    }
-    if (yint && strip >= a.s_lo && strip < a.s_hi)
-        stream_strip_pairs<PD, WR, false>(a, A.q.it, A.q.pr, lane, X0, Y0, Y1, wsm);
-    else if (yint)
-        stream_strip_pairs<PD, WR, true>(a, A.q.it, A.q.pr, lane, X0, Y0, Y1, wsm);
-    else
-        stream_strip<float, PD, WR, false>(a, A.q.it, lane, X0, Y0, Y1);
-}
-
-// quadrature segment holding DOF row r
-template <typename P, int PD>
-__device__ __forceinline__ int q_seg_of(const StreamArgs<P>& q, int r) {
-    if (!q.split) return r / q.seg;
-    if (r < 2 * PD) return 0;
-    if (r >= q.Ny - 2 * PD) return q.nsegs - 1;
-    return 1 + (r - 2 * PD) / q.seg;
-}
-
 // ---- x-line tile (whole CTA): G lines of one array -----------------------------------------
 // The operations of k_xsolve_warp (without the fused right-hand side); rows are staged from L2
 // with plain loads (they were written by other CTAs of this launch).  `restage`: the factors in
@@ -236,7 +177,7 @@ __device__ void x_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int
         }
     }
     if (restage) stage_factors<P, PD>(v, mmax, fm, tid, nt);
-    __syncwarp();
+    __syncthreads();
     const int k = lane & ((1 << a.lsh) - 1);
     const int r = (warp << (5 - a.lsh)) + (lane >> a.lsh);
     const bool active = r < rows && k < C;
@@ -262,7 +203,7 @@ __device__ void x_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int
     P tn[PD], bp[PD];
     interface_solve<P, PD>(ch, k < C ? k : 0, mmax, fm.S, fm.E, top, bot, nxt_top, prv_bot, tn, bp);
     if (active) spike_fix<P, PD>(g, m, fm.S + t * mmax * FacW<PD>::S, tn, bp);
-    __syncwarp();
+    __syncthreads();
     if (sizeof(P) == 4 && A.vec) {
         const int n4 = (N + 3) >> 2;
         for (int i = tid; i < rows * n4; i += nt) {
@@ -302,7 +243,7 @@ __device__ void y_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int
     const size_t pitch = (size_t)a.pitch;
     P* g = buf + (size_t)(thr ? tid : 0) * mpad;
     if (restage) stage_factors<P, PD>(v, mmax, fm, tid, nt);
-    __syncwarp();
+    __syncthreads();
     if (thr) {
         const P* Fk = fm.F + t * mmax * NF;
         P prev[PD];
@@ -327,7 +268,7 @@ __device__ void y_tile(const PersistArgs<P>& A, const FastArgs<P>& a, int z, int
         }
         lu_backward<P, PD>(g, m, fm.U + t * mmax * NU);
     }
-    __syncwarp();
+    __syncthreads();
     if (!valid) return;  // no barrier follows in this tile
     const P* gn = buf + (size_t)((k + 1 < C ? k + 1 : k) * G + c) * mpad;
     const P* gp = buf + (size_t)((k > 0 ? k - 1 : k) * G + c) * mpad + (base - PD);
@@ -462,11 +403,6 @@ struct MvRows {
 };
 
 // ---- the kernel ----------------------------------------------------------------------------
-// Every warp is a worker: it claims the next tile of the ticket order (any pass), waits for the
-// tiles it reads, runs it in its own shared-memory region and signals its arrival; nothing but
-// __syncwarp synchronises threads, so sixteen warps per SM work on whatever is ready and the
-// ALU-heavy quadrature tiles of one group of slots run beside the memory-bound line tiles of
-// older groups.
 
 // a slot takes part in this step: active and its step budget not spent
 template <typename P>
@@ -474,8 +410,8 @@ __device__ __forceinline__ bool slot_live(const PersistArgs<P>& A, int z) {
     return ld_relaxed(A.active + z) != 0 && (!A.budget || ld_relaxed(A.budget + z) != 0);
 }
 
-// a tile of slot z finished; the slot's last tile of the step spends one step of its budget
-// (every tile of the slot has then started, so all of them saw the same budget)
+// an item of slot z finished; the slot's last item of the step spends one step of its budget
+// (every item of the slot has then started, so all of them saw the same budget)
 template <typename P>
 __device__ __forceinline__ void slot_done(const PersistArgs<P>& A, int* cnt, int z) {
     const int old = atomicAdd(cnt + A.cl.done, 1);
@@ -485,88 +421,95 @@ __device__ __forceinline__ void slot_done(const PersistArgs<P>& A, int* cnt, int
     }
 }
 
-template <int PD, int WR>
-__global__ void __launch_bounds__(kPT, 2) k_step_persist(const __grid_constant__ PersistArgs<float> A) {
-    using P = float;
+// CTAs per SM: three for FP32 with p <= 2 (80 registers: a few spills), else two (128 registers)
+template <typename P, int PD>
+struct LinesOcc {
+    static constexpr int value = (sizeof(P) == 4 && PD <= 2) ? 3 : 2;
+};
+
+template <typename P, int PD>
+__global__ void __launch_bounds__(kPT, LinesOcc<P, PD>::value) k_lines_persist(const __grid_constant__ PersistArgs<P> A) {
     constexpr int RS = MvRows<PD>::value;
     extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char* wsm = smem + (size_t)warp * A.warp_smem;
+    __shared__ int s_item, s_go, s_key;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n = *A.nitems;
-    int key = -1;  // (slot, pass, array) whose factors sit in this warp's shared memory
     int next = 0;
-    if (lane == 0) next = atomicAdd(A.ctl, 1);
-    next = __shfl_sync(0xffffffffu, next, 0);
+    if (tid == 0) {
+        next = atomicAdd(A.ctl, 1);
+        s_key = -1;
+    }
     for (;;) {
-        const int it = next;
+        if (tid == 0) {
+            s_item = next;
+            if (next < n) next = atomicAdd(A.ctl, 1);  // fetched while this item runs
+        }
+        __syncthreads();
+        const int it = s_item;
         if (it >= n) break;
         const int4 d = A.items[it];
         const int ph = d.x, z = d.y;
         int* cnt = A.cnt + (size_t)z * A.cl.stride;
         int* slot_status = shift(A.status, (long long)z * A.sbytes);
-        int go = 0;
-        if (lane == 0) {
-            next = atomicAdd(A.ctl, 1);  // fetched while this tile runs
+        if (tid == 0) {
+            // bit 1: the slot takes part in this step; bit 0: go ahead (its line inputs are ready)
             const bool live = slot_live(A, z);
             bool ok = live && !ld_relaxed(A.ctl + 1);
-            // the tiles this one reads
-            if (ok) {
-                if (ph == PH_X1 || ph == PH_X2) {
-                    const FastArgs<P>& a = ph == PH_X1 ? A.x1 : A.x2;
-                    const int j0 = d.w * a.G, j1 = min(a.nlines, j0 + a.G) - 1;
-                    if (ph == PH_X1) {
-                        for (int s = q_seg_of<P, PD>(A.q, j0); s <= q_seg_of<P, PD>(A.q, j1) && ok; ++s)
-                            ok = wait_count(A, cnt + A.cl.qseg + s, A.q.nstrips, slot_status);
-                    } else {
-                        for (int s = j0 / RS; s <= j1 / RS && ok; ++s)
-                            ok = wait_count(A, cnt + A.cl.mvseg + s, A.mv_nstrips, slot_status);
-                    }
+            if (ok && ph != PH_MV && ph != PH_X1) {
+                if (ph == PH_X2) {
+                    const int j0 = d.w * A.x2.G, j1 = min(A.x2.nlines, j0 + A.x2.G) - 1;
+                    for (int s = j0 / RS; s <= j1 / RS && ok; ++s)
+                        ok = wait_count(A, cnt + A.cl.mvseg + s, A.mv_nstrips, slot_status);
                 } else if (ph == PH_Y1) {
                     ok = wait_count(A, cnt + A.cl.x1 + d.z, A.nxg, slot_status);
-                } else if (ph == PH_Y2) {
+                } else {
                     ok = wait_count(A, cnt + A.cl.x2, A.nxg, slot_status);
-                } else if (ph == PH_MV) {
-                    const int st = d.z % A.mv_nstrips;
-                    const int xlo = max(0, st * (32 - 2 * PD) - PD), xhi = min(A.Nx - 1, st * (32 - 2 * PD) - PD + 31);
-                    for (int gq = xlo / A.y1.G; gq <= xhi / A.y1.G && ok; ++gq)
-                        ok = wait_count(A, cnt + A.cl.y1col + gq, 1, slot_status);
                 }
             }
-            go = (live ? 2 : 0) | (ok ? 1 : 0);
+            s_go = (live ? 2 : 0) | (ok ? 1 : 0);
         }
-        next = __shfl_sync(0xffffffffu, next, 0);
-        go = __shfl_sync(0xffffffffu, go, 0);
-        __syncwarp();  // orders the other lanes' loads after lane 0's acquire
-        if (!(go & 2)) continue;  // the slot does not take part in this step (not counted)
+        const int key = (z << 4) | (ph << 1) | d.z;  // ph <= 4, arr <= 1: bits 0..3
+        const bool restage = s_key != key;           // read before thread 0 updates it below
+        __syncthreads();
+        const int go = s_go;
         if (go & 1) {
-            if (ph == PH_Q) {
-                q_tile<PD, WR>(A, z, d.z, reinterpret_cast<float*>(wsm));
-                key = -1;  // the wind rows overwrite the staged factors
-                __syncwarp();
-                if (lane == 0) arrive(cnt + A.cl.qseg + d.z / A.q.nstrips);
-            } else if (ph == PH_MV) {
-                mv_tile<P, PD, RS>(A, z, d.z);
-                __syncwarp();
-                if (lane == 0) arrive(cnt + A.cl.mvseg + d.z / A.mv_nstrips);
+            if (ph == PH_MV) {
+                // eight warp tiles (d.z: the first); each warp waits for the Y1 column groups that
+                // cover its strip's columns and halo
+                const int w = d.z + warp;
+                if (w < A.mv_nstrips * A.mv_nsegs) {
+                    const int st = w % A.mv_nstrips;
+                    const int xlo = max(0, st * (32 - 2 * PD) - PD), xhi = min(A.Nx - 1, st * (32 - 2 * PD) - PD + 31);
+                    int ok = 1;
+                    if (lane == 0)
+                        for (int gq = xlo / A.y1.G; gq <= xhi / A.y1.G && ok; ++gq)
+                            ok = wait_count(A, cnt + A.cl.y1col + gq, 1, slot_status) ? 1 : 0;
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    __syncwarp();  // orders the other lanes' loads after lane 0's acquire
+                    if (ok) {
+                        mv_tile<P, PD, RS>(A, z, w);
+                        __syncwarp();
+                        if (lane == 0) arrive(cnt + A.cl.mvseg + w / A.mv_nstrips);
+                    }
+                }
             } else {
                 const int arr = d.z, tile = d.w;
-                const int k2 = (z << 4) | (ph << 1) | arr;  // ph <= 5: bits 1..3
                 if (ph == PH_X1 || ph == PH_X2) {
                     const FastArgs<P>& a = ph == PH_X1 ? A.x1 : A.x2;
-                    x_tile<P, PD>(A, a, z, arr, tile * a.G, wsm, k2 != key, lane, 32);
-                    __syncwarp();
-                    if (lane == 0) arrive(cnt + (ph == PH_X1 ? A.cl.x1 + arr : A.cl.x2));
+                    x_tile<P, PD>(A, a, z, arr, tile * a.G, smem, restage, tid, kPT);
+                    __syncthreads();
+                    if (tid == 0) arrive(cnt + (ph == PH_X1 ? A.cl.x1 + arr : A.cl.x2));
                 } else {
                     const FastArgs<P>& a = ph == PH_Y1 ? A.y1 : A.y2;
-                    y_tile<P, PD, 16>(A, a, z, arr, tile, wsm, k2 != key, lane, 32);
-                    __syncwarp();
-                    if (lane == 0 && ph == PH_Y1 && arr == 0) arrive(cnt + A.cl.y1col + tile);
+                    y_tile<P, PD, 16>(A, a, z, arr, tile, smem, restage, tid, kPT);
+                    __syncthreads();
+                    if (tid == 0 && ph == PH_Y1 && arr == 0) arrive(cnt + A.cl.y1col + tile);
                 }
-                key = k2;
+                if (tid == 0) s_key = key;
             }
         }
-        if (lane == 0) slot_done(A, cnt, z);
-        __syncwarp();  // the warp's shared memory is reused by its next tile
+        if (tid == 0 && (go & 2)) slot_done(A, cnt, z);
+        __syncthreads();  // s_item, s_key and the shared memory are reused by the next item
     }
 }
 
@@ -581,8 +524,7 @@ int sm_count() {
 // Line-pass kernel arguments of the persistent tiles (compact factors only).
 template <typename P, int PD>
 bool fill_line(const LineArgs& la, bool xdir, int G_req, FastArgs<P>& f, size_t* smem) {
-    constexpr int W = 2 * PD + 1;
-    (void)W;
+    const size_t kSmemBudget = (size_t)(220 * 1024) / LinesOcc<P, PD>::value;  // per CTA
     const Chunks& ch = la.f[0].ch;
     for (int q = 0; q < la.narr; ++q)
         if (!la.f[q].compact || la.f[q].ch.base != ch.base || la.f[q].ch.C != ch.C) return false;
@@ -606,6 +548,8 @@ bool fill_line(const LineArgs& la, bool xdir, int G_req, FastArgs<P>& f, size_t*
     f.b = la.b;
     f.mpad = (ch.base > ch.last ? ch.base : ch.last) | 1;
     if (xdir) {
+        // as the per-pass x pass: lines per warp by the chunk count, the shared-memory row stride
+        // spreading a warp's lines over the banks, up to eight warps' lines per tile
         int lsh = ch.C <= 8 ? 3 : (ch.C <= 16 ? 4 : 5);
         if (la.rpw == 1) lsh = 5;
         else if (la.rpw == 2 && lsh < 4) lsh = 4;
@@ -615,95 +559,83 @@ bool fill_line(const LineArgs& la, bool xdir, int G_req, FastArgs<P>& f, size_t*
         int sp = la.pitch;
         if (L < slots)
             while (sp % (2 * L) != L || (sp * sizeof(P)) % 16 != 0) ++sp;
-        const int G = lpw;  // a tile is one warp's lines
-        (void)G_req;
+        int G = (kPT / 32) * lpw;
+        if (G_req > 0 && G_req < G) G = (G_req + lpw - 1) / lpw * lpw;
+        auto need = [&](int g) { return (size_t)g * sp * sizeof(P) + fbytes; };
+        while (G > lpw && need(G) > kSmemBudget) G = ((G / 2) + lpw - 1) / lpw * lpw;
+        if (need(G) > kSmemBudget) return false;
         f.G = G;
         f.lsh = lsh;
         f.sp = sp;
-        *smem = (size_t)G * sp * sizeof(P) + fbytes;
+        *smem = need(G);
     } else {
-        // a tile is one warp: G columns x C chunks of threads
-        int G = 32 / ch.C;
-        if (G_req > 0 && G_req < G) G = G_req;
-        if (G < 1) return false;
+        int G = G_req > 0 ? G_req : kPT;
+        while (G > 1 && G * ch.C > kPT) G /= 2;
+        if (G * ch.C > kPT) return false;
+        auto need = [&](int g) { return fbytes + (size_t)g * ch.C * f.mpad * sizeof(P); };
+        while (G > 1 && need(G) > kSmemBudget) G /= 2;
+        if (need(G) > kSmemBudget) return false;
         f.G = G;
-        *smem = fbytes + (size_t)G * ch.C * f.mpad * sizeof(P);
+        *smem = need(G);
     }
     return true;
 }
 
-template <int PD, int WR>
+template <typename P, int PD>
 cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, cudaStream_t s) {
-    PersistArgs<float> A;
+    PersistArgs<P> A;
     memset(&A, 0, sizeof(A));
-    const int sms = sm_count();
-    // quadrature segments: as in the per-pass kernel, tall enough for few items, short enough to
-    // give every CTA work
-    const int nstrips = (h.q.Nx + (32 - PD) - 1) / (32 - PD);
-    int seg = 64;
-    while (seg > 16 && (long)nstrips * ((h.q.Ny + seg - 1) / seg) * h.nslots < 16L * sms) seg /= 2;
-    if (h.seg > 0) seg = h.seg;
-    fill_stream_args<float, PD>(h.q, seg, A.q);
     size_t sx1 = 0, sy1 = 0, sx2 = 0, sy2 = 0;
-    if (!fill_line<float, PD>(h.x1, true, h.xG, A.x1, &sx1) || !fill_line<float, PD>(h.y1, false, h.yG, A.y1, &sy1) ||
-        !fill_line<float, PD>(h.x2, true, h.xG, A.x2, &sx2) || !fill_line<float, PD>(h.y2, false, h.yG, A.y2, &sy2))
+    if (!fill_line<P, PD>(h.x1, true, h.xG, A.x1, &sx1) || !fill_line<P, PD>(h.y1, false, h.yG, A.y1, &sy1) ||
+        !fill_line<P, PD>(h.x2, true, h.xG, A.x2, &sx2) || !fill_line<P, PD>(h.y2, false, h.yG, A.y2, &sy2))
         return cudaErrorNotSupported;
     if (A.y1.G != A.y2.G || A.x1.G != A.x2.G) return cudaErrorNotSupported;
     constexpr int RS = MvRows<PD>::value;
-    A.mT = (const float*)h.mv.T;
-    A.mF = (const float*)h.mv.F;
-    A.mR = (float*)h.mv.R;
-    A.mA1 = (const float*)h.mv.A1;
-    A.mB1 = (const float*)h.mv.B1;
-    A.mA2 = (const float*)h.mv.A2;
-    A.mB2 = (const float*)h.mv.B2;
-    A.mFscale = (float)h.mv.Fscale;
-    A.mc1 = (float)h.mv.c1;
-    A.mc2 = (float)h.mv.c2;
+    A.mT = (const P*)h.mv.T;
+    A.mF = (const P*)h.mv.F;
+    A.mR = (P*)h.mv.R;
+    A.mA1 = (const P*)h.mv.A1;
+    A.mB1 = (const P*)h.mv.B1;
+    A.mA2 = (const P*)h.mv.A2;
+    A.mB2 = (const P*)h.mv.B2;
+    A.mFscale = (P)h.mv.Fscale;
+    A.mc1 = (P)h.mv.c1;
+    A.mc2 = (P)h.mv.c2;
     A.mv_nstrips = (h.mv.Nx + (32 - 2 * PD) - 1) / (32 - 2 * PD);
     A.mv_nsegs = (h.mv.Ny + RS - 1) / RS;
-    A.sbytes = h.q.b.sbytes;
-    A.Nx = h.q.Nx;
-    A.Ny = h.q.Ny;
-    A.pitch = h.q.pitch;
-    A.nq = A.q.nstrips * A.q.nsegs;
+    A.sbytes = h.mv.b.sbytes;
+    A.Nx = h.mv.Nx;
+    A.Ny = h.mv.Ny;
+    A.pitch = h.mv.pitch;
     A.nxg = (h.x1.nlines + A.x1.G - 1) / A.x1.G;
     A.nyg = (h.y1.nlines + A.y1.G - 1) / A.y1.G;
-    bool vec = (h.q.pitch % 4) == 0 && (A.sbytes % 16) == 0;
+    bool vec = sizeof(P) == 4 && (h.mv.pitch % 4) == 0 && (A.sbytes % 16) == 0;
     for (const LineArgs* la : {&h.x1, &h.x2})
         for (int q = 0; q < la->narr; ++q) vec = vec && ((uintptr_t)la->in[q] % 16 == 0) && ((uintptr_t)la->out[q] % 16 == 0);
     A.vec = vec ? 1 : 0;
-    A.wsm_floats = WR > 0 ? 2 * WR * (PD + 1) * (seg + PD) : 0;
     CntLayout cl;
-    cl.qseg = 0;
-    cl.x1 = cl.qseg + A.q.nsegs;
+    cl.x1 = 0;
     cl.y1col = cl.x1 + 2;
     cl.mvseg = cl.y1col + A.nyg;
     cl.x2 = cl.mvseg + A.mv_nsegs;
     cl.done = cl.x2 + 1;
     cl.stride = (cl.done + 1 + 31) & ~31;  // 128-byte blocks per slot
     A.cl = cl;
-    // shared memory of each warp: the largest of its tiles' needs (line rows and factors, or the
-    // quadrature's wind rows)
-    size_t wsm = std::max(std::max(sx1, sx2), std::max(sy1, sy2));
-    wsm = std::max(wsm, (size_t)A.wsm_floats * sizeof(float));
-    wsm = (wsm + 127) & ~(size_t)127;
-    A.warp_smem = (int)wsm;
-    const size_t smem = (size_t)(kPT / 32) * wsm;
-    if (smem > 110 * 1024) return cudaErrorNotSupported;  // two CTAs per SM
-    plan->nq = A.nq;
-    plan->nmv = A.mv_nstrips * A.mv_nsegs;
+    const size_t smem = std::max(std::max(sx1, sx2), std::max(sy1, sy2));
+    const int nmv8 = (A.mv_nstrips * A.mv_nsegs + 7) / 8;
+    plan->nq = 0;
+    plan->nmv = nmv8;
     plan->nxg = A.nxg;
     plan->nyg = A.nyg;
     plan->narr1 = h.x1.narr;
     plan->cstride = cl.stride;
-    plan->items_per_slot = plan->nq + plan->nmv + 2 * A.nxg + 2 * A.nyg + A.nxg + A.nyg;
-    plan->seg = seg;
+    plan->items_per_slot = 2 * A.nxg + 2 * A.nyg + nmv8 + A.nxg + A.nyg;
+    plan->seg = 0;
     plan->xG = A.x1.G;
     plan->yG = A.y1.G;
     plan->smem = smem;
     if (!launch) return cudaSuccess;
-    auto kern = k_step_persist<PD, WR>;
+    auto kern = k_lines_persist<P, PD>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -724,7 +656,7 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h.cnt, 0, (size_t)h.nslots_cap * cl.stride * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    const int grid = per_sm * sms;
+    const int grid = per_sm * sm_count();
     kern<<<grid, kPT, smem, s>>>(A);
     count_launches(1);
     return cudaGetLastError();
@@ -732,24 +664,27 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
 
 }  // namespace
 
-bool persist_supported(int prec, int p, int wind_rank) { return prec == 0 && (p == 1 || p == 2) && wind_rank <= 2; }
+bool persist_supported(int prec, int p, int wind_rank) {
+    (void)prec;
+    (void)wind_rank;
+    return p >= 1 && p <= 3;
+}
 
 cudaError_t persist_step(const PersistHost& h, PersistPlan* plan, bool launch, cudaStream_t s) {
-    if (!persist_supported(h.prec, h.p, h.q.wind_rank)) return cudaErrorNotSupported;
     PersistPlan dummy;
     if (!plan) plan = &dummy;
-#define WF_PS(PD, WR) return persist_typed<PD, WR>(h, plan, launch, s)
-    if (h.p == 1) {
-        switch (h.q.wind_rank) {
-            case 0: WF_PS(1, 0);
-            case 1: WF_PS(1, 1);
-            case 2: WF_PS(1, 2);
+#define WF_PS(P, PD) return persist_typed<P, PD>(h, plan, launch, s)
+    if (h.prec == 0) {
+        switch (h.p) {
+            case 1: WF_PS(float, 1);
+            case 2: WF_PS(float, 2);
+            case 3: WF_PS(float, 3);
         }
     } else {
-        switch (h.q.wind_rank) {
-            case 0: WF_PS(2, 0);
-            case 1: WF_PS(2, 1);
-            case 2: WF_PS(2, 2);
+        switch (h.p) {
+            case 1: WF_PS(double, 1);
+            case 2: WF_PS(double, 2);
+            case 3: WF_PS(double, 3);
         }
     }
 #undef WF_PS
@@ -772,9 +707,6 @@ int persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs,
             for (int k = g * gs; k < std::min(nslots, (g + 1) * gs); ++k) {
                 const int z = slots[k];
                 switch (ph) {
-                    case PH_Q:
-                        for (int i = 0; i < plan.nq; ++i) put(PH_Q, z, i, 0);
-                        break;
                     case PH_X1:
                         for (int arr = 0; arr < plan.narr1; ++arr)
                             for (int i = 0; i < plan.nxg; ++i) put(PH_X1, z, arr, i);
@@ -784,7 +716,7 @@ int persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs,
                             for (int i = 0; i < plan.nyg; ++i) put(PH_Y1, z, arr, i);
                         break;
                     case PH_MV:
-                        for (int i = 0; i < plan.nmv; ++i) put(PH_MV, z, i, 0);
+                        for (int i = 0; i < plan.nmv; ++i) put(PH_MV, z, 8 * i, 0);
                         break;
                     case PH_X2:
                         for (int i = 0; i < plan.nxg; ++i) put(PH_X2, z, 0, i);

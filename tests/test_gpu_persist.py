@@ -1,12 +1,13 @@
-"""The persistent step (one launch per step over every active slot) against the per-pass launches.
+"""The persistent form (the quadrature launch, then one launch over every line pass of every active
+slot) against the per-pass launches.
 
 The persistent kernel runs the tiles of the per-pass kernels (the same device functions or the
 same operations in the same order) under a different schedule: work items claimed from a
 ticket counter in a wavefront over groups of slots, with per-slot arrival counters between the
 passes.  Its results must therefore equal the per-pass launches bit for bit whatever the
-schedule (group size, segment height, lines per tile, slots joining and leaving), and sit
-within the parity bars of the FP64 oracle.  A zero wait limit makes its counter waits give up:
-the step reports WF_ETIMEOUT, nothing hangs, and the handle steps normally afterwards.
+schedule (group size, lines per tile, slots joining and leaving), in FP32 and FP64, p = 1..3,
+and sit within the parity bars of the FP64 oracle.  A zero wait limit makes its counter waits
+give up: the step reports WF_ETIMEOUT, nothing hangs, and the handle steps normally afterwards.
 """
 import numpy as np
 import pytest
@@ -24,9 +25,10 @@ def wf():
     return need_gpu()
 
 
-def _run(wf, scs, steps, form, shape=(0, 0, 0, 0, 0, 0, 0, 0), active=None, wind_rank=True):
+def _run(wf, scs, steps, form, shape=(0, 0, 0, 0, 0, 0, 0, 0), active=None, prec=None):
     sc0 = scs[0]
-    prm = wf.wf_params_default(Lx=sc0.Lx, Ly=sc0.Ly, wind_x=sc0.wind[0], wind_y=sc0.wind[1], precision=wf.WF_FP32)
+    prec = wf.WF_FP32 if prec is None else prec
+    prm = wf.wf_params_default(Lx=sc0.Lx, Ly=sc0.Ly, wind_x=sc0.wind[0], wind_y=sc0.wind[1], precision=prec)
     b = wf.Batch(sc0.nx, sc0.ny, sc0.p, sc0.dt, prm, capacity=len(scs))
     for k, sc in enumerate(scs):
         b.load_scenario(k, sc, active=True if active is None else bool(active[k]))
@@ -46,20 +48,23 @@ def _scs(n, p, k, seed, rank=True):
                           wind_perturbation=0.1 if (rank and i % 2 == 0) else 0.0) for i in range(k)]
 
 
-@pytest.mark.parametrize("n,p,k", [(40, 2, 1), (96, 2, 3), (150, 2, 2), (61, 1, 3), (7, 2, 2), (300, 2, 1)])
-def test_persistent_equals_per_pass_bitwise(wf, n, p, k):
+@pytest.mark.parametrize("n,p,k,prec", [(40, 2, 1, "fp32"), (96, 2, 3, "fp32"), (150, 2, 2, "fp32"), (61, 1, 3, "fp32"),
+                                        (7, 2, 2, "fp32"), (300, 2, 1, "fp32"), (70, 3, 3, "fp32"), (90, 2, 3, "fp64"),
+                                        (50, 3, 2, "fp64"), (33, 1, 2, "fp64")])
+def test_persistent_equals_per_pass_bitwise(wf, n, p, k, prec):
     scs = _scs(n, p, k, 900 + n + p)
-    st1, a = _run(wf, scs, 4, PER_PASS)
-    st2, b = _run(wf, scs, 4, PERSIST)
+    P = wf.WF_FP32 if prec == "fp32" else wf.WF_FP64
+    st1, a = _run(wf, scs, 4, PER_PASS, prec=P)
+    st2, b = _run(wf, scs, 4, PERSIST, prec=P)
     assert st1 == wf.WF_OK and st2 == wf.WF_OK
     for i in range(k):
         assert np.array_equal(a[i][0], b[i][0]) and np.array_equal(a[i][1], b[i][1]), i
 
 
 @pytest.mark.parametrize("shape", [(0, 0, 16, 0, 0, 0, 0, 1), (8, 4, 32, 1, 0, 0, 0, 2), (2, 16, 128, 2, 0, 0, 0, 5),
-                                   (32, 1, 20, 4, 0, 0, 0, 3)])
+                                   (32, 1, 20, 4, 0, 0, 0, 3), (4, 2, 0, 0, 0, 0, 0, 64)])
 def test_persistent_schedules_bitwise(wf, shape):
-    # group size, segment height, lines per tile and lines per warp change the schedule only
+    # group size, lines per tile and lines per warp change the schedule only
     scs = _scs(120, 2, 5, 950, rank=False)
     st1, ref = _run(wf, scs, 3, PER_PASS)
     st2, got = _run(wf, scs, 3, PERSIST, shape=shape)
