@@ -521,6 +521,7 @@ RhsArgs rhs_args(wf_handle* h, const void* T, void* F, void* Phi, void* R, doubl
     a.aux = h->aux;
     a.ev_fork = h->ev_fork;
     a.ev_join = h->ev_join;
+    a.single = 0;
     a.tx = h->dx.itab;
     a.ty = h->dy.itab;
     a.phys = h->phys;
@@ -678,7 +679,9 @@ int prepare_persist(wf_handle* h) {
     for (int z = 0; z < h->S; ++z)
         if (h->active_host[z]) act.push_back(z);
     // room for every slot active, so that slots joining later need no reallocation
-    const size_t cap = std::max<size_t>(1, (size_t)h->S * plan.items_per_slot);
+    // at most one item per tile
+    const size_t most = (size_t)plan.narr1 * (plan.nxg + plan.nyg) + (plan.nmv + 7) / 8 + plan.nxg + plan.nyg;
+    const size_t cap = std::max<size_t>(1, (size_t)h->S * most);
     const size_t need_cnt = (size_t)h->S * plan.cstride;
     if (cap > h->p_items_cap || need_cnt > h->p_cnt_cap || !h->p_ctl) {
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;
@@ -698,10 +701,12 @@ int prepare_persist(wf_handle* h) {
         drop_graphs(h);  // captured graphs hold the old buffers
     }
     std::vector<int4> items(cap);
-    const int n = persist_items(plan, act.data(), (int)act.size(), persist_group(h), items.data(), (int)cap);
-    if ((size_t)n > cap) return WF_ECUDA;
-    WF_TRY(cudaMemcpyAsync(h->p_items, items.data(), sizeof(int4) * std::max(n, 1), cudaMemcpyHostToDevice, h->stream));
-    WF_TRY(cudaMemcpyAsync(h->p_ctl + 2, &n, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    int counts[2] = {0, 0};  // items, items of one slot
+    counts[0] = persist_items(plan, act.data(), (int)act.size(), persist_group(h), items.data(), (int)cap, &counts[1]);
+    if ((size_t)counts[0] > cap) return WF_ECUDA;
+    WF_TRY(cudaMemcpyAsync(h->p_items, items.data(), sizeof(int4) * std::max(counts[0], 1), cudaMemcpyHostToDevice,
+                           h->stream));
+    WF_TRY(cudaMemcpyAsync(h->p_ctl + 2, counts, sizeof(counts), cudaMemcpyHostToDevice, h->stream));
     WF_TRY(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
     h->p_dirty = false;
     return WF_OK;
@@ -745,6 +750,7 @@ cudaError_t enqueue_step_body(wf_handle* h) {
         // the quadrature (and forcing) as in the per-pass form, then one launch for the rest
         const double th = 0.5 * h->dt;
         RhsArgs r1 = rhs_args(h, h->T, h->F, h->Phi, h->R, th, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
+        r1.single = 1;  // the quadrature in one launch: two launches per step in all
         auto l1 = [&] { return rhs_and_forcing(h, r1, h->R, th, h->F, 1.0); };
         if ((e = timed(h, S_RHS1, l1)) != cudaSuccess) return e;
         PersistHost ph;

@@ -150,6 +150,7 @@ struct RhsArgs {
     // there, beside its interior items (NULL: one stream)
     cudaStream_t aux;
     cudaEvent_t ev_fork, ev_join;
+    int single;  // FP32: all items in one launch (no second stream)
     ElemTabs tx, ty;
     Phys phys;
     Batch b;  // per scenario: T, phi, F, Phi, R, A1, B1, A2, B2, fxq, gxq, fyq, gyq
@@ -235,13 +236,13 @@ struct PersistHost {
     long long wait_ns;
     int* status;              // slot-0 flag word
     const int4* items;        // device: work items in their order
-    int* ctl;                 // device: [0] ticket, [1] abort flag, [2] number of items
+    int* ctl;                 // device: [0] ticket, [1] abort flag, [2] items, [3] items per slot
     int* cnt;                 // device: nslots_cap x cstride arrival counters
     const int* active;        // device: per-slot activity flags (an inactive slot's items are skipped)
     int* budget;              // device: per-slot step budgets, or NULL (a spent budget, 0, skips too)
 };
 struct PersistPlan {
-    int nq, nmv, nxg, nyg, narr1, cstride, items_per_slot, seg, xG, yG;
+    int nq, nmv, nxg, nyg, narr1, cstride, ctas, seg, xG, yG;
     size_t smem;
 };
 bool persist_supported(int prec, int p, int wind_rank);
@@ -249,8 +250,9 @@ bool persist_supported(int prec, int p, int wind_rank);
 // when the persistent form cannot take these arguments
 cudaError_t persist_step(const PersistHost& h, PersistPlan* plan, bool launch, cudaStream_t s);
 // work items of one step for the given active slots, groups of gs slots in wavefront order;
-// returns the count (entries past cap are not written)
-int persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs, int4* out, int cap);
+// returns the count (entries past cap are not written) and the items of one slot
+int persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs, int4* out, int cap,
+                  int* items_per_slot);
 
 // launch-shape helpers shared with the host driver
 int line_rows_per_cta(int prec);

@@ -70,14 +70,13 @@ struct PersistArgs {
     int vec;       // rows 16-byte aligned: stage x lines with 16-byte loads
     const int4* items;
     const int* nitems;
-    int* ctl;  // [0] ticket, [1] abort flag
+    int* ctl;  // [0] ticket, [1] abort flag, [2] items, [3] items per slot
     int* cnt;  // slot z's counters at cnt + z * cl.stride
     CntLayout cl;
     long long wait_ns;
     int* status;  // slot 0's flag word (slot z: z * sbytes further)
     const int* active;  // per-slot activity flags: an inactive slot's items are skipped
     int* budget;        // per-slot step budgets (NULL: none); a spent one (0) skips the slot too
-    int items_per_slot;
 };
 
 template <typename T>
@@ -415,7 +414,7 @@ __device__ __forceinline__ bool slot_live(const PersistArgs<P>& A, int z) {
 template <typename P>
 __device__ __forceinline__ void slot_done(const PersistArgs<P>& A, int* cnt, int z) {
     const int old = atomicAdd(cnt + A.cl.done, 1);
-    if (old == A.items_per_slot - 1 && A.budget) {
+    if (old == A.ctl[3] - 1 && A.budget) {
         const int b = A.budget[z];
         if (b > 0) A.budget[z] = b - 1;
     }
@@ -448,36 +447,29 @@ __global__ void __launch_bounds__(kPT, LinesOcc<P, PD>::value) k_lines_persist(c
         const int it = s_item;
         if (it >= n) break;
         const int4 d = A.items[it];
-        const int ph = d.x, z = d.y;
+        const int ph = d.x & 0xff, m = d.x >> 8, z = d.y;  // m: tiles of this item
         int* cnt = A.cnt + (size_t)z * A.cl.stride;
         int* slot_status = shift(A.status, (long long)z * A.sbytes);
         if (tid == 0) {
-            // bit 1: the slot takes part in this step; bit 0: go ahead (its line inputs are ready)
+            // bit 1: the slot takes part in this step; bit 0: go ahead (the inputs of the item's
+            // tiles are ready: Y1 and Y2 wait once here; X2 and MV per tile below)
             const bool live = slot_live(A, z);
             bool ok = live && !ld_relaxed(A.ctl + 1);
-            if (ok && ph != PH_MV && ph != PH_X1) {
-                if (ph == PH_X2) {
-                    const int j0 = d.w * A.x2.G, j1 = min(A.x2.nlines, j0 + A.x2.G) - 1;
-                    for (int s = j0 / RS; s <= j1 / RS && ok; ++s)
-                        ok = wait_count(A, cnt + A.cl.mvseg + s, A.mv_nstrips, slot_status);
-                } else if (ph == PH_Y1) {
-                    ok = wait_count(A, cnt + A.cl.x1 + d.z, A.nxg, slot_status);
-                } else {
-                    ok = wait_count(A, cnt + A.cl.x2, A.nxg, slot_status);
-                }
-            }
+            if (ok && ph == PH_Y1) ok = wait_count(A, cnt + A.cl.x1 + d.z, A.nxg, slot_status);
+            if (ok && ph == PH_Y2) ok = wait_count(A, cnt + A.cl.x2, A.nxg, slot_status);
             s_go = (live ? 2 : 0) | (ok ? 1 : 0);
         }
-        const int key = (z << 4) | (ph << 1) | d.z;  // ph <= 4, arr <= 1: bits 0..3
-        const bool restage = s_key != key;           // read before thread 0 updates it below
+        const int key = (z << 4) | (ph << 1) | (ph == PH_MV ? 0 : d.z);  // ph <= 4, arr <= 1: bits 0..3
+        bool restage = s_key != key;  // read before thread 0 updates it below
         __syncthreads();
         const int go = s_go;
         if (go & 1) {
             if (ph == PH_MV) {
-                // eight warp tiles (d.z: the first); each warp waits for the Y1 column groups that
-                // cover its strip's columns and halo
-                const int w = d.z + warp;
-                if (w < A.mv_nstrips * A.mv_nsegs) {
+                // warp tiles d.z + warp + 8k, k < m; each waits for the Y1 column groups that cover
+                // its strip's columns and halo
+                for (int k = 0; k < m; ++k) {
+                    const int w = d.z + warp + 8 * k;
+                    if (w >= A.mv_nstrips * A.mv_nsegs) break;
                     const int st = w % A.mv_nstrips;
                     const int xlo = max(0, st * (32 - 2 * PD) - PD), xhi = min(A.Nx - 1, st * (32 - 2 * PD) - PD + 31);
                     int ok = 1;
@@ -486,24 +478,39 @@ __global__ void __launch_bounds__(kPT, LinesOcc<P, PD>::value) k_lines_persist(c
                             ok = wait_count(A, cnt + A.cl.y1col + gq, 1, slot_status) ? 1 : 0;
                     ok = __shfl_sync(0xffffffffu, ok, 0);
                     __syncwarp();  // orders the other lanes' loads after lane 0's acquire
-                    if (ok) {
-                        mv_tile<P, PD, RS>(A, z, w);
-                        __syncwarp();
-                        if (lane == 0) arrive(cnt + A.cl.mvseg + w / A.mv_nstrips);
-                    }
+                    if (!ok) break;
+                    mv_tile<P, PD, RS>(A, z, w);
+                    __syncwarp();
+                    if (lane == 0) arrive(cnt + A.cl.mvseg + w / A.mv_nstrips);
                 }
             } else {
-                const int arr = d.z, tile = d.w;
-                if (ph == PH_X1 || ph == PH_X2) {
-                    const FastArgs<P>& a = ph == PH_X1 ? A.x1 : A.x2;
-                    x_tile<P, PD>(A, a, z, arr, tile * a.G, smem, restage, tid, kPT);
-                    __syncthreads();
-                    if (tid == 0) arrive(cnt + (ph == PH_X1 ? A.cl.x1 + arr : A.cl.x2));
-                } else {
-                    const FastArgs<P>& a = ph == PH_Y1 ? A.y1 : A.y2;
-                    y_tile<P, PD, 16>(A, a, z, arr, tile, smem, restage, tid, kPT);
-                    __syncthreads();
-                    if (tid == 0 && ph == PH_Y1 && arr == 0) arrive(cnt + A.cl.y1col + tile);
+                const int arr = d.z;
+                const bool xd = ph == PH_X1 || ph == PH_X2;
+                const FastArgs<P>& a = ph == PH_X1 ? A.x1 : (ph == PH_X2 ? A.x2 : (ph == PH_Y1 ? A.y1 : A.y2));
+                for (int k = 0; k < m; ++k) {
+                    const int tile = d.w + k;
+                    if (ph == PH_X2) {
+                        // the MV segments that cover this tile's rows (every strip)
+                        if (tid == 0) {
+                            const int j0 = tile * a.G, j1 = min(a.nlines, j0 + a.G) - 1;
+                            bool ok = true;
+                            for (int sgm = j0 / RS; sgm <= j1 / RS && ok; ++sgm)
+                                ok = wait_count(A, cnt + A.cl.mvseg + sgm, A.mv_nstrips, slot_status);
+                            s_go = ok ? 3 : 2;
+                        }
+                        __syncthreads();
+                        if (!(s_go & 1)) break;
+                    }
+                    if (xd) {
+                        x_tile<P, PD>(A, a, z, arr, tile * a.G, smem, restage, tid, kPT);
+                        __syncthreads();
+                        if (tid == 0) arrive(cnt + (ph == PH_X1 ? A.cl.x1 + arr : A.cl.x2));
+                    } else {
+                        y_tile<P, PD, 16>(A, a, z, arr, tile, smem, restage, tid, kPT);
+                        __syncthreads();
+                        if (tid == 0 && ph == PH_Y1 && arr == 0) arrive(cnt + A.cl.y1col + tile);
+                    }
+                    restage = false;  // the next tile of the item uses the same factors
                 }
                 if (tid == 0) s_key = key;
             }
@@ -622,19 +629,6 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     cl.stride = (cl.done + 1 + 31) & ~31;  // 128-byte blocks per slot
     A.cl = cl;
     const size_t smem = std::max(std::max(sx1, sx2), std::max(sy1, sy2));
-    const int nmv8 = (A.mv_nstrips * A.mv_nsegs + 7) / 8;
-    plan->nq = 0;
-    plan->nmv = nmv8;
-    plan->nxg = A.nxg;
-    plan->nyg = A.nyg;
-    plan->narr1 = h.x1.narr;
-    plan->cstride = cl.stride;
-    plan->items_per_slot = 2 * A.nxg + 2 * A.nyg + nmv8 + A.nxg + A.nyg;
-    plan->seg = 0;
-    plan->xG = A.x1.G;
-    plan->yG = A.y1.G;
-    plan->smem = smem;
-    if (!launch) return cudaSuccess;
     auto kern = k_lines_persist<P, PD>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -642,6 +636,18 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorNotSupported;
+    plan->nq = 0;
+    plan->nmv = A.mv_nstrips * A.mv_nsegs;  // warp tiles
+    plan->nxg = A.nxg;
+    plan->nyg = A.nyg;
+    plan->narr1 = h.x1.narr;
+    plan->cstride = cl.stride;
+    plan->ctas = per_sm * sm_count();
+    plan->seg = 0;
+    plan->xG = A.x1.G;
+    plan->yG = A.y1.G;
+    plan->smem = smem;
+    if (!launch) return cudaSuccess;
     A.items = h.items;
     A.nitems = h.ctl + 2;
     A.ctl = h.ctl;
@@ -650,7 +656,6 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     A.status = h.status;
     A.active = h.active;
     A.budget = h.budget;
-    A.items_per_slot = plan->items_per_slot;
     // every counter of this step starts at zero (ticket, abort flag, arrival counters)
     e = cudaMemsetAsync(h.ctl, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -692,13 +697,28 @@ cudaError_t persist_step(const PersistHost& h, PersistPlan* plan, bool launch, c
 }
 
 // Wavefront order of the work items over groups of `gs` active slots (see the top of the file).
-int persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs, int4* out, int cap) {
+// An item covers several consecutive tiles of one (pass, slot, array): about two items per CTA
+// in every pass over all active slots, so that a CTA stages an operator's factors once for
+// several tiles and the fixed costs of an item (claim, barriers, dependency check) amortise.
+int persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs, int4* out, int cap,
+                  int* items_per_slot) {
     if (gs < 1) gs = 1;
     const int ngroups = (nslots + gs - 1) / gs;
-    int n = 0;
-    auto put = [&](int ph, int z, int a, int b) {
-        if (n < cap) out[n] = make_int4(ph, z, a, b);
+    const long target = 2L * std::max(1, plan.ctas);
+    auto per_item = [&](long tiles_all, int most) {
+        return (int)std::max(1L, std::min((long)most, tiles_all / target));
+    };
+    const int tx = per_item((long)nslots * plan.narr1 * plan.nxg, plan.nxg);
+    const int ty = per_item((long)nslots * plan.narr1 * plan.nyg, plan.nyg);
+    const int mv8 = (plan.nmv + 7) / 8;  // CTA rounds of eight warp tiles
+    const int tm = per_item((long)nslots * mv8, mv8);
+    int n = 0, per_slot = 0;
+    auto put = [&](int ph, int m, int z, int a, int b) {
+        if (n < cap) out[n] = make_int4(ph | (m << 8), z, a, b);
         ++n;
+    };
+    auto tiles = [&](int ph, int z, int arr, int count, int per) {
+        for (int i = 0; i < count; i += per) put(ph, std::min(per, count - i), z, arr, i);
     };
     for (int t = 0; t < ngroups + PH_N - 1; ++t)
         for (int ph = 0; ph < PH_N; ++ph) {
@@ -706,27 +726,28 @@ int persist_items(const PersistPlan& plan, const int* slots, int nslots, int gs,
             if (g < 0 || g >= ngroups) continue;
             for (int k = g * gs; k < std::min(nslots, (g + 1) * gs); ++k) {
                 const int z = slots[k];
+                const int n0 = n;
                 switch (ph) {
                     case PH_X1:
-                        for (int arr = 0; arr < plan.narr1; ++arr)
-                            for (int i = 0; i < plan.nxg; ++i) put(PH_X1, z, arr, i);
+                        for (int arr = 0; arr < plan.narr1; ++arr) tiles(PH_X1, z, arr, plan.nxg, tx);
                         break;
                     case PH_Y1:
-                        for (int arr = 0; arr < plan.narr1; ++arr)
-                            for (int i = 0; i < plan.nyg; ++i) put(PH_Y1, z, arr, i);
+                        for (int arr = 0; arr < plan.narr1; ++arr) tiles(PH_Y1, z, arr, plan.nyg, ty);
                         break;
                     case PH_MV:
-                        for (int i = 0; i < plan.nmv; ++i) put(PH_MV, z, 8 * i, 0);
+                        for (int i = 0; i < mv8; i += tm) put(PH_MV, std::min(tm, mv8 - i), z, 8 * i, 0);
                         break;
                     case PH_X2:
-                        for (int i = 0; i < plan.nxg; ++i) put(PH_X2, z, 0, i);
+                        tiles(PH_X2, z, 0, plan.nxg, tx);
                         break;
                     case PH_Y2:
-                        for (int i = 0; i < plan.nyg; ++i) put(PH_Y2, z, 0, i);
+                        tiles(PH_Y2, z, 0, plan.nyg, ty);
                         break;
                 }
+                if (k == 0) per_slot += n - n0;
             }
         }
+    *items_per_slot = per_slot;
     return n;
 }
 

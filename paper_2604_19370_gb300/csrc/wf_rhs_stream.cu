@@ -44,9 +44,11 @@ namespace {
 // of the interior segments in the packed form with x tables in registers (on segments of
 // their own, shorter height) and the boundary segments in the general form.  One warp per
 // CTA, so that a warp slot frees as soon as its own item ends.
+// MODE 3 (FP32): the items of MODE 0 followed by those of MODE 1 in one launch at sixteen warps per
+// SM, for a step that must take one launch for its quadrature.
 template <typename P, int PD, int WR, int MODE>
 struct RhsOcc {
-    static constexpr int value = sizeof(P) != 4 || PD > 2 ? 1 : (MODE == 0 ? 16 : 12);
+    static constexpr int value = sizeof(P) != 4 || PD > 2 ? 1 : (MODE == 0 || MODE == 3 ? 16 : 12);
 };
 
 template <typename P, int PD, int WR, int MODE>
@@ -74,13 +76,17 @@ __global__ void __launch_bounds__(32, RhsOcc<P, PD, WR, MODE>::value) k_rhs_stre
     // item -> strip and segment; segments: 0 .. nseg_in-1 interior (height seg), nseg_in the
     // first 2p DOF rows, nseg_in+1 the last 2p (split), or plain pieces of height seg
     int sg, strip, seg = a.seg;
-    if (MODE == 0) {
+    // MODE 3: the first nsi * nseg_in items as MODE 0, the rest as MODE 1
+    const bool as0 = MODE == 0 || (MODE == 3 && item < nsi * nseg_in);
+    const int item1 = MODE == 3 ? item - nsi * nseg_in : item;
+    if (as0) {
         if (item >= nsi * nseg_in) return;  // whole warp leaves; no block barrier in this kernel
         sg = item / nsi;
         strip = a.s_lo + (item - sg * nsi);
-    } else if (MODE == 1) {
+    } else if (MODE == 1 || MODE == 3) {
         const int nb = a.nstrips - nsi;      // boundary strips: [0, s_lo) and [s_hi, nstrips)
         const int first = nb * a.nseg_b;     // boundary strips x interior segments of height
+        const int item = item1;
         if (item < first) {                  // seg_b, then every strip x the two boundary segments
             sg = item / nb;
             const int bs = item - sg * nb;
@@ -121,7 +127,7 @@ __global__ void __launch_bounds__(32, RhsOcc<P, PD, WR, MODE>::value) k_rhs_stre
         // FP32: interior strips of interior segments with constant tables (MODE 0), the other
         // strips of interior segments with x tables in registers, boundary segments general.
         // MODE 2 runs in FP32 only where no strip is interior.
-        if (MODE == 0)
+        if (as0)
             stream_strip_pairs<PD, WR, false>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1, wind_rows);
         else if (yint)
             stream_strip_pairs<PD, WR, true>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1, wind_rows);
@@ -183,6 +189,16 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
     const long n_side = (long)(a.nstrips - (a.s_hi - a.s_lo)) * a.nseg_b + 2L * a.nstrips;
     // FP32 only (FP64 runs every item in one launch): split launches when interior items exist
     if constexpr (sizeof(P) == 4) {
+        if (n_fast > 0 && r.single) {
+            // one launch: the interior items, then the others (a step form with one launch for
+            // its quadrature)
+            const size_t wb3 = wind_smem<P, PD, WR, 3>(a.seg);
+            if (wb3 == SIZE_MAX) return cudaErrorInvalidValue;
+            dim3 g3((unsigned)((n_fast + n_side + WARPS - 1) / WARPS), 1, r.b.S);
+            k_rhs_stream<P, PD, WR, 3><<<g3, 32 * WARPS, wb3, s>>>(a);
+            count_launches(1);
+            return cudaGetLastError();
+        }
         if (n_fast > 0) {
             // interior items in one launch, the rest in a second (their register budgets differ);
             // with the handle's second stream the two run side by side and join before returning
