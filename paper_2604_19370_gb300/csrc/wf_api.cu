@@ -590,14 +590,12 @@ cudaError_t rhs_and_forcing(wf_handle* h, const RhsArgs& r, void* out1, double s
 cudaError_t enqueue_step_body(wf_handle* h);
 void drop_graphs(wf_handle* h);
 
-// The persistent form (the quadrature launch, then one launch over every pass and active slot)
-// takes PR with one F per step; tuning value 6 picks it (2) or the per-pass launches (1); the
-// rule (0) takes it for batches (two slots or more), where its work order keeps each group of
-// slots' fields in L2 from one pass to the next.
+// The persistent form (one quadrature launch, then one launch over every line pass of every active
+// slot) takes PR with one F per step; tuning value 6 picks it (2) or the per-pass launches (1,
+// and the rule 0: measured faster on the ensemble and on a single domain).
 bool use_persist(const wf_handle* h) {
     if (h->noalloc_run || h->prm.scheme != WF_PR || h->prm.F_timing != WF_F_ONCE) return false;
     if (!persist_supported(h->prec, h->p, h->wr)) return false;
-    if (h->tune[6] == 0) return h->S >= 2;
     return h->tune[6] == 2;
 }
 
@@ -649,15 +647,12 @@ void persist_args(wf_handle* h, PersistHost* ph) {
     ph->budget = h->budget_on ? h->budget_dev : nullptr;
 }
 
-// Slots per group of the persistent order: about five groups are live at once; their fields (five
-// per slot) should take at most about half of the L2 cache.
+// Slots per group of the persistent order.  The rule is one group (the passes in order): groups
+// small enough for five of them to stay in L2 leave too few items per pass to fill the GPU, and
+// their tiles then wait on one another (measured on the 256-slot ensemble).
 int persist_group(const wf_handle* h) {
     if (h->tune[7] > 0) return h->tune[7];
-    int dev = 0, l2 = 126 << 20;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
-    const double slot = 5.0 * h->Ny * h->pitch * esize(h->prec);
-    const int g = (int)(0.5 * l2 / (5.0 * slot));
-    return std::max(1, std::min(g, h->S));
+    return h->S;
 }
 
 // Allocate the persistent buffers and upload the item list of the active slots when needed.

@@ -420,10 +420,10 @@ __device__ __forceinline__ void slot_done(const PersistArgs<P>& A, int* cnt, int
     }
 }
 
-// CTAs per SM: three for FP32 with p <= 2 (80 registers: a few spills), else two (128 registers)
+// CTAs per SM: four for FP32 with p <= 2 (64 registers: a few spills), else two (128 registers)
 template <typename P, int PD>
 struct LinesOcc {
-    static constexpr int value = (sizeof(P) == 4 && PD <= 2) ? 3 : 2;
+    static constexpr int value = (sizeof(P) == 4 && PD <= 2) ? 4 : 2;
 };
 
 template <typename P, int PD>
