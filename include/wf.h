@@ -240,7 +240,7 @@ int wf_launch_count(unsigned long long* n);
 
 /*
  * Launch-shape autotuner (no counterpart in the paper, whose solver runs on
- * CPU threads).  Nine values are tuned (int shape[9]):
+ * CPU threads).  Eight values are tuned (int shape[8]):
  *   shape[0]  lines per CTA of the first x pass of a step (rows staged per
  *             CTA; at most 8 warps' worth); lines per tile of both x passes of
  *             the persistent step,
@@ -259,14 +259,10 @@ int wf_launch_count(unsigned long long* n);
  *             persistent launch per step over every active slot (Peaceman-
  *             Rachford with one F per step, FP32, p <= 2, wind rank <= 2,
  *             no manufactured forcing; elsewhere the per-pass form runs);
- *   shape[7]  slots per group of the persistent step's work order (the
- *             passes of a group follow one another; default one group),
- *   shape[8]  x-pass form: 1 one CTA per group of lines, 2 persistent CTAs
- *             that walk their block of line groups with two row buffers (the
- *             next group's bulk copies land while the current one is solved);
+ *   shape[7]  slots per group of the persistent step's work order (the order
+ *             keeps about six groups' fields live, sized for the L2 cache);
  * 0 selects the built-in rule (shape[5]: inside the pass; shape[6]: the
- * per-pass launches; shape[8]: the pipelined x pass where the rows allow
- * bulk copies).
+ * persistent step where it applies).
  * Every value changes the schedule only: both right-hand-side placements and
  * both step forms perform the same operations in the same order, so the
  * results are the same bits.  wf_autotune tunes one value at a
@@ -282,9 +278,9 @@ int wf_launch_count(unsigned long long* n);
  * are captured again by the next wf_step) and discards kernel times
  * collected under wf_set_profiling.  No active slot: WF_OK, nothing tuned.
  * Errors: WF_EINVAL (reps outside 1..100), WF_ENOMEM, WF_ECUDA.
- * wf_get_tuning / wf_set_tuning read and write the nine values
- * (wf_set_tuning: shape[5], shape[6] and shape[8] 0..2, the others 0..1024,
- * else WF_EINVAL).
+ * wf_get_tuning / wf_set_tuning read and write the eight values
+ * (wf_set_tuning: shape[5] and shape[6] 0..2, the others 0..1024, else
+ * WF_EINVAL).
  */
 int wf_autotune(wf_handle* h, int reps);
 int wf_get_tuning(const wf_handle* h, int* shape);

@@ -32,7 +32,7 @@ using namespace wf;
 namespace {
 
 constexpr double kTmax = 1e5;  // guard on |T| (K)
-constexpr int kTune = 9;       // tuned launch shapes (wf_autotune)
+constexpr int kTune = 8;       // tuned launch shapes (wf_autotune)
 
 struct Arena {
     char* base = nullptr;
@@ -117,13 +117,12 @@ struct wf_handle {
     bool mms_on = false;       // manufactured-solution forcing (wf_set_mms)
     MmsArgs mms{};
     double* tdev = nullptr;    // device: start time of the next step (advanced only with forcing)
-    int tune[kTune] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // x lines per CTA (first x pass), y lines per
-                                           // CTA, quadrature segment rows, x lines per warp, x lines
+    int tune[kTune] = {0, 0, 0, 0, 0, 0, 0, 0};  // x lines per CTA (first x pass), y lines per CTA,
+                                           // quadrature segment rows, x lines per warp, x lines
                                            // per CTA of the second x pass, its right-hand side
                                            // (1 fused, 2 separate matvec), step form (1 per-pass
                                            // launches, 2 persistent), slots per group of the
-                                           // persistent order, x-pass form (1 one CTA per row
-                                           // group, 2 pipelined) (0: the launchers' rules)
+                                           // persistent order (0: the launchers' rules)
     // persistent step: work items, ticket / abort / item count, arrival counters (allocated on
     // first use); the item list is rebuilt when the active slots or the shapes change
     int4* p_items = nullptr;
@@ -538,7 +537,6 @@ LineArgs line_args(wf_handle* h, int xsite) {
     a.nlines = xdir ? h->Ny : h->Nx;
     a.G = xsite == 1 ? h->tune[0] : (xsite == 2 ? h->tune[4] : h->tune[1]);
     a.rpw = xdir ? h->tune[3] : 0;
-    a.pipe = xdir && h->tune[8] != 1;
     a.pitch = h->pitch;
     a.tmax = kTmax;
     a.tstatus = h->status;
@@ -1519,7 +1517,6 @@ int wf_autotune(wf_handle* h, int reps) {
     static const int kFuse[] = {0, 2};
     static const int kMode[] = {1, 2};
     static const int kGroup[] = {0, 1, 2, 4, 8, 16, 32, 64};
-    static const int kXForm[] = {1, 2};
     struct Axis {
         int q;
         const int* v;
@@ -1527,8 +1524,7 @@ int wf_autotune(wf_handle* h, int reps) {
     };
     const bool pers = persist_supported(h->prec, h->p, h->wr) && h->prm.scheme == WF_PR &&
                       h->prm.F_timing == WF_F_ONCE;
-    const Axis order[] = {{8, kXForm, 2},
-                          {6, kMode, pers ? 2 : 0},
+    const Axis order[] = {{6, kMode, pers ? 2 : 0},
                           {7, kGroup, pers && h->S > 1 ? (int)(sizeof(kGroup) / sizeof(int)) : 0},
                           {2, kSeg, (int)(sizeof(kSeg) / sizeof(int))},
                           {0, kLines, (int)(sizeof(kLines) / sizeof(int))},
@@ -1692,7 +1688,7 @@ int wf_get_tuning(const wf_handle* h, int* shape) {
 int wf_set_tuning(wf_handle* h, const int* shape) {
     if (!h || !shape) return WF_EINVAL;
     for (int q = 0; q < kTune; ++q)
-        if (shape[q] < 0 || shape[q] > (q == 5 || q == 6 || q == 8 ? 2 : 1024)) return WF_EINVAL;
+        if (shape[q] < 0 || shape[q] > (q == 5 || q == 6 ? 2 : 1024)) return WF_EINVAL;
     for (int q = 0; q < kTune; ++q) h->tune[q] = shape[q];
     drop_graphs(h);
     return WF_OK;

@@ -184,7 +184,6 @@ cudaError_t launch_advance_time(double* t, double dt, cudaStream_t s);
 struct LineArgs {
     int G;       // lines per CTA of the compact-factor kernels (0: the launcher's rule; else an upper bound)
     int rpw;     // x pass: lines per warp (0: as many as the chunks allow; 1, 2: at most that many)
-    int pipe;    // x pass: the pipelined persistent form (double-buffered row groups) where it applies
     int nlines;  // number of independent lines
     int pitch;   // row pitch of the fields (elements)
     int narr;    // 1 or 2 arrays (blockIdx.y)

@@ -17,8 +17,6 @@
 // mbarrier); neighbouring chunks exchange boundary values by warp shuffles.
 // y pass: a CTA owns G columns; lanes of neighbouring columns read and write
 // contiguous runs of G elements per row, 16 or 32 loads in flight per thread.
-#include <algorithm>
-
 #include "wf_internal.h"
 
 #include "wf_line_blocks.cuh"
@@ -249,158 +247,6 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
     }
 }
 
-// Pipelined x pass: a persistent CTA walks a contiguous block of (slot, array, row group) items in
-// slot-major order.  While it solves one group's lines (the operations of k_xsolve_warp, in the
-// same order) the bulk copies of the next group's rows land in the other of two row buffers, and
-// the solved rows leave by bulk store; the factors are staged only when the slot or the array's
-// operator changes.  Items of inactive slots are skipped.
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
-template <typename P, int PD>
-__global__ void __launch_bounds__(256) k_xsolve_pipe(const FastArgs<P> a, int ngroups, int nitems, int per_cta) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const Chunks ch = a.ch;
-    const int C = ch.C, base = ch.base, G = a.G, sp = a.sp;
-    const int mmax = base + 2 * PD;
-    const size_t row_bytes = (size_t)a.pitch * sizeof(P);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // two barriers
-    P* buf0 = reinterpret_cast<P*>(smem_raw + 128);
-    P* buf1 = buf0 + (size_t)G * sp;
-    const FacSmem<P, PD> fm(buf1 + (size_t)G * sp, mmax);
-    const int i0 = blockIdx.x * per_cta, i1 = min(nitems, i0 + per_cta);
-    if (i0 >= i1) return;
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    // item -> slot z, array arr, first line j0 (slot-major, then array, then row group)
-    auto decode = [&](int i, int& z, int& arr, int& j0) {
-        const int per_slot = ngroups * 2;
-        z = i / per_slot;
-        const int r = i - z * per_slot;
-        arr = r / ngroups;
-        j0 = (r - arr * ngroups) * G;
-    };
-    // next item at or after i that is live (an existing array of an active slot), or i1
-    auto next_live = [&](int i) {
-        for (; i < i1; ++i) {
-            int z, arr, j0;
-            decode(i, z, arr, j0);
-            if (arr >= (a.in[1] ? 2 : 1)) continue;
-            if (a.b.active && !a.b.active[z]) continue;
-            if (a.b.budget && !a.b.budget[z]) continue;
-            return i;
-        }
-        return i1;
-    };
-    auto view = [&](int z, int arr) {
-        const bool one = arr != 0;
-        const long long off = (long long)z * a.b.sbytes;
-        auto shc = [&](const P* p) { return p ? reinterpret_cast<const P*>(reinterpret_cast<const char*>(p) + off) : p; };
-        LineView<P> v{};
-        v.in = shc(one ? a.in[1] : a.in[0]);
-        v.out = const_cast<P*>(shc(one ? a.out[1] : a.out[0]));
-        v.luc = shc(one ? a.luc[1] : a.luc[0]);
-        v.spkc = shc(one ? a.spkc[1] : a.spkc[0]);
-        v.Ec = shc(one ? a.Ec[1] : a.Ec[0]);
-        v.tstatus = a.tstatus ? reinterpret_cast<int*>(reinterpret_cast<char*>(a.tstatus) + off) : nullptr;
-        return v;
-    };
-    // one thread arms a buffer's barrier with the group's bytes, warp 0 issues one copy per row
-    auto load = [&](int i, int b) {
-        int z, arr, j0;
-        decode(i, z, arr, j0);
-        const LineView<P> v = view(z, arr);
-        const int rows = min(G, a.nlines - j0);
-        P* buf = b ? buf1 : buf0;
-        if (warp == 0) {
-            if (lane == 0) mbar_expect_tx(bar + b, (uint32_t)(rows * row_bytes));
-            __syncwarp();
-            for (int r = lane; r < rows; r += 32)
-                bulk_load(buf + (size_t)r * sp, v.in + (size_t)(j0 + r) * a.pitch, (uint32_t)row_bytes, bar + b);
-        }
-    };
-    uint32_t par[2] = {0u, 0u};  // phase of each buffer's barrier that the next load completes
-    bool inflight[2] = {false, false};
-    int cur = next_live(i0);
-    if (cur < i1) {
-        load(cur, 0);
-        inflight[0] = true;
-    }
-    int b = 0, key = -1;
-    bool ok = true;
-    while (cur < i1) {
-        const int nxt = next_live(cur + 1);
-        // the other buffer's bulk store (the previous group) has read it: refill it
-        if (nxt < i1) {
-            if (warp == 0) bulk_wait_read_all();
-            __syncthreads();
-            load(nxt, b ^ 1);
-            inflight[b ^ 1] = true;
-        }
-        int z, arr, j0;
-        decode(cur, z, arr, j0);
-        const LineView<P> v = view(z, arr);
-        const int rows = min(G, a.nlines - j0);
-        P* rowbuf = b ? buf1 : buf0;
-        const int k2 = z * 2 + arr;
-        if (k2 != key) stage_factors<P, PD>(v, mmax, fm);
-        key = k2;
-        ok = __syncthreads_and(mbar_wait_bounded(bar + b, par[b], a.wait_ns) ? 1 : 0) != 0;
-        if (!ok) {
-            if (tid == 0 && v.tstatus) atomicOr(v.tstatus, 4);
-            break;
-        }
-        par[b] ^= 1u;
-        inflight[b] = false;
-        const int kk = lane & ((1 << a.lsh) - 1);
-        const int r = (warp << (5 - a.lsh)) + (lane >> a.lsh);
-        const bool active = r < rows && kk < C;
-        const int m = (kk < C - 1) ? base : ch.last;
-        P* g = rowbuf + (size_t)(r < rows ? r : 0) * sp + (size_t)kk * base;
-        const int t = chunk_type(ch, kk < C ? kk : 0);
-        if (active) {
-            lu_forward<P, PD>(g, m, fm.F + t * mmax * FacW<PD>::F);
-            lu_backward<P, PD>(g, m, fm.U + t * mmax * FacW<PD>::U);
-        }
-        __syncwarp();
-        P top[PD], bot[PD], nxt_top[PD], prv_bot[PD];
-#pragma unroll
-        for (int q = 0; q < PD; ++q) {
-            top[q] = active ? g[q] : P(0);
-            bot[q] = (active && kk + 1 < C) ? g[base - PD + q] : P(0);
-        }
-#pragma unroll
-        for (int q = 0; q < PD; ++q) {
-            nxt_top[q] = __shfl_down_sync(0xffffffffu, top[q], 1);
-            prv_bot[q] = __shfl_up_sync(0xffffffffu, bot[q], 1);
-        }
-        P tn[PD], bp[PD];
-        interface_solve<P, PD>(ch, kk < C ? kk : 0, mmax, fm.S, fm.E, top, bot, nxt_top, prv_bot, tn, bp);
-        if (active) spike_fix<P, PD>(g, m, fm.S + t * mmax * FacW<PD>::S, tn, bp);
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (warp == 0) {
-            for (int rr = lane; rr < rows; rr += 32)
-                bulk_store(v.out + (size_t)(j0 + rr) * a.pitch, rowbuf + (size_t)rr * sp, (uint32_t)row_bytes);
-            bulk_commit();
-        }
-        b ^= 1;
-        cur = nxt;
-    }
-    if (!ok) {
-        // give up: let the copies in flight land before the shared memory is released
-        if (inflight[0]) mbar_drain(bar, par[0]);
-        if (inflight[1]) mbar_drain(bar + 1, par[1]);
-    }
-    if (warp == 0) bulk_wait_all();  // the stores have left before the CTA exits
-}
-
 // y pass.  CTA = G columns x C chunks (blockDim = G*C <= 256); thread tid = k*G + c owns chunk k
 // of column c in its private shared-memory strip (odd stride: distinct banks).  The column values
 // are loaded 16 or 32 rows at a time and eliminated forward as they arrive, so the strip is written
@@ -584,29 +430,6 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         f.sp = sp;
         f.tsp = tsp;
         f.tma = aligned ? 1 : 0;
-        if (!pre && aligned && a.pipe) {
-            // pipelined form: two row buffers, factors once per slot and operator
-            const size_t psmem = 128 + 2 * (size_t)G * srow + fbytes;
-            if (psmem <= 227 * 1024) {
-                auto pk = k_xsolve_pipe<P, PD>;
-                cudaError_t e = cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
-                if (e != cudaSuccess) return e;
-                int per_sm = 0;
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pk, 32 * (G / lpw), psmem);
-                if (e != cudaSuccess) return e;
-                int sms = 152, dev = 0;
-                if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-                const int ngroups = (a.nlines + G - 1) / G;
-                const int nitems = ngroups * 2 * a.b.S;
-                const int ctas = std::max(1, per_sm) * sms;
-                // contiguous blocks of items; a few items per CTA so that the loads overlap the solves
-                const int per_cta = std::max(1, (nitems + ctas - 1) / ctas);
-                const int grid = (nitems + per_cta - 1) / per_cta;
-                pk<<<grid, 32 * (G / lpw), psmem, s>>>(f, ngroups, nitems, per_cta);
-                count_launches(1);
-                return cudaGetLastError();
-            }
-        }
         auto kern = pre ? k_xsolve_warp<P, PD, true> : k_xsolve_warp<P, PD, false>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -38,7 +38,7 @@ def test_shapes_do_not_change_results(wf, prec, scheme):
     sc = make_scenario("shape", 150, 2, 1e-3, 1, 91, wind=(1.2, -0.7), fuel_sigma=3.0)
     ref = None
     # every shape in both step forms (per-pass launches; the persistent launch where it applies)
-    for shape in [tuple(s6) + (form, 0, xf) for s6 in SHAPES for form in (1, 2) for xf in (1, 2)]:
+    for shape in [tuple(s6) + (form, 0) for s6 in SHAPES for form in (1, 2)]:
         sim = _sim(wf, sc, P, code)
         wf.wf_set_tuning(sim.h, shape)
         assert wf.wf_get_tuning(sim.h) == shape
@@ -80,7 +80,7 @@ def test_autotune_keeps_state_and_parity(wf):
     assert shape[0] in (0, 32, 16, 8, 4, 2, 1) and shape[1] in (0, 32, 16, 8, 4, 2, 1)
     assert shape[2] in (0, 128, 96, 80, 64, 56, 48, 40, 32, 28, 24, 21, 20, 16, 12) and shape[3] in (0, 1, 2, 4)
     assert shape[4] in (0, 32, 16, 8, 4, 2, 1) and shape[5] in (0, 2)
-    assert shape[6] in (0, 1, 2) and shape[7] in (0, 1, 2, 4, 8, 16, 32, 64) and shape[8] in (0, 1, 2)
+    assert shape[6] in (0, 1, 2) and shape[7] in (0, 1, 2, 4, 8, 16, 32, 64)
     T1, p1 = sim.state()
     assert np.array_equal(T0, T1) and np.array_equal(p0, p1)
     sim.step(4)
@@ -121,13 +121,11 @@ def test_tuning_argument_checks(wf):
     sim = _sim(wf, sc, wf.WF_FP32, wf.WF_PR)
     L = wf.lib()
     assert L.wf_autotune(sim.h, 0) == wf.WF_EINVAL
-    bad = (wf.ctypes.c_int * 9)(1, -1, 0, 0, 0, 0, 0, 0, 0)
+    bad = (wf.ctypes.c_int * 8)(1, -1, 0, 0, 0, 0, 0, 0)
     assert L.wf_set_tuning(sim.h, bad) == wf.WF_EINVAL
-    bad = (wf.ctypes.c_int * 9)(0, 0, 0, 0, 0, 3, 0, 0, 0)
+    bad = (wf.ctypes.c_int * 8)(0, 0, 0, 0, 0, 3, 0, 0)
     assert L.wf_set_tuning(sim.h, bad) == wf.WF_EINVAL
-    bad = (wf.ctypes.c_int * 9)(0, 0, 0, 0, 0, 0, 3, 0, 0)
-    assert L.wf_set_tuning(sim.h, bad) == wf.WF_EINVAL
-    bad = (wf.ctypes.c_int * 9)(0, 0, 0, 0, 0, 0, 0, 0, 3)
+    bad = (wf.ctypes.c_int * 8)(0, 0, 0, 0, 0, 0, 3, 0)
     assert L.wf_set_tuning(sim.h, bad) == wf.WF_EINVAL
     sim.close()
 
