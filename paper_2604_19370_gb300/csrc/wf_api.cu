@@ -641,6 +641,7 @@ void persist_args(wf_handle* h, PersistHost* ph) {
     ph->wait_ns = h->wait_ns;
     ph->status = h->status;
     ph->items = h->p_items;
+    ph->cnt_cap = h->p_cnt_cap;
     ph->ctl = h->p_ctl;
     ph->cnt = h->p_cnt;
     ph->active = h->active_dev;
@@ -1591,6 +1592,7 @@ int wf_autotune(wf_handle* h, int reps) {
                     const int i = (round & 1) ? ax.n - 1 - n : n;
                     for (int q = 0; q < kTune; ++q) h->tune[q] = best[q];
                     h->tune[ax.q] = ax.v[i];
+                    h->p_dirty = true;  // the persistent form's plan follows the shapes
                     double t = 0.0;
                     rc = measure(&t);
                     if (rc == WF_OK && t < tmin[i]) tmin[i] = t;

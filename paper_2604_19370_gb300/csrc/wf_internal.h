@@ -238,6 +238,7 @@ struct PersistHost {
     const int4* items;        // device: work items in their order
     int* ctl;                 // device: [0] ticket, [1] abort flag, [2] items, [3] items per slot
     int* cnt;                 // device: nslots_cap x cstride arrival counters
+    size_t cnt_cap;           // ints allocated at cnt (the launch refuses a larger plan)
     const int* active;        // device: per-slot activity flags (an inactive slot's items are skipped)
     int* budget;              // device: per-slot step budgets, or NULL (a spent budget, 0, skips too)
 };

@@ -648,6 +648,8 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     plan->yG = A.y1.G;
     plan->smem = smem;
     if (!launch) return cudaSuccess;
+    // the item list and counters were laid out for this plan (prepare step): never write past them
+    if (!h.items || !h.ctl || !h.cnt || (size_t)h.nslots_cap * cl.stride > h.cnt_cap) return cudaErrorInvalidValue;
     A.items = h.items;
     A.nitems = h.ctl + 2;
     A.ctl = h.ctl;
