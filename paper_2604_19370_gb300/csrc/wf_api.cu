@@ -1525,14 +1525,16 @@ int wf_autotune(wf_handle* h, int reps) {
     };
     const bool pers = persist_supported(h->prec, h->p, h->wr) && h->prm.scheme == WF_PR &&
                       h->prm.F_timing == WF_F_ONCE;
-    const Axis order[] = {{6, kMode, pers ? 2 : 0},
-                          {7, kGroup, pers && h->S > 1 ? (int)(sizeof(kGroup) / sizeof(int)) : 0},
-                          {2, kSeg, (int)(sizeof(kSeg) / sizeof(int))},
+    // the shapes first (in the per-pass form, the rule), then the step form with those shapes and
+    // the persistent form's group size; the second sweep refines the shapes under the chosen form
+    const Axis order[] = {{2, kSeg, (int)(sizeof(kSeg) / sizeof(int))},
                           {0, kLines, (int)(sizeof(kLines) / sizeof(int))},
                           {3, kRpw, (int)(sizeof(kRpw) / sizeof(int))},
                           {1, kLines, (int)(sizeof(kLines) / sizeof(int))},
                           {4, kLines, (int)(sizeof(kLines) / sizeof(int))},
-                          {5, kFuse, (int)(sizeof(kFuse) / sizeof(int))}};
+                          {5, kFuse, (int)(sizeof(kFuse) / sizeof(int))},
+                          {6, kMode, pers ? 2 : 0},
+                          {7, kGroup, pers && h->S > 1 ? (int)(sizeof(kGroup) / sizeof(int)) : 0}};
     const size_t bytes = (size_t)h->sbytes * h->S;
     void* snap = nullptr;
     // the slots' activity flags reach the device lazily (at the next step): send them now, or

@@ -5,9 +5,16 @@ the bench times (steps replayed from the step graph; the ensemble in one batch h
 The oracle runs on a window of elements around each fire (tests/long_oracle.py; the windowing is
 pinned against a full-domain run in tests/test_oracle_window.py), started in background
 processes at collection; the comparison covers the window's interior, at the fire's hottest
-phase and after the last step, with the element-wise bars of the parity tests.  Outside the
-window the GPU state must have stayed ambient.  The 800 K isotherm of the FP32 run must lie
-within one element of the oracle's while the front exists.
+phase and after the last step.  Outside the window the GPU state must have stayed ambient.
+
+FP64 is held to the element-wise bars of the parity tests (1e-10).  FP32 is held to the bars
+the target states for it — relative L2 of T <= 1e-4 and the 800 K isotherm within one element
+of the oracle's while the front exists — and to max |phi - phi_o| <= 1e-5, but element by element
+on T only to 5e-2 of the fire's departure from ambient: over hundreds of steps a Gauss point whose
+temperature sits within FP32 rounding of the ignition temperature can burn in one precision and
+not the other, and such a flip changes that point's source by K_ign T exp(-T_a/T) (about 3.9e4 K/s
+at 800 K), about 19 K over a half step, i.e. about 1e-2 of a 1600 K departure; 5e-2 allows a few
+such flips along the front.  The errors at each snapshot are printed.
 """
 import numpy as np
 import pytest
@@ -19,6 +26,7 @@ from scenarios import config_c2, config_c4
 pytestmark = pytest.mark.gpu
 
 EDGE = 16  # coefficients left out at each edge of a window
+FP32_LONG_DT = 5e-2  # element-wise bar on T of the FP32 all-steps runs (see the module docstring)
 
 
 @pytest.fixture(scope="module")
@@ -60,7 +68,10 @@ def test_c2_all_steps(wf, prec):
         T, phi = sim.state()
         To, po = ref[snap]
         Tg, pg = _cut(T, org, n, sc.p), _cut(phi, org, n, sc.p)
-        assert_parity(_inner(Tg, n, sc.p), _inner(pg, n, sc.p), _inner(To, n, sc.p), _inner(po, n, sc.p), prec)
+        e = parity_errors(_inner(Tg, n, sc.p), _inner(pg, n, sc.p), _inner(To, n, sc.p), _inner(po, n, sc.p))
+        print(f"c2 {prec} step {snap}: {e}")
+        assert_parity(_inner(Tg, n, sc.p), _inner(pg, n, sc.p), _inner(To, n, sc.p), _inner(po, n, sc.p), prec,
+                      dT_bar=None if prec == "fp64" else FP32_LONG_DT)
         assert _outside_ambient(T, org, n, sc.p, 1e-9 if prec == "fp64" else 1e-3), snap
         if snap == 150:
             assert To.max() > 1500.0  # the fire burns inside the window
@@ -96,7 +107,10 @@ def test_c4_all_steps_sampled_members(wf):
                 T, phi = b.state(k)
                 To, po = ref[snap]
                 Tg, pg = _cut(T, org, n, 2), _cut(phi, org, n, 2)
-                assert_parity(_inner(Tg, n, 2), _inner(pg, n, 2), _inner(To, n, 2), _inner(po, n, 2), "fp32")
+                e = parity_errors(_inner(Tg, n, 2), _inner(pg, n, 2), _inner(To, n, 2), _inner(po, n, 2))
+                print(f"{name} step {snap}: {e}")
+                assert_parity(_inner(Tg, n, 2), _inner(pg, n, 2), _inner(To, n, 2), _inner(po, n, 2), "fp32",
+                              dT_bar=FP32_LONG_DT)
                 assert _outside_ambient(T, org, n, 2, 1e-3), (name, snap)
         for k in range(S):
             T, _ = b.state(k)
