@@ -166,8 +166,23 @@ def _traffic_record(kernel_site: str, workload: str):
         return None
 
 
+def soak(run_chunk, seconds: float) -> int:
+    """Untimed steps for about `seconds` just before the timed region.
+
+    nvidia-smi samples every 200 ms, so a timed region of a few milliseconds holds one sample at
+    most; the sampler runs over this soak and the timed region together, with the GPU under the
+    same load throughout.  run_chunk() enqueues some steps and waits for them; returns the calls.
+    """
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        run_chunk()
+        n += 1
+    return n
+
+
 class ClockSampler:
-    """nvidia-smi clock and throttle sampling during the timed region."""
+    """nvidia-smi clock and throttle sampling over the soak and the timed region."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -221,7 +236,8 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons),
+                "window": "soak steps of the same workload, then the timed region"}
 
 
 def _dist():
@@ -439,8 +455,20 @@ def run_ensemble(args) -> None:
         wf.wf_set_profiling(b.h, False)
         return e0.elapsed_time(e1) * 1e-3
 
-    # timed region: K steps replayed from the step graph (the production launch path)
+    def chunk():
+        with torch.cuda.stream(stream):
+            b.step(64)
+        stream.synchronize()
+
+    # timed region: K steps replayed from the step graph (the production launch path); the soak
+    # runs first under the clock sampler, then the initial states are put back and warmed up again
     with ClockSampler(local) as clk:
+        soak(chunk, args.clock_soak)
+        for k, sc in enumerate(scs):
+            b.load_scenario(k, sc)
+        with torch.cuda.stream(stream):
+            b.step(args.warmup)
+        stream.synchronize()
         secs = timed(False)
     status = wf.wf_sync(b.h)
     value, slowest = whole_job_throughput(dofs * args.steps, secs, world, dev)
@@ -576,10 +604,25 @@ def fp64_c2_extra(wf, dev, args) -> dict:
     stream.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev) / K
     st = sim.sync()
+    # end to end through the FP64 host boundary: state from pinned float64 arrays, one step, state back
+    n = sc.dofs
+    hT = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hP = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hT.numpy()[:] = sc.T0.ravel()
+    hP.numpy()[:] = sc.fuel0.ravel()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        wf.wf_set_state_ptr(sim.h, hT.data_ptr(), hP.data_ptr(), n)
+        wf.wf_step(sim.h, 1)
+        wf.wf_get_state_ptr(sim.h, hT.data_ptr(), hP.data_ptr(), n)
+    e2e_s = (time.perf_counter() - t0) / K
     sim.close()
     out = {"workload": "c2_1024x1024_p2_pr_fp64", "value": sc.dofs / (ms * 1e-3), "unit": UNIT,
            "ms_per_step": ms, "steps": K, "l2": "flushed before every timed step (256 MiB write)",
-           "status": wf.wf_strerror(st)}
+           "status": wf.wf_strerror(st),
+           "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 16 * n,
+                   "ms_per_step": e2e_s * 1e3, "host_dtype": "float64"}}
     if not args.no_cpu_baseline:
         ks = 2
         o = oracle_runs([("c2", 0, 0, ks, "pr", True)], 1)[0]
@@ -631,8 +674,22 @@ def run_single(args) -> None:
         wf.wf_set_profiling(sim.h, False)
         return float(sum(a.elapsed_time(b) for a, b in ev))
 
+    # the soak steps a twin of the domain (same shapes), so the timed one keeps its state and status
+    twin = wf.simulation_from_scenario(sc, precision=prec, scheme=scheme)
+    wf.wf_set_stream(twin.h, stream.cuda_stream)
+    wf.wf_set_tuning(twin.h, tuning)
+
+    def chunk():
+        with torch.cuda.stream(stream):
+            for _ in range(16):
+                flush.zero_()
+                wf.wf_step(twin.h, 1)
+        stream.synchronize()
+
     with ClockSampler(local) as clk:
+        soak(chunk, args.clock_soak)
         ms_total = run_steps(False)
+    twin.close()
     status = sim.sync()
     value, slowest_s = whole_job_throughput(sc.dofs * args.steps, ms_total * 1e-3, world, dev)
     ms_per_step = slowest_s * 1e3 / args.steps
@@ -816,6 +873,8 @@ def main():
     ap.add_argument("--scenarios", type=int, default=256)
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--max-slots", type=int, default=16)
+    ap.add_argument("--clock-soak", type=float, default=1.0,
+                    help="seconds of untimed steps sampled with the timed region by the clock sampler")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

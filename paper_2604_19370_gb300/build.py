@@ -65,7 +65,7 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     """
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "wf.h"))
     key = _stamp_key(nvcc, headers)
     try:

@@ -55,6 +55,7 @@ struct Op {
     void *bandP = nullptr, *luP = nullptr, *spkP = nullptr, *EP = nullptr;
     double *luc64 = nullptr, *spkc64 = nullptr, *Ec64 = nullptr;
     void *lucP = nullptr, *spkcP = nullptr, *EcP = nullptr;
+    void* fpadP = nullptr;  // compact factors in the line kernels' padded layout (working precision)
 };
 
 struct Dir {
@@ -271,6 +272,7 @@ void layout_slot(wf_handle* h, Arena& A) {
                 o.spkcP = o.spkc64;
                 o.EcP = o.Ec64;
             }
+            o.fpadP = o.factored ? (void*)A.take<char>(fac_pad_elems(h->p, o.mmax) * es) : nullptr;
         }
     }
     const size_t qx = (size_t)kMaxRank * h->nx * h->q, qy = (size_t)kMaxRank * h->ny * h->q;
@@ -436,6 +438,11 @@ int build_factors(wf_handle* h, int slot, double tol, double* worst) {
             }
         }
     }
+    for (Dir* d : ds)
+        for (Op& o : d->op)
+            if (o.factored)
+                WF_TRY(launch_pad_factors(h->prec, h->p, o.mmax, at(h, o.lucP, slot), at(h, o.spkcP, slot),
+                                          at(h, o.EcP, slot), at(h, o.fpadP, slot), s));
     WF_TRY(cudaStreamSynchronize(s));
     return *worst > tol ? WF_ETRUNC : WF_OK;
 }
@@ -453,6 +460,7 @@ FactorV fv(const Op& o, const Chunks& ch) {
     f.luc = o.lucP;
     f.spkc = o.spkcP;
     f.Ec = o.EcP;
+    f.fpad = o.compact ? o.fpadP : nullptr;
     return f;
 }
 

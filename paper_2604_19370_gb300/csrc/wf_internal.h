@@ -86,6 +86,9 @@ struct FactorV {
     const void* luc;
     const void* spkc;
     const void* Ec;
+    // the compact factors already in the padded shared-memory layout of the line kernels
+    // (fac_pad_elems elements; one bulk copy stages them), or NULL
+    const void* fpad;
 };
 
 // ---- tables and factorisation (FP64, wf_tables.cu) ---------------------------------
@@ -210,6 +213,11 @@ cudaError_t launch_ysolve(int prec, int p, const LineArgs& a, cudaStream_t s);
 // compact-factor form (wf_linefast.cu); returns cudaErrorNotSupported when it cannot
 // take the arguments (factors not compact, more than 256 threads, shared memory)
 cudaError_t launch_line_fast(int prec, int p, bool xdir, const LineArgs& a, cudaStream_t s);
+// elements of the padded factor block of one operator (chunk rows mmax), and the kernel that
+// writes it from the compact factors (luc, spkc, Ec in the working precision)
+size_t fac_pad_elems(int p, int mmax);
+cudaError_t launch_pad_factors(int prec, int p, int mmax, const void* luc, const void* spkc, const void* Ec,
+                               void* fpad, cudaStream_t s);
 
 // R = Fscale F + c1 (A1 (x) B1) T + c2 (A2 (x) B2) T   (A2 may be NULL)
 struct MatvecArgs {

@@ -23,6 +23,7 @@ struct FastArgs {
     const P* luc[2];
     const P* spkc[2];
     const P* Ec[2];
+    const P* fpad[2];   // padded factor blocks (FacSmem layout), or NULL: staged element by element
     int* status;
     int* tstatus;       // x pass: bit 4 set when the staging wait gave up
     long long wait_ns;  // x pass: limit of the staging wait
@@ -45,7 +46,7 @@ struct LineView {
     const P* base;
     const P* premul;
     P prescale;
-    const P *luc, *spkc, *Ec;
+    const P *luc, *spkc, *Ec, *fpad;
     int* status;
     int* tstatus;
     const P *preT, *preF, *pA1, *pB1, *pA2, *pB2;
@@ -63,6 +64,7 @@ __device__ __forceinline__ LineView<P> scene_line(const FastArgs<P>& a, int arr)
     v.luc = scene_ptr(one ? a.luc[1] : a.luc[0], a.b);
     v.spkc = scene_ptr(one ? a.spkc[1] : a.spkc[0], a.b);
     v.Ec = scene_ptr(one ? a.Ec[1] : a.Ec[0], a.b);
+    v.fpad = scene_ptr(one ? a.fpad[1] : a.fpad[0], a.b);
     v.status = scene_ptr(a.status, a.b);
     v.tstatus = scene_ptr(a.tstatus, a.b);
     v.preT = scene_ptr(a.preT, a.b);
@@ -381,14 +383,14 @@ __device__ __forceinline__ void interface_solve(const Chunks& ch, int k, int mma
 // Compact factors (global, [3][mmax][2p+1], [3][mmax][2p], [3][p*p]) into the padded
 // shared-memory layout of FacSmem; padding entries are zero.
 // (threads tid of nt stage the factors; the CTA's threads by default)
+// The same layout is written once per operator into global memory (the padded factor block,
+// launch_pad_factors), from where a kernel stages it with one bulk copy.
 template <typename P, int PD>
-__device__ __forceinline__ void stage_factors(const LineView<P>& v, int mmax, const FacSmem<P, PD>& fm, int tid,
-                                              int nt) {
+__device__ __forceinline__ void fill_factors(const P* __restrict__ g1, const P* __restrict__ g2,
+                                             const P* __restrict__ g3, int mmax, const FacSmem<P, PD>& fm, int tid,
+                                             int nt) {
     constexpr int W = 2 * PD + 1, S2 = 2 * PD;
     constexpr int NF = FacW<PD>::F, NU = FacW<PD>::U, NS = FacW<PD>::S;
-    const P* __restrict__ g1 = v.luc;
-    const P* __restrict__ g2 = v.spkc;
-    const P* __restrict__ g3 = v.Ec;
     const int rows = 3 * mmax;
     for (int i = tid; i < rows * NF; i += nt) {
         const int r = i / NF, c = i - r * NF;
@@ -403,6 +405,11 @@ __device__ __forceinline__ void stage_factors(const LineView<P>& v, int mmax, co
         fm.S[i] = c < S2 ? g2[r * S2 + c] : P(0);
     }
     for (int i = tid; i < 3 * PD * PD; i += nt) fm.E[i] = g3[i];
+}
+template <typename P, int PD>
+__device__ __forceinline__ void stage_factors(const LineView<P>& v, int mmax, const FacSmem<P, PD>& fm, int tid,
+                                              int nt) {
+    fill_factors<P, PD>(v.luc, v.spkc, v.Ec, mmax, fm, tid, nt);
 }
 template <typename P, int PD>
 __device__ __forceinline__ void stage_factors(const LineView<P>& v, int mmax, const FacSmem<P, PD>& fm) {

@@ -58,6 +58,10 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
     // rows of the halo block that exist (pre): lo .. hi-1
     const int lo = max(0, j0 - PD), hi = min(a.nlines, j0 + rows + PD);
 
+    // factors: one bulk copy of the operator's padded block beside the rows, else staged element
+    // by element
+    const bool fbulk = a.tma && v.fpad != nullptr;
+    const uint32_t fbytes = (uint32_t)(fac_elems<PD>(mmax) * sizeof(P));
     bool staged = true;
     if (pre) {
         // halo rows outside the domain read as zero; so do the PD columns left of every row
@@ -78,10 +82,11 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
             mbar_fence_init();
             const uint32_t bytes = (uint32_t)(rows * row_bytes);
             const uint32_t tbytes = pre ? (uint32_t)((hi - lo) * row_bytes) : 0u;
-            mbar_expect_tx(bar, bytes + tbytes);
+            mbar_expect_tx(bar, bytes + tbytes + (fbulk ? fbytes : 0u));
         }
         __syncwarp();
         if (warp == 0) {
+            if (fbulk && lane == 31) bulk_load(fm.F, v.fpad, fbytes, bar);
             for (int r = lane; r < rows; r += 32)
                 bulk_load(rowbuf + (size_t)r * sp, in + (size_t)(j0 + r) * a.pitch, (uint32_t)row_bytes, bar);
             if (pre)
@@ -97,7 +102,7 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
                 for (int x = tid; x < N; x += blockDim.x)
                     tbuf[(size_t)(r - (j0 - PD)) * tsp + HO + x] = v.preT[(size_t)r * a.pitch + x];
     }
-    stage_factors<P, PD>(v, mmax, fm);
+    if (!fbulk) stage_factors<P, PD>(v, mmax, fm);
     if (pre) {
         P* bco = fm.end();
         for (int i = tid; i < rows * W; i += blockDim.x) {
@@ -108,6 +113,7 @@ __global__ void __launch_bounds__(256) k_xsolve_warp(const FastArgs<P> a) {
     }
     __syncthreads();  // mbarrier initialised, factors staged, halo zeroed
     if (a.tma) staged = mbar_wait_bounded(bar, 0, a.wait_ns);
+    staged = __syncthreads_and(staged);  // one decision for the whole CTA (barriers follow)
     if (!staged) {
         // drain the copies in flight before the shared memory is released; the step's output is
         // not valid (bit 4 invalidates it for the whole handle)
@@ -262,7 +268,8 @@ __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
     const Chunks ch = a.ch;
     const int N = ch.N, C = ch.C, base = ch.base, G = a.G, mpad = a.mpad;
     const int mmax = base + 2 * PD;
-    const FacSmem<P, PD> fm(reinterpret_cast<P*>(smem_raw), mmax);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // 16 bytes: the factors' mbarrier
+    const FacSmem<P, PD> fm(reinterpret_cast<P*>(smem_raw + 16), mmax);
     P* buf = fm.end();  // [nt][mpad]
     const int arr = blockIdx.y;
     const int k = tid / G, c = tid - k * G;
@@ -276,8 +283,29 @@ __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
     const size_t pitch = (size_t)a.pitch;
     P* g = buf + (size_t)tid * mpad;
 
-    stage_factors<P, PD>(v, mmax, fm);
+    // factors: one bulk copy of the operator's padded block (bounded wait; a CTA that gives up
+    // stores nothing and sets bit 4 of the slot's flag word), else staged element by element
+    const bool fbulk = v.fpad != nullptr;
+    if (fbulk) {
+        if (tid == 0) {
+            const uint32_t fbytes = (uint32_t)(fac_elems<PD>(mmax) * sizeof(P));
+            mbar_init(bar, 1);
+            mbar_fence_init();
+            mbar_expect_tx(bar, fbytes);
+            bulk_load(fm.F, v.fpad, fbytes, bar);
+        }
+    } else {
+        stage_factors<P, PD>(v, mmax, fm);
+    }
     __syncthreads();
+    if (fbulk) {
+        const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0, a.wait_ns));
+        if (!ok) {
+            mbar_drain(bar, 0);
+            if (tid == 0 && v.tstatus) atomicOr(v.tstatus, 4);
+            return;
+        }
+    }
     const P* __restrict__ pre = v.premul;
     const P* Fk = fm.F + t * mmax * NF;
     P prev[PD];
@@ -374,6 +402,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         f.luc[q] = (const P*)a.f[q].luc;
         f.spkc[q] = (const P*)a.f[q].spkc;
         f.Ec[q] = (const P*)a.f[q].Ec;
+        f.fpad[q] = (const P*)a.f[q].fpad;
     }
     f.status = a.status;
     f.tstatus = a.tstatus;
@@ -441,7 +470,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         while (G > 1 && G * ch.C > 256) G /= 2;
         const int nt = G * ch.C;
         if (nt > 256) return cudaErrorNotSupported;
-        const size_t smem = fbytes + (size_t)nt * f.mpad * sizeof(P);
+        const size_t smem = 16 + fbytes + (size_t)nt * f.mpad * sizeof(P);
         if (smem > 227 * 1024) return cudaErrorNotSupported;
         f.G = G;
         f.tma = 0;
@@ -458,6 +487,15 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         count_launches(1);
     }
     return cudaGetLastError();
+}
+
+// Padded factor block of one operator: the layout stage_factors builds in shared memory, written
+// once to global memory when the operator is factored (padding entries zero).
+template <typename P, int PD>
+__global__ void k_pad_factors(const P* __restrict__ luc, const P* __restrict__ spkc, const P* __restrict__ Ec,
+                              int mmax, P* out) {
+    const FacSmem<P, PD> fm(out, mmax);
+    fill_factors<P, PD>(luc, spkc, Ec, mmax, fm, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // ---- streaming explicit Kronecker matvec ---------------------------------------------
@@ -588,6 +626,41 @@ cudaError_t launch_line_fast(int prec, int p, bool xdir, const LineArgs& a, cuda
     }
 #undef WF_FAST
     return cudaErrorNotSupported;
+}
+
+size_t fac_pad_elems(int p, int mmax) {
+    switch (p) {
+        case 1: return (size_t)fac_elems<1>(mmax);
+        case 2: return (size_t)fac_elems<2>(mmax);
+        case 3: return (size_t)fac_elems<3>(mmax);
+    }
+    return 0;
+}
+
+cudaError_t launch_pad_factors(int prec, int p, int mmax, const void* luc, const void* spkc, const void* Ec,
+                               void* fpad, cudaStream_t s) {
+    const size_t es = prec == 0 ? sizeof(float) : sizeof(double);
+    const size_t n = fac_pad_elems(p, mmax);
+    if (n == 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(fpad, 0, n * es, s);
+    if (e != cudaSuccess) return e;
+#define WF_PAD(P, PD) \
+    k_pad_factors<P, PD><<<4, 256, 0, s>>>((const P*)luc, (const P*)spkc, (const P*)Ec, mmax, (P*)fpad)
+    if (prec == 0) {
+        switch (p) {
+            case 1: WF_PAD(float, 1); break;
+            case 2: WF_PAD(float, 2); break;
+            case 3: WF_PAD(float, 3); break;
+        }
+    } else {
+        switch (p) {
+            case 1: WF_PAD(double, 1); break;
+            case 2: WF_PAD(double, 2); break;
+            case 3: WF_PAD(double, 3); break;
+        }
+    }
+#undef WF_PAD
+    return cudaGetLastError();
 }
 
 cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s) {

@@ -97,6 +97,7 @@ __device__ __forceinline__ LineView<P> line_at(const FastArgs<P>& a, int arr, lo
     v.luc = shift(one ? a.luc[1] : a.luc[0], off);
     v.spkc = shift(one ? a.spkc[1] : a.spkc[0], off);
     v.Ec = shift(one ? a.Ec[1] : a.Ec[0], off);
+    v.fpad = nullptr;
     v.status = shift(a.status, off);
     v.tstatus = nullptr;
     v.preT = v.preF = v.pA1 = v.pB1 = v.pA2 = v.pB2 = nullptr;
@@ -549,6 +550,7 @@ bool fill_line(const LineArgs& la, bool xdir, int G_req, FastArgs<P>& f, size_t*
         f.luc[q] = (const P*)la.f[q].luc;
         f.spkc[q] = (const P*)la.f[q].spkc;
         f.Ec[q] = (const P*)la.f[q].Ec;
+        f.fpad[q] = nullptr;  // staged element by element (a CTA restages only on a change of operator)
     }
     f.status = la.status;
     f.tmax = (P)la.tmax;
