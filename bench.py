@@ -447,8 +447,7 @@ def run_ensemble(args) -> None:
         torch.cuda.synchronize(dev)
         with torch.cuda.stream(stream):
             e0.record(stream)
-            for _ in range(args.steps):
-                wf.wf_step(b.h, 1)
+            wf.wf_step(b.h, args.steps)  # K steps in one call (step graphs of eight and one)
             e1.record(stream)
         stream.synchronize()
         torch.cuda.synchronize(dev)
@@ -489,25 +488,31 @@ def run_ensemble(args) -> None:
     roof = roofline(dom, ktab[dom]["ms_per_launch"], dofs, costs, 4, peaks["hbm_gbs"], peaks["src"], alu, alu_src,
                     _traffic_record(dom, "c4_ensemble_256x256x256_p2_pr") if S_all == 256 else None)
     step_flops = costs["step_persistent"]["flops"] * dofs
-    # the other step form, timed the same way: one quadrature launch and one persistent launch over
-    # every line pass of every slot (the autotuner times both forms and keeps the faster)
-    other = list(tuning)
-    other[6] = 1 if tuning[6] == 2 else 2
-    wf.wf_set_tuning(b.h, other)
-    with torch.cuda.stream(stream):
-        b.step(3)
-    stream.synchronize()
-    other_s = timed(False)
-    wf.wf_kernel_times(b.h)
-    n1 = wf.wf_launch_count()
-    timed(True)
-    other_launches = wf.wf_launch_count() - n1
-    other_kt = _kernel_table(wf.wf_kernel_times(b.h))
+    # the other step forms, timed the same way with the same shapes (the autotuner times every form
+    # and keeps the fastest): per-pass launches; one quadrature launch and one persistent launch over
+    # every line pass of every slot; the per-pass launches over two slot groups on two streams
+    forms = {1: "per-pass launches", 2: "persistent line passes",
+             3: "per-pass launches, two slot groups overlapped on two streams"}
+    chosen = tuning[6] if tuning[6] else 1
+    other_forms = {}
+    for form in (1, 2, 3):
+        if form == chosen:
+            continue
+        other = list(tuning)
+        other[6] = form
+        wf.wf_set_tuning(b.h, other)
+        with torch.cuda.stream(stream):
+            b.step(3)
+        stream.synchronize()
+        other_s = timed(False)
+        wf.wf_kernel_times(b.h)
+        n1 = wf.wf_launch_count()
+        timed(True)
+        other_launches = wf.wf_launch_count() - n1
+        other_kt = _kernel_table(wf.wf_kernel_times(b.h))
+        other_forms[forms[form]] = {"ms_per_step": other_s * 1e3 / args.steps, "value": dofs * args.steps / other_s,
+                                    "launches_per_step": other_launches / args.steps, "kernels": other_kt}
     wf.wf_set_tuning(b.h, tuning)
-    forms = {1: "per-pass launches", 2: "persistent line passes"}
-    other_form = {"step_form": forms[other[6]], "ms_per_step": other_s * 1e3 / args.steps,
-                  "value": dofs * args.steps / other_s, "launches_per_step": other_launches / args.steps,
-                  "kernels": other_kt}
     # end to end through the C ABI: every slot's state from pinned float32 host arrays in one call,
     # one step, every slot's state back in one call
     n = first.dofs
@@ -544,9 +549,11 @@ def run_ensemble(args) -> None:
                           "flops_per_dof": costs["step_persistent"]["flops"]},
         "profiled_ms_per_step": prof_s * 1e3 / args.steps,
         "kernels": ktab,
-        "gpu_launches": launches,
-        "step_form": forms[tuning[6] if tuning[6] else 1],
-        "other_step_form": other_form,
+        # the profiled pass launches each kernel once per step over all slots; step form 3 launches
+        # every kernel once per slot group
+        "gpu_launches": launches * (2 if chosen == 3 and S >= 2 else 1),
+        "step_form": forms[chosen],
+        "other_step_forms": other_forms,
         "e2e": {"value": world * dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * dofs,
                 "d2h_bytes_per_step": 2 * 4 * dofs, "ms_per_step": e2e_s * 1e3, "host_dtype": "float32"},
         "clocks": clk.summary(),

@@ -258,19 +258,27 @@ int wf_launch_count(unsigned long long* n);
  *   shape[6]  step form: 1 one launch per pass (six or seven per step), 2 one
  *             persistent launch per step over every active slot (Peaceman-
  *             Rachford with one F per step, FP32, p <= 2, wind rank <= 2,
- *             no manufactured forcing; elsewhere the per-pass form runs);
+ *             no manufactured forcing; elsewhere the per-pass form runs),
+ *             3 the per-pass launches over two groups of slots (the first
+ *             and the second half) on two streams, the second group's
+ *             quadrature of a step starting when the first group's ends, so
+ *             that one group's quadrature runs beside the other group's line
+ *             passes; the groups join at the end of each wf_step call (and
+ *             of each captured graph of steps).  Batches of two or more
+ *             slots without manufactured forcing; profiled steps and
+ *             wf_step_noalloc run the per-pass form;
  *   shape[7]  slots per group of the persistent step's work order (the order
  *             keeps about six groups' fields live, sized for the L2 cache);
  * 0 selects the built-in rule (shape[5]: inside the pass; shape[6]: the
- * persistent step where it applies).
+ * per-pass launches).
  * Every value changes the schedule only: both right-hand-side placements and
- * both step forms perform the same operations in the same order, so the
+ * every step form perform the same operations in the same order, so the
  * results are the same bits.  wf_autotune tunes one value at a
  * time (two sweeps, the others held at their best values): each candidate
  * is timed in three rounds (the candidates in alternating order, so that a
- * drift of the clocks favours none), each round reps steps (after one
- * warm-up step) of the handle's active slots; the value whose fastest round
- * took least device time is kept,
+ * drift of the clocks favours none), each round about reps steps (graphs
+ * of up to four steps, after one warm-up graph) of the handle's active
+ * slots; the value whose fastest round took least device time is kept,
  * and restores every slot's device state afterwards, so the trajectory is
  * unchanged.  It needs a temporary device copy of the slot blocks
  * (S x the per-slot bytes, freed before return; WF_ENOMEM if it cannot be
@@ -279,7 +287,7 @@ int wf_launch_count(unsigned long long* n);
  * collected under wf_set_profiling.  No active slot: WF_OK, nothing tuned.
  * Errors: WF_EINVAL (reps outside 1..100), WF_ENOMEM, WF_ECUDA.
  * wf_get_tuning / wf_set_tuning read and write the eight values
- * (wf_set_tuning: shape[5] and shape[6] 0..2, the others 0..1024, else
+ * (wf_set_tuning: shape[5] 0..2, shape[6] 0..3, the others 0..1024, else
  * WF_EINVAL).
  */
 int wf_autotune(wf_handle* h, int reps);

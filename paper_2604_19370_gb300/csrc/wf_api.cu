@@ -95,6 +95,12 @@ struct wf_handle {
     // second stream: the quadrature's boundary items run there beside its interior items
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // step form 3: the slots in two groups, the second group's launches on stream gs; while a
+    // launch runs over one group (gn > 0) its kernels see slots gz0 .. gz0+gn-1, and ev_rhs (if
+    // set) is recorded after the group's first quadrature
+    cudaStream_t gs = nullptr;
+    cudaEvent_t ev_q = nullptr, ev_g = nullptr, ev_rhs = nullptr;
+    int gz0 = 0, gn = 0;
     void* mem = nullptr;
     size_t mem_bytes = 0;
     // shared region
@@ -175,10 +181,11 @@ T* at(const wf_handle* h, T* p, int slot) {
 
 Batch batch(const wf_handle* h) {
     Batch b;
-    b.S = h->S;
+    b.S = h->gn > 0 ? h->gn : h->S;
     b.sbytes = h->sbytes;
     b.active = h->active_dev;
     b.budget = h->budget_on ? h->budget_dev : nullptr;
+    b.z0 = h->gn > 0 ? h->gz0 : 0;
     return b;
 }
 
@@ -526,7 +533,7 @@ RhsArgs rhs_args(wf_handle* h, const void* T, void* F, void* Phi, void* R, doubl
     a.c2 = c2;
     a.tau = h->dt;
     a.seg = h->tune[2];
-    a.aux = h->aux;
+    a.aux = h->gn > 0 ? nullptr : h->aux;  // a slot group's launches stay on its own stream
     a.ev_fork = h->ev_fork;
     a.ev_join = h->ev_join;
     a.single = 0;
@@ -721,8 +728,52 @@ cudaError_t enqueue_step(wf_handle* h) {
     cudaError_t e = enqueue_step_body(h);
     if (e == cudaSuccess && h->mms_on) e = launch_advance_time(h->tdev, h->dt, h->stream);
     // step budgets: the persistent kernel spends them itself when a slot's last item ends
-    if (e == cudaSuccess && h->budget_on && !persistent)
-        e = launch_step_budget(h->active_dev, h->budget_dev, h->S, h->stream);
+    if (e == cudaSuccess && h->budget_on && !persistent) {
+        const int z0 = h->gn > 0 ? h->gz0 : 0, n = h->gn > 0 ? h->gn : h->S;
+        e = launch_step_budget(h->active_dev + z0, h->budget_dev + z0, n, h->stream);
+    }
+    return e;
+}
+
+// Step form 3 applies to a batch of two or more slots whose steps run eagerly or from graphs
+// (profiled steps and the allocation-free call take the per-pass launches).
+bool use_groups(const wf_handle* h) {
+    return h->tune[6] == 3 && h->S >= 2 && !h->profiling && !h->noalloc_run && !h->mms_on && h->gs;
+}
+
+// n steps of every active slot.  Step form 3: the slots are split into two groups, A (the first
+// half) on the handle's stream and B on the second stream; B's quadrature of a step waits for
+// A's quadrature of that step, so each group's quadrature (bound by instruction issue) runs
+// beside the other group's line passes (bound by memory latency), and the two groups stay half
+// a step apart until the join at the end of the n steps.  The slots are independent, so the
+// results are those of the per-pass form bit for bit.
+cudaError_t enqueue_steps(wf_handle* h, int n) {
+    if (!use_groups(h)) {
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < n && e == cudaSuccess; ++k) e = enqueue_step(h);
+        return e;
+    }
+    const int nA = (h->S + 1) / 2;
+    cudaStream_t s = h->stream, s2 = h->gs;
+    cudaError_t e = cudaEventRecord(h->ev_g, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, h->ev_g, 0);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        h->gz0 = 0;
+        h->gn = nA;
+        h->ev_rhs = h->ev_q;
+        e = enqueue_step(h);
+        h->ev_rhs = nullptr;
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, h->ev_q, 0);
+        h->gz0 = nA;
+        h->gn = h->S - nA;
+        h->stream = s2;
+        if (e == cudaSuccess) e = enqueue_step(h);
+        h->stream = s;
+    }
+    h->gz0 = h->gn = 0;
+    h->ev_rhs = nullptr;
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_g, s2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_g, 0);
     return e;
 }
 
@@ -739,6 +790,7 @@ cudaError_t enqueue_step_body(wf_handle* h) {
         RhsArgs r1 = rhs_args(h, h->T, nullptr, h->Phi, h->R, h->dt, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
         auto l1 = [&] { return rhs_and_forcing(h, r1, h->R, h->dt, nullptr, 0.0); };
         if ((e = timed(h, S_RHS1, l1)) != cudaSuccess) return e;
+        if (h->ev_rhs && (e = cudaEventRecord(h->ev_rhs, s)) != cudaSuccess) return e;
         LineArgs x1 = line_args(h, 1);
         add_line(x1, h->R, h->R, X[0], cx);
         add_line(x1, h->Phi, h->Phi, X[0], cx);
@@ -767,6 +819,7 @@ cudaError_t enqueue_step_body(wf_handle* h) {
         RhsArgs r1 = rhs_args(h, h->T, once ? h->F : nullptr, h->Phi, h->R, th, X[1], Y[0], 1.0, &X[0], &Y[1], 1.0);
         auto l1 = [&] { return rhs_and_forcing(h, r1, h->R, th, once ? h->F : nullptr, 1.0); };
         if ((e = timed(h, S_RHS1, l1)) != cudaSuccess) return e;
+        if (h->ev_rhs && (e = cudaEventRecord(h->ev_rhs, s)) != cudaSuccess) return e;
         LineArgs x1 = line_args(h, 1);
         add_line(x1, h->R, h->R, X[2], cx);
         add_line(x1, h->Phi, h->Phi, X[0], cx);
@@ -833,6 +886,7 @@ cudaError_t enqueue_step_body(wf_handle* h) {
     RhsArgs r1 = rhs_args(h, h->T, nullptr, h->Phi, h->R, half, X[1], Y[0], 2.0, nullptr, nullptr, 0.0);
     auto l1 = [&] { return rhs_and_forcing(h, r1, h->R, half, nullptr, 0.0); };
     if ((e = timed(h, S_RHS1, l1)) != cudaSuccess) return e;
+    if (h->ev_rhs && (e = cudaEventRecord(h->ev_rhs, s)) != cudaSuccess) return e;
     LineArgs x1 = line_args(h, 1);
     add_line(x1, h->R, h->R, X[2], cx);
     add_line(x1, h->Phi, h->Phi, X[0], cx);
@@ -869,8 +923,7 @@ cudaError_t capture(wf_handle* h, int steps, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return e;
-    cudaError_t le = cudaSuccess;
-    for (int k = 0; k < steps && le == cudaSuccess; ++k) le = enqueue_step(h);
+    cudaError_t le = enqueue_steps(h, steps);
     e = cudaStreamEndCapture(h->stream, &g);
     if (le != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -907,6 +960,9 @@ void destroy(wf_handle* h) {
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->gs) cudaStreamDestroy(h->gs);
+    if (h->ev_q) cudaEventDestroy(h->ev_q);
+    if (h->ev_g) cudaEventDestroy(h->ev_g);
     delete h;
 }
 
@@ -1132,7 +1188,10 @@ int wf_batch_create(int nx, int ny, int p, double dt, const wf_params* params, i
     if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_q, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming) != cudaSuccess) {
         destroy(h);
         return WF_ECUDA;
     }
@@ -1524,7 +1583,7 @@ int wf_autotune(wf_handle* h, int reps) {
     static const int kLines[] = {0, 32, 16, 8, 4, 2, 1};
     static const int kRpw[] = {0, 1, 2, 4};
     static const int kFuse[] = {0, 2};
-    static const int kMode[] = {1, 2};
+    static const int kModeAll[] = {1, 2, 3};  // per-pass, persistent, per-pass in two slot groups
     static const int kGroup[] = {0, 1, 2, 4, 8, 16, 32, 64};
     struct Axis {
         int q;
@@ -1533,6 +1592,10 @@ int wf_autotune(wf_handle* h, int reps) {
     };
     const bool pers = persist_supported(h->prec, h->p, h->wr) && h->prm.scheme == WF_PR &&
                       h->prm.F_timing == WF_F_ONCE;
+    const bool grp = h->S >= 2 && !h->mms_on;
+    int kMode[3], nMode = 0;
+    for (int m : kModeAll)
+        if (m == 1 || (m == 2 && pers) || (m == 3 && grp)) kMode[nMode++] = m;
     // the shapes first (in the per-pass form, the rule), then the step form with those shapes and
     // the persistent form's group size; the second sweep refines the shapes under the chosen form
     const Axis order[] = {{2, kSeg, (int)(sizeof(kSeg) / sizeof(int))},
@@ -1541,7 +1604,7 @@ int wf_autotune(wf_handle* h, int reps) {
                           {1, kLines, (int)(sizeof(kLines) / sizeof(int))},
                           {4, kLines, (int)(sizeof(kLines) / sizeof(int))},
                           {5, kFuse, (int)(sizeof(kFuse) / sizeof(int))},
-                          {6, kMode, pers ? 2 : 0},
+                          {6, kMode, nMode > 1 ? nMode : 0},
                           {7, kGroup, pers && h->S > 1 ? (int)(sizeof(kGroup) / sizeof(int)) : 0}};
     const size_t bytes = (size_t)h->sbytes * h->S;
     void* snap = nullptr;
@@ -1565,15 +1628,18 @@ int wf_autotune(wf_handle* h, int reps) {
     wf_kernel_times(h, nullptr, nullptr, nullptr, 0);  // discard kernel times collected so far
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess) rc = WF_ECUDA;
-    // device time of reps steps (after one warm-up step) with the shapes in h->tune, replayed from
-    // a captured one-step graph as wf_step runs them, under one event pair
+    // device time of about reps steps (after one warm-up launch) with the shapes in h->tune,
+    // replayed from a captured graph of up to four steps as wf_step runs them (several steps per
+    // graph: step form 3 keeps its slot groups half a step apart within a graph), under one event
+    // pair
+    const int gsteps = std::min(reps, 4), glaunch = (reps + gsteps - 1) / gsteps;
     auto measure = [&](double* t) -> int {
         cudaGraphExec_t ge = nullptr;
-        if (capture(h, 1, &ge) != cudaSuccess) return WF_ECUDA;
+        if (capture(h, gsteps, &ge) != cudaSuccess) return WF_ECUDA;
         int r = WF_OK;
         if (cudaGraphLaunch(ge, h->stream) != cudaSuccess || cudaEventRecord(ev0, h->stream) != cudaSuccess)
             r = WF_ECUDA;
-        for (int k = 0; k < reps && r == WF_OK; ++k)
+        for (int k = 0; k < glaunch && r == WF_OK; ++k)
             if (cudaGraphLaunch(ge, h->stream) != cudaSuccess) r = WF_ECUDA;
         if (r == WF_OK && (cudaEventRecord(ev1, h->stream) != cudaSuccess || cudaEventSynchronize(ev1) != cudaSuccess))
             r = WF_ECUDA;
@@ -1700,7 +1766,7 @@ int wf_get_tuning(const wf_handle* h, int* shape) {
 int wf_set_tuning(wf_handle* h, const int* shape) {
     if (!h || !shape) return WF_EINVAL;
     for (int q = 0; q < kTune; ++q)
-        if (shape[q] < 0 || shape[q] > (q == 5 || q == 6 ? 2 : 1024)) return WF_EINVAL;
+        if (shape[q] < 0 || shape[q] > (q == 5 ? 2 : (q == 6 ? 3 : 1024))) return WF_EINVAL;
     for (int q = 0; q < kTune; ++q) h->tune[q] = shape[q];
     drop_graphs(h);
     return WF_OK;

@@ -19,7 +19,7 @@ def wf():
     return need_gpu()
 
 
-@pytest.mark.parametrize("prec,n,form,per_step", [("fp32", 200, 1, 6), ("fp64", 200, 1, 5), ("fp32", 6, 1, 5),
+@pytest.mark.parametrize("prec,n,form,per_step", [("fp32", 200, 1, 6), ("fp64", 200, 1, 5), ("fp32", 6, 1, 5), ("fp32", 200, 3, 6),
                                                   ("fp32", 200, 2, 2), ("fp32", 6, 2, 2), ("fp64", 200, 2, 2)])
 @pytest.mark.parametrize("graph", [False, True])
 def test_launches_per_step(wf, prec, n, form, per_step, graph):
