@@ -96,8 +96,9 @@ struct wf_handle {
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // step form 3: the slots in two groups, the second group's launches on stream gs; while a
-    // launch runs over one group (gn > 0) its kernels see slots gz0 .. gz0+gn-1, and ev_rhs (if
-    // set) is recorded after the group's first quadrature
+    // launch runs over one group (gn > 0) its kernels see slots gz0 .. gz0+gn-1 (the per-slot
+    // pointers then point at slot gz0's block), and ev_rhs (if set) is recorded after the group's
+    // first quadrature
     cudaStream_t gs = nullptr;
     cudaEvent_t ev_q = nullptr, ev_g = nullptr, ev_rhs = nullptr;
     int gz0 = 0, gn = 0;
@@ -180,12 +181,14 @@ T* at(const wf_handle* h, T* p, int slot) {
 }
 
 Batch batch(const wf_handle* h) {
+    // a launch over a slot group: the group's flags (its per-slot pointers are rebased by
+    // rebase_slots)
+    const int z0 = h->gn > 0 ? h->gz0 : 0;
     Batch b;
     b.S = h->gn > 0 ? h->gn : h->S;
     b.sbytes = h->sbytes;
-    b.active = h->active_dev;
-    b.budget = h->budget_on ? h->budget_dev : nullptr;
-    b.z0 = h->gn > 0 ? h->gz0 : 0;
+    b.active = h->active_dev + z0;
+    b.budget = h->budget_on ? h->budget_dev + z0 : nullptr;
     return b;
 }
 
@@ -533,7 +536,9 @@ RhsArgs rhs_args(wf_handle* h, const void* T, void* F, void* Phi, void* R, doubl
     a.c2 = c2;
     a.tau = h->dt;
     a.seg = h->tune[2];
-    a.aux = h->gn > 0 ? nullptr : h->aux;  // a slot group's launches stay on its own stream
+    // the boundary items' stream (both slot groups of step form 3 fork to it in turn: a group's
+    // quadrature joins back before its line passes, and group B's starts after group A's)
+    a.aux = h->aux;
     a.ev_fork = h->ev_fork;
     a.ev_join = h->ev_join;
     a.single = 0;
@@ -735,6 +740,14 @@ cudaError_t enqueue_step(wf_handle* h) {
     return e;
 }
 
+// Point the handle's per-slot pointers (fields, flags, operators, factors, wind factors) at slot
+// z0's block: launches then treat slot z0 as their first slot.  z0 = 0 restores the layout.
+void rebase_slots(wf_handle* h, int z0) {
+    Arena B;
+    B.base = h->slots_mem + (size_t)h->sbytes * z0;
+    layout_slot(h, B);
+}
+
 // Step form 3 applies to a batch of two or more slots whose steps run eagerly or from graphs
 // (profiled steps and the allocation-free call take the per-pass launches).
 bool use_groups(const wf_handle* h) {
@@ -767,7 +780,9 @@ cudaError_t enqueue_steps(wf_handle* h, int n) {
         h->gz0 = nA;
         h->gn = h->S - nA;
         h->stream = s2;
+        rebase_slots(h, nA);
         if (e == cudaSuccess) e = enqueue_step(h);
+        rebase_slots(h, 0);
         h->stream = s;
     }
     h->gz0 = h->gn = 0;
@@ -1661,6 +1676,8 @@ int wf_autotune(wf_handle* h, int reps) {
     constexpr int kRounds = 3, kMaxCand = 16;
     for (int sweep = 0; sweep < 2 && rc == WF_OK; ++sweep)
         for (const Axis& ax : order) {
+            // the persistent step's group size matters only when that form is the one kept
+            if (ax.q == 7 && best[6] != 2) continue;
             double tmin[kMaxCand];
             for (int i = 0; i < ax.n; ++i) tmin[i] = 1e300;
             for (int round = 0; round < kRounds && rc == WF_OK; ++round)

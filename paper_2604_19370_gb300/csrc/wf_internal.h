@@ -25,23 +25,24 @@ constexpr int kMaxRank = 4;
 // scenario z's copy lies z * sbytes bytes further (each scenario owns one block of device
 // memory with the same internal layout).  Launches cover all S scenarios with grid.z = S;
 // a scenario whose active flag is 0, or whose step budget is spent (0), is skipped.
+// Slots of one launch (its grid.z); every per-slot pointer of the launch refers to the launch's
+// first slot, the next ones follow sbytes apart (a launch over a group of slots gets pointers to
+// the group's first slot).
 struct Batch {
-    int S;              // slots of the launch (its grid.z)
+    int S;
     long long sbytes;
-    const int* active;  // [z0 + S] or nullptr (all active)
-    const int* budget;  // [z0 + S] step budgets (negative: unlimited) or nullptr (none)
-    int z0;             // slot of blockIdx.z == 0 (a launch over a group of slots)
+    const int* active;  // [S] or nullptr (all active)
+    const int* budget;  // [S] step budgets (negative: unlimited) or nullptr (none)
 };
 #ifdef __CUDACC__
 template <typename T>
 __device__ __forceinline__ T* scene_ptr(T* p, const Batch& b) {
     return p ? reinterpret_cast<T*>(reinterpret_cast<char*>(const_cast<typename std::remove_const<T>::type*>(p)) +
-                                    (long long)(blockIdx.z + b.z0) * b.sbytes)
+                                    (long long)blockIdx.z * b.sbytes)
              : p;
 }
 __device__ __forceinline__ bool scene_active(const Batch& b) {
-    const int z = blockIdx.z + b.z0;
-    return (!b.active || b.active[z] != 0) && (!b.budget || b.budget[z] != 0);
+    return (!b.active || b.active[blockIdx.z] != 0) && (!b.budget || b.budget[blockIdx.z] != 0);
 }
 #endif
 

@@ -499,22 +499,19 @@ __global__ void k_pad_factors(const P* __restrict__ luc, const P* __restrict__ s
 }
 
 // ---- streaming explicit Kronecker matvec ---------------------------------------------
-// R = Fscale F + c1 (A1^x (x) B1^y) T + c2 (A2^x (x) B2^y) T.  A warp owns a strip of 32 columns
-// (lane L <-> column X0 - p + L; lanes p .. 31-p are outputs) and a segment of `seg` output
-// rows, and walks down its rows once: each T row is x-convolved with both bands as it arrives
-// (neighbours' values by warp shuffles) and enters a window of the last 2p+1 convolved rows,
-// from which the y bands finish one output row.  Loads run 2p+1 rows ahead of the row in use
-// (register queues of T and F rows), so every warp keeps several rows in flight; the row loop is
-// unrolled by 2p+1, so the windows and the queues rotate by register renaming.  A segment
-// re-reads 2p rows of T above and below it.  Values outside the domain are zeros, and the
-// operations (and their order) are those of the right-hand side fused into the x pass.
-template <typename P, int PD>
+// R = Fscale F + c1 (A1^x (x) B1^y) T + c2 (A2^x (x) B2^y) T.  A warp owns 32 columns (lane L
+// <-> column X0 - p + L; lanes p .. 31-p are outputs) and RS output rows: it issues every load
+// of its RS + 2p rows of T and RS rows of F first, x-convolves each row with neighbours'
+// values taken by shuffles, and reduces the y bands from registers.  No shared memory, no
+// barriers, every warp independent.  Values outside the domain are zeros, and the operations
+// (and their order) are those of the right-hand side fused into the x pass.
+template <typename P, int PD, int RS>
 __global__ void __launch_bounds__(128) k_matvec_stream(int Nx, int Ny, int pitch, const P* __restrict__ T,
                                                        const P* __restrict__ F, P* R, const P* __restrict__ A1,
                                                        const P* __restrict__ B1, const P* __restrict__ A2,
                                                        const P* __restrict__ B2, P Fscale, P c1, P c2, Batch b,
-                                                       int nstrips, int nsegs, int seg) {
-    constexpr int W = 2 * PD + 1, D = W;
+                                                       int nstrips, int nsegs) {
+    constexpr int W = 2 * PD + 1, NR = RS + 2 * PD;
     if (!scene_active(b)) return;
     const int lane = threadIdx.x & 31;
     const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -530,71 +527,80 @@ __global__ void __launch_bounds__(128) k_matvec_stream(int Nx, int Ny, int pitch
     const int x = st * (32 - 2 * PD) - PD + lane;  // this lane's column
     const bool xok = x >= 0 && x < Nx;
     const bool out = lane >= PD && lane < 32 - PD && x < Nx;
-    const int j0 = sg * seg, j1 = min(Ny, j0 + seg);  // output rows j0 .. j1-1
-    const P* __restrict__ tc = T + (xok ? x : 0);
-    const P* __restrict__ fc = F + (out ? x : 0);
-    P* rc = R + (out ? x : 0);
-    P a1v[W], a2v[W], b1i[W], b2i[W];
+    const int j0 = sg * RS;  // first output row
+    // interior segment: every T row it reads exists and every output row has the interior
+    // y bands (rows 2p .. Ny-2p-1 of a band all equal row 2p), so no row needs a guard
+    const bool yint = j0 >= 2 * PD && j0 + RS + 2 * PD <= Ny;
+    P tv[NR], fv[RS];
+    if (yint) {
+        const P* tp = T + (size_t)(j0 - PD) * pitch + (xok ? x : 0);
+        const P* fp = F + (size_t)j0 * pitch + (xok ? x : 0);
+#pragma unroll
+        for (int i = 0; i < NR; ++i) tv[i] = xok ? tp[(size_t)i * pitch] : P(0);
+#pragma unroll
+        for (int i = 0; i < RS; ++i) fv[i] = out ? fp[(size_t)i * pitch] : P(0);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int r = j0 - PD + i;
+            tv[i] = (xok && r >= 0 && r < Ny) ? T[(size_t)r * pitch + x] : P(0);
+        }
+#pragma unroll
+        for (int i = 0; i < RS; ++i) {
+            const int r = j0 + i;
+            fv[i] = (out && r < Ny) ? F[(size_t)r * pitch + x] : P(0);
+        }
+    }
+    P a1v[W], a2v[W];
 #pragma unroll
     for (int d = 0; d < W; ++d) {
         a1v[d] = out ? A1[(size_t)x * W + d] : P(0);
         a2v[d] = (out && A2) ? A2[(size_t)x * W + d] : P(0);
-        // y bands of the interior rows (rows 2p .. Ny-2p-1 of a band all equal row 2p)
-        b1i[d] = c1 * B1[(size_t)(2 * PD) * W + d];
-        b2i[d] = A2 ? c2 * B2[(size_t)(2 * PD) * W + d] : P(0);
     }
-    // T row r is convolved at step r; output row j = r - p is finished at the same step
-    const int r0 = j0 - PD, r1 = j1 + PD;
-    auto ldT = [&](int r) { return (xok && r >= 0 && r < Ny) ? tc[(size_t)r * pitch] : P(0); };
-    auto ldF = [&](int j) { return (out && j >= j0 && j < j1) ? fc[(size_t)j * pitch] : P(0); };
-    P tq[D], fq[D], w1[W], w2[W];
+    // x-convolution of every row (outputs lanes read lanes lane - p .. lane + p)
+    P w1[NR], w2[NR];
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-        tq[i] = ldT(r0 + i);
-        fq[i] = ldF(r0 - PD + i);
-        w1[i] = w2[i] = P(0);
-    }
-#pragma unroll W
-    for (int r = r0; r < r1; ++r) {
-        const P tv = tq[0];
-        const P fv = fq[0];
-#pragma unroll
-        for (int i = 0; i + 1 < D; ++i) {
-            tq[i] = tq[i + 1];
-            fq[i] = fq[i + 1];
-        }
-        tq[D - 1] = ldT(r + D);
-        fq[D - 1] = ldF(r - PD + D);
+    for (int i = 0; i < NR; ++i) {
         P t1 = 0, t2 = 0;
 #pragma unroll
         for (int dk = 0; dk < W; ++dk) {
-            const P val = (dk == PD) ? tv : __shfl_sync(0xffffffffu, tv, (lane - PD + dk) & 31);
+            const P val = (dk == PD) ? tv[i] : __shfl_sync(0xffffffffu, tv[i], (lane - PD + dk) & 31);
             t1 += a1v[dk] * val;
             t2 += a2v[dk] * val;
         }
+        w1[i] = t1;
+        w2[i] = t2;
+    }
+    if (!out) return;
+    if (yint) {
+        P b1i[W], b2i[W];
 #pragma unroll
-        for (int d = 0; d + 1 < W; ++d) {
-            w1[d] = w1[d + 1];
-            w2[d] = w2[d + 1];
+        for (int d = 0; d < W; ++d) {
+            b1i[d] = c1 * B1[(size_t)(2 * PD) * W + d];
+            b2i[d] = A2 ? c2 * B2[(size_t)(2 * PD) * W + d] : P(0);
         }
-        w1[W - 1] = t1;
-        w2[W - 1] = t2;
-        const int j = r - PD;
-        if (j >= j0 && out) {
-            P acc = Fscale * fv;
-            if (j >= 2 * PD && j < Ny - 2 * PD) {
+        P* rp = R + (size_t)j0 * pitch + x;
 #pragma unroll
-                for (int dl = 0; dl < W; ++dl) acc = fma(b1i[dl], w1[dl], fma(b2i[dl], w2[dl], acc));
-            } else {
+        for (int o = 0; o < RS; ++o) {
+            P acc = Fscale * fv[o];
 #pragma unroll
-                for (int dl = 0; dl < W; ++dl) {
-                    const P b1 = c1 * B1[(size_t)j * W + dl];
-                    const P b2 = A2 ? c2 * B2[(size_t)j * W + dl] : P(0);
-                    acc = fma(b1, w1[dl], fma(b2, w2[dl], acc));
-                }
-            }
-            rc[(size_t)j * pitch] = acc;
+            for (int dl = 0; dl < W; ++dl) acc = fma(b1i[dl], w1[o + dl], fma(b2i[dl], w2[o + dl], acc));
+            rp[(size_t)o * pitch] = acc;
         }
+        return;
+    }
+#pragma unroll
+    for (int o = 0; o < RS; ++o) {
+        const int j = j0 + o;
+        if (j >= Ny) break;
+        P acc = Fscale * fv[o];
+#pragma unroll
+        for (int dl = 0; dl < W; ++dl) {
+            const P b1 = c1 * B1[(size_t)j * W + dl];
+            const P b2 = A2 ? c2 * B2[(size_t)j * W + dl] : P(0);
+            acc = fma(b1, w1[o + dl], fma(b2, w2[o + dl], acc));
+        }
+        R[(size_t)j * pitch + x] = acc;
     }
 }
 
@@ -658,22 +664,18 @@ cudaError_t launch_pad_factors(int prec, int p, int mmax, const void* luc, const
 }
 
 cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s) {
-    // segment height: the largest of 64, 32, 16, 8 rows that still gives three warps' items per
-    // resident warp slot (32 per SM); taller segments re-read fewer halo rows
+    // output rows per warp item: 8 for p <= 2; 16 for p = 3, whose 2p-row halo would otherwise
+    // nearly double the rows a warp loads
     constexpr int WARPS = 4;
     if (p < 1 || p > 3) return cudaErrorInvalidValue;
-    int sms = 152, dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int nstrips = (a.Nx + (32 - 2 * p) - 1) / (32 - 2 * p);
-    int seg = 64;
-    while (seg > 8 && (long)nstrips * ((a.Ny + seg - 1) / seg) * a.b.S < 3L * 32 * sms) seg /= 2;
-    const int nsegs = (a.Ny + seg - 1) / seg;
+    const int rs = p > 2 ? 16 : 8;
+    const int nstrips = (a.Nx + (32 - 2 * p) - 1) / (32 - 2 * p), nsegs = (a.Ny + rs - 1) / rs;
     const long items = (long)nstrips * nsegs;
     dim3 grid((unsigned)((items + WARPS - 1) / WARPS), 1, a.b.S), block(32 * WARPS);
 #define WF_MV(P, PD)                                                                                          \
-    k_matvec_stream<P, PD><<<grid, block, 0, s>>>(a.Nx, a.Ny, a.pitch, (const P*)a.T, (const P*)a.F, (P*)a.R,         \
-                                                  (const P*)a.A1, (const P*)a.B1, (const P*)a.A2, (const P*)a.B2, \
-                                                  (P)a.Fscale, (P)a.c1, (P)a.c2, a.b, nstrips, nsegs, seg)
+    k_matvec_stream<P, PD, (PD > 2 ? 16 : 8)><<<grid, block, 0, s>>>(                                         \
+        a.Nx, a.Ny, a.pitch, (const P*)a.T, (const P*)a.F, (P*)a.R, (const P*)a.A1, (const P*)a.B1,           \
+        (const P*)a.A2, (const P*)a.B2, (P)a.Fscale, (P)a.c1, (P)a.c2, a.b, nstrips, nsegs)
     if (prec == 0) {
         switch (p) {
             case 1: WF_MV(float, 1); break;

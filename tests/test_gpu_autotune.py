@@ -37,8 +37,9 @@ def test_shapes_do_not_change_results(wf, prec, scheme):
     # rectangular, several chunks per line and several quadrature segments
     sc = make_scenario("shape", 150, 2, 1e-3, 1, 91, wind=(1.2, -0.7), fuel_sigma=3.0)
     ref = None
-    # every shape in both step forms (per-pass launches; the persistent launch where it applies)
-    for shape in [tuple(s6) + (form, 0) for s6 in SHAPES for form in (1, 2)]:
+    # every shape in every step form (per-pass launches; the persistent launch where it applies; the
+    # slot-group form, which a single slot runs as per-pass launches)
+    for shape in [tuple(s6) + (form, 0) for s6 in SHAPES for form in (1, 2, 3)]:
         sim = _sim(wf, sc, P, code)
         wf.wf_set_tuning(sim.h, shape)
         assert wf.wf_get_tuning(sim.h) == shape
@@ -125,8 +126,10 @@ def test_tuning_argument_checks(wf):
     assert L.wf_set_tuning(sim.h, bad) == wf.WF_EINVAL
     bad = (wf.ctypes.c_int * 8)(0, 0, 0, 0, 0, 3, 0, 0)
     assert L.wf_set_tuning(sim.h, bad) == wf.WF_EINVAL
-    bad = (wf.ctypes.c_int * 8)(0, 0, 0, 0, 0, 0, 3, 0)
+    bad = (wf.ctypes.c_int * 8)(0, 0, 0, 0, 0, 0, 4, 0)
     assert L.wf_set_tuning(sim.h, bad) == wf.WF_EINVAL
+    ok = (wf.ctypes.c_int * 8)(0, 0, 0, 0, 0, 0, 3, 0)
+    assert L.wf_set_tuning(sim.h, ok) == wf.WF_OK
     sim.close()
 
 
