@@ -37,18 +37,18 @@ namespace {
 
 // Work items = (strip, segment) of one scenario.  MODE 2: every item, interior segments first and
 // the short boundary segments last, each warp taking the fast or the general form.  With
-// FP32 the items are split between two launches whose register budgets differ: MODE 0 runs the
+// FP32 the items are split between launches whose register budgets differ: MODE 0 runs the
 // interior items (interior strip x interior segment: the packed form with constant tables,
-// which needs few registers, so sixteen one-warp CTAs fit an SM) and MODE 1 the rest, twelve
-// per SM: the boundary strips
+// which needs few registers, so sixteen one-warp CTAs fit an SM), MODE 1 the boundary strips
 // of the interior segments in the packed form with x tables in registers (on segments of
-// their own, shorter height) and the boundary segments in the general form.  One warp per
-// CTA, so that a warp slot frees as soon as its own item ends.
-// MODE 3 (FP32): the items of MODE 0 followed by those of MODE 1 in one launch at sixteen warps per
-// SM, for a step that must take one launch for its quadrature.
+// their own, shorter height; sixteen per SM) and MODE 4 the boundary segments in the general
+// form (twelve per SM).  One warp per CTA, so that a warp slot frees as soon as its own item
+// ends.
+// MODE 3 (FP32): the items of MODE 0 followed by those of MODE 1 and MODE 4 in one launch at sixteen
+// warps per SM, for a step that must take one launch for its quadrature.
 template <typename P, int PD, int WR, int MODE>
 struct RhsOcc {
-    static constexpr int value = sizeof(P) != 4 || PD > 2 ? 1 : (MODE == 0 || MODE == 3 ? 16 : 12);
+    static constexpr int value = sizeof(P) != 4 || PD > 2 ? 1 : (MODE == 0 || MODE == 3 || MODE == 1 ? 16 : 12);
 };
 
 template <typename P, int PD, int WR, int MODE>
@@ -83,10 +83,12 @@ __global__ void __launch_bounds__(32, RhsOcc<P, PD, WR, MODE>::value) k_rhs_stre
         if (item >= nsi * nseg_in) return;  // whole warp leaves; no block barrier in this kernel
         sg = item / nsi;
         strip = a.s_lo + (item - sg * nsi);
-    } else if (MODE == 1 || MODE == 3) {
+    } else if (MODE == 1 || MODE == 3 || MODE == 4) {
         const int nb = a.nstrips - nsi;      // boundary strips: [0, s_lo) and [s_hi, nstrips)
         const int first = nb * a.nseg_b;     // boundary strips x interior segments of height
-        const int item = item1;
+        // MODE 1: the boundary strips' items only; MODE 4: the boundary segments' only
+        if (MODE == 1 && item1 >= first) return;
+        const int item = MODE == 4 ? item1 + first : item1;
         if (item < first) {                  // seg_b, then every strip x the two boundary segments
             sg = item / nb;
             const int bs = item - sg * nb;
@@ -127,12 +129,18 @@ __global__ void __launch_bounds__(32, RhsOcc<P, PD, WR, MODE>::value) k_rhs_stre
         // FP32: interior strips of interior segments with constant tables (MODE 0), the other
         // strips of interior segments with x tables in registers, boundary segments general.
         // MODE 2 runs in FP32 only where no strip is interior.
-        if (as0)
-            stream_strip_pairs<PD, WR, false>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1, wind_rows);
-        else if (yint)
+        if constexpr (MODE == 1) {
             stream_strip_pairs<PD, WR, true>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1, wind_rows);
-        else
+        } else if constexpr (MODE == 4) {
             stream_strip<P, PD, WR, false>(a, a_in.it, lane, X0, Y0, Y1);
+        } else {
+            if (as0)
+                stream_strip_pairs<PD, WR, false>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1, wind_rows);
+            else if (yint)
+                stream_strip_pairs<PD, WR, true>(a, a_in.it, a_in.pr, lane, X0, Y0, Y1, wind_rows);
+            else
+                stream_strip<P, PD, WR, false>(a, a_in.it, lane, X0, Y0, Y1);
+        }
     } else {
         if (xint && yint)
             stream_strip<P, PD, WR, true>(a, a_in.it, lane, X0, Y0, Y1);
@@ -211,10 +219,21 @@ cudaError_t run_stream(const RhsArgs& r, cudaStream_t s) {
             }
             const size_t wb0 = wind_smem<P, PD, WR, 0>(a.seg), wb1 = wind_smem<P, PD, WR, 1>(a.seg_b);
             if (wb0 == SIZE_MAX || wb1 == SIZE_MAX) return cudaErrorInvalidValue;
-            dim3 g1((unsigned)((n_side + WARPS - 1) / WARPS), 1, r.b.S);
-            k_rhs_stream<P, PD, WR, 1><<<g1, 32 * WARPS, wb1, s1>>>(a);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            count_launches(1);
+            // the boundary strips' items (packed form, sixteen warps per SM) and the boundary
+            // segments' items (general form, twelve) in launches of their own
+            const long n_bstrip = (long)(a.nstrips - (a.s_hi - a.s_lo)) * a.nseg_b, n_bseg = n_side - n_bstrip;
+            if (n_bstrip > 0) {
+                dim3 g1((unsigned)((n_bstrip + WARPS - 1) / WARPS), 1, r.b.S);
+                k_rhs_stream<P, PD, WR, 1><<<g1, 32 * WARPS, wb1, s1>>>(a);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                count_launches(1);
+            }
+            if (n_bseg > 0) {
+                dim3 g4((unsigned)((n_bseg + WARPS - 1) / WARPS), 1, r.b.S);
+                k_rhs_stream<P, PD, WR, 4><<<g4, 32 * WARPS, 0, s1>>>(a);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                count_launches(1);
+            }
             dim3 g0((unsigned)((n_fast + WARPS - 1) / WARPS), 1, r.b.S);
             k_rhs_stream<P, PD, WR, 0><<<g0, 32 * WARPS, wb0, s>>>(a);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -1,8 +1,8 @@
 """Kernels per time step, as counted by wf_launch_count (the bench's gpu_launches).
 
 Per-pass form: a PR step with one F per step launches the quadrature (FP32 with interior
-elements: an interior launch and a boundary launch), the first x and y passes and the second x
-and y passes.  Persistent form: one quadrature launch, then one launch for every line pass,
+elements: an interior launch, a launch for the boundary strips and one for the boundary segments),
+the first x and y passes, the substep-2 right-hand side and the second x and y passes.  Persistent form: one quadrature launch, then one launch for every line pass,
 whatever the number of slots.  The library counts the kernels it launches (eager steps, and captures once); a replayed
 step graph runs the captured kernels without counting them again.
 """
@@ -19,7 +19,7 @@ def wf():
     return need_gpu()
 
 
-@pytest.mark.parametrize("prec,n,form,per_step", [("fp32", 200, 1, 6), ("fp64", 200, 1, 5), ("fp32", 6, 1, 5), ("fp32", 200, 3, 6),
+@pytest.mark.parametrize("prec,n,form,per_step", [("fp32", 200, 1, 7), ("fp64", 200, 1, 5), ("fp32", 6, 1, 5), ("fp32", 200, 3, 7),
                                                   ("fp32", 200, 2, 2), ("fp32", 6, 2, 2), ("fp64", 200, 2, 2)])
 @pytest.mark.parametrize("graph", [False, True])
 def test_launches_per_step(wf, prec, n, form, per_step, graph):
