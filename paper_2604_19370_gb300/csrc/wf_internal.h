@@ -215,6 +215,19 @@ cudaError_t launch_xsolve(int prec, int p, const LineArgs& a, cudaStream_t s);
 cudaError_t launch_ysolve(int prec, int p, const LineArgs& a, cudaStream_t s);
 // compact-factor form (wf_linefast.cu); returns cudaErrorNotSupported when it cannot
 // take the arguments (factors not compact, more than 256 threads, shared memory)
+// Raise (never lower) the dynamic shared memory a kernel may be launched with.  The limit is a
+// property of the kernel, read when a launch is made; the launches captured in a graph keep the
+// size each needed, so a later, smaller request for the same kernel (another pass, other launch
+// shapes) must not take the limit below them.
+template <typename K>
+inline cudaError_t allow_dynamic_smem(K kern, size_t bytes) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(kern));
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(reinterpret_cast<const void*>(kern), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes);
+}
 cudaError_t launch_line_fast(int prec, int p, bool xdir, const LineArgs& a, cudaStream_t s);
 // elements of the padded factor block of one operator (chunk rows mmax), and the kernel that
 // writes it from the compact factors (luc, spkc, Ec in the working precision)

@@ -460,7 +460,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         f.tsp = tsp;
         f.tma = aligned ? 1 : 0;
         auto kern = pre ? k_xsolve_warp<P, PD, true> : k_xsolve_warp<P, PD, false>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_dynamic_smem(kern, (size_t)smem);
         if (e != cudaSuccess) return e;
         dim3 grid((a.nlines + G - 1) / G, a.narr, a.b.S);
         kern<<<grid, 32 * (G / lpw), smem, s>>>(f);
@@ -481,7 +481,7 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const bool wide = (long)grid.x * grid.y * grid.z <= 2L * sms;
         auto kern = wide ? k_ysolve_cols<P, PD, 32> : k_ysolve_cols<P, PD, 16>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_dynamic_smem(kern, (size_t)smem);
         if (e != cudaSuccess) return e;
         kern<<<grid, nt, smem, s>>>(f);
         count_launches(1);

@@ -632,7 +632,7 @@ cudaError_t persist_typed(const PersistHost& h, PersistPlan* plan, bool launch, 
     A.cl = cl;
     const size_t smem = std::max(std::max(sx1, sx2), std::max(sy1, sy2));
     auto kern = k_lines_persist<P, PD>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(kern, (size_t)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPT, smem);

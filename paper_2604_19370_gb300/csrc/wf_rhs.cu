@@ -344,7 +344,7 @@ cudaError_t run_rhs(const RhsArgs& a, cudaStream_t s) {
     auto kern = k_rhs<P, PD, TJ, TI, NT>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S_::bytes);
+        cudaError_t e = allow_dynamic_smem(kern, (size_t)S_::bytes);
         if (e != cudaSuccess) return e;
         configured = true;
     }

@@ -159,8 +159,7 @@ size_t wind_smem(int seg) {
     const size_t bytes = (size_t)2 * WR * (PD + 1) * (seg + PD) * sizeof(float);
     if (bytes > 48 * 1024) {
         if (bytes > 227 * 1024) return SIZE_MAX;
-        if (cudaFuncSetAttribute(k_rhs_stream<P, PD, WR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bytes) != cudaSuccess)
+        if (allow_dynamic_smem(k_rhs_stream<P, PD, WR, MODE>, bytes) != cudaSuccess)
             return SIZE_MAX;
     }
     return bytes;

@@ -318,12 +318,12 @@ cudaError_t run_line(const LineArgs& a, cudaStream_t s) {
     dim3 grid((a.nlines + G - 1) / G, a.narr, a.b.S);
     if (X) {
         auto kern = k_xsolve<P, PD, G>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_dynamic_smem(kern, (size_t)smem);
         if (e != cudaSuccess) return e;
         kern<<<grid, threads, smem, s>>>(to_typed<P>(a, mpad));
     } else {
         auto kern = k_ysolve<P, PD, G>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_dynamic_smem(kern, (size_t)smem);
         if (e != cudaSuccess) return e;
         kern<<<grid, threads, smem, s>>>(to_typed<P>(a, mpad));
     }
