@@ -13,8 +13,9 @@
 //     left no longer shortens the quantum of the others;
 //   - queued requests are admitted (first come, first served) into free slots of idle pools of
 //     their class; a class with no free slot gets a new pool when the memory budget allows it,
-//     its capacity set by the class's queued demand and checked with wf_batch_bytes before
-//     anything is allocated; a class that did not fit is not retried until memory is freed;
+//     its capacity set by the class's queued demand (at least kMinPoolSlots) and checked with
+//     wf_batch_bytes before anything is allocated; a class that did not fit is not retried until
+//     memory is freed;
 //   - a pool's finished slots are retired as soon as its quantum completes: the state is copied
 //     into the request's arrays, the slot freed and the latency recorded.
 // New requests therefore join running work at quantum boundaries of their own class, and a
@@ -40,6 +41,12 @@
 namespace {
 
 constexpr int kQuantum = 25;  // steps per quantum of a pool
+// Slots of a new pool at least (within max_slots and the budget): under a thin stream of arrivals
+// a class's queued demand is one request at a time, and pools sized by it alone came one slot
+// each -- a pool per request, each created (allocation, factorisation) on the worker thread and
+// stepped by launches over a single slot.  Later requests of the class join a pool's free slots
+// at its next quantum instead.
+constexpr int kMinPoolSlots = 8;
 
 using Clock = std::chrono::steady_clock;
 
@@ -231,9 +238,11 @@ bool admit(wf_server* s) {
             }
         }
         if (!target && !any_free && !s->blocked.count(key)) {
-            // no free slot in the class: a new pool sized by the class's queued demand
-            auto pl = make_pool(s, q->r, pow2ceil(std::max(1, demand[key])));
-            if (!pl && drop_idle_pools(s)) pl = make_pool(s, q->r, pow2ceil(std::max(1, demand[key])));
+            // no free slot in the class: a new pool sized by the class's queued demand (at least
+            // kMinPoolSlots)
+            const int want = std::max(kMinPoolSlots, pow2ceil(std::max(1, demand[key])));
+            auto pl = make_pool(s, q->r, want);
+            if (!pl && drop_idle_pools(s)) pl = make_pool(s, q->r, want);
             if (pl) {
                 c.pools.push_back(std::move(pl));
                 target = c.pools.back().get();
