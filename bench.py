@@ -835,7 +835,9 @@ def run_serving(args, wf=None, as_extra: bool = False):
     lat_c, ds_c, span_c, _ = run(closed, None)
     capacity = len(lat_c) / span_c
     rate = 0.8 * capacity
-    open_reqs = request_stream_c5(args.requests, rate, seed=6)
+    # the same requests (sizes, orders, step counts, precisions, seeds) with Poisson arrival times at
+    # the rate: the capacity was measured on exactly this work
+    open_reqs = request_stream_c5(args.requests, rate, seed=5)
     lat, ds, span, fails = run(open_reqs, rate)
     res = {"workload": "c5_served_poisson", "requests": len(open_reqs), "arrival_rate_hz": rate,
            "capacity_rps": capacity, "sizes": [128, 256, 512, 1024], "p": [2, 3], "steps": "U[200,2000]",
