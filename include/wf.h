@@ -343,6 +343,26 @@ int wf_batch_set_states_f32(wf_handle* h, const float* T, const float* fuel, siz
 int wf_batch_get_states(wf_handle* h, double* T, double* fuel, size_t n);
 int wf_batch_get_states_f32(wf_handle* h, float* T, float* fuel, size_t n);
 
+/*
+ * End-to-end run from host arrays (no counterpart in the paper): every
+ * slot's state from T_in, fuel_in, `steps` steps of every active slot, every
+ * slot's state into T_out, fuel_out (slot-major [S][Ny][Nx], float64 or,
+ * the _f32 call, float32; out may equal in).  The slots are taken in `groups`
+ * groups of consecutive slots (1..8, at most S) pipelined over three streams:
+ * group g's upload overlaps the steps of group g-1 and the download of group
+ * g-2, so that the host copies hide behind the steps.  Each group's steps are
+ * the per-pass launches over its slots (the same operations as wf_step: the
+ * results are bit for bit those of wf_batch_set_states, wf_step,
+ * wf_batch_get_states).  Uses the staging area of the calls above; waits for
+ * completion; the caller's arrays should be pinned for the copies to overlap.
+ * Errors: WF_EINVAL (NULL handle or array, n != S*Nx*Ny, steps < 0, groups
+ * outside 1..8), WF_ENOMEM, WF_ECUDA.
+ */
+int wf_batch_run(wf_handle* h, const double* T_in, const double* fuel_in, double* T_out, double* fuel_out,
+                 size_t n, int steps, int groups);
+int wf_batch_run_f32(wf_handle* h, const float* T_in, const float* fuel_in, float* T_out, float* fuel_out,
+                     size_t n, int steps, int groups);
+
 /* Include (on != 0) or exclude a slot from the following wf_step calls.
  * Errors: WF_EINVAL. */
 int wf_batch_activate(wf_handle* h, int slot, int on);

@@ -102,6 +102,10 @@ struct wf_handle {
     cudaStream_t gs = nullptr;
     cudaEvent_t ev_q = nullptr, ev_g = nullptr, ev_rhs = nullptr;
     int gz0 = 0, gn = 0;
+    // wf_batch_run: upload and download streams, and events (per group: uploaded, done; a start
+    // and an end event), created on the first call
+    cudaStream_t io_in = nullptr, io_out = nullptr;
+    cudaEvent_t ev_io[18] = {};
     void* mem = nullptr;
     size_t mem_bytes = 0;
     // shared region
@@ -614,7 +618,9 @@ void drop_graphs(wf_handle* h);
 // slot) takes PR with one F per step; tuning value 6 picks it (2) or the per-pass launches (1,
 // and the rule 0: measured faster on the ensemble and on a single domain).
 bool use_persist(const wf_handle* h) {
-    if (h->noalloc_run || h->prm.scheme != WF_PR || h->prm.F_timing != WF_F_ONCE) return false;
+    // (a launch over a group of slots, gn > 0, takes the per-pass form: the persistent plan lists
+    // every active slot of the handle)
+    if (h->noalloc_run || h->gn > 0 || h->prm.scheme != WF_PR || h->prm.F_timing != WF_F_ONCE) return false;
     if (!persist_supported(h->prec, h->p, h->wr)) return false;
     return h->tune[6] == 2;
 }
@@ -976,6 +982,10 @@ void destroy(wf_handle* h) {
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->gs) cudaStreamDestroy(h->gs);
+    if (h->io_in) cudaStreamDestroy(h->io_in);
+    if (h->io_out) cudaStreamDestroy(h->io_out);
+    for (cudaEvent_t e : h->ev_io)
+        if (e) cudaEventDestroy(e);
     if (h->ev_q) cudaEventDestroy(h->ev_q);
     if (h->ev_g) cudaEventDestroy(h->ev_g);
     delete h;
@@ -1399,6 +1409,92 @@ static int batch_states(wf_handle* h, const void* Tin, const void* Fin, void* To
     }
     WF_TRY(cudaStreamSynchronize(s));
     return WF_OK;
+}
+
+// End-to-end run from host arrays, the slots in groups pipelined over three streams: the upload
+// stream copies group g's host arrays into its part of the staging area, the handle's stream
+// converts them into the slots' pitched fields, steps the group (its per-slot pointers rebased to
+// its first slot, as in step form 3) and converts the results back into the staging part, and the
+// download stream copies them out.  Group g's upload runs beside group g-1's steps and group g-2's
+// download.
+static int batch_run(wf_handle* h, const void* Tin, const void* Fin, void* Tout, void* Fout, size_t n, int steps,
+                     int groups, int host32) {
+    const size_t per = (size_t)h->Nx * h->Ny;
+    if (!Tin || !Fin || !Tout || !Fout || n != per * (size_t)h->S || steps < 0 || groups < 1 || groups > 8)
+        return WF_EINVAL;
+    // (manufactured forcing advances the handle's time once per enqueued step: one group)
+    const int G = h->mms_on ? 1 : std::min(groups, h->S);
+    const size_t es = host32 ? sizeof(float) : sizeof(double);
+    const size_t need = 2 * n * es;
+    if (h->bstage_bytes < need) {
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return WF_ECUDA;
+        if (h->bstage) cudaFree(h->bstage);
+        h->bstage = nullptr;
+        h->bstage_bytes = 0;
+        if (cudaMalloc(&h->bstage, need) != cudaSuccess) return WF_ENOMEM;
+        h->bstage_bytes = need;
+    }
+    if (!h->io_in) {
+        if (cudaStreamCreateWithFlags(&h->io_in, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&h->io_out, cudaStreamNonBlocking) != cudaSuccess)
+            return WF_ECUDA;
+        for (cudaEvent_t& e : h->ev_io)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return WF_ECUDA;
+    }
+    if (upload_active(h) != cudaSuccess) return WF_ECUDA;
+    const char* hin[2] = {static_cast<const char*>(Tin), static_cast<const char*>(Fin)};
+    char* hout[2] = {static_cast<char*>(Tout), static_cast<char*>(Fout)};
+    char* st[2] = {reinterpret_cast<char*>(h->bstage), reinterpret_cast<char*>(h->bstage) + n * es};
+    void* dev[2] = {h->T, h->phi};
+    cudaStream_t s = h->stream, sin = h->io_in, sout = h->io_out;
+    cudaEvent_t* ev_in = h->ev_io;
+    cudaEvent_t* ev_done = h->ev_io + 8;
+    cudaEvent_t ev_start = h->ev_io[16], ev_end = h->ev_io[17];
+    cudaError_t e = cudaEventRecord(ev_start, s);  // after the handle's earlier work
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sin, ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, ev_start, 0);
+    for (int g = 0; g < G && e == cudaSuccess; ++g) {
+        const int z0 = (int)((long)g * h->S / G), cnt = (int)((long)(g + 1) * h->S / G) - z0;
+        const size_t off = (size_t)z0 * per * es, bytes = (size_t)cnt * per * es;
+        for (int f = 0; f < 2 && e == cudaSuccess; ++f)
+            e = cudaMemcpyAsync(st[f] + off, hin[f] + off, bytes, cudaMemcpyHostToDevice, sin);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in[g], sin);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_in[g], 0);
+        for (int f = 0; f < 2 && e == cudaSuccess; ++f)
+            e = launch_convert_batch(1, h->prec, st[f] + off, host32, at(h, dev[f], z0), h->sbytes, cnt, h->Nx,
+                                     h->Ny, h->pitch, s);
+        if (e == cudaSuccess && steps > 0) {
+            h->gz0 = z0;
+            h->gn = cnt;
+            rebase_slots(h, z0);
+            for (int k = 0; k < steps && e == cudaSuccess; ++k) e = enqueue_step(h);
+            rebase_slots(h, 0);
+            h->gz0 = h->gn = 0;
+        }
+        for (int f = 0; f < 2 && e == cudaSuccess; ++f)
+            e = launch_convert_batch(0, h->prec, st[f] + off, host32, at(h, dev[f], z0), h->sbytes, cnt, h->Nx,
+                                     h->Ny, h->pitch, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_done[g], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, ev_done[g], 0);
+        for (int f = 0; f < 2 && e == cudaSuccess; ++f)
+            e = cudaMemcpyAsync(hout[f] + off, st[f] + off, bytes, cudaMemcpyDeviceToHost, sout);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev_end, sout);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_end, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? WF_OK : WF_ECUDA;
+}
+
+int wf_batch_run(wf_handle* h, const double* T_in, const double* fuel_in, double* T_out, double* fuel_out,
+                 size_t n, int steps, int groups) {
+    if (!h) return WF_EINVAL;
+    return batch_run(h, T_in, fuel_in, T_out, fuel_out, n, steps, groups, 0);
+}
+
+int wf_batch_run_f32(wf_handle* h, const float* T_in, const float* fuel_in, float* T_out, float* fuel_out,
+                     size_t n, int steps, int groups) {
+    if (!h) return WF_EINVAL;
+    return batch_run(h, T_in, fuel_in, T_out, fuel_out, n, steps, groups, 1);
 }
 
 int wf_batch_set_states(wf_handle* h, const double* T, const double* fuel, size_t n) {

@@ -96,6 +96,8 @@ def lib() -> ctypes.CDLL:
         L.wf_batch_set_states_f32.argtypes = [vp, fp, fp, sz]
         L.wf_batch_get_states.argtypes = [vp, dp, dp, sz]
         L.wf_batch_get_states_f32.argtypes = [vp, fp, fp, sz]
+        L.wf_batch_run.argtypes = [vp, dp, dp, dp, dp, sz, i, i]
+        L.wf_batch_run_f32.argtypes = [vp, fp, fp, fp, fp, sz, i, i]
         L.wf_get_dims.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
         L.wf_set_stream.argtypes = [vp, vp]
         L.wf_set_profiling.argtypes = [vp, i]
@@ -260,6 +262,15 @@ def wf_batch_states_ptr(h, T_ptr: int, fuel_ptr: int, n: int, f32: bool, set_: b
     fn = getattr(lib(), name)
     _check(fn(h, ctypes.cast(T_ptr, tp) if T_ptr else None, ctypes.cast(fuel_ptr, tp) if fuel_ptr else None, n),
            name)
+
+
+def wf_batch_run_ptr(h, T_in: int, fuel_in: int, T_out: int, fuel_out: int, n: int, steps: int, groups: int,
+                     f32: bool) -> None:
+    """End-to-end run through raw host addresses: states in, `steps` steps, states out ([S][Ny][Nx])."""
+    tp = ctypes.POINTER(ctypes.c_float if f32 else ctypes.c_double)
+    name = "wf_batch_run_f32" if f32 else "wf_batch_run"
+    _check(getattr(lib(), name)(h, ctypes.cast(T_in, tp), ctypes.cast(fuel_in, tp), ctypes.cast(T_out, tp),
+                                ctypes.cast(fuel_out, tp), n, steps, groups), name)
 
 
 def wf_set_stream(h, stream_ptr: Optional[int]) -> None:
