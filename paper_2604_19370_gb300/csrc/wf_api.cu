@@ -565,6 +565,8 @@ LineArgs line_args(wf_handle* h, int xsite) {
     a.tmax = kTmax;
     a.tstatus = h->status;
     a.wait_ns = h->wait_ns;
+    // every y pass of a step reads a right-hand side that the step writes again before its next use
+    a.in_dead = xdir ? 0 : 1;
     a.b = batch(h);
     return a;
 }

@@ -201,6 +201,8 @@ struct LineArgs {
     const void* base[2];    // y pass only: out = base + solution (or NULL: out = solution)
     int* status;            // y pass only: guard flag for out[0] (or NULL)
     int* tstatus;           // x pass: flag word whose bit 4 records a bounded wait that gave up
+    int in_dead;            // y pass: the input arrays are dead after the pass (a kernel may use them
+                            // as scratch)
     long long wait_ns;      // limit of a bounded device wait (ns of %globaltimer; 0: give up at once)
     double tmax;
     Batch b;  // per scenario: in, out, factors, premul, base, status, pre*

@@ -382,6 +382,148 @@ __global__ void __launch_bounds__(256) k_ysolve_cols(const FastArgs<P> a) {
     if (bad && v.status != nullptr && arr == 0) atomicOr(v.status, 1);
 }
 
+// y pass for long lines (many chunks): CTA = 32 columns x C chunks (up to 1024 threads), thread
+// tid = k*32 + c owns chunk k of column c, so a warp's loads and stores cover 32 consecutive columns
+// (128-byte row pieces) whatever the chunk count.  The chunk's partial results are kept in the
+// pass's input array (the right-hand side, dead after the pass: LineArgs::in_dead) instead of a
+// shared-memory strip (a strip per thread of a long chunk fills the shared memory with one CTA of
+// eight columns): each thread overwrites the input elements it has read and reads them back in the
+// later sweeps (its own writes, in program order; the CTA's column block stays in L2); neighbouring
+// chunks exchange their first and last p values through shared memory.
+// Per column the operations, and their order, are those of k_ysolve_cols: the same bits.
+template <typename P, int PD, int B>
+__global__ void __launch_bounds__(1024) k_ysolve_long(const FastArgs<P> a) {
+    constexpr int B2 = 8;
+    constexpr int NF = FacW<PD>::F, NU = FacW<PD>::U, NS = FacW<PD>::S;
+    if (!scene_active(a.b)) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int tid = threadIdx.x;
+    const Chunks ch = a.ch;
+    const int C = ch.C, base = ch.base;
+    constexpr int G = 32;
+    const int mmax = base + 2 * PD;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // 16 bytes: the factors' mbarrier
+    const FacSmem<P, PD> fm(reinterpret_cast<P*>(smem_raw + 16), mmax);
+    P* xch = fm.end();  // [C][G][2p]: the first and the last p values of every chunk
+    const int arr = blockIdx.y;
+    const int k = tid / G, c = tid - k * G;
+    const int s = k * base;
+    const int m = (k < C - 1) ? base : ch.last;
+    const int t = chunk_type(ch, k);
+    const int line = blockIdx.x * G + c;
+    const bool valid = line < a.nlines;  // threads past the last line only take part in the barriers
+    const LineView<P> v = scene_line(a, arr);
+    const size_t pitch = (size_t)a.pitch;
+    const bool fbulk = v.fpad != nullptr;
+    if (fbulk) {
+        if (tid == 0) {
+            const uint32_t fbytes = (uint32_t)(fac_elems<PD>(mmax) * sizeof(P));
+            mbar_init(bar, 1);
+            mbar_fence_init();
+            mbar_expect_tx(bar, fbytes);
+            bulk_load(fm.F, v.fpad, fbytes, bar);
+        }
+    } else {
+        stage_factors<P, PD>(v, mmax, fm);
+    }
+    __syncthreads();
+    if (fbulk) {
+        const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0, a.wait_ns));
+        if (!ok) {
+            mbar_drain(bar, 0);
+            if (tid == 0 && v.tstatus) atomicOr(v.tstatus, 4);
+            return;
+        }
+    }
+    P* g = const_cast<P*>(v.in) + (size_t)s * pitch + (valid ? line : 0);  // this chunk's input elements
+    P top[PD], bot[PD];
+    if (valid) {
+        const P* Fk = fm.F + t * mmax * NF;
+        P prev[PD];
+#pragma unroll
+        for (int i = 0; i < PD; ++i) prev[i] = P(0);
+        const P* src = v.in + (size_t)s * pitch + line;  // the elements g overwrites, each after its read
+        int o = 0;
+        for (; o + B <= m; o += B) {
+            P r[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) r[q] = src[q * pitch];
+            src += B * pitch;
+            fwd_rows<P, PD, B>(r, Fk + o * NF, prev);
+#pragma unroll
+            for (int q = 0; q < B; ++q) g[(size_t)(o + q) * pitch] = r[q];
+        }
+        for (; o < m; ++o) {
+            P r[1] = {*src};
+            src += pitch;
+            fwd_rows<P, PD, 1>(r, Fk + o * NF, prev);
+            g[(size_t)o * pitch] = r[0];
+        }
+        // backward substitution from the last row up, on the elements just written
+        const P* Uk = fm.U + t * mmax * NU;
+#pragma unroll
+        for (int i = 0; i < PD; ++i) prev[i] = P(0);
+        int top_r = m - 1;
+        for (; top_r - B2 + 1 >= 0; top_r -= B2) {
+            P gv[B2];
+#pragma unroll
+            for (int q = 0; q < B2; ++q) gv[q] = g[(size_t)(top_r - q) * pitch];
+            bwd_rows<P, PD, B2>(gv, Uk + top_r * NU, prev);
+#pragma unroll
+            for (int q = 0; q < B2; ++q) g[(size_t)(top_r - q) * pitch] = gv[q];
+        }
+        for (; top_r >= 0; --top_r) {
+            P gv[1] = {g[(size_t)top_r * pitch]};
+            bwd_rows<P, PD, 1>(gv, Uk + top_r * NU, prev);
+            g[(size_t)top_r * pitch] = gv[0];
+        }
+        P* mine = xch + (size_t)tid * 2 * PD;
+#pragma unroll
+        for (int q = 0; q < PD; ++q) {
+            top[q] = g[(size_t)q * pitch];
+            bot[q] = g[(size_t)(base - PD + q) * pitch];
+            mine[q] = top[q];
+            mine[PD + q] = bot[q];
+        }
+    }
+    __syncthreads();
+    if (!valid) return;  // no barrier follows
+    const P* nx = xch + (size_t)((k + 1 < C ? k + 1 : k) * G + c) * 2 * PD;
+    const P* pv = xch + (size_t)((k > 0 ? k - 1 : k) * G + c) * 2 * PD + PD;
+    P nt[PD], pb[PD], tn[PD], bp[PD];
+#pragma unroll
+    for (int q = 0; q < PD; ++q) {
+        nt[q] = nx[q];
+        pb[q] = pv[q];
+    }
+    interface_solve<P, PD>(ch, k, mmax, fm.S, fm.E, top, bot, nt, pb, tn, bp);
+    const P* Sk = fm.S + t * mmax * NS;
+    const P* bs = v.base ? v.base + (size_t)s * pitch + line : nullptr;  // may be the output array
+    P* dst = v.out + (size_t)s * pitch + line;
+    const P tmax = a.tmax;
+    bool bad = false;
+    auto finish = [&](auto nrows, int o) {
+        constexpr int R = decltype(nrows)::value;
+        P x[R], bv[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            x[q] = g[(size_t)(o + q) * pitch];
+            bv[q] = bs ? bs[(size_t)(o + q) * pitch] : P(0);
+        }
+        spike_rows<P, PD, R>(x, Sk + o * NS, tn, bp);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const P y = x[q] + bv[q];
+            dst[(size_t)(o + q) * pitch] = y;
+            bad |= !(fabs(y) <= tmax);  // also catches NaN
+        }
+    };
+    int o = 0;
+    for (; o + B2 <= m; o += B2) finish(std::integral_constant<int, B2>{}, o);
+    for (; o < m; ++o) finish(std::integral_constant<int, 1>{}, o);
+    if (bad && v.status != nullptr && arr == 0) atomicOr(v.status, 1);
+}
+
 template <typename P, int PD, bool X>
 cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
     constexpr int W = 2 * PD + 1;
@@ -466,6 +608,25 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         kern<<<grid, 32 * (G / lpw), smem, s>>>(f);
         count_launches(1);
     } else {
+        int sms = 152, dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // long lines (more than 8 chunks) whose input is dead after the pass, no prescale band, and
+        // enough 32-column blocks for half the SMs: 32 columns per CTA, partial results in the input
+        bool lng = a.in_dead && ch.C > 8 && (long)((a.nlines + 31) / 32) * a.narr * a.b.S >= sms / 2;
+        for (int q = 0; q < a.narr; ++q) lng = lng && a.premul[q] == nullptr;
+        if (lng) {
+            const int ntl = 32 * ch.C;
+            const size_t smeml = 16 + fbytes + (size_t)ntl * 2 * PD * sizeof(P);
+            f.G = 32;
+            f.tma = 0;
+            dim3 grid((a.nlines + 31) / 32, a.narr, a.b.S);
+            auto kern = k_ysolve_long<P, PD, 16>;
+            cudaError_t e = allow_dynamic_smem(kern, smeml);
+            if (e != cudaSuccess) return e;
+            kern<<<grid, ntl, smeml, s>>>(f);
+            count_launches(1);
+            return cudaGetLastError();
+        }
         int G = a.G > 0 ? (a.G < 256 ? a.G : 256) : (sizeof(P) == 4 ? 8 : 4);
         while (G > 1 && G * ch.C > 256) G /= 2;
         const int nt = G * ch.C;
@@ -477,8 +638,6 @@ cudaError_t run_fast(const LineArgs& a, cudaStream_t s) {
         // rows loaded per batch: 32 when the launch leaves at most two CTAs per SM (its threads then
         // wait on load latency, and more loads in flight pay), else 16 (fewer registers, more CTAs)
         dim3 grid((a.nlines + G - 1) / G, a.narr, a.b.S);
-        int sms = 152, dev = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const bool wide = (long)grid.x * grid.y * grid.z <= 2L * sms;
         auto kern = wide ? k_ysolve_cols<P, PD, 32> : k_ysolve_cols<P, PD, 16>;
         cudaError_t e = allow_dynamic_smem(kern, (size_t)smem);
