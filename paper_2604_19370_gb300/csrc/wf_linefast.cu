@@ -481,7 +481,8 @@ __global__ void __launch_bounds__(1024) k_ysolve_long(const FastArgs<P> a) {
 #pragma unroll
         for (int q = 0; q < PD; ++q) {
             top[q] = g[(size_t)q * pitch];
-            bot[q] = g[(size_t)(base - PD + q) * pitch];
+            // the last chunk may be shorter than base (its last p values are not used)
+            bot[q] = (k + 1 < C) ? g[(size_t)(base - PD + q) * pitch] : P(0);
             mine[q] = top[q];
             mine[PD + q] = bot[q];
         }
