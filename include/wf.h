@@ -255,7 +255,7 @@ int wf_launch_count(unsigned long long* n);
  *             side of its second x pass: 1 inside that pass (from staged rows
  *             of T* and F), 2 in a streaming matvec kernel before it (one more
  *             pass over R, but every thread busy on short lines);
- *   shape[6]  step form: 1 one launch per pass (six or seven per step), 2 one
+ *   shape[6]  step form: 1 one launch per pass (seven or eight per step), 2 one
  *             persistent launch per step over every active slot (Peaceman-
  *             Rachford with one F per step, FP32, p <= 2, wind rank <= 2,
  *             no manufactured forcing; elsewhere the per-pass form runs),
