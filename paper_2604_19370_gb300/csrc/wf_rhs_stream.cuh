@@ -565,6 +565,89 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
     // one element row.  HOT: some point may exceed the ignition temperature, so the reaction term
     // is evaluated point by point; otherwise it is zero at every point (E = 0: no reaction source,
     // no fuel change), which is exactly what the point-by-point test would give
+    // the odd Gauss point of the x direction at y point b (q = Q - 1, the one-point form)
+    auto odd_one = [&](int b, auto hot_c) {
+        constexpr bool HOT = decltype(hot_c)::value;
+        constexpr int q = Q - 1;
+        P T = 0, Ty = 0, Tx = 0, ph = 0;
+#pragma unroll
+        for (int l = 0; l < NB; ++l) {
+            T += it.by[b][l] * xvs[l];
+            Ty += it.dy[b][l] * xvs[l];
+            Tx += it.by[b][l] * xds[l];
+            if (HOT) ph += it.by[b][l] * xps[l];
+        }
+        P bpx = 0, bpy = 0;
+#pragma unroll
+        for (int r = 0; r < WR; ++r) {
+            bpx += fxs[r] * gxr[r][b];
+            bpy += fys[r] * gyr[r][b];
+        }
+        const P T2 = T * T, T3 = T2 * T;
+        P src = fma(-c.c_rad, T2 * T2, c.K0);
+        P EP = P(0);
+        if (HOT) {
+            const bool burn = (T > c.T_ig) && (ph > c.phi_min);
+            const P E = burn ? T * arrhenius<P>(c, T) : P(0);
+            EP = E * ph;
+            src = fma(c.K_ign, c.heat_by_fuel ? EP : E, src);
+        }
+        if (WR > 0) src = fma(-c.c_W, fma(bpx, Tx, bpy * Ty), src);
+        const P t3x = T3 * Tx, t3y = T3 * Ty;
+#pragma unroll
+        for (int l = 0; l < NB; ++l) {
+            ass[l] = fma(it.ys[b][q][l], src, fma(it.yd[b][q][l], t3y, ass[l]));
+            aqs[l] = fma(it.yq[b][q][l], t3x, aqs[l]);
+            if (HOT) ags[l] = fma(it.yg[b][q][l], EP, ags[l]);
+        }
+    };
+    // the odd Gauss point of the x direction at y points b0 and b0 + 1, side by side in packed FMAs
+    // (each lane of a pair computes what odd_one computes for its y point)
+    auto odd_pair = [&](int b0, auto hot_c) {
+        constexpr bool HOT = decltype(hot_c)::value;
+        constexpr int q = Q - 1;
+        const int b1 = b0 + 1;
+        float2 T = f2(0.f), Ty = f2(0.f), Tx = f2(0.f), ph = f2(0.f);
+#pragma unroll
+        for (int l = 0; l < NB; ++l) {
+            const float2 by = make_float2(it.by[b0][l], it.by[b1][l]), dy = make_float2(it.dy[b0][l], it.dy[b1][l]);
+            T = fma2(by, f2(xvs[l]), T);
+            Ty = fma2(dy, f2(xvs[l]), Ty);
+            Tx = fma2(by, f2(xds[l]), Tx);
+            if (HOT) ph = fma2(by, f2(xps[l]), ph);
+        }
+        float2 bpx = f2(0.f), bpy = f2(0.f);
+#pragma unroll
+        for (int r = 0; r < WR; ++r) {
+            bpx = fma2(f2(fxs[r]), make_float2(gxr[r][b0], gxr[r][b1]), bpx);
+            bpy = fma2(f2(fys[r]), make_float2(gyr[r][b0], gyr[r][b1]), bpy);
+        }
+        const float2 T2 = mul2(T, T), T3 = mul2(T2, T);
+        float2 src = fma2(f2(-c.c_rad), mul2(T2, T2), f2(c.K0));
+        float2 EP = f2(0.f);
+        if (HOT) {
+            const bool bx0 = (T.x > c.T_ig) && (ph.x > c.phi_min);
+            const bool bx1 = (T.y > c.T_ig) && (ph.y > c.phi_min);
+            const float2 E = make_float2(bx0 ? T.x * arrhenius<P>(c, T.x) : P(0),
+                                         bx1 ? T.y * arrhenius<P>(c, T.y) : P(0));
+            EP = mul2(E, ph);
+            src = fma2(f2(c.K_ign), c.heat_by_fuel ? EP : E, src);
+        }
+        if (WR > 0) src = fma2(f2(-c.c_W), fma2(bpx, Tx, mul2(bpy, Ty)), src);
+        const float2 t3x = mul2(T3, Tx), t3y = mul2(T3, Ty);
+#pragma unroll
+        for (int l = 0; l < NB; ++l) {
+            ass[l] = fma(it.ys[b0][q][l], src.x, fma(it.yd[b0][q][l], t3y.x, ass[l]));
+            aqs[l] = fma(it.yq[b0][q][l], t3x.x, aqs[l]);
+            if (HOT) ags[l] = fma(it.yg[b0][q][l], EP.x, ags[l]);
+        }
+#pragma unroll
+        for (int l = 0; l < NB; ++l) {
+            ass[l] = fma(it.ys[b1][q][l], src.y, fma(it.yd[b1][q][l], t3y.y, ass[l]));
+            aqs[l] = fma(it.yq[b1][q][l], t3x.y, aqs[l]);
+            if (HOT) ags[l] = fma(it.yg[b1][q][l], EP.y, ags[l]);
+        }
+    };
     auto element_row_body = [&](auto hot_c) {
         constexpr bool HOT = decltype(hot_c)::value;
 #pragma unroll
@@ -608,40 +691,14 @@ __device__ __forceinline__ void stream_strip_pairs(const StreamArgs<float>& a, c
                     if (HOT) ag2[l][j] = fma2(pt.yg[b][l][j], EP, ag2[l][j]);
                 }
             }
-            if (QS) {
-                constexpr int q = Q - 1;
-                P T = 0, Ty = 0, Tx = 0, ph = 0;
+        }
+        if (QS) {
+            // the odd Gauss point of the x direction: y points b and b+1 side by side in packed FMAs,
+            // then the last y point alone; per y point the operations, and their order into each
+            // accumulator, are those of the one-point form
 #pragma unroll
-                for (int l = 0; l < NB; ++l) {
-                    T += it.by[b][l] * xvs[l];
-                    Ty += it.dy[b][l] * xvs[l];
-                    Tx += it.by[b][l] * xds[l];
-                    if (HOT) ph += it.by[b][l] * xps[l];
-                }
-                P bpx = 0, bpy = 0;
-#pragma unroll
-                for (int r = 0; r < WR; ++r) {
-                    bpx += fxs[r] * gxr[r][b];
-                    bpy += fys[r] * gyr[r][b];
-                }
-                const P T2 = T * T, T3 = T2 * T;
-                P src = fma(-c.c_rad, T2 * T2, c.K0);
-                P EP = P(0);
-                if (HOT) {
-                    const bool burn = (T > c.T_ig) && (ph > c.phi_min);
-                    const P E = burn ? T * arrhenius<P>(c, T) : P(0);
-                    EP = E * ph;
-                    src = fma(c.K_ign, c.heat_by_fuel ? EP : E, src);
-                }
-                if (WR > 0) src = fma(-c.c_W, fma(bpx, Tx, bpy * Ty), src);
-                const P t3x = T3 * Tx, t3y = T3 * Ty;
-#pragma unroll
-                for (int l = 0; l < NB; ++l) {
-                    ass[l] = fma(it.ys[b][q][l], src, fma(it.yd[b][q][l], t3y, ass[l]));
-                    aqs[l] = fma(it.yq[b][q][l], t3x, aqs[l]);
-                    if (HOT) ags[l] = fma(it.yg[b][q][l], EP, ags[l]);
-                }
-            }
+            for (int b = 0; b + 1 < Q; b += 2) odd_pair(b, hot_c);
+            if (Q % 2) odd_one(Q - 1, hot_c);
         }
     };
 
