@@ -719,26 +719,55 @@ __global__ void __launch_bounds__(128) k_matvec_stream(int Nx, int Ny, int pitch
     }
     // x-convolution of every row (outputs lanes read lanes lane - p .. lane + p)
     P w1[NR], w2[NR];
-#pragma unroll
-    for (int i = 0; i < NR; ++i) {
-        P t1 = 0, t2 = 0;
-#pragma unroll
-        for (int dk = 0; dk < W; ++dk) {
-            const P val = (dk == PD) ? tv[i] : __shfl_sync(0xffffffffu, tv[i], (lane - PD + dk) & 31);
-            t1 += a1v[dk] * val;
-            t2 += a2v[dk] * val;
-        }
-        w1[i] = t1;
-        w2[i] = t2;
-    }
-    if (!out) return;
-    if (yint) {
-        P b1i[W], b2i[W];
+    if constexpr (sizeof(P) == 4 && NR % 2 == 0) {
+        // FP32: rows i and i+1 side by side in packed FMAs (per row the same operations)
+        float2 a1p[W], a2p[W];
 #pragma unroll
         for (int d = 0; d < W; ++d) {
-            b1i[d] = c1 * B1[(size_t)(2 * PD) * W + d];
-            b2i[d] = A2 ? c2 * B2[(size_t)(2 * PD) * W + d] : P(0);
+            a1p[d] = make_float2(a1v[d], a1v[d]);
+            a2p[d] = make_float2(a2v[d], a2v[d]);
         }
+#pragma unroll
+        for (int i = 0; i < NR; i += 2) {
+            float2 t1 = make_float2(0.f, 0.f), t2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int dk = 0; dk < W; ++dk) {
+                const int src = (lane - PD + dk) & 31;
+                const float2 val = (dk == PD) ? make_float2(tv[i], tv[i + 1])
+                                              : make_float2(__shfl_sync(0xffffffffu, tv[i], src),
+                                                            __shfl_sync(0xffffffffu, tv[i + 1], src));
+                t1 = __ffma2_rn(a1p[dk], val, t1);
+                t2 = __ffma2_rn(a2p[dk], val, t2);
+            }
+            w1[i] = t1.x;
+            w1[i + 1] = t1.y;
+            w2[i] = t2.x;
+            w2[i + 1] = t2.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            P t1 = 0, t2 = 0;
+#pragma unroll
+            for (int dk = 0; dk < W; ++dk) {
+                const P val = (dk == PD) ? tv[i] : __shfl_sync(0xffffffffu, tv[i], (lane - PD + dk) & 31);
+                t1 += a1v[dk] * val;
+                t2 += a2v[dk] * val;
+            }
+            w1[i] = t1;
+            w2[i] = t2;
+        }
+    }
+    if (!out) return;
+    // the interior y bands (rows 2p .. Ny-2p-1 of a band all equal row 2p), where such rows exist
+    const bool has_int = Ny > 4 * PD;
+    P b1i[W], b2i[W];
+#pragma unroll
+    for (int d = 0; d < W; ++d) {
+        b1i[d] = has_int ? c1 * B1[(size_t)(2 * PD) * W + d] : P(0);
+        b2i[d] = (has_int && A2) ? c2 * B2[(size_t)(2 * PD) * W + d] : P(0);
+    }
+    if (yint) {
         P* rp = R + (size_t)j0 * pitch + x;
 #pragma unroll
         for (int o = 0; o < RS; ++o) {
@@ -754,11 +783,17 @@ __global__ void __launch_bounds__(128) k_matvec_stream(int Nx, int Ny, int pitch
         const int j = j0 + o;
         if (j >= Ny) break;
         P acc = Fscale * fv[o];
+        if (j < 2 * PD || j >= Ny - 2 * PD) {
+            // the first and last 2p rows have bands of their own
 #pragma unroll
-        for (int dl = 0; dl < W; ++dl) {
-            const P b1 = c1 * B1[(size_t)j * W + dl];
-            const P b2 = A2 ? c2 * B2[(size_t)j * W + dl] : P(0);
-            acc = fma(b1, w1[o + dl], fma(b2, w2[o + dl], acc));
+            for (int dl = 0; dl < W; ++dl) {
+                const P b1 = c1 * B1[(size_t)j * W + dl];
+                const P b2 = A2 ? c2 * B2[(size_t)j * W + dl] : P(0);
+                acc = fma(b1, w1[o + dl], fma(b2, w2[o + dl], acc));
+            }
+        } else {
+#pragma unroll
+            for (int dl = 0; dl < W; ++dl) acc = fma(b1i[dl], w1[o + dl], fma(b2i[dl], w2[o + dl], acc));
         }
         R[(size_t)j * pitch + x] = acc;
     }
@@ -824,16 +859,16 @@ cudaError_t launch_pad_factors(int prec, int p, int mmax, const void* luc, const
 }
 
 cudaError_t launch_matvec(int prec, int p, const MatvecArgs& a, cudaStream_t s) {
-    // output rows per warp item: 8 for p <= 2; 16 for p = 3, whose 2p-row halo would otherwise
-    // nearly double the rows a warp loads
+    // output rows per warp item: 16 (the 2p halo rows and the item's setup spread over more
+    // outputs), except 8 for FP64 with p <= 2, where 16 rows would take twice the registers
     constexpr int WARPS = 4;
     if (p < 1 || p > 3) return cudaErrorInvalidValue;
-    const int rs = p > 2 ? 16 : 8;
+    const int rs = (prec != 0 && p <= 2) ? 8 : 16;
     const int nstrips = (a.Nx + (32 - 2 * p) - 1) / (32 - 2 * p), nsegs = (a.Ny + rs - 1) / rs;
     const long items = (long)nstrips * nsegs;
     dim3 grid((unsigned)((items + WARPS - 1) / WARPS), 1, a.b.S), block(32 * WARPS);
 #define WF_MV(P, PD)                                                                                          \
-    k_matvec_stream<P, PD, (PD > 2 ? 16 : 8)><<<grid, block, 0, s>>>(                                         \
+    k_matvec_stream<P, PD, (sizeof(P) == 8 && PD <= 2 ? 8 : 16)><<<grid, block, 0, s>>>(                                         \
         a.Nx, a.Ny, a.pitch, (const P*)a.T, (const P*)a.F, (P*)a.R, (const P*)a.A1, (const P*)a.B1,           \
         (const P*)a.A2, (const P*)a.B2, (P)a.Fscale, (P)a.c1, (P)a.c2, a.b, nstrips, nsegs)
     if (prec == 0) {

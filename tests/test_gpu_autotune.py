@@ -54,10 +54,12 @@ def test_shapes_do_not_change_results(wf, prec, scheme):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_shapes_do_not_change_results_cubic(wf, prec):
-    # p = 3: the matvec's taller items and the fused right-hand side give the same bits
+@pytest.mark.parametrize("p", [1, 3])
+def test_shapes_do_not_change_results_p1_p3(wf, prec, p):
+    # p = 1 and p = 3: the matvec's items (16 rows; 8 in FP64 at p = 1) and the fused right-hand
+    # side give the same bits
     P = wf.WF_FP32 if prec == "fp32" else wf.WF_FP64
-    sc = make_scenario("shape3", 120, 3, 1e-3, 1, 95, wind=(-0.9, 1.1), fuel_sigma=3.0)
+    sc = make_scenario(f"shape{p}", 120, p, 1e-3, 1, 95, wind=(-0.9, 1.1), fuel_sigma=3.0)
     ref = None
     for shape in [(0, 0, 0, 0, 0, 0), (8, 16, 32, 2, 4, 2), (1, 4, 16, 1, 2, 1), (4, 2, 64, 0, 8, 2)]:
         sim = _sim(wf, sc, P, wf.WF_PR)
