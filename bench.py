@@ -541,6 +541,9 @@ def run_ensemble(args) -> None:
                             True)
     e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dev)
     b.close()
+    # the host link's own rates, on the same pinned arrays (their contents are no longer needed)
+    link = link_bound(wf.wf_measure_host_link_ptr(hT.data_ptr(), hP.data_ptr(), hT.numel() * 4), 2 * 4 * dofs,
+                      2 * 4 * dofs, e2e_s * 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -567,7 +570,8 @@ def run_ensemble(args) -> None:
         "e2e": {"value": world * dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * dofs,
                 "d2h_bytes_per_step": 2 * 4 * dofs, "ms_per_step": e2e_s * 1e3, "host_dtype": "float32",
                 "call": "wf_batch_run_f32 (states in, one step, states out)", "groups": e2e_groups,
-                "trial_ms_per_step": {str(g): round(t * 1e3, 4) for g, t in e2e_try.items()}},
+                "trial_ms_per_step": {str(g): round(t * 1e3, 4) for g, t in e2e_try.items()},
+                "host_link": link},
         "clocks": clk.summary(),
         "status": wf.wf_strerror(status),
     }
@@ -785,6 +789,20 @@ def run_single(args) -> None:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def link_bound(rates, bytes_in: int, bytes_out: int, e2e_ms: float) -> dict:
+    """The host-link bound of an end-to-end step: its copies at the measured rates.
+
+    rates = (host to device, device to host, both directions at once) in GB/s.  The step needs at
+    least as long as either direction alone and as both directions' bytes at the combined rate.
+    """
+    h2d, d2h, both = rates
+    bound_ms = max(bytes_in / h2d, bytes_out / d2h, (bytes_in + bytes_out) / both) / 1e6
+    return {"h2d_gbs": h2d, "d2h_gbs": d2h, "both_gbs": both, "bound_ms_per_step": bound_ms,
+            "frac": bound_ms / e2e_ms,
+            "source": "measured: wf_measure_host_link (cudaMemcpyAsync between pinned host arrays and the "
+                      "device, each direction alone and both at once, best of three)"}
 
 
 def _percentile(xs, q):

@@ -493,6 +493,21 @@ int wf_step_noalloc(wf_handle* h, void* T, void* fuel, int pitch, int nsteps);
  */
 int wf_measure_fma_peak(int precision, double* tflops);
 
+/*
+ * Measure the copy rate (GB/s) between pinned host memory and this GPU:
+ * host_in -> device (gbs_h2d), device -> host_out (gbs_d2h), and both at
+ * once on two streams (gbs_both: the bytes of both directions over the
+ * time of the pair).  host_in and host_out: caller-owned page-locked
+ * arrays of `bytes` bytes each (host_out is overwritten); best of three
+ * copies after a warm-up, CUDA events.  The bound of an end-to-end step
+ * whose states come from and return to host memory.  Allocates and frees
+ * two device buffers of `bytes`, two streams and two events; synchronises.
+ * Errors: WF_EINVAL (a NULL pointer, bytes = 0), WF_ENOMEM, WF_ECUDA.  No
+ * counterpart in the paper.
+ */
+int wf_measure_host_link(const void* host_in, void* host_out, size_t bytes, double* gbs_h2d, double* gbs_d2h,
+                         double* gbs_both);
+
 /* Free every resource of the handle (NULL is accepted). */
 void wf_destroy(wf_handle* h);
 

@@ -133,3 +133,53 @@ extern "C" int wf_measure_fma_peak(int precision, double* tflops) {
     *tflops = best;
     return WF_OK;
 }
+
+// Host-link probe: the copy rate between caller-owned pinned host arrays and the device, alone in
+// each direction and with both directions at once (two streams), each best of three after a
+// warm-up.  It bounds any end-to-end step whose inputs arrive from, and whose results return to,
+// host memory.
+extern "C" int wf_measure_host_link(const void* host_in, void* host_out, size_t bytes, double* gbs_h2d,
+                                    double* gbs_d2h, double* gbs_both) {
+    if (!host_in || !host_out || bytes == 0 || !gbs_h2d || !gbs_d2h || !gbs_both) return WF_EINVAL;
+    void *din = nullptr, *dout = nullptr;
+    if (cudaMalloc(&din, bytes) != cudaSuccess) return WF_ENOMEM;
+    if (cudaMalloc(&dout, bytes) != cudaSuccess) {
+        cudaFree(din);
+        return WF_ENOMEM;
+    }
+    cudaStream_t s = nullptr, s2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dout, 0, bytes, s);
+    float t_in = 0.f, t_out = 0.f, t_both = 0.f;
+    if (e == cudaSuccess)
+        e = time_best([&] { cudaMemcpyAsync(din, host_in, bytes, cudaMemcpyHostToDevice, s); }, s, &t_in);
+    if (e == cudaSuccess)
+        e = time_best([&] { cudaMemcpyAsync(host_out, dout, bytes, cudaMemcpyDeviceToHost, s); }, s, &t_out);
+    if (e == cudaSuccess)
+        e = time_best(
+            [&] {
+                cudaEventRecord(fork, s);
+                cudaStreamWaitEvent(s2, fork, 0);
+                cudaMemcpyAsync(din, host_in, bytes, cudaMemcpyHostToDevice, s);
+                cudaMemcpyAsync(host_out, dout, bytes, cudaMemcpyDeviceToHost, s2);
+                cudaEventRecord(join, s2);
+                cudaStreamWaitEvent(s, join, 0);
+            },
+            s, &t_both);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (join) cudaEventDestroy(join);
+    if (fork) cudaEventDestroy(fork);
+    if (s2) cudaStreamDestroy(s2);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(dout);
+    cudaFree(din);
+    if (e != cudaSuccess) return WF_ECUDA;
+    *gbs_h2d = (double)bytes / (t_in * 1e-3) / 1e9;
+    *gbs_d2h = (double)bytes / (t_out * 1e-3) / 1e9;
+    *gbs_both = 2.0 * (double)bytes / (t_both * 1e-3) / 1e9;
+    return WF_OK;
+}

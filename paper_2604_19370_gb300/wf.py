@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
         L.wf_batch_bytes.argtypes = [i, i, i, d, ctypes.POINTER(wf_params), i, ctypes.POINTER(sz)]
         L.wf_set_wait_limit.argtypes = [vp, d]
         L.wf_measure_fma_peak.argtypes = [i, dp]
+        L.wf_measure_host_link.argtypes = [vp, vp, sz, dp, dp, dp]
         L.wf_server_create.argtypes = [sz, i, ctypes.POINTER(vp)]
         L.wf_submit.argtypes = [vp, ctypes.POINTER(wf_request), ctypes.POINTER(ctypes.c_uint64)]
         L.wf_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(wf_result)]
@@ -422,6 +423,15 @@ def wf_measure_fma_peak(precision: int) -> float:
     t = ctypes.c_double()
     _check(lib().wf_measure_fma_peak(precision, ctypes.byref(t)), "wf_measure_fma_peak")
     return t.value
+
+
+def wf_measure_host_link_ptr(host_in: int, host_out: int, nbytes: int):
+    """Copy rates (GB/s) between pinned host arrays (raw addresses) and the GPU:
+    (host to device, device to host, both directions at once)."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().wf_measure_host_link(ctypes.c_void_p(host_in), ctypes.c_void_p(host_out), nbytes, ctypes.byref(a),
+                                      ctypes.byref(b), ctypes.byref(c)), "wf_measure_host_link")
+    return a.value, b.value, c.value
 
 
 def wf_set_wait_limit(h, seconds: float) -> None:

@@ -67,6 +67,11 @@ def test_argument_validation_without_device(libpath):
     assert L.wf_batch_set_states_f32(None, None, None, 0) == wf.WF_EINVAL
     assert L.wf_batch_get_states(None, None, None, 0) == wf.WF_EINVAL
     assert L.wf_batch_get_states_f32(None, None, None, 0) == wf.WF_EINVAL
+    d = ctypes.c_double()
+    buf = ctypes.create_string_buffer(64)
+    assert L.wf_measure_host_link(None, buf, 64, ctypes.byref(d), ctypes.byref(d), ctypes.byref(d)) == wf.WF_EINVAL
+    assert L.wf_measure_host_link(buf, buf, 0, ctypes.byref(d), ctypes.byref(d), ctypes.byref(d)) == wf.WF_EINVAL
+    assert L.wf_measure_host_link(buf, buf, 64, None, ctypes.byref(d), ctypes.byref(d)) == wf.WF_EINVAL
     L.wf_destroy(None)
 
 

@@ -87,3 +87,14 @@ def test_throughput_helpers_single_rank():
     assert max(len(p) for p in parts) - min(len(p) for p in parts) <= 1
     assert bench._percentile([1.0, 2.0, 3.0, 4.0], 0.5) == pytest.approx(2.5)
     assert bench._percentile([1.0, 2.0, 3.0, 4.0], 0.99) == pytest.approx(3.97)
+
+
+def test_link_bound_takes_the_slowest_constraint():
+    # 136 MB each way: 0.648 ms in at 210 GB/s, 0.708 ms out at 192 GB/s, 0.802 ms for both at
+    # 339 GB/s combined; the bound is the largest
+    r = bench.link_bound((210.0, 192.0, 339.0), 136_000_000, 136_000_000, 1.6)
+    assert r["bound_ms_per_step"] == pytest.approx(272e6 / 339e9 * 1e3)
+    assert r["frac"] == pytest.approx(r["bound_ms_per_step"] / 1.6)
+    # a one-way step is bound by its own direction
+    r = bench.link_bound((210.0, 192.0, 339.0), 136_000_000, 0, 1.0)
+    assert r["bound_ms_per_step"] == pytest.approx(136e6 / 210e9 * 1e3)
