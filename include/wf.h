@@ -348,9 +348,12 @@ int wf_batch_get_states_f32(wf_handle* h, float* T, float* fuel, size_t n);
  * slot's state from T_in, fuel_in, `steps` steps of every active slot, every
  * slot's state into T_out, fuel_out (slot-major [S][Ny][Nx], float64 or,
  * the _f32 call, float32; out may equal in).  The slots are taken in `groups`
- * groups of consecutive slots (1..8, at most S) pipelined over three streams:
- * group g's upload overlaps the steps of group g-1 and the download of group
- * g-2, so that the host copies hide behind the steps.  Each group's steps are
+ * groups of consecutive slots (1..8, at most S) pipelined over four streams
+ * (upload, download, and two compute streams that the groups alternate on):
+ * group g's upload overlaps the steps of groups g-1 and g-2 and the downloads
+ * of earlier groups, so that the host copies hide behind the steps, and
+ * neighbouring groups' steps run side by side (each group's first quadrature
+ * after the previous group's).  Each group's steps are
  * the per-pass launches over its slots (the same operations as wf_step: the
  * results are bit for bit those of wf_batch_set_states, wf_step,
  * wf_batch_get_states).  Uses the staging area of the calls above; waits for

@@ -1413,12 +1413,13 @@ static int batch_states(wf_handle* h, const void* Tin, const void* Fin, void* To
     return WF_OK;
 }
 
-// End-to-end run from host arrays, the slots in groups pipelined over three streams: the upload
-// stream copies group g's host arrays into its part of the staging area, the handle's stream
-// converts them into the slots' pitched fields, steps the group (its per-slot pointers rebased to
-// its first slot, as in step form 3) and converts the results back into the staging part, and the
-// download stream copies them out.  Group g's upload runs beside group g-1's steps and group g-2's
-// download.
+// End-to-end run from host arrays, the slots in groups pipelined over four streams: the upload
+// stream copies group g's host arrays into its part of the staging area, a compute stream (the
+// handle's stream for even groups, the second group stream for odd ones) converts them into the
+// slots' pitched fields, steps the group (its per-slot pointers rebased to its first slot, as in
+// step form 3) and converts the results back into the staging part, and the download stream copies
+// them out.  Group g's upload runs beside the steps of groups g-1 and g-2 and the downloads of
+// earlier groups.
 static int batch_run(wf_handle* h, const void* Tin, const void* Fin, void* Tout, void* Fout, size_t n, int steps,
                      int groups, int host32) {
     const size_t per = (size_t)h->Nx * h->Ny;
@@ -1452,31 +1453,45 @@ static int batch_run(wf_handle* h, const void* Tin, const void* Fin, void* Tout,
     cudaEvent_t* ev_in = h->ev_io;
     cudaEvent_t* ev_done = h->ev_io + 8;
     cudaEvent_t ev_start = h->ev_io[16], ev_end = h->ev_io[17];
+    // compute streams: the groups alternate between the handle's stream and the second group
+    // stream, so that a group's conversions and steps run beside its neighbour's (whose kernels fill
+    // the other's last waves); each group's first quadrature starts after the previous group's, as
+    // in step form 3
+    const bool two = G >= 2 && h->gs && !h->profiling;
     cudaError_t e = cudaEventRecord(ev_start, s);  // after the handle's earlier work
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sin, ev_start, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, ev_start, 0);
+    if (e == cudaSuccess && two) e = cudaStreamWaitEvent(h->gs, ev_start, 0);
     for (int g = 0; g < G && e == cudaSuccess; ++g) {
         const int z0 = (int)((long)g * h->S / G), cnt = (int)((long)(g + 1) * h->S / G) - z0;
         const size_t off = (size_t)z0 * per * es, bytes = (size_t)cnt * per * es;
+        cudaStream_t cs = (two && (g & 1)) ? h->gs : s;
         for (int f = 0; f < 2 && e == cudaSuccess; ++f)
             e = cudaMemcpyAsync(st[f] + off, hin[f] + off, bytes, cudaMemcpyHostToDevice, sin);
         if (e == cudaSuccess) e = cudaEventRecord(ev_in[g], sin);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_in[g], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_in[g], 0);
         for (int f = 0; f < 2 && e == cudaSuccess; ++f)
             e = launch_convert_batch(1, h->prec, st[f] + off, host32, at(h, dev[f], z0), h->sbytes, cnt, h->Nx,
-                                     h->Ny, h->pitch, s);
+                                     h->Ny, h->pitch, cs);
         if (e == cudaSuccess && steps > 0) {
             h->gz0 = z0;
             h->gn = cnt;
+            h->stream = cs;
             rebase_slots(h, z0);
-            for (int k = 0; k < steps && e == cudaSuccess; ++k) e = enqueue_step(h);
+            for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+                if (two && k == 0 && g > 0) e = cudaStreamWaitEvent(cs, h->ev_q, 0);
+                h->ev_rhs = (two && k == 0) ? h->ev_q : nullptr;
+                if (e == cudaSuccess) e = enqueue_step(h);
+                h->ev_rhs = nullptr;
+            }
             rebase_slots(h, 0);
+            h->stream = s;
             h->gz0 = h->gn = 0;
         }
         for (int f = 0; f < 2 && e == cudaSuccess; ++f)
             e = launch_convert_batch(0, h->prec, st[f] + off, host32, at(h, dev[f], z0), h->sbytes, cnt, h->Nx,
-                                     h->Ny, h->pitch, s);
-        if (e == cudaSuccess) e = cudaEventRecord(ev_done[g], s);
+                                     h->Ny, h->pitch, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_done[g], cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, ev_done[g], 0);
         for (int f = 0; f < 2 && e == cudaSuccess; ++f)
             e = cudaMemcpyAsync(hout[f] + off, st[f] + off, bytes, cudaMemcpyDeviceToHost, sout);
