@@ -7,7 +7,10 @@
   (not the expanded form the oracle uses);
 * the forcing load vector against a brute-force integration with scipy's B-splines;
 * first-order convergence in time of the PR, Strang and explicit schemes with the
-  forcing switched on (the paper's conclusion), on a coarse grid.
+  forcing switched on (the paper's conclusion), on a coarse grid;
+* the study's tools: the L2 projection against an independent projection (scipy's B-splines,
+  numpy's Gauss rule), exact for constants, converging at O(h^(p+1)); the reference norm against
+  the closed form of the modes' integrals; the error norm against a ten-point brute force.
 """
 import numpy as np
 import pytest
@@ -131,3 +134,92 @@ def test_first_order_in_time(scheme):
     errs = [_study_error(scheme, 20, tau) for tau in taus]
     rates = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
     assert all(0.8 < r < 1.3 for r in rates), (errs, rates)
+
+
+# ---- the study's projection and norms, pinned by independent code (scipy's B-splines, numpy's
+# Gauss-Legendre rule, the closed form of the modes' integrals) ----------------------------------
+
+def _open_knots(n, p, L):
+    return np.r_[np.zeros(p), np.linspace(0.0, L, n + 1), np.full(p, L)]
+
+
+def _gauss_points(n, L, q):
+    """Points and weights of the q-point Gauss-Legendre rule on each of n equal elements of [0, L]."""
+    xi, w = np.polynomial.legendre.leggauss(q)
+    h = L / n
+    xs = ((np.arange(n)[:, None] + 0.5 * (xi[None, :] + 1.0)) * h).ravel()
+    return xs, np.tile(0.5 * h * w, n)
+
+
+def _design(xs, n, p, L):
+    return BSpline.design_matrix(xs, _open_knots(n, p, L), p).toarray()  # (points, n + p)
+
+
+def test_projection_equals_an_independent_l2_projection():
+    # rectangular domain and grid, so a transposed operand fails
+    m = Manufactured(Lx=100.0, Ly=60.0)
+    nx, ny, p, t = 7, 5, 2, 0.3
+    tx, ty = ElementTables(nx, p, 100.0), ElementTables(ny, p, 60.0)
+    C = m.project(tx, ty, t)
+    xs, wx = _gauss_points(nx, 100.0, p + 1)
+    ys, wy = _gauss_points(ny, 60.0, p + 1)
+    Bx, By = _design(xs, nx, p, 100.0), _design(ys, ny, p, 60.0)
+    Mx, My = Bx.T @ (wx[:, None] * Bx), By.T @ (wy[:, None] * By)
+    U = m.fields(xs[None, :], ys[:, None], t)[0]  # (y, x)
+    b = By.T @ (wy[:, None] * U * wx[None, :]) @ Bx  # int u* B_i(x) B_j(y), (Ny, Nx)
+    ref = np.linalg.solve(My, np.linalg.solve(Mx, b.T).T)
+    assert C.shape == (ny + p, nx + p)
+    assert np.abs(C - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_projection_of_a_constant_is_exact():
+    # B-splines sum to one: the constant's coefficients are the constant
+    m = Manufactured(modes=(), base=300.0)
+    tx, ty = ElementTables(6, 3, 100.0), ElementTables(4, 3, 100.0)
+    C = m.project(tx, ty, 0.0)
+    assert np.abs(C - 300.0).max() <= 1e-10
+
+
+def test_reference_norm_matches_the_closed_form():
+    # over whole periods: int (1 - cos kx) = L, int (1 - cos k x)(1 - cos k' x) = L + L/2 [k = k']
+    m = Manufactured(Lx=100.0, Ly=80.0)
+    t = 0.25
+    tx, ty = ElementTables(20, 2, 100.0), ElementTables(16, 2, 80.0)
+    _, ref = m.l2_norms(tx, ty, np.zeros((16 + 2, 20 + 2)), t)
+    Lx, Ly, base = 100.0, 80.0, 300.0
+    amp = [(a * np.exp(-lam * t), n, mm) for a, n, mm, lam in m.modes]
+    sq = base * base * Lx * Ly + 2.0 * base * Lx * Ly * sum(e for e, _, _ in amp)
+    for ea, na, ma in amp:
+        for eb, nb, mb in amp:
+            sq += ea * eb * (Lx + 0.5 * Lx * (na == nb)) * (Ly + 0.5 * Ly * (ma == mb))
+    assert ref == pytest.approx(np.sqrt(sq), rel=1e-12)
+
+
+def test_error_norm_matches_brute_force():
+    m = Manufactured(Lx=100.0, Ly=60.0)
+    nx, ny, p, t = 9, 6, 2, 0.1
+    tx, ty = ElementTables(nx, p, 100.0), ElementTables(ny, p, 60.0)
+    rng = np.random.default_rng(7)
+    C = 300.0 + 50.0 * rng.standard_normal((ny + p, nx + p))
+    err, _ = m.l2_norms(tx, ty, C, t)
+    # ten points per element: far more accurate than the oracle's p + 4
+    xs, wx = _gauss_points(nx, 100.0, 10)
+    ys, wy = _gauss_points(ny, 60.0, 10)
+    uh = _design(ys, ny, p, 60.0) @ C @ _design(xs, nx, p, 100.0).T
+    d = uh - m.fields(xs[None, :], ys[:, None], t)[0]
+    ref = np.sqrt((wy[:, None] * d * d * wx[None, :]).sum())
+    assert err == pytest.approx(ref, rel=1e-9)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_projection_error_converges_at_order_p_plus_one(p):
+    # the L2 projection onto splines of degree p approximates a smooth function to O(h^(p+1))
+    # (grids fine enough for the asymptotic rate: at least eight elements per shortest wavelength)
+    m = Manufactured()
+    errs = []
+    for n in (32, 64, 128):
+        tx = ElementTables(n, p, 100.0)
+        e, _ = m.l2_norms(tx, tx, m.project(tx, tx, 0.0), 0.0)
+        errs.append(e)
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(r - (p + 1)) < 0.15 for r in rates), (errs, rates)
