@@ -5,7 +5,9 @@
 * the closed-form interior rows of M (values of the cardinal B-spline of
   degree 2p+1 at the integers, times h);
 * integral identities: M 1 = int B_i = (t_{i+p+1} - t_i)/(p+1), K 1 = 0,
-  G 1 = 0 and G + G^T = e_last e_last^T - e_0 e_0^T (integration by parts).
+  G 1 = 0 and G + G^T = e_last e_last^T - e_0 e_0^T (integration by parts);
+* the Gauss rule: closed-form nodes and weights of the 1- to 3-point rules, exactness up to degree
+  2q - 1 and the closed-form remainder at degree 2q.
 """
 import numpy as np
 import pytest
@@ -134,3 +136,30 @@ def test_neumann_eigenvalues_converge():
         errs.append(abs(lam[3] - (3 * np.pi / L) ** 2) / (3 * np.pi / L) ** 2)
     # quadratic splines: eigenvalue error O(h^4)
     assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10
+
+
+def test_gauss_rule_closed_forms_and_exactness():
+    # nodes and weights of the 1-, 2- and 3-point rules on [0, 1] in closed form (roots of the
+    # shifted Legendre polynomials), and exactness of the q-point rule for x^k, k <= 2q - 1
+    from oracle.bspline import gauss01
+
+    x, w = gauss01(1)
+    assert np.allclose(x, [0.5], rtol=0, atol=1e-15) and np.allclose(w, [1.0], rtol=0, atol=1e-15)
+    x, w = gauss01(2)
+    d = 0.5 / np.sqrt(3.0)
+    assert np.allclose(np.sort(x), [0.5 - d, 0.5 + d], rtol=0, atol=1e-15)
+    assert np.allclose(w, [0.5, 0.5], rtol=0, atol=1e-15)
+    x, w = gauss01(3)
+    d = 0.5 * np.sqrt(0.6)
+    order = np.argsort(x)
+    assert np.allclose(x[order], [0.5 - d, 0.5, 0.5 + d], rtol=0, atol=1e-15)
+    assert np.allclose(w[order], [5 / 18, 4 / 9, 5 / 18], rtol=0, atol=1e-15)
+    for q in range(1, 8):
+        x, w = gauss01(q)
+        for k in range(2 * q):
+            assert abs((w * x ** k).sum() - 1.0 / (k + 1)) <= 1e-14, (q, k)
+        # x^(2q) leaves the rule's remainder (q!)^4 / ((2q+1) ((2q)!)^2) (its (2q)-th derivative
+        # is (2q)!): the rule has degree exactly 2q - 1
+        from math import factorial
+        rem = factorial(q) ** 4 / ((2 * q + 1) * factorial(2 * q) ** 2)
+        assert (1.0 / (2 * q + 1) - (w * x ** (2 * q)).sum()) == pytest.approx(rem, rel=1e-8, abs=1e-16)
