@@ -85,7 +85,8 @@ typedef struct wf_params {
 
 typedef struct wf_handle wf_handle;
 
-/* Fill *p with the defaults above and Lx = Ly = 100 (m).  Never fails for p != NULL. */
+/* Fill *p with the defaults above (the Table of Sec. 2.2 plus the stated readings) and
+ * Lx = Ly = 100 (m).  Errors: WF_EINVAL for p == NULL, else none. */
 int wf_params_default(wf_params* p);
 
 /*
@@ -100,14 +101,17 @@ int wf_create(int nx, int ny, int p, double dt, const wf_params* params, wf_hand
 
 /*
  * Copy the state from host arrays T and fuel, each n = Nx*Ny float64
- * values ([Ny][Nx]).  Converts to the handle's precision on the device.
+ * values ([Ny][Nx]): the B-spline coefficients of temperature (K) and fuel
+ * fraction (Sec. 3.1; the initial state of Sec. 5 and 7 is given in this
+ * form).  Converts to the handle's precision on the device.
  * Waits for earlier work on the handle's stream.  Errors: WF_EINVAL
  * (NULL pointer or n != Nx*Ny), WF_ECUDA.
  */
 int wf_set_state(wf_handle* h, const double* T, const double* fuel, size_t n);
 
 /*
- * wf_set_state with float32 host arrays (n = Nx*Ny values each, [Ny][Nx]):
+ * wf_set_state with float32 host arrays (n = Nx*Ny values each, [Ny][Nx];
+ * no counterpart in the paper):
  * half the bytes over the host link for a handle that computes in FP32
  * (an FP64 handle widens them).  The arrays are the caller's; pinned
  * memory makes the copy asynchronous to the host.  Same waiting and
@@ -116,7 +120,9 @@ int wf_set_state(wf_handle* h, const double* T, const double* fuel, size_t n);
 int wf_set_state_f32(wf_handle* h, const float* T, const float* fuel, size_t n);
 
 /*
- * Set the explicit, spatially varying part b'(x, y) of the wind:
+ * Set the explicit, spatially varying part b'(x, y) of the wind (the wind
+ * term c_W b.grad T of Sec. 2, split as in Sec. 3: the mean wind b is
+ * implicit in the 1-D operators, the variation b' enters F):
  *   b'_x(x,y) = sum_r fx_r(x) gx_r(y),  b'_y(x,y) = sum_r fy_r(x) gy_r(y),
  * r < rank (0..4), each factor a 1-D spline of the handle's degree and
  * knots given by its coefficients.  `factors` holds, in this order,
@@ -127,7 +133,8 @@ int wf_set_state_f32(wf_handle* h, const float* T, const float* fuel, size_t n);
 int wf_set_wind(wf_handle* h, int rank, const double* factors);
 
 /*
- * Enqueue nsteps >= 0 time steps on the handle's stream and return
+ * Enqueue nsteps >= 0 time steps (Sec. 3.1 / 3.2 / the explicit scheme of
+ * Sec. 6, per the handle's scheme) on the handle's stream and return
  * without waiting.  Steps are replayed from a CUDA graph captured on the
  * first call.  Errors: WF_EINVAL, WF_ECUDA (launch failure).
  */
@@ -156,36 +163,38 @@ int wf_sync(wf_handle* h);
 int wf_set_wait_limit(wf_handle* h, double seconds);
 
 /*
- * Wait for enqueued work and copy the state into host arrays T and fuel
- * (n = Nx*Ny float64 each; either may be NULL to skip it).
- * Errors: WF_EINVAL, WF_ECUDA.
+ * Wait for enqueued work and copy the state (B-spline coefficients of T and
+ * fuel, Sec. 3.1) into host arrays T and fuel (n = Nx*Ny float64 each;
+ * either may be NULL to skip it).  Errors: WF_EINVAL, WF_ECUDA.
  */
 int wf_get_state(wf_handle* h, double* T, double* fuel, size_t n);
 
 /*
  * wf_get_state into float32 host arrays (n = Nx*Ny values each; either
- * may be NULL).  An FP64 handle's state is rounded to float32.  Same
- * waiting and errors as wf_get_state.
+ * may be NULL; no counterpart in the paper).  An FP64 handle's state is
+ * rounded to float32.  Same waiting and errors as wf_get_state.
  */
 int wf_get_state_f32(wf_handle* h, float* T, float* fuel, size_t n);
 
-/* Grid sizes of a handle (any pointer may be NULL).  Errors: WF_EINVAL. */
+/* Grid sizes of a handle (Nx = nx + p, Ny = ny + p coefficients per direction, Sec. 3.1; any
+ * pointer may be NULL).  Errors: WF_EINVAL. */
 int wf_get_dims(const wf_handle* h, int* Nx, int* Ny, int* p, int* precision);
 
 /*
  * Use the caller's CUDA stream (a cudaStream_t passed as void*; NULL
- * restores the handle's own stream).  The captured step graph is kept;
+ * restores the handle's own stream; no counterpart in the paper).  The captured step graph is kept;
  * it is launched on whichever stream is current.  Errors: WF_EINVAL.
  */
 int wf_set_stream(wf_handle* h, void* stream);
 
 /*
- * Per-kernel timing.  With on != 0, wf_step launches its kernels
+ * Per-kernel timing (no counterpart in the paper).  With on != 0, wf_step launches its kernels
  * directly (no graph) with a CUDA event pair around each launch, on the
  * launching stream; wf_kernel_times then returns, per kernel class k <
  * max_k, the summed milliseconds ms[k], the launch count counts[k] and a
  * NUL-terminated name (names[k], up to 47 characters, may be NULL), and
- * resets the sums.  Returns the number of classes (>= 0) or an error.
+ * resets the sums.  Returns the number of classes (>= 0) or an error:
+ * WF_EINVAL (NULL handle, max_k < 0), WF_ECUDA (an event failed).
  */
 int wf_set_profiling(wf_handle* h, int on);
 int wf_kernel_times(wf_handle* h, double* ms, int* counts, char (*names)[48], int max_k);
@@ -231,7 +240,7 @@ int wf_set_mms(wf_handle* h, const wf_mms* m);
 int wf_get_time(wf_handle* h, double* t);
 
 /*
- * Number of time-step kernels the library has launched in this process (every
+ * (No counterpart in the paper.)  Number of time-step kernels the library has launched in this process (every
  * handle, eager launches and graph captures alike; a replayed graph launches
  * again the kernels it captured).  For measurement: the difference over eager
  * steps is the number of kernels one step launches.  Errors: WF_EINVAL.
@@ -309,25 +318,26 @@ int wf_set_tuning(wf_handle* h, const int* shape);
  */
 
 /* Create a batch of `capacity` (1..65535) inactive slots, all with the mean wind
- * of `params`.  Errors as wf_create.  The device memory it holds is reported by
+ * of `params` (the tables and operators of wf_create, Sec. 3.1, per slot; batches
+ * extend Sec. 4 as above).  Errors as wf_create.  The device memory it holds is reported by
  * wf_device_bytes. */
 int wf_batch_create(int nx, int ny, int p, double dt, const wf_params* params, int capacity, wf_handle** out);
 
-/* Load slot `slot`: state T, fuel ([Ny][Nx] float64 each), mean wind (wind_x,
- * wind_y) and wind variation of rank 0..4 (factors as in wf_set_wind, NULL for
- * rank 0).  A new mean wind refactors the slot's operators on the GPU.  Clears
- * the slot's guard flag; does not change whether the slot is active.  Waits for
- * earlier work on the handle's stream.  Errors: WF_EINVAL, WF_ETRUNC,
- * WF_ESINGULAR, WF_ECUDA. */
+/* (Batches extend Sec. 4 as above.) Load slot `slot`: state T, fuel ([Ny][Nx]
+ * float64 each), mean wind (wind_x, wind_y) and wind variation of rank 0..4 (factors
+ * as in wf_set_wind, NULL for rank 0). A new mean wind refactors the slot's
+ * operators on the GPU. Clears the slot's guard flag; does not change whether the
+ * slot is active. Waits for earlier work on the handle's stream. Errors: WF_EINVAL,
+ * WF_ETRUNC, WF_ESINGULAR, WF_ECUDA. */
 int wf_batch_set_slot(wf_handle* h, int slot, const double* T, const double* fuel, double wind_x, double wind_y,
                       int wind_rank, const double* wind_factors);
 
-/* Copy slot `slot`'s state into host arrays (either may be NULL); waits.
- * Errors: WF_EINVAL, WF_ECUDA. */
+/* Copy slot `slot`'s state (B-spline coefficients, Sec. 3.1) into host arrays
+ * (either may be NULL); waits.  Errors: WF_EINVAL, WF_ECUDA. */
 int wf_batch_get_slot(wf_handle* h, int slot, double* T, double* fuel);
 
 /*
- * Every slot's state in one call: T and fuel are host arrays of
+ * Every slot's state in one call (no counterpart in the paper): T and fuel are host arrays of
  * n = S*Nx*Ny values each, slot-major ([S][Ny][Nx]), float64 or (the _f32
  * calls) float32; one copy per field and one conversion over all slots,
  * through a device staging area that the first call allocates (2*n values
@@ -366,16 +376,17 @@ int wf_batch_run(wf_handle* h, const double* T_in, const double* fuel_in, double
 int wf_batch_run_f32(wf_handle* h, const float* T_in, const float* fuel_in, float* T_out, float* fuel_out,
                      size_t n, int steps, int groups);
 
-/* Include (on != 0) or exclude a slot from the following wf_step calls.
+/* Include (on != 0) or exclude a slot from the following wf_step calls (a host
+ * flag, uploaded with the next step; no counterpart in the paper).
  * Errors: WF_EINVAL. */
 int wf_batch_activate(wf_handle* h, int slot, int on);
 
-/* Waits and writes, per slot, its flag word since the last call into
- * status[0 .. capacity-1] (n >= capacity), and clears the flags:
- *   WF_STATUS_UNSTABLE  a temperature became non-finite or exceeded 1e5 K;
- *   WF_STATUS_TIMEOUT   a bounded device wait gave up (the step's output is
- *                       invalid for every slot of the handle);
- * 0 when neither happened.  Errors: WF_EINVAL, WF_ECUDA. */
+/* (The guards have no counterpart in the paper.) Waits and writes, per slot, its
+ * flag word since the last call into status[0 .. capacity-1] (n >= capacity), and
+ * clears the flags: WF_STATUS_UNSTABLE a temperature became non-finite or exceeded
+ * 1e5 K; WF_STATUS_TIMEOUT a bounded device wait gave up (the step's output is
+ * invalid for every slot of the handle); 0 when neither happened. Errors: WF_EINVAL,
+ * WF_ECUDA. */
 #define WF_STATUS_UNSTABLE 1
 #define WF_STATUS_TIMEOUT 4
 int wf_batch_status(wf_handle* h, int* status, int n);
@@ -392,10 +403,11 @@ int wf_batch_status(wf_handle* h, int* status, int n);
  * server run one quantum for slots with different step counts left. */
 int wf_batch_set_budget(wf_handle* h, int slot, int steps);
 
-/* Number of slots of a handle (>= 1), or WF_EINVAL. */
+/* Number of slots of a handle (>= 1), or WF_EINVAL.  No counterpart in the paper. */
 int wf_batch_capacity(const wf_handle* h);
 
-/* Device bytes held by the handle.  Errors: WF_EINVAL. */
+/* Device bytes held by the handle (the layout of its slots and tables).  Errors:
+ * WF_EINVAL.  No counterpart in the paper. */
 int wf_device_bytes(const wf_handle* h, size_t* bytes);
 
 /* Upper bound of the device bytes wf_batch_create would allocate for these
@@ -440,25 +452,30 @@ typedef struct wf_result {
 
 typedef struct wf_server wf_server;
 
-/* Start a server on the current device with a device-memory budget (bytes) and at
- * most max_slots (1..4096) slots per class.  Errors: WF_EINVAL, WF_ENOMEM, WF_ECUDA. */
+/* Start a server (see the section note: no counterpart in the paper) on the current
+ * device with a device-memory budget (bytes) and at most max_slots (1..4096) slots
+ * per class.  Errors: WF_EINVAL, WF_ENOMEM, WF_ECUDA. */
 int wf_server_create(size_t hbm_budget_bytes, int max_slots, wf_server** out);
 
-/* Queue a request; copies its inputs and returns a ticket.  Thread-safe.
- * Errors: WF_EINVAL. */
+/* Queue a request (its steps are those of wf_step for its scheme, Sec. 3); copies its inputs
+ * and returns a ticket.  Thread-safe.  Errors: WF_EINVAL. */
 int wf_submit(wf_server* s, const wf_request* req, uint64_t* ticket);
 
-/* WF_PENDING while the request is queued or running; otherwise fills *res (may be
- * NULL), forgets the ticket and returns the request's status (WF_OK once T_out and
- * fuel_out hold the result).  WF_ENOTFOUND for an unknown or already reported
- * ticket.  Thread-safe, never blocks on the GPU. */
+/* (Serving layer, no counterpart in the paper.) WF_PENDING while the request is
+ * queued or running; otherwise fills *res (may be NULL), forgets the ticket and
+ * returns the request's status (WF_OK once T_out and fuel_out hold the result).
+ * WF_ENOTFOUND for an unknown or already reported ticket. Thread-safe, never blocks
+ * on the GPU. */
 int wf_poll(wf_server* s, uint64_t ticket, wf_result* res);
 
-/* Completed DOF-steps ((nx+p)(ny+p) x steps summed over finished requests), number
- * of finished requests and device bytes held by the server's batch handles. */
+/* (Serving layer, no counterpart in the paper.) Completed DOF-steps ((nx+p)(ny+p) x
+ * steps summed over finished requests), number of finished requests and device bytes
+ * held by the server's batch handles (any pointer may be NULL). Thread-safe. Errors:
+ * WF_EINVAL (NULL server). */
 int wf_server_stats(wf_server* s, double* dof_steps, uint64_t* completed, size_t* hbm_used);
 
-/* Stop the worker (running requests are abandoned) and free everything. */
+/* Stop the worker (running requests are abandoned) and free everything (NULL is
+ * accepted).  No return value.  No counterpart in the paper. */
 void wf_server_destroy(wf_server* s);
 
 /*
@@ -511,10 +528,12 @@ int wf_measure_fma_peak(int precision, double* tflops);
 int wf_measure_host_link(const void* host_in, void* host_out, size_t bytes, double* gbs_h2d, double* gbs_d2h,
                          double* gbs_both);
 
-/* Free every resource of the handle (NULL is accepted). */
+/* Free every resource of the handle (NULL is accepted).  No return value; the
+ * handle must not be used afterwards.  No counterpart in the paper. */
 void wf_destroy(wf_handle* h);
 
-/* Static text for a status code. */
+/* Static text for a status code (unknown codes included); never NULL.  No
+ * counterpart in the paper. */
 const char* wf_strerror(int code);
 
 #ifdef __cplusplus
