@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI (no GPU needed).
 
-* libwf.so builds for sm_103a and exports every function include/wf.h declares;
+* libwf.so builds for sm_103a and exports every function include/wf.h declares, each documented
+  with its passage of the paper (or that it has none) and its errors;
 * the calls that need no device behave as documented: defaults, error strings,
   argument validation before any CUDA call, and WF_ECUDA (not a crash) when no
   device is present.
@@ -31,6 +32,22 @@ def test_exports_every_declared_symbol(libpath, repo_root):
     assert "wf_create" in names and "wf_step" in names
     missing = [n for n in names if not hasattr(L, n)]
     assert not missing, missing
+
+
+def test_every_declaration_is_documented(repo_root):
+    # the comment above each declaration cites the paper's passage or says that it has none, and
+    # states the call's errors (or that it returns none)
+    src = open(os.path.join(repo_root, "include", "wf.h")).read()
+    undocumented = []
+    for m in re.finditer(r"^(?:int|void|const char\*)\s+(wf_\w+)\(", src, re.M):
+        before = src[:m.start()]
+        end = before.rfind("*/")
+        comment = before[before.rfind("/*", 0, end):end]
+        cites = "Sec." in comment or "counterpart" in comment or "paper" in comment
+        errors = any(k in comment for k in ("Errors", "WF_E", "error", "No return value", "never NULL"))
+        if not (cites and errors):
+            undocumented.append(m.group(1))
+    assert not undocumented, undocumented
 
 
 def test_defaults_and_strings(libpath):
