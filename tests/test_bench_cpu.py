@@ -1,5 +1,6 @@
 """The measurement's arithmetic, on the CPU: the algorithmic counts behind `roofline`, the bound it
-picks, the traffic records' source check and the throughput helpers.
+picks, the traffic records' source check, the throughput helpers, the host-link bound, and the
+reference arm's JSON line (the FP64 oracle on the host cores, which needs no GPU).
 
 The counts are restated here by hand for p = 2 (q = 3 Gauss points, bands of W = 5), so a change of
 the bench's formula that moves a figure fails a test rather than the roofline silently.
@@ -98,3 +99,23 @@ def test_link_bound_takes_the_slowest_constraint():
     # a one-way step is bound by its own direction
     r = bench.link_bound((210.0, 192.0, 339.0), 136_000_000, 0, 1.0)
     assert r["bound_ms_per_step"] == pytest.approx(136e6 / 210e9 * 1e3)
+
+
+def test_reference_arm_prints_the_contract_line():
+    # the reference arm is the FP64 oracle on the host cores: it runs without a GPU
+    import subprocess
+    import sys
+
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=bench.ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT and line["higher_is_better"] is True
+    assert line["steps"] == 1 and line["warmup"] == 3          # at least three warm-up steps, as run
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+    assert line["config"]["workload"] == "c4_ensemble_256x256x256_p2_pr"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
