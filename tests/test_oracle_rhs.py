@@ -25,7 +25,7 @@ def _raw_source(T, phi, prm):
     inv = 1.0 / (prm.rho * prm.cp)
     delta = 1.0 if (T > prm.T_ig and phi > prm.fuel_thresh + prm.thresh_guard) else 0.0
     r = delta * prm.A_r * T * math.exp(-prm.T_a / T)
-    Rc = -1e4 * prm.rho * prm.ch * prm.hc * prm.M_ratio * r
+    Rc = -1e4 * prm.rho * prm.ch * prm.hc * prm.M_ratio * r * (phi if prm.scale_heat_by_fuel else 1.0)
     Qconv_explicit = prm.chi * prm.T_amb
     Qrz = prm.sigma * prm.eps / prm.delta_z * (prm.T_amb ** 4 - T ** 4)
     s = (Rc + Qconv_explicit + Qrz) * inv
@@ -34,8 +34,8 @@ def _raw_source(T, phi, prm):
     return s, flux_coef, fval
 
 
-@pytest.mark.parametrize("p", [2, 3])
-def test_load_vectors_brute_force(p):
+@pytest.mark.parametrize("p,heat_by_fuel", [(1, False), (2, False), (3, False), (2, True)])
+def test_load_vectors_brute_force(p, heat_by_fuel):
     nx, ny = 3, 2
     Lx, Ly = 4.6875, 3.125
     Nx, Ny = nx + p, ny + p
@@ -46,7 +46,7 @@ def test_load_vectors_brute_force(p):
     R = 2
     fx, gx = rng.normal(size=(R, Nx)), rng.normal(size=(R, Ny))
     fy, gy = rng.normal(size=(R, Nx)), rng.normal(size=(R, Ny))
-    prm = Params()
+    prm = Params(scale_heat_by_fuel=heat_by_fuel)
     tau = 1e-3
     F, Phi = load_vectors(tx, ty, T, phi, prm, tau, (fx, gx, fy, gy))
 
