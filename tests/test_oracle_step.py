@@ -7,7 +7,8 @@
   th = tau/2; one Strang step by [(1 - tau C_d l_x/4)/(1 + tau C_d l_x/4)]^2 (1 - tau C_d l_y/2)/(1 + tau C_d l_y/2);
   one explicit L2-projection step by 1 - tau C_d (l_x + l_y).
 * A spatially uniform state follows the scalar recurrences derived from the schemes
-  (source recomputed from raw Table constants, not from the oracle).
+  (source recomputed from raw Table constants, not from the oracle), for PR also with the
+  second substep's F evaluated at T*.
 * The ambient state T = T_amb is steady for any wind and fuel.
 * With zero wind and only diffusion (linear and T^3), the heat content
   1^T (M (x) M) T is conserved.
@@ -40,6 +41,17 @@ def _uniform_pr(T, phi, prm, tau):
     s, r = _raw_s(T, phi, prm)
     Ts = (T + th * s) / (1 + th * c_chi)
     Tn = (1 - th * c_chi) * Ts + th * s
+    return Tn, phi * (1 - tau * 3e2 * r)
+
+
+def _uniform_pr_per_substep(T, phi, prm, tau):
+    # the second substep's F is evaluated at T* (with the step's starting fuel)
+    c_chi = prm.chi / (prm.rho * prm.cp)
+    th = tau / 2
+    s, r = _raw_s(T, phi, prm)
+    Ts = (T + th * s) / (1 + th * c_chi)
+    s2, _ = _raw_s(Ts, phi, prm)
+    Tn = (1 - th * c_chi) * Ts + th * s2
     return Tn, phi * (1 - tau * 3e2 * r)
 
 
@@ -132,6 +144,22 @@ def test_uniform_state_recurrence(scheme, T, phi):
     Te, pe = f(T, phi, prm, sc.dt)
     assert np.abs(Tn / Te - 1).max() < 1e-12
     assert np.abs(pn / pe - 1).max() < 1e-12
+
+
+@pytest.mark.parametrize("T,phi", [(1000.0, 0.8), (790.0, 0.8), (500.0, 0.9)])
+def test_uniform_state_recurrence_f_per_substep(T, phi):
+    # (burning, just below ignition, and cool)
+    sc = make_scenario("u", 5, 2, 2e-3, 1, 3, wind=(1.0, 0.5))
+    prm = Params(F_timing="per_substep")
+    P = Problem.from_scenario(sc, prm=prm, scheme="pr", mode="direct")
+    shape = sc.T0.shape
+    Tn, pn = P.step(np.full(shape, T), np.full(shape, phi))
+    Te, pe = _uniform_pr_per_substep(T, phi, prm, sc.dt)
+    assert np.abs(Tn / Te - 1).max() < 1e-12
+    assert np.abs(pn / pe - 1).max() < 1e-12
+    # and it differs from the one-F step (the T^4 loss and the reaction change with T)
+    To, _ = _uniform_pr(T, phi, Params(), sc.dt)
+    assert abs(Te - To) > 0
 
 
 @pytest.mark.parametrize("scheme", ["pr", "strang", "explicit"])
